@@ -1,0 +1,404 @@
+"""Benchmark of the pseudo-spectral stochastic-PDE step on GB300.
+
+Workload (default): 2D Model B (Cahn-Hilliard) with conserved noise on a
+periodic 1024 x 1024 lattice, FP32 fields / complex64 spectra, dx = 1,
+dt = 0.01, a = -1, b = 1, K = 1, D = 0.01 (noise D q^2), 2/3-rule de-aliasing,
+phi_0 i.i.d. uniform in [-0.1, 0.1] from Philox seed 2405; runs of 1000 steps
+between outputs.  One bench "step" is one time step of that system.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line.  ``--impl reference`` times the FP64 CPU oracle on the
+host cores instead (bounded sample of the same workload).  With N > 1 (under
+torchrun) every rank runs an independent replica (the single-system path does
+not shard); value = all ranks' site-steps / the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "site-steps/s, Model B FP32 1024² & 256³, vs HBM roofline; adjoint/forward time"
+UNIT = "site-steps/s"
+WORKLOAD = dict(shape=(1024, 1024), dt=0.01, a=-1.0, b=1.0, K=1.0, D=0.01, seed=2405, lo=-0.1, hi=0.1)
+INTERVAL = 1000        # steps between outputs (and between L2 flushes)
+L2_FLUSH_BYTES = 512 << 20
+
+
+def algorithmic_bytes_2d(nx, ny, order=2, csize=8):
+    """Per-launch compulsory HBM bytes of the two kernels of a 2D step.
+
+    k_col: read T2 + read phi + write phi (all M modes) + write T1 (kept columns);
+    k_row: read T1 (kept columns) + write T2 (all modes).  M = (nx/2+1) ny.
+    """
+    hx = nx // 2 + 1
+    M = hx * ny
+    kept = (nx - 1) // (order + 1) + 1
+    f = kept / hx
+    return {"col": csize * M * (3 + f), "row": csize * M * (1 + f), "step": csize * M * (4 + 2 * f)}
+
+
+def algorithmic_bytes_3d(nx, ny, nz, order=2, csize=8):
+    """Per field-step bytes of the four kernels of a 3D step (z-fused column, y inverse, x rows, y forward)."""
+    hx = nx // 2 + 1
+    M = hx * ny * nz
+    fx = ((nx - 1) // (order + 1) + 1) / hx
+    fy = (2 * ((ny - 1) // (order + 1)) + 1) / ny
+    col = csize * M * (3 + fx * fy)
+    mid_inv = csize * M * (fx * fy + fx)
+    row = csize * M * (fx + 1)
+    mid_fwd = csize * M * 2
+    return {"col": col, "mid_inv": mid_inv, "row": row, "mid_fwd": mid_fwd,
+            "step": col + mid_inv + row + mid_fwd}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2405_02410_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, name), "rb") as fh:
+            h.update(name.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the current kernels."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+            rec = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    if rec.get("source_hash") != kernel_source_hash():
+        return None
+    return rec.get("kernels", {}).get(kernel)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            p = [x.strip() for x in l.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (replicas)
+# ---------------------------------------------------------------------------
+def dist_setup(n_gpus):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if torch.cuda.is_available() and dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# the CPU oracle leg
+# ---------------------------------------------------------------------------
+def oracle_rate(shape, steps, budget_s=20.0):
+    """Site-steps/s of the FP64 oracle (one thread) on the Model B workload, bounded to ~budget_s."""
+    from oracle import oracle as O
+    w = WORKLOAD
+    m = O.model_b(shape, dt=w["dt"], a=w["a"], b=w["b"], K=w["K"], D=w["D"], seed=w["seed"])
+    phi = O.to_spectrum(m, O.init_uniform(m, w["lo"], w["hi"]))
+    t0 = time.perf_counter()
+    phi = O.run(m, phi, 0, 1)
+    t1 = time.perf_counter()
+    per = t1 - t0
+    n = max(1, min(steps, int(budget_s / max(per, 1e-9))))
+    t0 = time.perf_counter()
+    O.run(m, phi, 1, n)
+    dt = time.perf_counter() - t0
+    sites = 1
+    for s in shape:
+        sites *= s
+    return sites * n / dt, n, dt
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup(args.gpus)
+    if rank != 0:
+        return 0
+    shape = WORKLOAD["shape"]
+    sites = shape[0] * shape[1]
+    # warm-up: one oracle step (the oracle has no caches to warm beyond that)
+    rate, n, dt = oracle_rate(shape, max(1, args.steps), budget_s=float(os.environ.get("PSS_REF_BUDGET_S", "60")))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / n,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "2D Model B 1024x1024 (FP64 CPU oracle)", "global_batch": 1, "seq_len": sites,
+                   "parallelism": "replicas"},
+        "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{n} oracle steps of the 1024x1024 Model B workload (single thread, C, FP64)"},
+        "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# the GPU arm
+# ---------------------------------------------------------------------------
+def make_system(pss, shape, precision="f32"):
+    w = WORKLOAD
+    s = pss.model_b(shape, dt=w["dt"], a=w["a"], b=w["b"], K=w["K"], D=w["D"], seed=w["seed"],
+                    precision=precision)
+    return s
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    world, rank, local = dist_setup(args.gpus)
+    assert torch.cuda.is_available(), "the GPU arm needs CUDA"
+    torch.cuda.set_device(local)
+    from paper_2405_02410_gb300 import build
+    build.build()
+    from paper_2405_02410_gb300 import pss
+
+    w = WORKLOAD
+    shape = w["shape"]
+    sites = shape[0] * shape[1]
+    stream = torch.cuda.Stream()
+    s = make_system(pss, shape)
+    s.set_stream(stream)
+    s.init_uniform(0, w["lo"], w["hi"])
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    # warm-up (graph capture, clocks)
+    with torch.cuda.stream(stream):
+        s.step(args.warmup)
+    torch.cuda.synchronize()
+
+    K = args.steps
+    chunks = []
+    left = K
+    while left > 0:
+        chunks.append(min(INTERVAL, left))
+        left -= chunks[-1]
+    launches0 = s.launch_count
+    total_ms = 0.0
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for c in chunks:
+            with torch.cuda.stream(stream):
+                flush.fill_(1.0)                          # L2 flush, outside the timed events
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                s.step(c)
+                e1.record(stream)
+            e1.synchronize()
+            total_ms += e0.elapsed_time(e1)
+    torch.cuda.synchronize()
+    barrier(world)
+    launches = s.launch_count - launches0
+    s.sync()
+    t_max = max_over_ranks(total_ms, world)
+    value = sites * K * world / (t_max * 1e-3)
+    ms_per_step = t_max / K
+
+    # per-kernel durations (CUDA events around each launch, same stream)
+    kern_ms = s.time_kernels(200)
+    ab = algorithmic_bytes_2d(shape[1], shape[0])
+    peaks, peak_kind = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    names = {0: "col", 2: "row"}
+    dom = max((0, 2), key=lambda k: kern_ms[k])
+    dom_name = names[dom]
+    achieved = ab[dom_name] / (kern_ms[dom] * 1e-3) / 1e9
+    traffic = recorded_traffic("k_col" if dom == 0 else "k_row")
+
+    # end to end through the public API with host buffers: pinned upload of phi_0,
+    # steps, S(q) to the host every INTERVAL steps, final field to the host
+    host_in = torch.empty(shape, dtype=torch.float32).pin_memory()
+    host_in.numpy()[:] = np.random.default_rng(w["seed"]).uniform(w["lo"], w["hi"], size=shape)
+    host_out = torch.empty(shape, dtype=torch.float32).pin_memory()
+    s2 = make_system(pss, shape)
+    s2.set_stream(stream)
+    s2.set_field(0, host_in.numpy())
+    with torch.cuda.stream(stream):
+        s2.step(args.warmup)
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    s2.set_field(0, host_in.numpy())
+    nb = 64
+    for c in chunks:
+        s2.step(c)
+        s2.structure_factor(0, nb)
+    s2.get_field(0, host_out.numpy())
+    torch.cuda.synchronize()
+    t_e2e = max_over_ranks(time.perf_counter() - t0, world)
+    h2d = 4 * sites
+    d2h = 4 * sites + len(chunks) * (2 * nb + 2) * 8
+
+    # secondary: 3D 256^3 Model A + Model B pair (two fields), FP32
+    extra = {}
+    if not args.no_3d:
+        s3 = pss.System((256, 256, 256), dt=0.005, seed=w["seed"], precision="f32")
+        pss.add_model_a_field(s3, a=-1, b=1, K=1, D=0.05, name="psi")
+        pss.add_model_b_field(s3, a=-1, b=1, K=1, D=0.05, name="phi")
+        s3.set_stream(stream)
+        s3.init_uniform(0, -0.05, 0.05)
+        s3.init_uniform(1, -0.05, 0.05)
+        with torch.cuda.stream(stream):
+            s3.step(20)
+            n3 = 200
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s3.step(n3)
+            e1.record(stream)
+        e1.synchronize()
+        ms3 = e0.elapsed_time(e1) / n3
+        k3 = s3.time_kernels(20)
+        ab3 = algorithmic_bytes_3d(256, 256, 256)
+        extra["model_ab_256cubed"] = {
+            "site_steps_per_s_per_field": 256 ** 3 * 2 / (ms3 * 1e-3),
+            "ms_per_step_two_fields": ms3,
+            "algorithmic_bytes_per_field_step": ab3["step"],
+            "hbm_frac_of_measured": (2 * ab3["step"] / (ms3 * 1e-3) / 1e9) / hbm,
+            "kernel_ms_two_fields": {"col": k3[0], "mid_inv": k3[1], "row": k3[2], "mid_fwd": k3[3]},
+        }
+        s3.close()
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
+        "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "2D Model B 1024x1024, FP32, dt=0.01, a=-1, b=1, K=1, D=0.01 (noise D q^2), "
+                               "2/3 de-aliasing, output every 1000 steps",
+                   "global_batch": world, "seq_len": sites, "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "flushed (512 MiB write) before every 1000-step interval; the ~11 MB working set is "
+                         "L2-resident inside an interval"},
+        "roofline": {"bound": "hbm", "kernel": "k_col" if dom == 0 else "k_row", "achieved": achieved,
+                     "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
+                     "peak_source": f"{peak_kind} hbm_gbs", "step_frac": (ab["step"] / (ms_per_step * 1e-3) / 1e9) / hbm,
+                     "kernel_ms": {"col": kern_ms[0], "row": kern_ms[2]},
+                     "algorithmic_bytes": {"col": ab["col"], "row": ab["row"], "step": ab["step"]}},
+        "e2e": {"value": sites * K * world / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d / K,
+                "d2h_bytes_per_step": d2h / K},
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+        "extra": extra,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        rate, n, dt = oracle_rate(shape, 1000, budget_s=float(os.environ.get("PSS_CPU_BUDGET_S", "15")))
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"{n} steps of the 1024x1024 Model B workload, FP64 C oracle, 1 thread"}
+    s.close()
+    s2.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10000)
+    ap.add_argument("--warmup", type=int, default=100)
+    ap.add_argument("--impl", default="pss", choices=["pss", "reference"])
+    ap.add_argument("--no-3d", action="store_true", help="skip the 256^3 secondary measurement")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

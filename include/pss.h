@@ -1,0 +1,160 @@
+/*
+ * pss.h -- C ABI of libpss, the GB300 (sm_103a) implementation of one time
+ * step of the cuPSS pseudo-spectral method (arXiv:2405.02410) for stochastic
+ * PDEs on periodic 1D/2D/3D lattices.
+ *
+ * The calls follow the paper's recipe for building a model (section "Writing
+ * models"): create a system (lattice size, spacing, time step), add named
+ * parameters, add fields, add the implicit ("lhs") and explicit ("rhs") terms
+ * of each field's equation "dt phi + lhs = rhs", add noise, set an initial
+ * condition, then evolve.  Equations are given as structured terms instead of
+ * strings.
+ *
+ * One time step (section "What cuPSS calculates", Eq. timeupdate) of every
+ * dynamic field phi:
+ *     phi_q <- (phi_q + dt M(q) P_q + xi_q) / (1 + dt O(q))
+ * with O(q) = sum_m c_m (q^2)^p_m the implicit operator (L~ = -O),
+ * M(q) the explicit operator, P_q = F[(F^-1[m phi])^p] the pseudo-spectral
+ * product of the de-aliased field (section "De-aliasing"), and xi_q the noise
+ * of strength D~(q) = D (q^2)^r (Eq. noise_eq, section "Adding noise").
+ *
+ * Conventions
+ *   - sizes: nx is the contiguous axis; every used axis is a power of two in
+ *     [4, 1024]; unused axes are 1.  Real fields are [nz][ny][nx] row-major.
+ *   - spectra exchanged with the caller are the R2C half spectrum
+ *     [nz][ny][nx/2+1] of complex values (interleaved re, im), forward DFT
+ *     unnormalised, inverse with 1/(nx ny nz).
+ *   - precision PSS_F32: real fields float, spectra float2; PSS_F64: double,
+ *     double2.  Arithmetic runs in that precision on the GPU.
+ *   - "where" PSS_HOST: the pointer is host memory (copied synchronously);
+ *     PSS_DEVICE: device memory of the system's device, used on the system's
+ *     stream.
+ *   - ownership: the system owns every device buffer it allocates; caller
+ *     buffers are only read or written during the call.
+ *   - errors: every call returns PSS_OK (0) or a negative pss_status and sets
+ *     a message readable with pss_last_error().  Nothing throws across the
+ *     ABI.  Errors found on the device (non-finite values) are reported by the
+ *     next call that synchronises (pss_get_*, pss_sync).
+ *   - thread safety: one handle must not be used from two threads at once.
+ */
+#ifndef PSS_H
+#define PSS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pss_system pss_system;
+
+typedef enum {
+    PSS_OK = 0,
+    PSS_EINVAL = -1,        /* bad argument */
+    PSS_ENOMEM = -2,        /* device allocation failed */
+    PSS_ECUDA = -3,         /* a CUDA call failed */
+    PSS_ETIMEOUT = -4,      /* a bounded device wait ran out */
+    PSS_ENONFINITE = -5,    /* a field became NaN or Inf */
+    PSS_EUNSUPPORTED = -6   /* valid, but outside what this build implements */
+} pss_status;
+
+enum { PSS_F32 = 0, PSS_F64 = 1 };
+enum { PSS_HOST = 0, PSS_DEVICE = 1 };
+
+/* Create a system on the current CUDA device ("evolver(dim, Nx, Ny, dx, dy,
+ * dt, output)" of section "Example").  dim in {1,2,3}; seed keys the Philox
+ * generator of the noise and of pss_init_uniform; precision PSS_F32/PSS_F64.
+ * *out receives the handle (NULL on failure). */
+int pss_create_system(pss_system **out, int dim, int nx, int ny, int nz,
+                      double dx, double dy, double dz, double dt,
+                      uint64_t seed, int precision);
+/* Free every device buffer and the handle.  NULL is accepted. */
+int pss_destroy_system(pss_system *s);
+/* Launch all work on this cudaStream_t (NULL = legacy default stream). */
+int pss_set_stream(pss_system *s, void *cuda_stream);
+
+/* Named scalar parameter ("addParameter", section "Writing models"); *id
+ * receives its index.  A parameter may be changed later with pss_set_param;
+ * the change applies from the next step on. */
+int pss_add_param(pss_system *s, const char *name, double value, int *id);
+int pss_set_param(pss_system *s, int id, double value);
+int pss_get_param(pss_system *s, int id, double *value);
+
+/* Add a field ("createField(name, dynamic)").  Only dynamic fields are
+ * implemented (dynamic = 1; 0 returns PSS_EUNSUPPORTED).  At most 4 fields.
+ * Fields start at zero. */
+int pss_add_field(pss_system *s, const char *name, int dynamic, int *field_id);
+
+/* Add a term to the equation of field_id.  The term's operator is
+ *     sum_{m < n_mono} scales[m] * param[param_ids[m]] * (q^2)^q2_pows[m]
+ * (param_ids[m] < 0 means the factor 1), applied to prod_k field_k^powers[k].
+ * implicit = 1: an lhs term of "dt phi + lhs = rhs"; it must be linear in the
+ *   field itself (n_factors = 1, factor_fields[0] = field_id, powers[0] = 1).
+ * implicit = 0: an rhs term, treated explicitly.  This build implements rhs
+ *   terms whose product is a power 1..3 of the field itself; several rhs terms
+ *   of one field must share that power (their operators add up).
+ * q2_pows in [0, 4], n_mono <= 8. */
+int pss_add_term(pss_system *s, int field_id, int implicit,
+                 int n_mono, const int *param_ids, const double *scales, const int *q2_pows,
+                 int n_factors, const int *factor_fields, const int *powers);
+
+/* Noise of strength D~(q) = param[D_param_id] * (q^2)^q2_pow on field_id
+ * ("addNoise(phi, D*q^2)", section "Adding noise").  q2_pow in [0, 4]. */
+int pss_set_noise(pss_system *s, int field_id, int D_param_id, int q2_pow);
+
+/* De-aliasing order n of field_id (section "De-aliasing"): the field enters
+ * products with its modes kept iff (n+1)|k_j| < N_j on every axis.  Default 2
+ * (the two-thirds rule); 0 keeps every mode. */
+int pss_set_dealias(pss_system *s, int field_id, int order);
+
+/* Copy a real field [nz][ny][nx] in (and transform it). */
+int pss_set_field(pss_system *s, int field_id, const void *real, int where);
+/* Set a real field to lo + (hi - lo) u, u = ((x >> 8) + 0.5) / 2^24 with x the
+ * first word of Philox4x32-10(counter = (site, 0, field_id, 1), key = seed). */
+int pss_init_uniform(pss_system *s, int field_id, double lo, double hi);
+
+/* Advance every dynamic field by n >= 0 steps.  Asynchronous on the system's
+ * stream.  Step k of the run draws noise with Philox counter word 1 = k. */
+int pss_step(pss_system *s, int64_t n);
+/* Measurement: take n >= 1 steps like pss_step, but launch every kernel on
+ * its own with a CUDA event pair around it, and return in avg_ms[0..3] the
+ * mean duration (milliseconds) of each kind of launch of a step:
+ * 0 = fused column kernel (update), 1 = inverse y pass (3D only),
+ * 2 = row kernel (x transforms and product), 3 = forward y pass (3D only);
+ * kinds that do not run read 0.  Synchronises. */
+int pss_time_kernels(pss_system *s, int64_t n, double *avg_ms);
+
+/* Steps taken so far (the next step's noise index). */
+int pss_get_step(pss_system *s, int64_t *step);
+int pss_set_step(pss_system *s, int64_t step);
+
+/* Real field [nz][ny][nx] out (synchronises; reports device-side errors). */
+int pss_get_field(pss_system *s, int field_id, void *real_out, int where);
+/* Half spectrum [nz][ny][nx/2+1] out / in. */
+int pss_get_spectrum(pss_system *s, int field_id, void *half_out, int where);
+int pss_set_spectrum(pss_system *s, int field_id, const void *half_in, int where);
+
+/* Radially binned structure factor S(q) = |phi_q|^2 / N_sites over
+ * 0 < |q| <= pi/dx, nbins equal bins (b = ceil(|q| nbins dx / pi) - 1), over
+ * the full Hermitian set of modes; S_out[nbins] are bin means (FP64 sums),
+ * count_out[nbins] (may be NULL) the modes per bin, *L_out (may be NULL) the
+ * length 2 pi sum S / sum |q| S.  Host pointers; synchronises. */
+int pss_structure_factor(pss_system *s, int field_id, int nbins,
+                         double *S_out, double *count_out, double *L_out);
+
+/* Wait for the system's stream and report device-side errors. */
+int pss_sync(pss_system *s);
+
+/* Message of the last failed call on this handle (valid until the next
+ * call).  pss_last_error(NULL) returns the message of a failed create. */
+const char *pss_last_error(const pss_system *s);
+
+/* Number of kernel launches this handle has issued (a count kept by the
+ * host; for measurement). */
+int64_t pss_launch_count(const pss_system *s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

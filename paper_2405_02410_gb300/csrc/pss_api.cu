@@ -1,0 +1,796 @@
+// pss_api.cu -- host side of libpss: the C ABI declared in include/pss.h.
+//
+// A system owns, per field, the spectral state phi_q and two work arrays A, B
+// (same tiled layout, see pss_internal.h).  B carries the x-transformed
+// nonlinear product from one step to the next; A holds the inverse-transformed
+// de-aliased field inside a step.  All kernels of a step are issued on one
+// stream; runs of steps are replayed from a captured CUDA graph.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/pss.h"
+#include "pss_internal.h"
+
+using namespace pss;
+
+namespace {
+
+struct Mono {
+    int param;       // < 0: factor 1
+    double scale;
+    int pow;
+};
+
+struct Field {
+    std::string name;
+    std::vector<Mono> lhs, rhs;
+    int power = 0;
+    bool noisy = false;
+    int noise_param = -1;
+    int noise_pow = 0;
+    int dealias = 2;
+    void *state = nullptr, *A = nullptr, *B = nullptr;
+};
+
+struct Param {
+    std::string name;
+    double value;
+};
+
+constexpr int kGraphSteps = 16;
+constexpr double kPi = 3.14159265358979323846;
+
+}  // namespace
+
+struct pss_system {
+    int dim = 0, nx = 1, ny = 1, nz = 1;
+    double dx[3] = {1, 1, 1};
+    double dt = 0;
+    uint64_t seed = 0;
+    int prec = PSS_F32;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    std::vector<Param> params;
+    std::vector<Field> fields;
+    int hx = 0, ntiles = 0, rows = 0, n_outer = 1, n_inner = 1;
+    long long nsites = 0;
+    size_t field_elems = 0;   // complex elements of one spectral array
+    void *tw = nullptr;       // roots of unity, precision of the system
+    void *real = nullptr;     // real scratch [nz][ny][nx]
+    void *half = nullptr;     // half-spectrum scratch
+    double *sq = nullptr;     // structure-factor accumulator
+    int sq_cap = 0;
+    long long *d_step = nullptr;
+    int *d_status = nullptr;
+    int64_t step = 0;
+    bool stale = true;        // B does not hold the product of the current state
+    cudaGraphExec_t graph = nullptr;
+    bool graph_valid = false;
+    int64_t launches = 0;
+    std::string err;
+};
+
+namespace {
+
+std::string g_create_err;
+
+int fail(pss_system *s, int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (s) s->err = buf;
+    else g_create_err = buf;
+    return code;
+}
+
+int cuda_fail(pss_system *s, cudaError_t e, const char *what) {
+    return fail(s, e == cudaErrorMemoryAllocation ? PSS_ENOMEM : PSS_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(call)                                                       \
+    do {                                                               \
+        cudaError_t _e = (call);                                       \
+        if (_e != cudaSuccess) return cuda_fail(s, _e, #call);         \
+    } while (0)
+
+bool pow2_in(int n, int lo, int hi) { return n >= lo && n <= hi && (n & (n - 1)) == 0; }
+
+size_t csize(const pss_system *s) { return s->prec == PSS_F64 ? 16 : 8; }
+size_t rsize(const pss_system *s) { return s->prec == PSS_F64 ? 8 : 4; }
+
+// largest kept |k| on an axis of n points: (order+1)|k| < n; every |k| <= n/2
+// is kept when order = 0
+int kmax_axis(int n, int order) {
+    if (n == 1) return 0;
+    if (order <= 0) return n / 2;
+    return std::min((n - 1) / (order + 1), n / 2);
+}
+
+template <typename T> SysP<T> sys_params(const pss_system *s) {
+    SysP<T> p{};
+    p.dim = s->dim;
+    p.nx = s->nx; p.ny = s->ny; p.nz = s->nz; p.hx = s->hx;
+    p.ntiles = s->ntiles; p.rows = s->rows;
+    p.n_outer = s->n_outer; p.n_inner = s->n_inner;
+    const double two_pi = 6.283185307179586476925286766559;
+    p.gx = T(two_pi / (s->nx * s->dx[0]));
+    p.gy = s->ny > 1 ? T(two_pi / (s->ny * s->dx[1])) : T(0);
+    p.gz = s->nz > 1 ? T(two_pi / (s->nz * s->dx[2])) : T(0);
+    p.dt = T(s->dt);
+    p.inv_nsites = T(1.0 / (double)s->nsites);
+    p.seed_lo = (uint32_t)(s->seed & 0xffffffffu);
+    p.seed_hi = (uint32_t)(s->seed >> 32);
+    return p;
+}
+
+double pval(const pss_system *s, int id) { return id < 0 ? 1.0 : s->params[id].value; }
+
+template <typename T> FieldP<T> field_params(const pss_system *s, int fi) {
+    const Field &f = s->fields[fi];
+    FieldP<T> p{};
+    double O[kPolyTerms] = {0}, M[kPolyTerms] = {0};
+    for (const Mono &m : f.lhs) O[m.pow] += m.scale * pval(s, m.param);
+    for (const Mono &m : f.rhs) M[m.pow] += m.scale * pval(s, m.param);
+    for (int i = 0; i < kPolyTerms; ++i) { p.O[i] = T(O[i]); p.M[i] = T(M[i]); }
+    double dV = 1.0;
+    for (int j = 0; j < s->dim; ++j) dV *= s->dx[j];
+    p.noisy = f.noisy ? 1 : 0;
+    p.amp2 = f.noisy ? T((double)s->nsites * pval(s, f.noise_param) * s->dt / dV) : T(0);
+    p.noise_pow = f.noise_pow;
+    p.power = f.power;
+    p.kmax[0] = kmax_axis(s->nx, f.dealias);
+    p.kmax[1] = kmax_axis(s->ny, f.dealias);
+    p.kmax[2] = kmax_axis(s->nz, f.dealias);
+    p.field_id = fi;
+    return p;
+}
+
+// ---- launch shapes -------------------------------------------------------
+int col_tiles_per_cta(const pss_system *s) {
+    const int NP = s->dim == 3 ? 2 : 1;
+    const int per_tile = kTileW * NP * fft_TPF(s->n_inner);
+    int tc = std::max(1, 64 / per_tile);
+    tc = std::min(tc, s->ntiles);
+    while (tc > 1 && tc * per_tile > 256) --tc;
+    return tc;
+}
+
+int row_G(const pss_system *s) {
+    const int tpf = fft_TPF(s->nx);
+    int G = std::max(1, 128 / tpf);
+    const int want = std::max(1, (s->rows / 2 + 7) / 8);
+    G = std::min(G, want);
+    while (G > 1 && G * tpf > 256) --G;
+    return G;
+}
+
+int mid_PZ(const pss_system *s) {
+    const int tpf = fft_TPF(s->ny);
+    int pz = std::max(1, 256 / (kTileW * tpf));
+    pz = std::min(pz, s->nz);
+    return pz;
+}
+
+// kept half-spectrum columns kx = 0..kmax (never more than the nx/2+1 stored)
+int kept_cols(const pss_system *s, int fi) { return std::min(kmax_axis(s->nx, s->fields[fi].dealias) + 1, s->hx); }
+
+// ---- kernel sequences ----------------------------------------------------
+// Optional per-launch CUDA events (pss_time_kernels): kind 0 = k_col,
+// 1 = k_mid inverse, 2 = k_row, 3 = k_mid forward.
+struct Timer {
+    std::vector<cudaEvent_t> ev[4];
+    int begin(int kind, cudaStream_t st) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return -1;
+        ev[kind].push_back(e);
+        return cudaEventRecord(e, st) == cudaSuccess ? 0 : -1;
+    }
+    ~Timer() {
+        for (auto &v : ev)
+            for (cudaEvent_t e : v) cudaEventDestroy(e);
+    }
+};
+
+template <typename T> struct Seq {
+    pss_system *s;
+    cudaStream_t st;
+    int f0, nf;   // fields [f0, f0 + nf)
+    Timer *timer = nullptr;
+
+    cplx<T> *state(int i) const { return (cplx<T> *)s->fields[f0 + i].state; }
+    cplx<T> *A(int i) const { return (cplx<T> *)s->fields[f0 + i].A; }
+    cplx<T> *B(int i) const { return (cplx<T> *)s->fields[f0 + i].B; }
+
+    int max_kept_tiles() const {
+        int m = 0;
+        for (int i = 0; i < nf; ++i) m = std::max(m, (kept_cols(s, f0 + i) + kTileW - 1) / kTileW);
+        return std::min(m, s->ntiles);
+    }
+
+    int col(int mode, bool in_is_B, bool out_is_A) {
+        ColArgs<T> a{};
+        a.sp = sys_params<T>(s);
+        for (int i = 0; i < nf; ++i) {
+            a.fp[i] = field_params<T>(s, f0 + i);
+            a.in[i] = in_is_B ? B(i) : A(i);
+            a.out[i] = out_is_A ? A(i) : B(i);
+            a.state[i] = state(i);
+        }
+        a.tw = (const cplx<T> *)s->tw;
+        a.d_step = s->d_step;
+        a.d_status = s->d_status;
+        a.mode = mode;
+        a.tiles_per_cta = col_tiles_per_cta(s);
+        a.n_tiles = mode == COL_INV_MASK ? max_kept_tiles() : s->ntiles;
+        const int gx = (a.n_tiles + a.tiles_per_cta - 1) / a.tiles_per_cta;
+        const int gy = s->dim == 3 ? s->ny / 2 + 1 : 1;
+        if (timer) timer->begin(0, st);
+        cudaError_t e = launch_col<T>(a, nf, gx, gy, st);
+        if (timer) timer->begin(0, st);
+        s->launches++;
+        if (e != cudaSuccess) return cuda_fail(s, e, "k_col launch");
+        return PSS_OK;
+    }
+
+    // in: A or B (complex), or real (ROW_R2C); out: A or B (complex), or real (ROW_C2R)
+    int row(int mode, bool in_is_A, bool out_is_B, bool inc, void *real) {
+        RowArgs<T> a{};
+        a.sp = sys_params<T>(s);
+        for (int i = 0; i < nf; ++i) {
+            a.power[i] = s->fields[f0 + i].power;
+            a.in[i] = in_is_A ? A(i) : B(i);
+            a.out[i] = out_is_B ? B(i) : A(i);
+            a.real_in[i] = (const T *)real + (size_t)i * s->nsites;
+            a.real_out[i] = (T *)real + (size_t)i * s->nsites;
+        }
+        a.tw = (const cplx<T> *)s->tw;
+        a.d_step = s->d_step;
+        a.mode = mode;
+        a.G = row_G(s);
+        for (int i = 0; i < nf; ++i) a.kx_cols[i] = mode == ROW_FUSED ? kept_cols(s, f0 + i) : s->hx;
+        a.inc_step = inc ? 1 : 0;
+        if (timer) timer->begin(2, st);
+        cudaError_t e = launch_row<T>(a, nf, st);
+        if (timer) timer->begin(2, st);
+        s->launches++;
+        if (e != cudaSuccess) return cuda_fail(s, e, "k_row launch");
+        return PSS_OK;
+    }
+
+    int mid(int mode, bool in_is_A, bool inc) {
+        MidArgs<T> a{};
+        a.sp = sys_params<T>(s);
+        for (int i = 0; i < nf; ++i) {
+            a.kmax_y[i] = kmax_axis(s->ny, s->fields[f0 + i].dealias);
+            a.in[i] = in_is_A ? A(i) : B(i);
+            a.out[i] = in_is_A ? B(i) : A(i);
+        }
+        a.tw = (const cplx<T> *)s->tw;
+        a.d_step = s->d_step;
+        a.mode = mode;
+        a.PZ = mid_PZ(s);
+        a.inc_step = inc ? 1 : 0;
+        const int nt = mode == MID_INV_MASK ? max_kept_tiles() : s->ntiles;
+        const int kind = mode == MID_FWD ? 3 : 1;
+        if (timer) timer->begin(kind, st);
+        cudaError_t e = launch_mid<T>(a, nf, nt, st);
+        if (timer) timer->begin(kind, st);
+        s->launches++;
+        if (e != cudaSuccess) return cuda_fail(s, e, "k_mid launch");
+        return PSS_OK;
+    }
+
+    // B <- x-transformed product of the current state (start of a run)
+    int prologue() {
+        int rc;
+        if ((rc = col(COL_INV_MASK, false, true))) return rc;                 // state -> A
+        if (s->dim == 3) {
+            if ((rc = mid(MID_INV_MASK, true, false))) return rc;             // A -> B
+            if ((rc = row(ROW_FUSED, false, false, false, nullptr))) return rc;   // B -> A
+            return mid(MID_FWD, true, false);                                 // A -> B
+        }
+        return row(ROW_FUSED, true, true, false, nullptr);                     // A -> B
+    }
+
+    int one_step() {
+        int rc;
+        if ((rc = col(COL_STEP, true, true))) return rc;                      // B, state -> state, A
+        if (s->dim == 3) {
+            if ((rc = mid(MID_INV_MASK, true, false))) return rc;             // A -> B
+            if ((rc = row(ROW_FUSED, false, false, false, nullptr))) return rc;   // B -> A
+            return mid(MID_FWD, true, true);                                  // A -> B, step++
+        }
+        return row(ROW_FUSED, true, true, true, nullptr);                      // A -> B, step++
+    }
+
+    // real scratch (fields f0..f0+nf) -> state
+    int forward_from_real() {
+        int rc;
+        if (s->dim == 3) {
+            if ((rc = row(ROW_R2C, true, false, false, s->real))) return rc;  // real -> A
+            if ((rc = mid(MID_FWD, true, false))) return rc;                  // A -> B
+        } else {
+            if ((rc = row(ROW_R2C, true, true, false, s->real))) return rc;   // real -> B
+        }
+        return col(COL_FWD, true, true);                                      // B -> state
+    }
+
+    // state -> real scratch
+    int inverse_to_real() {
+        int rc;
+        if ((rc = col(COL_INV_FULL, false, true))) return rc;                 // state -> A
+        if (s->dim == 3) {
+            if ((rc = mid(MID_INV_FULL, true, false))) return rc;             // A -> B
+            return row(ROW_C2R, false, false, false, s->real);                // B -> real
+        }
+        return row(ROW_C2R, true, false, false, s->real);                     // A -> real
+    }
+};
+
+template <typename T> int run_prologue(pss_system *s) {
+    Seq<T> q{s, s->stream, 0, (int)s->fields.size()};
+    return q.prologue();
+}
+
+template <typename T> int run_steps(pss_system *s, int64_t n) {
+    const int nf = (int)s->fields.size();
+    int64_t done = 0;
+    if (n >= kGraphSteps) {
+        if (!s->graph_valid) {
+            if (s->graph) { cudaGraphExecDestroy(s->graph); s->graph = nullptr; }
+            CK(cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal));
+            Seq<T> q{s, s->cap_stream, 0, nf};
+            int rc = PSS_OK;
+            const int64_t before = s->launches;
+            for (int k = 0; k < kGraphSteps && rc == PSS_OK; ++k) rc = q.one_step();
+            s->launches = before;
+            cudaGraph_t g = nullptr;
+            cudaError_t e = cudaStreamEndCapture(s->cap_stream, &g);
+            if (rc) { if (g) cudaGraphDestroy(g); return rc; }
+            if (e != cudaSuccess) return cuda_fail(s, e, "cudaStreamEndCapture");
+            e = cudaGraphInstantiate(&s->graph, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) return cuda_fail(s, e, "cudaGraphInstantiate");
+            s->graph_valid = true;
+        }
+        const int per_step = s->dim == 3 ? 4 : 2;
+        while (n - done >= kGraphSteps) {
+            CK(cudaGraphLaunch(s->graph, s->stream));
+            s->launches += (int64_t)kGraphSteps * per_step;
+            done += kGraphSteps;
+        }
+    }
+    Seq<T> q{s, s->stream, 0, nf};
+    for (; done < n; ++done) {
+        int rc = q.one_step();
+        if (rc) return rc;
+    }
+    return PSS_OK;
+}
+
+template <typename T> int timed_steps(pss_system *s, int64_t n, double *avg_ms) {
+    Timer timer;
+    Seq<T> q{s, s->stream, 0, (int)s->fields.size(), &timer};
+    for (int64_t k = 0; k < n; ++k) {
+        int rc = q.one_step();
+        if (rc) return rc;
+    }
+    CK(cudaStreamSynchronize(s->stream));
+    for (int kind = 0; kind < 4; ++kind) {
+        const auto &v = timer.ev[kind];
+        double tot = 0;
+        for (size_t i = 0; i + 1 < v.size(); i += 2) {
+            float ms = 0;
+            CK(cudaEventElapsedTime(&ms, v[i], v[i + 1]));
+            tot += ms;
+        }
+        avg_ms[kind] = v.size() >= 2 ? tot / (double)(v.size() / 2) : 0.0;
+    }
+    return PSS_OK;
+}
+
+int check_field(pss_system *s, int fid) {
+    if (!s) return PSS_EINVAL;
+    if (fid < 0 || fid >= (int)s->fields.size()) return fail(s, PSS_EINVAL, "no field %d", fid);
+    return PSS_OK;
+}
+
+int ensure_real(pss_system *s) {
+    if (!s->real) {
+        const size_t bytes = rsize(s) * (size_t)s->nsites * kMaxFields;
+        CK(cudaMalloc(&s->real, bytes));
+    }
+    return PSS_OK;
+}
+
+int ensure_half(pss_system *s) {
+    if (!s->half) CK(cudaMalloc(&s->half, csize(s) * (size_t)s->hx * s->ny * s->nz));
+    return PSS_OK;
+}
+
+int device_errors(pss_system *s) {
+    int st = 0;
+    CK(cudaMemcpyAsync(&st, s->d_status, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    if (st) {
+        CK(cudaMemsetAsync(s->d_status, 0, sizeof(int), s->stream));
+        return fail(s, PSS_ENONFINITE, "a field became NaN or Inf");
+    }
+    return PSS_OK;
+}
+
+void invalidate(pss_system *s) { s->graph_valid = false; }
+
+}  // namespace
+
+// ==========================================================================
+// C ABI
+// ==========================================================================
+extern "C" {
+
+int pss_create_system(pss_system **out, int dim, int nx, int ny, int nz, double dx, double dy, double dz,
+                      double dt, uint64_t seed, int precision) {
+    if (!out) return fail(nullptr, PSS_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (dim < 1 || dim > 3) return fail(nullptr, PSS_EINVAL, "dim must be 1, 2 or 3");
+    if (dim < 2) ny = 1;
+    if (dim < 3) nz = 1;
+    if (!pow2_in(nx, 4, 1024) || (dim >= 2 && !pow2_in(ny, 4, 1024)) || (dim == 3 && !pow2_in(nz, 4, 1024)))
+        return fail(nullptr, PSS_EUNSUPPORTED, "sizes must be powers of two in [4, 1024]");
+    if (!(dx > 0) || (dim >= 2 && !(dy > 0)) || (dim == 3 && !(dz > 0)) || !(dt > 0))
+        return fail(nullptr, PSS_EINVAL, "spacings and dt must be positive");
+    if (precision != PSS_F32 && precision != PSS_F64) return fail(nullptr, PSS_EINVAL, "precision");
+    if ((long long)nx * ny * nz > (1ll << 31)) return fail(nullptr, PSS_EUNSUPPORTED, "lattice too large");
+    pss_system *s = new pss_system();
+    s->dim = dim; s->nx = nx; s->ny = ny; s->nz = nz;
+    s->dx[0] = dx; s->dx[1] = dim >= 2 ? dy : 1.0; s->dx[2] = dim == 3 ? dz : 1.0;
+    s->dt = dt; s->seed = seed; s->prec = precision;
+    s->hx = nx / 2 + 1;
+    s->ntiles = (s->hx + kTileW - 1) / kTileW;
+    s->rows = ny * nz;
+    s->n_outer = dim == 3 ? ny : 1;
+    s->n_inner = dim == 3 ? nz : (dim == 2 ? ny : 1);
+    s->nsites = (long long)nx * ny * nz;
+    s->field_elems = (size_t)s->ntiles * s->rows * kTileW;
+    cudaError_t e = cudaGetDevice(&s->device);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_step, sizeof(long long));
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_status, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(s->d_step, 0, sizeof(long long));
+    if (e == cudaSuccess) e = cudaMemset(s->d_status, 0, sizeof(int));
+    // roots of unity exp(-2 pi i m / 1024), built in FP64 on the host
+    if (e == cudaSuccess) {
+        const int n = 1024;
+        if (precision == PSS_F64) {
+            std::vector<double2> h(n);
+            for (int m = 0; m < n; ++m) h[m] = make_double2(std::cos(2 * kPi * m / n), -std::sin(2 * kPi * m / n));
+            e = cudaMalloc(&s->tw, sizeof(double2) * n);
+            if (e == cudaSuccess) e = cudaMemcpy(s->tw, h.data(), sizeof(double2) * n, cudaMemcpyHostToDevice);
+        } else {
+            std::vector<float2> h(n);
+            for (int m = 0; m < n; ++m)
+                h[m] = make_float2((float)std::cos(2 * kPi * m / n), (float)-std::sin(2 * kPi * m / n));
+            e = cudaMalloc(&s->tw, sizeof(float2) * n);
+            if (e == cudaSuccess) e = cudaMemcpy(s->tw, h.data(), sizeof(float2) * n, cudaMemcpyHostToDevice);
+        }
+    }
+    if (e != cudaSuccess) {
+        int rc = cuda_fail(nullptr, e, "pss_create_system");
+        pss_destroy_system(s);
+        return rc;
+    }
+    *out = s;
+    return PSS_OK;
+}
+
+int pss_destroy_system(pss_system *s) {
+    if (!s) return PSS_OK;
+    if (s->graph) cudaGraphExecDestroy(s->graph);
+    for (Field &f : s->fields) {
+        cudaFree(f.state);
+        cudaFree(f.A);
+        cudaFree(f.B);
+    }
+    cudaFree(s->tw);
+    cudaFree(s->real);
+    cudaFree(s->half);
+    cudaFree(s->sq);
+    cudaFree(s->d_step);
+    cudaFree(s->d_status);
+    if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
+    delete s;
+    return PSS_OK;
+}
+
+int pss_set_stream(pss_system *s, void *stream) {
+    if (!s) return PSS_EINVAL;
+    s->stream = (cudaStream_t)stream;
+    return PSS_OK;
+}
+
+int pss_add_param(pss_system *s, const char *name, double value, int *id) {
+    if (!s || !name) return s ? fail(s, PSS_EINVAL, "name is NULL") : PSS_EINVAL;
+    for (const Param &p : s->params)
+        if (p.name == name) return fail(s, PSS_EINVAL, "parameter '%s' exists", name);
+    s->params.push_back({name, value});
+    if (id) *id = (int)s->params.size() - 1;
+    invalidate(s);
+    return PSS_OK;
+}
+
+int pss_set_param(pss_system *s, int id, double value) {
+    if (!s) return PSS_EINVAL;
+    if (id < 0 || id >= (int)s->params.size()) return fail(s, PSS_EINVAL, "no parameter %d", id);
+    s->params[id].value = value;
+    invalidate(s);
+    return PSS_OK;
+}
+
+int pss_get_param(pss_system *s, int id, double *value) {
+    if (!s || !value) return PSS_EINVAL;
+    if (id < 0 || id >= (int)s->params.size()) return fail(s, PSS_EINVAL, "no parameter %d", id);
+    *value = s->params[id].value;
+    return PSS_OK;
+}
+
+int pss_add_field(pss_system *s, const char *name, int dynamic, int *field_id) {
+    if (!s || !name) return s ? fail(s, PSS_EINVAL, "name is NULL") : PSS_EINVAL;
+    if (!dynamic) return fail(s, PSS_EUNSUPPORTED, "only dynamic fields are implemented");
+    if ((int)s->fields.size() >= kMaxFields) return fail(s, PSS_EUNSUPPORTED, "at most %d fields", kMaxFields);
+    for (const Field &f : s->fields)
+        if (f.name == name) return fail(s, PSS_EINVAL, "field '%s' exists", name);
+    Field f;
+    f.name = name;
+    const size_t bytes = csize(s) * s->field_elems;
+    cudaError_t e = cudaMalloc(&f.state, bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&f.A, bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&f.B, bytes);
+    if (e == cudaSuccess) e = cudaMemset(f.state, 0, bytes);
+    if (e == cudaSuccess) e = cudaMemset(f.A, 0, bytes);
+    if (e == cudaSuccess) e = cudaMemset(f.B, 0, bytes);
+    if (e != cudaSuccess) {
+        cudaFree(f.state); cudaFree(f.A); cudaFree(f.B);
+        return cuda_fail(s, e, "pss_add_field");
+    }
+    s->fields.push_back(f);
+    if (field_id) *field_id = (int)s->fields.size() - 1;
+    s->stale = true;
+    invalidate(s);
+    return PSS_OK;
+}
+
+int pss_add_term(pss_system *s, int field_id, int implicit, int n_mono, const int *param_ids, const double *scales,
+                 const int *q2_pows, int n_factors, const int *factor_fields, const int *powers) {
+    int rc = check_field(s, field_id);
+    if (rc) return rc;
+    if (n_mono < 1 || n_mono > 8 || !scales || !q2_pows) return fail(s, PSS_EINVAL, "need 1..8 monomials");
+    for (int m = 0; m < n_mono; ++m) {
+        if (q2_pows[m] < 0 || q2_pows[m] >= kPolyTerms) return fail(s, PSS_EINVAL, "q^2 power must be in [0, 4]");
+        const int pid = param_ids ? param_ids[m] : -1;
+        if (pid >= (int)s->params.size()) return fail(s, PSS_EINVAL, "no parameter %d", pid);
+    }
+    if (n_factors < 1 || !factor_fields || !powers) return fail(s, PSS_EINVAL, "need at least one factor");
+    if (n_factors != 1 || factor_fields[0] != field_id)
+        return fail(s, PSS_EUNSUPPORTED, "terms must be a power of the field itself in this build");
+    const int p = powers[0];
+    Field &f = s->fields[field_id];
+    if (implicit) {
+        if (p != 1) return fail(s, PSS_EINVAL, "implicit terms must be linear in the field");
+        for (int m = 0; m < n_mono; ++m) f.lhs.push_back({param_ids ? param_ids[m] : -1, scales[m], q2_pows[m]});
+    } else {
+        if (p < 1 || p > 3) return fail(s, PSS_EUNSUPPORTED, "explicit products must be a power 1..3");
+        if (f.power != 0 && f.power != p) return fail(s, PSS_EUNSUPPORTED, "explicit terms of a field share one power");
+        f.power = p;
+        for (int m = 0; m < n_mono; ++m) f.rhs.push_back({param_ids ? param_ids[m] : -1, scales[m], q2_pows[m]});
+    }
+    s->stale = true;
+    invalidate(s);
+    return PSS_OK;
+}
+
+int pss_set_noise(pss_system *s, int field_id, int D_param_id, int q2_pow) {
+    int rc = check_field(s, field_id);
+    if (rc) return rc;
+    if (D_param_id < 0 || D_param_id >= (int)s->params.size()) return fail(s, PSS_EINVAL, "no parameter %d", D_param_id);
+    if (q2_pow < 0 || q2_pow >= kPolyTerms) return fail(s, PSS_EINVAL, "q^2 power must be in [0, 4]");
+    Field &f = s->fields[field_id];
+    f.noisy = true;
+    f.noise_param = D_param_id;
+    f.noise_pow = q2_pow;
+    invalidate(s);
+    return PSS_OK;
+}
+
+int pss_set_dealias(pss_system *s, int field_id, int order) {
+    int rc = check_field(s, field_id);
+    if (rc) return rc;
+    if (order < 0) return fail(s, PSS_EINVAL, "order must be >= 0");
+    s->fields[field_id].dealias = order;
+    s->stale = true;
+    invalidate(s);
+    return PSS_OK;
+}
+
+static int forward_field(pss_system *s, int field_id) {
+    int rc;
+    if (s->prec == PSS_F64) rc = Seq<double>{s, s->stream, field_id, 1}.forward_from_real();
+    else rc = Seq<float>{s, s->stream, field_id, 1}.forward_from_real();
+    s->stale = true;
+    return rc;
+}
+
+int pss_set_field(pss_system *s, int field_id, const void *real, int where) {
+    int rc = check_field(s, field_id);
+    if (rc) return rc;
+    if (!real) return fail(s, PSS_EINVAL, "real is NULL");
+    if ((rc = ensure_real(s))) return rc;
+    const size_t bytes = rsize(s) * (size_t)s->nsites;
+    CK(cudaMemcpyAsync(s->real, real, bytes, where == PSS_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                       s->stream));
+    return forward_field(s, field_id);
+}
+
+int pss_init_uniform(pss_system *s, int field_id, double lo, double hi) {
+    int rc = check_field(s, field_id);
+    if (rc) return rc;
+    if ((rc = ensure_real(s))) return rc;
+    const uint32_t s0 = (uint32_t)(s->seed & 0xffffffffu), s1 = (uint32_t)(s->seed >> 32);
+    cudaError_t e = s->prec == PSS_F64
+        ? launch_init_uniform<double>((double *)s->real, s->nsites, lo, hi, s0, s1, field_id, s->stream)
+        : launch_init_uniform<float>((float *)s->real, s->nsites, lo, hi, s0, s1, field_id, s->stream);
+    s->launches++;
+    if (e != cudaSuccess) return cuda_fail(s, e, "init kernel");
+    return forward_field(s, field_id);
+}
+
+int pss_step(pss_system *s, int64_t n) {
+    if (!s) return PSS_EINVAL;
+    if (n < 0) return fail(s, PSS_EINVAL, "n must be >= 0");
+    if (s->fields.empty()) return fail(s, PSS_EINVAL, "no fields");
+    if (n == 0) return PSS_OK;
+    int rc;
+    if (s->stale) {
+        rc = s->prec == PSS_F64 ? run_prologue<double>(s) : run_prologue<float>(s);
+        if (rc) return rc;
+        s->stale = false;
+    }
+    rc = s->prec == PSS_F64 ? run_steps<double>(s, n) : run_steps<float>(s, n);
+    if (rc) return rc;
+    s->step += n;
+    return PSS_OK;
+}
+
+int pss_time_kernels(pss_system *s, int64_t n, double *avg_ms) {
+    if (!s || !avg_ms) return PSS_EINVAL;
+    if (n < 1) return fail(s, PSS_EINVAL, "n must be >= 1");
+    if (s->fields.empty()) return fail(s, PSS_EINVAL, "no fields");
+    int rc;
+    if (s->stale) {
+        rc = s->prec == PSS_F64 ? run_prologue<double>(s) : run_prologue<float>(s);
+        if (rc) return rc;
+        s->stale = false;
+    }
+    rc = s->prec == PSS_F64 ? timed_steps<double>(s, n, avg_ms) : timed_steps<float>(s, n, avg_ms);
+    if (rc) return rc;
+    s->step += n;
+    return device_errors(s);
+}
+
+int pss_get_step(pss_system *s, int64_t *step) {
+    if (!s || !step) return PSS_EINVAL;
+    *step = s->step;
+    return PSS_OK;
+}
+
+int pss_set_step(pss_system *s, int64_t step) {
+    if (!s) return PSS_EINVAL;
+    if (step < 0) return fail(s, PSS_EINVAL, "step must be >= 0");
+    long long v = step;
+    CK(cudaMemcpyAsync(s->d_step, &v, sizeof v, cudaMemcpyHostToDevice, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    s->step = step;
+    return PSS_OK;
+}
+
+int pss_get_field(pss_system *s, int field_id, void *real_out, int where) {
+    int rc = check_field(s, field_id);
+    if (rc) return rc;
+    if (!real_out) return fail(s, PSS_EINVAL, "real_out is NULL");
+    if ((rc = ensure_real(s))) return rc;
+    rc = s->prec == PSS_F64 ? Seq<double>{s, s->stream, field_id, 1}.inverse_to_real()
+                            : Seq<float>{s, s->stream, field_id, 1}.inverse_to_real();
+    if (rc) return rc;
+    if (s->dim == 3) s->stale = true;   // the y pass reused B
+    const size_t bytes = rsize(s) * (size_t)s->nsites;
+    CK(cudaMemcpyAsync(real_out, s->real, bytes, where == PSS_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                       s->stream));
+    return device_errors(s);
+}
+
+int pss_get_spectrum(pss_system *s, int field_id, void *half_out, int where) {
+    int rc = check_field(s, field_id);
+    if (rc) return rc;
+    if (!half_out) return fail(s, PSS_EINVAL, "half_out is NULL");
+    if ((rc = ensure_half(s))) return rc;
+    cudaError_t e = s->prec == PSS_F64
+        ? launch_tiles_to_half<double>(sys_params<double>(s), (const double2 *)s->fields[field_id].state,
+                                       (double2 *)s->half, s->stream)
+        : launch_tiles_to_half<float>(sys_params<float>(s), (const float2 *)s->fields[field_id].state,
+                                      (float2 *)s->half, s->stream);
+    s->launches++;
+    if (e != cudaSuccess) return cuda_fail(s, e, "layout kernel");
+    const size_t bytes = csize(s) * (size_t)s->hx * s->ny * s->nz;
+    CK(cudaMemcpyAsync(half_out, s->half, bytes, where == PSS_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                       s->stream));
+    return device_errors(s);
+}
+
+int pss_set_spectrum(pss_system *s, int field_id, const void *half_in, int where) {
+    int rc = check_field(s, field_id);
+    if (rc) return rc;
+    if (!half_in) return fail(s, PSS_EINVAL, "half_in is NULL");
+    if ((rc = ensure_half(s))) return rc;
+    const size_t bytes = csize(s) * (size_t)s->hx * s->ny * s->nz;
+    CK(cudaMemcpyAsync(s->half, half_in, bytes, where == PSS_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                       s->stream));
+    cudaError_t e = s->prec == PSS_F64
+        ? launch_half_to_tiles<double>(sys_params<double>(s), (const double2 *)s->half,
+                                       (double2 *)s->fields[field_id].state, s->stream)
+        : launch_half_to_tiles<float>(sys_params<float>(s), (const float2 *)s->half,
+                                      (float2 *)s->fields[field_id].state, s->stream);
+    s->launches++;
+    if (e != cudaSuccess) return cuda_fail(s, e, "layout kernel");
+    s->stale = true;
+    return PSS_OK;
+}
+
+int pss_structure_factor(pss_system *s, int field_id, int nbins, double *S_out, double *count_out, double *L_out) {
+    int rc = check_field(s, field_id);
+    if (rc) return rc;
+    if (nbins < 1 || nbins > 4096 || !S_out) return fail(s, PSS_EINVAL, "nbins in [1, 4096] and S_out required");
+    const int need = 2 * nbins + 2;
+    if (s->sq_cap < need) {
+        cudaFree(s->sq);
+        s->sq = nullptr;
+        CK(cudaMalloc(&s->sq, sizeof(double) * need));
+        s->sq_cap = need;
+    }
+    CK(cudaMemsetAsync(s->sq, 0, sizeof(double) * need, s->stream));
+    cudaError_t e = s->prec == PSS_F64
+        ? launch_structure_factor<double>(sys_params<double>(s), s->dx, (const double2 *)s->fields[field_id].state,
+                                          nbins, s->sq, s->stream)
+        : launch_structure_factor<float>(sys_params<float>(s), s->dx, (const float2 *)s->fields[field_id].state,
+                                         nbins, s->sq, s->stream);
+    s->launches++;
+    if (e != cudaSuccess) return cuda_fail(s, e, "structure factor kernel");
+    std::vector<double> h(need);
+    CK(cudaMemcpyAsync(h.data(), s->sq, sizeof(double) * need, cudaMemcpyDeviceToHost, s->stream));
+    if ((rc = device_errors(s))) return rc;
+    for (int b = 0; b < nbins; ++b) {
+        S_out[b] = h[nbins + b] > 0 ? h[b] / h[nbins + b] : 0.0;
+        if (count_out) count_out[b] = h[nbins + b];
+    }
+    if (L_out) *L_out = h[2 * nbins + 1] > 0 ? 2 * kPi * h[2 * nbins] / h[2 * nbins + 1] : 0.0;
+    return PSS_OK;
+}
+
+int pss_sync(pss_system *s) {
+    if (!s) return PSS_EINVAL;
+    return device_errors(s);
+}
+
+const char *pss_last_error(const pss_system *s) { return s ? s->err.c_str() : g_create_err.c_str(); }
+
+int64_t pss_launch_count(const pss_system *s) { return s ? s->launches : 0; }
+
+}  // extern "C"

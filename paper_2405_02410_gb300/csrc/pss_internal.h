@@ -1,0 +1,112 @@
+// pss_internal.h -- types shared by the host side of libpss and its kernels.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace pss {
+
+// complex numbers: float2 / double2 (x = real part, y = imaginary part)
+template <typename T> struct CplxOf;
+template <> struct CplxOf<float> { using type = float2; };
+template <> struct CplxOf<double> { using type = double2; };
+template <typename T> using cplx = typename CplxOf<T>::type;
+
+constexpr int kTileW = 4;       // kx columns per tile of every spectral array
+constexpr int kMaxFields = 4;
+constexpr int kPolyTerms = 5;   // operators are polynomials of degree <= 4 in q^2
+
+// Spectral arrays are stored as [tile][row][kTileW] complex values, where
+// tile = kx / kTileW over the Nx/2+1 half-spectrum columns (the last tile
+// padded with zero columns) and row = o * n_inner + pos:
+//   3D: o = ky (or y), pos = kz (or z);  2D: o = 0, pos = ky (or y);  1D: one row.
+// A tile of one row range is contiguous, so the y/z passes read whole
+// pencils of kTileW columns with unit stride and the x pass reads
+// kTileW-wide segments of many rows at once.
+
+template <typename T> struct FieldP {
+    T O[kPolyTerms];      // implicit operator O(q) = sum O[p] (q^2)^p  (L~ = -O)
+    T M[kPolyTerms];      // explicit operator M(q) applied to the product term
+    T amp2;               // N_sites * D * dt / dV (noise variance per component and unit D~/D)
+    int noise_pow;        // D~ = D (q^2)^noise_pow
+    int noisy;
+    int power;            // product (phi^d)^power; 0 = no explicit term
+    int kmax[3];          // largest kept |k| per axis of the de-alias mask
+    int field_id;
+};
+
+template <typename T> struct SysP {
+    int dim, nx, ny, nz, hx;
+    int ntiles, rows;     // rows = ny * nz
+    int n_outer, n_inner;
+    T gx, gy, gz;         // 2 pi / (N dx) per axis (0 for unused axes)
+    T dt, inv_nsites;
+    uint32_t seed_lo, seed_hi;
+};
+
+enum ColMode { COL_STEP = 0, COL_FWD = 1, COL_INV_MASK = 2, COL_INV_FULL = 3 };
+enum RowMode { ROW_FUSED = 0, ROW_R2C = 1, ROW_C2R = 2 };
+enum MidMode { MID_INV_MASK = 0, MID_INV_FULL = 1, MID_FWD = 2 };
+
+
+template <typename T> struct ColArgs {
+    SysP<T> sp;
+    FieldP<T> fp[kMaxFields];
+    const cplx<T> *in[kMaxFields];
+    cplx<T> *out[kMaxFields];
+    cplx<T> *state[kMaxFields];
+    const cplx<T> *tw;
+    const long long *d_step;
+    int *d_status;
+    int mode, tiles_per_cta, n_tiles;
+};
+
+template <typename T> struct RowArgs {
+    SysP<T> sp;
+    int power[kMaxFields];
+    const cplx<T> *in[kMaxFields];
+    cplx<T> *out[kMaxFields];
+    const T *real_in[kMaxFields];
+    T *real_out[kMaxFields];
+    const cplx<T> *tw;
+    long long *d_step;
+    int kx_cols[kMaxFields];   // half-spectrum columns read from the input (the rest are zero)
+    int mode, G, inc_step;
+};
+
+template <typename T> struct MidArgs {
+    SysP<T> sp;
+    int kmax_y[kMaxFields];
+    const cplx<T> *in[kMaxFields];
+    cplx<T> *out[kMaxFields];
+    const cplx<T> *tw;
+    long long *d_step;
+    int mode, PZ, inc_step;
+};
+
+// Launch configuration chosen by the host.
+struct ColCfg { int tiles_per_cta; };
+struct RowCfg { int G; };
+struct MidCfg { int PZ; };
+
+// Launchers (one instantiation per precision; defined in pss_kern_f32.cu / pss_kern_f64.cu).
+template <typename T> cudaError_t launch_col(const ColArgs<T> &a, int nfields, int grid_x, int grid_y, cudaStream_t st);
+template <typename T> cudaError_t launch_row(const RowArgs<T> &a, int nfields, cudaStream_t st);
+template <typename T> cudaError_t launch_mid(const MidArgs<T> &a, int nfields, int n_tiles, cudaStream_t st);
+template <typename T> cudaError_t launch_init_uniform(T *real, long long nsites, double lo, double hi,
+                                                      uint32_t seed_lo, uint32_t seed_hi, int field_id,
+                                                      cudaStream_t st);
+template <typename T> cudaError_t launch_tiles_to_half(const SysP<T> &sp, const cplx<T> *tiles,
+                                                       cplx<T> *half, cudaStream_t st);
+template <typename T> cudaError_t launch_half_to_tiles(const SysP<T> &sp, const cplx<T> *half,
+                                                       cplx<T> *tiles, cudaStream_t st);
+template <typename T> cudaError_t launch_structure_factor(const SysP<T> &sp, const double dx[3],
+                                                          const cplx<T> *tiles, int nbins,
+                                                          double *acc /* 2*nbins + 2 */, cudaStream_t st);
+
+// FFT shape helpers visible to the host
+inline int fft_E(int n) { return n < 16 ? n : 16; }
+inline int fft_TPF(int n) { return n / fft_E(n); }
+inline int fft_smem_elems_h(int n, int F) { return (n + n / 16) * F; }
+
+}  // namespace pss

@@ -1,0 +1,269 @@
+"""Thin ctypes binding of libpss (include/pss.h).
+
+Every method marshals arguments and calls the C function of the same name
+(``pss_<method>``); all numerical work runs in the library's sm_103a kernels.
+Host arrays are numpy; device arrays are torch CUDA tensors (their raw pointers
+are passed with where=PSS_DEVICE).  There is no CPU fallback: if the library
+is missing, importing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Iterable, Optional, Sequence
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIBPATH = os.path.join(HERE, "_lib", "libpss.so")
+
+PSS_OK, PSS_EINVAL, PSS_ENOMEM, PSS_ECUDA, PSS_ETIMEOUT, PSS_ENONFINITE, PSS_EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
+PSS_F32, PSS_F64 = 0, 1
+PSS_HOST, PSS_DEVICE = 0, 1
+
+EXPORTS = [
+    "pss_create_system", "pss_destroy_system", "pss_set_stream", "pss_add_param", "pss_set_param",
+    "pss_get_param", "pss_add_field", "pss_add_term", "pss_set_noise", "pss_set_dealias", "pss_set_field",
+    "pss_init_uniform", "pss_step", "pss_get_step", "pss_set_step", "pss_get_field", "pss_get_spectrum",
+    "pss_set_spectrum", "pss_structure_factor", "pss_sync", "pss_last_error", "pss_launch_count",
+    "pss_time_kernels",
+]
+
+
+class PssError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"libpss error {code}: {msg}")
+        self.code = code
+
+
+def _load():
+    if not os.path.exists(LIBPATH):
+        raise ImportError(f"{LIBPATH} is missing: build it with paper_2405_02410_gb300.build.build()")
+    L = ctypes.CDLL(LIBPATH)
+    vp, i32, i64, d, u64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double, ctypes.c_uint64
+    P = ctypes.POINTER
+    sig = {
+        "pss_create_system": ([P(vp), i32, i32, i32, i32, d, d, d, d, u64, i32], i32),
+        "pss_destroy_system": ([vp], i32),
+        "pss_set_stream": ([vp, vp], i32),
+        "pss_add_param": ([vp, ctypes.c_char_p, d, P(i32)], i32),
+        "pss_set_param": ([vp, i32, d], i32),
+        "pss_get_param": ([vp, i32, P(d)], i32),
+        "pss_add_field": ([vp, ctypes.c_char_p, i32, P(i32)], i32),
+        "pss_add_term": ([vp, i32, i32, i32, P(i32), P(d), P(i32), i32, P(i32), P(i32)], i32),
+        "pss_set_noise": ([vp, i32, i32, i32], i32),
+        "pss_set_dealias": ([vp, i32, i32], i32),
+        "pss_set_field": ([vp, i32, vp, i32], i32),
+        "pss_init_uniform": ([vp, i32, d, d], i32),
+        "pss_step": ([vp, i64], i32),
+        "pss_get_step": ([vp, P(i64)], i32),
+        "pss_set_step": ([vp, i64], i32),
+        "pss_get_field": ([vp, i32, vp, i32], i32),
+        "pss_get_spectrum": ([vp, i32, vp, i32], i32),
+        "pss_set_spectrum": ([vp, i32, vp, i32], i32),
+        "pss_structure_factor": ([vp, i32, i32, P(d), P(d), P(d)], i32),
+        "pss_sync": ([vp], i32),
+        "pss_last_error": ([vp], ctypes.c_char_p),
+        "pss_launch_count": ([vp], i64),
+        "pss_time_kernels": ([vp, i64, P(d)], i32),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = res
+    return L
+
+
+lib = _load()
+
+
+def _arr(ctype, vals):
+    vals = list(vals)
+    return (ctype * max(1, len(vals)))(*vals)
+
+
+class System:
+    """One lattice system: ``System(dim, shape, dx, dt, seed, precision)``; shape is
+    (nx,), (ny, nx) or (nz, ny, nx) like numpy arrays of the real field."""
+
+    def __init__(self, shape: Sequence[int], dt: float, dx: Sequence[float] = (1.0, 1.0, 1.0),
+                 seed: int = 0, precision: str = "f32"):
+        self.shape = tuple(int(n) for n in shape)
+        self.dim = len(self.shape)
+        n = list(reversed(self.shape)) + [1] * (3 - self.dim)
+        self.nx, self.ny, self.nz = n
+        self.precision = precision
+        self.rdtype = np.float64 if precision == "f64" else np.float32
+        self.cdtype = np.complex128 if precision == "f64" else np.complex64
+        h = ctypes.c_void_p()
+        dxs = list(dx) + [1.0] * (3 - len(dx))
+        rc = lib.pss_create_system(ctypes.byref(h), self.dim, self.nx, self.ny, self.nz, dxs[0], dxs[1], dxs[2],
+                                   float(dt), ctypes.c_uint64(int(seed) & 0xFFFFFFFFFFFFFFFF),
+                                   PSS_F64 if precision == "f64" else PSS_F32)
+        if rc != PSS_OK:
+            raise PssError(rc, lib.pss_last_error(None).decode())
+        self._h = h
+        self.half_shape = self.shape[:-1] + (self.nx // 2 + 1,)
+
+    # -- lifetime ------------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.pss_destroy_system(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _ck(self, rc: int):
+        if rc != PSS_OK:
+            raise PssError(rc, lib.pss_last_error(self._h).decode())
+
+    # -- model description ---------------------------------------------------
+    def set_stream(self, stream=None):
+        """stream: a torch.cuda.Stream, a raw cudaStream_t int, or None (legacy default)."""
+        ptr = getattr(stream, "cuda_stream", stream)
+        self._ck(lib.pss_set_stream(self._h, ctypes.c_void_p(ptr or 0)))
+
+    def add_param(self, name: str, value: float) -> int:
+        i = ctypes.c_int()
+        self._ck(lib.pss_add_param(self._h, name.encode(), float(value), ctypes.byref(i)))
+        return i.value
+
+    def set_param(self, pid: int, value: float):
+        self._ck(lib.pss_set_param(self._h, pid, float(value)))
+
+    def get_param(self, pid: int) -> float:
+        v = ctypes.c_double()
+        self._ck(lib.pss_get_param(self._h, pid, ctypes.byref(v)))
+        return v.value
+
+    def add_field(self, name: str, dynamic: bool = True) -> int:
+        i = ctypes.c_int()
+        self._ck(lib.pss_add_field(self._h, name.encode(), int(dynamic), ctypes.byref(i)))
+        return i.value
+
+    def add_term(self, field: int, implicit: bool, monomials: Iterable, factors: Iterable):
+        """monomials: (param_id or -1, scale, q2_power); factors: (field_id, power)."""
+        mono = list(monomials)
+        fac = list(factors)
+        self._ck(lib.pss_add_term(self._h, field, int(implicit), len(mono),
+                                  _arr(ctypes.c_int, [m[0] for m in mono]),
+                                  _arr(ctypes.c_double, [float(m[1]) for m in mono]),
+                                  _arr(ctypes.c_int, [m[2] for m in mono]), len(fac),
+                                  _arr(ctypes.c_int, [f[0] for f in fac]), _arr(ctypes.c_int, [f[1] for f in fac])))
+
+    def set_noise(self, field: int, D_param: int, q2_pow: int = 0):
+        self._ck(lib.pss_set_noise(self._h, field, D_param, q2_pow))
+
+    def set_dealias(self, field: int, order: int):
+        self._ck(lib.pss_set_dealias(self._h, field, order))
+
+    # -- data ----------------------------------------------------------------
+    def set_field(self, field: int, data):
+        if _is_cuda_tensor(data):
+            assert data.is_contiguous() and tuple(data.shape) == self.shape
+            self._ck(lib.pss_set_field(self._h, field, ctypes.c_void_p(data.data_ptr()), PSS_DEVICE))
+        else:
+            a = np.ascontiguousarray(data, dtype=self.rdtype).reshape(self.shape)
+            self._ck(lib.pss_set_field(self._h, field, a.ctypes.data_as(ctypes.c_void_p), PSS_HOST))
+
+    def init_uniform(self, field: int, lo: float, hi: float):
+        self._ck(lib.pss_init_uniform(self._h, field, float(lo), float(hi)))
+
+    def step(self, n: int = 1):
+        self._ck(lib.pss_step(self._h, int(n)))
+
+    def get_step(self) -> int:
+        v = ctypes.c_int64()
+        self._ck(lib.pss_get_step(self._h, ctypes.byref(v)))
+        return v.value
+
+    def set_step(self, step: int):
+        self._ck(lib.pss_set_step(self._h, int(step)))
+
+    def get_field(self, field: int, out=None):
+        """Real field; into ``out`` (numpy or torch CUDA tensor) or a new numpy array."""
+        if out is not None and _is_cuda_tensor(out):
+            self._ck(lib.pss_get_field(self._h, field, ctypes.c_void_p(out.data_ptr()), PSS_DEVICE))
+            return out
+        a = np.empty(self.shape, dtype=self.rdtype) if out is None else out
+        self._ck(lib.pss_get_field(self._h, field, a.ctypes.data_as(ctypes.c_void_p), PSS_HOST))
+        return a
+
+    def get_spectrum(self, field: int, out=None):
+        if out is not None and _is_cuda_tensor(out):
+            self._ck(lib.pss_get_spectrum(self._h, field, ctypes.c_void_p(out.data_ptr()), PSS_DEVICE))
+            return out
+        a = np.empty(self.half_shape, dtype=self.cdtype) if out is None else out
+        self._ck(lib.pss_get_spectrum(self._h, field, a.ctypes.data_as(ctypes.c_void_p), PSS_HOST))
+        return a
+
+    def set_spectrum(self, field: int, half):
+        if _is_cuda_tensor(half):
+            self._ck(lib.pss_set_spectrum(self._h, field, ctypes.c_void_p(half.data_ptr()), PSS_DEVICE))
+        else:
+            a = np.ascontiguousarray(half, dtype=self.cdtype).reshape(self.half_shape)
+            self._ck(lib.pss_set_spectrum(self._h, field, a.ctypes.data_as(ctypes.c_void_p), PSS_HOST))
+
+    def structure_factor(self, field: int, nbins: int = 64):
+        S = np.zeros(nbins)
+        cnt = np.zeros(nbins)
+        L = ctypes.c_double()
+        dp = ctypes.POINTER(ctypes.c_double)
+        self._ck(lib.pss_structure_factor(self._h, field, nbins, S.ctypes.data_as(dp), cnt.ctypes.data_as(dp),
+                                          ctypes.byref(L)))
+        return S, cnt, L.value
+
+    def time_kernels(self, n: int):
+        """Mean per-launch milliseconds of (column, inverse-y, row, forward-y) kernels over n steps."""
+        out = (ctypes.c_double * 4)()
+        self._ck(lib.pss_time_kernels(self._h, int(n), out))
+        return list(out)
+
+    def sync(self):
+        self._ck(lib.pss_sync(self._h))
+
+    @property
+    def launch_count(self) -> int:
+        return int(lib.pss_launch_count(self._h))
+
+
+def _is_cuda_tensor(x) -> bool:
+    return hasattr(x, "is_cuda") and bool(getattr(x, "is_cuda"))
+
+
+# ---------------------------------------------------------------------------
+# model builders (section "Example": Model B; its non-conserved sibling Model A)
+# ---------------------------------------------------------------------------
+def model_b(shape, dt=0.01, a=-1.0, b=1.0, K=1.0, D=0.01, noisy=True, seed=2405, precision="f32",
+            dealias_order=2, dx=(1.0, 1.0, 1.0), system: Optional[System] = None) -> System:
+    """dt phi + (a q^2 + K q^4) phi = -b q^2 phi^3, noise D q^2."""
+    s = system or System(shape, dt=dt, dx=dx, seed=seed, precision=precision)
+    add_model_b_field(s, a=a, b=b, K=K, D=D, noisy=noisy, dealias_order=dealias_order)
+    return s
+
+
+def add_model_b_field(s: System, a=-1.0, b=1.0, K=1.0, D=0.01, noisy=True, dealias_order=2, name="phi"):
+    f = s.add_field(name)
+    pa, pb, pK, pD = (s.add_param(f"{name}.{k}", v) for k, v in (("a", a), ("b", b), ("K", K), ("D", D)))
+    s.add_term(f, True, [(pa, 1.0, 1), (pK, 1.0, 2)], [(f, 1)])
+    s.add_term(f, False, [(pb, -1.0, 1)], [(f, 3)])
+    if noisy:
+        s.set_noise(f, pD, 1)
+    s.set_dealias(f, dealias_order)
+    return f
+
+
+def add_model_a_field(s: System, a=-1.0, b=1.0, K=1.0, D=0.05, noisy=True, dealias_order=2, name="psi"):
+    """dt psi + (a + K q^2) psi = -b psi^3, noise D."""
+    f = s.add_field(name)
+    pa, pb, pK, pD = (s.add_param(f"{name}.{k}", v) for k, v in (("a", a), ("b", b), ("K", K), ("D", D)))
+    s.add_term(f, True, [(pa, 1.0, 0), (pK, 1.0, 1)], [(f, 1)])
+    s.add_term(f, False, [(pb, -1.0, 0)], [(f, 3)])
+    if noisy:
+        s.set_noise(f, pD, 0)
+    s.set_dealias(f, dealias_order)
+    return f

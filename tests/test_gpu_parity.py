@@ -1,0 +1,210 @@
+"""Parity of the sm_103a path (through the C ABI) with the FP64 CPU oracle.
+
+Bars: FP32 rel-L2 <= 1e-4 and FP64 rel-L2 <= 1e-10 over <= 200 steps (sizes the
+oracle finishes in seconds, spanning several tiles and a ragged last tile),
+bit-identical results for replays, resumes and graph vs. eager launches.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from tests import inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f32": 1e-4, "f64": 1e-10}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_2405_02410_gb300 import build
+    build.build()
+
+
+def pss():
+    from paper_2405_02410_gb300 import pss as m
+    return m
+
+
+def rel(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(np.asarray(b)), 1e-300)
+
+
+SHAPES = [(4,), (64,), (1024,), (4, 4), (8, 16), (64, 64), (32, 128), (128, 32), (4, 8, 4), (8, 16, 32), (16, 16, 16)]
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+@pytest.mark.parametrize("shape", SHAPES)
+def test_transform_roundtrip_and_spectrum(shape, prec):
+    s = pss().System(shape, dt=0.1, precision=prec)
+    f = s.add_field("phi")
+    x = inputs.real_field(shape, seed=101)
+    s.set_field(f, x)
+    spec = s.get_spectrum(f)
+    ref = np.fft.rfftn(x)
+    assert rel(spec, ref) < (2e-6 if prec == "f32" else 1e-13)
+    back = s.get_field(f)
+    assert rel(back, x) < (2e-6 if prec == "f32" else 1e-13)
+
+
+@pytest.mark.parametrize("shape", [(64, 64), (8, 8, 8), (64,)])
+def test_init_uniform_matches_oracle(shape):
+    s = pss().System(shape, dt=0.1, seed=77, precision="f64")
+    f = s.add_field("phi")
+    s.init_uniform(f, -0.1, 0.3)
+    m = O.Model(shape=shape, dt=0.1, seed=77)
+    assert rel(s.get_field(f), O.init_uniform(m, -0.1, 0.3)) < 1e-13
+
+
+def _oracle_b(shape, steps, **kw):
+    m = O.model_b(shape, **kw)
+    phi = O.to_spectrum(m, O.init_uniform(m, -0.1, 0.1))
+    return O.half(O.run(m, phi, 0, steps))
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_model_b_64x64_100_steps(prec):
+    # the 64 x 64 Model B parity workload: a=-1, b=1, K=1, D=0.01, dt=0.01, 2/3 rule
+    shape, steps = (64, 64), 100
+    s = pss().model_b(shape, dt=0.01, a=-1, b=1, K=1, D=0.01, seed=2405, precision=prec)
+    s.init_uniform(0, -0.1, 0.1)
+    s.step(steps)
+    ref = _oracle_b(shape, steps, dt=0.01, a=-1, b=1, K=1, D=0.01, seed=2405)
+    err = rel(s.get_spectrum(0), ref)
+    assert err < TOL[prec], err
+    assert rel(s.get_field(0), np.fft.irfftn(ref, s=shape)) < TOL[prec] * 10
+
+
+def _full_from_half(half, shape):
+    """Hermitian completion of a half spectrum (numpy helper, no method arithmetic)."""
+    return np.fft.fftn(np.fft.irfftn(half, s=shape))
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+@pytest.mark.parametrize("shape,order,noisy", [
+    ((64,), 2, True), ((256,), 3, True), ((8, 16), 2, True), ((32, 128), 0, True), ((128, 32), 3, False),
+    ((4, 4), 2, True), ((8, 8, 8), 2, True), ((8, 16, 32), 3, True), ((16, 16, 16), 0, False),
+])
+def test_model_b_shapes_and_dealias_orders(shape, order, noisy, prec):
+    steps = 50
+    kw = dict(dt=0.01, a=-1, b=1, K=1, D=0.05, seed=11, dealias_order=order, noisy=noisy)
+    s = pss().model_b(shape, precision=prec, **kw)
+    s.init_uniform(0, -0.1, 0.1)
+    s.step(steps)
+    ref = _oracle_b(shape, steps, **kw)
+    err = rel(s.get_spectrum(0), ref)
+    assert err < TOL[prec], err
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_model_a_and_b_pair_3d(prec):
+    # two uncoupled fields in one system (Model A field 0, Model B field 1), sharing the seed
+    shape, steps = (8, 16, 16), 40
+    P = pss()
+    s = P.System(shape, dt=0.005, seed=5, precision=prec)
+    P.add_model_a_field(s, a=-1, b=1, K=1, D=0.05, name="psi")
+    P.add_model_b_field(s, a=-1, b=1, K=1, D=0.05, name="phi")
+    s.init_uniform(0, -0.05, 0.05)
+    s.init_uniform(1, -0.05, 0.05)
+    s.step(steps)
+    ma = O.model_a(shape, dt=0.005, a=-1, b=1, K=1, D=0.05, seed=5, field_id=0)
+    mb = O.model_b(shape, dt=0.005, a=-1, b=1, K=1, D=0.05, seed=5, field_id=1)
+    for fid, m in ((0, ma), (1, mb)):
+        ref = O.half(O.run(m, O.to_spectrum(m, O.init_uniform(m, -0.05, 0.05)), 0, steps))
+        err = rel(s.get_spectrum(fid), ref)
+        assert err < TOL[prec], (fid, err)
+
+
+def test_noise_only_linear_model_every_step():
+    # b = 0: phi' = (phi + xi) / (1 + dt O); checks the noise of every mode, step by step
+    shape = (16, 32)
+    P = pss()
+    s = P.System(shape, dt=0.1, seed=9, precision="f64")
+    f = s.add_field("phi")
+    pa, pD = s.add_param("a", 0.5), s.add_param("D", 0.3)
+    s.add_term(f, True, [(pa, 1.0, 0), (-1, 1.0, 1)], [(f, 1)])
+    s.set_noise(f, pD, 0)
+    m = O.Model(shape=shape, dt=0.1, lhs=[(0.5, 0), (1.0, 1)], noise_D=0.3, noise_pow=0, noisy=True, seed=9)
+    phi = np.zeros(shape, dtype=complex)
+    for k in range(3):
+        s.step(1)
+        phi = O.run(m, phi, k, 1)
+        assert rel(s.get_spectrum(f), O.half(phi)) < 1e-12
+
+
+def test_mass_is_conserved_bitwise_in_the_spectrum():
+    s = pss().model_b((64, 64), D=0.1, seed=3, precision="f32")
+    s.init_uniform(0, -0.2, 0.4)
+    m0 = s.get_spectrum(0)[0, 0]
+    s.step(200)
+    assert s.get_spectrum(0)[0, 0] == m0
+
+
+def test_graph_replay_resume_and_determinism():
+    P = pss()
+
+    def run(chunks):
+        s = P.model_b((64, 64), D=0.05, seed=21, precision="f32")
+        s.init_uniform(0, -0.1, 0.1)
+        for c in chunks:
+            s.step(c)
+        return s.get_spectrum(0), s.get_step()
+
+    a, na = run([40])          # 2 graph launches of 16 steps + 8 eager steps
+    b, nb = run([1] * 40)      # eager only
+    c, nc = run([17, 3, 20])
+    assert na == nb == nc == 40
+    np.testing.assert_array_equal(a, b)
+    np.testing.assert_array_equal(a, c)
+
+
+def test_structure_factor_matches_oracle():
+    shape, steps = (64, 64), 60
+    kw = dict(dt=0.01, a=-1, b=1, K=1, D=0.05, seed=13)
+    s = pss().model_b(shape, precision="f64", **kw)
+    s.init_uniform(0, -0.1, 0.1)
+    s.step(steps)
+    S, cnt, L = s.structure_factor(0, 64)
+    m = O.model_b(shape, **kw)
+    full = O.run(m, O.to_spectrum(m, O.init_uniform(m, -0.1, 0.1)), 0, steps)
+    So, co, Lo = O.structure_factor(m, full, 64)
+    np.testing.assert_array_equal(cnt, co)
+    assert rel(S, So) < 1e-10 and abs(L - Lo) < 1e-10 * Lo
+
+
+def test_set_spectrum_roundtrip_and_param_change():
+    P = pss()
+    s = P.model_b((32, 32), D=0.0, noisy=False, seed=1, precision="f64")
+    half = np.fft.rfftn(inputs.real_field((32, 32), seed=5, lo=-0.2, hi=0.2))
+    s.set_spectrum(0, half)
+    assert rel(s.get_spectrum(0), half) == 0
+    s.set_param(0, -0.5)   # a
+    s.step(20)
+    m = O.model_b((32, 32), a=-0.5, D=0.0, noisy=False)
+    ref = O.half(O.run(m, _full_from_half(half, (32, 32)), 0, 20))
+    assert rel(s.get_spectrum(0), ref) < 1e-10
+
+
+def test_nonfinite_is_reported():
+    P = pss()
+    s = P.model_b((16, 16), noisy=False, precision="f32")
+    x = np.zeros((16, 16))
+    x[3, 4] = np.inf
+    s.set_field(0, x)
+    s.step(2)
+    with pytest.raises(P.PssError) as ei:
+        s.sync()
+    assert ei.value.code == P.PSS_ENONFINITE
+
+
+def test_model_b_1024_sampled_against_oracle():
+    # the 1024 x 1024 workload in its timed launch configuration, a few steps, every mode checked
+    shape, steps = (1024, 1024), 3
+    kw = dict(dt=0.01, a=-1, b=1, K=1, D=0.01, seed=2405)
+    s = pss().model_b(shape, precision="f32", **kw)
+    s.init_uniform(0, -0.1, 0.1)
+    s.step(steps)
+    ref = _oracle_b(shape, steps, **kw)
+    assert rel(s.get_spectrum(0), ref) < 1e-4
