@@ -81,6 +81,7 @@ def lib():
         _lib.orc_uniform24.argtypes = [ctypes.c_uint32]
         _lib.orc_uniform24.restype = ctypes.c_double
         _lib.orc_normal_pair.argtypes = [ctypes.c_uint64] + [ctypes.c_uint32] * 4 + [d, d]
+        _lib.orc_normal_pair_words.argtypes = [ctypes.c_uint64] + [ctypes.c_uint32] * 4 + [ctypes.c_int, d, d]
         _lib.orc_dft.argtypes = [ctypes.c_int, P(ctypes.c_int), d, ctypes.c_int, ctypes.c_int]
         _lib.orc_mask.argtypes = [f, ctypes.c_int, ctypes.c_int, ctypes.c_int]
         _lib.orc_q2.argtypes = [f, ctypes.c_int, ctypes.c_int, ctypes.c_int]
@@ -193,6 +194,13 @@ def uniform24(x: int) -> float:
 def normal_pair(seed, c0, c1, c2, c3):
     n1, n2 = ctypes.c_double(), ctypes.c_double()
     lib().orc_normal_pair(ctypes.c_uint64(int(seed)), c0, c1, c2, c3, ctypes.byref(n1), ctypes.byref(n2))
+    return n1.value, n2.value
+
+
+def normal_pair_words(seed, c0, c1, c2, c3, upper):
+    n1, n2 = ctypes.c_double(), ctypes.c_double()
+    lib().orc_normal_pair_words(ctypes.c_uint64(int(seed)), c0, c1, c2, c3, int(upper), ctypes.byref(n1),
+                                ctypes.byref(n2))
     return n1.value, n2.value
 
 

@@ -69,12 +69,18 @@ double orc_uniform24(uint32_t x)
 void orc_normal_pair(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
                      double *n1, double *n2)
 {
+    orc_normal_pair_words(seed, c0, c1, c2, c3, 0, n1, n2);
+}
+
+void orc_normal_pair_words(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                           int upper, double *n1, double *n2)
+{
     uint32_t ctr[4] = {c0, c1, c2, c3};
     uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
     uint32_t x[4];
     orc_philox4x32_10(ctr, key, x);
-    double u0 = orc_uniform24(x[0]);
-    double u1 = orc_uniform24(x[1]);
+    double u0 = orc_uniform24(x[upper ? 2 : 0]);
+    double u1 = orc_uniform24(x[upper ? 3 : 1]);
     /* Box-Muller transform */
     double r = sqrt(-2.0 * log(u0));
     *n1 = r * cos(2.0 * M_PI * u1);
@@ -289,10 +295,19 @@ int orc_noise(const orc_field *f, int64_t step, double *xi)
                 long par = pkx <= N[0] / 2 ? ((long)pkz * N[1] + pky) * Hx + pkx : -1;
                 long canon;
                 int conj;
+                int ckx, cky, ckz;   /* the canonical member */
                 if (own < 0) { canon = par; conj = 1; }
                 else if (par < 0) { canon = own; conj = 0; }
                 else { canon = own < par ? own : par; conj = canon != own; }
+                if (canon == own) { ckx = kx; cky = ky; ckz = kz; }
+                else { ckx = pkx; cky = pky; ckz = pkz; }
                 int selfconj = own >= 0 && own == par;
+                /* One Philox call serves the canonical modes kx = 2j and 2j + 1
+                 * of a row: counter word 0 = ((kz Ny + ky) Hxe + kx) / 2 with
+                 * Hxe = Nx/2+1 rounded up to even; words (x0, x1) feed even kx,
+                 * (x2, x3) odd kx. */
+                long Hxe = Hx + (Hx & 1);
+                long pairidx = (((long)ckz * N[1] + cky) * Hxe + ckx) >> 1;
                 double q2 = orc_q2(f, kx, ky, kz);
                 double Dq = f->noise_D * pow(q2, (double)f->noise_pow);
                 if (f->noise_pow > 0 && q2 == 0.0) Dq = 0.0;
@@ -300,8 +315,8 @@ int orc_noise(const orc_field *f, int64_t step, double *xi)
                  * 2 D~ (2pi)^d delta(q+q') delta(t-t') integrated over one step */
                 double sigma = sqrt((double)ns * Dq * f->dt / dV);
                 double n1, n2;
-                orc_normal_pair(f->seed, (uint32_t)canon, (uint32_t)step, (uint32_t)f->field_id, 0u,
-                                &n1, &n2);
+                orc_normal_pair_words(f->seed, (uint32_t)pairidx, (uint32_t)step, (uint32_t)f->field_id, 0u,
+                                      ckx & 1, &n1, &n2);
                 if (selfconj) {
                     xi[2 * i] = sqrt(2.0) * sigma * n1;
                     xi[2 * i + 1] = 0.0;

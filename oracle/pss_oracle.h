@@ -52,9 +52,12 @@ typedef struct {
 void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 /* u = ((x >> 8) + 0.5) / 2^24, strictly inside (0, 1). */
 double orc_uniform24(uint32_t x);
-/* Box-Muller pair from Philox(ctr = (c0, c1, c2, c3), key = seed). */
+/* Box-Muller pair from Philox(ctr = (c0, c1, c2, c3), key = seed): from
+ * output words (x0, x1), or (x2, x3) when upper != 0. */
 void orc_normal_pair(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
                      double *n1, double *n2);
+void orc_normal_pair_words(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                           int upper, double *n1, double *n2);
 
 /* In-place d-dimensional complex transform of data[2*N_sites]; sign = -1
  * forward, +1 inverse (both unnormalised).  method: 1 naive DFT, 2 radix-2 FFT. */
@@ -67,7 +70,10 @@ double orc_q2(const orc_field *f, int kx, int ky, int kz);
 
 /* P_q = F[ (F^-1[m phi])^p ] for a full spectrum phi (Eq. nonlin_general without M). */
 int orc_nonlinear(const orc_field *f, const double *phi, double *P);
-/* Noise increment xi_q of time step `step` (full spectrum), i.e. sqrt(dt) eta~_q of Eq. timeupdate. */
+/* Noise increment xi_q of time step `step` (full spectrum), i.e. sqrt(dt) eta~_q of Eq. timeupdate.
+ * Counter (((kz Ny + ky) Hxe + kx) / 2, step, field_id, 0) of the canonical
+ * member (kx, ky, kz) of the Hermitian pair, Hxe = Nx/2+1 rounded up to even;
+ * words (x0, x1) for even kx, (x2, x3) for odd kx. */
 int orc_noise(const orc_field *f, int64_t step, double *xi);
 /* nsteps steps of Eq. timeupdate on the full spectrum phi, steps step0 .. step0+nsteps-1. */
 int orc_run(const orc_field *f, double *phi, int64_t step0, int64_t nsteps);

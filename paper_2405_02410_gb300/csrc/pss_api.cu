@@ -120,6 +120,7 @@ template <typename T> SysP<T> sys_params(const pss_system *s) {
     SysP<T> p{};
     p.dim = s->dim;
     p.nx = s->nx; p.ny = s->ny; p.nz = s->nz; p.hx = s->hx;
+    p.hxe = s->hx + (s->hx & 1);
     p.ntiles = s->ntiles; p.rows = s->rows;
     p.n_outer = s->n_outer; p.n_inner = s->n_inner;
     const double two_pi = 6.283185307179586476925286766559;
@@ -145,7 +146,7 @@ template <typename T> FieldP<T> field_params(const pss_system *s, int fi) {
     double dV = 1.0;
     for (int j = 0; j < s->dim; ++j) dV *= s->dx[j];
     p.noisy = f.noisy ? 1 : 0;
-    p.amp2 = f.noisy ? T((double)s->nsites * pval(s, f.noise_param) * s->dt / dV) : T(0);
+    p.sigma0 = f.noisy ? T(std::sqrt(std::max(0.0, (double)s->nsites * pval(s, f.noise_param) * s->dt / dV))) : T(0);
     p.noise_pow = f.noise_pow;
     p.power = f.power;
     p.kmax[0] = kmax_axis(s->nx, f.dealias);
@@ -156,21 +157,23 @@ template <typename T> FieldP<T> field_params(const pss_system *s, int fi) {
 }
 
 // ---- launch shapes -------------------------------------------------------
+// tiles per CTA of the column kernel: a power of two, so that the CTA's
+// FFT count F = tiles * kTileW * NP is one; aims at >= 64 threads per CTA
 int col_tiles_per_cta(const pss_system *s) {
     const int NP = s->dim == 3 ? 2 : 1;
     const int per_tile = kTileW * NP * fft_TPF(s->n_inner);
-    int tc = std::max(1, 64 / per_tile);
-    tc = std::min(tc, s->ntiles);
-    while (tc > 1 && tc * per_tile > 256) --tc;
+    int tc = 1;
+    while (tc * 2 * per_tile <= 64 && tc * 2 <= s->ntiles) tc *= 2;
     return tc;
 }
 
+// row pairs per CTA of the row kernel: a power of two with G * TPF <= 128
+// threads, and at least ~8 CTAs when there are few rows
 int row_G(const pss_system *s) {
     const int tpf = fft_TPF(s->nx);
-    int G = std::max(1, 128 / tpf);
     const int want = std::max(1, (s->rows / 2 + 7) / 8);
-    G = std::min(G, want);
-    while (G > 1 && G * tpf > 256) --G;
+    int G = 1;
+    while (G * 2 * tpf <= 128 && G * 2 <= want) G *= 2;
     return G;
 }
 
@@ -186,14 +189,16 @@ int kept_cols(const pss_system *s, int fi) { return std::min(kmax_axis(s->nx, s-
 
 // ---- kernel sequences ----------------------------------------------------
 // Optional per-launch CUDA events (pss_time_kernels): kind 0 = k_col,
-// 1 = k_mid inverse, 2 = k_row, 3 = k_mid forward.
+// 1 = k_mid inverse, 2 = k_row, 3 = k_mid forward.  The events are recorded
+// into a captured graph as event-record nodes, so that the GPU never waits
+// for the host between an event and its kernel.
 struct Timer {
     std::vector<cudaEvent_t> ev[4];
     int begin(int kind, cudaStream_t st) {
         cudaEvent_t e;
         if (cudaEventCreate(&e) != cudaSuccess) return -1;
         ev[kind].push_back(e);
-        return cudaEventRecord(e, st) == cudaSuccess ? 0 : -1;
+        return cudaEventRecordWithFlags(e, st, cudaEventRecordExternal) == cudaSuccess ? 0 : -1;
     }
     ~Timer() {
         for (auto &v : ev)
@@ -231,6 +236,7 @@ template <typename T> struct Seq {
         a.d_status = s->d_status;
         a.mode = mode;
         a.tiles_per_cta = col_tiles_per_cta(s);
+        a.F = a.tiles_per_cta * kTileW * (s->dim == 3 ? 2 : 1);
         a.n_tiles = mode == COL_INV_MASK ? max_kept_tiles() : s->ntiles;
         const int gx = (a.n_tiles + a.tiles_per_cta - 1) / a.tiles_per_cta;
         const int gy = s->dim == 3 ? s->ny / 2 + 1 : 1;
@@ -255,6 +261,7 @@ template <typename T> struct Seq {
         }
         a.tw = (const cplx<T> *)s->tw;
         a.d_step = s->d_step;
+        a.d_status = s->d_status;
         a.mode = mode;
         a.G = row_G(s);
         for (int i = 0; i < nf; ++i) a.kx_cols[i] = mode == ROW_FUSED ? kept_cols(s, f0 + i) : s->hx;
@@ -277,6 +284,7 @@ template <typename T> struct Seq {
         }
         a.tw = (const cplx<T> *)s->tw;
         a.d_step = s->d_step;
+        a.d_status = s->d_status;
         a.mode = mode;
         a.PZ = mid_PZ(s);
         a.inc_step = inc ? 1 : 0;
@@ -380,12 +388,22 @@ template <typename T> int run_steps(pss_system *s, int64_t n) {
 
 template <typename T> int timed_steps(pss_system *s, int64_t n, double *avg_ms) {
     Timer timer;
-    Seq<T> q{s, s->stream, 0, (int)s->fields.size(), &timer};
-    for (int64_t k = 0; k < n; ++k) {
-        int rc = q.one_step();
-        if (rc) return rc;
-    }
-    CK(cudaStreamSynchronize(s->stream));
+    Seq<T> q{s, s->cap_stream, 0, (int)s->fields.size(), &timer};
+    CK(cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal));
+    int rc = PSS_OK;
+    for (int64_t k = 0; k < n && rc == PSS_OK; ++k) rc = q.one_step();
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(s->cap_stream, &g);
+    if (rc) { if (g) cudaGraphDestroy(g); return rc; }
+    if (e != cudaSuccess) return cuda_fail(s, e, "cudaStreamEndCapture");
+    cudaGraphExec_t ge = nullptr;
+    e = cudaGraphInstantiate(&ge, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(s, e, "cudaGraphInstantiate");
+    e = cudaGraphLaunch(ge, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    cudaGraphExecDestroy(ge);
+    if (e != cudaSuccess) return cuda_fail(s, e, "timed graph");
     for (int kind = 0; kind < 4; ++kind) {
         const auto &v = timer.ev[kind];
         double tot = 0;

@@ -1,7 +1,8 @@
 // pss_device.cuh -- device building blocks of the sm_103a pseudo-spectral step:
 // complex arithmetic, the counter-based Philox4x32-10 generator, in-register
-// radix-2/4/8/16 DFTs and the shared-memory Stockham pass that strings them
-// into length-N FFTs (the F and F^-1 of Eq. cubicexample, arXiv:2405.02410).
+// radix-2/4/8/16 DFTs, the shared-memory Stockham pass that strings them into
+// length-N FFTs (the F and F^-1 of Eq. cubicexample, arXiv:2405.02410), and
+// the TMA bulk-copy / mbarrier helpers that stage tiles into shared memory.
 #pragma once
 
 #include <cstdint>
@@ -14,14 +15,12 @@ namespace pss {
 // ---------------------------------------------------------------------------
 // complex numbers (float2 / double2)
 // ---------------------------------------------------------------------------
-
 template <typename T> __device__ __forceinline__ cplx<T> mk(T x, T y) { cplx<T> r; r.x = x; r.y = y; return r; }
 template <typename T> __device__ __forceinline__ cplx<T> cadd(cplx<T> a, cplx<T> b) { return mk<T>(a.x + b.x, a.y + b.y); }
 template <typename T> __device__ __forceinline__ cplx<T> csub(cplx<T> a, cplx<T> b) { return mk<T>(a.x - b.x, a.y - b.y); }
 template <typename T> __device__ __forceinline__ cplx<T> cmul(cplx<T> a, cplx<T> b) {
     return mk<T>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
-template <typename T> __device__ __forceinline__ cplx<T> cconj(cplx<T> a) { return mk<T>(a.x, -a.y); }
 template <typename T> __device__ __forceinline__ cplx<T> cscale(cplx<T> a, T s) { return mk<T>(a.x * s, a.y * s); }
 
 // ---------------------------------------------------------------------------
@@ -50,12 +49,19 @@ template <typename T> __device__ __forceinline__ T uniform24(uint32_t x) {
     return (T(x >> 8) + T(0.5)) * T(5.9604644775390625e-08);
 }
 
-// Box-Muller pair from two uniforms; sincospi(2 u1) gives cos/sin(2 pi u1) with
-// an exact argument.
+// square root and reciprocal: FP32 through the hardware approximations
+// (about 2 ulp), FP64 correctly rounded
+__device__ __forceinline__ float fast_sqrt(float x) { return x > 0.0f ? x * rsqrtf(x) : 0.0f; }
+__device__ __forceinline__ double fast_sqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float fast_rcp(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ double fast_rcp(double x) { return 1.0 / x; }
+
+// Box-Muller pair.  FP32 uses the hardware log2 / sin / cos approximations
+// (absolute error ~1e-6 on these arguments); FP64 uses the libdevice calls.
 __device__ __forceinline__ void box_muller(float u0, float u1, float &n1, float &n2) {
-    const float r = sqrtf(-2.0f * logf(u0));
+    const float r = fast_sqrt(-2.0f * __logf(u0));
     float s, c;
-    sincospif(2.0f * u1, &s, &c);
+    __sincosf(6.283185307179586f * u1, &s, &c);
     n1 = r * c;
     n2 = r * s;
 }
@@ -124,86 +130,190 @@ template <int R, int DIR, typename T> __device__ __forceinline__ void dft_reg(cp
 }
 
 // ---------------------------------------------------------------------------
-// Batched length-N Stockham FFT.  A CTA runs F FFTs side by side; FFT f is
-// served by TPF = N / E threads ("lanes"), each holding E = min(N, 16) values
-// in registers.  On entry and on exit lane l holds positions l + TPF * e
-// (e = 0..E-1) in natural order.  Passes exchange data through shared memory
-// laid out as element (pos, f) at (pos + pos/16) * F + f: the one-slot pad per
-// 16 positions keeps the stride-R writes of the first pass free of bank
-// conflicts for F <= 16.
+// Batched length-N Stockham FFT in shared memory.  A CTA runs several FFTs
+// side by side; FFT f is served by TPF = N/16 threads ("lanes"; one thread
+// for N <= 16) and owns a contiguous buffer slice of SF elements in which
+// position p lives at pos + pos/16 (one pad slot per 16 keeps the stride-R
+// writes of a pass free of bank conflicts).  SF is chosen per thread mapping
+// so that FFTs side by side fall in different banks too.
 //
 // Stockham radix-R pass with P = product of the radices already done:
 // butterfly i (0 <= i < N/R) reads x[i + r N/R], multiplies by
 // exp(DIR 2 pi i r k / (P R)) with k = i mod P, transforms over r, and writes
-// y[(i / P) P R + k + r P].
+// y[(i / P) P R + k + r P].  N = R0 * 16^m: one radix-R0 pass, then m radix-16
+// passes that share one loop body.  The first pass reads through a source
+// functor and the last pass writes through a sink functor, so that
+// element-wise work (a power, a mask, a scale, a store to global memory)
+// rides on the loads and stores the transform makes anyway.
 // ---------------------------------------------------------------------------
-constexpr int kTwiddleN = 1024;   // roots-of-unity table length (largest FFT)
+constexpr int kTwiddleLog = 10;
+constexpr int kTwiddleN = 1 << kTwiddleLog;   // roots-of-unity table length (largest FFT)
 
 template <int N> struct FftShape {
-    static constexpr int E = N < 16 ? N : 16;
-    static constexpr int TPF = N / E;
+    static constexpr int E = N < 16 ? N : 16;   // values per thread and pass
+    static constexpr int TPF = N / E;           // threads per FFT
+    static constexpr int LOG = N <= 1 ? 0 : N <= 2 ? 1 : N <= 4 ? 2 : N <= 8 ? 3 : N <= 16 ? 4 : N <= 32 ? 5 :
+                               N <= 64 ? 6 : N <= 128 ? 7 : N <= 256 ? 8 : N <= 512 ? 9 : 10;
+    static constexpr int R0 = (LOG % 4 == 0) ? (N > 1 ? 16 : 1) : (1 << (LOG % 4));
 };
 
 __device__ __forceinline__ int spad(int pos) { return pos + (pos >> 4); }
+__host__ __device__ constexpr int padded(int n) { return n + n / 16; }
 
-template <typename T, int N, int DIR, int P>
-__device__ __forceinline__ void fft_passes(cplx<T> *v, int lane, cplx<T> *sbuf, int F, int f,
-                                           const cplx<T> *__restrict__ tw) {
-    constexpr int E = FftShape<N>::E, TPF = FftShape<N>::TPF;
-    constexpr int REM = N / P;
-    constexpr int R = REM >= 16 ? 16 : REM;
-    constexpr bool LAST = (P * R == N);
-    constexpr int BPT = E / R;                    // butterflies per thread
-    static_assert(R >= 1 && E % R == 0, "radix must divide the values per thread");
-    cplx<T> out[E];
-#pragma unroll
+// Buffer slice per FFT when consecutive threads are lanes of one FFT: the
+// slices of FFTs sharing a half-warp (TPF < 16) start TPF banks apart.
+__host__ __device__ constexpr int sf_lane_fastest(int n) { return n < 16 ? n + 1 : padded(n); }
+// Buffer slice per FFT when consecutive threads belong to consecutive FFTs
+// (F FFTs per CTA): slices start 16/F (F <= 16) or an odd number of elements apart.
+__host__ __device__ constexpr int sf_fft_fastest(int n, int F) {
+    const int m = F >= 16 ? 1 : 16 / F;
+    const int s = padded(n) > 1 ? padded(n) : 1;
+    return s + ((m - s % 16 + 16) % 16);
+}
+
+// Buffer slice per FFT for the row kernel: lane-fastest passes, and a
+// split loop that reads 4 pairs side by side (slices 8 banks apart when a
+// half-warp is a single FFT, N >= 256).
+__host__ __device__ constexpr int sf_row(int n) {
+    return n >= 256 ? padded(n) + ((4 - padded(n) % 16 + 16) % 16) : sf_lane_fastest(n);
+}
+
+template <typename T, int N, int R, int DIR, class Src, class Dst>
+__device__ __forceinline__ void stockham_pass(Src src, Dst dst, int logP, int lane,
+                                              const cplx<T> *__restrict__ tw) {
+    constexpr int LOGR = R == 1 ? 0 : R == 2 ? 1 : R == 4 ? 2 : R == 8 ? 3 : 4;
+    constexpr int TPF = FftShape<N>::TPF;
+    constexpr int STRIDE = N / R;
+    constexpr int BPT = STRIDE / TPF;            // butterflies per thread
+    const int P = 1 << logP;
+    const int twshift = kTwiddleLog - logP - LOGR;
+#pragma unroll 1
     for (int s = 0; s < BPT; ++s) {
         const int i = lane + s * TPF;
         const int k = i & (P - 1);
         cplx<T> u[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) u[r] = v[s + r * BPT];
-        if constexpr (P > 1) {
+        for (int r = 0; r < R; ++r) u[r] = src(i + r * STRIDE);
+        if (P > 1) {
+            const int kk = k << twshift;
 #pragma unroll
             for (int r = 1; r < R; ++r) {
                 // exp(DIR 2 pi i r k / (P R)) from the forward table exp(-2 pi i m / kTwiddleN)
-                const int m = r * k * (kTwiddleN / (P * R));
-                cplx<T> w = tw[m];
+                cplx<T> w = tw[r * kk];
                 if (DIR > 0) w.y = -w.y;
                 u[r] = cmul<T>(u[r], w);
             }
         }
         dft_reg<R, DIR, T>(u);
+        const int j = ((i - k) << LOGR) + k;
 #pragma unroll
-        for (int r = 0; r < R; ++r) out[s + r * BPT] = u[r];
-        if constexpr (!LAST) {
-            const int j = (i / P) * P * R + k;
-#pragma unroll
-            for (int r = 0; r < R; ++r) sbuf[spad(j + r * P) * F + f] = u[r];
-        }
+        for (int r = 0; r < R; ++r) dst(j + (r << logP), u[r]);
     }
-    if constexpr (LAST) {
-        // positions i + r N/R = lane + TPF (s + r BPT): already the exit layout
-#pragma unroll
-        for (int e = 0; e < E; ++e) v[e] = out[e];
+}
+
+// Full unnormalised FFT (DIR = -1 forward, +1 inverse) of the thread's FFT.
+// src(p) gives input position p; the last pass hands (p, value, free) to
+// sink, where `free` is this FFT's slice of the work buffer the last pass
+// does not read (b0 or b1; the returned index says which).  b0, b1 are this
+// FFT's slices; src may read b1 but never b0.  Every thread of the CTA must
+// call it (it synchronises the CTA between passes); threads with
+// active = false only take part in the barriers.
+template <typename T, int N, int DIR, class Src, class Sink>
+__device__ __forceinline__ int fft_run(Src src, Sink sink, cplx<T> *b0, cplx<T> *b1, int lane, bool active,
+                                       const cplx<T> *__restrict__ tw) {
+    using S = FftShape<N>;
+    if constexpr (N == 1) {
+        if (active) sink(0, src(0), b0);
+        return 0;
+    } else if constexpr (S::LOG <= 4) {
+        if (active) stockham_pass<T, N, S::R0, DIR>(src, [&](int p, cplx<T> v) { sink(p, v, b0); }, 0, lane, tw);
+        return 0;
     } else {
+        if (active)
+            stockham_pass<T, N, S::R0, DIR>(src, [&](int p, cplx<T> v) { b0[spad(p)] = v; }, 0, lane, tw);
         __syncthreads();
-#pragma unroll
-        for (int e = 0; e < E; ++e) v[e] = sbuf[spad(lane + TPF * e) * F + f];
-        __syncthreads();
-        fft_passes<T, N, DIR, P * R>(v, lane, sbuf, F, f, tw);
+        cplx<T> *cur = b0, *nxt = b1;
+        int which = 1;
+        int logP = S::LOG % 4 == 0 ? 4 : S::LOG % 4;
+#pragma unroll 1
+        for (; logP + 4 < S::LOG; logP += 4) {
+            if (active)
+                stockham_pass<T, N, 16, DIR>([&](int p) { return cur[spad(p)]; },
+                                             [&](int p, cplx<T> v) { nxt[spad(p)] = v; }, logP, lane, tw);
+            __syncthreads();
+            cplx<T> *tmp = cur; cur = nxt; nxt = tmp;
+            which ^= 1;
+        }
+        if (active)
+            stockham_pass<T, N, 16, DIR>([&](int p) { return cur[spad(p)]; },
+                                         [&](int p, cplx<T> v) { sink(p, v, nxt); }, logP, lane, tw);
+        return which;
     }
 }
 
-// Full unnormalised FFT of the values held by this thread (see above).
-// Every thread of the CTA must call it (it synchronises the CTA).
-template <typename T, int N, int DIR>
-__device__ __forceinline__ void fft(cplx<T> *v, int lane, cplx<T> *sbuf, int F, int f,
-                                    const cplx<T> *__restrict__ tw) {
-    if constexpr (N > 1) fft_passes<T, N, DIR, 1>(v, lane, sbuf, F, f, tw);
+// ---------------------------------------------------------------------------
+// TMA bulk copies (cp.async.bulk, no tensor map) completing on an mbarrier.
+// Every wait is bounded: after kWaitLimit polls the kernel records
+// PSS_STATUS_TIMEOUT and takes its early exit.
+// ---------------------------------------------------------------------------
+constexpr int kWaitLimit = 1 << 22;
+constexpr int kStatusNonFinite = 1;
+constexpr int kStatusTimeout = 2;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
-// shared-memory complex elements one FFT batch needs for its exchanges
-__host__ __device__ constexpr int fft_smem_elems(int N, int F) { return (N + N / 16) * F; }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// global -> shared bulk copy of `bytes` (multiple of 16; both addresses 16-byte aligned)
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+// shared -> global bulk copy (bytes a multiple of 16; both addresses 16-byte
+// aligned); the issuing thread commits and later waits for the group
+__device__ __forceinline__ void bulk_s2g(void *dst, const void *src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_u32(src)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// generic-proxy shared-memory writes become visible to the bulk copy engine
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t phase) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(phase)
+        : "memory");
+    return ok != 0;
+}
+
+// All threads wait for phase `phase` of `bar`.  Returns true for the whole
+// CTA when the copies landed; false (for the whole CTA) when a bounded wait
+// ran out, after a second bounded wait for the copies still in flight.
+__device__ __forceinline__ bool mbar_wait_all(uint64_t *bar, uint32_t phase, int *status) {
+    bool ok = false;
+    for (int it = 0; it < kWaitLimit && !ok; ++it) ok = mbar_try_wait(bar, phase);
+    if (__syncthreads_and(ok)) return true;
+    if (threadIdx.x == 0 && status) atomicOr(status, kStatusTimeout);
+    for (int it = 0; it < kWaitLimit && !ok; ++it) ok = mbar_try_wait(bar, phase);
+    __syncthreads();
+    return false;
+}
 
 }  // namespace pss

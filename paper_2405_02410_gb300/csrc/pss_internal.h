@@ -27,7 +27,7 @@ constexpr int kPolyTerms = 5;   // operators are polynomials of degree <= 4 in q
 template <typename T> struct FieldP {
     T O[kPolyTerms];      // implicit operator O(q) = sum O[p] (q^2)^p  (L~ = -O)
     T M[kPolyTerms];      // explicit operator M(q) applied to the product term
-    T amp2;               // N_sites * D * dt / dV (noise variance per component and unit D~/D)
+    T sigma0;             // sqrt(N_sites D dt / dV): noise std per component is sigma0 |q|^noise_pow
     int noise_pow;        // D~ = D (q^2)^noise_pow
     int noisy;
     int power;            // product (phi^d)^power; 0 = no explicit term
@@ -37,6 +37,7 @@ template <typename T> struct FieldP {
 
 template <typename T> struct SysP {
     int dim, nx, ny, nz, hx;
+    int hxe;              // hx rounded up to even (row width of the noise counter)
     int ntiles, rows;     // rows = ny * nz
     int n_outer, n_inner;
     T gx, gy, gz;         // 2 pi / (N dx) per axis (0 for unused axes)
@@ -59,6 +60,7 @@ template <typename T> struct ColArgs {
     const long long *d_step;
     int *d_status;
     int mode, tiles_per_cta, n_tiles;
+    int F;                // FFTs per CTA = tiles_per_cta * kTileW * (2 in 3D, else 1); a power of two
 };
 
 template <typename T> struct RowArgs {
@@ -70,6 +72,7 @@ template <typename T> struct RowArgs {
     T *real_out[kMaxFields];
     const cplx<T> *tw;
     long long *d_step;
+    int *d_status;
     int kx_cols[kMaxFields];   // half-spectrum columns read from the input (the rest are zero)
     int mode, G, inc_step;
 };
@@ -81,6 +84,7 @@ template <typename T> struct MidArgs {
     cplx<T> *out[kMaxFields];
     const cplx<T> *tw;
     long long *d_step;
+    int *d_status;
     int mode, PZ, inc_step;
 };
 

@@ -11,6 +11,11 @@
 // so each step reads and writes phi_q once and moves the product through
 // HBM twice.  In 3D the column kernel runs along z, and k_mid adds the y
 // passes (inverse before k_row, forward after it).  1D is 2D with one row.
+//
+// Every kernel stages its input tiles into shared memory with TMA bulk copies
+// (one mbarrier, bounded wait), transforms there, does its element-wise work
+// in rolled loops over shared memory and writes its outputs with coalesced
+// stores.
 #pragma once
 
 #include "pss_device.cuh"
@@ -24,153 +29,260 @@ template <typename T> __device__ __forceinline__ T poly5(const T *c, T x) {
     return (((c[4] * x + c[3]) * x + c[2]) * x + c[1]) * x + c[0];
 }
 
-template <typename T> __device__ __forceinline__ int signed_k(int k, int n) { return k < (n + 1) / 2 ? k : k - n; }
+__device__ __forceinline__ int signed_k(int k, int n) { return k < (n + 1) / 2 ? k : k - n; }
 
-// Noise increment xi_q of one mode of the half spectrum (Eq. noise_eq over one
-// step).  Each Hermitian pair is drawn once, with Philox counter word 0 = the
-// smaller of the two half-spectrum indices [kz][ky][kx]; a mode that is its
-// own partner is real.
+// Noise increments xi_q of two neighbouring modes kx0 = 2j, kx1 = 2j + 1 of
+// one row (ky, kz) of the half spectrum (Eq. noise_eq over one step).  Each
+// Hermitian pair of modes is drawn once, by its canonical member (the smaller
+// index in the half spectrum [kz][ky][kx]); one Philox4x32-10 call, counter
+// (((kz Ny + ky) Hxe + kx) / 2, step, field, 0), serves the canonical modes
+// 2j and 2j + 1 of a row: words (x0, x1) the even one, (x2, x3) the odd one.
+// A mode that is its own partner is real.  amp0/amp1 are the per-component
+// standard deviations sqrt(N_sites D~(q) dt / dV) of the two modes.
+// on_plane: kx0 is 0 or Nx/2 (its partner is (kx0, -ky, -kz)).
 template <typename T>
-__device__ __forceinline__ cplx<T> noise_mode(int kx, int ky, int kz, T q2, const SysP<T> &sp,
-                                              const FieldP<T> &fp, uint32_t step) {
-    const uint32_t own = (uint32_t)(((long long)kz * sp.ny + ky) * sp.hx + kx);
-    uint32_t canon = own;
+__device__ __forceinline__ void noise_pair(bool on_plane, int kx0, int ky, int kz, T amp0, T amp1, bool has1,
+                                           const SysP<T> &sp, uint32_t fid, uint32_t step, cplx<T> &xi0,
+                                           cplx<T> &xi1) {
+    const uint32_t row = (uint32_t)(kz * sp.ny + ky);
+    uint32_t crow = row;
     bool cj = false, selfc = false;
-    if (kx == 0 || 2 * kx == sp.nx) {
-        const int pky = (sp.ny - ky) % sp.ny, pkz = (sp.nz - kz) % sp.nz;
-        const uint32_t par = (uint32_t)(((long long)pkz * sp.ny + pky) * sp.hx + kx);
-        selfc = par == own;
-        if (par < own) { canon = par; cj = true; }
+    if (on_plane) {
+        const uint32_t prow = (uint32_t)(((sp.nz - kz) & (sp.nz - 1)) * sp.ny + ((sp.ny - ky) & (sp.ny - 1)));
+        selfc = prow == row;
+        if (prow < row) { crow = prow; cj = true; }
     }
-    const u32x4 r = philox4x32_10(u32x4{canon, step, (uint32_t)fp.field_id, 0u}, sp.seed_lo, sp.seed_hi);
+    u32x4 r = philox4x32_10(u32x4{(crow * (uint32_t)sp.hxe + (uint32_t)kx0) >> 1, step, fid, 0u}, sp.seed_lo,
+                            sp.seed_hi);
     T n1, n2;
     box_muller(uniform24<T>(r.x), uniform24<T>(r.y), n1, n2);
-    T q2p = T(1);
-    for (int p = 0; p < fp.noise_pow; ++p) q2p *= q2;
-    const T amp = sqrt(fp.amp2 * q2p);
-    if (selfc) return mk<T>(T(1.4142135623730951) * amp * n1, T(0));
-    return mk<T>(amp * n1, cj ? -amp * n2 : amp * n2);
+    xi0 = selfc ? mk<T>(T(1.4142135623730951) * amp0 * n1, T(0)) : mk<T>(amp0 * n1, cj ? -amp0 * n2 : amp0 * n2);
+    if (has1) {
+        // kx1 is odd, so it is never 0 or Nx/2: it is its own canonical member
+        if (crow != row)
+            r = philox4x32_10(u32x4{(row * (uint32_t)sp.hxe + (uint32_t)kx0) >> 1, step, fid, 0u}, sp.seed_lo,
+                              sp.seed_hi);
+        box_muller(uniform24<T>(r.z), uniform24<T>(r.w), n1, n2);
+        xi1 = mk<T>(amp1 * n1, amp1 * n2);
+    }
+}
+
+// sigma0 |q|^p with |q| = sqrt(q2)
+template <typename T> __device__ __forceinline__ T noise_amp(T sigma0, int p, T q2) {
+    if (p == 0) return sigma0;
+    const T qa = fast_sqrt(q2);
+    T amp = sigma0;
+    for (int i = 0; i < p; ++i) amp *= qa;
+    return amp;
+}
+
+// Eq. (timeupdate): (phi + dt M P + xi) / (1 + dt O), O = -L~
+template <typename T>
+__device__ __forceinline__ cplx<T> update_mode(cplx<T> phi, cplx<T> P, cplx<T> xi, T q2, const SysP<T> &sp,
+                                               const FieldP<T> &fp) {
+    T nx = phi.x + xi.x, ny = phi.y + xi.y;
+    if (fp.power > 0) {
+        const T dtM = sp.dt * poly5<T>(fp.M, q2);
+        nx += dtM * P.x;
+        ny += dtM * P.y;
+    }
+    const T g = fast_rcp(T(1) + sp.dt * poly5<T>(fp.O, q2));
+    return mk<T>(nx * g, ny * g);
 }
 
 // ---------------------------------------------------------------------------
 // k_col: FFTs along the slowest axis (N = n_inner points), fused with the
-// update.  CTA = tiles_per_cta tiles x NP pencils x kTileW columns; in 3D the
-// two pencils are ky and -ky so that the Hermitian pair of every kx = 0 mode
-// sits in the same CTA.
+// update.  A CTA holds F = tiles_per_cta x NP x kTileW columns ("chunks" of
+// kTileW columns of one pencil); in 3D the two pencils of a CTA are ky and
+// -ky so that the Hermitian partner of every kx = 0 mode sits in the same CTA.
+// The CTA has 2 F TPF threads: FFT f = t mod F (consecutive threads,
+// consecutive columns), lane t / F; lanes >= TPF only join the element-wise
+// phases.  Shared memory: PHI (staged state chunks, [chunk][pos][W] with a
+// chunk stride of N W + 8), X (staged product chunks, then a work buffer),
+// Y (work buffer).
 // ---------------------------------------------------------------------------
+template <typename T, int N> struct ColSmem {
+    static constexpr int CS = N * W + 8;                         // chunk stride (elements)
+    __host__ __device__ static int xs(int F) {                   // X / Y size (elements)
+        const int a = F * sf_fft_fastest(N, F), b = (F / W) * CS;
+        return a > b ? a : b;
+    }
+    __host__ __device__ static size_t bytes(int F) {
+        return 128 + sizeof(cplx<T>) * ((size_t)(F / W) * CS + 2 * (size_t)xs(F));
+    }
+};
+
 template <typename T, int N>
-__global__ void __launch_bounds__(256) k_col(const ColArgs<T> a) {
+__global__ void __launch_bounds__(512) k_col(const ColArgs<T> a) {
     using C = cplx<T>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    C *sbuf = reinterpret_cast<C *>(smem_raw);
-    constexpr int E = FftShape<N>::E, TPF = FftShape<N>::TPF;
+    using L = ColSmem<T, N>;
+    constexpr int TPF = FftShape<N>::TPF;
+    constexpr int CS = L::CS;
+    constexpr int LOGNW = FftShape<N>::LOG + 2;                 // log2(N W)
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw);
+    const int F = a.F;                                           // a power of two, multiple of W
+    const int logF = __ffs(F) - 1;
+    const int nchunks = F / W, lognch = logF - 2;
+    const int SF = sf_fft_fastest(N, F);
+    C *PHI = reinterpret_cast<C *>(smem_raw + 128);
+    C *X = PHI + nchunks * CS;
+    C *Y = X + L::xs(F);
     const SysP<T> &sp = a.sp;
     const int fld = blockIdx.z;
     const FieldP<T> &fp = a.fp[fld];
-    const int NP = sp.dim == 3 ? 2 : 1;
-    const int F = a.tiles_per_cta * W * NP;
-    const int t = threadIdx.x;
-    const int f = t % F, lane = t / F;
-    const int c = f % W, pp = (f / W) % NP, tl = f / (W * NP);
-    const int tile = blockIdx.x * a.tiles_per_cta + tl;
+    const int logNP = sp.dim == 3 ? 1 : 0;
+    const int t = threadIdx.x, nthr = blockDim.x;
     const int op = blockIdx.y;
-    const int o = pp == 0 ? op : (sp.n_outer - op) % sp.n_outer;
-    const bool tile_ok = tile < a.n_tiles;
-    const bool writer = tile_ok && !(pp == 1 && o == op);
-    const int kx = tile * W + c;
-    const size_t base = ((size_t)(tile * sp.n_outer + o) * N) * W + c;
-    const C *__restrict__ tw = a.tw;
+    const int opp = (sp.n_outer - op) & (sp.n_outer - 1);        // partner pencil (-ky)
     const int mode = a.mode;
+    const int first_tile = blockIdx.x * a.tiles_per_cta;
+    const C *__restrict__ tw = a.tw;
 
-    C v[E];
-    const C *src = (mode == COL_STEP || mode == COL_FWD) ? a.in[fld] : a.state[fld];
-#pragma unroll
-    for (int e = 0; e < E; ++e) v[e] = tile_ok ? src[base + (size_t)(lane + TPF * e) * W] : mk<T>(0, 0);
+    auto chunk_tile = [&](int ch) { return first_tile + (ch >> logNP); };
+    auto chunk_o = [&](int ch) { return (ch & logNP) ? opp : op; };
+    auto chunk_ok = [&](int ch) { return chunk_tile(ch) < a.n_tiles; };
+    auto chunk_writes = [&](int ch) { return chunk_ok(ch) && !((ch & logNP) && opp == op); };
+    auto gofs = [&](int ch) { return ((size_t)(chunk_tile(ch) * sp.n_outer + chunk_o(ch)) * N) * W; };
 
-    if (mode == COL_STEP || mode == COL_FWD) {
-        fft<T, N, -1>(v, lane, sbuf, F, f, tw);
+    // ---- stage: state chunks -> PHI (not for COL_FWD), product chunks -> X (COL_STEP, COL_FWD)
+    const bool need_in = mode == COL_STEP || mode == COL_FWD;
+    const bool need_phi = mode != COL_FWD;
+    const uint32_t chunk_bytes = (uint32_t)(N * W * sizeof(C));
+    int nvalid = 0;                                              // chunks 0..nvalid-1 lie inside the grid
+    for (int ch = 0; ch < nchunks; ++ch) nvalid += chunk_ok(ch) ? 1 : 0;
+    if (t == 0) {
+        mbar_init(bar, 1);
+        mbar_expect_tx(bar, chunk_bytes * nvalid * ((need_in ? 1 : 0) + (need_phi ? 1 : 0)));
+        for (int ch = 0; ch < nvalid; ++ch) {
+            if (need_phi) bulk_g2s(PHI + ch * CS, a.state[fld] + gofs(ch), chunk_bytes, bar);
+            if (need_in) bulk_g2s(X + ch * CS, a.in[fld] + gofs(ch), chunk_bytes, bar);
+        }
+    }
+    __syncthreads();   // the barrier is initialised before anyone polls it
+    for (int i = nvalid * (N * W) + t; i < nchunks * (N * W); i += nthr) {   // chunks past the last tile read as zero
+        const int ch = i >> LOGNW, r = i & (N * W - 1);
+        PHI[ch * CS + r] = mk<T>(0, 0);
+        X[ch * CS + r] = mk<T>(0, 0);
+    }
+    if (!mbar_wait_all(bar, 0, a.d_status)) return;
+
+    // this thread's FFT: column c of chunk ch
+    const int f = t & (F - 1), lane = t >> logF;
+    const bool active = lane < TPF;
+    const int ch = f >> 2, c = f & 3;
+    const int my_tile = chunk_tile(ch), my_o = chunk_o(ch);
+    const int kx = my_tile * W + c;
+
+    if (need_in) {
+        // forward transform along this axis: P_q
+        const C *xb = X + ch * CS + c;
+        const int which = fft_run<T, N, -1>([&](int p) { return xb[p * W]; },
+                                            [&](int p, C v, C *fr) { fr[spad(p)] = v; },
+                                            Y + f * SF, X + f * SF, lane, active, tw);
+        __syncthreads();
+        const C *P = which == 0 ? Y : X;
         const uint32_t step = (uint32_t)(*a.d_step);
-        C *__restrict__ st = a.state[fld];
+        // update: each thread keeps one pair of neighbouring columns (they share
+        // one Philox draw) of one chunk and walks the positions
+        const int cp = t & 1, chq = (t >> 1) & (nchunks - 1);
+        const int pos_step = nthr >> (1 + lognch);
+        const int tile = chunk_tile(chq), o = chunk_o(chq);
+        const int c0 = 2 * cp, kx0 = tile * W + c0;
+        const bool has0 = kx0 < sp.hx, has1 = kx0 + 1 < sp.hx;
+        const bool on_plane = kx0 == 0 || 2 * kx0 == sp.nx;
+        const T qx0 = T(kx0) * sp.gx, qx1 = T(kx0 + 1) * sp.gx;
+        const T qx0s = qx0 * qx0, qx1s = qx1 * qx1;
+        const C *P0 = P + (chq * W + c0) * SF, *P1 = P0 + SF;
+        C *phb = PHI + chq * CS + c0;
         bool bad = false;
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-            const int pos = lane + TPF * e;
-            const int ky = sp.dim == 3 ? o : (sp.dim == 2 ? pos : 0);
-            const int kz = sp.dim == 3 ? pos : 0;
-            C phi;
-            if (mode == COL_FWD) {
-                phi = v[e];
-            } else {
-                phi = tile_ok ? st[base + (size_t)pos * W] : mk<T>(0, 0);
-                const T qx = T(kx) * sp.gx, qy = T(signed_k<T>(ky, sp.ny)) * sp.gy,
-                        qz = T(signed_k<T>(kz, sp.nz)) * sp.gz;
-                const T q2 = qx * qx + qy * qy + qz * qz;
-                C num = phi;
-                if (fp.power > 0) {
-                    const T dtM = sp.dt * poly5<T>(fp.M, q2);
-                    num = mk<T>(num.x + dtM * v[e].x, num.y + dtM * v[e].y);
+        if (tile < a.n_tiles) {
+#pragma unroll 1
+            for (int pos = t >> (1 + lognch); pos < N; pos += pos_step) {
+                C v0 = P0[spad(pos)], v1 = P1[spad(pos)];
+                C *ph = phb + pos * W;
+                if (mode == COL_STEP) {
+                    const int ky = sp.dim == 3 ? o : (sp.dim == 2 ? pos : 0);
+                    const int kz = sp.dim == 3 ? pos : 0;
+                    const T qy = T(signed_k(ky, sp.ny)) * sp.gy, qz = T(signed_k(kz, sp.nz)) * sp.gz;
+                    const T qyz2 = qy * qy + qz * qz;
+                    const T q2a = qx0s + qyz2, q2b = qx1s + qyz2;
+                    C xi0 = mk<T>(0, 0), xi1 = mk<T>(0, 0);
+                    if (fp.noisy)
+                        noise_pair<T>(on_plane, kx0, ky, kz, noise_amp<T>(fp.sigma0, fp.noise_pow, q2a),
+                                      noise_amp<T>(fp.sigma0, fp.noise_pow, q2b), has1, sp, (uint32_t)fp.field_id,
+                                      step, xi0, xi1);
+                    v0 = update_mode<T>(ph[0], v0, xi0, q2a, sp, fp);
+                    v1 = update_mode<T>(ph[1], v1, xi1, q2b, sp, fp);
+                    // false for NaN and for infinities (or values next to overflow)
+                    bad |= !(fabs(v0.x) + fabs(v0.y) + fabs(v1.x) + fabs(v1.y) <= T(sizeof(T) == 4 ? 3.0e38 : 1.0e300));
                 }
-                if (fp.noisy) num = cadd<T>(num, noise_mode<T>(kx, ky, kz, q2, sp, fp, step));
-                const T den = T(1) + sp.dt * poly5<T>(fp.O, q2);
-                phi = mk<T>(num.x / den, num.y / den);
-                bad |= !(isfinite(phi.x) && isfinite(phi.y));
+                ph[0] = has0 ? v0 : mk<T>(0, 0);
+                ph[1] = has1 ? v1 : mk<T>(0, 0);
             }
-            if (kx >= sp.hx) phi = mk<T>(0, 0);
-            v[e] = phi;
         }
-        // Hermitian part on the kx = 0 and kx = Nx/2 planes (the field is real)
-        const int first = blockIdx.x * a.tiles_per_cta * W, last = first + a.tiles_per_cta * W;
-        const bool proj = first == 0 || (first <= sp.nx / 2 && sp.nx / 2 < last);
-        if (proj) {
-            __syncthreads();
-#pragma unroll
-            for (int e = 0; e < E; ++e) sbuf[spad(lane + TPF * e) * F + f] = v[e];
-            __syncthreads();
-            const int fp2 = NP == 2 ? (pp == 0 ? f + W : f - W) : f;
-#pragma unroll
-            for (int e = 0; e < E; ++e) {
-                const int pos = lane + TPF * e;
+        if (bad && a.d_status) atomicOr(a.d_status, kStatusNonFinite);
+        __syncthreads();
+        // Hermitian part on the kx = 0 and kx = Nx/2 planes (the field is real):
+        // phi(kx, k) <- (phi(kx, k) + conj phi(kx, -k)) / 2, each pair by one thread
+        const int last_tile = first_tile + a.tiles_per_cta;
+        if (first_tile == 0 || (first_tile * W <= sp.nx / 2 && sp.nx / 2 < last_tile * W)) {
+#pragma unroll 1
+            for (int i = t; i < N * F; i += nthr) {
+                const int pos = i >> logF, ff = i & (F - 1);
+                const int cq = ff >> 2, cc = ff & 3;
+                const int kq = chunk_tile(cq) * W + cc;
+                if (!(kq == 0 || 2 * kq == sp.nx) || (cq & logNP) != 0) continue;
                 const int ppos = (N - pos) & (N - 1);
-                const C q = sbuf[spad(ppos) * F + fp2];
-                if (kx == 0 || 2 * kx == sp.nx) v[e] = mk<T>(T(0.5) * (v[e].x + q.x), T(0.5) * (v[e].y - q.y));
+                if (logNP == 0 && ppos < pos) continue;
+                C *p0 = &PHI[cq * CS + pos * W + cc];
+                C *p1 = &PHI[(cq + logNP) * CS + ppos * W + cc];
+                const C u0 = *p0, u1 = *p1;
+                const C h = mk<T>(T(0.5) * (u0.x + u1.x), T(0.5) * (u0.y - u1.y));
+                *p0 = h;
+                *p1 = mk<T>(h.x, -h.y);
             }
             __syncthreads();
         }
-        if (writer) {
-#pragma unroll
-            for (int e = 0; e < E; ++e) st[base + (size_t)(lane + TPF * e) * W] = v[e];
+        // write the state back: one bulk copy per chunk (contiguous in global memory)
+        fence_proxy_async();   // every thread's PHI writes, before the copy engine reads them
+        __syncthreads();
+        if (t == 0) {
+            for (int cq = 0; cq < nvalid; ++cq)
+                if (chunk_writes(cq)) bulk_s2g(a.state[fld] + gofs(cq), PHI + cq * CS, chunk_bytes);
+            bulk_commit();
         }
-        if (bad && a.d_status) atomicOr(a.d_status, 1);
-        if (mode == COL_FWD) return;
+        if (mode == COL_FWD) {
+            if (t == 0) bulk_wait_read();
+            return;
+        }
     }
 
-    // ---- inverse along this axis: de-alias (not for COL_INV_FULL), scale by 1/N_sites
+    // ---- inverse along this axis of the de-aliased (not for COL_INV_FULL),
+    // 1/N_sites-scaled field, stored straight from the last pass
     const bool full = mode == COL_INV_FULL;
+    bool skip = false;
     if (!full) {
-        // CTA-uniform early exit when no column or pencil of the CTA is kept
-        const int first_kx = blockIdx.x * a.tiles_per_cta * W;
-        const int ky0 = op;
-        const bool ky_kept = sp.dim != 3 || abs(signed_k<T>(ky0, sp.ny)) <= fp.kmax[1];
-        if (first_kx > fp.kmax[0] || !ky_kept) return;
+        const bool ky_kept = sp.dim != 3 || abs(signed_k(op, sp.ny)) <= fp.kmax[1];
+        skip = first_tile * W > fp.kmax[0] || !ky_kept;              // CTA-uniform: nothing kept
     }
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
-        const int pos = lane + TPF * e;
-        bool keep = kx < sp.hx;
-        if (!full) {
-            const int ky = sp.dim == 3 ? o : (sp.dim == 2 ? pos : 0);
-            const int kz = sp.dim == 3 ? pos : 0;
-            keep = keep && kx <= fp.kmax[0] && abs(signed_k<T>(ky, sp.ny)) <= fp.kmax[1] &&
-                   abs(signed_k<T>(kz, sp.nz)) <= fp.kmax[2];
-        }
-        v[e] = keep ? cscale<T>(v[e], sp.inv_nsites) : mk<T>(0, 0);
+    if (!skip) {
+        __syncthreads();   // PHI is final; X and Y are free
+        const bool kx_keep = kx < sp.hx && (full || kx <= fp.kmax[0]);
+        const bool o_keep = full || sp.dim != 3 || abs(signed_k(my_o, sp.ny)) <= fp.kmax[1];
+        const int kmax_pos = full ? N : (sp.dim == 3 ? fp.kmax[2] : (sp.dim == 2 ? fp.kmax[1] : 0));
+        const T scale = (kx_keep && o_keep) ? sp.inv_nsites : T(0);
+        const C *pb = PHI + ch * CS + c;
+        const bool writes = chunk_writes(ch) && (full || my_tile * W <= fp.kmax[0]);
+        C *__restrict__ dst = a.out[fld] + gofs(ch) + c;
+        fft_run<T, N, +1>(
+            [&](int p) { return abs(signed_k(p, N)) <= kmax_pos ? cscale<T>(pb[p * W], scale) : mk<T>(0, 0); },
+            [&](int p, C v, C *) {
+                if (writes) dst[p * W] = v;
+            },
+            X + f * SF, Y + f * SF, lane, active, tw);
     }
-    fft<T, N, +1>(v, lane, sbuf, F, f, tw);
-    if (writer && (full || tile * W <= fp.kmax[0])) {
-        C *__restrict__ dst = a.out[fld];
-#pragma unroll
-        for (int e = 0; e < E; ++e) dst[base + (size_t)(lane + TPF * e) * W] = v[e];
-    }
+    if (need_in && t == 0) bulk_wait_read();   // PHI must outlive the state write-back
 }
 
 // ---------------------------------------------------------------------------
@@ -178,6 +290,9 @@ __global__ void __launch_bounds__(256) k_col(const ColArgs<T> a) {
 // rows a, b ride on one complex FFT z = a + i b: C2R builds
 // Z_k = A_k + i B_k from the two half spectra, and R2C splits the transform W
 // of z by A_k = (W_k + conj W_{N-k}) / 2, B_k = (W_k - conj W_{N-k}) / (2i).
+// Threads: lane t mod TPF of pair t / TPF.  Shared memory: S (the staged
+// input, tile segments of 2G rows with a stride of 2G W + 4; also a work
+// buffer), B0, B1 (work buffers).
 // ---------------------------------------------------------------------------
 template <typename T>
 __device__ __forceinline__ size_t real_row_offset(const SysP<T> &sp, int row) {
@@ -194,136 +309,203 @@ template <typename T> __device__ __forceinline__ T ipow(T x, int p) {
     return r;
 }
 
+template <typename T, int N> struct RowSmem {
+    __host__ __device__ static int tstride(int G) { return 2 * G * W + 4; }
+    __host__ __device__ static int s_elems(int G, int ntiles) {
+        int a = ntiles * tstride(G), b = G * N, c = G * sf_row(N);   // tiles, 2G real rows, work
+        a = a > b ? a : b;
+        return a > c ? a : c;
+    }
+    __host__ __device__ static size_t bytes(int G, int ntiles) {
+        return 128 + sizeof(cplx<T>) * ((size_t)s_elems(G, ntiles) + 2 * (size_t)G * sf_row(N));
+    }
+};
+
 template <typename T, int N>
 __global__ void __launch_bounds__(256) k_row(const RowArgs<T> a) {
     using C = cplx<T>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    C *S = reinterpret_cast<C *>(smem_raw);
-    T *Sr = reinterpret_cast<T *>(smem_raw);
-    constexpr int E = FftShape<N>::E, TPF = FftShape<N>::TPF;
+    using L = RowSmem<T, N>;
+    constexpr int TPF = FftShape<N>::TPF;
+    constexpr int SF = sf_row(N);
+    constexpr int LOGTPF = FftShape<N>::LOG - (N < 16 ? FftShape<N>::LOG : 4);
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw);
     const SysP<T> &sp = a.sp;
-    const int G = a.G, G2 = 2 * a.G;
+    const int G = a.G, G2 = 2 * a.G;                            // G a power of two
+    const int logG = __ffs(G) - 1;
+    const int TS = L::tstride(G);
+    C *S = reinterpret_cast<C *>(smem_raw + 128);
+    T *Sr = reinterpret_cast<T *>(S);
+    C *B0 = S + L::s_elems(G, sp.ntiles);
+    C *B1 = B0 + G * SF;
     const int fld = blockIdx.y;
     const int t = threadIdx.x, nthr = blockDim.x;
-    const int g = t % G, lane = t / G;
     const int r0 = blockIdx.x * G2;
     const int rows = sp.rows;
-    const C *__restrict__ tw = a.tw;
+    const int nrow = rows - r0 < G2 ? rows - r0 : G2;          // rows present in this CTA
     const int mode = a.mode;
-    C v[E];
+    const C *__restrict__ tw = a.tw;
 
+    // ---- stage the input rows
     if (mode == ROW_R2C) {
         const T *__restrict__ src = a.real_in[fld];
-        for (int L = t; L < G2 * N; L += nthr) {
-            const int x = L % N, rl = L / N, row = r0 + rl;
-            Sr[x * G2 + rl] = row < rows ? src[real_row_offset(sp, row) + x] : T(0);
+        const uint32_t row_bytes = (uint32_t)(N * sizeof(T));
+        if (t == 0) {
+            mbar_init(bar, 1);
+            mbar_expect_tx(bar, row_bytes * nrow);
+            for (int rl = 0; rl < nrow; ++rl) bulk_g2s(Sr + rl * N, src + real_row_offset(sp, r0 + rl), row_bytes, bar);
         }
-        __syncthreads();
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-            const int k = lane + TPF * e;
-            v[e] = mk<T>(Sr[k * G2 + g], Sr[k * G2 + G + g]);
-        }
-        __syncthreads();
+        __syncthreads();   // the barrier is initialised before anyone polls it
+        for (int i = nrow * N + t; i < G2 * N; i += nthr) Sr[i] = T(0);
     } else {
         const C *__restrict__ src = a.in[fld];
-        const int kxc = a.kx_cols[fld];
-        const int ntl = (kxc + W - 1) / W;
-        for (int L = t; L < ntl * G2 * W; L += nthr) {
-            const int cc = L % W, rl = (L / W) % G2, tl = L / (W * G2);
-            const int kx = tl * W + cc, row = r0 + rl;
-            if (kx < kxc) S[kx * G2 + rl] = row < rows ? src[((size_t)tl * rows + row) * W + cc] : mk<T>(0, 0);
+        const int ntl = (a.kx_cols[fld] + W - 1) / W;
+        const uint32_t seg = (uint32_t)(nrow * W * sizeof(C));
+        if (t == 0) {
+            mbar_init(bar, 1);
+            mbar_expect_tx(bar, seg * ntl);
         }
         __syncthreads();
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-            const int k = lane + TPF * e;
-            const int kk = k <= N / 2 ? k : N - k;
-            C xa = kk < kxc ? S[kk * G2 + g] : mk<T>(0, 0);
-            C xb = kk < kxc ? S[kk * G2 + G + g] : mk<T>(0, 0);
-            if (k > N / 2) { xa.y = -xa.y; xb.y = -xb.y; }
-            if (k == 0 || 2 * k == N) { xa.y = T(0); xb.y = T(0); }
-            v[e] = mk<T>(xa.x - xb.y, xa.y + xb.x);
-        }
-        __syncthreads();
-        fft<T, N, +1>(v, lane, S, G, g, tw);
-        if (mode == ROW_C2R) {
-#pragma unroll
-            for (int e = 0; e < E; ++e) {
-                const int x = lane + TPF * e;
-                Sr[x * G2 + g] = v[e].x;
-                Sr[x * G2 + G + g] = v[e].y;
+        for (int tl = t; tl < ntl; tl += nthr) bulk_g2s(S + tl * TS, src + ((size_t)tl * rows + r0) * W, seg, bar);
+        if (nrow < G2)
+            for (int i = t; i < ntl * G2 * W; i += nthr) {
+                const int tl = i / (G2 * W), r = i - tl * (G2 * W);
+                if (r / W >= nrow) S[tl * TS + r] = mk<T>(0, 0);
             }
-            __syncthreads();
+    }
+    if (!mbar_wait_all(bar, 0, a.d_status)) return;
+
+    const int lane = t & (TPF - 1), g = t >> LOGTPF;
+    const bool active = g < G;
+    C *b0 = B0 + g * SF, *b1 = B1 + g * SF;
+    auto smem_sink = [&](int p, C v, C *fr) { fr[spad(p)] = v; };
+    const C *R;          // this CTA's result buffer (B0 or B1)
+    if (mode == ROW_R2C) {
+        const int which = fft_run<T, N, -1>([&](int p) { return mk<T>(Sr[g * N + p], Sr[(G + g) * N + p]); },
+                                            smem_sink, b0, b1, lane, active, tw);
+        R = which == 0 ? B0 : B1;
+    } else {
+        const int kxc = a.kx_cols[fld];
+        const int which = fft_run<T, N, +1>(
+            [&](int k) {
+                const int kk = k <= N / 2 ? k : N - k;
+                C xa = mk<T>(0, 0), xb = mk<T>(0, 0);
+                if (kk < kxc) {
+                    const int base = (kk >> 2) * TS + (kk & 3);
+                    xa = S[base + g * W];
+                    xb = S[base + (G + g) * W];
+                }
+                if (k > N / 2) { xa.y = -xa.y; xb.y = -xb.y; }
+                if (k == 0 || 2 * k == N) { xa.y = T(0); xb.y = T(0); }
+                return mk<T>(xa.x - xb.y, xa.y + xb.x);
+            },
+            smem_sink, b0, b1, lane, active, tw);
+        __syncthreads();
+        C *Z = which == 0 ? B0 : B1;
+        if (mode == ROW_C2R) {
             T *__restrict__ dst = a.real_out[fld];
-            for (int L = t; L < G2 * N; L += nthr) {
-                const int x = L % N, rl = L / N, row = r0 + rl;
-                if (row < rows) dst[real_row_offset(sp, row) + x] = Sr[x * G2 + rl];
+#pragma unroll 1
+            for (int i = t; i < nrow * N; i += nthr) {
+                const int rl = i / N, x = i - rl * N;
+                const C z = Z[(rl & (G - 1)) * SF + spad(x)];
+                dst[real_row_offset(sp, r0 + rl) + x] = rl < G ? z.x : z.y;
             }
             return;
         }
-        // real-space product of the de-aliased field
+        // forward transform of the real-space product (phi^d)^p of both rows
         const int p = a.power[fld];
-#pragma unroll
-        for (int e = 0; e < E; ++e) v[e] = mk<T>(ipow<T>(v[e].x, p), ipow<T>(v[e].y, p));
+        C *zf = Z + g * SF;
+        C *other = (which == 0 ? B1 : B0) + g * SF;
+        const int which2 = fft_run<T, N, -1>(
+            [&](int k) {
+                const C z = zf[spad(k)];
+                return mk<T>(ipow<T>(z.x, p), ipow<T>(z.y, p));
+            },
+            smem_sink, other, zf, lane, active, tw);
+        R = which2 == 0 ? (which == 0 ? B1 : B0) : (which == 0 ? B0 : B1);
     }
-    fft<T, N, -1>(v, lane, S, G, g, tw);
-#pragma unroll
-    for (int e = 0; e < E; ++e) S[spad(lane + TPF * e) * G + g] = v[e];
     __syncthreads();
+    // ---- split the pairs and write the half spectra of all tiles (coalesced)
     C *__restrict__ dst = a.out[fld];
-    const int ntl = sp.ntiles;
-    for (int L = t; L < ntl * G2 * W; L += nthr) {
-        const int cc = L % W, rl = (L / W) % G2, tl = L / (W * G2);
-        const int kx = tl * W + cc, row = r0 + rl;
-        if (row >= rows) continue;
+    const int logG2 = logG + 1;
+#pragma unroll 1
+    for (int i = t; i < sp.ntiles * G2 * W; i += nthr) {
+        const int cc = i & 3, rl = (i >> 2) & (G2 - 1), tl = i >> (2 + logG2);
+        if (rl >= nrow) continue;
+        const int kx = tl * W + cc;
         C val = mk<T>(0, 0);
         if (kx <= N / 2) {
-            const int gg = rl % G;
-            const C wk = S[spad(kx) * G + gg];
-            const C wm = S[spad((N - kx) & (N - 1)) * G + gg];
+            const C *rb = R + (rl & (G - 1)) * SF;
+            const C wk = rb[spad(kx)];
+            const C wm = rb[spad((N - kx) & (N - 1))];
             val = rl < G ? mk<T>(T(0.5) * (wk.x + wm.x), T(0.5) * (wk.y - wm.y))
                          : mk<T>(T(0.5) * (wk.y + wm.y), T(-0.5) * (wk.x - wm.x));
         }
-        dst[((size_t)tl * rows + row) * W + cc] = val;
+        dst[((size_t)tl * rows + r0 + rl) * W + cc] = val;
     }
     if (a.inc_step && blockIdx.x == 0 && blockIdx.y == 0 && t == 0) *a.d_step += 1;
 }
 
 // ---------------------------------------------------------------------------
-// k_mid: FFTs along y in 3D (N = ny points) for one tile and PZ z-planes.
+// k_mid: FFTs along y in 3D (N = ny points) for one tile and PZ z-planes,
+// F = PZ W FFTs.  Threads: FFT f = t mod F, lane t / F.  Shared memory: S
+// (the staged [ky][F] input; also a work buffer), B0.
 // ---------------------------------------------------------------------------
+template <typename T, int N> struct MidSmem {
+    __host__ __device__ static int s_elems(int F) {
+        const int a = N * F, b = F * sf_fft_fastest(N, F);
+        return a > b ? a : b;
+    }
+    __host__ __device__ static size_t bytes(int F) {
+        return 128 + sizeof(cplx<T>) * ((size_t)s_elems(F) + (size_t)F * sf_fft_fastest(N, F));
+    }
+};
+
 template <typename T, int N>
 __global__ void __launch_bounds__(256) k_mid(const MidArgs<T> a) {
     using C = cplx<T>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    C *sbuf = reinterpret_cast<C *>(smem_raw);
-    constexpr int E = FftShape<N>::E, TPF = FftShape<N>::TPF;
+    using L = MidSmem<T, N>;
+    constexpr int TPF = FftShape<N>::TPF;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw);
     const SysP<T> &sp = a.sp;
-    const int fld = blockIdx.z;
     const int F = a.PZ * W;
-    const int t = threadIdx.x;
-    const int f = t % F, lane = t / F;
-    const int c = f % W, pz = f / W;
+    const int logF = __ffs(F) - 1;
+    const int SF = sf_fft_fastest(N, F);
+    C *S = reinterpret_cast<C *>(smem_raw + 128);
+    C *B0 = S + L::s_elems(F);
+    const int fld = blockIdx.z;
+    const int t = threadIdx.x, nthr = blockDim.x;
     const int tile = blockIdx.x;
-    const int pos = blockIdx.y * a.PZ + pz;
+    const int pos0 = blockIdx.y * a.PZ;
     const int nz = sp.nz;
-    const size_t base = ((size_t)tile * N * nz + pos) * W + c;   // + o * nz * W
-    const C *__restrict__ src = a.in[fld];
     const bool masked_in = a.mode == MID_INV_MASK;
     const int kmy = a.kmax_y[fld];
-    C v[E];
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
-        const int o = lane + TPF * e;
-        const bool ld = !masked_in || abs(signed_k<T>(o, N)) <= kmy;
-        v[e] = ld ? src[base + (size_t)o * nz * W] : mk<T>(0, 0);
+    const C *__restrict__ src = a.in[fld];
+    const uint32_t seg = (uint32_t)(F * sizeof(C));
+    if (t == 0) {
+        int n = 0;
+        for (int o = 0; o < N; ++o) n += (!masked_in || abs(signed_k(o, N)) <= kmy) ? 1 : 0;
+        mbar_init(bar, 1);
+        mbar_expect_tx(bar, seg * n);
     }
-    if (a.mode == MID_FWD) fft<T, N, -1>(v, lane, sbuf, F, f, a.tw);
-    else fft<T, N, +1>(v, lane, sbuf, F, f, a.tw);
-    C *__restrict__ dst = a.out[fld];
-#pragma unroll
-    for (int e = 0; e < E; ++e) dst[base + (size_t)(lane + TPF * e) * nz * W] = v[e];
+    __syncthreads();
+    for (int o = t; o < N; o += nthr) {
+        if (!masked_in || abs(signed_k(o, N)) <= kmy)
+            bulk_g2s(S + o * F, src + (((size_t)tile * N + o) * nz + pos0) * W, seg, bar);
+    }
+    if (masked_in)
+        for (int i = t; i < N * F; i += nthr)
+            if (abs(signed_k(i >> logF, N)) > kmy) S[i] = mk<T>(0, 0);
+    if (!mbar_wait_all(bar, 0, a.d_status)) return;
+    const int f = t & (F - 1), lane = t >> logF;
+    const bool active = lane < TPF;
+    C *__restrict__ dst = a.out[fld] + (((size_t)tile * N) * nz + pos0) * W + f;
+    const size_t ostride = (size_t)nz * W;
+    auto src_f = [&](int p) { return S[p * F + f]; };
+    auto sink = [&](int p, C v, C *) { dst[p * ostride] = v; };
+    if (a.mode == MID_FWD) fft_run<T, N, -1>(src_f, sink, B0 + f * SF, S + f * SF, lane, active, a.tw);
+    else fft_run<T, N, +1>(src_f, sink, B0 + f * SF, S + f * SF, lane, active, a.tw);
     if (a.inc_step && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && t == 0) *a.d_step += 1;
 }
 
@@ -372,7 +554,7 @@ __global__ void k_structure_factor(SysP<T> sp, double dx0, double dx1, double dx
         const int kx = (int)(i % sp.hx);
         const long long r2 = i / sp.hx;
         const int ky = (int)(r2 % sp.ny), kz = (int)(r2 / sp.ny);
-        const int ks[3] = {kx, signed_k<T>(ky, sp.ny), signed_k<T>(kz, sp.nz)};
+        const int ks[3] = {kx, signed_k(ky, sp.ny), signed_k(kz, sp.nz)};
         double s2 = 0.0, qq = 0.0;
         for (int j = 0; j < 3; ++j) {
             if (Ns[j] == 1) continue;
@@ -403,16 +585,18 @@ __global__ void k_structure_factor(SysP<T> sp, double dx0, double dx1, double dx
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
+template <class K> cudaError_t ensure_smem(K kernel, size_t smem) {
+    if (smem <= 48 * 1024) return cudaSuccess;
+    if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
 template <typename T, int N> cudaError_t launch_col_n(const ColArgs<T> &a, int nf, int gx, int gy, cudaStream_t st) {
-    const int NP = a.sp.dim == 3 ? 2 : 1;
-    const int F = a.tiles_per_cta * W * NP;
-    const int threads = F * FftShape<N>::TPF;
-    const size_t smem = sizeof(cplx<T>) * (size_t)fft_smem_elems(N, F);
-    if (threads > 256) return cudaErrorInvalidConfiguration;
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_col<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
+    const int threads = 2 * a.F * FftShape<N>::TPF < 32 ? 32 : 2 * a.F * FftShape<N>::TPF;
+    const size_t smem = ColSmem<T, N>::bytes(a.F);
+    if (threads > 512 || (a.F & (a.F - 1)) != 0 || a.F % W != 0) return cudaErrorInvalidConfiguration;
+    cudaError_t e = ensure_smem(k_col<T, N>, smem);
+    if (e != cudaSuccess) return e;
     k_col<T, N><<<dim3(gx, gy, nf), threads, smem, st>>>(a);
     return cudaGetLastError();
 }
@@ -435,16 +619,11 @@ template <typename T> cudaError_t launch_col(const ColArgs<T> &a, int nf, int gx
 
 template <typename T, int N> cudaError_t launch_row_n(const RowArgs<T> &a, int nf, cudaStream_t st) {
     const int G = a.G;
-    const int threads = G * FftShape<N>::TPF;
-    size_t elems = (size_t)fft_smem_elems(N, G);
-    elems = elems > (size_t)(N / 2 + 1) * 2 * G ? elems : (size_t)(N / 2 + 1) * 2 * G;
-    elems = elems > (size_t)N * G ? elems : (size_t)N * G;   // 2G rows of N reals
-    const size_t smem = sizeof(cplx<T>) * elems;
-    if (threads > 256) return cudaErrorInvalidConfiguration;
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_row<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
+    const int threads = G * FftShape<N>::TPF < 32 ? 32 : G * FftShape<N>::TPF;
+    const size_t smem = RowSmem<T, N>::bytes(G, a.sp.ntiles);
+    if (threads > 256 || (G & (G - 1)) != 0) return cudaErrorInvalidConfiguration;
+    cudaError_t e = ensure_smem(k_row<T, N>, smem);
+    if (e != cudaSuccess) return e;
     const int grid = (a.sp.rows + 2 * G - 1) / (2 * G);
     k_row<T, N><<<dim3(grid, nf), threads, smem, st>>>(a);
     return cudaGetLastError();
@@ -467,13 +646,11 @@ template <typename T> cudaError_t launch_row(const RowArgs<T> &a, int nf, cudaSt
 
 template <typename T, int N> cudaError_t launch_mid_n(const MidArgs<T> &a, int nf, int n_tiles, cudaStream_t st) {
     const int F = a.PZ * W;
-    const int threads = F * FftShape<N>::TPF;
-    const size_t smem = sizeof(cplx<T>) * (size_t)fft_smem_elems(N, F);
-    if (threads > 256) return cudaErrorInvalidConfiguration;
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_mid<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
+    const int threads = F * FftShape<N>::TPF < 32 ? 32 : F * FftShape<N>::TPF;
+    const size_t smem = MidSmem<T, N>::bytes(F);
+    if (threads > 256 || (F & (F - 1)) != 0) return cudaErrorInvalidConfiguration;
+    cudaError_t e = ensure_smem(k_mid<T, N>, smem);
+    if (e != cudaSuccess) return e;
     k_mid<T, N><<<dim3(n_tiles, a.sp.nz / a.PZ, nf), threads, smem, st>>>(a);
     return cudaGetLastError();
 }
@@ -517,7 +694,7 @@ cudaError_t launch_half_to_tiles(const SysP<T> &sp, const cplx<T> *half, cplx<T>
     const long long n = (long long)sp.nz * sp.ny * sp.hx;
     long long blocks = (n + 255) / 256;
     if (blocks > 65535) blocks = 65535;
-    k_tiles_half<T><<<(int)blocks, 256, 0, st>>>(sp, const_cast<cplx<T> *>(tiles), const_cast<cplx<T> *>(half), 0);
+    k_tiles_half<T><<<(int)blocks, 256, 0, st>>>(sp, tiles, const_cast<cplx<T> *>(half), 0);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,50 @@
+"""Run a fixed number of Model B steps for profilers (ncu wraps this command).
+
+    python -m paper_2405_02410_gb300.profile_run --shape 1024 1024 --steps 20 [--eager] [--fields 1|2]
+
+--eager launches every step's kernels one by one (no CUDA graph); --fields 2
+adds a Model A field (the 3D Model A + B pair).
+"""
+import argparse
+import os
+import sys
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--shape", type=int, nargs="+", default=[1024, 1024])
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--fields", type=int, default=1)
+    ap.add_argument("--precision", default="f32")
+    ap.add_argument("--eager", action="store_true")
+    args = ap.parse_args()
+    import torch
+    from paper_2405_02410_gb300 import build
+    build.build()
+    from paper_2405_02410_gb300 import pss
+    shape = tuple(args.shape)
+    if len(shape) == 3:
+        s = pss.System(shape, dt=0.005, seed=2405, precision=args.precision)
+        if args.fields == 2:
+            pss.add_model_a_field(s, a=-1, b=1, K=1, D=0.05, name="psi")
+        pss.add_model_b_field(s, a=-1, b=1, K=1, D=0.05, name="phi")
+    else:
+        s = pss.model_b(shape, dt=0.01, a=-1, b=1, K=1, D=0.01, seed=2405, precision=args.precision)
+        if args.fields == 2:
+            pss.add_model_a_field(s, a=-1, b=1, K=1, D=0.05, name="psi")
+    for f in range(args.fields):
+        s.init_uniform(f, -0.1, 0.1)
+    if args.eager:
+        for _ in range(args.steps):
+            s.step(1)
+    else:
+        s.step(args.steps)
+    s.sync()
+    torch.cuda.synchronize()
+    print(f"ok: {shape} {args.steps} steps, launches={s.launch_count}")
+
+
+if __name__ == "__main__":
+    main()
