@@ -71,7 +71,9 @@ int pss_create_system(pss_system **out, int dim, int nx, int ny, int nz,
                       uint64_t seed, int precision);
 /* Free every device buffer and the handle.  NULL is accepted. */
 int pss_destroy_system(pss_system *s);
-/* Launch all work on this cudaStream_t (NULL = legacy default stream). */
+/* Launch all further work on this cudaStream_t (NULL = legacy default
+ * stream).  Work issued after the call is ordered after all work the system
+ * issued before it, on whichever stream. */
 int pss_set_stream(pss_system *s, void *cuda_stream);
 
 /* Named scalar parameter ("addParameter", section "Writing models"); *id
@@ -124,6 +126,16 @@ int pss_step(pss_system *s, int64_t n);
  * 2 = row kernel (x transforms and product), 3 = forward y pass (3D only);
  * kinds that do not run read 0.  Synchronises. */
 int pss_time_kernels(pss_system *s, int64_t n, double *avg_ms);
+
+/* Launch-shape tuning (results do not depend on it).  key / value:
+ *   "pdl"         1 = launch the step kernels with programmatic dependent
+ *                 launch, 0 = plain stream order (default);
+ *   "row_pairs"   row pairs per CTA of the x-transform kernel (power of two);
+ *   "col_tiles"   column tiles per CTA of the fused column kernel;
+ *   "mid_planes"  z planes per CTA of the 3D y-transform kernel;
+ *   "graph_steps" steps per replayed CUDA graph;
+ * 0 restores the automatic choice.  Unknown keys return PSS_EINVAL. */
+int pss_set_tuning(pss_system *s, const char *key, int value);
 
 /* Steps taken so far (the next step's noise index). */
 int pss_get_step(pss_system *s, int64_t *step);

@@ -44,7 +44,7 @@ struct Param {
     double value;
 };
 
-constexpr int kGraphSteps = 16;
+constexpr int kDefaultGraphSteps = 16;
 constexpr double kPi = 3.14159265358979323846;
 
 }  // namespace
@@ -74,6 +74,8 @@ struct pss_system {
     bool stale = true;        // B does not hold the product of the current state
     cudaGraphExec_t graph = nullptr;
     bool graph_valid = false;
+    // launch-shape tuning (pss_set_tuning); 0 = automatic
+    int tune_pdl = 0, tune_row_pairs = 0, tune_col_tiles = 0, tune_graph_steps = 0, tune_mid_planes = 0;
     int64_t launches = 0;
     std::string err;
 };
@@ -131,6 +133,7 @@ template <typename T> SysP<T> sys_params(const pss_system *s) {
     p.inv_nsites = T(1.0 / (double)s->nsites);
     p.seed_lo = (uint32_t)(s->seed & 0xffffffffu);
     p.seed_hi = (uint32_t)(s->seed >> 32);
+    p.pdl = s->tune_pdl;
     return p;
 }
 
@@ -162,6 +165,11 @@ template <typename T> FieldP<T> field_params(const pss_system *s, int fi) {
 int col_tiles_per_cta(const pss_system *s) {
     const int NP = s->dim == 3 ? 2 : 1;
     const int per_tile = kTileW * NP * fft_TPF(s->n_inner);
+    if (s->tune_col_tiles > 0) {
+        int tc = 1;
+        while (tc * 2 <= s->tune_col_tiles && tc * 2 <= s->ntiles && 2 * tc * 2 * per_tile <= 512) tc *= 2;
+        return tc;
+    }
     int tc = 1;
     while (tc * 2 * per_tile <= 64 && tc * 2 <= s->ntiles) tc *= 2;
     return tc;
@@ -171,6 +179,11 @@ int col_tiles_per_cta(const pss_system *s) {
 // threads, and at least ~8 CTAs when there are few rows
 int row_G(const pss_system *s) {
     const int tpf = fft_TPF(s->nx);
+    if (s->tune_row_pairs > 0) {
+        int G = 1;
+        while (G * 2 <= s->tune_row_pairs && G * 2 * tpf <= 256 && G * 2 <= std::max(1, s->rows / 2)) G *= 2;
+        return G;
+    }
     const int want = std::max(1, (s->rows / 2 + 7) / 8);
     int G = 1;
     while (G * 2 * tpf <= 128 && G * 2 <= want) G *= 2;
@@ -180,6 +193,11 @@ int row_G(const pss_system *s) {
 int mid_PZ(const pss_system *s) {
     const int tpf = fft_TPF(s->ny);
     int pz = std::max(1, 256 / (kTileW * tpf));
+    if (s->tune_mid_planes > 0) {
+        int p = 1;
+        while (p * 2 <= s->tune_mid_planes && p * 2 <= pz) p *= 2;
+        pz = p;
+    }
     pz = std::min(pz, s->nz);
     return pz;
 }
@@ -352,6 +370,7 @@ template <typename T> int run_prologue(pss_system *s) {
 
 template <typename T> int run_steps(pss_system *s, int64_t n) {
     const int nf = (int)s->fields.size();
+    const int kGraphSteps = s->tune_graph_steps > 0 ? s->tune_graph_steps : kDefaultGraphSteps;
     int64_t done = 0;
     if (n >= kGraphSteps) {
         if (!s->graph_valid) {
@@ -532,7 +551,17 @@ int pss_destroy_system(pss_system *s) {
 
 int pss_set_stream(pss_system *s, void *stream) {
     if (!s) return PSS_EINVAL;
-    s->stream = (cudaStream_t)stream;
+    cudaStream_t next = (cudaStream_t)stream;
+    if (next != s->stream) {
+        // work issued on the new stream starts after everything issued so far
+        cudaEvent_t ev;
+        CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        cudaError_t e = cudaEventRecord(ev, s->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(next, ev, 0);
+        cudaEventDestroy(ev);
+        if (e != cudaSuccess) return cuda_fail(s, e, "pss_set_stream");
+        s->stream = next;
+    }
     return PSS_OK;
 }
 
@@ -702,6 +731,20 @@ int pss_time_kernels(pss_system *s, int64_t n, double *avg_ms) {
     if (rc) return rc;
     s->step += n;
     return device_errors(s);
+}
+
+int pss_set_tuning(pss_system *s, const char *key, int value) {
+    if (!s || !key) return PSS_EINVAL;
+    if (value < 0) return fail(s, PSS_EINVAL, "tuning values are >= 0");
+    const std::string k = key;
+    if (k == "pdl") s->tune_pdl = value ? 1 : 0;
+    else if (k == "row_pairs") s->tune_row_pairs = value;
+    else if (k == "col_tiles") s->tune_col_tiles = value;
+    else if (k == "mid_planes") s->tune_mid_planes = value;
+    else if (k == "graph_steps") s->tune_graph_steps = value;
+    else return fail(s, PSS_EINVAL, "unknown tuning key '%s'", key);
+    invalidate(s);
+    return PSS_OK;
 }
 
 int pss_get_step(pss_system *s, int64_t *step) {

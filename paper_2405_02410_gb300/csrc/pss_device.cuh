@@ -252,6 +252,18 @@ __device__ __forceinline__ int fft_run(Src src, Sink sink, cplx<T> *b0, cplx<T> 
 }
 
 // ---------------------------------------------------------------------------
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialisation may start while its predecessor drains.  pdl_wait() blocks
+// until the predecessor grid has completed and its writes are visible (a
+// no-op without PDL); pdl_trigger() lets the successor launch.  Every kernel
+// waits before touching data the previous kernel wrote and triggers only
+// after that wait, so a successor's launch implies that every kernel before
+// the current one has completed.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// ---------------------------------------------------------------------------
 // TMA bulk copies (cp.async.bulk, no tensor map) completing on an mbarrier.
 // Every wait is bounded: after kWaitLimit polls the kernel records
 // PSS_STATUS_TIMEOUT and takes its early exit.

@@ -43,6 +43,7 @@ template <typename T> struct SysP {
     T gx, gy, gz;         // 2 pi / (N dx) per axis (0 for unused axes)
     T dt, inv_nsites;
     uint32_t seed_lo, seed_hi;
+    int pdl;              // launch with programmatic stream serialisation
 };
 
 enum ColMode { COL_STEP = 0, COL_FWD = 1, COL_INV_MASK = 2, COL_INV_FULL = 3 };

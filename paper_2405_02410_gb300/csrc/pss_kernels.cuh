@@ -151,6 +151,8 @@ __global__ void __launch_bounds__(512) k_col(const ColArgs<T> a) {
     const uint32_t chunk_bytes = (uint32_t)(N * W * sizeof(C));
     int nvalid = 0;                                              // chunks 0..nvalid-1 lie inside the grid
     for (int ch = 0; ch < nchunks; ++ch) nvalid += chunk_ok(ch) ? 1 : 0;
+    pdl_wait();
+    pdl_trigger();
     if (t == 0) {
         mbar_init(bar, 1);
         mbar_expect_tx(bar, chunk_bytes * nvalid * ((need_in ? 1 : 0) + (need_phi ? 1 : 0)));
@@ -345,6 +347,8 @@ __global__ void __launch_bounds__(256) k_row(const RowArgs<T> a) {
     const int nrow = rows - r0 < G2 ? rows - r0 : G2;          // rows present in this CTA
     const int mode = a.mode;
     const C *__restrict__ tw = a.tw;
+    pdl_wait();
+    pdl_trigger();
 
     // ---- stage the input rows
     if (mode == ROW_R2C) {
@@ -483,6 +487,8 @@ __global__ void __launch_bounds__(256) k_mid(const MidArgs<T> a) {
     const int kmy = a.kmax_y[fld];
     const C *__restrict__ src = a.in[fld];
     const uint32_t seg = (uint32_t)(F * sizeof(C));
+    pdl_wait();
+    pdl_trigger();
     if (t == 0) {
         int n = 0;
         for (int o = 0; o < N; ++o) n += (!masked_in || abs(signed_k(o, N)) <= kmy) ? 1 : 0;
@@ -585,6 +591,26 @@ __global__ void k_structure_factor(SysP<T> sp, double dx0, double dx1, double dx
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
+// launch with programmatic stream serialisation (PDL)
+template <class K, class A>
+cudaError_t launch_pdl(K kernel, dim3 grid, int threads, size_t smem, cudaStream_t st, const A &args) {
+    if (!args.sp.pdl) {
+        kernel<<<grid, threads, smem, st>>>(args);
+        return cudaGetLastError();
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(threads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args);
+}
+
 template <class K> cudaError_t ensure_smem(K kernel, size_t smem) {
     if (smem <= 48 * 1024) return cudaSuccess;
     if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
@@ -597,8 +623,7 @@ template <typename T, int N> cudaError_t launch_col_n(const ColArgs<T> &a, int n
     if (threads > 512 || (a.F & (a.F - 1)) != 0 || a.F % W != 0) return cudaErrorInvalidConfiguration;
     cudaError_t e = ensure_smem(k_col<T, N>, smem);
     if (e != cudaSuccess) return e;
-    k_col<T, N><<<dim3(gx, gy, nf), threads, smem, st>>>(a);
-    return cudaGetLastError();
+    return launch_pdl(k_col<T, N>, dim3(gx, gy, nf), threads, smem, st, a);
 }
 
 template <typename T> cudaError_t launch_col(const ColArgs<T> &a, int nf, int gx, int gy, cudaStream_t st) {
@@ -625,8 +650,7 @@ template <typename T, int N> cudaError_t launch_row_n(const RowArgs<T> &a, int n
     cudaError_t e = ensure_smem(k_row<T, N>, smem);
     if (e != cudaSuccess) return e;
     const int grid = (a.sp.rows + 2 * G - 1) / (2 * G);
-    k_row<T, N><<<dim3(grid, nf), threads, smem, st>>>(a);
-    return cudaGetLastError();
+    return launch_pdl(k_row<T, N>, dim3(grid, nf), threads, smem, st, a);
 }
 
 template <typename T> cudaError_t launch_row(const RowArgs<T> &a, int nf, cudaStream_t st) {
@@ -651,8 +675,7 @@ template <typename T, int N> cudaError_t launch_mid_n(const MidArgs<T> &a, int n
     if (threads > 256 || (F & (F - 1)) != 0) return cudaErrorInvalidConfiguration;
     cudaError_t e = ensure_smem(k_mid<T, N>, smem);
     if (e != cudaSuccess) return e;
-    k_mid<T, N><<<dim3(n_tiles, a.sp.nz / a.PZ, nf), threads, smem, st>>>(a);
-    return cudaGetLastError();
+    return launch_pdl(k_mid<T, N>, dim3(n_tiles, a.sp.nz / a.PZ, nf), threads, smem, st, a);
 }
 
 template <typename T> cudaError_t launch_mid(const MidArgs<T> &a, int nf, int n_tiles, cudaStream_t st) {

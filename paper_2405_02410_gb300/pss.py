@@ -26,7 +26,7 @@ EXPORTS = [
     "pss_get_param", "pss_add_field", "pss_add_term", "pss_set_noise", "pss_set_dealias", "pss_set_field",
     "pss_init_uniform", "pss_step", "pss_get_step", "pss_set_step", "pss_get_field", "pss_get_spectrum",
     "pss_set_spectrum", "pss_structure_factor", "pss_sync", "pss_last_error", "pss_launch_count",
-    "pss_time_kernels",
+    "pss_time_kernels", "pss_set_tuning",
 ]
 
 
@@ -66,6 +66,7 @@ def _load():
         "pss_last_error": ([vp], ctypes.c_char_p),
         "pss_launch_count": ([vp], i64),
         "pss_time_kernels": ([vp, i64, P(d)], i32),
+        "pss_set_tuning": ([vp, ctypes.c_char_p, i32], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -222,6 +223,10 @@ class System:
         out = (ctypes.c_double * 4)()
         self._ck(lib.pss_time_kernels(self._h, int(n), out))
         return list(out)
+
+    def set_tuning(self, key: str, value: int):
+        """Launch-shape knob ("pdl", "row_pairs", "col_tiles", "mid_planes", "graph_steps"); 0 = automatic."""
+        self._ck(lib.pss_set_tuning(self._h, key.encode(), int(value)))
 
     def sync(self):
         self._ck(lib.pss_sync(self._h))

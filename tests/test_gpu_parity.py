@@ -208,3 +208,45 @@ def test_model_b_1024_sampled_against_oracle():
     s.step(steps)
     ref = _oracle_b(shape, steps, **kw)
     assert rel(s.get_spectrum(0), ref) < 1e-4
+
+
+@pytest.mark.parametrize("knobs", [
+    dict(row_pairs=1), dict(row_pairs=2), dict(row_pairs=4), dict(row_pairs=8),
+    dict(mid_planes=1), dict(mid_planes=2), dict(mid_planes=4), dict(col_tiles=2), dict(col_tiles=4),
+    dict(pdl=1), dict(row_pairs=2, mid_planes=4, pdl=1),
+])
+@pytest.mark.parametrize("shape", [(16, 32, 32), (8, 64, 16), (64, 128)])
+def test_launch_shapes_do_not_change_results(shape, knobs):
+    # every launch-shape knob must give the oracle's result (Model A + B pair)
+    steps = 12
+    P = pss()
+    s = P.System(shape, dt=0.005, seed=8, precision="f32")
+    P.add_model_a_field(s, a=-1, b=1, K=1, D=0.05, name="psi")
+    P.add_model_b_field(s, a=-1, b=1, K=1, D=0.05, name="phi")
+    for k, v in knobs.items():
+        s.set_tuning(k, v)
+    s.init_uniform(0, -0.05, 0.05)
+    s.init_uniform(1, -0.05, 0.05)
+    s.step(steps)
+    ma = O.model_a(shape, dt=0.005, a=-1, b=1, K=1, D=0.05, seed=8, field_id=0)
+    mb = O.model_b(shape, dt=0.005, a=-1, b=1, K=1, D=0.05, seed=8, field_id=1)
+    for fid, m in ((0, ma), (1, mb)):
+        ref = O.half(O.run(m, O.to_spectrum(m, O.init_uniform(m, -0.05, 0.05)), 0, steps))
+        err = rel(s.get_spectrum(fid), ref)
+        assert err < 1e-4, (fid, err)
+
+
+def test_stream_switch_keeps_order():
+    # initialise on the default stream, then step on a non-blocking torch stream
+    import torch
+    P = pss()
+    ref_sys = P.model_b((256, 256), seed=31, precision="f32")
+    ref_sys.init_uniform(0, -0.1, 0.1)
+    ref_sys.step(30)
+    ref = ref_sys.get_spectrum(0)
+    s = P.model_b((256, 256), seed=31, precision="f32")
+    s.init_uniform(0, -0.1, 0.1)
+    st = torch.cuda.Stream()
+    s.set_stream(st)
+    s.step(30)
+    np.testing.assert_array_equal(s.get_spectrum(0), ref)
