@@ -69,6 +69,18 @@ enum { PSS_HOST = 0, PSS_DEVICE = 1 };
 int pss_create_system(pss_system **out, int dim, int nx, int ny, int nz,
                       double dx, double dy, double dz, double dt,
                       uint64_t seed, int precision);
+/* A batch of `batch` independent instances of one system (an ensemble of
+ * noise realisations or a parameter sweep): same lattice, fields and terms,
+ * instance b keyed by seeds[b] and with its own parameter values
+ * (pss_set_param_batch).  Every step advances all instances; the per-field
+ * calls (set/get/init/structure factor) act on the instance chosen with
+ * pss_select_instance (default 0).  pss_create_system is a batch of one. */
+int pss_create_batch(pss_system **out, int batch, int dim, int nx, int ny, int nz,
+                     double dx, double dy, double dz, double dt,
+                     const uint64_t *seeds, int precision);
+int pss_batch_size(const pss_system *s);
+int pss_select_instance(pss_system *s, int instance);
+
 /* Free every device buffer and the handle.  NULL is accepted. */
 int pss_destroy_system(pss_system *s);
 /* Launch all further work on this cudaStream_t (NULL = legacy default
@@ -77,15 +89,18 @@ int pss_destroy_system(pss_system *s);
 int pss_set_stream(pss_system *s, void *cuda_stream);
 
 /* Named scalar parameter ("addParameter", section "Writing models"); *id
- * receives its index.  A parameter may be changed later with pss_set_param;
- * the change applies from the next step on. */
+ * receives its index; every instance starts with `value`.  A parameter may
+ * be changed later with pss_set_param / pss_set_param_batch; the change
+ * applies from the next step on.  pss_get_param reads the selected instance. */
 int pss_add_param(pss_system *s, const char *name, double value, int *id);
-int pss_set_param(pss_system *s, int id, double value);
+int pss_set_param(pss_system *s, int id, double value);              /* all instances */
+int pss_set_param_batch(pss_system *s, int id, const double *values); /* values[batch] */
 int pss_get_param(pss_system *s, int id, double *value);
 
 /* Add a field ("createField(name, dynamic)").  Only dynamic fields are
  * implemented (dynamic = 1; 0 returns PSS_EUNSUPPORTED).  At most 4 fields.
- * Fields start at zero. */
+ * Fields start at zero.  Add fields before setting data: adding a field
+ * reallocates the arrays (existing fields keep their values). */
 int pss_add_field(pss_system *s, const char *name, int dynamic, int *field_id);
 
 /* Add a term to the equation of field_id.  The term's operator is
@@ -119,6 +134,11 @@ int pss_init_uniform(pss_system *s, int field_id, double lo, double hi);
 /* Advance every dynamic field by n >= 0 steps.  Asynchronous on the system's
  * stream.  Step k of the run draws noise with Philox counter word 1 = k. */
 int pss_step(pss_system *s, int64_t n);
+/* Advance n systems (for instance the size classes of an ensemble) by
+ * `steps` steps each, replayed from one captured CUDA graph on systems[0]'s
+ * stream (the other systems are moved to that stream).  Errors are reported
+ * on systems[0]. */
+int pss_step_many(pss_system **systems, int n, int64_t steps);
 /* Measurement: take n >= 1 steps like pss_step, but launch every kernel on
  * its own with a CUDA event pair around it, and return in avg_ms[0..3] the
  * mean duration (milliseconds) of each kind of launch of a step:

@@ -1,10 +1,14 @@
 // pss_api.cu -- host side of libpss: the C ABI declared in include/pss.h.
 //
-// A system owns, per field, the spectral state phi_q and two work arrays A, B
-// (same tiled layout, see pss_internal.h).  B carries the x-transformed
-// nonlinear product from one step to the next; A holds the inverse-transformed
-// de-aliased field inside a step.  All kernels of a step are issued on one
-// stream; runs of steps are replayed from a captured CUDA graph.
+// A system holds `batch` independent instances of one lattice problem.  Each
+// (instance, field) pair is a slot; the spectral state phi_q of all slots and
+// two work arrays A, B live back to back in three device buffers (tiled
+// layout, see pss_internal.h).  B carries the x-transformed nonlinear
+// product from one step to the next; A holds the inverse-transformed
+// de-aliased field inside a step.  Per-slot parameters (operators, noise
+// amplitude, mask, seed) live in a device array that is refreshed before
+// launches, so runs of steps replay one captured CUDA graph even when
+// parameters change between runs.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -36,15 +40,10 @@ struct Field {
     int noise_param = -1;
     int noise_pow = 0;
     int dealias = 2;
-    void *state = nullptr, *A = nullptr, *B = nullptr;
-};
-
-struct Param {
-    std::string name;
-    double value;
 };
 
 constexpr int kDefaultGraphSteps = 16;
+constexpr int kMaxBatch = 65535 / kMaxFields;
 constexpr double kPi = 3.14159265358979323846;
 
 }  // namespace
@@ -53,31 +52,39 @@ struct pss_system {
     int dim = 0, nx = 1, ny = 1, nz = 1;
     double dx[3] = {1, 1, 1};
     double dt = 0;
-    uint64_t seed = 0;
+    int batch = 1;
+    std::vector<uint64_t> seeds;             // per instance
     int prec = PSS_F32;
     int device = 0;
     cudaStream_t stream = nullptr;
     cudaStream_t cap_stream = nullptr;
-    std::vector<Param> params;
+    std::vector<std::string> param_names;
+    std::vector<double> param_values;        // [instance][param]
     std::vector<Field> fields;
+    int cur = 0;                             // instance addressed by the per-field calls
     int hx = 0, ntiles = 0, rows = 0, n_outer = 1, n_inner = 1;
     long long nsites = 0;
-    size_t field_elems = 0;   // complex elements of one spectral array
-    void *tw = nullptr;       // roots of unity, precision of the system
-    void *real = nullptr;     // real scratch [nz][ny][nx]
-    void *half = nullptr;     // half-spectrum scratch
-    double *sq = nullptr;     // structure-factor accumulator
+    size_t field_elems = 0;                  // complex elements of one slot of one array
+    void *state = nullptr, *A = nullptr, *B = nullptr;   // [slot][field_elems]
+    void *fps = nullptr;                     // FieldP<T>[slots] on the device
+    bool fps_dirty = true;
+    void *tw = nullptr;                      // roots of unity, precision of the system
+    void *real = nullptr;                    // real scratch [nz][ny][nx] (one slot)
+    void *half = nullptr;                    // half-spectrum scratch (one slot)
+    double *sq = nullptr;                    // structure-factor accumulator
     int sq_cap = 0;
     long long *d_step = nullptr;
     int *d_status = nullptr;
     int64_t step = 0;
-    bool stale = true;        // B does not hold the product of the current state
+    bool stale = true;                       // B does not hold the product of the current state
     cudaGraphExec_t graph = nullptr;
     bool graph_valid = false;
     // launch-shape tuning (pss_set_tuning); 0 = automatic
     int tune_pdl = 0, tune_row_pairs = 0, tune_col_tiles = 0, tune_graph_steps = 0, tune_mid_planes = 0;
     int64_t launches = 0;
     std::string err;
+
+    int nslots() const { return batch * (int)fields.size(); }
 };
 
 namespace {
@@ -109,6 +116,7 @@ bool pow2_in(int n, int lo, int hi) { return n >= lo && n <= hi && (n & (n - 1))
 
 size_t csize(const pss_system *s) { return s->prec == PSS_F64 ? 16 : 8; }
 size_t rsize(const pss_system *s) { return s->prec == PSS_F64 ? 8 : 4; }
+size_t fpsize(const pss_system *s) { return s->prec == PSS_F64 ? sizeof(FieldP<double>) : sizeof(FieldP<float>); }
 
 // largest kept |k| on an axis of n points: (order+1)|k| < n; every |k| <= n/2
 // is kept when order = 0
@@ -117,6 +125,9 @@ int kmax_axis(int n, int order) {
     if (order <= 0) return n / 2;
     return std::min((n - 1) / (order + 1), n / 2);
 }
+
+// kept half-spectrum columns kx = 0..kmax (never more than the nx/2+1 stored)
+int kept_cols(const pss_system *s, int fi) { return std::min(kmax_axis(s->nx, s->fields[fi].dealias) + 1, s->hx); }
 
 template <typename T> SysP<T> sys_params(const pss_system *s) {
     SysP<T> p{};
@@ -131,33 +142,51 @@ template <typename T> SysP<T> sys_params(const pss_system *s) {
     p.gz = s->nz > 1 ? T(two_pi / (s->nz * s->dx[2])) : T(0);
     p.dt = T(s->dt);
     p.inv_nsites = T(1.0 / (double)s->nsites);
-    p.seed_lo = (uint32_t)(s->seed & 0xffffffffu);
-    p.seed_hi = (uint32_t)(s->seed >> 32);
     p.pdl = s->tune_pdl;
     return p;
 }
 
-double pval(const pss_system *s, int id) { return id < 0 ? 1.0 : s->params[id].value; }
+double pval(const pss_system *s, int inst, int id) {
+    return id < 0 ? 1.0 : s->param_values[(size_t)inst * s->param_names.size() + id];
+}
 
-template <typename T> FieldP<T> field_params(const pss_system *s, int fi) {
+template <typename T> FieldP<T> field_params(const pss_system *s, int inst, int fi) {
     const Field &f = s->fields[fi];
     FieldP<T> p{};
     double O[kPolyTerms] = {0}, M[kPolyTerms] = {0};
-    for (const Mono &m : f.lhs) O[m.pow] += m.scale * pval(s, m.param);
-    for (const Mono &m : f.rhs) M[m.pow] += m.scale * pval(s, m.param);
+    for (const Mono &m : f.lhs) O[m.pow] += m.scale * pval(s, inst, m.param);
+    for (const Mono &m : f.rhs) M[m.pow] += m.scale * pval(s, inst, m.param);
     for (int i = 0; i < kPolyTerms; ++i) { p.O[i] = T(O[i]); p.M[i] = T(M[i]); }
     double dV = 1.0;
     for (int j = 0; j < s->dim; ++j) dV *= s->dx[j];
     p.noisy = f.noisy ? 1 : 0;
-    p.sigma0 = f.noisy ? T(std::sqrt(std::max(0.0, (double)s->nsites * pval(s, f.noise_param) * s->dt / dV))) : T(0);
+    p.sigma0 = f.noisy ? T(std::sqrt(std::max(0.0, (double)s->nsites * pval(s, inst, f.noise_param) * s->dt / dV)))
+                       : T(0);
     p.noise_pow = f.noise_pow;
     p.power = f.power;
     p.kmax[0] = kmax_axis(s->nx, f.dealias);
     p.kmax[1] = kmax_axis(s->ny, f.dealias);
     p.kmax[2] = kmax_axis(s->nz, f.dealias);
+    p.kx_cols = kept_cols(s, fi);
     p.field_id = fi;
+    p.seed_lo = (uint32_t)(s->seeds[inst] & 0xffffffffu);
+    p.seed_hi = (uint32_t)(s->seeds[inst] >> 32);
     return p;
 }
+
+// refresh the device copy of the per-slot parameters (ordered on the system's stream)
+template <typename T> int upload_params_t(pss_system *s) {
+    if (!s->fps_dirty) return PSS_OK;
+    std::vector<FieldP<T>> h;
+    h.reserve(s->nslots());
+    for (int b = 0; b < s->batch; ++b)
+        for (int fi = 0; fi < (int)s->fields.size(); ++fi) h.push_back(field_params<T>(s, b, fi));
+    if (!h.empty()) CK(cudaMemcpyAsync(s->fps, h.data(), sizeof(FieldP<T>) * h.size(), cudaMemcpyHostToDevice, s->stream));
+    s->fps_dirty = false;
+    return PSS_OK;
+}
+
+int upload_params(pss_system *s) { return s->prec == PSS_F64 ? upload_params_t<double>(s) : upload_params_t<float>(s); }
 
 // ---- launch shapes -------------------------------------------------------
 // tiles per CTA of the column kernel: a power of two, so that the CTA's
@@ -202,10 +231,12 @@ int mid_PZ(const pss_system *s) {
     return pz;
 }
 
-// kept half-spectrum columns kx = 0..kmax (never more than the nx/2+1 stored)
-int kept_cols(const pss_system *s, int fi) { return std::min(kmax_axis(s->nx, s->fields[fi].dealias) + 1, s->hx); }
+int max_kept_tiles(const pss_system *s) {
+    int m = 0;
+    for (int i = 0; i < (int)s->fields.size(); ++i) m = std::max(m, (kept_cols(s, i) + kTileW - 1) / kTileW);
+    return std::min(m, s->ntiles);
+}
 
-// ---- kernel sequences ----------------------------------------------------
 // Optional per-launch CUDA events (pss_time_kernels): kind 0 = k_col,
 // 1 = k_mid inverse, 2 = k_row, 3 = k_mid forward.  The events are recorded
 // into a captured graph as event-record nodes, so that the GPU never waits
@@ -224,42 +255,39 @@ struct Timer {
     }
 };
 
+// ---- kernel sequences ----------------------------------------------------
+// A sequence acts on slots slot0 .. slot0 + nslots - 1.  real_stride = 0 makes
+// every slot of a real-space transfer use the same (one-slot) scratch.
 template <typename T> struct Seq {
     pss_system *s;
     cudaStream_t st;
-    int f0, nf;   // fields [f0, f0 + nf)
+    int slot0, nslots;
     Timer *timer = nullptr;
 
-    cplx<T> *state(int i) const { return (cplx<T> *)s->fields[f0 + i].state; }
-    cplx<T> *A(int i) const { return (cplx<T> *)s->fields[f0 + i].A; }
-    cplx<T> *B(int i) const { return (cplx<T> *)s->fields[f0 + i].B; }
-
-    int max_kept_tiles() const {
-        int m = 0;
-        for (int i = 0; i < nf; ++i) m = std::max(m, (kept_cols(s, f0 + i) + kTileW - 1) / kTileW);
-        return std::min(m, s->ntiles);
-    }
+    cplx<T> *state() const { return (cplx<T> *)s->state; }
+    cplx<T> *A() const { return (cplx<T> *)s->A; }
+    cplx<T> *B() const { return (cplx<T> *)s->B; }
 
     int col(int mode, bool in_is_B, bool out_is_A) {
         ColArgs<T> a{};
         a.sp = sys_params<T>(s);
-        for (int i = 0; i < nf; ++i) {
-            a.fp[i] = field_params<T>(s, f0 + i);
-            a.in[i] = in_is_B ? B(i) : A(i);
-            a.out[i] = out_is_A ? A(i) : B(i);
-            a.state[i] = state(i);
-        }
+        a.fps = (const FieldP<T> *)s->fps;
+        a.in = in_is_B ? B() : A();
+        a.out = out_is_A ? A() : B();
+        a.state = state();
+        a.slot_stride = s->field_elems;
+        a.slot0 = slot0;
         a.tw = (const cplx<T> *)s->tw;
         a.d_step = s->d_step;
         a.d_status = s->d_status;
         a.mode = mode;
         a.tiles_per_cta = col_tiles_per_cta(s);
         a.F = a.tiles_per_cta * kTileW * (s->dim == 3 ? 2 : 1);
-        a.n_tiles = mode == COL_INV_MASK ? max_kept_tiles() : s->ntiles;
+        a.n_tiles = mode == COL_INV_MASK ? max_kept_tiles(s) : s->ntiles;
         const int gx = (a.n_tiles + a.tiles_per_cta - 1) / a.tiles_per_cta;
         const int gy = s->dim == 3 ? s->ny / 2 + 1 : 1;
         if (timer) timer->begin(0, st);
-        cudaError_t e = launch_col<T>(a, nf, gx, gy, st);
+        cudaError_t e = launch_col<T>(a, nslots, gx, gy, st);
         if (timer) timer->begin(0, st);
         s->launches++;
         if (e != cudaSuccess) return cuda_fail(s, e, "k_col launch");
@@ -267,25 +295,25 @@ template <typename T> struct Seq {
     }
 
     // in: A or B (complex), or real (ROW_R2C); out: A or B (complex), or real (ROW_C2R)
-    int row(int mode, bool in_is_A, bool out_is_B, bool inc, void *real) {
+    int row(int mode, bool in_is_A, bool out_is_B, bool inc, void *real, size_t real_stride) {
         RowArgs<T> a{};
         a.sp = sys_params<T>(s);
-        for (int i = 0; i < nf; ++i) {
-            a.power[i] = s->fields[f0 + i].power;
-            a.in[i] = in_is_A ? A(i) : B(i);
-            a.out[i] = out_is_B ? B(i) : A(i);
-            a.real_in[i] = (const T *)real + (size_t)i * s->nsites;
-            a.real_out[i] = (T *)real + (size_t)i * s->nsites;
-        }
+        a.fps = (const FieldP<T> *)s->fps;
+        a.in = in_is_A ? A() : B();
+        a.out = out_is_B ? B() : A();
+        a.real_in = (const T *)real;
+        a.real_out = (T *)real;
+        a.slot_stride = s->field_elems;
+        a.real_stride = real_stride;
+        a.slot0 = slot0;
         a.tw = (const cplx<T> *)s->tw;
         a.d_step = s->d_step;
         a.d_status = s->d_status;
         a.mode = mode;
         a.G = row_G(s);
-        for (int i = 0; i < nf; ++i) a.kx_cols[i] = mode == ROW_FUSED ? kept_cols(s, f0 + i) : s->hx;
         a.inc_step = inc ? 1 : 0;
         if (timer) timer->begin(2, st);
-        cudaError_t e = launch_row<T>(a, nf, st);
+        cudaError_t e = launch_row<T>(a, nslots, st);
         if (timer) timer->begin(2, st);
         s->launches++;
         if (e != cudaSuccess) return cuda_fail(s, e, "k_row launch");
@@ -295,21 +323,21 @@ template <typename T> struct Seq {
     int mid(int mode, bool in_is_A, bool inc) {
         MidArgs<T> a{};
         a.sp = sys_params<T>(s);
-        for (int i = 0; i < nf; ++i) {
-            a.kmax_y[i] = kmax_axis(s->ny, s->fields[f0 + i].dealias);
-            a.in[i] = in_is_A ? A(i) : B(i);
-            a.out[i] = in_is_A ? B(i) : A(i);
-        }
+        a.fps = (const FieldP<T> *)s->fps;
+        a.in = in_is_A ? A() : B();
+        a.out = in_is_A ? B() : A();
+        a.slot_stride = s->field_elems;
+        a.slot0 = slot0;
         a.tw = (const cplx<T> *)s->tw;
         a.d_step = s->d_step;
         a.d_status = s->d_status;
         a.mode = mode;
         a.PZ = mid_PZ(s);
         a.inc_step = inc ? 1 : 0;
-        const int nt = mode == MID_INV_MASK ? max_kept_tiles() : s->ntiles;
+        const int nt = mode == MID_INV_MASK ? max_kept_tiles(s) : s->ntiles;
         const int kind = mode == MID_FWD ? 3 : 1;
         if (timer) timer->begin(kind, st);
-        cudaError_t e = launch_mid<T>(a, nf, nt, st);
+        cudaError_t e = launch_mid<T>(a, nslots, nt, st);
         if (timer) timer->begin(kind, st);
         s->launches++;
         if (e != cudaSuccess) return cuda_fail(s, e, "k_mid launch");
@@ -319,95 +347,118 @@ template <typename T> struct Seq {
     // B <- x-transformed product of the current state (start of a run)
     int prologue() {
         int rc;
-        if ((rc = col(COL_INV_MASK, false, true))) return rc;                 // state -> A
+        if ((rc = col(COL_INV_MASK, false, true))) return rc;                      // state -> A
         if (s->dim == 3) {
-            if ((rc = mid(MID_INV_MASK, true, false))) return rc;             // A -> B
-            if ((rc = row(ROW_FUSED, false, false, false, nullptr))) return rc;   // B -> A
-            return mid(MID_FWD, true, false);                                 // A -> B
+            if ((rc = mid(MID_INV_MASK, true, false))) return rc;                  // A -> B
+            if ((rc = row(ROW_FUSED, false, false, false, nullptr, 0))) return rc;  // B -> A
+            return mid(MID_FWD, true, false);                                      // A -> B
         }
-        return row(ROW_FUSED, true, true, false, nullptr);                     // A -> B
+        return row(ROW_FUSED, true, true, false, nullptr, 0);                       // A -> B
     }
 
     int one_step() {
         int rc;
-        if ((rc = col(COL_STEP, true, true))) return rc;                      // B, state -> state, A
+        if ((rc = col(COL_STEP, true, true))) return rc;                           // B, state -> state, A
         if (s->dim == 3) {
-            if ((rc = mid(MID_INV_MASK, true, false))) return rc;             // A -> B
-            if ((rc = row(ROW_FUSED, false, false, false, nullptr))) return rc;   // B -> A
-            return mid(MID_FWD, true, true);                                  // A -> B, step++
+            if ((rc = mid(MID_INV_MASK, true, false))) return rc;                  // A -> B
+            if ((rc = row(ROW_FUSED, false, false, false, nullptr, 0))) return rc;  // B -> A
+            return mid(MID_FWD, true, true);                                       // A -> B, step++
         }
-        return row(ROW_FUSED, true, true, true, nullptr);                      // A -> B, step++
+        return row(ROW_FUSED, true, true, true, nullptr, 0);                        // A -> B, step++
     }
 
-    // real scratch (fields f0..f0+nf) -> state
+    // real scratch -> state of the sequence's slots
     int forward_from_real() {
         int rc;
         if (s->dim == 3) {
-            if ((rc = row(ROW_R2C, true, false, false, s->real))) return rc;  // real -> A
-            if ((rc = mid(MID_FWD, true, false))) return rc;                  // A -> B
+            if ((rc = row(ROW_R2C, true, false, false, s->real, 0))) return rc;   // real -> A
+            if ((rc = mid(MID_FWD, true, false))) return rc;                      // A -> B
         } else {
-            if ((rc = row(ROW_R2C, true, true, false, s->real))) return rc;   // real -> B
+            if ((rc = row(ROW_R2C, true, true, false, s->real, 0))) return rc;    // real -> B
         }
-        return col(COL_FWD, true, true);                                      // B -> state
+        return col(COL_FWD, true, true);                                          // B -> state
     }
 
     // state -> real scratch
     int inverse_to_real() {
         int rc;
-        if ((rc = col(COL_INV_FULL, false, true))) return rc;                 // state -> A
+        if ((rc = col(COL_INV_FULL, false, true))) return rc;                     // state -> A
         if (s->dim == 3) {
-            if ((rc = mid(MID_INV_FULL, true, false))) return rc;             // A -> B
-            return row(ROW_C2R, false, false, false, s->real);                // B -> real
+            if ((rc = mid(MID_INV_FULL, true, false))) return rc;                 // A -> B
+            return row(ROW_C2R, false, false, false, s->real, 0);                 // B -> real
         }
-        return row(ROW_C2R, true, false, false, s->real);                     // A -> real
+        return row(ROW_C2R, true, false, false, s->real, 0);                      // A -> real
     }
 };
 
 template <typename T> int run_prologue(pss_system *s) {
-    Seq<T> q{s, s->stream, 0, (int)s->fields.size()};
+    Seq<T> q{s, s->stream, 0, s->nslots()};
     return q.prologue();
 }
 
-template <typename T> int run_steps(pss_system *s, int64_t n) {
-    const int nf = (int)s->fields.size();
-    const int kGraphSteps = s->tune_graph_steps > 0 ? s->tune_graph_steps : kDefaultGraphSteps;
-    int64_t done = 0;
-    if (n >= kGraphSteps) {
-        if (!s->graph_valid) {
-            if (s->graph) { cudaGraphExecDestroy(s->graph); s->graph = nullptr; }
-            CK(cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal));
-            Seq<T> q{s, s->cap_stream, 0, nf};
-            int rc = PSS_OK;
-            const int64_t before = s->launches;
-            for (int k = 0; k < kGraphSteps && rc == PSS_OK; ++k) rc = q.one_step();
-            s->launches = before;
-            cudaGraph_t g = nullptr;
-            cudaError_t e = cudaStreamEndCapture(s->cap_stream, &g);
-            if (rc) { if (g) cudaGraphDestroy(g); return rc; }
-            if (e != cudaSuccess) return cuda_fail(s, e, "cudaStreamEndCapture");
-            e = cudaGraphInstantiate(&s->graph, g, 0);
-            cudaGraphDestroy(g);
-            if (e != cudaSuccess) return cuda_fail(s, e, "cudaGraphInstantiate");
-            s->graph_valid = true;
-        }
-        const int per_step = s->dim == 3 ? 4 : 2;
-        while (n - done >= kGraphSteps) {
-            CK(cudaGraphLaunch(s->graph, s->stream));
-            s->launches += (int64_t)kGraphSteps * per_step;
-            done += kGraphSteps;
-        }
-    }
-    Seq<T> q{s, s->stream, 0, nf};
-    for (; done < n; ++done) {
-        int rc = q.one_step();
+int prologue(pss_system *s) {
+    if (!s->stale) return PSS_OK;
+    int rc = s->prec == PSS_F64 ? run_prologue<double>(s) : run_prologue<float>(s);
+    if (rc) return rc;
+    s->stale = false;
+    return PSS_OK;
+}
+
+int record_steps(pss_system *s, cudaStream_t st, int64_t n) {
+    for (int64_t k = 0; k < n; ++k) {
+        int rc = s->prec == PSS_F64 ? Seq<double>{s, st, 0, s->nslots()}.one_step()
+                                    : Seq<float>{s, st, 0, s->nslots()}.one_step();
         if (rc) return rc;
     }
     return PSS_OK;
 }
 
+// capture `steps` steps of every system into one graph (on systems[0]'s capture stream)
+int capture_graph(pss_system **sys, int n, int steps, cudaGraphExec_t *out) {
+    pss_system *s = sys[0];
+    CK(cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal));
+    int rc = PSS_OK;
+    std::vector<int64_t> before(n);
+    for (int i = 0; i < n; ++i) before[i] = sys[i]->launches;
+    for (int k = 0; k < steps && rc == PSS_OK; ++k)
+        for (int i = 0; i < n && rc == PSS_OK; ++i) {
+            rc = record_steps(sys[i], s->cap_stream, 1);
+            if (rc && i != 0) s->err = sys[i]->err;
+        }
+    for (int i = 0; i < n; ++i) sys[i]->launches = before[i];
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(s->cap_stream, &g);
+    if (rc) { if (g) cudaGraphDestroy(g); return rc; }
+    if (e != cudaSuccess) return cuda_fail(s, e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(s, e, "cudaGraphInstantiate");
+    return PSS_OK;
+}
+
+int run_steps(pss_system *s, int64_t n) {
+    const int chunk = s->tune_graph_steps > 0 ? s->tune_graph_steps : kDefaultGraphSteps;
+    int64_t done = 0;
+    if (n >= chunk) {
+        if (!s->graph_valid) {
+            if (s->graph) { cudaGraphExecDestroy(s->graph); s->graph = nullptr; }
+            int rc = capture_graph(&s, 1, chunk, &s->graph);
+            if (rc) return rc;
+            s->graph_valid = true;
+        }
+        const int per_step = s->dim == 3 ? 4 : 2;
+        while (n - done >= chunk) {
+            CK(cudaGraphLaunch(s->graph, s->stream));
+            s->launches += (int64_t)chunk * per_step;
+            done += chunk;
+        }
+    }
+    return record_steps(s, s->stream, n - done);
+}
+
 template <typename T> int timed_steps(pss_system *s, int64_t n, double *avg_ms) {
     Timer timer;
-    Seq<T> q{s, s->cap_stream, 0, (int)s->fields.size(), &timer};
+    Seq<T> q{s, s->cap_stream, 0, s->nslots(), &timer};
     CK(cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal));
     int rc = PSS_OK;
     for (int64_t k = 0; k < n && rc == PSS_OK; ++k) rc = q.one_step();
@@ -442,11 +493,10 @@ int check_field(pss_system *s, int fid) {
     return PSS_OK;
 }
 
+int cur_slot(const pss_system *s, int fid) { return s->cur * (int)s->fields.size() + fid; }
+
 int ensure_real(pss_system *s) {
-    if (!s->real) {
-        const size_t bytes = rsize(s) * (size_t)s->nsites * kMaxFields;
-        CK(cudaMalloc(&s->real, bytes));
-    }
+    if (!s->real) CK(cudaMalloc(&s->real, rsize(s) * (size_t)s->nsites));
     return PSS_OK;
 }
 
@@ -461,6 +511,7 @@ int device_errors(pss_system *s) {
     CK(cudaStreamSynchronize(s->stream));
     if (st) {
         CK(cudaMemsetAsync(s->d_status, 0, sizeof(int), s->stream));
+        if (st & 2) return fail(s, PSS_ETIMEOUT, "a bounded device wait ran out");
         return fail(s, PSS_ENONFINITE, "a field became NaN or Inf");
     }
     return PSS_OK;
@@ -468,18 +519,37 @@ int device_errors(pss_system *s) {
 
 void invalidate(pss_system *s) { s->graph_valid = false; }
 
-}  // namespace
+// (re)allocate the slot arrays for the current number of slots, keeping the
+// data of the slots that exist
+int grow_arrays(pss_system *s, int old_nf) {
+    const int nf = (int)s->fields.size();
+    const size_t slot_bytes = csize(s) * s->field_elems;
+    void **arrays[3] = {&s->state, &s->A, &s->B};
+    for (void **arr : arrays) {
+        void *nb = nullptr;
+        CK(cudaMalloc(&nb, slot_bytes * (size_t)s->batch * nf));
+        CK(cudaMemset(nb, 0, slot_bytes * (size_t)s->batch * nf));
+        if (*arr && old_nf > 0)
+            for (int b = 0; b < s->batch; ++b)
+                CK(cudaMemcpy((char *)nb + slot_bytes * ((size_t)b * nf), (char *)*arr + slot_bytes * ((size_t)b * old_nf),
+                              slot_bytes * old_nf, cudaMemcpyDeviceToDevice));
+        cudaFree(*arr);
+        *arr = nb;
+    }
+    cudaFree(s->fps);
+    s->fps = nullptr;
+    CK(cudaMalloc(&s->fps, fpsize(s) * (size_t)s->batch * nf));
+    s->fps_dirty = true;
+    return PSS_OK;
+}
 
-// ==========================================================================
-// C ABI
-// ==========================================================================
-extern "C" {
-
-int pss_create_system(pss_system **out, int dim, int nx, int ny, int nz, double dx, double dy, double dz,
-                      double dt, uint64_t seed, int precision) {
+int do_create(pss_system **out, int batch, int dim, int nx, int ny, int nz, double dx, double dy, double dz, double dt,
+              const uint64_t *seeds, int precision) {
     if (!out) return fail(nullptr, PSS_EINVAL, "out is NULL");
     *out = nullptr;
     if (dim < 1 || dim > 3) return fail(nullptr, PSS_EINVAL, "dim must be 1, 2 or 3");
+    if (batch < 1 || batch > kMaxBatch) return fail(nullptr, PSS_EINVAL, "batch must be in [1, %d]", kMaxBatch);
+    if (!seeds) return fail(nullptr, PSS_EINVAL, "seeds is NULL");
     if (dim < 2) ny = 1;
     if (dim < 3) nz = 1;
     if (!pow2_in(nx, 4, 1024) || (dim >= 2 && !pow2_in(ny, 4, 1024)) || (dim == 3 && !pow2_in(nz, 4, 1024)))
@@ -487,11 +557,13 @@ int pss_create_system(pss_system **out, int dim, int nx, int ny, int nz, double 
     if (!(dx > 0) || (dim >= 2 && !(dy > 0)) || (dim == 3 && !(dz > 0)) || !(dt > 0))
         return fail(nullptr, PSS_EINVAL, "spacings and dt must be positive");
     if (precision != PSS_F32 && precision != PSS_F64) return fail(nullptr, PSS_EINVAL, "precision");
-    if ((long long)nx * ny * nz > (1ll << 31)) return fail(nullptr, PSS_EUNSUPPORTED, "lattice too large");
+    if ((long long)nx * ny * nz > (1ll << 30)) return fail(nullptr, PSS_EUNSUPPORTED, "lattice too large");
     pss_system *s = new pss_system();
     s->dim = dim; s->nx = nx; s->ny = ny; s->nz = nz;
     s->dx[0] = dx; s->dx[1] = dim >= 2 ? dy : 1.0; s->dx[2] = dim == 3 ? dz : 1.0;
-    s->dt = dt; s->seed = seed; s->prec = precision;
+    s->dt = dt; s->prec = precision;
+    s->batch = batch;
+    s->seeds.assign(seeds, seeds + batch);
     s->hx = nx / 2 + 1;
     s->ntiles = (s->hx + kTileW - 1) / kTileW;
     s->rows = ny * nz;
@@ -530,14 +602,47 @@ int pss_create_system(pss_system **out, int dim, int nx, int ny, int nz, double 
     return PSS_OK;
 }
 
+// per-slot real-space transfers go through the one-slot scratch
+template <typename T> int forward_slot(pss_system *s, int slot) {
+    return Seq<T>{s, s->stream, slot, 1}.forward_from_real();
+}
+template <typename T> int inverse_slot(pss_system *s, int slot) {
+    return Seq<T>{s, s->stream, slot, 1}.inverse_to_real();
+}
+
+int forward_field(pss_system *s, int field_id) {
+    int rc = upload_params(s);
+    if (rc) return rc;
+    const int slot = cur_slot(s, field_id);
+    rc = s->prec == PSS_F64 ? forward_slot<double>(s, slot) : forward_slot<float>(s, slot);
+    s->stale = true;
+    return rc;
+}
+
+}  // namespace
+
+// ==========================================================================
+// C ABI
+// ==========================================================================
+extern "C" {
+
+int pss_create_system(pss_system **out, int dim, int nx, int ny, int nz, double dx, double dy, double dz,
+                      double dt, uint64_t seed, int precision) {
+    return do_create(out, 1, dim, nx, ny, nz, dx, dy, dz, dt, &seed, precision);
+}
+
+int pss_create_batch(pss_system **out, int batch, int dim, int nx, int ny, int nz, double dx, double dy, double dz,
+                     double dt, const uint64_t *seeds, int precision) {
+    return do_create(out, batch, dim, nx, ny, nz, dx, dy, dz, dt, seeds, precision);
+}
+
 int pss_destroy_system(pss_system *s) {
     if (!s) return PSS_OK;
     if (s->graph) cudaGraphExecDestroy(s->graph);
-    for (Field &f : s->fields) {
-        cudaFree(f.state);
-        cudaFree(f.A);
-        cudaFree(f.B);
-    }
+    cudaFree(s->state);
+    cudaFree(s->A);
+    cudaFree(s->B);
+    cudaFree(s->fps);
     cudaFree(s->tw);
     cudaFree(s->real);
     cudaFree(s->half);
@@ -567,28 +672,52 @@ int pss_set_stream(pss_system *s, void *stream) {
 
 int pss_add_param(pss_system *s, const char *name, double value, int *id) {
     if (!s || !name) return s ? fail(s, PSS_EINVAL, "name is NULL") : PSS_EINVAL;
-    for (const Param &p : s->params)
-        if (p.name == name) return fail(s, PSS_EINVAL, "parameter '%s' exists", name);
-    s->params.push_back({name, value});
-    if (id) *id = (int)s->params.size() - 1;
-    invalidate(s);
+    for (const std::string &p : s->param_names)
+        if (p == name) return fail(s, PSS_EINVAL, "parameter '%s' exists", name);
+    const size_t np = s->param_names.size();
+    std::vector<double> v((np + 1) * s->batch);
+    for (int b = 0; b < s->batch; ++b) {
+        for (size_t i = 0; i < np; ++i) v[b * (np + 1) + i] = s->param_values[b * np + i];
+        v[b * (np + 1) + np] = value;
+    }
+    s->param_values.swap(v);
+    s->param_names.push_back(name);
+    if (id) *id = (int)np;
+    s->fps_dirty = true;
     return PSS_OK;
 }
 
 int pss_set_param(pss_system *s, int id, double value) {
     if (!s) return PSS_EINVAL;
-    if (id < 0 || id >= (int)s->params.size()) return fail(s, PSS_EINVAL, "no parameter %d", id);
-    s->params[id].value = value;
-    invalidate(s);
+    if (id < 0 || id >= (int)s->param_names.size()) return fail(s, PSS_EINVAL, "no parameter %d", id);
+    for (int b = 0; b < s->batch; ++b) s->param_values[(size_t)b * s->param_names.size() + id] = value;
+    s->fps_dirty = true;
+    return PSS_OK;
+}
+
+int pss_set_param_batch(pss_system *s, int id, const double *values) {
+    if (!s || !values) return PSS_EINVAL;
+    if (id < 0 || id >= (int)s->param_names.size()) return fail(s, PSS_EINVAL, "no parameter %d", id);
+    for (int b = 0; b < s->batch; ++b) s->param_values[(size_t)b * s->param_names.size() + id] = values[b];
+    s->fps_dirty = true;
     return PSS_OK;
 }
 
 int pss_get_param(pss_system *s, int id, double *value) {
     if (!s || !value) return PSS_EINVAL;
-    if (id < 0 || id >= (int)s->params.size()) return fail(s, PSS_EINVAL, "no parameter %d", id);
-    *value = s->params[id].value;
+    if (id < 0 || id >= (int)s->param_names.size()) return fail(s, PSS_EINVAL, "no parameter %d", id);
+    *value = pval(s, s->cur, id);
     return PSS_OK;
 }
+
+int pss_select_instance(pss_system *s, int instance) {
+    if (!s) return PSS_EINVAL;
+    if (instance < 0 || instance >= s->batch) return fail(s, PSS_EINVAL, "no instance %d", instance);
+    s->cur = instance;
+    return PSS_OK;
+}
+
+int pss_batch_size(const pss_system *s) { return s ? s->batch : 0; }
 
 int pss_add_field(pss_system *s, const char *name, int dynamic, int *field_id) {
     if (!s || !name) return s ? fail(s, PSS_EINVAL, "name is NULL") : PSS_EINVAL;
@@ -596,21 +725,16 @@ int pss_add_field(pss_system *s, const char *name, int dynamic, int *field_id) {
     if ((int)s->fields.size() >= kMaxFields) return fail(s, PSS_EUNSUPPORTED, "at most %d fields", kMaxFields);
     for (const Field &f : s->fields)
         if (f.name == name) return fail(s, PSS_EINVAL, "field '%s' exists", name);
+    const int old_nf = (int)s->fields.size();
     Field f;
     f.name = name;
-    const size_t bytes = csize(s) * s->field_elems;
-    cudaError_t e = cudaMalloc(&f.state, bytes);
-    if (e == cudaSuccess) e = cudaMalloc(&f.A, bytes);
-    if (e == cudaSuccess) e = cudaMalloc(&f.B, bytes);
-    if (e == cudaSuccess) e = cudaMemset(f.state, 0, bytes);
-    if (e == cudaSuccess) e = cudaMemset(f.A, 0, bytes);
-    if (e == cudaSuccess) e = cudaMemset(f.B, 0, bytes);
-    if (e != cudaSuccess) {
-        cudaFree(f.state); cudaFree(f.A); cudaFree(f.B);
-        return cuda_fail(s, e, "pss_add_field");
-    }
     s->fields.push_back(f);
-    if (field_id) *field_id = (int)s->fields.size() - 1;
+    int rc = grow_arrays(s, old_nf);
+    if (rc) {
+        s->fields.pop_back();
+        return rc;
+    }
+    if (field_id) *field_id = old_nf;
     s->stale = true;
     invalidate(s);
     return PSS_OK;
@@ -624,7 +748,7 @@ int pss_add_term(pss_system *s, int field_id, int implicit, int n_mono, const in
     for (int m = 0; m < n_mono; ++m) {
         if (q2_pows[m] < 0 || q2_pows[m] >= kPolyTerms) return fail(s, PSS_EINVAL, "q^2 power must be in [0, 4]");
         const int pid = param_ids ? param_ids[m] : -1;
-        if (pid >= (int)s->params.size()) return fail(s, PSS_EINVAL, "no parameter %d", pid);
+        if (pid >= (int)s->param_names.size()) return fail(s, PSS_EINVAL, "no parameter %d", pid);
     }
     if (n_factors < 1 || !factor_fields || !powers) return fail(s, PSS_EINVAL, "need at least one factor");
     if (n_factors != 1 || factor_fields[0] != field_id)
@@ -641,20 +765,21 @@ int pss_add_term(pss_system *s, int field_id, int implicit, int n_mono, const in
         for (int m = 0; m < n_mono; ++m) f.rhs.push_back({param_ids ? param_ids[m] : -1, scales[m], q2_pows[m]});
     }
     s->stale = true;
-    invalidate(s);
+    s->fps_dirty = true;
     return PSS_OK;
 }
 
 int pss_set_noise(pss_system *s, int field_id, int D_param_id, int q2_pow) {
     int rc = check_field(s, field_id);
     if (rc) return rc;
-    if (D_param_id < 0 || D_param_id >= (int)s->params.size()) return fail(s, PSS_EINVAL, "no parameter %d", D_param_id);
+    if (D_param_id < 0 || D_param_id >= (int)s->param_names.size())
+        return fail(s, PSS_EINVAL, "no parameter %d", D_param_id);
     if (q2_pow < 0 || q2_pow >= kPolyTerms) return fail(s, PSS_EINVAL, "q^2 power must be in [0, 4]");
     Field &f = s->fields[field_id];
     f.noisy = true;
     f.noise_param = D_param_id;
     f.noise_pow = q2_pow;
-    invalidate(s);
+    s->fps_dirty = true;
     return PSS_OK;
 }
 
@@ -664,16 +789,9 @@ int pss_set_dealias(pss_system *s, int field_id, int order) {
     if (order < 0) return fail(s, PSS_EINVAL, "order must be >= 0");
     s->fields[field_id].dealias = order;
     s->stale = true;
-    invalidate(s);
+    s->fps_dirty = true;
+    invalidate(s);   // the number of kept tiles is baked into the launches
     return PSS_OK;
-}
-
-static int forward_field(pss_system *s, int field_id) {
-    int rc;
-    if (s->prec == PSS_F64) rc = Seq<double>{s, s->stream, field_id, 1}.forward_from_real();
-    else rc = Seq<float>{s, s->stream, field_id, 1}.forward_from_real();
-    s->stale = true;
-    return rc;
 }
 
 int pss_set_field(pss_system *s, int field_id, const void *real, int where) {
@@ -691,10 +809,10 @@ int pss_init_uniform(pss_system *s, int field_id, double lo, double hi) {
     int rc = check_field(s, field_id);
     if (rc) return rc;
     if ((rc = ensure_real(s))) return rc;
-    const uint32_t s0 = (uint32_t)(s->seed & 0xffffffffu), s1 = (uint32_t)(s->seed >> 32);
+    const uint64_t seed = s->seeds[s->cur];
     cudaError_t e = s->prec == PSS_F64
-        ? launch_init_uniform<double>((double *)s->real, s->nsites, lo, hi, s0, s1, field_id, s->stream)
-        : launch_init_uniform<float>((float *)s->real, s->nsites, lo, hi, s0, s1, field_id, s->stream);
+        ? launch_init_uniform<double>((double *)s->real, s->nsites, lo, hi, seed, field_id, s->stream)
+        : launch_init_uniform<float>((float *)s->real, s->nsites, lo, hi, seed, field_id, s->stream);
     s->launches++;
     if (e != cudaSuccess) return cuda_fail(s, e, "init kernel");
     return forward_field(s, field_id);
@@ -705,15 +823,49 @@ int pss_step(pss_system *s, int64_t n) {
     if (n < 0) return fail(s, PSS_EINVAL, "n must be >= 0");
     if (s->fields.empty()) return fail(s, PSS_EINVAL, "no fields");
     if (n == 0) return PSS_OK;
-    int rc;
-    if (s->stale) {
-        rc = s->prec == PSS_F64 ? run_prologue<double>(s) : run_prologue<float>(s);
-        if (rc) return rc;
-        s->stale = false;
-    }
-    rc = s->prec == PSS_F64 ? run_steps<double>(s, n) : run_steps<float>(s, n);
+    int rc = upload_params(s);
     if (rc) return rc;
+    if ((rc = prologue(s))) return rc;
+    if ((rc = run_steps(s, n))) return rc;
     s->step += n;
+    return PSS_OK;
+}
+
+int pss_step_many(pss_system **systems, int n, int64_t steps) {
+    if (!systems || n < 1) return fail(nullptr, PSS_EINVAL, "need at least one system");
+    pss_system *s0 = systems[0];
+    if (!s0) return fail(nullptr, PSS_EINVAL, "systems[0] is NULL");
+    if (steps < 0) return fail(s0, PSS_EINVAL, "steps must be >= 0");
+    for (int i = 0; i < n; ++i) {
+        pss_system *s = systems[i];
+        if (!s || s->fields.empty()) return fail(s0, PSS_EINVAL, "system %d has no fields", i);
+        if (i > 0) {
+            int rc = pss_set_stream(s, s0->stream);
+            if (rc) return fail(s0, rc, "%s", s->err.c_str());
+        }
+        int rc = upload_params(s);
+        if (!rc) rc = prologue(s);
+        if (rc) return i == 0 ? rc : fail(s0, rc, "%s", s->err.c_str());
+    }
+    if (steps == 0) return PSS_OK;
+    const int chunk = s0->tune_graph_steps > 0 ? s0->tune_graph_steps : kDefaultGraphSteps;
+    int64_t done = 0;
+    if (steps >= chunk) {
+        cudaGraphExec_t ge = nullptr;
+        int rc = capture_graph(systems, n, chunk, &ge);
+        if (rc) return rc;
+        cudaError_t e = cudaSuccess;
+        for (; steps - done >= chunk && e == cudaSuccess; done += chunk) e = cudaGraphLaunch(ge, s0->stream);
+        cudaGraphExecDestroy(ge);
+        if (e != cudaSuccess) return cuda_fail(s0, e, "cudaGraphLaunch");
+        for (int i = 0; i < n; ++i) systems[i]->launches += done * (systems[i]->dim == 3 ? 4 : 2);
+    }
+    for (; done < steps; ++done)
+        for (int i = 0; i < n; ++i) {
+            int rc = record_steps(systems[i], s0->stream, 1);
+            if (rc) return i == 0 ? rc : fail(s0, rc, "%s", systems[i]->err.c_str());
+        }
+    for (int i = 0; i < n; ++i) systems[i]->step += steps;
     return PSS_OK;
 }
 
@@ -721,12 +873,9 @@ int pss_time_kernels(pss_system *s, int64_t n, double *avg_ms) {
     if (!s || !avg_ms) return PSS_EINVAL;
     if (n < 1) return fail(s, PSS_EINVAL, "n must be >= 1");
     if (s->fields.empty()) return fail(s, PSS_EINVAL, "no fields");
-    int rc;
-    if (s->stale) {
-        rc = s->prec == PSS_F64 ? run_prologue<double>(s) : run_prologue<float>(s);
-        if (rc) return rc;
-        s->stale = false;
-    }
+    int rc = upload_params(s);
+    if (rc) return rc;
+    if ((rc = prologue(s))) return rc;
     rc = s->prec == PSS_F64 ? timed_steps<double>(s, n, avg_ms) : timed_steps<float>(s, n, avg_ms);
     if (rc) return rc;
     s->step += n;
@@ -768,8 +917,9 @@ int pss_get_field(pss_system *s, int field_id, void *real_out, int where) {
     if (rc) return rc;
     if (!real_out) return fail(s, PSS_EINVAL, "real_out is NULL");
     if ((rc = ensure_real(s))) return rc;
-    rc = s->prec == PSS_F64 ? Seq<double>{s, s->stream, field_id, 1}.inverse_to_real()
-                            : Seq<float>{s, s->stream, field_id, 1}.inverse_to_real();
+    if ((rc = upload_params(s))) return rc;
+    const int slot = cur_slot(s, field_id);
+    rc = s->prec == PSS_F64 ? inverse_slot<double>(s, slot) : inverse_slot<float>(s, slot);
     if (rc) return rc;
     if (s->dim == 3) s->stale = true;   // the y pass reused B
     const size_t bytes = rsize(s) * (size_t)s->nsites;
@@ -783,11 +933,12 @@ int pss_get_spectrum(pss_system *s, int field_id, void *half_out, int where) {
     if (rc) return rc;
     if (!half_out) return fail(s, PSS_EINVAL, "half_out is NULL");
     if ((rc = ensure_half(s))) return rc;
+    const size_t ofs = csize(s) * s->field_elems * (size_t)cur_slot(s, field_id);
     cudaError_t e = s->prec == PSS_F64
-        ? launch_tiles_to_half<double>(sys_params<double>(s), (const double2 *)s->fields[field_id].state,
+        ? launch_tiles_to_half<double>(sys_params<double>(s), (const double2 *)((char *)s->state + ofs),
                                        (double2 *)s->half, s->stream)
-        : launch_tiles_to_half<float>(sys_params<float>(s), (const float2 *)s->fields[field_id].state,
-                                      (float2 *)s->half, s->stream);
+        : launch_tiles_to_half<float>(sys_params<float>(s), (const float2 *)((char *)s->state + ofs), (float2 *)s->half,
+                                      s->stream);
     s->launches++;
     if (e != cudaSuccess) return cuda_fail(s, e, "layout kernel");
     const size_t bytes = csize(s) * (size_t)s->hx * s->ny * s->nz;
@@ -804,11 +955,12 @@ int pss_set_spectrum(pss_system *s, int field_id, const void *half_in, int where
     const size_t bytes = csize(s) * (size_t)s->hx * s->ny * s->nz;
     CK(cudaMemcpyAsync(s->half, half_in, bytes, where == PSS_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
                        s->stream));
+    const size_t ofs = csize(s) * s->field_elems * (size_t)cur_slot(s, field_id);
     cudaError_t e = s->prec == PSS_F64
         ? launch_half_to_tiles<double>(sys_params<double>(s), (const double2 *)s->half,
-                                       (double2 *)s->fields[field_id].state, s->stream)
-        : launch_half_to_tiles<float>(sys_params<float>(s), (const float2 *)s->half,
-                                      (float2 *)s->fields[field_id].state, s->stream);
+                                       (double2 *)((char *)s->state + ofs), s->stream)
+        : launch_half_to_tiles<float>(sys_params<float>(s), (const float2 *)s->half, (float2 *)((char *)s->state + ofs),
+                                      s->stream);
     s->launches++;
     if (e != cudaSuccess) return cuda_fail(s, e, "layout kernel");
     s->stale = true;
@@ -827,11 +979,12 @@ int pss_structure_factor(pss_system *s, int field_id, int nbins, double *S_out, 
         s->sq_cap = need;
     }
     CK(cudaMemsetAsync(s->sq, 0, sizeof(double) * need, s->stream));
+    const size_t ofs = csize(s) * s->field_elems * (size_t)cur_slot(s, field_id);
     cudaError_t e = s->prec == PSS_F64
-        ? launch_structure_factor<double>(sys_params<double>(s), s->dx, (const double2 *)s->fields[field_id].state,
-                                          nbins, s->sq, s->stream)
-        : launch_structure_factor<float>(sys_params<float>(s), s->dx, (const float2 *)s->fields[field_id].state,
-                                         nbins, s->sq, s->stream);
+        ? launch_structure_factor<double>(sys_params<double>(s), s->dx, (const double2 *)((char *)s->state + ofs), nbins,
+                                          s->sq, s->stream)
+        : launch_structure_factor<float>(sys_params<float>(s), s->dx, (const float2 *)((char *)s->state + ofs), nbins,
+                                         s->sq, s->stream);
     s->launches++;
     if (e != cudaSuccess) return cuda_fail(s, e, "structure factor kernel");
     std::vector<double> h(need);

@@ -24,6 +24,9 @@ constexpr int kPolyTerms = 5;   // operators are polynomials of degree <= 4 in q
 // pencils of kTileW columns with unit stride and the x pass reads
 // kTileW-wide segments of many rows at once.
 
+// Parameters of one (instance, field) slot.  Slots are numbered
+// slot = instance * n_fields + field; every array of a system holds its slots
+// back to back, slot_stride elements apart.
 template <typename T> struct FieldP {
     T O[kPolyTerms];      // implicit operator O(q) = sum O[p] (q^2)^p  (L~ = -O)
     T M[kPolyTerms];      // explicit operator M(q) applied to the product term
@@ -32,7 +35,9 @@ template <typename T> struct FieldP {
     int noisy;
     int power;            // product (phi^d)^power; 0 = no explicit term
     int kmax[3];          // largest kept |k| per axis of the de-alias mask
-    int field_id;
+    int kx_cols;          // kept half-spectrum columns (kmax[0] + 1, at most Nx/2 + 1)
+    int field_id;         // Philox counter word 2
+    uint32_t seed_lo, seed_hi;   // Philox key of the slot's instance
 };
 
 template <typename T> struct SysP {
@@ -42,7 +47,6 @@ template <typename T> struct SysP {
     int n_outer, n_inner;
     T gx, gy, gz;         // 2 pi / (N dx) per axis (0 for unused axes)
     T dt, inv_nsites;
-    uint32_t seed_lo, seed_hi;
     int pdl;              // launch with programmatic stream serialisation
 };
 
@@ -50,13 +54,17 @@ enum ColMode { COL_STEP = 0, COL_FWD = 1, COL_INV_MASK = 2, COL_INV_FULL = 3 };
 enum RowMode { ROW_FUSED = 0, ROW_R2C = 1, ROW_C2R = 2 };
 enum MidMode { MID_INV_MASK = 0, MID_INV_FULL = 1, MID_FWD = 2 };
 
-
+// Arrays: slot s of an array starts at base + s * slot_stride (complex
+// elements; real arrays: s * real_stride reals).  A launch covers slots
+// slot0 .. slot0 + gridDim.z - 1.
 template <typename T> struct ColArgs {
     SysP<T> sp;
-    FieldP<T> fp[kMaxFields];
-    const cplx<T> *in[kMaxFields];
-    cplx<T> *out[kMaxFields];
-    cplx<T> *state[kMaxFields];
+    const FieldP<T> *fps;
+    const cplx<T> *in;
+    cplx<T> *out;
+    cplx<T> *state;
+    size_t slot_stride;
+    int slot0;
     const cplx<T> *tw;
     const long long *d_step;
     int *d_status;
@@ -66,23 +74,26 @@ template <typename T> struct ColArgs {
 
 template <typename T> struct RowArgs {
     SysP<T> sp;
-    int power[kMaxFields];
-    const cplx<T> *in[kMaxFields];
-    cplx<T> *out[kMaxFields];
-    const T *real_in[kMaxFields];
-    T *real_out[kMaxFields];
+    const FieldP<T> *fps;
+    const cplx<T> *in;
+    cplx<T> *out;
+    const T *real_in;
+    T *real_out;
+    size_t slot_stride, real_stride;
+    int slot0;
     const cplx<T> *tw;
     long long *d_step;
     int *d_status;
-    int kx_cols[kMaxFields];   // half-spectrum columns read from the input (the rest are zero)
     int mode, G, inc_step;
 };
 
 template <typename T> struct MidArgs {
     SysP<T> sp;
-    int kmax_y[kMaxFields];
-    const cplx<T> *in[kMaxFields];
-    cplx<T> *out[kMaxFields];
+    const FieldP<T> *fps;
+    const cplx<T> *in;
+    cplx<T> *out;
+    size_t slot_stride;
+    int slot0;
     const cplx<T> *tw;
     long long *d_step;
     int *d_status;
@@ -95,12 +106,11 @@ struct RowCfg { int G; };
 struct MidCfg { int PZ; };
 
 // Launchers (one instantiation per precision; defined in pss_kern_f32.cu / pss_kern_f64.cu).
-template <typename T> cudaError_t launch_col(const ColArgs<T> &a, int nfields, int grid_x, int grid_y, cudaStream_t st);
-template <typename T> cudaError_t launch_row(const RowArgs<T> &a, int nfields, cudaStream_t st);
-template <typename T> cudaError_t launch_mid(const MidArgs<T> &a, int nfields, int n_tiles, cudaStream_t st);
+template <typename T> cudaError_t launch_col(const ColArgs<T> &a, int nslots, int grid_x, int grid_y, cudaStream_t st);
+template <typename T> cudaError_t launch_row(const RowArgs<T> &a, int nslots, cudaStream_t st);
+template <typename T> cudaError_t launch_mid(const MidArgs<T> &a, int nslots, int n_tiles, cudaStream_t st);
 template <typename T> cudaError_t launch_init_uniform(T *real, long long nsites, double lo, double hi,
-                                                      uint32_t seed_lo, uint32_t seed_hi, int field_id,
-                                                      cudaStream_t st);
+                                                      uint64_t seed, int field_id, cudaStream_t st);
 template <typename T> cudaError_t launch_tiles_to_half(const SysP<T> &sp, const cplx<T> *tiles,
                                                        cplx<T> *half, cudaStream_t st);
 template <typename T> cudaError_t launch_half_to_tiles(const SysP<T> &sp, const cplx<T> *half,

@@ -42,8 +42,8 @@ __device__ __forceinline__ int signed_k(int k, int n) { return k < (n + 1) / 2 ?
 // on_plane: kx0 is 0 or Nx/2 (its partner is (kx0, -ky, -kz)).
 template <typename T>
 __device__ __forceinline__ void noise_pair(bool on_plane, int kx0, int ky, int kz, T amp0, T amp1, bool has1,
-                                           const SysP<T> &sp, uint32_t fid, uint32_t step, cplx<T> &xi0,
-                                           cplx<T> &xi1) {
+                                           const SysP<T> &sp, uint32_t fid, uint32_t seed_lo, uint32_t seed_hi,
+                                           uint32_t step, cplx<T> &xi0, cplx<T> &xi1) {
     const uint32_t row = (uint32_t)(kz * sp.ny + ky);
     uint32_t crow = row;
     bool cj = false, selfc = false;
@@ -52,16 +52,14 @@ __device__ __forceinline__ void noise_pair(bool on_plane, int kx0, int ky, int k
         selfc = prow == row;
         if (prow < row) { crow = prow; cj = true; }
     }
-    u32x4 r = philox4x32_10(u32x4{(crow * (uint32_t)sp.hxe + (uint32_t)kx0) >> 1, step, fid, 0u}, sp.seed_lo,
-                            sp.seed_hi);
+    u32x4 r = philox4x32_10(u32x4{(crow * (uint32_t)sp.hxe + (uint32_t)kx0) >> 1, step, fid, 0u}, seed_lo, seed_hi);
     T n1, n2;
     box_muller(uniform24<T>(r.x), uniform24<T>(r.y), n1, n2);
     xi0 = selfc ? mk<T>(T(1.4142135623730951) * amp0 * n1, T(0)) : mk<T>(amp0 * n1, cj ? -amp0 * n2 : amp0 * n2);
     if (has1) {
         // kx1 is odd, so it is never 0 or Nx/2: it is its own canonical member
         if (crow != row)
-            r = philox4x32_10(u32x4{(row * (uint32_t)sp.hxe + (uint32_t)kx0) >> 1, step, fid, 0u}, sp.seed_lo,
-                              sp.seed_hi);
+            r = philox4x32_10(u32x4{(row * (uint32_t)sp.hxe + (uint32_t)kx0) >> 1, step, fid, 0u}, seed_lo, seed_hi);
         box_muller(uniform24<T>(r.z), uniform24<T>(r.w), n1, n2);
         xi1 = mk<T>(amp1 * n1, amp1 * n2);
     }
@@ -76,17 +74,18 @@ template <typename T> __device__ __forceinline__ T noise_amp(T sigma0, int p, T 
     return amp;
 }
 
-// Eq. (timeupdate): (phi + dt M P + xi) / (1 + dt O), O = -L~
+// Eq. (timeupdate): (phi + dt M P + xi) / (1 + dt O), O = -L~; dtO, dtM are
+// dt times the operator coefficients
 template <typename T>
-__device__ __forceinline__ cplx<T> update_mode(cplx<T> phi, cplx<T> P, cplx<T> xi, T q2, const SysP<T> &sp,
-                                               const FieldP<T> &fp) {
+__device__ __forceinline__ cplx<T> update_mode(cplx<T> phi, cplx<T> P, cplx<T> xi, T q2, const T *dtO, const T *dtM,
+                                               bool has_product) {
     T nx = phi.x + xi.x, ny = phi.y + xi.y;
-    if (fp.power > 0) {
-        const T dtM = sp.dt * poly5<T>(fp.M, q2);
-        nx += dtM * P.x;
-        ny += dtM * P.y;
+    if (has_product) {
+        const T m = poly5<T>(dtM, q2);
+        nx += m * P.x;
+        ny += m * P.y;
     }
-    const T g = fast_rcp(T(1) + sp.dt * poly5<T>(fp.O, q2));
+    const T g = fast_rcp(T(1) + poly5<T>(dtO, q2));
     return mk<T>(nx * g, ny * g);
 }
 
@@ -129,8 +128,9 @@ __global__ void __launch_bounds__(512) k_col(const ColArgs<T> a) {
     C *X = PHI + nchunks * CS;
     C *Y = X + L::xs(F);
     const SysP<T> &sp = a.sp;
-    const int fld = blockIdx.z;
-    const FieldP<T> &fp = a.fp[fld];
+    const int slot = a.slot0 + blockIdx.z;
+    const FieldP<T> &fp = a.fps[slot];
+    const size_t sofs = (size_t)slot * a.slot_stride;
     const int logNP = sp.dim == 3 ? 1 : 0;
     const int t = threadIdx.x, nthr = blockDim.x;
     const int op = blockIdx.y;
@@ -157,8 +157,8 @@ __global__ void __launch_bounds__(512) k_col(const ColArgs<T> a) {
         mbar_init(bar, 1);
         mbar_expect_tx(bar, chunk_bytes * nvalid * ((need_in ? 1 : 0) + (need_phi ? 1 : 0)));
         for (int ch = 0; ch < nvalid; ++ch) {
-            if (need_phi) bulk_g2s(PHI + ch * CS, a.state[fld] + gofs(ch), chunk_bytes, bar);
-            if (need_in) bulk_g2s(X + ch * CS, a.in[fld] + gofs(ch), chunk_bytes, bar);
+            if (need_phi) bulk_g2s(PHI + ch * CS, a.state + sofs + gofs(ch), chunk_bytes, bar);
+            if (need_in) bulk_g2s(X + ch * CS, a.in + sofs + gofs(ch), chunk_bytes, bar);
         }
     }
     __syncthreads();   // the barrier is initialised before anyone polls it
@@ -198,6 +198,16 @@ __global__ void __launch_bounds__(512) k_col(const ColArgs<T> a) {
         const C *P0 = P + (chq * W + c0) * SF, *P1 = P0 + SF;
         C *phb = PHI + chq * CS + c0;
         bool bad = false;
+        T dtO[kPolyTerms], dtM[kPolyTerms];
+#pragma unroll
+        for (int i = 0; i < kPolyTerms; ++i) {
+            dtO[i] = sp.dt * fp.O[i];
+            dtM[i] = sp.dt * fp.M[i];
+        }
+        const bool has_product = fp.power > 0, noisy = fp.noisy != 0;
+        const int noise_pow = fp.noise_pow, fid = fp.field_id;
+        const T sigma0 = fp.sigma0;
+        const uint32_t seed_lo = fp.seed_lo, seed_hi = fp.seed_hi;
         if (tile < a.n_tiles) {
 #pragma unroll 1
             for (int pos = t >> (1 + lognch); pos < N; pos += pos_step) {
@@ -210,12 +220,12 @@ __global__ void __launch_bounds__(512) k_col(const ColArgs<T> a) {
                     const T qyz2 = qy * qy + qz * qz;
                     const T q2a = qx0s + qyz2, q2b = qx1s + qyz2;
                     C xi0 = mk<T>(0, 0), xi1 = mk<T>(0, 0);
-                    if (fp.noisy)
-                        noise_pair<T>(on_plane, kx0, ky, kz, noise_amp<T>(fp.sigma0, fp.noise_pow, q2a),
-                                      noise_amp<T>(fp.sigma0, fp.noise_pow, q2b), has1, sp, (uint32_t)fp.field_id,
+                    if (noisy)
+                        noise_pair<T>(on_plane, kx0, ky, kz, noise_amp<T>(sigma0, noise_pow, q2a),
+                                      noise_amp<T>(sigma0, noise_pow, q2b), has1, sp, (uint32_t)fid, seed_lo, seed_hi,
                                       step, xi0, xi1);
-                    v0 = update_mode<T>(ph[0], v0, xi0, q2a, sp, fp);
-                    v1 = update_mode<T>(ph[1], v1, xi1, q2b, sp, fp);
+                    v0 = update_mode<T>(ph[0], v0, xi0, q2a, dtO, dtM, has_product);
+                    v1 = update_mode<T>(ph[1], v1, xi1, q2b, dtO, dtM, has_product);
                     // false for NaN and for infinities (or values next to overflow)
                     bad |= !(fabs(v0.x) + fabs(v0.y) + fabs(v1.x) + fabs(v1.y) <= T(sizeof(T) == 4 ? 3.0e38 : 1.0e300));
                 }
@@ -251,7 +261,7 @@ __global__ void __launch_bounds__(512) k_col(const ColArgs<T> a) {
         __syncthreads();
         if (t == 0) {
             for (int cq = 0; cq < nvalid; ++cq)
-                if (chunk_writes(cq)) bulk_s2g(a.state[fld] + gofs(cq), PHI + cq * CS, chunk_bytes);
+                if (chunk_writes(cq)) bulk_s2g(a.state + sofs + gofs(cq), PHI + cq * CS, chunk_bytes);
             bulk_commit();
         }
         if (mode == COL_FWD) {
@@ -276,7 +286,7 @@ __global__ void __launch_bounds__(512) k_col(const ColArgs<T> a) {
         const T scale = (kx_keep && o_keep) ? sp.inv_nsites : T(0);
         const C *pb = PHI + ch * CS + c;
         const bool writes = chunk_writes(ch) && (full || my_tile * W <= fp.kmax[0]);
-        C *__restrict__ dst = a.out[fld] + gofs(ch) + c;
+        C *__restrict__ dst = a.out + sofs + gofs(ch) + c;
         fft_run<T, N, +1>(
             [&](int p) { return abs(signed_k(p, N)) <= kmax_pos ? cscale<T>(pb[p * W], scale) : mk<T>(0, 0); },
             [&](int p, C v, C *) {
@@ -340,7 +350,9 @@ __global__ void __launch_bounds__(256) k_row(const RowArgs<T> a) {
     T *Sr = reinterpret_cast<T *>(S);
     C *B0 = S + L::s_elems(G, sp.ntiles);
     C *B1 = B0 + G * SF;
-    const int fld = blockIdx.y;
+    const int slot = a.slot0 + blockIdx.y;
+    const FieldP<T> &fp = a.fps[slot];
+    const size_t sofs = (size_t)slot * a.slot_stride;
     const int t = threadIdx.x, nthr = blockDim.x;
     const int r0 = blockIdx.x * G2;
     const int rows = sp.rows;
@@ -352,7 +364,7 @@ __global__ void __launch_bounds__(256) k_row(const RowArgs<T> a) {
 
     // ---- stage the input rows
     if (mode == ROW_R2C) {
-        const T *__restrict__ src = a.real_in[fld];
+        const T *__restrict__ src = a.real_in + (size_t)slot * a.real_stride;
         const uint32_t row_bytes = (uint32_t)(N * sizeof(T));
         if (t == 0) {
             mbar_init(bar, 1);
@@ -362,8 +374,9 @@ __global__ void __launch_bounds__(256) k_row(const RowArgs<T> a) {
         __syncthreads();   // the barrier is initialised before anyone polls it
         for (int i = nrow * N + t; i < G2 * N; i += nthr) Sr[i] = T(0);
     } else {
-        const C *__restrict__ src = a.in[fld];
-        const int ntl = (a.kx_cols[fld] + W - 1) / W;
+        const C *__restrict__ src = a.in + sofs;
+        const int kxc_in = mode == ROW_FUSED ? fp.kx_cols : sp.hx;
+        const int ntl = (kxc_in + W - 1) / W;
         const uint32_t seg = (uint32_t)(nrow * W * sizeof(C));
         if (t == 0) {
             mbar_init(bar, 1);
@@ -389,7 +402,7 @@ __global__ void __launch_bounds__(256) k_row(const RowArgs<T> a) {
                                             smem_sink, b0, b1, lane, active, tw);
         R = which == 0 ? B0 : B1;
     } else {
-        const int kxc = a.kx_cols[fld];
+        const int kxc = mode == ROW_FUSED ? fp.kx_cols : sp.hx;
         const int which = fft_run<T, N, +1>(
             [&](int k) {
                 const int kk = k <= N / 2 ? k : N - k;
@@ -407,7 +420,7 @@ __global__ void __launch_bounds__(256) k_row(const RowArgs<T> a) {
         __syncthreads();
         C *Z = which == 0 ? B0 : B1;
         if (mode == ROW_C2R) {
-            T *__restrict__ dst = a.real_out[fld];
+            T *__restrict__ dst = a.real_out + (size_t)slot * a.real_stride;
 #pragma unroll 1
             for (int i = t; i < nrow * N; i += nthr) {
                 const int rl = i / N, x = i - rl * N;
@@ -417,7 +430,7 @@ __global__ void __launch_bounds__(256) k_row(const RowArgs<T> a) {
             return;
         }
         // forward transform of the real-space product (phi^d)^p of both rows
-        const int p = a.power[fld];
+        const int p = fp.power;
         C *zf = Z + g * SF;
         C *other = (which == 0 ? B1 : B0) + g * SF;
         const int which2 = fft_run<T, N, -1>(
@@ -430,7 +443,7 @@ __global__ void __launch_bounds__(256) k_row(const RowArgs<T> a) {
     }
     __syncthreads();
     // ---- split the pairs and write the half spectra of all tiles (coalesced)
-    C *__restrict__ dst = a.out[fld];
+    C *__restrict__ dst = a.out + sofs;
     const int logG2 = logG + 1;
 #pragma unroll 1
     for (int i = t; i < sp.ntiles * G2 * W; i += nthr) {
@@ -478,14 +491,15 @@ __global__ void __launch_bounds__(256) k_mid(const MidArgs<T> a) {
     const int SF = sf_fft_fastest(N, F);
     C *S = reinterpret_cast<C *>(smem_raw + 128);
     C *B0 = S + L::s_elems(F);
-    const int fld = blockIdx.z;
+    const int slot = a.slot0 + blockIdx.z;
+    const size_t sofs = (size_t)slot * a.slot_stride;
     const int t = threadIdx.x, nthr = blockDim.x;
     const int tile = blockIdx.x;
     const int pos0 = blockIdx.y * a.PZ;
     const int nz = sp.nz;
     const bool masked_in = a.mode == MID_INV_MASK;
-    const int kmy = a.kmax_y[fld];
-    const C *__restrict__ src = a.in[fld];
+    const int kmy = a.fps[slot].kmax[1];
+    const C *__restrict__ src = a.in + sofs;
     const uint32_t seg = (uint32_t)(F * sizeof(C));
     pdl_wait();
     pdl_trigger();
@@ -506,7 +520,7 @@ __global__ void __launch_bounds__(256) k_mid(const MidArgs<T> a) {
     if (!mbar_wait_all(bar, 0, a.d_status)) return;
     const int f = t & (F - 1), lane = t >> logF;
     const bool active = lane < TPF;
-    C *__restrict__ dst = a.out[fld] + (((size_t)tile * N) * nz + pos0) * W + f;
+    C *__restrict__ dst = a.out + sofs + (((size_t)tile * N) * nz + pos0) * W + f;
     const size_t ostride = (size_t)nz * W;
     auto src_f = [&](int p) { return S[p * F + f]; };
     auto sink = [&](int p, C v, C *) { dst[p * ostride] = v; };
@@ -694,12 +708,13 @@ template <typename T> cudaError_t launch_mid(const MidArgs<T> &a, int nf, int n_
 }
 
 template <typename T>
-cudaError_t launch_init_uniform(T *real, long long nsites, double lo, double hi, uint32_t s0, uint32_t s1,
-                                int field_id, cudaStream_t st) {
+cudaError_t launch_init_uniform(T *real, long long nsites, double lo, double hi, uint64_t seed, int field_id,
+                                cudaStream_t st) {
     const int threads = 256;
     long long blocks = (nsites + threads - 1) / threads;
     if (blocks > 65535) blocks = 65535;
-    k_init_uniform<T><<<(int)blocks, threads, 0, st>>>(real, nsites, T(lo), T(hi), s0, s1, field_id);
+    k_init_uniform<T><<<(int)blocks, threads, 0, st>>>(real, nsites, T(lo), T(hi), (uint32_t)(seed & 0xffffffffu),
+                                                     (uint32_t)(seed >> 32), field_id);
     return cudaGetLastError();
 }
 
@@ -736,8 +751,7 @@ cudaError_t launch_structure_factor(const SysP<T> &sp, const double dx[3], const
     template cudaError_t launch_col<T>(const ColArgs<T> &, int, int, int, cudaStream_t);                     \
     template cudaError_t launch_row<T>(const RowArgs<T> &, int, cudaStream_t);                               \
     template cudaError_t launch_mid<T>(const MidArgs<T> &, int, int, cudaStream_t);                          \
-    template cudaError_t launch_init_uniform<T>(T *, long long, double, double, uint32_t, uint32_t, int,     \
-                                                cudaStream_t);                                               \
+    template cudaError_t launch_init_uniform<T>(T *, long long, double, double, uint64_t, int, cudaStream_t); \
     template cudaError_t launch_tiles_to_half<T>(const SysP<T> &, const cplx<T> *, cplx<T> *, cudaStream_t); \
     template cudaError_t launch_half_to_tiles<T>(const SysP<T> &, const cplx<T> *, cplx<T> *, cudaStream_t); \
     template cudaError_t launch_structure_factor<T>(const SysP<T> &, const double *, const cplx<T> *, int,   \

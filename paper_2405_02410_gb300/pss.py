@@ -26,7 +26,8 @@ EXPORTS = [
     "pss_get_param", "pss_add_field", "pss_add_term", "pss_set_noise", "pss_set_dealias", "pss_set_field",
     "pss_init_uniform", "pss_step", "pss_get_step", "pss_set_step", "pss_get_field", "pss_get_spectrum",
     "pss_set_spectrum", "pss_structure_factor", "pss_sync", "pss_last_error", "pss_launch_count",
-    "pss_time_kernels", "pss_set_tuning",
+    "pss_time_kernels", "pss_set_tuning", "pss_create_batch", "pss_batch_size", "pss_select_instance",
+    "pss_set_param_batch", "pss_step_many",
 ]
 
 
@@ -67,6 +68,11 @@ def _load():
         "pss_launch_count": ([vp], i64),
         "pss_time_kernels": ([vp, i64, P(d)], i32),
         "pss_set_tuning": ([vp, ctypes.c_char_p, i32], i32),
+        "pss_create_batch": ([P(vp), i32, i32, i32, i32, i32, d, d, d, d, P(u64), i32], i32),
+        "pss_batch_size": ([vp], i32),
+        "pss_select_instance": ([vp, i32], i32),
+        "pss_set_param_batch": ([vp, i32, P(d)], i32),
+        "pss_step_many": ([P(vp), i32, i64], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -88,7 +94,7 @@ class System:
     (nx,), (ny, nx) or (nz, ny, nx) like numpy arrays of the real field."""
 
     def __init__(self, shape: Sequence[int], dt: float, dx: Sequence[float] = (1.0, 1.0, 1.0),
-                 seed: int = 0, precision: str = "f32"):
+                 seed: int = 0, precision: str = "f32", batch: int = 1, seeds: Optional[Sequence[int]] = None):
         self.shape = tuple(int(n) for n in shape)
         self.dim = len(self.shape)
         n = list(reversed(self.shape)) + [1] * (3 - self.dim)
@@ -98,9 +104,17 @@ class System:
         self.cdtype = np.complex128 if precision == "f64" else np.complex64
         h = ctypes.c_void_p()
         dxs = list(dx) + [1.0] * (3 - len(dx))
-        rc = lib.pss_create_system(ctypes.byref(h), self.dim, self.nx, self.ny, self.nz, dxs[0], dxs[1], dxs[2],
-                                   float(dt), ctypes.c_uint64(int(seed) & 0xFFFFFFFFFFFFFFFF),
-                                   PSS_F64 if precision == "f64" else PSS_F32)
+        prec = PSS_F64 if precision == "f64" else PSS_F32
+        self.batch = int(batch)
+        if self.batch == 1 and seeds is None:
+            rc = lib.pss_create_system(ctypes.byref(h), self.dim, self.nx, self.ny, self.nz, dxs[0], dxs[1], dxs[2],
+                                       float(dt), ctypes.c_uint64(int(seed) & 0xFFFFFFFFFFFFFFFF), prec)
+        else:
+            sd = list(seeds) if seeds is not None else [int(seed) + i for i in range(self.batch)]
+            assert len(sd) == self.batch
+            arr = (ctypes.c_uint64 * self.batch)(*[int(x) & 0xFFFFFFFFFFFFFFFF for x in sd])
+            rc = lib.pss_create_batch(ctypes.byref(h), self.batch, self.dim, self.nx, self.ny, self.nz, dxs[0],
+                                      dxs[1], dxs[2], float(dt), arr, prec)
         if rc != PSS_OK:
             raise PssError(rc, lib.pss_last_error(None).decode())
         self._h = h
@@ -135,6 +149,14 @@ class System:
 
     def set_param(self, pid: int, value: float):
         self._ck(lib.pss_set_param(self._h, pid, float(value)))
+
+    def set_param_batch(self, pid: int, values):
+        v = np.ascontiguousarray(values, dtype=np.float64)
+        assert v.shape == (self.batch,)
+        self._ck(lib.pss_set_param_batch(self._h, pid, v.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+
+    def select_instance(self, instance: int):
+        self._ck(lib.pss_select_instance(self._h, int(instance)))
 
     def get_param(self, pid: int) -> float:
         v = ctypes.c_double()
@@ -234,6 +256,14 @@ class System:
     @property
     def launch_count(self) -> int:
         return int(lib.pss_launch_count(self._h))
+
+
+def step_many(systems: Sequence[System], n: int):
+    """Advance several systems by n steps from one captured CUDA graph (on systems[0]'s stream)."""
+    arr = (ctypes.c_void_p * len(systems))(*[s._h for s in systems])
+    rc = lib.pss_step_many(arr, len(systems), int(n))
+    if rc != PSS_OK:
+        raise PssError(rc, lib.pss_last_error(systems[0]._h).decode())
 
 
 def _is_cuda_tensor(x) -> bool:
