@@ -231,6 +231,66 @@ def make_system(pss, shape, precision="f32"):
     return s
 
 
+def ensemble_systems(pss, n=512, gen_seed=2405, base_seed=10000):
+    """512 independent 2D Model B instances, sizes drawn uniformly from {64, 128, 256, 512}^2, per-instance
+    seeds base + i and a ~ U[-1.5, -0.5], grouped into one batched system per size class."""
+    import numpy as np
+    g = np.random.default_rng(gen_seed)
+    sizes = g.choice([64, 128, 256, 512], size=n)
+    a_vals = g.uniform(-1.5, -0.5, size=n)
+    systems, sites = [], 0
+    for sz in (64, 128, 256, 512):
+        idx = np.nonzero(sizes == sz)[0]
+        if len(idx) == 0:
+            continue
+        s = pss.System((int(sz), int(sz)), dt=0.01, batch=len(idx), seeds=[base_seed + int(i) for i in idx])
+        pss.add_model_b_field(s, a=-1.0, b=1.0, K=1.0, D=0.01)
+        s.set_param_batch(0, a_vals[idx])
+        for j in range(len(idx)):
+            s.select_instance(j)
+            s.init_uniform(0, -0.1, 0.1)
+        systems.append(s)
+        sites += len(idx) * int(sz) * int(sz)
+    return systems, sites, {int(k): int((sizes == k).sum()) for k in (64, 128, 256, 512)}
+
+
+def ensemble_measurement(pss, torch, stream, steps=200):
+    systems, sites, counts = ensemble_systems(pss)
+    for s in systems:
+        s.set_stream(stream)
+    pss.step_many(systems, 32)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    pss.step_many(systems, steps)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    for s in systems:
+        s.sync()
+        s.close()
+    # the plain single-system path on the same instances: one system per instance, run one after another
+    seq_ms = 0.0
+    for sz, cnt in counts.items():
+        one = pss.model_b((sz, sz), seed=1)
+        one.set_stream(stream)
+        one.init_uniform(0, -0.1, 0.1)
+        one.step(32)
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        one.step(steps)
+        f1.record(stream)
+        f1.synchronize()
+        seq_ms += cnt * f0.elapsed_time(f1) / steps
+        one.close()
+    return {"instances": 512, "size_counts": counts, "sites": sites, "ms_per_step": ms,
+            "site_steps_per_s": sites / (ms * 1e-3),
+            "sequential_single_system_ms_per_step": seq_ms,
+            "speedup_vs_sequential": seq_ms / ms}
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -350,6 +410,9 @@ def run_gpu(args):
         }
         s3.close()
 
+    if not args.no_ensemble:
+        extra["ensemble_512"] = ensemble_measurement(pss, torch, stream)
+
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
         "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -392,6 +455,7 @@ def main(argv=None):
     ap.add_argument("--impl", default="pss", choices=["pss", "reference"])
     ap.add_argument("--no-3d", action="store_true", help="skip the 256^3 secondary measurement")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-ensemble", action="store_true", help="skip the 512-instance ensemble measurement")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

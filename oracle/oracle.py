@@ -91,6 +91,7 @@ def lib():
         _lib.orc_run.argtypes = [f, d, ctypes.c_int64, ctypes.c_int64]
         _lib.orc_init_uniform.argtypes = [f, ctypes.c_double, ctypes.c_double, d]
         _lib.orc_structure_factor.argtypes = [f, d, ctypes.c_int, d, d, d]
+        _lib.orc_adjoint.argtypes = [f, d, ctypes.c_int64, ctypes.c_int64, d, d]
     return _lib
 
 
@@ -294,3 +295,47 @@ def structure_factor(m: Model, phi: np.ndarray, nbins: int = 64):
     lib().orc_structure_factor(ctypes.byref(s), _dptr(phi.view(np.float64)), int(nbins),
                                _dptr(S), _dptr(cnt), ctypes.byref(L))
     return S, cnt, L.value
+
+
+def adjoint(m: Model, phi0: np.ndarray, step0: int, nsteps: int, lambda_T: np.ndarray):
+    """Return (dJ/dphi_0, grad[11]) for dJ/dphi_T = lambda_T (full spectra; see orc_adjoint):
+    grad[0:5] = dJ/dO_k, grad[5:10] = dJ/dM_k, grad[10] = dJ/dD."""
+    s = m.c_struct()
+    phi0 = np.ascontiguousarray(phi0, dtype=np.complex128)
+    lam = np.ascontiguousarray(lambda_T, dtype=np.complex128).copy()
+    g = np.zeros(11)
+    rc = lib().orc_adjoint(ctypes.byref(s), _dptr(phi0.view(np.float64)), int(step0), int(nsteps),
+                           _dptr(lam.view(np.float64)), _dptr(g))
+    if rc:
+        raise RuntimeError(f"orc_adjoint failed ({rc})")
+    return lam, g
+
+
+def binned_sq_loss(m: Model, phi: np.ndarray, target: np.ndarray, nbins: int = 64):
+    """J = mean over non-empty bins of (S_b - target_b)^2 and its gradient dJ/dphi (full spectrum)."""
+    S, cnt, _ = structure_factor(m, phi, nbins)
+    sel = cnt > 0
+    nb = int(sel.sum())
+    J = float(np.sum((S[sel] - target[sel]) ** 2) / nb)
+    coef = np.zeros(nbins)
+    coef[sel] = 2.0 / nb * (S[sel] - target[sel]) * 2.0 / (m.n_sites * cnt[sel])
+    return J, coef
+
+
+def sq_bin_index(m: Model, nbins: int = 64) -> np.ndarray:
+    """Bin of every full-spectrum mode (-1: not binned), same arithmetic as orc_structure_factor."""
+    N = list(reversed(m.shape)) + [1] * (3 - m.dim)
+    dx = list(m.dx) + [1.0] * 3
+    ks = [np.fft.fftfreq(n) * n if n > 1 else np.zeros(1) for n in N]
+    s2 = np.zeros((N[2], N[1], N[0]))
+    for j, kk in enumerate((ks[0], ks[1], ks[2])):
+        if N[j] == 1:
+            continue
+        t = (2.0 * nbins * kk * dx[0]) / (N[j] * dx[j])
+        shape = [1, 1, 1]
+        shape[2 - j] = N[j]
+        s2 = s2 + (t * t).reshape(shape)
+    s = np.sqrt(s2)
+    b = np.ceil(s).astype(int) - 1
+    b[(s2 == 0) | (s > nbins)] = -1
+    return b.reshape(m.shape)

@@ -440,3 +440,122 @@ int orc_structure_factor(const orc_field *f, const double *phi, int nbins,
     *L_out = sumQS > 0 ? 2.0 * M_PI * sumS / sumQS : 0.0;
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Adjoint of orc_run.                                                      */
+/*                                                                          */
+/* Gradients use the real inner product <a, b> = Re sum_q conj(a_q) b_q    */
+/* over the full spectrum, so that dJ = <lambda, dphi>.  One forward step   */
+/* phi' = H[g (phi + dt M P + xi)], g = 1/(1 + dt O), P = F[r^p],           */
+/* r = Re F^-1[m phi], H the Hermitian part, has the adjoint                */
+/*   mu      = g H[lambda']                                                 */
+/*   nu      = dt M mu                                                      */
+/*   s       = Re( N F^-1[nu] )          (F^dagger = N F^-1)                */
+/*   w       = p r^(p-1) s                                                  */
+/*   lambda  = mu + m F[w] / N           ((F^-1)^dagger = F / N)            */
+/* and the coefficient gradients                                            */
+/*   dJ/dO_k += -dt sum q^2k Re(conj(mu) phi')                              */
+/*   dJ/dM_k +=  dt sum q^2k Re(conj(mu) P)                                 */
+/*   dJ/dD   +=     sum      Re(conj(mu) xi) / (2 D)                        */
+/* (O and M grouped by power k of q^2; xi is proportional to sqrt(D)).      */
+/* ------------------------------------------------------------------------ */
+int orc_adjoint(const orc_field *f, const double *phi0, int64_t step0, int64_t nsteps, double *lambda,
+                double *grad)
+{
+    int N[3];
+    dims(f, N);
+    long ns = n_sites(f);
+    int method = transform_method(f);
+    size_t sz = (size_t)(2 * ns);
+    double *states = malloc(sizeof(double) * sz * (size_t)(nsteps + 1));
+    double *P = malloc(sizeof(double) * sz);
+    double *r = malloc(sizeof(double) * sz);
+    double *xi = malloc(sizeof(double) * sz);
+    double *tmp = malloc(sizeof(double) * sz);
+    if (!states || !P || !r || !xi || !tmp) {
+        free(states); free(P); free(r); free(xi); free(tmp);
+        return -2;
+    }
+    for (int k = 0; k < 11; ++k) grad[k] = 0.0;
+    /* forward pass, every state kept */
+    memcpy(states, phi0, sizeof(double) * sz);
+    for (int64_t n = 0; n < nsteps; ++n) {
+        memcpy(states + sz * (size_t)(n + 1), states + sz * (size_t)n, sizeof(double) * sz);
+        if (orc_run(f, states + sz * (size_t)(n + 1), step0 + n, 1)) goto fail;
+    }
+    /* backward pass */
+    for (int64_t n = nsteps - 1; n >= 0; --n) {
+        const double *phi = states + sz * (size_t)n;
+        const double *phin = states + sz * (size_t)(n + 1);
+        hermitian_part(f, lambda);
+        /* r = Re F^-1[m phi] and P = F[r^p] */
+        for (int kz = 0; kz < N[2]; ++kz)
+            for (int ky = 0; ky < N[1]; ++ky)
+                for (int kx = 0; kx < N[0]; ++kx) {
+                    long i = ((long)kz * N[1] + ky) * N[0] + kx;
+                    int m = orc_mask(f, kx, ky, kz);
+                    r[2 * i] = m ? phi[2 * i] : 0.0;
+                    r[2 * i + 1] = m ? phi[2 * i + 1] : 0.0;
+                }
+        if (orc_dft(f->dim, f->n, r, +1, method)) goto fail;
+        for (long i = 0; i < ns; ++i) {
+            double x = r[2 * i] / (double)ns, u = 1.0;
+            for (int p = 0; p < f->power; ++p) u *= x;
+            r[2 * i] = x;
+            r[2 * i + 1] = 0.0;
+            P[2 * i] = u;
+            P[2 * i + 1] = 0.0;
+        }
+        if (f->power > 0 && orc_dft(f->dim, f->n, P, -1, method)) goto fail;
+        orc_noise(f, step0 + n, xi);
+        /* mu, coefficient gradients, nu */
+        for (int kz = 0; kz < N[2]; ++kz)
+            for (int ky = 0; ky < N[1]; ++ky)
+                for (int kx = 0; kx < N[0]; ++kx) {
+                    long i = ((long)kz * N[1] + ky) * N[0] + kx;
+                    double q2 = orc_q2(f, kx, ky, kz);
+                    double O = poly_q2(f->n_lhs, f->lhs_coef, f->lhs_pow, q2);
+                    double M = f->power > 0 ? poly_q2(f->n_rhs, f->rhs_coef, f->rhs_pow, q2) : 0.0;
+                    double g = 1.0 / (1.0 + f->dt * O);
+                    double mr = g * lambda[2 * i], mi = g * lambda[2 * i + 1];
+                    double a_phi = mr * phin[2 * i] + mi * phin[2 * i + 1];     /* Re(conj(mu) phi') */
+                    double a_P = f->power > 0 ? mr * P[2 * i] + mi * P[2 * i + 1] : 0.0;
+                    double a_xi = mr * xi[2 * i] + mi * xi[2 * i + 1];
+                    double q2k = 1.0;
+                    for (int k = 0; k < 5; ++k) {
+                        grad[k] += -f->dt * q2k * a_phi;
+                        grad[5 + k] += f->dt * q2k * a_P;
+                        q2k *= q2;
+                    }
+                    if (f->noisy && f->noise_D > 0.0) grad[10] += a_xi / (2.0 * f->noise_D);
+                    lambda[2 * i] = mr;
+                    lambda[2 * i + 1] = mi;
+                    tmp[2 * i] = f->dt * M * mr;
+                    tmp[2 * i + 1] = f->dt * M * mi;
+                }
+        if (f->power > 0) {
+            /* s = Re(N F^-1[nu]) is the unnormalised inverse transform */
+            if (orc_dft(f->dim, f->n, tmp, +1, method)) goto fail;
+            for (long i = 0; i < ns; ++i) {
+                double rp = 1.0;
+                for (int p = 0; p < f->power - 1; ++p) rp *= r[2 * i];
+                tmp[2 * i] = (double)f->power * rp * tmp[2 * i];
+                tmp[2 * i + 1] = 0.0;
+            }
+            if (orc_dft(f->dim, f->n, tmp, -1, method)) goto fail;
+            for (int kz = 0; kz < N[2]; ++kz)
+                for (int ky = 0; ky < N[1]; ++ky)
+                    for (int kx = 0; kx < N[0]; ++kx) {
+                        long i = ((long)kz * N[1] + ky) * N[0] + kx;
+                        if (!orc_mask(f, kx, ky, kz)) continue;
+                        lambda[2 * i] += tmp[2 * i] / (double)ns;
+                        lambda[2 * i + 1] += tmp[2 * i + 1] / (double)ns;
+                    }
+        }
+    }
+    free(states); free(P); free(r); free(xi); free(tmp);
+    return 0;
+fail:
+    free(states); free(P); free(r); free(xi); free(tmp);
+    return -1;
+}

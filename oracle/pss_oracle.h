@@ -85,4 +85,12 @@ int orc_init_uniform(const orc_field *f, double lo, double hi, double *phi_real)
 int orc_structure_factor(const orc_field *f, const double *phi, int nbins,
                          double *S_out, double *count_out, double *L_out);
 
+/* Adjoint of orc_run(f, phi, step0, nsteps) at phi0 (full spectrum).  On entry
+ * lambda holds dJ/dphi_T, on exit dJ/dphi_0, both for the inner product
+ * <a, b> = Re sum conj(a) b over the full spectrum.  grad[0..4] receives
+ * dJ/dO_k (the implicit coefficient of (q^2)^k), grad[5..9] dJ/dM_k, grad[10]
+ * dJ/dD.  Keeps every intermediate state (nsteps + 1 spectra). */
+int orc_adjoint(const orc_field *f, const double *phi0, int64_t step0, int64_t nsteps, double *lambda,
+                double *grad);
+
 #endif
