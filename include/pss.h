@@ -139,6 +139,23 @@ int pss_step(pss_system *s, int64_t n);
  * stream (the other systems are moved to that stream).  Errors are reported
  * on systems[0]. */
 int pss_step_many(pss_system **systems, int n, int64_t steps);
+/* Gradients by the hand-written adjoint of the step (single field, batch 1).
+ * Inner product: dJ = Re sum_q conj(lambda_q) dphi_q over the full spectrum,
+ * both lambda and phi given as half spectra (the other half follows from
+ * Hermitian symmetry).  The noise realisation is the one of the forward run.
+ * pss_adjoint_forward: advance n >= 1 steps from the current state, keeping
+ *   a checkpoint every ceil(sqrt(n)) steps on the device.
+ * pss_adjoint_backward: lambda_T = dJ/dphi_T (half spectrum) of a loss of the
+ *   state after that run; returns dJ/dparams[i] for every named parameter
+ *   (operator coefficients and the noise strength; parameters not used by
+ *   the field read 0) and, if lambda_0 != NULL, dJ/dphi_0 (half spectrum).
+ *   Recomputes each segment forward from its checkpoint; accumulates the
+ *   parameter gradients in FP64.  Leaves the state and step counter as after
+ *   the forward run.  Synchronises. */
+int pss_adjoint_forward(pss_system *s, int64_t n);
+int pss_adjoint_backward(pss_system *s, const void *lambda_T, int where, double *dJ_dparams,
+                         void *lambda_0, int where0);
+
 /* Measurement: take n >= 1 steps like pss_step, but launch every kernel on
  * its own with a CUDA event pair around it, and return in avg_ms[0..3] the
  * mean duration (milliseconds) of each kind of launch of a step:

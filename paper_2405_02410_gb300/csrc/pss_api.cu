@@ -83,6 +83,14 @@ struct pss_system {
     int tune_pdl = 0, tune_row_pairs = 0, tune_col_tiles = 0, tune_graph_steps = 0, tune_mid_planes = 0;
     int64_t launches = 0;
     std::string err;
+    // adjoint: checkpoints of the last pss_adjoint_forward run
+    void *L = nullptr;                       // adjoint state lambda / mu (tiled, one slot)
+    void *ck = nullptr;                      // checkpoints [nck + 1][slot]
+    void *seg = nullptr;                     // recomputed states of one segment [K + 1][slot]
+    void *real_r = nullptr, *real_s = nullptr;
+    double *d_grad = nullptr;                // [11]
+    int64_t adj_n = 0, adj_step0 = 0, adj_K = 0, adj_nck = 0;
+    bool adj_ready = false;
 
     int nslots() const { return batch * (int)fields.size(); }
 };
@@ -269,12 +277,20 @@ template <typename T> struct Seq {
     cplx<T> *B() const { return (cplx<T> *)s->B; }
 
     int col(int mode, bool in_is_B, bool out_is_A) {
+        return col_ptrs(mode, state(), in_is_B ? B() : A(), out_is_A ? A() : B(), nullptr, 0);
+    }
+
+    int col_ptrs(int mode, cplx<T> *st_ptr, const cplx<T> *in_ptr, cplx<T> *out_ptr, const cplx<T> *aux,
+                 long long adj_step) {
         ColArgs<T> a{};
         a.sp = sys_params<T>(s);
         a.fps = (const FieldP<T> *)s->fps;
-        a.in = in_is_B ? B() : A();
-        a.out = out_is_A ? A() : B();
-        a.state = state();
+        a.in = in_ptr;
+        a.out = out_ptr;
+        a.state = st_ptr;
+        a.aux = aux;
+        a.adj_step = adj_step;
+        a.grad = s->d_grad;
         a.slot_stride = s->field_elems;
         a.slot0 = slot0;
         a.tw = (const cplx<T> *)s->tw;
@@ -388,6 +404,47 @@ template <typename T> struct Seq {
             return row(ROW_C2R, false, false, false, s->real, 0);                 // B -> real
         }
         return row(ROW_C2R, true, false, false, s->real, 0);                      // A -> real
+    }
+
+    // One adjoint step for the forward step phi_n -> phi_n1 (noise step n_step),
+    // with the state array holding phi_n and s->L holding lambda_{n+1} on entry,
+    // lambda_n on exit (see the adjoint recursion in COL_ADJ_A / COL_ADJ_B).
+    int adjoint_step(const cplx<T> *phi_n1, long long n_step, int power) {
+        int rc;
+        T *rr = (T *)s->real_r, *rs = (T *)s->real_s;
+        cplx<T> *Lb = (cplx<T> *)s->L;
+        // r = F^-1[m phi_n] (real) and B = the x(y)-transformed product r^p
+        if ((rc = col(COL_INV_MASK, false, true))) return rc;                      // state -> A
+        if (s->dim == 3) {
+            if ((rc = mid(MID_INV_MASK, true, false))) return rc;                  // A -> B
+            if ((rc = row(ROW_C2R_KEPT, false, false, false, rr, 0))) return rc;   // B -> r
+            if ((rc = row(ROW_FUSED, false, false, false, nullptr, 0))) return rc; // B -> A
+            if ((rc = mid(MID_FWD, true, false))) return rc;                       // A -> B
+        } else {
+            if ((rc = row(ROW_C2R_KEPT, true, false, false, rr, 0))) return rc;    // A -> r
+            if ((rc = row(ROW_FUSED, true, true, false, nullptr, 0))) return rc;   // A -> B
+        }
+        // mu = g lambda, gradients, nu = dt M mu back along the slowest axis -> A
+        if ((rc = col_ptrs(COL_ADJ_A, Lb, B(), A(), phi_n1, n_step))) return rc;
+        // s = N F^-1[nu] (real)
+        if (s->dim == 3) {
+            if ((rc = mid(MID_INV_FULL, true, false))) return rc;                  // A -> B
+            if ((rc = row(ROW_C2R, false, false, false, rs, 0))) return rc;        // B -> s
+        } else {
+            if ((rc = row(ROW_C2R, true, false, false, rs, 0))) return rc;         // A -> s
+        }
+        // w = p r^(p-1) s, then its x(y) transform -> B
+        cudaError_t e = launch_adj_pointwise<T>(rr, rs, s->nsites, power, 1, st);
+        s->launches++;
+        if (e != cudaSuccess) return cuda_fail(s, e, "adjoint point-wise kernel");
+        if (s->dim == 3) {
+            if ((rc = row(ROW_R2C, true, false, false, rs, 0))) return rc;         // w -> A
+            if ((rc = mid(MID_FWD, true, false))) return rc;                       // A -> B
+        } else {
+            if ((rc = row(ROW_R2C, true, true, false, rs, 0))) return rc;          // w -> B
+        }
+        // lambda_n = mu + m F[w] / N
+        return col_ptrs(COL_ADJ_B, Lb, B(), A(), nullptr, n_step);
     }
 };
 
@@ -619,6 +676,56 @@ int forward_field(pss_system *s, int field_id) {
     return rc;
 }
 
+int adj_alloc(pss_system *s, int64_t nck, int64_t K) {
+    const size_t slot_bytes = csize(s) * s->field_elems;
+    cudaFree(s->ck);
+    cudaFree(s->seg);
+    s->ck = s->seg = nullptr;
+    CK(cudaMalloc(&s->ck, slot_bytes * (size_t)(nck + 1)));
+    CK(cudaMalloc(&s->seg, slot_bytes * (size_t)(K + 1)));
+    if (!s->L) CK(cudaMalloc(&s->L, slot_bytes));
+    if (!s->real_r) CK(cudaMalloc(&s->real_r, rsize(s) * (size_t)s->nsites));
+    if (!s->real_s) CK(cudaMalloc(&s->real_s, rsize(s) * (size_t)s->nsites));
+    if (!s->d_grad) CK(cudaMalloc(&s->d_grad, sizeof(double) * 11));
+    return PSS_OK;
+}
+
+int copy_slot(pss_system *s, void *dst, const void *src) {
+    CK(cudaMemcpyAsync(dst, src, csize(s) * s->field_elems, cudaMemcpyDeviceToDevice, s->stream));
+    return PSS_OK;
+}
+
+void *slot_ptr(const pss_system *s, void *base, int64_t i) { return (char *)base + csize(s) * s->field_elems * i; }
+
+template <typename T> int adjoint_backward_t(pss_system *s) {
+    Seq<T> q{s, s->stream, 0, 1};
+    const int power = s->fields[0].power;
+    for (int64_t j = s->adj_nck - 1; j >= 0; --j) {
+        const int64_t t0 = j * s->adj_K;
+        const int64_t len = std::min<int64_t>(s->adj_K, s->adj_n - t0);
+        // recompute the segment's states from its checkpoint
+        int rc = copy_slot(s, s->state, slot_ptr(s, s->ck, j));
+        if (rc) return rc;
+        long long st = s->adj_step0 + t0;
+        CK(cudaMemcpyAsync(s->d_step, &st, sizeof st, cudaMemcpyHostToDevice, s->stream));
+        CK(cudaStreamSynchronize(s->stream));
+        s->stale = true;
+        if ((rc = copy_slot(s, slot_ptr(s, s->seg, 0), s->state))) return rc;
+        for (int64_t i = 1; i <= len; ++i) {
+            if ((rc = prologue(s))) return rc;
+            if ((rc = q.one_step())) return rc;
+            if ((rc = copy_slot(s, slot_ptr(s, s->seg, i), s->state))) return rc;
+        }
+        // adjoint steps of the segment, last first
+        for (int64_t i = len - 1; i >= 0; --i) {
+            if ((rc = copy_slot(s, s->state, slot_ptr(s, s->seg, i)))) return rc;
+            rc = q.adjoint_step((const cplx<T> *)slot_ptr(s, s->seg, i + 1), (long long)(s->adj_step0 + t0 + i), power);
+            if (rc) return rc;
+        }
+    }
+    return PSS_OK;
+}
+
 }  // namespace
 
 // ==========================================================================
@@ -649,6 +756,12 @@ int pss_destroy_system(pss_system *s) {
     cudaFree(s->sq);
     cudaFree(s->d_step);
     cudaFree(s->d_status);
+    cudaFree(s->L);
+    cudaFree(s->ck);
+    cudaFree(s->seg);
+    cudaFree(s->real_r);
+    cudaFree(s->real_s);
+    cudaFree(s->d_grad);
     if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
     delete s;
     return PSS_OK;
@@ -866,6 +979,82 @@ int pss_step_many(pss_system **systems, int n, int64_t steps) {
             if (rc) return i == 0 ? rc : fail(s0, rc, "%s", systems[i]->err.c_str());
         }
     for (int i = 0; i < n; ++i) systems[i]->step += steps;
+    return PSS_OK;
+}
+
+int pss_adjoint_forward(pss_system *s, int64_t n) {
+    if (!s) return PSS_EINVAL;
+    if (n < 1) return fail(s, PSS_EINVAL, "n must be >= 1");
+    if (s->nslots() != 1) return fail(s, PSS_EUNSUPPORTED, "the adjoint needs one field and batch 1 in this build");
+    int64_t K = (int64_t)std::ceil(std::sqrt((double)n));
+    const int64_t nck = (n + K - 1) / K;
+    int rc = adj_alloc(s, nck, K);
+    if (rc) return rc;
+    s->adj_ready = false;
+    s->adj_n = n;
+    s->adj_step0 = s->step;
+    s->adj_K = K;
+    s->adj_nck = nck;
+    for (int64_t j = 0; j < nck; ++j) {
+        if ((rc = copy_slot(s, slot_ptr(s, s->ck, j), s->state))) return rc;
+        if ((rc = pss_step(s, std::min<int64_t>(K, n - j * K)))) return rc;
+    }
+    if ((rc = copy_slot(s, slot_ptr(s, s->ck, nck), s->state))) return rc;
+    s->adj_ready = true;
+    return PSS_OK;
+}
+
+int pss_adjoint_backward(pss_system *s, const void *lambda_T, int where, double *dJ_dparams, void *lambda_0,
+                         int where0) {
+    if (!s || !lambda_T) return PSS_EINVAL;
+    if (!s->adj_ready) return fail(s, PSS_EINVAL, "call pss_adjoint_forward first");
+    int rc = upload_params(s);
+    if (rc) return rc;
+    // lambda_T (half spectrum) -> L (tiles)
+    if ((rc = ensure_half(s))) return rc;
+    const size_t hbytes = csize(s) * (size_t)s->hx * s->ny * s->nz;
+    CK(cudaMemcpyAsync(s->half, lambda_T, hbytes, where == PSS_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                       s->stream));
+    CK(cudaMemsetAsync(s->L, 0, csize(s) * s->field_elems, s->stream));
+    cudaError_t e = s->prec == PSS_F64
+        ? launch_half_to_tiles<double>(sys_params<double>(s), (const double2 *)s->half, (double2 *)s->L, s->stream)
+        : launch_half_to_tiles<float>(sys_params<float>(s), (const float2 *)s->half, (float2 *)s->L, s->stream);
+    s->launches++;
+    if (e != cudaSuccess) return cuda_fail(s, e, "layout kernel");
+    CK(cudaMemsetAsync(s->d_grad, 0, sizeof(double) * 11, s->stream));
+    rc = s->prec == PSS_F64 ? adjoint_backward_t<double>(s) : adjoint_backward_t<float>(s);
+    if (rc) return rc;
+    // gradients of the named parameters
+    double g[11];
+    CK(cudaMemcpyAsync(g, s->d_grad, sizeof g, cudaMemcpyDeviceToHost, s->stream));
+    if (lambda_0) {
+        e = s->prec == PSS_F64
+            ? launch_tiles_to_half<double>(sys_params<double>(s), (const double2 *)s->L, (double2 *)s->half, s->stream)
+            : launch_tiles_to_half<float>(sys_params<float>(s), (const float2 *)s->L, (float2 *)s->half, s->stream);
+        s->launches++;
+        if (e != cudaSuccess) return cuda_fail(s, e, "layout kernel");
+        CK(cudaMemcpyAsync(lambda_0, s->half, hbytes, where0 == PSS_HOST ? cudaMemcpyDeviceToHost
+                                                                          : cudaMemcpyDeviceToDevice, s->stream));
+    }
+    // back to the state after the forward run
+    if ((rc = copy_slot(s, s->state, slot_ptr(s, s->ck, s->adj_nck)))) return rc;
+    long long st = s->adj_step0 + s->adj_n;
+    CK(cudaMemcpyAsync(s->d_step, &st, sizeof st, cudaMemcpyHostToDevice, s->stream));
+    s->step = st;
+    s->stale = true;
+    if ((rc = device_errors(s))) return rc;
+    if (dJ_dparams) {
+        const Field &f = s->fields[0];
+        for (size_t i = 0; i < s->param_names.size(); ++i) dJ_dparams[i] = 0.0;
+        for (const Mono &m : f.lhs)
+            if (m.param >= 0) dJ_dparams[m.param] += m.scale * g[m.pow];
+        for (const Mono &m : f.rhs)
+            if (m.param >= 0) dJ_dparams[m.param] += m.scale * g[5 + m.pow];
+        if (f.noisy && f.noise_param >= 0) {
+            const double D = pval(s, 0, f.noise_param);
+            if (D > 0) dJ_dparams[f.noise_param] += g[10] / (2.0 * D);
+        }
+    }
     return PSS_OK;
 }
 

@@ -50,8 +50,12 @@ template <typename T> struct SysP {
     int pdl;              // launch with programmatic stream serialisation
 };
 
-enum ColMode { COL_STEP = 0, COL_FWD = 1, COL_INV_MASK = 2, COL_INV_FULL = 3 };
-enum RowMode { ROW_FUSED = 0, ROW_R2C = 1, ROW_C2R = 2 };
+enum ColMode {
+    COL_STEP = 0, COL_FWD = 1, COL_INV_MASK = 2, COL_INV_FULL = 3,
+    COL_ADJ_A = 4,   // adjoint: mu = g lambda, coefficient gradients, inverse of nu = dt M mu (all columns)
+    COL_ADJ_B = 5    // adjoint: lambda = mu + m F[w] / N
+};
+enum RowMode { ROW_FUSED = 0, ROW_R2C = 1, ROW_C2R = 2, ROW_C2R_KEPT = 3 /* C2R of the kept columns only */ };
 enum MidMode { MID_INV_MASK = 0, MID_INV_FULL = 1, MID_FWD = 2 };
 
 // Arrays: slot s of an array starts at base + s * slot_stride (complex
@@ -70,6 +74,11 @@ template <typename T> struct ColArgs {
     int *d_status;
     int mode, tiles_per_cta, n_tiles;
     int F;                // FFTs per CTA = tiles_per_cta * kTileW * (2 in 3D, else 1); a power of two
+    // adjoint (COL_ADJ_A): the forward state after the step, its noise step, and
+    // the FP64 gradient sums [slot][11] (dO_0..4, dM_0..4, sum Re(conj(mu) xi))
+    const cplx<T> *aux;
+    long long adj_step;
+    double *grad;
 };
 
 template <typename T> struct RowArgs {
@@ -115,6 +124,8 @@ template <typename T> cudaError_t launch_tiles_to_half(const SysP<T> &sp, const 
                                                        cplx<T> *half, cudaStream_t st);
 template <typename T> cudaError_t launch_half_to_tiles(const SysP<T> &sp, const cplx<T> *half,
                                                        cplx<T> *tiles, cudaStream_t st);
+template <typename T> cudaError_t launch_adj_pointwise(const T *r, T *s, long long n, int power, int mode,
+                                                       cudaStream_t st);
 template <typename T> cudaError_t launch_structure_factor(const SysP<T> &sp, const double dx[3],
                                                           const cplx<T> *tiles, int nbins,
                                                           double *acc /* 2*nbins + 2 */, cudaStream_t st);

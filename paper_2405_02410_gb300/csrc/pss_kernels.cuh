@@ -100,6 +100,150 @@ __device__ __forceinline__ cplx<T> update_mode(cplx<T> phi, cplx<T> P, cplx<T> x
 // chunk stride of N W + 8), X (staged product chunks, then a work buffer),
 // Y (work buffer).
 // ---------------------------------------------------------------------------
+// ---------------------------------------------------------------------------
+// Adjoint of one step, column part (after the forward transform P of the
+// kernel's X input along this axis):
+//   COL_ADJ_A: PHI = lambda', P = F[r^p] of the step, aux = phi' (global):
+//       mu = g lambda' (stored back), gradient sums of the implicit / explicit
+//       coefficients and of the noise, and nu = dt M mu transformed back along
+//       this axis (all columns, unscaled) -> out.
+//   COL_ADJ_B: PHI = mu, P = F[w]: lambda = mu + m F[w] / N (stored back),
+//       Hermitian part on the kx = 0, Nx/2 planes.
+// Inner products run over the full Hermitian set: weight 2 for 0 < kx < Nx/2.
+// ---------------------------------------------------------------------------
+template <typename T, int N>
+__device__ __forceinline__ void col_adjoint(const ColArgs<T> &a, const FieldP<T> &fp, cplx<T> *PHI, const cplx<T> *P,
+                                            cplx<T> *X, cplx<T> *Y, int which, int F, int SF, int nchunks,
+                                            int lognch, int first_tile, int op, int opp, int logNP, size_t sofs,
+                                            int ch, int c, int f, int lane, bool active) {
+    using C = cplx<T>;
+    constexpr int CS = N * W + 8;
+    const SysP<T> &sp = a.sp;
+    const int t = threadIdx.x, nthr = blockDim.x;
+    const bool mode_a = a.mode == COL_ADJ_A;
+    auto chunk_tile = [&](int q) { return first_tile + (q >> logNP); };
+    auto chunk_o = [&](int q) { return (q & logNP) ? opp : op; };
+    auto chunk_writes = [&](int q) { return chunk_tile(q) < a.n_tiles && !((q & logNP) && opp == op); };
+    auto gofs = [&](int q) { return ((size_t)(chunk_tile(q) * sp.n_outer + chunk_o(q)) * N) * W; };
+    // ADJ_A writes nu into the work buffer that does not hold P
+    C *NU = which == 0 ? X : Y;
+    double acc[11];
+#pragma unroll
+    for (int i = 0; i < 11; ++i) acc[i] = 0.0;
+    const uint32_t step = (uint32_t)a.adj_step;
+#pragma unroll 1
+    for (int i = t; i < N * F; i += nthr) {
+        const int pos = i >> (__ffs(F) - 1), ff = i & (F - 1);
+        const int chq = ff >> 2, cc = ff & 3;
+        const int tile = chunk_tile(chq);
+        const int kx = tile * W + cc;
+        const int o = chunk_o(chq);
+        const int ky = sp.dim == 3 ? o : (sp.dim == 2 ? pos : 0);
+        const int kz = sp.dim == 3 ? pos : 0;
+        const bool valid = tile < a.n_tiles && kx < sp.hx;
+        const T qx = T(kx) * sp.gx, qy = T(signed_k(ky, sp.ny)) * sp.gy, qz = T(signed_k(kz, sp.nz)) * sp.gz;
+        const T q2 = qx * qx + qy * qy + qz * qz;
+        C *ph = &PHI[chq * CS + pos * W + cc];
+        const C pv = P[ff * SF + spad(pos)];
+        if (mode_a) {
+            const T g = T(1) / (T(1) + sp.dt * poly5<T>(fp.O, q2));
+            const C mu = valid ? cscale<T>(*ph, g) : mk<T>(0, 0);
+            *ph = mu;
+            const T dtM = fp.power > 0 ? sp.dt * poly5<T>(fp.M, q2) : T(0);
+            NU[ff * SF + spad(pos)] = cscale<T>(mu, dtM);
+            // the duplicate pencil of a self-paired 3D CTA does not count twice
+            if (valid && chunk_writes(chq)) {
+                const double wgt = (kx == 0 || 2 * kx == sp.nx) ? 1.0 : 2.0;
+                const C phin = a.aux[sofs + gofs(chq) + pos * W + cc];
+                const double a_phi = wgt * ((double)mu.x * phin.x + (double)mu.y * phin.y);
+                const double a_P = wgt * ((double)mu.x * pv.x + (double)mu.y * pv.y);
+                double q2k = 1.0;
+#pragma unroll
+                for (int k = 0; k < 5; ++k) {
+                    acc[k] += -(double)sp.dt * q2k * a_phi;
+                    acc[5 + k] += (double)sp.dt * q2k * a_P;
+                    q2k *= (double)q2;
+                }
+                if (fp.noisy) {
+                    // the noise of this mode (one draw per pair of kx columns; use the even member's)
+                    const int kx0 = kx & ~1;
+                    const T qe = T(kx0) * sp.gx, qo = T(kx0 + 1) * sp.gx;
+                    const T q2e = qe * qe + qy * qy + qz * qz, q2o = qo * qo + qy * qy + qz * qz;
+                    C xi0 = mk<T>(0, 0), xi1 = mk<T>(0, 0);
+                    noise_pair<T>(kx0 == 0 || 2 * kx0 == sp.nx, kx0, ky, kz, noise_amp<T>(fp.sigma0, fp.noise_pow, q2e),
+                                  noise_amp<T>(fp.sigma0, fp.noise_pow, q2o), kx0 + 1 < sp.hx, sp,
+                                  (uint32_t)fp.field_id, fp.seed_lo, fp.seed_hi, step, xi0, xi1);
+                    const C xi = (kx & 1) ? xi1 : xi0;
+                    acc[10] += wgt * ((double)mu.x * xi.x + (double)mu.y * xi.y);
+                }
+            }
+        } else {
+            bool keep = valid && kx <= fp.kmax[0] && abs(signed_k(ky, sp.ny)) <= fp.kmax[1] &&
+                        abs(signed_k(kz, sp.nz)) <= fp.kmax[2];
+            const C mu = *ph;
+            *ph = keep ? mk<T>(mu.x + pv.x * sp.inv_nsites, mu.y + pv.y * sp.inv_nsites) : (valid ? mu : mk<T>(0, 0));
+        }
+    }
+    __syncthreads();
+    if (mode_a) {
+        // CTA reduction of the gradient sums, one FP64 atomic per value
+        __shared__ double red[11];
+        if (t < 11) red[t] = 0.0;
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < 11; ++k) {
+            double v = acc[k];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if ((t & 31) == 0 && v != 0.0) atomicAdd(&red[k], v);
+        }
+        __syncthreads();
+        if (t < 11 && red[t] != 0.0) atomicAdd(&a.grad[(size_t)(a.slot0 + blockIdx.z) * 11 + t], red[t]);
+    } else {
+        // Hermitian part of lambda on the kx = 0, Nx/2 planes
+        const int last_tile = first_tile + a.tiles_per_cta;
+        if (first_tile == 0 || (first_tile * W <= sp.nx / 2 && sp.nx / 2 < last_tile * W)) {
+#pragma unroll 1
+            for (int i = t; i < N * F; i += nthr) {
+                const int pos = i >> (__ffs(F) - 1), ff = i & (F - 1);
+                const int cq = ff >> 2, cc = ff & 3;
+                const int kq = chunk_tile(cq) * W + cc;
+                if (!(kq == 0 || 2 * kq == sp.nx) || (cq & logNP) != 0) continue;
+                const int ppos = (N - pos) & (N - 1);
+                if (logNP == 0 && ppos < pos) continue;
+                C *p0 = &PHI[cq * CS + pos * W + cc];
+                C *p1 = &PHI[(cq + logNP) * CS + ppos * W + cc];
+                const C u0 = *p0, u1 = *p1;
+                const C h = mk<T>(T(0.5) * (u0.x + u1.x), T(0.5) * (u0.y - u1.y));
+                *p0 = h;
+                *p1 = mk<T>(h.x, -h.y);
+            }
+            __syncthreads();
+        }
+    }
+    // store PHI (mu or lambda) back with one bulk copy per chunk
+    fence_proxy_async();
+    __syncthreads();
+    const uint32_t chunk_bytes = (uint32_t)(N * W * sizeof(C));
+    if (t == 0) {
+        for (int q = 0; q < nchunks; ++q)
+            if (chunk_writes(q)) bulk_s2g(a.state + sofs + gofs(q), PHI + q * CS, chunk_bytes);
+        bulk_commit();
+    }
+    if (mode_a) {
+        // nu back along this axis (all columns), stored straight from the last pass
+        C *__restrict__ dst = a.out + sofs + gofs(ch) + c;
+        const bool writes = chunk_writes(ch);
+        C *nb = NU + f * SF;
+        C *other = (NU == X ? Y : X) + f * SF;
+        fft_run<T, N, +1>([&](int p) { return nb[spad(p)]; },
+                          [&](int p, C v, C *) {
+                              if (writes) dst[p * W] = v;
+                          },
+                          other, nb, lane, active, a.tw);
+    }
+    if (t == 0) bulk_wait_read();
+}
+
 template <typename T, int N> struct ColSmem {
     static constexpr int CS = N * W + 8;                         // chunk stride (elements)
     __host__ __device__ static int xs(int F) {                   // X / Y size (elements)
@@ -111,8 +255,8 @@ template <typename T, int N> struct ColSmem {
     }
 };
 
-template <typename T, int N>
-__global__ void __launch_bounds__(512) k_col(const ColArgs<T> a) {
+template <typename T, int N, bool ADJ>
+__global__ void __launch_bounds__(512, N >= 512 ? 1 : 2) k_col(const ColArgs<T> a) {
     using C = cplx<T>;
     using L = ColSmem<T, N>;
     constexpr int TPF = FftShape<N>::TPF;
@@ -146,7 +290,8 @@ __global__ void __launch_bounds__(512) k_col(const ColArgs<T> a) {
     auto gofs = [&](int ch) { return ((size_t)(chunk_tile(ch) * sp.n_outer + chunk_o(ch)) * N) * W; };
 
     // ---- stage: state chunks -> PHI (not for COL_FWD), product chunks -> X (COL_STEP, COL_FWD)
-    const bool need_in = mode == COL_STEP || mode == COL_FWD;
+    constexpr bool adj = ADJ;   // the adjoint modes are a separate instantiation
+    const bool need_in = mode == COL_STEP || mode == COL_FWD || adj;
     const bool need_phi = mode != COL_FWD;
     const uint32_t chunk_bytes = (uint32_t)(N * W * sizeof(C));
     int nvalid = 0;                                              // chunks 0..nvalid-1 lie inside the grid
@@ -184,6 +329,11 @@ __global__ void __launch_bounds__(512) k_col(const ColArgs<T> a) {
                                             Y + f * SF, X + f * SF, lane, active, tw);
         __syncthreads();
         const C *P = which == 0 ? Y : X;
+        if constexpr (ADJ) {
+            col_adjoint<T, N>(a, fp, PHI, P, X, Y, which, F, SF, nchunks, lognch, first_tile, op, opp, logNP, sofs,
+                              ch, c, f, lane, active);
+            return;
+        }
         const uint32_t step = (uint32_t)(*a.d_step);
         // update: each thread keeps one pair of neighbouring columns (they share
         // one Philox draw) of one chunk and walks the positions
@@ -375,7 +525,7 @@ __global__ void __launch_bounds__(256) k_row(const RowArgs<T> a) {
         for (int i = nrow * N + t; i < G2 * N; i += nthr) Sr[i] = T(0);
     } else {
         const C *__restrict__ src = a.in + sofs;
-        const int kxc_in = mode == ROW_FUSED ? fp.kx_cols : sp.hx;
+        const int kxc_in = (mode == ROW_FUSED || mode == ROW_C2R_KEPT) ? fp.kx_cols : sp.hx;
         const int ntl = (kxc_in + W - 1) / W;
         const uint32_t seg = (uint32_t)(nrow * W * sizeof(C));
         if (t == 0) {
@@ -402,7 +552,7 @@ __global__ void __launch_bounds__(256) k_row(const RowArgs<T> a) {
                                             smem_sink, b0, b1, lane, active, tw);
         R = which == 0 ? B0 : B1;
     } else {
-        const int kxc = mode == ROW_FUSED ? fp.kx_cols : sp.hx;
+        const int kxc = (mode == ROW_FUSED || mode == ROW_C2R_KEPT) ? fp.kx_cols : sp.hx;
         const int which = fft_run<T, N, +1>(
             [&](int k) {
                 const int kk = k <= N / 2 ? k : N - k;
@@ -419,7 +569,7 @@ __global__ void __launch_bounds__(256) k_row(const RowArgs<T> a) {
             smem_sink, b0, b1, lane, active, tw);
         __syncthreads();
         C *Z = which == 0 ? B0 : B1;
-        if (mode == ROW_C2R) {
+        if (mode == ROW_C2R || mode == ROW_C2R_KEPT) {
             T *__restrict__ dst = a.real_out + (size_t)slot * a.real_stride;
 #pragma unroll 1
             for (int i = t; i < nrow * N; i += nthr) {
@@ -556,6 +706,22 @@ __global__ void k_tiles_half(SysP<T> sp, cplx<T> *tiles, cplx<T> *half, int to_h
     }
 }
 
+// adjoint point-wise factors in real space: mode 0: s <- r^p, mode 1: s <- p r^(p-1) s
+template <typename T> __global__ void k_adj_pointwise(const T *r, T *s, long long n, int power, int mode) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const T x = r[i];
+        if (mode == 0) s[i] = ipow<T>(x, power);
+        else s[i] = T(power) * ipow<T>(x, power - 1) * s[i];
+    }
+}
+
+template <typename T> cudaError_t launch_adj_pointwise(const T *r, T *s, long long n, int power, int mode, cudaStream_t st) {
+    long long blocks = (n + 255) / 256;
+    if (blocks > 65535) blocks = 65535;
+    k_adj_pointwise<T><<<(int)blocks, 256, 0, st>>>(r, s, n, power, mode);
+    return cudaGetLastError();
+}
+
 // S(q) accumulation: acc[0..nbins) sum S, acc[nbins..2nbins) counts,
 // acc[2nbins] sum S, acc[2nbins+1] sum |q| S.  Bin arithmetic in FP64 with
 // explicit round-to-nearest operations (no contraction).
@@ -635,9 +801,11 @@ template <typename T, int N> cudaError_t launch_col_n(const ColArgs<T> &a, int n
     const int threads = 2 * a.F * FftShape<N>::TPF < 32 ? 32 : 2 * a.F * FftShape<N>::TPF;
     const size_t smem = ColSmem<T, N>::bytes(a.F);
     if (threads > 512 || (a.F & (a.F - 1)) != 0 || a.F % W != 0) return cudaErrorInvalidConfiguration;
-    cudaError_t e = ensure_smem(k_col<T, N>, smem);
+    const bool adj = a.mode == COL_ADJ_A || a.mode == COL_ADJ_B;
+    cudaError_t e = adj ? ensure_smem(k_col<T, N, true>, smem) : ensure_smem(k_col<T, N, false>, smem);
     if (e != cudaSuccess) return e;
-    return launch_pdl(k_col<T, N>, dim3(gx, gy, nf), threads, smem, st, a);
+    if (adj) return launch_pdl(k_col<T, N, true>, dim3(gx, gy, nf), threads, smem, st, a);
+    return launch_pdl(k_col<T, N, false>, dim3(gx, gy, nf), threads, smem, st, a);
 }
 
 template <typename T> cudaError_t launch_col(const ColArgs<T> &a, int nf, int gx, int gy, cudaStream_t st) {
@@ -754,6 +922,7 @@ cudaError_t launch_structure_factor(const SysP<T> &sp, const double dx[3], const
     template cudaError_t launch_init_uniform<T>(T *, long long, double, double, uint64_t, int, cudaStream_t); \
     template cudaError_t launch_tiles_to_half<T>(const SysP<T> &, const cplx<T> *, cplx<T> *, cudaStream_t); \
     template cudaError_t launch_half_to_tiles<T>(const SysP<T> &, const cplx<T> *, cplx<T> *, cudaStream_t); \
+    template cudaError_t launch_adj_pointwise<T>(const T *, T *, long long, int, int, cudaStream_t);        \
     template cudaError_t launch_structure_factor<T>(const SysP<T> &, const double *, const cplx<T> *, int,   \
                                                     double *, cudaStream_t);
 

@@ -27,7 +27,7 @@ EXPORTS = [
     "pss_init_uniform", "pss_step", "pss_get_step", "pss_set_step", "pss_get_field", "pss_get_spectrum",
     "pss_set_spectrum", "pss_structure_factor", "pss_sync", "pss_last_error", "pss_launch_count",
     "pss_time_kernels", "pss_set_tuning", "pss_create_batch", "pss_batch_size", "pss_select_instance",
-    "pss_set_param_batch", "pss_step_many",
+    "pss_set_param_batch", "pss_step_many", "pss_adjoint_forward", "pss_adjoint_backward",
 ]
 
 
@@ -73,6 +73,8 @@ def _load():
         "pss_select_instance": ([vp, i32], i32),
         "pss_set_param_batch": ([vp, i32, P(d)], i32),
         "pss_step_many": ([P(vp), i32, i64], i32),
+        "pss_adjoint_forward": ([vp, i64], i32),
+        "pss_adjoint_backward": ([vp, vp, i32, P(d), vp, i32], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -249,6 +251,20 @@ class System:
     def set_tuning(self, key: str, value: int):
         """Launch-shape knob ("pdl", "row_pairs", "col_tiles", "mid_planes", "graph_steps"); 0 = automatic."""
         self._ck(lib.pss_set_tuning(self._h, key.encode(), int(value)))
+
+    def adjoint_forward(self, n: int):
+        """Advance n steps keeping sqrt(n)-spaced checkpoints for adjoint_backward."""
+        self._ck(lib.pss_adjoint_forward(self._h, int(n)))
+
+    def adjoint_backward(self, lambda_T, n_params: int):
+        """dJ/dphi_T (half spectrum, numpy) -> (dJ/dparams[n_params], dJ/dphi_0 half spectrum)."""
+        lam = np.ascontiguousarray(lambda_T, dtype=self.cdtype).reshape(self.half_shape)
+        out = np.empty(self.half_shape, dtype=self.cdtype)
+        g = np.zeros(max(1, n_params))
+        self._ck(lib.pss_adjoint_backward(self._h, lam.ctypes.data_as(ctypes.c_void_p), PSS_HOST,
+                                          g.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                          out.ctypes.data_as(ctypes.c_void_p), PSS_HOST))
+        return g[:n_params], out
 
     def sync(self):
         self._ck(lib.pss_sync(self._h))

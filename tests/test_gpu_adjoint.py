@@ -1,0 +1,109 @@
+"""The GPU adjoint (pss_adjoint_forward / pss_adjoint_backward) against the FP64
+oracle adjoint and against finite differences of the GPU's own forward map."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from tests import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_2405_02410_gb300 import build
+    build.build()
+
+
+def pss():
+    from paper_2405_02410_gb300 import pss as m
+    return m
+
+
+def rel(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(np.asarray(b)), 1e-300)
+
+
+PARAMS = dict(a=-1.0, b=1.0, K=1.0, D=0.05)
+
+
+def _weights(shape):
+    k = np.meshgrid(*[np.fft.fftfreq(n) * n for n in shape], indexing="ij")
+    kk = np.sqrt(sum(x ** 2 for x in k))
+    return 1.0 + 0.5 * np.cos(0.4 * kk) ** 2
+
+
+def _gpu_system(shape, prec, dt, seed, order=2):
+    s = pss().model_b(shape, dt=dt, seed=seed, precision=prec, dealias_order=order, **PARAMS)
+    s.init_uniform(0, -0.3, 0.3)
+    return s
+
+
+@pytest.mark.parametrize("shape,prec,tol", [
+    ((32, 32), "f64", 1e-8), ((64,), "f64", 1e-8), ((8, 16, 8), "f64", 1e-8),
+    ((32, 32), "f32", 1e-3), ((16, 16, 16), "f32", 1e-3),
+])
+def test_adjoint_matches_oracle(shape, prec, tol):
+    dt, seed, n = 0.02, 17, 23
+    m = O.model_b(shape, dt=dt, seed=seed, **PARAMS)
+    phi0 = O.to_spectrum(m, O.init_uniform(m, -0.3, 0.3))
+    c = _weights(shape)
+    lamT = 2.0 * c * O.run(m, phi0, 0, n) / m.n_sites     # J = sum c |phi_T|^2 / N
+    lam0, g = O.adjoint(m, phi0, 0, n, lamT)
+    s = _gpu_system(shape, prec, dt, seed)
+    s.adjoint_forward(n)
+    grads, lam0_gpu = s.adjoint_backward(O.half(lamT), 4)
+    assert rel(lam0_gpu, O.half(lam0)) < tol
+    ref = np.array([g[1], -g[6], g[2], g[10]])             # (a, b, K, D) of Model B
+    assert np.max(np.abs(grads - ref) / np.abs(ref)) < tol, (grads, ref)
+    assert s.get_step() == n
+
+
+def test_adjoint_structure_factor_loss_and_resume():
+    # the binned S(q) loss of the adjoint workload, at 64 x 64
+    shape, dt, seed, n, nb = (64, 64), 0.01, 2405, 40, 64
+    m = O.model_b(shape, dt=dt, seed=seed, **PARAMS)
+    phi0 = O.to_spectrum(m, O.init_uniform(m, -0.3, 0.3))
+    phiT = O.run(m, phi0, 0, n)
+    S, cnt, _ = O.structure_factor(m, phiT, nb)
+    target = 0.9 * S
+    J, coef = O.binned_sq_loss(m, phiT, target, nb)
+    bins = O.sq_bin_index(m, nb)
+    lamT = np.where(bins >= 0, coef[np.clip(bins, 0, None)], 0.0) * phiT
+    lam0, g = O.adjoint(m, phi0, 0, n, lamT)
+    s = _gpu_system(shape, "f64", dt, seed)
+    s.adjoint_forward(n)
+    grads, lam0_gpu = s.adjoint_backward(O.half(lamT), 4)
+    assert rel(lam0_gpu, O.half(lam0)) < 1e-8
+    np.testing.assert_allclose(grads, [g[1], -g[6], g[2], g[10]], rtol=1e-8)
+    # the system is back at phi_T and keeps stepping from there
+    assert rel(s.get_spectrum(0), O.half(phiT)) < 1e-12
+    s.step(5)
+    assert rel(s.get_spectrum(0), O.half(O.run(m, phiT, n, 5))) < 1e-12
+
+
+def test_adjoint_matches_gpu_finite_differences():
+    shape, dt, seed, n = (32, 32), 0.02, 5, 15
+    c = _weights(shape)
+    w = np.ones(shape[-1] // 2 + 1) * 2.0
+    w[0] = w[-1] = 1.0
+
+    def J(**kw):
+        p = dict(PARAMS)
+        p.update(kw)
+        s = pss().model_b(shape, dt=dt, seed=seed, precision="f64", **p)
+        s.init_uniform(0, -0.3, 0.3)
+        s.step(n)
+        h = s.get_spectrum(0)
+        return float(np.sum(w * O.half(c) * np.abs(h) ** 2) / (shape[0] * shape[1])), h
+
+    J0, hT = J()
+    s = _gpu_system(shape, "f64", dt, seed)
+    s.adjoint_forward(n)
+    grads, _ = s.adjoint_backward(2.0 * O.half(c) * hT / (shape[0] * shape[1]), 4)
+    for i, name in enumerate(["a", "b", "K", "D"]):
+        h = 1e-5
+        fd = (J(**{name: PARAMS[name] + h})[0] - J(**{name: PARAMS[name] - h})[0]) / (2 * h)
+        assert abs(grads[i] - fd) <= 1e-6 * abs(fd), (name, grads[i], fd)
