@@ -147,6 +147,7 @@ class System:
     def add_param(self, name: str, value: float) -> int:
         i = ctypes.c_int()
         self._ck(lib.pss_add_param(self._h, name.encode(), float(value), ctypes.byref(i)))
+        self._param_names = getattr(self, "_param_names", []) + [name]
         return i.value
 
     def set_param(self, pid: int, value: float):

@@ -107,3 +107,36 @@ def test_adjoint_matches_gpu_finite_differences():
         h = 1e-5
         fd = (J(**{name: PARAMS[name] + h})[0] - J(**{name: PARAMS[name] - h})[0]) / (2 * h)
         assert abs(grads[i] - fd) <= 1e-6 * abs(fd), (name, grads[i], fd)
+
+
+def test_torch_autograd_function_matches_finite_differences():
+    import torch
+    from paper_2405_02410_gb300 import autograd as A
+    shape, dt, n = (32, 32), 0.02, 12
+    P = pss()
+    s = P.model_b(shape, dt=dt, seed=9, precision="f64", **PARAMS)
+    h0_np = np.fft.rfftn(inputs.real_field(shape, seed=3, lo=-0.3, hi=0.3))
+    target = torch.linspace(0.01, 0.02, 16, dtype=torch.float64)
+
+    def loss(h0, params):
+        hT = A.run(h0, params, s, [0, 1, 2, 3], n)
+        S, cnt = A.binned_structure_factor(hT, shape, 16)
+        sel = cnt > 0
+        return ((S[sel] - target[sel]) ** 2).mean()
+
+    h0 = torch.tensor(h0_np, requires_grad=True)
+    params = torch.tensor([PARAMS["a"], PARAMS["b"], PARAMS["K"], PARAMS["D"]], dtype=torch.float64,
+                          requires_grad=True)
+    L = loss(h0, params)
+    L.backward()
+    # central differences in every parameter and along a random Hermitian direction of h0
+    for i in range(4):
+        e = torch.zeros(4, dtype=torch.float64)
+        e[i] = 1e-5
+        fd = (loss(h0.detach(), params.detach() + e) - loss(h0.detach(), params.detach() - e)) / 2e-5
+        assert abs(params.grad[i].item() - fd.item()) <= 1e-6 * abs(fd.item()), (i, params.grad[i], fd)
+    d = torch.tensor(np.fft.rfftn(inputs.real_field(shape, seed=4)))
+    eps = 1e-4
+    fd = (loss(h0.detach() + eps * d, params.detach()) - loss(h0.detach() - eps * d, params.detach())) / (2 * eps)
+    ad = torch.real(torch.vdot(h0.grad.reshape(-1), d.reshape(-1)))
+    assert abs(ad.item() - fd.item()) <= 1e-6 * abs(fd.item())
