@@ -291,6 +291,60 @@ def ensemble_measurement(pss, torch, stream, steps=200):
             "speedup_vs_sequential": seq_ms / ms}
 
 
+def adjoint_measurement(pss, torch, stream, n=2000, shape=(256, 256), nbins=64):
+    """The adjoint workload: 2D Model B 256^2, FP32, n steps with a fixed noise realisation and sqrt(n)
+    checkpoints; loss = mean over the 64 S(q) bins of (S - S*)^2 with S* from (a, b, K) = (-0.8, 1.2, 0.9)."""
+    import numpy as np
+
+    def system(a, b, K):
+        s = pss.model_b(shape, dt=0.01, a=a, b=b, K=K, D=0.01, seed=2405)
+        s.set_stream(stream)
+        s.init_uniform(0, -0.1, 0.1)
+        return s
+
+    tgt = system(-0.8, 1.2, 0.9)
+    tgt.step(n)
+    S_star, cnt, _ = tgt.structure_factor(0, nbins)
+    tgt.close()
+    plain = system(-1.0, 1.0, 1.0)
+    plain.step(32)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plain.step(n)
+    plain.sync()
+    t_plain = time.perf_counter() - t0
+    plain.close()
+    s = system(-1.0, 1.0, 1.0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s.adjoint_forward(n)
+    s.sync()
+    t_fwd = time.perf_counter() - t0
+    # loss gradient of the binned S(q) on the host (marshalling: 64 bins)
+    h = s.get_spectrum(0).astype(np.complex128)
+    S, cnt, _ = s.structure_factor(0, nbins)
+    sel = cnt > 0
+    nb = int(sel.sum())
+    loss = float(np.sum((S[sel] - S_star[sel]) ** 2) / nb)
+    coef = np.zeros(nbins)
+    coef[sel] = 2.0 / nb * (S[sel] - S_star[sel]) * 2.0 / (shape[0] * shape[1] * cnt[sel])
+    ky = np.fft.fftfreq(shape[0]) * shape[0]
+    kx = np.arange(shape[1] // 2 + 1)
+    s2 = (2.0 * nbins * ky[:, None] / shape[0]) ** 2 + (2.0 * nbins * kx[None, :] / shape[1]) ** 2
+    b = np.ceil(np.sqrt(s2)).astype(int) - 1
+    ok = (s2 > 0) & (np.sqrt(s2) <= nbins)
+    lam = np.where(ok, coef[np.clip(b, 0, nbins - 1)], 0.0) * h
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    grads, lam0 = s.adjoint_backward(lam, 4)
+    t_bwd = time.perf_counter() - t0
+    s.close()
+    return {"workload": "2D Model B 256x256 FP32, 2000 steps, sqrt(n) checkpoints, binned-S(q) loss",
+            "steps": n, "loss": loss, "dJ_d(a,b,K,D)": [float(x) for x in grads],
+            "forward_plain_ms": t_plain * 1e3, "forward_with_checkpoints_ms": t_fwd * 1e3,
+            "adjoint_ms": t_bwd * 1e3, "adjoint_over_forward": t_bwd / t_plain}
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -412,6 +466,8 @@ def run_gpu(args):
 
     if not args.no_ensemble:
         extra["ensemble_512"] = ensemble_measurement(pss, torch, stream)
+    if not args.no_adjoint:
+        extra["adjoint_256"] = adjoint_measurement(pss, torch, stream)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
@@ -456,6 +512,7 @@ def main(argv=None):
     ap.add_argument("--no-3d", action="store_true", help="skip the 256^3 secondary measurement")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the 512-instance ensemble measurement")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint measurement")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
