@@ -634,20 +634,22 @@ int do_create(pss_system **out, int batch, int dim, int nx, int ny, int nz, doub
     if (e == cudaSuccess) e = cudaMalloc(&s->d_status, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(s->d_step, 0, sizeof(long long));
     if (e == cudaSuccess) e = cudaMemset(s->d_status, 0, sizeof(int));
-    // roots of unity exp(-2 pi i m / 1024), built in FP64 on the host
+    // roots of unity exp(-2 pi i m / n) for every transform length n = 1, 2, ..., 1024,
+    // the table of length n at offset n - 1; built in FP64 on the host
     if (e == cudaSuccess) {
-        const int n = 1024;
-        if (precision == PSS_F64) {
-            std::vector<double2> h(n);
-            for (int m = 0; m < n; ++m) h[m] = make_double2(std::cos(2 * kPi * m / n), -std::sin(2 * kPi * m / n));
-            e = cudaMalloc(&s->tw, sizeof(double2) * n);
-            if (e == cudaSuccess) e = cudaMemcpy(s->tw, h.data(), sizeof(double2) * n, cudaMemcpyHostToDevice);
-        } else {
-            std::vector<float2> h(n);
+        const int total = 2 * kMaxFftN - 1;
+        std::vector<double2> h(total);
+        for (int n = 1; n <= kMaxFftN; n *= 2)
             for (int m = 0; m < n; ++m)
-                h[m] = make_float2((float)std::cos(2 * kPi * m / n), (float)-std::sin(2 * kPi * m / n));
-            e = cudaMalloc(&s->tw, sizeof(float2) * n);
-            if (e == cudaSuccess) e = cudaMemcpy(s->tw, h.data(), sizeof(float2) * n, cudaMemcpyHostToDevice);
+                h[twiddle_offset(n) + m] = make_double2(std::cos(2 * kPi * m / n), -std::sin(2 * kPi * m / n));
+        if (precision == PSS_F64) {
+            e = cudaMalloc(&s->tw, sizeof(double2) * total);
+            if (e == cudaSuccess) e = cudaMemcpy(s->tw, h.data(), sizeof(double2) * total, cudaMemcpyHostToDevice);
+        } else {
+            std::vector<float2> hf(total);
+            for (int m = 0; m < total; ++m) hf[m] = make_float2((float)h[m].x, (float)h[m].y);
+            e = cudaMalloc(&s->tw, sizeof(float2) * total);
+            if (e == cudaSuccess) e = cudaMemcpy(s->tw, hf.data(), sizeof(float2) * total, cudaMemcpyHostToDevice);
         }
     }
     if (e != cudaSuccess) {

@@ -146,8 +146,6 @@ template <int R, int DIR, typename T> __device__ __forceinline__ void dft_reg(cp
 // element-wise work (a power, a mask, a scale, a store to global memory)
 // rides on the loads and stores the transform makes anyway.
 // ---------------------------------------------------------------------------
-constexpr int kTwiddleLog = 10;
-constexpr int kTwiddleN = 1 << kTwiddleLog;   // roots-of-unity table length (largest FFT)
 
 template <int N> struct FftShape {
     static constexpr int E = N < 16 ? N : 16;   // values per thread and pass
@@ -186,7 +184,7 @@ __device__ __forceinline__ void stockham_pass(Src src, Dst dst, int logP, int la
     constexpr int STRIDE = N / R;
     constexpr int BPT = STRIDE / TPF;            // butterflies per thread
     const int P = 1 << logP;
-    const int twshift = kTwiddleLog - logP - LOGR;
+    const int twshift = FftShape<N>::LOG - logP - LOGR;
 #pragma unroll 1
     for (int s = 0; s < BPT; ++s) {
         const int i = lane + s * TPF;
@@ -198,7 +196,7 @@ __device__ __forceinline__ void stockham_pass(Src src, Dst dst, int logP, int la
             const int kk = k << twshift;
 #pragma unroll
             for (int r = 1; r < R; ++r) {
-                // exp(DIR 2 pi i r k / (P R)) from the forward table exp(-2 pi i m / kTwiddleN)
+                // exp(DIR 2 pi i r k / (P R)) from the forward table exp(-2 pi i m / N)
                 cplx<T> w = tw[r * kk];
                 if (DIR > 0) w.y = -w.y;
                 u[r] = cmul<T>(u[r], w);

@@ -12,6 +12,12 @@ template <> struct CplxOf<float> { using type = float2; };
 template <> struct CplxOf<double> { using type = double2; };
 template <typename T> using cplx = typename CplxOf<T>::type;
 
+// Roots of unity: the host builds, in FP64, one table per transform length,
+// exp(-2 pi i m / n) for m < n, for n = 1, 2, 4, ..., kMaxFftN back to back
+// (the table of length n starts at entry n - 1).
+constexpr int kMaxFftN = 1024;
+__host__ __device__ constexpr int twiddle_offset(int n) { return n - 1; }
+
 constexpr int kTileW = 4;       // kx columns per tile of every spectral array
 constexpr int kMaxFields = 4;
 constexpr int kPolyTerms = 5;   // operators are polynomials of degree <= 4 in q^2

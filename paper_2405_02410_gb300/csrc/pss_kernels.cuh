@@ -239,7 +239,7 @@ __device__ __forceinline__ void col_adjoint(const ColArgs<T> &a, const FieldP<T>
                           [&](int p, C v, C *) {
                               if (writes) dst[p * W] = v;
                           },
-                          other, nb, lane, active, a.tw);
+                          other, nb, lane, active, a.tw + twiddle_offset(N));
     }
     if (t == 0) bulk_wait_read();
 }
@@ -281,7 +281,7 @@ __global__ void __launch_bounds__(512, N >= 512 ? 1 : 2) k_col(const ColArgs<T> 
     const int opp = (sp.n_outer - op) & (sp.n_outer - 1);        // partner pencil (-ky)
     const int mode = a.mode;
     const int first_tile = blockIdx.x * a.tiles_per_cta;
-    const C *__restrict__ tw = a.tw;
+    const C *__restrict__ tw = a.tw + twiddle_offset(N);
 
     auto chunk_tile = [&](int ch) { return first_tile + (ch >> logNP); };
     auto chunk_o = [&](int ch) { return (ch & logNP) ? opp : op; };
@@ -508,7 +508,7 @@ __global__ void __launch_bounds__(256) k_row(const RowArgs<T> a) {
     const int rows = sp.rows;
     const int nrow = rows - r0 < G2 ? rows - r0 : G2;          // rows present in this CTA
     const int mode = a.mode;
-    const C *__restrict__ tw = a.tw;
+    const C *__restrict__ tw = a.tw + twiddle_offset(N);
     pdl_wait();
     pdl_trigger();
 
@@ -674,8 +674,9 @@ __global__ void __launch_bounds__(256) k_mid(const MidArgs<T> a) {
     const size_t ostride = (size_t)nz * W;
     auto src_f = [&](int p) { return S[p * F + f]; };
     auto sink = [&](int p, C v, C *) { dst[p * ostride] = v; };
-    if (a.mode == MID_FWD) fft_run<T, N, -1>(src_f, sink, B0 + f * SF, S + f * SF, lane, active, a.tw);
-    else fft_run<T, N, +1>(src_f, sink, B0 + f * SF, S + f * SF, lane, active, a.tw);
+    const C *__restrict__ tw = a.tw + twiddle_offset(N);
+    if (a.mode == MID_FWD) fft_run<T, N, -1>(src_f, sink, B0 + f * SF, S + f * SF, lane, active, tw);
+    else fft_run<T, N, +1>(src_f, sink, B0 + f * SF, S + f * SF, lane, active, tw);
     if (a.inc_step && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && t == 0) *a.d_step += 1;
 }
 
