@@ -912,6 +912,8 @@ cudaError_t launch_structure_factor(const SysP<T> &sp, const double dx[3], const
     long long blocks = (n + 255) / 256;
     if (blocks > 4096) blocks = 4096;
     const size_t smem = sizeof(double) * (size_t)(2 * nbins + 2);
+    cudaError_t e = ensure_smem(k_structure_factor<T>, smem);
+    if (e != cudaSuccess) return e;
     k_structure_factor<T><<<(int)blocks, 256, smem, st>>>(sp, dx[0], dx[1], dx[2], tiles, nbins, acc);
     return cudaGetLastError();
 }

@@ -174,6 +174,21 @@ def test_structure_factor_matches_oracle():
     assert rel(S, So) < 1e-10 and abs(L - Lo) < 1e-10 * Lo
 
 
+def test_structure_factor_many_bins():
+    # 4096 bins need more than 48 KB of shared memory per block
+    shape = (256, 256)
+    kw = dict(dt=0.01, a=-1, b=1, K=1, D=0.05, seed=21)
+    s = pss().model_b(shape, precision="f64", **kw)
+    s.init_uniform(0, -0.1, 0.1)
+    s.step(3)
+    S, cnt, L = s.structure_factor(0, 4096)
+    m = O.model_b(shape, **kw)
+    full = O.run(m, O.to_spectrum(m, O.init_uniform(m, -0.1, 0.1)), 0, 3)
+    So, co, Lo = O.structure_factor(m, full, 4096)
+    np.testing.assert_array_equal(cnt, co)
+    assert rel(S, So) < 1e-10 and abs(L - Lo) < 1e-10 * Lo
+
+
 def test_set_spectrum_roundtrip_and_param_change():
     P = pss()
     s = P.model_b((32, 32), D=0.0, noisy=False, seed=1, precision="f64")
