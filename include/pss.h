@@ -192,6 +192,35 @@ int pss_set_spectrum(pss_system *s, int field_id, const void *half_in, int where
 int pss_structure_factor(pss_system *s, int field_id, int nbins,
                          double *S_out, double *count_out, double *L_out);
 
+/* The same binned structure factor as pss_structure_factor, computed without
+ * allocating any memory.  The paper has no counterpart: this is a library
+ * service for callers that must not allocate while they run, such as a
+ * process whose device memory is handed out up front by another allocator
+ * (a late cudaMalloc there fails or fragments the pool), or a loop that
+ * cannot afford cudaFree, which waits for the whole device and so stalls
+ * work on every stream.  pss_structure_factor may grow its accumulator
+ * with cudaFree + cudaMalloc; this entry point never does.
+ *
+ * The FP64 bin accumulator is a fixed array of 2 * PSS_NOALLOC_MAX_BINS + 2
+ * doubles (16.4 KB) inside the library, present on every GPU that loads the
+ * library until the process exits.  nbins must lie in
+ * [1, PSS_NOALLOC_MAX_BINS]; larger requests fail with PSS_EINVAL and touch
+ * nothing.  The system's device must be the current device.
+ *
+ * The first call on a device looks up the array's device address (set-up,
+ * once per device); make that first call before any stream capture.
+ *
+ * Every call, from every system on the device, shares the one array; each
+ * call clears the part it uses before accumulating and synchronises the
+ * system's stream before returning.  Calls whose GPU work overlaps (two
+ * host threads calling on different streams at once) race on the array and
+ * return wrong sums: serialise them.
+ *
+ * Arguments, outputs and errors are those of pss_structure_factor. */
+#define PSS_NOALLOC_MAX_BINS 1024
+int pss_structure_factor_noalloc(pss_system *s, int field_id, int nbins,
+                                 double *S_out, double *count_out, double *L_out);
+
 /* Wait for the system's stream and report device-side errors. */
 int pss_sync(pss_system *s);
 

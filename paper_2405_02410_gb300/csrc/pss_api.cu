@@ -16,6 +16,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -1180,6 +1181,71 @@ int pss_structure_factor(pss_system *s, int field_id, int nbins, double *S_out, 
     if (e != cudaSuccess) return cuda_fail(s, e, "structure factor kernel");
     std::vector<double> h(need);
     CK(cudaMemcpyAsync(h.data(), s->sq, sizeof(double) * need, cudaMemcpyDeviceToHost, s->stream));
+    if ((rc = device_errors(s))) return rc;
+    for (int b = 0; b < nbins; ++b) {
+        S_out[b] = h[nbins + b] > 0 ? h[b] / h[nbins + b] : 0.0;
+        if (count_out) count_out[b] = h[nbins + b];
+    }
+    if (L_out) *L_out = h[2 * nbins + 1] > 0 ? 2 * kPi * h[2 * nbins] / h[2 * nbins + 1] : 0.0;
+    return PSS_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Structure factor without allocation.  The bin accumulator is a fixed array
+// of this file; host code reaches it only through the device address that
+// cudaGetSymbolAddress returns (the name itself, in host code, is a host-side
+// stand-in and must never be handed to a kernel).
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int kNoAllocSlots = 2 * PSS_NOALLOC_MAX_BINS + 2;   // bin sums, bin counts, two totals
+constexpr int kNoAllocMaxDevices = 64;
+
+static __device__ __align__(256) double g_sq_scratch[kNoAllocSlots];
+
+std::mutex g_sq_setup_mutex;
+double *g_sq_scratch_addr[kNoAllocMaxDevices];   // device address of g_sq_scratch, per device, once set up
+}  // namespace
+
+extern "C" {
+
+int pss_structure_factor_noalloc(pss_system *s, int field_id, int nbins, double *S_out, double *count_out,
+                                 double *L_out) {
+    int rc = check_field(s, field_id);
+    if (rc) return rc;
+    if (nbins < 1 || nbins > PSS_NOALLOC_MAX_BINS || !S_out)
+        return fail(s, PSS_EINVAL, "nbins in [1, PSS_NOALLOC_MAX_BINS = %d] and S_out required",
+                    PSS_NOALLOC_MAX_BINS);
+    int dev = -1;
+    CK(cudaGetDevice(&dev));
+    if (dev != s->device) return fail(s, PSS_EINVAL, "the system's device (%d) is not the current device", s->device);
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(s, PSS_EUNSUPPORTED, "device index %d too large", dev);
+    double *acc = nullptr;
+    {
+        // set-up, once per device, with that device current
+        std::lock_guard<std::mutex> lock(g_sq_setup_mutex);
+        if (!g_sq_scratch_addr[dev]) {
+            void *addr = nullptr;
+            cudaError_t e = cudaGetSymbolAddress((void **)&addr, g_sq_scratch);
+            if (e != cudaSuccess) return cuda_fail(s, e, "cudaGetSymbolAddress of the structure-factor array");
+            g_sq_scratch_addr[dev] = (double *)addr;
+        }
+        acc = g_sq_scratch_addr[dev];
+    }
+    const int need = 2 * nbins + 2;
+    // the array keeps the previous call's sums: clear the part this call accumulates into
+    CK(cudaMemsetAsync(acc, 0, sizeof(double) * need, s->stream));
+    const size_t ofs = csize(s) * s->field_elems * (size_t)cur_slot(s, field_id);
+    cudaError_t e = s->prec == PSS_F64
+        ? launch_structure_factor<double>(sys_params<double>(s), s->dx, (const double2 *)((char *)s->state + ofs), nbins,
+                                          acc, s->stream)
+        : launch_structure_factor<float>(sys_params<float>(s), s->dx, (const float2 *)((char *)s->state + ofs), nbins,
+                                         acc, s->stream);
+    s->launches++;
+    if (e != cudaSuccess) return cuda_fail(s, e, "structure factor kernel");
+    double h[kNoAllocSlots];   // host copy on the stack: no heap allocation either
+    CK(cudaMemcpyAsync(h, acc, sizeof(double) * need, cudaMemcpyDeviceToHost, s->stream));
     if ((rc = device_errors(s))) return rc;
     for (int b = 0; b < nbins; ++b) {
         S_out[b] = h[nbins + b] > 0 ? h[b] / h[nbins + b] : 0.0;

@@ -20,6 +20,7 @@ LIBPATH = os.path.join(HERE, "_lib", "libpss.so")
 PSS_OK, PSS_EINVAL, PSS_ENOMEM, PSS_ECUDA, PSS_ETIMEOUT, PSS_ENONFINITE, PSS_EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
 PSS_F32, PSS_F64 = 0, 1
 PSS_HOST, PSS_DEVICE = 0, 1
+NOALLOC_MAX_BINS = 1024   # PSS_NOALLOC_MAX_BINS of the C header
 
 EXPORTS = [
     "pss_create_system", "pss_destroy_system", "pss_set_stream", "pss_add_param", "pss_set_param",
@@ -28,6 +29,7 @@ EXPORTS = [
     "pss_set_spectrum", "pss_structure_factor", "pss_sync", "pss_last_error", "pss_launch_count",
     "pss_time_kernels", "pss_set_tuning", "pss_create_batch", "pss_batch_size", "pss_select_instance",
     "pss_set_param_batch", "pss_step_many", "pss_adjoint_forward", "pss_adjoint_backward",
+    "pss_structure_factor_noalloc",
 ]
 
 
@@ -63,6 +65,7 @@ def _load():
         "pss_get_spectrum": ([vp, i32, vp, i32], i32),
         "pss_set_spectrum": ([vp, i32, vp, i32], i32),
         "pss_structure_factor": ([vp, i32, i32, P(d), P(d), P(d)], i32),
+        "pss_structure_factor_noalloc": ([vp, i32, i32, P(d), P(d), P(d)], i32),
         "pss_sync": ([vp], i32),
         "pss_last_error": ([vp], ctypes.c_char_p),
         "pss_launch_count": ([vp], i64),
@@ -241,6 +244,18 @@ class System:
         dp = ctypes.POINTER(ctypes.c_double)
         self._ck(lib.pss_structure_factor(self._h, field, nbins, S.ctypes.data_as(dp), cnt.ctypes.data_as(dp),
                                           ctypes.byref(L)))
+        return S, cnt, L.value
+
+    def structure_factor_noalloc(self, field: int, nbins: int = 64):
+        """structure_factor computed with the library's fixed accumulator (at most
+        NOALLOC_MAX_BINS bins): the library allocates no memory for it, for callers
+        that must not allocate while they run.  Calls that overlap on the GPU race."""
+        S = np.zeros(nbins)
+        cnt = np.zeros(nbins)
+        L = ctypes.c_double()
+        dp = ctypes.POINTER(ctypes.c_double)
+        self._ck(lib.pss_structure_factor_noalloc(self._h, field, nbins, S.ctypes.data_as(dp),
+                                                  cnt.ctypes.data_as(dp), ctypes.byref(L)))
         return S, cnt, L.value
 
     def time_kernels(self, n: int):
