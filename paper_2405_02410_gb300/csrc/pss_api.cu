@@ -636,10 +636,10 @@ int do_create(pss_system **out, int batch, int dim, int nx, int ny, int nz, doub
     if (e == cudaSuccess) e = cudaMemset(s->d_step, 0, sizeof(long long));
     if (e == cudaSuccess) e = cudaMemset(s->d_status, 0, sizeof(int));
     // roots of unity exp(-2 pi i m / n) for every transform length n = 1, 2, ..., 1024,
-    // the table of length n at offset n - 1; built in FP64 on the host
+    // the table of length n at offset n; built in FP64 on the host
     if (e == cudaSuccess) {
-        const int total = 2 * kMaxFftN - 1;
-        std::vector<double2> h(total);
+        const int total = kTwiddleEntries;
+        std::vector<double2> h(total, make_double2(0.0, 0.0));
         for (int n = 1; n <= kMaxFftN; n *= 2)
             for (int m = 0; m < n; ++m)
                 h[twiddle_offset(n) + m] = make_double2(std::cos(2 * kPi * m / n), -std::sin(2 * kPi * m / n));

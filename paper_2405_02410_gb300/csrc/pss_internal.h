@@ -14,9 +14,11 @@ template <typename T> using cplx = typename CplxOf<T>::type;
 
 // Roots of unity: the host builds, in FP64, one table per transform length,
 // exp(-2 pi i m / n) for m < n, for n = 1, 2, 4, ..., kMaxFftN back to back
-// (the table of length n starts at entry n - 1).
+// after one unused entry, so that the table of length n starts at entry n
+// (16-byte aligned for n >= 2: kernels stage it with a bulk copy).
 constexpr int kMaxFftN = 1024;
-__host__ __device__ constexpr int twiddle_offset(int n) { return n - 1; }
+__host__ __device__ constexpr int twiddle_offset(int n) { return n; }
+constexpr int kTwiddleEntries = 2 * kMaxFftN;
 
 constexpr int kTileW = 4;       // kx columns per tile of every spectral array
 constexpr int kMaxFields = 4;

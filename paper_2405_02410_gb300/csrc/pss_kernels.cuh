@@ -25,6 +25,14 @@ namespace pss {
 
 constexpr int W = kTileW;
 
+// Bytes of the roots-of-unity table a kernel with transforms of length N
+// stages into shared memory (none below 16 points: one pass, no twiddles).
+template <typename C, int N> __host__ __device__ constexpr uint32_t twiddle_bytes() {
+    return N >= 16 ? (uint32_t)(N * sizeof(C)) : 0u;
+}
+// its size in elements (a multiple of 16, so the buffers after it keep their alignment)
+template <int N> __host__ __device__ constexpr int twiddle_elems() { return N >= 16 ? N : 0; }
+
 template <typename T> __device__ __forceinline__ T poly5(const T *c, T x) {
     return (((c[4] * x + c[3]) * x + c[2]) * x + c[1]) * x + c[0];
 }
@@ -115,7 +123,8 @@ template <typename T, int N>
 __device__ __forceinline__ void col_adjoint(const ColArgs<T> &a, const FieldP<T> &fp, cplx<T> *PHI, const cplx<T> *P,
                                             cplx<T> *X, cplx<T> *Y, int which, int F, int SF, int nchunks,
                                             int lognch, int first_tile, int op, int opp, int logNP, size_t sofs,
-                                            int ch, int c, int f, int lane, bool active) {
+                                            int ch, int c, int f, int lane, bool active,
+                                            const cplx<T> *__restrict__ tw) {
     using C = cplx<T>;
     constexpr int CS = N * W + 8;
     const SysP<T> &sp = a.sp;
@@ -239,7 +248,7 @@ __device__ __forceinline__ void col_adjoint(const ColArgs<T> &a, const FieldP<T>
                           [&](int p, C v, C *) {
                               if (writes) dst[p * W] = v;
                           },
-                          other, nb, lane, active, a.tw + twiddle_offset(N));
+                          other, nb, lane, active, tw);
     }
     if (t == 0) bulk_wait_read();
 }
@@ -251,7 +260,7 @@ template <typename T, int N> struct ColSmem {
         return a > b ? a : b;
     }
     __host__ __device__ static size_t bytes(int F) {
-        return 128 + sizeof(cplx<T>) * ((size_t)(F / W) * CS + 2 * (size_t)xs(F));
+        return 128 + sizeof(cplx<T>) * ((size_t)twiddle_elems<N>() + (size_t)(F / W) * CS + 2 * (size_t)xs(F));
     }
 };
 
@@ -268,7 +277,8 @@ __global__ void __launch_bounds__(512, N >= 512 ? 1 : 2) k_col(const ColArgs<T> 
     const int logF = __ffs(F) - 1;
     const int nchunks = F / W, lognch = logF - 2;
     const int SF = sf_fft_fastest(N, F);
-    C *PHI = reinterpret_cast<C *>(smem_raw + 128);
+    C *TW = reinterpret_cast<C *>(smem_raw + 128);             // roots of unity of length N
+    C *PHI = TW + twiddle_elems<N>();
     C *X = PHI + nchunks * CS;
     C *Y = X + L::xs(F);
     const SysP<T> &sp = a.sp;
@@ -281,7 +291,7 @@ __global__ void __launch_bounds__(512, N >= 512 ? 1 : 2) k_col(const ColArgs<T> 
     const int opp = (sp.n_outer - op) & (sp.n_outer - 1);        // partner pencil (-ky)
     const int mode = a.mode;
     const int first_tile = blockIdx.x * a.tiles_per_cta;
-    const C *__restrict__ tw = a.tw + twiddle_offset(N);
+    const C *__restrict__ tw = TW;
 
     auto chunk_tile = [&](int ch) { return first_tile + (ch >> logNP); };
     auto chunk_o = [&](int ch) { return (ch & logNP) ? opp : op; };
@@ -300,7 +310,8 @@ __global__ void __launch_bounds__(512, N >= 512 ? 1 : 2) k_col(const ColArgs<T> 
     pdl_trigger();
     if (t == 0) {
         mbar_init(bar, 1);
-        mbar_expect_tx(bar, chunk_bytes * nvalid * ((need_in ? 1 : 0) + (need_phi ? 1 : 0)));
+        mbar_expect_tx(bar, chunk_bytes * nvalid * ((need_in ? 1 : 0) + (need_phi ? 1 : 0)) + twiddle_bytes<C, N>());
+        if (twiddle_bytes<C, N>()) bulk_g2s(TW, a.tw + twiddle_offset(N), twiddle_bytes<C, N>(), bar);
         for (int ch = 0; ch < nvalid; ++ch) {
             if (need_phi) bulk_g2s(PHI + ch * CS, a.state + sofs + gofs(ch), chunk_bytes, bar);
             if (need_in) bulk_g2s(X + ch * CS, a.in + sofs + gofs(ch), chunk_bytes, bar);
@@ -331,7 +342,7 @@ __global__ void __launch_bounds__(512, N >= 512 ? 1 : 2) k_col(const ColArgs<T> 
         const C *P = which == 0 ? Y : X;
         if constexpr (ADJ) {
             col_adjoint<T, N>(a, fp, PHI, P, X, Y, which, F, SF, nchunks, lognch, first_tile, op, opp, logNP, sofs,
-                              ch, c, f, lane, active);
+                              ch, c, f, lane, active, tw);
             return;
         }
         const uint32_t step = (uint32_t)(*a.d_step);
@@ -479,7 +490,7 @@ template <typename T, int N> struct RowSmem {
         return a > c ? a : c;
     }
     __host__ __device__ static size_t bytes(int G, int ntiles) {
-        return 128 + sizeof(cplx<T>) * ((size_t)s_elems(G, ntiles) + 2 * (size_t)G * sf_row(N));
+        return 128 + sizeof(cplx<T>) * ((size_t)twiddle_elems<N>() + (size_t)s_elems(G, ntiles) + 2 * (size_t)G * sf_row(N));
     }
 };
 
@@ -496,7 +507,8 @@ __global__ void __launch_bounds__(256) k_row(const RowArgs<T> a) {
     const int G = a.G, G2 = 2 * a.G;                            // G a power of two
     const int logG = __ffs(G) - 1;
     const int TS = L::tstride(G);
-    C *S = reinterpret_cast<C *>(smem_raw + 128);
+    C *TW = reinterpret_cast<C *>(smem_raw + 128);             // roots of unity of length N
+    C *S = TW + twiddle_elems<N>();
     T *Sr = reinterpret_cast<T *>(S);
     C *B0 = S + L::s_elems(G, sp.ntiles);
     C *B1 = B0 + G * SF;
@@ -508,7 +520,7 @@ __global__ void __launch_bounds__(256) k_row(const RowArgs<T> a) {
     const int rows = sp.rows;
     const int nrow = rows - r0 < G2 ? rows - r0 : G2;          // rows present in this CTA
     const int mode = a.mode;
-    const C *__restrict__ tw = a.tw + twiddle_offset(N);
+    const C *__restrict__ tw = TW;
     pdl_wait();
     pdl_trigger();
 
@@ -518,7 +530,8 @@ __global__ void __launch_bounds__(256) k_row(const RowArgs<T> a) {
         const uint32_t row_bytes = (uint32_t)(N * sizeof(T));
         if (t == 0) {
             mbar_init(bar, 1);
-            mbar_expect_tx(bar, row_bytes * nrow);
+            mbar_expect_tx(bar, row_bytes * nrow + twiddle_bytes<C, N>());
+            if (twiddle_bytes<C, N>()) bulk_g2s(TW, a.tw + twiddle_offset(N), twiddle_bytes<C, N>(), bar);
             for (int rl = 0; rl < nrow; ++rl) bulk_g2s(Sr + rl * N, src + real_row_offset(sp, r0 + rl), row_bytes, bar);
         }
         __syncthreads();   // the barrier is initialised before anyone polls it
@@ -530,7 +543,8 @@ __global__ void __launch_bounds__(256) k_row(const RowArgs<T> a) {
         const uint32_t seg = (uint32_t)(nrow * W * sizeof(C));
         if (t == 0) {
             mbar_init(bar, 1);
-            mbar_expect_tx(bar, seg * ntl);
+            mbar_expect_tx(bar, seg * ntl + twiddle_bytes<C, N>());
+            if (twiddle_bytes<C, N>()) bulk_g2s(TW, a.tw + twiddle_offset(N), twiddle_bytes<C, N>(), bar);
         }
         __syncthreads();
         for (int tl = t; tl < ntl; tl += nthr) bulk_g2s(S + tl * TS, src + ((size_t)tl * rows + r0) * W, seg, bar);
@@ -624,7 +638,7 @@ template <typename T, int N> struct MidSmem {
         return a > b ? a : b;
     }
     __host__ __device__ static size_t bytes(int F) {
-        return 128 + sizeof(cplx<T>) * ((size_t)s_elems(F) + (size_t)F * sf_fft_fastest(N, F));
+        return 128 + sizeof(cplx<T>) * ((size_t)twiddle_elems<N>() + (size_t)s_elems(F) + (size_t)F * sf_fft_fastest(N, F));
     }
 };
 
@@ -639,7 +653,8 @@ __global__ void __launch_bounds__(256) k_mid(const MidArgs<T> a) {
     const int F = a.PZ * W;
     const int logF = __ffs(F) - 1;
     const int SF = sf_fft_fastest(N, F);
-    C *S = reinterpret_cast<C *>(smem_raw + 128);
+    C *TW = reinterpret_cast<C *>(smem_raw + 128);             // roots of unity of length N
+    C *S = TW + twiddle_elems<N>();
     C *B0 = S + L::s_elems(F);
     const int slot = a.slot0 + blockIdx.z;
     const size_t sofs = (size_t)slot * a.slot_stride;
@@ -657,7 +672,8 @@ __global__ void __launch_bounds__(256) k_mid(const MidArgs<T> a) {
         int n = 0;
         for (int o = 0; o < N; ++o) n += (!masked_in || abs(signed_k(o, N)) <= kmy) ? 1 : 0;
         mbar_init(bar, 1);
-        mbar_expect_tx(bar, seg * n);
+        mbar_expect_tx(bar, seg * n + twiddle_bytes<C, N>());
+        if (twiddle_bytes<C, N>()) bulk_g2s(TW, a.tw + twiddle_offset(N), twiddle_bytes<C, N>(), bar);
     }
     __syncthreads();
     for (int o = t; o < N; o += nthr) {
@@ -674,7 +690,7 @@ __global__ void __launch_bounds__(256) k_mid(const MidArgs<T> a) {
     const size_t ostride = (size_t)nz * W;
     auto src_f = [&](int p) { return S[p * F + f]; };
     auto sink = [&](int p, C v, C *) { dst[p * ostride] = v; };
-    const C *__restrict__ tw = a.tw + twiddle_offset(N);
+    const C *__restrict__ tw = TW;
     if (a.mode == MID_FWD) fft_run<T, N, -1>(src_f, sink, B0 + f * SF, S + f * SF, lane, active, tw);
     else fft_run<T, N, +1>(src_f, sink, B0 + f * SF, S + f * SF, lane, active, tw);
     if (a.inc_step && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && t == 0) *a.d_step += 1;
