@@ -171,6 +171,9 @@ int pss_time_kernels(pss_system *s, int64_t n, double *avg_ms);
  *   "col_tiles"   column tiles per CTA of the fused column kernel;
  *   "mid_planes"  z planes per CTA of the 3D y-transform kernel;
  *   "graph_steps" steps per replayed CUDA graph;
+ *   "col_radix", "row_radix", "mid_radix"
+ *                 largest FFT pass radix (8 or 16) of the column, x and
+ *                 3D y kernels;
  * 0 restores the automatic choice.  Unknown keys return PSS_EINVAL. */
 int pss_set_tuning(pss_system *s, const char *key, int value);
 

@@ -82,6 +82,7 @@ struct pss_system {
     bool graph_valid = false;
     // launch-shape tuning (pss_set_tuning); 0 = automatic
     int tune_pdl = 0, tune_row_pairs = 0, tune_col_tiles = 0, tune_graph_steps = 0, tune_mid_planes = 0;
+    int tune_col_radix = 0, tune_row_radix = 0, tune_mid_radix = 0;   // FFT radix caps (8 or 16; 0 = automatic)
     int64_t launches = 0;
     std::string err;
     // adjoint: checkpoints of the last pss_adjoint_forward run
@@ -198,11 +199,23 @@ template <typename T> int upload_params_t(pss_system *s) {
 int upload_params(pss_system *s) { return s->prec == PSS_F64 ? upload_params_t<double>(s) : upload_params_t<float>(s); }
 
 // ---- launch shapes -------------------------------------------------------
+// FFT radix cap of each kernel.  Radix 16 takes fewer passes (less shared-
+// memory traffic and fewer barriers), radix 8 twice the threads per FFT
+// (more warps to hide latency).  Measured on GB300: the column kernel is
+// faster with radix 16 for 3D pencils and 1024-point columns, the row
+// kernel with radix 8, the 3D y kernel with radix 16.
+int col_emax(const pss_system *s) {
+    if (s->tune_col_radix) return s->tune_col_radix;
+    return (s->dim == 3 || s->n_inner >= 1024) ? 16 : 8;
+}
+int row_emax(const pss_system *s) { return s->tune_row_radix ? s->tune_row_radix : 8; }
+int mid_emax(const pss_system *s) { return s->tune_mid_radix ? s->tune_mid_radix : 16; }
+
 // tiles per CTA of the column kernel: a power of two, so that the CTA's
 // FFT count F = tiles * kTileW * NP is one; aims at >= 64 threads per CTA
 int col_tiles_per_cta(const pss_system *s) {
     const int NP = s->dim == 3 ? 2 : 1;
-    const int per_tile = kTileW * NP * fft_TPF(s->n_inner);
+    const int per_tile = kTileW * NP * fft_TPF(s->n_inner, col_emax(s));
     if (s->tune_col_tiles > 0) {
         int tc = 1;
         while (tc * 2 <= s->tune_col_tiles && tc * 2 <= s->ntiles && 2 * tc * 2 * per_tile <= 512) tc *= 2;
@@ -216,7 +229,7 @@ int col_tiles_per_cta(const pss_system *s) {
 // row pairs per CTA of the row kernel: a power of two with G * TPF <= 128
 // threads, and at least ~8 CTAs when there are few rows
 int row_G(const pss_system *s) {
-    const int tpf = fft_TPF(s->nx);
+    const int tpf = fft_TPF(s->nx, row_emax(s));
     if (s->tune_row_pairs > 0) {
         int G = 1;
         while (G * 2 <= s->tune_row_pairs && G * 2 * tpf <= 256 && G * 2 <= std::max(1, s->rows / 2)) G *= 2;
@@ -229,7 +242,7 @@ int row_G(const pss_system *s) {
 }
 
 int mid_PZ(const pss_system *s) {
-    const int tpf = fft_TPF(s->ny);
+    const int tpf = fft_TPF(s->ny, mid_emax(s));
     int pz = std::max(1, 256 / (kTileW * tpf));
     if (s->tune_mid_planes > 0) {
         int p = 1;
@@ -298,6 +311,7 @@ template <typename T> struct Seq {
         a.d_step = s->d_step;
         a.d_status = s->d_status;
         a.mode = mode;
+        a.E = col_emax(s);
         a.tiles_per_cta = col_tiles_per_cta(s);
         a.F = a.tiles_per_cta * kTileW * (s->dim == 3 ? 2 : 1);
         a.n_tiles = mode == COL_INV_MASK ? max_kept_tiles(s) : s->ntiles;
@@ -327,6 +341,7 @@ template <typename T> struct Seq {
         a.d_step = s->d_step;
         a.d_status = s->d_status;
         a.mode = mode;
+        a.E = row_emax(s);
         a.G = row_G(s);
         a.inc_step = inc ? 1 : 0;
         if (timer) timer->begin(2, st);
@@ -349,6 +364,7 @@ template <typename T> struct Seq {
         a.d_step = s->d_step;
         a.d_status = s->d_status;
         a.mode = mode;
+        a.E = mid_emax(s);
         a.PZ = mid_PZ(s);
         a.inc_step = inc ? 1 : 0;
         const int nt = mode == MID_INV_MASK ? max_kept_tiles(s) : s->ntiles;
@@ -1083,6 +1099,10 @@ int pss_set_tuning(pss_system *s, const char *key, int value) {
     else if (k == "col_tiles") s->tune_col_tiles = value;
     else if (k == "mid_planes") s->tune_mid_planes = value;
     else if (k == "graph_steps") s->tune_graph_steps = value;
+    else if (k == "col_radix" || k == "row_radix" || k == "mid_radix") {
+        if (value != 0 && value != 8 && value != 16) return fail(s, PSS_EINVAL, "radix caps are 8 or 16 (0 = automatic)");
+        (k == "col_radix" ? s->tune_col_radix : k == "row_radix" ? s->tune_row_radix : s->tune_mid_radix) = value;
+    }
     else return fail(s, PSS_EINVAL, "unknown tuning key '%s'", key);
     invalidate(s);
     return PSS_OK;

@@ -131,7 +131,7 @@ template <int R, int DIR, typename T> __device__ __forceinline__ void dft_reg(cp
 
 // ---------------------------------------------------------------------------
 // Batched length-N Stockham FFT in shared memory.  A CTA runs several FFTs
-// side by side; FFT f is served by TPF = N/16 threads ("lanes"; one thread
+// side by side; FFT f is served by TPF = N/E threads ("lanes"; one thread
 // for N <= 16) and owns a contiguous buffer slice of SF elements in which
 // position p lives at pos + pos/16 (one pad slot per 16 keeps the stride-R
 // writes of a pass free of bank conflicts).  SF is chosen per thread mapping
@@ -147,12 +147,13 @@ template <int R, int DIR, typename T> __device__ __forceinline__ void dft_reg(cp
 // rides on the loads and stores the transform makes anyway.
 // ---------------------------------------------------------------------------
 
-template <int N> struct FftShape {
-    static constexpr int E = N < 16 ? N : 16;   // values per thread and pass
+template <int N, int EMAX> struct FftShape {
+    static constexpr int E = fft_E(N, EMAX);    // values per thread and pass (the radix of the main passes)
     static constexpr int TPF = N / E;           // threads per FFT
-    static constexpr int LOG = N <= 1 ? 0 : N <= 2 ? 1 : N <= 4 ? 2 : N <= 8 ? 3 : N <= 16 ? 4 : N <= 32 ? 5 :
-                               N <= 64 ? 6 : N <= 128 ? 7 : N <= 256 ? 8 : N <= 512 ? 9 : 10;
-    static constexpr int R0 = (LOG % 4 == 0) ? (N > 1 ? 16 : 1) : (1 << (LOG % 4));
+    static constexpr int LOG = ilog2(N);
+    static constexpr int LOGE = ilog2(E);
+    // N = R0 * E^m: the first pass has radix R0, the others radix E
+    static constexpr int R0 = N <= 1 ? 1 : (LOG % LOGE == 0 ? E : 1 << (LOG % LOGE));
 };
 
 __device__ __forceinline__ int spad(int pos) { return pos + (pos >> 4); }
@@ -176,15 +177,15 @@ __host__ __device__ constexpr int sf_row(int n) {
     return n >= 256 ? padded(n) + ((4 - padded(n) % 16 + 16) % 16) : sf_lane_fastest(n);
 }
 
-template <typename T, int N, int R, int DIR, class Src, class Dst>
+template <typename T, int N, int EMAX, int R, int DIR, class Src, class Dst>
 __device__ __forceinline__ void stockham_pass(Src src, Dst dst, int logP, int lane,
                                               const cplx<T> *__restrict__ tw) {
     constexpr int LOGR = R == 1 ? 0 : R == 2 ? 1 : R == 4 ? 2 : R == 8 ? 3 : 4;
-    constexpr int TPF = FftShape<N>::TPF;
+    constexpr int TPF = FftShape<N, EMAX>::TPF;
     constexpr int STRIDE = N / R;
     constexpr int BPT = STRIDE / TPF;            // butterflies per thread
     const int P = 1 << logP;
-    const int twshift = FftShape<N>::LOG - logP - LOGR;
+    const int twshift = FftShape<N, EMAX>::LOG - logP - LOGR;
 #pragma unroll 1
     for (int s = 0; s < BPT; ++s) {
         const int i = lane + s * TPF;
@@ -216,35 +217,36 @@ __device__ __forceinline__ void stockham_pass(Src src, Dst dst, int logP, int la
 // FFT's slices; src may read b1 but never b0.  Every thread of the CTA must
 // call it (it synchronises the CTA between passes); threads with
 // active = false only take part in the barriers.
-template <typename T, int N, int DIR, class Src, class Sink>
+template <typename T, int N, int EMAX, int DIR, class Src, class Sink>
 __device__ __forceinline__ int fft_run(Src src, Sink sink, cplx<T> *b0, cplx<T> *b1, int lane, bool active,
                                        const cplx<T> *__restrict__ tw) {
-    using S = FftShape<N>;
+    using S = FftShape<N, EMAX>;
     if constexpr (N == 1) {
         if (active) sink(0, src(0), b0);
         return 0;
-    } else if constexpr (S::LOG <= 4) {
-        if (active) stockham_pass<T, N, S::R0, DIR>(src, [&](int p, cplx<T> v) { sink(p, v, b0); }, 0, lane, tw);
+    } else if constexpr (S::LOG <= S::LOGE) {
+        if (active) stockham_pass<T, N, EMAX, S::R0, DIR>(src, [&](int p, cplx<T> v) { sink(p, v, b0); }, 0, lane, tw);
         return 0;
     } else {
+        constexpr int E = S::E, LOGE = S::LOGE;
         if (active)
-            stockham_pass<T, N, S::R0, DIR>(src, [&](int p, cplx<T> v) { b0[spad(p)] = v; }, 0, lane, tw);
+            stockham_pass<T, N, EMAX, S::R0, DIR>(src, [&](int p, cplx<T> v) { b0[spad(p)] = v; }, 0, lane, tw);
         __syncthreads();
         cplx<T> *cur = b0, *nxt = b1;
         int which = 1;
-        int logP = S::LOG % 4 == 0 ? 4 : S::LOG % 4;
+        int logP = ilog2(S::R0);
 #pragma unroll 1
-        for (; logP + 4 < S::LOG; logP += 4) {
+        for (; logP + LOGE < S::LOG; logP += LOGE) {
             if (active)
-                stockham_pass<T, N, 16, DIR>([&](int p) { return cur[spad(p)]; },
-                                             [&](int p, cplx<T> v) { nxt[spad(p)] = v; }, logP, lane, tw);
+                stockham_pass<T, N, EMAX, E, DIR>([&](int p) { return cur[spad(p)]; },
+                                            [&](int p, cplx<T> v) { nxt[spad(p)] = v; }, logP, lane, tw);
             __syncthreads();
             cplx<T> *tmp = cur; cur = nxt; nxt = tmp;
             which ^= 1;
         }
         if (active)
-            stockham_pass<T, N, 16, DIR>([&](int p) { return cur[spad(p)]; },
-                                         [&](int p, cplx<T> v) { sink(p, v, nxt); }, logP, lane, tw);
+            stockham_pass<T, N, EMAX, E, DIR>([&](int p) { return cur[spad(p)]; },
+                                        [&](int p, cplx<T> v) { sink(p, v, nxt); }, logP, lane, tw);
         return which;
     }
 }

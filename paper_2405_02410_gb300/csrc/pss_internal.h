@@ -81,6 +81,7 @@ template <typename T> struct ColArgs {
     const long long *d_step;
     int *d_status;
     int mode, tiles_per_cta, n_tiles;
+    int E;                // FFT radix cap (8 or 16), chosen by the host
     int F;                // FFTs per CTA = tiles_per_cta * kTileW * (2 in 3D, else 1); a power of two
     // adjoint (COL_ADJ_A): the forward state after the step, its noise step, and
     // the FP64 gradient sums [slot][11] (dO_0..4, dM_0..4, sum Re(conj(mu) xi))
@@ -102,6 +103,7 @@ template <typename T> struct RowArgs {
     long long *d_step;
     int *d_status;
     int mode, G, inc_step;
+    int E;                // FFT radix cap (8 or 16)
 };
 
 template <typename T> struct MidArgs {
@@ -115,6 +117,7 @@ template <typename T> struct MidArgs {
     long long *d_step;
     int *d_status;
     int mode, PZ, inc_step;
+    int E;                // FFT radix cap (8 or 16)
 };
 
 // Launch configuration chosen by the host.
@@ -122,10 +125,22 @@ struct ColCfg { int tiles_per_cta; };
 struct RowCfg { int G; };
 struct MidCfg { int PZ; };
 
-// Launchers (one instantiation per precision; defined in pss_kern_f32.cu / pss_kern_f64.cu).
-template <typename T> cudaError_t launch_col(const ColArgs<T> &a, int nslots, int grid_x, int grid_y, cudaStream_t st);
-template <typename T> cudaError_t launch_row(const RowArgs<T> &a, int nslots, cudaStream_t st);
-template <typename T> cudaError_t launch_mid(const MidArgs<T> &a, int nslots, int n_tiles, cudaStream_t st);
+// Launchers of the step kernels, one instantiation per precision and FFT
+// radix cap EMAX (pss_kern_{f32,f64}.cu: 8, pss_kern_{f32,f64}_r16.cu: 16).
+template <typename T, int EMAX>
+cudaError_t launch_col_e(const ColArgs<T> &a, int nslots, int grid_x, int grid_y, cudaStream_t st);
+template <typename T, int EMAX> cudaError_t launch_row_e(const RowArgs<T> &a, int nslots, cudaStream_t st);
+template <typename T, int EMAX> cudaError_t launch_mid_e(const MidArgs<T> &a, int nslots, int n_tiles, cudaStream_t st);
+template <typename T>
+inline cudaError_t launch_col(const ColArgs<T> &a, int nslots, int grid_x, int grid_y, cudaStream_t st) {
+    return a.E == 16 ? launch_col_e<T, 16>(a, nslots, grid_x, grid_y, st) : launch_col_e<T, 8>(a, nslots, grid_x, grid_y, st);
+}
+template <typename T> inline cudaError_t launch_row(const RowArgs<T> &a, int nslots, cudaStream_t st) {
+    return a.E == 16 ? launch_row_e<T, 16>(a, nslots, st) : launch_row_e<T, 8>(a, nslots, st);
+}
+template <typename T> inline cudaError_t launch_mid(const MidArgs<T> &a, int nslots, int n_tiles, cudaStream_t st) {
+    return a.E == 16 ? launch_mid_e<T, 16>(a, nslots, n_tiles, st) : launch_mid_e<T, 8>(a, nslots, n_tiles, st);
+}
 template <typename T> cudaError_t launch_init_uniform(T *real, long long nsites, double lo, double hi,
                                                       uint64_t seed, int field_id, cudaStream_t st);
 template <typename T> cudaError_t launch_tiles_to_half(const SysP<T> &sp, const cplx<T> *tiles,
@@ -139,8 +154,18 @@ template <typename T> cudaError_t launch_structure_factor(const SysP<T> &sp, con
                                                           double *acc /* 2*nbins + 2 */, cudaStream_t st);
 
 // FFT shape helpers visible to the host
-inline int fft_E(int n) { return n < 16 ? n : 16; }
-inline int fft_TPF(int n) { return n / fft_E(n); }
+__host__ __device__ constexpr int ilog2(int n) { return n <= 1 ? 0 : 1 + ilog2(n >> 1); }
+// Values per thread and pass of a length-n FFT (the radix of its main
+// passes) when a kernel runs its FFTs with at most emax (8 or 16) values per
+// thread: radix 16 means fewer passes, radix 8 twice the threads per FFT.
+__host__ __device__ constexpr int fft_E(int n, int emax) { return n < emax ? n : emax; }
+__host__ __device__ constexpr int fft_TPF(int n, int emax) { return n / fft_E(n, emax); }
+// threads of a column-kernel CTA with F FFTs: two per FFT lane where that
+// stays within 512 (the element-wise phases use them all), at least a warp
+__host__ __device__ constexpr int col_threads(int n, int emax, int F) {
+    return 2 * F * fft_TPF(n, emax) <= 512 ? (2 * F * fft_TPF(n, emax) < 32 ? 32 : 2 * F * fft_TPF(n, emax))
+                                            : F * fft_TPF(n, emax);
+}
 inline int fft_smem_elems_h(int n, int F) { return (n + n / 16) * F; }
 
 }  // namespace pss

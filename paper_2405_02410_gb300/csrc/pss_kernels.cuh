@@ -119,7 +119,7 @@ __device__ __forceinline__ cplx<T> update_mode(cplx<T> phi, cplx<T> P, cplx<T> x
 //       Hermitian part on the kx = 0, Nx/2 planes.
 // Inner products run over the full Hermitian set: weight 2 for 0 < kx < Nx/2.
 // ---------------------------------------------------------------------------
-template <typename T, int N>
+template <typename T, int N, int EMAX>
 __device__ __forceinline__ void col_adjoint(const ColArgs<T> &a, const FieldP<T> &fp, cplx<T> *PHI, const cplx<T> *P,
                                             cplx<T> *X, cplx<T> *Y, int which, int F, int SF, int nchunks,
                                             int lognch, int first_tile, int op, int opp, int logNP, size_t sofs,
@@ -244,7 +244,7 @@ __device__ __forceinline__ void col_adjoint(const ColArgs<T> &a, const FieldP<T>
         const bool writes = chunk_writes(ch);
         C *nb = NU + f * SF;
         C *other = (NU == X ? Y : X) + f * SF;
-        fft_run<T, N, +1>([&](int p) { return nb[spad(p)]; },
+        fft_run<T, N, EMAX, +1>([&](int p) { return nb[spad(p)]; },
                           [&](int p, C v, C *) {
                               if (writes) dst[p * W] = v;
                           },
@@ -264,13 +264,13 @@ template <typename T, int N> struct ColSmem {
     }
 };
 
-template <typename T, int N, bool ADJ>
+template <typename T, int N, int EMAX, bool ADJ>
 __global__ void __launch_bounds__(512, N >= 512 ? 1 : 2) k_col(const ColArgs<T> a) {
     using C = cplx<T>;
     using L = ColSmem<T, N>;
-    constexpr int TPF = FftShape<N>::TPF;
+    constexpr int TPF = FftShape<N, EMAX>::TPF;
     constexpr int CS = L::CS;
-    constexpr int LOGNW = FftShape<N>::LOG + 2;                 // log2(N W)
+    constexpr int LOGNW = FftShape<N, EMAX>::LOG + 2;                 // log2(N W)
     extern __shared__ __align__(128) unsigned char smem_raw[];
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw);
     const int F = a.F;                                           // a power of two, multiple of W
@@ -283,7 +283,11 @@ __global__ void __launch_bounds__(512, N >= 512 ? 1 : 2) k_col(const ColArgs<T> 
     C *Y = X + L::xs(F);
     const SysP<T> &sp = a.sp;
     const int slot = a.slot0 + blockIdx.z;
-    const FieldP<T> &fp = a.fps[slot];
+    // the slot's parameters and the step number, fetched into shared memory
+    // while the bulk copies are in flight
+    __shared__ FieldP<T> sfp;
+    __shared__ uint32_t sstep;
+    const FieldP<T> &fp = sfp;
     const size_t sofs = (size_t)slot * a.slot_stride;
     const int logNP = sp.dim == 3 ? 1 : 0;
     const int t = threadIdx.x, nthr = blockDim.x;
@@ -317,6 +321,10 @@ __global__ void __launch_bounds__(512, N >= 512 ? 1 : 2) k_col(const ColArgs<T> 
             if (need_in) bulk_g2s(X + ch * CS, a.in + sofs + gofs(ch), chunk_bytes, bar);
         }
     }
+    static_assert(sizeof(FieldP<T>) % 4 == 0, "FieldP is copied as 32-bit words");
+    if (t < (int)(sizeof(FieldP<T>) / 4))
+        reinterpret_cast<uint32_t *>(&sfp)[t] = reinterpret_cast<const uint32_t *>(&a.fps[slot])[t];
+    if (t == 0) sstep = (uint32_t)(*a.d_step);
     __syncthreads();   // the barrier is initialised before anyone polls it
     for (int i = nvalid * (N * W) + t; i < nchunks * (N * W); i += nthr) {   // chunks past the last tile read as zero
         const int ch = i >> LOGNW, r = i & (N * W - 1);
@@ -335,17 +343,17 @@ __global__ void __launch_bounds__(512, N >= 512 ? 1 : 2) k_col(const ColArgs<T> 
     if (need_in) {
         // forward transform along this axis: P_q
         const C *xb = X + ch * CS + c;
-        const int which = fft_run<T, N, -1>([&](int p) { return xb[p * W]; },
+        const int which = fft_run<T, N, EMAX, -1>([&](int p) { return xb[p * W]; },
                                             [&](int p, C v, C *fr) { fr[spad(p)] = v; },
                                             Y + f * SF, X + f * SF, lane, active, tw);
         __syncthreads();
         const C *P = which == 0 ? Y : X;
         if constexpr (ADJ) {
-            col_adjoint<T, N>(a, fp, PHI, P, X, Y, which, F, SF, nchunks, lognch, first_tile, op, opp, logNP, sofs,
+            col_adjoint<T, N, EMAX>(a, fp, PHI, P, X, Y, which, F, SF, nchunks, lognch, first_tile, op, opp, logNP, sofs,
                               ch, c, f, lane, active, tw);
             return;
         }
-        const uint32_t step = (uint32_t)(*a.d_step);
+        const uint32_t step = sstep;
         // update: each thread keeps one pair of neighbouring columns (they share
         // one Philox draw) of one chunk and walks the positions
         const int cp = t & 1, chq = (t >> 1) & (nchunks - 1);
@@ -397,15 +405,26 @@ __global__ void __launch_bounds__(512, N >= 512 ? 1 : 2) k_col(const ColArgs<T> 
         if (bad && a.d_status) atomicOr(a.d_status, kStatusNonFinite);
         __syncthreads();
         // Hermitian part on the kx = 0 and kx = Nx/2 planes (the field is real):
-        // phi(kx, k) <- (phi(kx, k) + conj phi(kx, -k)) / 2, each pair by one thread
-        const int last_tile = first_tile + a.tiles_per_cta;
-        if (first_tile == 0 || (first_tile * W <= sp.nx / 2 && sp.nx / 2 < last_tile * W)) {
+        // phi(kx, k) <- (phi(kx, k) + conj phi(kx, -k)) / 2, each pair by one thread.
+        // The CTA holds at most these two plane columns (chunk of the first
+        // pencil, column within the chunk); the partner of position pos sits at
+        // -pos of the same chunk (2D) or of the partner pencil's chunk (3D).
+        int pl_cq0 = 0, pl_cc0 = 0, pl_cq1 = 0, pl_cc1 = 0, npl = 0;
+        if (first_tile == 0) ++npl;
+        {
+            const int kh = sp.nx / 2, last_tile = first_tile + a.tiles_per_cta;
+            if (kh > 0 && first_tile * W <= kh && kh < last_tile * W) {
+                const int cqh = (kh / W - first_tile) << logNP, cch = kh & (W - 1);
+                if (npl == 0) { pl_cq0 = cqh; pl_cc0 = cch; } else { pl_cq1 = cqh; pl_cc1 = cch; }
+                ++npl;
+            }
+        }
+        if (npl > 0) {
+            constexpr int LOGN = FftShape<N, EMAX>::LOG;
 #pragma unroll 1
-            for (int i = t; i < N * F; i += nthr) {
-                const int pos = i >> logF, ff = i & (F - 1);
-                const int cq = ff >> 2, cc = ff & 3;
-                const int kq = chunk_tile(cq) * W + cc;
-                if (!(kq == 0 || 2 * kq == sp.nx) || (cq & logNP) != 0) continue;
+            for (int i = t; i < (npl << LOGN); i += nthr) {
+                const int j = i >> LOGN, pos = i & (N - 1);
+                const int cq = j ? pl_cq1 : pl_cq0, cc = j ? pl_cc1 : pl_cc0;
                 const int ppos = (N - pos) & (N - 1);
                 if (logNP == 0 && ppos < pos) continue;
                 C *p0 = &PHI[cq * CS + pos * W + cc];
@@ -448,7 +467,7 @@ __global__ void __launch_bounds__(512, N >= 512 ? 1 : 2) k_col(const ColArgs<T> 
         const C *pb = PHI + ch * CS + c;
         const bool writes = chunk_writes(ch) && (full || my_tile * W <= fp.kmax[0]);
         C *__restrict__ dst = a.out + sofs + gofs(ch) + c;
-        fft_run<T, N, +1>(
+        fft_run<T, N, EMAX, +1>(
             [&](int p) { return abs(signed_k(p, N)) <= kmax_pos ? cscale<T>(pb[p * W], scale) : mk<T>(0, 0); },
             [&](int p, C v, C *) {
                 if (writes) dst[p * W] = v;
@@ -494,13 +513,13 @@ template <typename T, int N> struct RowSmem {
     }
 };
 
-template <typename T, int N>
+template <typename T, int N, int EMAX>
 __global__ void __launch_bounds__(256) k_row(const RowArgs<T> a) {
     using C = cplx<T>;
     using L = RowSmem<T, N>;
-    constexpr int TPF = FftShape<N>::TPF;
+    constexpr int TPF = FftShape<N, EMAX>::TPF;
     constexpr int SF = sf_row(N);
-    constexpr int LOGTPF = FftShape<N>::LOG - (N < 16 ? FftShape<N>::LOG : 4);
+    constexpr int LOGTPF = FftShape<N, EMAX>::LOG - FftShape<N, EMAX>::LOGE;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw);
     const SysP<T> &sp = a.sp;
@@ -562,12 +581,12 @@ __global__ void __launch_bounds__(256) k_row(const RowArgs<T> a) {
     auto smem_sink = [&](int p, C v, C *fr) { fr[spad(p)] = v; };
     const C *R;          // this CTA's result buffer (B0 or B1)
     if (mode == ROW_R2C) {
-        const int which = fft_run<T, N, -1>([&](int p) { return mk<T>(Sr[g * N + p], Sr[(G + g) * N + p]); },
+        const int which = fft_run<T, N, EMAX, -1>([&](int p) { return mk<T>(Sr[g * N + p], Sr[(G + g) * N + p]); },
                                             smem_sink, b0, b1, lane, active, tw);
         R = which == 0 ? B0 : B1;
     } else {
         const int kxc = (mode == ROW_FUSED || mode == ROW_C2R_KEPT) ? fp.kx_cols : sp.hx;
-        const int which = fft_run<T, N, +1>(
+        const int which = fft_run<T, N, EMAX, +1>(
             [&](int k) {
                 const int kk = k <= N / 2 ? k : N - k;
                 C xa = mk<T>(0, 0), xb = mk<T>(0, 0);
@@ -597,7 +616,7 @@ __global__ void __launch_bounds__(256) k_row(const RowArgs<T> a) {
         const int p = fp.power;
         C *zf = Z + g * SF;
         C *other = (which == 0 ? B1 : B0) + g * SF;
-        const int which2 = fft_run<T, N, -1>(
+        const int which2 = fft_run<T, N, EMAX, -1>(
             [&](int k) {
                 const C z = zf[spad(k)];
                 return mk<T>(ipow<T>(z.x, p), ipow<T>(z.y, p));
@@ -642,11 +661,11 @@ template <typename T, int N> struct MidSmem {
     }
 };
 
-template <typename T, int N>
+template <typename T, int N, int EMAX>
 __global__ void __launch_bounds__(256) k_mid(const MidArgs<T> a) {
     using C = cplx<T>;
     using L = MidSmem<T, N>;
-    constexpr int TPF = FftShape<N>::TPF;
+    constexpr int TPF = FftShape<N, EMAX>::TPF;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw);
     const SysP<T> &sp = a.sp;
@@ -691,8 +710,8 @@ __global__ void __launch_bounds__(256) k_mid(const MidArgs<T> a) {
     auto src_f = [&](int p) { return S[p * F + f]; };
     auto sink = [&](int p, C v, C *) { dst[p * ostride] = v; };
     const C *__restrict__ tw = TW;
-    if (a.mode == MID_FWD) fft_run<T, N, -1>(src_f, sink, B0 + f * SF, S + f * SF, lane, active, tw);
-    else fft_run<T, N, +1>(src_f, sink, B0 + f * SF, S + f * SF, lane, active, tw);
+    if (a.mode == MID_FWD) fft_run<T, N, EMAX, -1>(src_f, sink, B0 + f * SF, S + f * SF, lane, active, tw);
+    else fft_run<T, N, EMAX, +1>(src_f, sink, B0 + f * SF, S + f * SF, lane, active, tw);
     if (a.inc_step && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && t == 0) *a.d_step += 1;
 }
 
@@ -814,80 +833,85 @@ template <class K> cudaError_t ensure_smem(K kernel, size_t smem) {
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
-template <typename T, int N> cudaError_t launch_col_n(const ColArgs<T> &a, int nf, int gx, int gy, cudaStream_t st) {
-    const int threads = 2 * a.F * FftShape<N>::TPF < 32 ? 32 : 2 * a.F * FftShape<N>::TPF;
+template <typename T, int N, int EMAX>
+cudaError_t launch_col_n(const ColArgs<T> &a, int nf, int gx, int gy, cudaStream_t st) {
+    const int threads = col_threads(N, EMAX, a.F);
     const size_t smem = ColSmem<T, N>::bytes(a.F);
-    if (threads > 512 || (a.F & (a.F - 1)) != 0 || a.F % W != 0) return cudaErrorInvalidConfiguration;
+    if (a.F * FftShape<N, EMAX>::TPF > 512 || (a.F & (a.F - 1)) != 0 || a.F % W != 0)
+        return cudaErrorInvalidConfiguration;
     const bool adj = a.mode == COL_ADJ_A || a.mode == COL_ADJ_B;
-    cudaError_t e = adj ? ensure_smem(k_col<T, N, true>, smem) : ensure_smem(k_col<T, N, false>, smem);
+    cudaError_t e = adj ? ensure_smem(k_col<T, N, EMAX, true>, smem) : ensure_smem(k_col<T, N, EMAX, false>, smem);
     if (e != cudaSuccess) return e;
-    if (adj) return launch_pdl(k_col<T, N, true>, dim3(gx, gy, nf), threads, smem, st, a);
-    return launch_pdl(k_col<T, N, false>, dim3(gx, gy, nf), threads, smem, st, a);
+    if (adj) return launch_pdl(k_col<T, N, EMAX, true>, dim3(gx, gy, nf), threads, smem, st, a);
+    return launch_pdl(k_col<T, N, EMAX, false>, dim3(gx, gy, nf), threads, smem, st, a);
 }
 
-template <typename T> cudaError_t launch_col(const ColArgs<T> &a, int nf, int gx, int gy, cudaStream_t st) {
+template <typename T, int EMAX>
+cudaError_t launch_col_e(const ColArgs<T> &a, int nf, int gx, int gy, cudaStream_t st) {
     switch (a.sp.n_inner) {
-        case 1: return launch_col_n<T, 1>(a, nf, gx, gy, st);
-        case 4: return launch_col_n<T, 4>(a, nf, gx, gy, st);
-        case 8: return launch_col_n<T, 8>(a, nf, gx, gy, st);
-        case 16: return launch_col_n<T, 16>(a, nf, gx, gy, st);
-        case 32: return launch_col_n<T, 32>(a, nf, gx, gy, st);
-        case 64: return launch_col_n<T, 64>(a, nf, gx, gy, st);
-        case 128: return launch_col_n<T, 128>(a, nf, gx, gy, st);
-        case 256: return launch_col_n<T, 256>(a, nf, gx, gy, st);
-        case 512: return launch_col_n<T, 512>(a, nf, gx, gy, st);
-        case 1024: return launch_col_n<T, 1024>(a, nf, gx, gy, st);
+        case 1: return launch_col_n<T, 1, EMAX>(a, nf, gx, gy, st);
+        case 4: return launch_col_n<T, 4, EMAX>(a, nf, gx, gy, st);
+        case 8: return launch_col_n<T, 8, EMAX>(a, nf, gx, gy, st);
+        case 16: return launch_col_n<T, 16, EMAX>(a, nf, gx, gy, st);
+        case 32: return launch_col_n<T, 32, EMAX>(a, nf, gx, gy, st);
+        case 64: return launch_col_n<T, 64, EMAX>(a, nf, gx, gy, st);
+        case 128: return launch_col_n<T, 128, EMAX>(a, nf, gx, gy, st);
+        case 256: return launch_col_n<T, 256, EMAX>(a, nf, gx, gy, st);
+        case 512: return launch_col_n<T, 512, EMAX>(a, nf, gx, gy, st);
+        case 1024: return launch_col_n<T, 1024, EMAX>(a, nf, gx, gy, st);
         default: return cudaErrorInvalidValue;
     }
 }
 
-template <typename T, int N> cudaError_t launch_row_n(const RowArgs<T> &a, int nf, cudaStream_t st) {
+template <typename T, int N, int EMAX> cudaError_t launch_row_n(const RowArgs<T> &a, int nf, cudaStream_t st) {
     const int G = a.G;
-    const int threads = G * FftShape<N>::TPF < 32 ? 32 : G * FftShape<N>::TPF;
+    const int threads = G * FftShape<N, EMAX>::TPF < 32 ? 32 : G * FftShape<N, EMAX>::TPF;
     const size_t smem = RowSmem<T, N>::bytes(G, a.sp.ntiles);
     if (threads > 256 || (G & (G - 1)) != 0) return cudaErrorInvalidConfiguration;
-    cudaError_t e = ensure_smem(k_row<T, N>, smem);
+    cudaError_t e = ensure_smem(k_row<T, N, EMAX>, smem);
     if (e != cudaSuccess) return e;
     const int grid = (a.sp.rows + 2 * G - 1) / (2 * G);
-    return launch_pdl(k_row<T, N>, dim3(grid, nf), threads, smem, st, a);
+    return launch_pdl(k_row<T, N, EMAX>, dim3(grid, nf), threads, smem, st, a);
 }
 
-template <typename T> cudaError_t launch_row(const RowArgs<T> &a, int nf, cudaStream_t st) {
+template <typename T, int EMAX> cudaError_t launch_row_e(const RowArgs<T> &a, int nf, cudaStream_t st) {
     switch (a.sp.nx) {
-        case 4: return launch_row_n<T, 4>(a, nf, st);
-        case 8: return launch_row_n<T, 8>(a, nf, st);
-        case 16: return launch_row_n<T, 16>(a, nf, st);
-        case 32: return launch_row_n<T, 32>(a, nf, st);
-        case 64: return launch_row_n<T, 64>(a, nf, st);
-        case 128: return launch_row_n<T, 128>(a, nf, st);
-        case 256: return launch_row_n<T, 256>(a, nf, st);
-        case 512: return launch_row_n<T, 512>(a, nf, st);
-        case 1024: return launch_row_n<T, 1024>(a, nf, st);
+        case 4: return launch_row_n<T, 4, EMAX>(a, nf, st);
+        case 8: return launch_row_n<T, 8, EMAX>(a, nf, st);
+        case 16: return launch_row_n<T, 16, EMAX>(a, nf, st);
+        case 32: return launch_row_n<T, 32, EMAX>(a, nf, st);
+        case 64: return launch_row_n<T, 64, EMAX>(a, nf, st);
+        case 128: return launch_row_n<T, 128, EMAX>(a, nf, st);
+        case 256: return launch_row_n<T, 256, EMAX>(a, nf, st);
+        case 512: return launch_row_n<T, 512, EMAX>(a, nf, st);
+        case 1024: return launch_row_n<T, 1024, EMAX>(a, nf, st);
         default: return cudaErrorInvalidValue;
     }
 }
 
-template <typename T, int N> cudaError_t launch_mid_n(const MidArgs<T> &a, int nf, int n_tiles, cudaStream_t st) {
+template <typename T, int N, int EMAX>
+cudaError_t launch_mid_n(const MidArgs<T> &a, int nf, int n_tiles, cudaStream_t st) {
     const int F = a.PZ * W;
-    const int threads = F * FftShape<N>::TPF < 32 ? 32 : F * FftShape<N>::TPF;
+    const int threads = F * FftShape<N, EMAX>::TPF < 32 ? 32 : F * FftShape<N, EMAX>::TPF;
     const size_t smem = MidSmem<T, N>::bytes(F);
     if (threads > 256 || (F & (F - 1)) != 0) return cudaErrorInvalidConfiguration;
-    cudaError_t e = ensure_smem(k_mid<T, N>, smem);
+    cudaError_t e = ensure_smem(k_mid<T, N, EMAX>, smem);
     if (e != cudaSuccess) return e;
-    return launch_pdl(k_mid<T, N>, dim3(n_tiles, a.sp.nz / a.PZ, nf), threads, smem, st, a);
+    return launch_pdl(k_mid<T, N, EMAX>, dim3(n_tiles, a.sp.nz / a.PZ, nf), threads, smem, st, a);
 }
 
-template <typename T> cudaError_t launch_mid(const MidArgs<T> &a, int nf, int n_tiles, cudaStream_t st) {
+template <typename T, int EMAX>
+cudaError_t launch_mid_e(const MidArgs<T> &a, int nf, int n_tiles, cudaStream_t st) {
     switch (a.sp.ny) {
-        case 4: return launch_mid_n<T, 4>(a, nf, n_tiles, st);
-        case 8: return launch_mid_n<T, 8>(a, nf, n_tiles, st);
-        case 16: return launch_mid_n<T, 16>(a, nf, n_tiles, st);
-        case 32: return launch_mid_n<T, 32>(a, nf, n_tiles, st);
-        case 64: return launch_mid_n<T, 64>(a, nf, n_tiles, st);
-        case 128: return launch_mid_n<T, 128>(a, nf, n_tiles, st);
-        case 256: return launch_mid_n<T, 256>(a, nf, n_tiles, st);
-        case 512: return launch_mid_n<T, 512>(a, nf, n_tiles, st);
-        case 1024: return launch_mid_n<T, 1024>(a, nf, n_tiles, st);
+        case 4: return launch_mid_n<T, 4, EMAX>(a, nf, n_tiles, st);
+        case 8: return launch_mid_n<T, 8, EMAX>(a, nf, n_tiles, st);
+        case 16: return launch_mid_n<T, 16, EMAX>(a, nf, n_tiles, st);
+        case 32: return launch_mid_n<T, 32, EMAX>(a, nf, n_tiles, st);
+        case 64: return launch_mid_n<T, 64, EMAX>(a, nf, n_tiles, st);
+        case 128: return launch_mid_n<T, 128, EMAX>(a, nf, n_tiles, st);
+        case 256: return launch_mid_n<T, 256, EMAX>(a, nf, n_tiles, st);
+        case 512: return launch_mid_n<T, 512, EMAX>(a, nf, n_tiles, st);
+        case 1024: return launch_mid_n<T, 1024, EMAX>(a, nf, n_tiles, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -934,10 +958,14 @@ cudaError_t launch_structure_factor(const SysP<T> &sp, const double dx[3], const
     return cudaGetLastError();
 }
 
-#define PSS_INSTANTIATE(T)                                                                                   \
-    template cudaError_t launch_col<T>(const ColArgs<T> &, int, int, int, cudaStream_t);                     \
-    template cudaError_t launch_row<T>(const RowArgs<T> &, int, cudaStream_t);                               \
-    template cudaError_t launch_mid<T>(const MidArgs<T> &, int, int, cudaStream_t);                          \
+// the step kernels of one precision and FFT radix cap
+#define PSS_INSTANTIATE_STEP(T, EMAX)                                                                       \
+    template cudaError_t launch_col_e<T, EMAX>(const ColArgs<T> &, int, int, int, cudaStream_t);           \
+    template cudaError_t launch_row_e<T, EMAX>(const RowArgs<T> &, int, cudaStream_t);                     \
+    template cudaError_t launch_mid_e<T, EMAX>(const MidArgs<T> &, int, int, cudaStream_t);
+
+// the auxiliary kernels of one precision
+#define PSS_INSTANTIATE_AUX(T)                                                                               \
     template cudaError_t launch_init_uniform<T>(T *, long long, double, double, uint64_t, int, cudaStream_t); \
     template cudaError_t launch_tiles_to_half<T>(const SysP<T> &, const cplx<T> *, cplx<T> *, cudaStream_t); \
     template cudaError_t launch_half_to_tiles<T>(const SysP<T> &, const cplx<T> *, cplx<T> *, cudaStream_t); \

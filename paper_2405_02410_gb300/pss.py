@@ -265,7 +265,8 @@ class System:
         return list(out)
 
     def set_tuning(self, key: str, value: int):
-        """Launch-shape knob ("pdl", "row_pairs", "col_tiles", "mid_planes", "graph_steps"); 0 = automatic."""
+        """Launch-shape knob ("pdl", "row_pairs", "col_tiles", "mid_planes", "graph_steps", "col_radix",
+        "row_radix", "mid_radix"); 0 = automatic."""
         self._ck(lib.pss_set_tuning(self._h, key.encode(), int(value)))
 
     def adjoint_forward(self, n: int):

@@ -229,8 +229,10 @@ def test_model_b_1024_sampled_against_oracle():
     dict(row_pairs=1), dict(row_pairs=2), dict(row_pairs=4), dict(row_pairs=8),
     dict(mid_planes=1), dict(mid_planes=2), dict(mid_planes=4), dict(col_tiles=2), dict(col_tiles=4),
     dict(pdl=1), dict(row_pairs=2, mid_planes=4, pdl=1),
+    dict(col_radix=8, row_radix=8, mid_radix=8), dict(col_radix=16, row_radix=16, mid_radix=16),
+    dict(col_radix=8, row_radix=16, mid_radix=8, row_pairs=2),
 ])
-@pytest.mark.parametrize("shape", [(16, 32, 32), (8, 64, 16), (64, 128)])
+@pytest.mark.parametrize("shape", [(16, 32, 32), (8, 64, 16), (64, 128), (1024, 32), (32, 1024)])
 def test_launch_shapes_do_not_change_results(shape, knobs):
     # every launch-shape knob must give the oracle's result (Model A + B pair)
     steps = 12
