@@ -343,6 +343,8 @@ template <typename T> struct Seq {
         a.mode = mode;
         a.E = row_emax(s);
         a.G = row_G(s);
+        a.kx_cols_max = 0;
+        for (int i = 0; i < (int)s->fields.size(); ++i) a.kx_cols_max = std::max(a.kx_cols_max, kept_cols(s, i));
         a.inc_step = inc ? 1 : 0;
         if (timer) timer->begin(2, st);
         cudaError_t e = launch_row<T>(a, nslots, st);
@@ -651,14 +653,20 @@ int do_create(pss_system **out, int batch, int dim, int nx, int ny, int nz, doub
     if (e == cudaSuccess) e = cudaMalloc(&s->d_status, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(s->d_step, 0, sizeof(long long));
     if (e == cudaSuccess) e = cudaMemset(s->d_status, 0, sizeof(int));
-    // roots of unity exp(-2 pi i m / n) for every transform length n = 1, 2, ..., 1024,
-    // the table of length n at offset n; built in FP64 on the host
+    // twiddle tables of every transform length and radix cap, built in FP64 on the host
     if (e == cudaSuccess) {
         const int total = kTwiddleEntries;
         std::vector<double2> h(total, make_double2(0.0, 0.0));
-        for (int n = 1; n <= kMaxFftN; n *= 2)
-            for (int m = 0; m < n; ++m)
-                h[twiddle_offset(n) + m] = make_double2(std::cos(2 * kPi * m / n), -std::sin(2 * kPi * m / n));
+        for (int emax : {8, 16})
+            for (int n = 2; n <= kMaxFftN; n *= 2) {
+                const int E = fft_E(n, emax);
+                for (int P = E, R = std::min(E, n / P); P < n; P *= R, R = std::min(E, n / P))
+                    for (int r = 1; r < R; ++r)
+                        for (int k = 0; k < P; ++k) {
+                            const double a = 2 * kPi * (double)(r * k) / (double)(P * R);
+                            h[twiddle_offset(n, emax) + (P - E) + (r - 1) * P + k] = make_double2(std::cos(a), -std::sin(a));
+                        }
+            }
         if (precision == PSS_F64) {
             e = cudaMalloc(&s->tw, sizeof(double2) * total);
             if (e == cudaSuccess) e = cudaMemcpy(s->tw, h.data(), sizeof(double2) * total, cudaMemcpyHostToDevice);

@@ -140,8 +140,8 @@ template <int R, int DIR, typename T> __device__ __forceinline__ void dft_reg(cp
 // Stockham radix-R pass with P = product of the radices already done:
 // butterfly i (0 <= i < N/R) reads x[i + r N/R], multiplies by
 // exp(DIR 2 pi i r k / (P R)) with k = i mod P, transforms over r, and writes
-// y[(i / P) P R + k + r P].  N = R0 * 16^m: one radix-R0 pass, then m radix-16
-// passes that share one loop body.  The first pass reads through a source
+// y[(i / P) P R + k + r P].  N = E^m * RL: m radix-E passes (E = 8 or 16; the
+// middle ones share one loop body), then one radix-RL pass.  The first pass reads through a source
 // functor and the last pass writes through a sink functor, so that
 // element-wise work (a power, a mask, a scale, a store to global memory)
 // rides on the loads and stores the transform makes anyway.
@@ -152,8 +152,10 @@ template <int N, int EMAX> struct FftShape {
     static constexpr int TPF = N / E;           // threads per FFT
     static constexpr int LOG = ilog2(N);
     static constexpr int LOGE = ilog2(E);
-    // N = R0 * E^m: the first pass has radix R0, the others radix E
-    static constexpr int R0 = N <= 1 ? 1 : (LOG % LOGE == 0 ? E : 1 << (LOG % LOGE));
+    // N = E^m * RL: radix-E passes, then a last pass of radix RL <= E (a
+    // small radix last keeps every pass's shared-memory stores conflict-free)
+    static constexpr int RL = N <= 1 ? 1 : (LOG % LOGE == 0 ? E : 1 << (LOG % LOGE));
+    static constexpr int LOGRL = ilog2(RL);
 };
 
 __device__ __forceinline__ int spad(int pos) { return pos + (pos >> 4); }
@@ -185,7 +187,6 @@ __device__ __forceinline__ void stockham_pass(Src src, Dst dst, int logP, int la
     constexpr int STRIDE = N / R;
     constexpr int BPT = STRIDE / TPF;            // butterflies per thread
     const int P = 1 << logP;
-    const int twshift = FftShape<N, EMAX>::LOG - logP - LOGR;
 #pragma unroll 1
     for (int s = 0; s < BPT; ++s) {
         const int i = lane + s * TPF;
@@ -194,11 +195,12 @@ __device__ __forceinline__ void stockham_pass(Src src, Dst dst, int logP, int la
 #pragma unroll
         for (int r = 0; r < R; ++r) u[r] = src(i + r * STRIDE);
         if (P > 1) {
-            const int kk = k << twshift;
+            // this pass's twiddles exp(-2 pi i r k / (P R)), stored [r - 1][k] from
+            // entry P - E on; consecutive lanes read consecutive entries
+            const cplx<T> *__restrict__ twp = tw + (P - FftShape<N, EMAX>::E) + k;
 #pragma unroll
             for (int r = 1; r < R; ++r) {
-                // exp(DIR 2 pi i r k / (P R)) from the forward table exp(-2 pi i m / N)
-                cplx<T> w = tw[r * kk];
+                cplx<T> w = twp[(r - 1) * P];
                 if (DIR > 0) w.y = -w.y;
                 u[r] = cmul<T>(u[r], w);
             }
@@ -225,18 +227,18 @@ __device__ __forceinline__ int fft_run(Src src, Sink sink, cplx<T> *b0, cplx<T> 
         if (active) sink(0, src(0), b0);
         return 0;
     } else if constexpr (S::LOG <= S::LOGE) {
-        if (active) stockham_pass<T, N, EMAX, S::R0, DIR>(src, [&](int p, cplx<T> v) { sink(p, v, b0); }, 0, lane, tw);
+        if (active) stockham_pass<T, N, EMAX, N, DIR>(src, [&](int p, cplx<T> v) { sink(p, v, b0); }, 0, lane, tw);
         return 0;
     } else {
         constexpr int E = S::E, LOGE = S::LOGE;
         if (active)
-            stockham_pass<T, N, EMAX, S::R0, DIR>(src, [&](int p, cplx<T> v) { b0[spad(p)] = v; }, 0, lane, tw);
+            stockham_pass<T, N, EMAX, E, DIR>(src, [&](int p, cplx<T> v) { b0[spad(p)] = v; }, 0, lane, tw);
         __syncthreads();
         cplx<T> *cur = b0, *nxt = b1;
         int which = 1;
-        int logP = ilog2(S::R0);
+        int logP = LOGE;
 #pragma unroll 1
-        for (; logP + LOGE < S::LOG; logP += LOGE) {
+        for (; logP + S::LOGRL < S::LOG; logP += LOGE) {
             if (active)
                 stockham_pass<T, N, EMAX, E, DIR>([&](int p) { return cur[spad(p)]; },
                                             [&](int p, cplx<T> v) { nxt[spad(p)] = v; }, logP, lane, tw);
@@ -245,8 +247,8 @@ __device__ __forceinline__ int fft_run(Src src, Sink sink, cplx<T> *b0, cplx<T> 
             which ^= 1;
         }
         if (active)
-            stockham_pass<T, N, EMAX, E, DIR>([&](int p) { return cur[spad(p)]; },
-                                        [&](int p, cplx<T> v) { sink(p, v, nxt); }, logP, lane, tw);
+            stockham_pass<T, N, EMAX, S::RL, DIR>([&](int p) { return cur[spad(p)]; },
+                                                  [&](int p, cplx<T> v) { sink(p, v, nxt); }, logP, lane, tw);
         return which;
     }
 }

@@ -12,13 +12,18 @@ template <> struct CplxOf<float> { using type = float2; };
 template <> struct CplxOf<double> { using type = double2; };
 template <typename T> using cplx = typename CplxOf<T>::type;
 
-// Roots of unity: the host builds, in FP64, one table per transform length,
-// exp(-2 pi i m / n) for m < n, for n = 1, 2, 4, ..., kMaxFftN back to back
-// after one unused entry, so that the table of length n starts at entry n
-// (16-byte aligned for n >= 2: kernels stage it with a bulk copy).
+// Twiddle factors: the host builds, in FP64, one table per transform length
+// n = 2, 4, ..., kMaxFftN and radix cap emax (8 or 16).  A length-n FFT runs
+// radix-E passes (E = min(n, emax)) and a last pass of radix n / P (<= E).
+// The pass that follows P > 1 points already transformed, of radix
+// R = min(E, n / P), needs exp(-2 pi i r k / (P R)) for 1 <= r < R, k < P,
+// which the table holds at entry (P - E) + (r - 1) P + k: n - E entries in
+// all.  The table of (n, emax) starts at entry twiddle_offset(n, emax)
+// (16-byte aligned, room for n entries), so kernels stage it with one bulk
+// copy.
 constexpr int kMaxFftN = 1024;
-__host__ __device__ constexpr int twiddle_offset(int n) { return n; }
-constexpr int kTwiddleEntries = 2 * kMaxFftN;
+__host__ __device__ constexpr int twiddle_offset(int n, int emax) { return (emax == 16 ? 2 * kMaxFftN : 0) + n; }
+constexpr int kTwiddleEntries = 4 * kMaxFftN;
 
 constexpr int kTileW = 4;       // kx columns per tile of every spectral array
 constexpr int kMaxFields = 4;
@@ -104,6 +109,7 @@ template <typename T> struct RowArgs {
     int *d_status;
     int mode, G, inc_step;
     int E;                // FFT radix cap (8 or 16)
+    int kx_cols_max;      // largest kept half-spectrum column count over the launch's slots
 };
 
 template <typename T> struct MidArgs {

@@ -73,6 +73,27 @@ __device__ __forceinline__ void noise_pair(bool on_plane, int kx0, int ky, int k
     }
 }
 
+// two neighbouring complex values at a 16-byte aligned address (one 16-byte
+// access for FP32)
+template <typename T> __device__ __forceinline__ void ld_pair(const cplx<T> *p, cplx<T> &a, cplx<T> &b) {
+    if constexpr (sizeof(T) == 4) {
+        const float4 v = *reinterpret_cast<const float4 *>(p);
+        a = mk<T>(v.x, v.y);
+        b = mk<T>(v.z, v.w);
+    } else {
+        a = p[0];
+        b = p[1];
+    }
+}
+template <typename T> __device__ __forceinline__ void st_pair(cplx<T> *p, cplx<T> a, cplx<T> b) {
+    if constexpr (sizeof(T) == 4) {
+        *reinterpret_cast<float4 *>(p) = make_float4(a.x, a.y, b.x, b.y);
+    } else {
+        p[0] = a;
+        p[1] = b;
+    }
+}
+
 // sigma0 |q|^p with |q| = sqrt(q2)
 template <typename T> __device__ __forceinline__ T noise_amp(T sigma0, int p, T q2) {
     if (p == 0) return sigma0;
@@ -315,7 +336,7 @@ __global__ void __launch_bounds__(512, N >= 512 ? 1 : 2) k_col(const ColArgs<T> 
     if (t == 0) {
         mbar_init(bar, 1);
         mbar_expect_tx(bar, chunk_bytes * nvalid * ((need_in ? 1 : 0) + (need_phi ? 1 : 0)) + twiddle_bytes<C, N>());
-        if (twiddle_bytes<C, N>()) bulk_g2s(TW, a.tw + twiddle_offset(N), twiddle_bytes<C, N>(), bar);
+        if (twiddle_bytes<C, N>()) bulk_g2s(TW, a.tw + twiddle_offset(N, EMAX), twiddle_bytes<C, N>(), bar);
         for (int ch = 0; ch < nvalid; ++ch) {
             if (need_phi) bulk_g2s(PHI + ch * CS, a.state + sofs + gofs(ch), chunk_bytes, bar);
             if (need_in) bulk_g2s(X + ch * CS, a.in + sofs + gofs(ch), chunk_bytes, bar);
@@ -383,6 +404,8 @@ __global__ void __launch_bounds__(512, N >= 512 ? 1 : 2) k_col(const ColArgs<T> 
                 C v0 = P0[spad(pos)], v1 = P1[spad(pos)];
                 C *ph = phb + pos * W;
                 if (mode == COL_STEP) {
+                    C f0, f1;
+                    ld_pair<T>(ph, f0, f1);
                     const int ky = sp.dim == 3 ? o : (sp.dim == 2 ? pos : 0);
                     const int kz = sp.dim == 3 ? pos : 0;
                     const T qy = T(signed_k(ky, sp.ny)) * sp.gy, qz = T(signed_k(kz, sp.nz)) * sp.gz;
@@ -393,13 +416,12 @@ __global__ void __launch_bounds__(512, N >= 512 ? 1 : 2) k_col(const ColArgs<T> 
                         noise_pair<T>(on_plane, kx0, ky, kz, noise_amp<T>(sigma0, noise_pow, q2a),
                                       noise_amp<T>(sigma0, noise_pow, q2b), has1, sp, (uint32_t)fid, seed_lo, seed_hi,
                                       step, xi0, xi1);
-                    v0 = update_mode<T>(ph[0], v0, xi0, q2a, dtO, dtM, has_product);
-                    v1 = update_mode<T>(ph[1], v1, xi1, q2b, dtO, dtM, has_product);
+                    v0 = update_mode<T>(f0, v0, xi0, q2a, dtO, dtM, has_product);
+                    v1 = update_mode<T>(f1, v1, xi1, q2b, dtO, dtM, has_product);
                     // false for NaN and for infinities (or values next to overflow)
                     bad |= !(fabs(v0.x) + fabs(v0.y) + fabs(v1.x) + fabs(v1.y) <= T(sizeof(T) == 4 ? 3.0e38 : 1.0e300));
                 }
-                ph[0] = has0 ? v0 : mk<T>(0, 0);
-                ph[1] = has1 ? v1 : mk<T>(0, 0);
+                st_pair<T>(ph, has0 ? v0 : mk<T>(0, 0), has1 ? v1 : mk<T>(0, 0));
             }
         }
         if (bad && a.d_status) atomicOr(a.d_status, kStatusNonFinite);
@@ -532,7 +554,8 @@ __global__ void __launch_bounds__(256) k_row(const RowArgs<T> a) {
     C *B0 = S + L::s_elems(G, sp.ntiles);
     C *B1 = B0 + G * SF;
     const int slot = a.slot0 + blockIdx.y;
-    const FieldP<T> &fp = a.fps[slot];
+    __shared__ FieldP<T> sfp;                                  // the slot's parameters, fetched during the copies
+    const FieldP<T> &fp = sfp;
     const size_t sofs = (size_t)slot * a.slot_stride;
     const int t = threadIdx.x, nthr = blockDim.x;
     const int r0 = blockIdx.x * G2;
@@ -550,20 +573,20 @@ __global__ void __launch_bounds__(256) k_row(const RowArgs<T> a) {
         if (t == 0) {
             mbar_init(bar, 1);
             mbar_expect_tx(bar, row_bytes * nrow + twiddle_bytes<C, N>());
-            if (twiddle_bytes<C, N>()) bulk_g2s(TW, a.tw + twiddle_offset(N), twiddle_bytes<C, N>(), bar);
+            if (twiddle_bytes<C, N>()) bulk_g2s(TW, a.tw + twiddle_offset(N, EMAX), twiddle_bytes<C, N>(), bar);
             for (int rl = 0; rl < nrow; ++rl) bulk_g2s(Sr + rl * N, src + real_row_offset(sp, r0 + rl), row_bytes, bar);
         }
         __syncthreads();   // the barrier is initialised before anyone polls it
         for (int i = nrow * N + t; i < G2 * N; i += nthr) Sr[i] = T(0);
     } else {
         const C *__restrict__ src = a.in + sofs;
-        const int kxc_in = (mode == ROW_FUSED || mode == ROW_C2R_KEPT) ? fp.kx_cols : sp.hx;
+        const int kxc_in = (mode == ROW_FUSED || mode == ROW_C2R_KEPT) ? a.kx_cols_max : sp.hx;
         const int ntl = (kxc_in + W - 1) / W;
         const uint32_t seg = (uint32_t)(nrow * W * sizeof(C));
         if (t == 0) {
             mbar_init(bar, 1);
             mbar_expect_tx(bar, seg * ntl + twiddle_bytes<C, N>());
-            if (twiddle_bytes<C, N>()) bulk_g2s(TW, a.tw + twiddle_offset(N), twiddle_bytes<C, N>(), bar);
+            if (twiddle_bytes<C, N>()) bulk_g2s(TW, a.tw + twiddle_offset(N, EMAX), twiddle_bytes<C, N>(), bar);
         }
         __syncthreads();
         for (int tl = t; tl < ntl; tl += nthr) bulk_g2s(S + tl * TS, src + ((size_t)tl * rows + r0) * W, seg, bar);
@@ -573,6 +596,9 @@ __global__ void __launch_bounds__(256) k_row(const RowArgs<T> a) {
                 if (r / W >= nrow) S[tl * TS + r] = mk<T>(0, 0);
             }
     }
+    static_assert(sizeof(FieldP<T>) % 4 == 0, "FieldP is copied as 32-bit words");
+    for (int i = t; i < (int)(sizeof(FieldP<T>) / 4); i += nthr)
+        reinterpret_cast<uint32_t *>(&sfp)[i] = reinterpret_cast<const uint32_t *>(&a.fps[slot])[i];
     if (!mbar_wait_all(bar, 0, a.d_status)) return;
 
     const int lane = t & (TPF - 1), g = t >> LOGTPF;
@@ -692,7 +718,7 @@ __global__ void __launch_bounds__(256) k_mid(const MidArgs<T> a) {
         for (int o = 0; o < N; ++o) n += (!masked_in || abs(signed_k(o, N)) <= kmy) ? 1 : 0;
         mbar_init(bar, 1);
         mbar_expect_tx(bar, seg * n + twiddle_bytes<C, N>());
-        if (twiddle_bytes<C, N>()) bulk_g2s(TW, a.tw + twiddle_offset(N), twiddle_bytes<C, N>(), bar);
+        if (twiddle_bytes<C, N>()) bulk_g2s(TW, a.tw + twiddle_offset(N, EMAX), twiddle_bytes<C, N>(), bar);
     }
     __syncthreads();
     for (int o = t; o < N; o += nthr) {
