@@ -291,6 +291,72 @@ def ensemble_measurement(pss, torch, stream, steps=200):
             "speedup_vs_sequential": seq_ms / ms}
 
 
+def cufft_comparison(torch, stream, shape=(1024, 1024), steps=2000, graph_steps=20):
+    """The Model B step written with cuFFT (torch.fft) and plain torch element-wise kernels, replayed
+    from a CUDA graph on the same GPU: a timed comparison only, never part of the product path (its
+    noise comes from torch's generator, not from the method's Philox stream)."""
+    import math
+    w = WORKLOAD
+    ny, nx = shape
+    dev = torch.device("cuda")
+    with torch.cuda.stream(stream):
+        ky = torch.fft.fftfreq(ny, d=1.0 / ny, device=dev)
+        kx = torch.fft.rfftfreq(nx, d=1.0 / nx, device=dev)
+        qy, qx = 2 * math.pi * ky / ny, 2 * math.pi * kx / nx
+        q2 = qy[:, None] ** 2 + qx[None, :] ** 2
+        mask = ((3 * ky.abs() < ny)[:, None] & (3 * kx < nx)[None, :]).to(torch.float32)
+        g = 1.0 / (1.0 + w["dt"] * (w["a"] * q2 + w["K"] * q2 * q2))
+        dtMg = (w["dt"] * (-w["b"]) * q2 * g).to(torch.complex64)
+        amp = (torch.sqrt(nx * ny * w["D"] * q2 * w["dt"]) * g).to(torch.complex64)
+        g = g.to(torch.complex64)
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(w["seed"])
+        x0 = torch.rand((ny, nx), generator=gen, device=dev) * (w["hi"] - w["lo"]) + w["lo"]
+        phi = torch.fft.rfft2(x0)
+
+        def step():
+            r = torch.fft.irfft2(phi * mask, s=shape)
+            P = torch.fft.rfft2(r * r * r)
+            xi = torch.randn(phi.shape, dtype=torch.complex64, device=dev) * amp
+            phi.copy_(phi * g + dtMg * P + xi)
+
+        for _ in range(5):
+            step()
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        for _ in range(graph_steps):
+            step()
+    reps = max(1, steps // graph_steps)
+    with torch.cuda.stream(stream):
+        graph.replay()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            graph.replay()
+        e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / (reps * graph_steps)
+    return {"what": "cuFFT R2C/C2R (torch.fft) + torch element-wise ops, CUDA-graph replay, FP32, same GPU",
+            "ms_per_step": ms, "site_steps_per_s": nx * ny / (ms * 1e-3)}
+
+
+def oracle_all_cores(shape, budget_s=10.0):
+    """Aggregate site-steps/s of independent oracle runs (one per host core, spawned processes)."""
+    import multiprocessing as mp
+    from oracle import oracle as O
+    O.build()
+    ncores = os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    per_step = oracle_rate(shape, 1, budget_s=0.0)[2]
+    n = max(1, int(budget_s / max(per_step, 1e-9)))
+    with ctx.Pool(ncores) as pool:
+        rates = pool.starmap(oracle_rate, [(shape, n, 1e9)] * ncores)
+    # the workers ran at the same time: their rates add up
+    return sum(r[0] for r in rates), ncores, n
+
+
 def adjoint_measurement(pss, torch, stream, n=2000, shape=(256, 256), nbins=64):
     """The adjoint workload: 2D Model B 256^2, FP32, n steps with a fixed noise realisation and sqrt(n)
     checkpoints; loss = mean over the 64 S(q) bins of (S - S*)^2 with S* from (a, b, K) = (-0.8, 1.2, 0.9)."""
@@ -468,6 +534,10 @@ def run_gpu(args):
         extra["ensemble_512"] = ensemble_measurement(pss, torch, stream)
     if not args.no_adjoint:
         extra["adjoint_256"] = adjoint_measurement(pss, torch, stream)
+    if not args.no_cufft:
+        cf = cufft_comparison(torch, stream)
+        cf["ours_over_cufft"] = value / cf["site_steps_per_s"]
+        extra["cufft_step_1024"] = cf
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
@@ -493,6 +563,10 @@ def run_gpu(args):
         rate, n, dt = oracle_rate(shape, 1000, budget_s=float(os.environ.get("PSS_CPU_BUDGET_S", "15")))
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": f"{n} steps of the 1024x1024 Model B workload, FP64 C oracle, 1 thread"}
+        all_rate, ncores, n_all = oracle_all_cores(shape, budget_s=float(os.environ.get("PSS_CPU_BUDGET_S", "15")) / 2)
+        line["cpu_baseline"]["all_cores"] = {
+            "value": all_rate, "unit": UNIT, "cores": ncores,
+            "sample": f"{ncores} independent oracle runs of {n_all} steps each (spawned processes, one per core)"}
     s.close()
     s2.close()
     if rank == 0:
@@ -513,6 +587,7 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the 512-instance ensemble measurement")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint measurement")
+    ap.add_argument("--no-cufft", action="store_true", help="skip the cuFFT + torch comparison step")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
