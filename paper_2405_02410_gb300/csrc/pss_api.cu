@@ -89,10 +89,15 @@ struct pss_system {
     void *L = nullptr;                       // adjoint state lambda / mu (tiled, one slot)
     void *ck = nullptr;                      // checkpoints [nck + 1][slot]
     void *seg = nullptr;                     // recomputed states of one segment [K + 1][slot]
-    void *real_r = nullptr, *real_s = nullptr;
+    void *seg_prod = nullptr;                // their x(y)-transformed products [K + 1][slot]
+    void *seg_real = nullptr;                // their de-aliased real fields [K + 1][nsites]
     double *d_grad = nullptr;                // [11]
+    long long *d_seg = nullptr;              // [2]: segment index, step of its first step (device)
     int64_t adj_n = 0, adj_step0 = 0, adj_K = 0, adj_nck = 0;
     bool adj_ready = false;
+    cudaGraphExec_t adj_graph = nullptr;     // one full segment of the backward pass
+    bool adj_graph_valid = false;
+    int64_t adj_graph_launches = 0;
 
     int nslots() const { return batch * (int)fields.size(); }
 };
@@ -295,15 +300,17 @@ template <typename T> struct Seq {
     }
 
     int col_ptrs(int mode, cplx<T> *st_ptr, const cplx<T> *in_ptr, cplx<T> *out_ptr, const cplx<T> *aux,
-                 long long adj_step) {
+                 long long adj_step, cplx<T> *st_out = nullptr) {
         ColArgs<T> a{};
         a.sp = sys_params<T>(s);
         a.fps = (const FieldP<T> *)s->fps;
         a.in = in_ptr;
         a.out = out_ptr;
         a.state = st_ptr;
+        a.state_out = st_out;
         a.aux = aux;
         a.adj_step = adj_step;
+        a.d_adj_base = (mode == COL_ADJ_A || mode == COL_ADJ_B) ? s->d_seg + 1 : nullptr;
         a.grad = s->d_grad;
         a.slot_stride = s->field_elems;
         a.slot0 = slot0;
@@ -327,13 +334,18 @@ template <typename T> struct Seq {
 
     // in: A or B (complex), or real (ROW_R2C); out: A or B (complex), or real (ROW_C2R)
     int row(int mode, bool in_is_A, bool out_is_B, bool inc, void *real, size_t real_stride) {
+        return row_ptrs(mode, in_is_A ? A() : B(), out_is_B ? B() : A(), inc, (const T *)real, (T *)real, real_stride);
+    }
+
+    int row_ptrs(int mode, const cplx<T> *in_ptr, cplx<T> *out_ptr, bool inc, const T *real_in, T *real_out,
+                 size_t real_stride) {
         RowArgs<T> a{};
         a.sp = sys_params<T>(s);
         a.fps = (const FieldP<T> *)s->fps;
-        a.in = in_is_A ? A() : B();
-        a.out = out_is_B ? B() : A();
-        a.real_in = (const T *)real;
-        a.real_out = (T *)real;
+        a.in = in_ptr;
+        a.out = out_ptr;
+        a.real_in = real_in;
+        a.real_out = real_out;
         a.slot_stride = s->field_elems;
         a.real_stride = real_stride;
         a.slot0 = slot0;
@@ -354,12 +366,14 @@ template <typename T> struct Seq {
         return PSS_OK;
     }
 
-    int mid(int mode, bool in_is_A, bool inc) {
+    int mid(int mode, bool in_is_A, bool inc) { return mid_ptrs(mode, in_is_A ? A() : B(), in_is_A ? B() : A(), inc); }
+
+    int mid_ptrs(int mode, const cplx<T> *in_ptr, cplx<T> *out_ptr, bool inc) {
         MidArgs<T> a{};
         a.sp = sys_params<T>(s);
         a.fps = (const FieldP<T> *)s->fps;
-        a.in = in_is_A ? A() : B();
-        a.out = in_is_A ? B() : A();
+        a.in = in_ptr;
+        a.out = out_ptr;
         a.slot_stride = s->field_elems;
         a.slot0 = slot0;
         a.tw = (const cplx<T> *)s->tw;
@@ -425,42 +439,49 @@ template <typename T> struct Seq {
         return row(ROW_C2R, true, false, false, s->real, 0);                      // A -> real
     }
 
-    // One adjoint step for the forward step phi_n -> phi_n1 (noise step n_step),
-    // with the state array holding phi_n and s->L holding lambda_{n+1} on entry,
-    // lambda_n on exit (see the adjoint recursion in COL_ADJ_A / COL_ADJ_B).
-    int adjoint_step(const cplx<T> *phi_n1, long long n_step, int power) {
+    // Recompute of one forward step for the adjoint: phi_n (st_in) -> phi_n+1
+    // (st_out), reading the x(y)-transformed product of phi_n (prod_in) and
+    // writing that of phi_n+1 (prod_out) and the de-aliased real field
+    // r_n+1 = F^-1[m phi_n+1] (real_out), which the adjoint step needs.
+    int recompute_step(cplx<T> *st_in, cplx<T> *st_out, const cplx<T> *prod_in, cplx<T> *prod_out, T *real_out) {
         int rc;
-        T *rr = (T *)s->real_r, *rs = (T *)s->real_s;
+        if ((rc = col_ptrs(COL_STEP, st_in, prod_in, A(), nullptr, 0, st_out))) return rc;  // -> A
+        if (s->dim == 3) {
+            if ((rc = mid(MID_INV_MASK, true, false))) return rc;                            // A -> B
+            if ((rc = row_ptrs(ROW_FUSED, B(), A(), false, nullptr, real_out, 0))) return rc; // B -> A, r
+            return mid_ptrs(MID_FWD, A(), prod_out, true);                                   // A -> prod, step++
+        }
+        return row_ptrs(ROW_FUSED, A(), prod_out, true, nullptr, real_out, 0);               // A -> prod, r, step++
+    }
+
+    // The product and real field of the state st (start of a recomputed segment).
+    int recompute_prologue(cplx<T> *st, cplx<T> *prod_out, T *real_out) {
+        int rc;
+        if ((rc = col_ptrs(COL_INV_MASK, st, nullptr, A(), nullptr, 0))) return rc;           // st -> A
+        if (s->dim == 3) {
+            if ((rc = mid(MID_INV_MASK, true, false))) return rc;                            // A -> B
+            if ((rc = row_ptrs(ROW_FUSED, B(), A(), false, nullptr, real_out, 0))) return rc; // B -> A, r
+            return mid_ptrs(MID_FWD, A(), prod_out, false);                                  // A -> prod
+        }
+        return row_ptrs(ROW_FUSED, A(), prod_out, false, nullptr, real_out, 0);              // A -> prod, r
+    }
+
+    // One adjoint step for the forward step phi_n -> phi_n1 (noise step n_step),
+    // with s->L holding lambda_{n+1} on entry, lambda_n on exit; prod is the
+    // x(y)-transformed product of phi_n and real_r its de-aliased real field
+    // (see the adjoint recursion in COL_ADJ_A / COL_ADJ_B).
+    int adjoint_step(const cplx<T> *phi_n1, const cplx<T> *prod, const T *real_r, long long n_step) {
+        int rc;
         cplx<T> *Lb = (cplx<T> *)s->L;
-        // r = F^-1[m phi_n] (real) and B = the x(y)-transformed product r^p
-        if ((rc = col(COL_INV_MASK, false, true))) return rc;                      // state -> A
-        if (s->dim == 3) {
-            if ((rc = mid(MID_INV_MASK, true, false))) return rc;                  // A -> B
-            if ((rc = row(ROW_C2R_KEPT, false, false, false, rr, 0))) return rc;   // B -> r
-            if ((rc = row(ROW_FUSED, false, false, false, nullptr, 0))) return rc; // B -> A
-            if ((rc = mid(MID_FWD, true, false))) return rc;                       // A -> B
-        } else {
-            if ((rc = row(ROW_C2R_KEPT, true, false, false, rr, 0))) return rc;    // A -> r
-            if ((rc = row(ROW_FUSED, true, true, false, nullptr, 0))) return rc;   // A -> B
-        }
         // mu = g lambda, gradients, nu = dt M mu back along the slowest axis -> A
-        if ((rc = col_ptrs(COL_ADJ_A, Lb, B(), A(), phi_n1, n_step))) return rc;
-        // s = N F^-1[nu] (real)
+        if ((rc = col_ptrs(COL_ADJ_A, Lb, prod, A(), phi_n1, n_step))) return rc;
+        // w = p r^(p-1) N F^-1[nu] in real space, then its x(y) transform -> B
         if (s->dim == 3) {
-            if ((rc = mid(MID_INV_FULL, true, false))) return rc;                  // A -> B
-            if ((rc = row(ROW_C2R, false, false, false, rs, 0))) return rc;        // B -> s
+            if ((rc = mid(MID_INV_FULL, true, false))) return rc;                            // A -> B
+            if ((rc = row_ptrs(ROW_ADJ, B(), A(), false, real_r, nullptr, 0))) return rc;     // B -> A
+            if ((rc = mid(MID_FWD, true, false))) return rc;                                 // A -> B
         } else {
-            if ((rc = row(ROW_C2R, true, false, false, rs, 0))) return rc;         // A -> s
-        }
-        // w = p r^(p-1) s, then its x(y) transform -> B
-        cudaError_t e = launch_adj_pointwise<T>(rr, rs, s->nsites, power, 1, st);
-        s->launches++;
-        if (e != cudaSuccess) return cuda_fail(s, e, "adjoint point-wise kernel");
-        if (s->dim == 3) {
-            if ((rc = row(ROW_R2C, true, false, false, rs, 0))) return rc;         // w -> A
-            if ((rc = mid(MID_FWD, true, false))) return rc;                       // A -> B
-        } else {
-            if ((rc = row(ROW_R2C, true, true, false, rs, 0))) return rc;          // w -> B
+            if ((rc = row_ptrs(ROW_ADJ, A(), B(), false, real_r, nullptr, 0))) return rc;     // A -> B
         }
         // lambda_n = mu + m F[w] / N
         return col_ptrs(COL_ADJ_B, Lb, B(), A(), nullptr, n_step);
@@ -593,7 +614,10 @@ int device_errors(pss_system *s) {
     return PSS_OK;
 }
 
-void invalidate(pss_system *s) { s->graph_valid = false; }
+void invalidate(pss_system *s) {
+    s->graph_valid = false;
+    s->adj_graph_valid = false;
+}
 
 // (re)allocate the slot arrays for the current number of slots, keeping the
 // data of the slots that exist
@@ -707,13 +731,19 @@ int adj_alloc(pss_system *s, int64_t nck, int64_t K) {
     const size_t slot_bytes = csize(s) * s->field_elems;
     cudaFree(s->ck);
     cudaFree(s->seg);
-    s->ck = s->seg = nullptr;
+    cudaFree(s->seg_prod);
+    cudaFree(s->seg_real);
+    s->ck = s->seg = s->seg_prod = s->seg_real = nullptr;
     CK(cudaMalloc(&s->ck, slot_bytes * (size_t)(nck + 1)));
     CK(cudaMalloc(&s->seg, slot_bytes * (size_t)(K + 1)));
+    CK(cudaMalloc(&s->seg_prod, slot_bytes * (size_t)(K + 1)));
+    CK(cudaMalloc(&s->seg_real, rsize(s) * (size_t)s->nsites * (size_t)(K + 1)));
     if (!s->L) CK(cudaMalloc(&s->L, slot_bytes));
-    if (!s->real_r) CK(cudaMalloc(&s->real_r, rsize(s) * (size_t)s->nsites));
-    if (!s->real_s) CK(cudaMalloc(&s->real_s, rsize(s) * (size_t)s->nsites));
     if (!s->d_grad) CK(cudaMalloc(&s->d_grad, sizeof(double) * 11));
+    if (!s->d_seg) CK(cudaMalloc(&s->d_seg, sizeof(long long) * 2));
+    if (s->adj_graph) cudaGraphExecDestroy(s->adj_graph);
+    s->adj_graph = nullptr;
+    s->adj_graph_valid = false;
     return PSS_OK;
 }
 
@@ -724,30 +754,57 @@ int copy_slot(pss_system *s, void *dst, const void *src) {
 
 void *slot_ptr(const pss_system *s, void *base, int64_t i) { return (char *)base + csize(s) * s->field_elems * i; }
 
+// One segment of the backward pass, of len steps: recompute it from checkpoint
+// *d_seg, keeping every state, its product and its real field, then run its
+// adjoint steps, last first.  The segment index is read on the device, so one
+// captured graph serves every full segment.
+template <typename T> int record_adjoint_segment(pss_system *s, cudaStream_t stream, int64_t len) {
+    Seq<T> q{s, stream, 0, 1};
+    auto st = [&](int64_t i) { return (cplx<T> *)slot_ptr(s, s->seg, i); };
+    auto prod = [&](int64_t i) { return (cplx<T> *)slot_ptr(s, s->seg_prod, i); };
+    auto real = [&](int64_t i) { return (T *)s->seg_real + (size_t)s->nsites * (size_t)i; };
+    cudaError_t e = launch_segment_begin<T>(st(0), (const cplx<T> *)s->ck, s->field_elems, s->d_seg,
+                                            (long long)s->adj_step0, (long long)s->adj_K, s->d_step, s->d_seg + 1,
+                                            stream);
+    s->launches++;
+    if (e != cudaSuccess) return cuda_fail(s, e, "segment start kernel");
+    int rc = q.recompute_prologue(st(0), prod(0), real(0));
+    if (rc) return rc;
+    for (int64_t i = 0; i < len; ++i)
+        if ((rc = q.recompute_step(st(i), st(i + 1), prod(i), prod(i + 1), real(i + 1)))) return rc;
+    for (int64_t i = len - 1; i >= 0; --i)
+        if ((rc = q.adjoint_step(st(i + 1), prod(i), real(i), i))) return rc;
+    return PSS_OK;
+}
+
 template <typename T> int adjoint_backward_t(pss_system *s) {
-    Seq<T> q{s, s->stream, 0, 1};
-    const int power = s->fields[0].power;
     for (int64_t j = s->adj_nck - 1; j >= 0; --j) {
-        const int64_t t0 = j * s->adj_K;
-        const int64_t len = std::min<int64_t>(s->adj_K, s->adj_n - t0);
-        // recompute the segment's states from its checkpoint
-        int rc = copy_slot(s, s->state, slot_ptr(s, s->ck, j));
-        if (rc) return rc;
-        long long st = s->adj_step0 + t0;
-        CK(cudaMemcpyAsync(s->d_step, &st, sizeof st, cudaMemcpyHostToDevice, s->stream));
-        CK(cudaStreamSynchronize(s->stream));
-        s->stale = true;
-        if ((rc = copy_slot(s, slot_ptr(s, s->seg, 0), s->state))) return rc;
-        for (int64_t i = 1; i <= len; ++i) {
-            if ((rc = prologue(s))) return rc;
-            if ((rc = q.one_step())) return rc;
-            if ((rc = copy_slot(s, slot_ptr(s, s->seg, i), s->state))) return rc;
-        }
-        // adjoint steps of the segment, last first
-        for (int64_t i = len - 1; i >= 0; --i) {
-            if ((rc = copy_slot(s, s->state, slot_ptr(s, s->seg, i)))) return rc;
-            rc = q.adjoint_step((const cplx<T> *)slot_ptr(s, s->seg, i + 1), (long long)(s->adj_step0 + t0 + i), power);
-            if (rc) return rc;
+        const int64_t len = std::min<int64_t>(s->adj_K, s->adj_n - j * s->adj_K);
+        cudaError_t e = launch_set_i64(s->d_seg, (long long)j, s->stream);
+        s->launches++;
+        if (e != cudaSuccess) return cuda_fail(s, e, "segment index kernel");
+        int rc;
+        if (len == s->adj_K && s->adj_nck > 1) {
+            if (!s->adj_graph_valid) {
+                if (s->adj_graph) { cudaGraphExecDestroy(s->adj_graph); s->adj_graph = nullptr; }
+                CK(cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal));
+                const int64_t before = s->launches;
+                rc = record_adjoint_segment<T>(s, s->cap_stream, len);
+                s->adj_graph_launches = s->launches - before;
+                s->launches = before;
+                cudaGraph_t g = nullptr;
+                e = cudaStreamEndCapture(s->cap_stream, &g);
+                if (rc) { if (g) cudaGraphDestroy(g); return rc; }
+                if (e != cudaSuccess) return cuda_fail(s, e, "cudaStreamEndCapture");
+                e = cudaGraphInstantiate(&s->adj_graph, g, 0);
+                cudaGraphDestroy(g);
+                if (e != cudaSuccess) return cuda_fail(s, e, "cudaGraphInstantiate");
+                s->adj_graph_valid = true;
+            }
+            CK(cudaGraphLaunch(s->adj_graph, s->stream));
+            s->launches += s->adj_graph_launches;
+        } else if ((rc = record_adjoint_segment<T>(s, s->stream, len))) {
+            return rc;
         }
     }
     return PSS_OK;
@@ -786,9 +843,11 @@ int pss_destroy_system(pss_system *s) {
     cudaFree(s->L);
     cudaFree(s->ck);
     cudaFree(s->seg);
-    cudaFree(s->real_r);
-    cudaFree(s->real_s);
+    cudaFree(s->seg_prod);
+    cudaFree(s->seg_real);
     cudaFree(s->d_grad);
+    cudaFree(s->d_seg);
+    if (s->adj_graph) cudaGraphExecDestroy(s->adj_graph);
     if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
     delete s;
     return PSS_OK;

@@ -68,7 +68,12 @@ enum ColMode {
     COL_ADJ_A = 4,   // adjoint: mu = g lambda, coefficient gradients, inverse of nu = dt M mu (all columns)
     COL_ADJ_B = 5    // adjoint: lambda = mu + m F[w] / N
 };
-enum RowMode { ROW_FUSED = 0, ROW_R2C = 1, ROW_C2R = 2, ROW_C2R_KEPT = 3 /* C2R of the kept columns only */ };
+enum RowMode {
+    ROW_FUSED = 0,      // C2R of the kept columns, power p, R2C (real_out: also store the real field)
+    ROW_R2C = 1, ROW_C2R = 2,
+    ROW_C2R_KEPT = 3,   // C2R of the kept columns only
+    ROW_ADJ = 4         // adjoint: C2R of all columns (s), times p r^(p-1) with r from real_in, R2C
+};
 enum MidMode { MID_INV_MASK = 0, MID_INV_FULL = 1, MID_FWD = 2 };
 
 // Arrays: slot s of an array starts at base + s * slot_stride (complex
@@ -80,6 +85,7 @@ template <typename T> struct ColArgs {
     const cplx<T> *in;
     cplx<T> *out;
     cplx<T> *state;
+    cplx<T> *state_out;   // where the updated state goes (nullptr: back to state)
     size_t slot_stride;
     int slot0;
     const cplx<T> *tw;
@@ -92,6 +98,7 @@ template <typename T> struct ColArgs {
     // the FP64 gradient sums [slot][11] (dO_0..4, dM_0..4, sum Re(conj(mu) xi))
     const cplx<T> *aux;
     long long adj_step;
+    const long long *d_adj_base;   // if set, the noise step is adj_step + *d_adj_base
     double *grad;
 };
 
@@ -153,8 +160,10 @@ template <typename T> cudaError_t launch_tiles_to_half(const SysP<T> &sp, const 
                                                        cplx<T> *half, cudaStream_t st);
 template <typename T> cudaError_t launch_half_to_tiles(const SysP<T> &sp, const cplx<T> *half,
                                                        cplx<T> *tiles, cudaStream_t st);
-template <typename T> cudaError_t launch_adj_pointwise(const T *r, T *s, long long n, int power, int mode,
-                                                       cudaStream_t st);
+template <typename T> cudaError_t launch_segment_begin(cplx<T> *dst, const cplx<T> *ck, size_t slot_elems,
+                                                       const long long *d_seg, long long step_base, long long K,
+                                                       long long *d_step, long long *d_adj_base, cudaStream_t st);
+cudaError_t launch_set_i64(long long *dst, long long value, cudaStream_t st);
 template <typename T> cudaError_t launch_structure_factor(const SysP<T> &sp, const double dx[3],
                                                           const cplx<T> *tiles, int nbins,
                                                           double *acc /* 2*nbins + 2 */, cudaStream_t st);

@@ -160,7 +160,7 @@ __device__ __forceinline__ void col_adjoint(const ColArgs<T> &a, const FieldP<T>
     double acc[11];
 #pragma unroll
     for (int i = 0; i < 11; ++i) acc[i] = 0.0;
-    const uint32_t step = (uint32_t)a.adj_step;
+    const uint32_t step = (uint32_t)(a.adj_step + (a.d_adj_base ? *a.d_adj_base : 0));
 #pragma unroll 1
     for (int i = t; i < N * F; i += nthr) {
         const int pos = i >> (__ffs(F) - 1), ff = i & (F - 1);
@@ -462,8 +462,9 @@ __global__ void __launch_bounds__(512, N >= 512 ? 1 : 2) k_col(const ColArgs<T> 
         fence_proxy_async();   // every thread's PHI writes, before the copy engine reads them
         __syncthreads();
         if (t == 0) {
+            cplx<T> *sdst = a.state_out ? a.state_out : a.state;
             for (int cq = 0; cq < nvalid; ++cq)
-                if (chunk_writes(cq)) bulk_s2g(a.state + sofs + gofs(cq), PHI + cq * CS, chunk_bytes);
+                if (chunk_writes(cq)) bulk_s2g(sdst + sofs + gofs(cq), PHI + cq * CS, chunk_bytes);
             bulk_commit();
         }
         if (mode == COL_FWD) {
@@ -639,12 +640,32 @@ __global__ void __launch_bounds__(256) k_row(const RowArgs<T> a) {
             return;
         }
         // forward transform of the real-space product (phi^d)^p of both rows
+        // (ROW_ADJ: of p r^(p-1) s, with s the rows just transformed and r read
+        // from real_in; ROW_FUSED with real_out: the rows are stored as well)
         const int p = fp.power;
         C *zf = Z + g * SF;
         C *other = (which == 0 ? B1 : B0) + g * SF;
+        const bool adj = mode == ROW_ADJ;
+        const T *ra = nullptr, *rb = nullptr;
+        T *wa = nullptr, *wb = nullptr;
+        if (adj) {
+            const T *base = a.real_in + (size_t)slot * a.real_stride;
+            if (g < nrow) ra = base + real_row_offset(sp, r0 + g);
+            if (G + g < nrow) rb = base + real_row_offset(sp, r0 + G + g);
+        } else if (a.real_out) {
+            T *base = a.real_out + (size_t)slot * a.real_stride;
+            if (g < nrow) wa = base + real_row_offset(sp, r0 + g);
+            if (G + g < nrow) wb = base + real_row_offset(sp, r0 + G + g);
+        }
         const int which2 = fft_run<T, N, EMAX, -1>(
             [&](int k) {
                 const C z = zf[spad(k)];
+                if (adj) {
+                    const T xa = ra ? ra[k] : T(0), xb = rb ? rb[k] : T(0);
+                    return mk<T>(T(p) * ipow<T>(xa, p - 1) * z.x, T(p) * ipow<T>(xb, p - 1) * z.y);
+                }
+                if (wa) wa[k] = z.x;
+                if (wb) wb[k] = z.y;
                 return mk<T>(ipow<T>(z.x, p), ipow<T>(z.y, p));
             },
             smem_sink, other, zf, lane, active, tw);
@@ -768,19 +789,29 @@ __global__ void k_tiles_half(SysP<T> sp, cplx<T> *tiles, cplx<T> *half, int to_h
     }
 }
 
-// adjoint point-wise factors in real space: mode 0: s <- r^p, mode 1: s <- p r^(p-1) s
-template <typename T> __global__ void k_adj_pointwise(const T *r, T *s, long long n, int power, int mode) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const T x = r[i];
-        if (mode == 0) s[i] = ipow<T>(x, power);
-        else s[i] = T(power) * ipow<T>(x, power - 1) * s[i];
+// Start of a recomputed adjoint segment j = *d_seg (read on the device, so that
+// one captured graph serves every segment): checkpoint j -> dst, and the step
+// counters of its first step.
+template <typename T>
+__global__ void k_segment_begin(cplx<T> *dst, const cplx<T> *ck, size_t slot_elems, const long long *d_seg,
+                                long long step_base, long long K, long long *d_step, long long *d_adj_base) {
+    const long long j = *d_seg;
+    const cplx<T> *src = ck + (size_t)j * slot_elems;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < slot_elems; i += (size_t)gridDim.x * blockDim.x)
+        dst[i] = src[i];
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        *d_step = step_base + j * K;
+        *d_adj_base = step_base + j * K;
     }
 }
 
-template <typename T> cudaError_t launch_adj_pointwise(const T *r, T *s, long long n, int power, int mode, cudaStream_t st) {
-    long long blocks = (n + 255) / 256;
-    if (blocks > 65535) blocks = 65535;
-    k_adj_pointwise<T><<<(int)blocks, 256, 0, st>>>(r, s, n, power, mode);
+template <typename T>
+cudaError_t launch_segment_begin(cplx<T> *dst, const cplx<T> *ck, size_t slot_elems, const long long *d_seg,
+                                 long long step_base, long long K, long long *d_step, long long *d_adj_base,
+                                 cudaStream_t st) {
+    long long blocks = (long long)((slot_elems + 255) / 256);
+    if (blocks > 1184) blocks = 1184;
+    k_segment_begin<T><<<(int)blocks, 256, 0, st>>>(dst, ck, slot_elems, d_seg, step_base, K, d_step, d_adj_base);
     return cudaGetLastError();
 }
 
@@ -995,7 +1026,8 @@ cudaError_t launch_structure_factor(const SysP<T> &sp, const double dx[3], const
     template cudaError_t launch_init_uniform<T>(T *, long long, double, double, uint64_t, int, cudaStream_t); \
     template cudaError_t launch_tiles_to_half<T>(const SysP<T> &, const cplx<T> *, cplx<T> *, cudaStream_t); \
     template cudaError_t launch_half_to_tiles<T>(const SysP<T> &, const cplx<T> *, cplx<T> *, cudaStream_t); \
-    template cudaError_t launch_adj_pointwise<T>(const T *, T *, long long, int, int, cudaStream_t);        \
+    template cudaError_t launch_segment_begin<T>(cplx<T> *, const cplx<T> *, size_t, const long long *, long long, \
+                                                 long long, long long *, long long *, cudaStream_t);             \
     template cudaError_t launch_structure_factor<T>(const SysP<T> &, const double *, const cplx<T> *, int,   \
                                                     double *, cudaStream_t);
 
