@@ -174,6 +174,14 @@ int pss_time_kernels(pss_system *s, int64_t n, double *avg_ms);
  *   "col_radix", "row_radix", "mid_radix"
  *                 largest FFT pass radix (8 or 16) of the column, x and
  *                 3D y kernels;
+ *   "fast2d"      FP32 2D systems whose sides are 256, 512 or 1024 points
+ *                 run every transform in one warp (1, default) or take the
+ *                 generic kernels (0); the two agree to FP32 rounding;
+ *   "col2_warps"  noise warps beside the FFT warps of a column CTA of that
+ *                 path (1..24);
+ *   "row2_pairs"  row pairs per row CTA of that path (power of two <= 8);
+ *   "col2_radix", "row2_radix"
+ *                 radix of that path's FFT passes (8 or 16);
  * 0 restores the automatic choice.  Unknown keys return PSS_EINVAL. */
 int pss_set_tuning(pss_system *s, const char *key, int value);
 

@@ -18,6 +18,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/pss.h"
@@ -78,11 +79,15 @@ struct pss_system {
     int *d_status = nullptr;
     int64_t step = 0;
     bool stale = true;                       // B does not hold the product of the current state
+    bool b_fast = false;                     // B is in the column-major layout of the fast 2D path
     cudaGraphExec_t graph = nullptr;
     bool graph_valid = false;
     // launch-shape tuning (pss_set_tuning); 0 = automatic
     int tune_pdl = 0, tune_row_pairs = 0, tune_col_tiles = 0, tune_graph_steps = 0, tune_mid_planes = 0;
     int tune_col_radix = 0, tune_row_radix = 0, tune_mid_radix = 0;   // FFT radix caps (8 or 16; 0 = automatic)
+    int tune_fast2d = 1;                     // FP32 2D sides of 256..1024: one warp per transform (0 = generic kernels)
+    int tune_col2_warps = 0, tune_row2_pairs = 0;   // its noise warps per column CTA, row pairs per row CTA
+    int tune_col2_radix = 0, tune_row2_radix = 0;   // its FFT pass radix (8 or 16; 0 = automatic)
     int64_t launches = 0;
     std::string err;
     // adjoint: checkpoints of the last pss_adjoint_forward run
@@ -258,6 +263,32 @@ int mid_PZ(const pss_system *s) {
     return pz;
 }
 
+// The FP32 2D path with one warp per transform serves sides of 256, 512 and
+// 1024 points; everything else runs the generic kernels.
+bool fast2d(const pss_system *s) {
+    auto side = [](int n) { return n == 256 || n == 512 || n == 1024; };
+    return s->tune_fast2d && s->prec == PSS_F32 && s->dim == 2 && side(s->nx) && side(s->ny);
+}
+// Launch shape of the fast path.  Measured on GB300 at 1024 x 1024: radix-16
+// passes (two warps per 1024-point transform, three passes) in both kernels,
+// 16 noise warps per column CTA and 4 row pairs per row CTA; sides of 256
+// always take radix 8 (one warp per transform).
+int col2_radix(const pss_system *s) { return s->ny >= 512 && s->tune_col2_radix != 8 ? 16 : 8; }
+int row2_radix(const pss_system *s) { return s->nx >= 512 && s->tune_row2_radix != 8 ? 16 : 8; }
+int col2_warps(const pss_system *s) {
+    const int fft_warps = 4 * s->ny / col2_radix(s) / 32;
+    const int want = s->tune_col2_warps > 0 ? s->tune_col2_warps : 16;
+    return std::min(want, (col2_radix(s) == 8 ? 32 : 24) - fft_warps);
+}
+// row pairs per CTA: a power of two with at most 512 threads per CTA
+int row2_pairs(const pss_system *s) {
+    const int tpf = s->nx / row2_radix(s);
+    const int nw = s->tune_row2_pairs > 0 ? s->tune_row2_pairs : 4;
+    int p = 1;
+    while (p * 2 <= nw && p * 2 <= 8 && p * 2 * tpf <= 512) p *= 2;
+    return p;
+}
+
 int max_kept_tiles(const pss_system *s) {
     int m = 0;
     for (int i = 0; i < (int)s->fields.size(); ++i) m = std::max(m, (kept_cols(s, i) + kTileW - 1) / kTileW);
@@ -393,9 +424,73 @@ template <typename T> struct Seq {
         return PSS_OK;
     }
 
+    // the fast 2D path (FP32 only): k2_col, then k2_row
+    int col2(int mode) {
+        if constexpr (std::is_same<T, float>::value) {
+            ColArgs<float> a{};
+            a.sp = sys_params<float>(s);
+            a.fps = (const FieldP<float> *)s->fps;
+            a.in = B();
+            a.out = A();
+            a.state = state();
+            a.slot_stride = s->field_elems;
+            a.slot0 = slot0;
+            a.tw = (const float2 *)s->tw;
+            a.d_step = s->d_step;
+            a.d_status = s->d_status;
+            a.mode = mode;
+            a.aux_warps = col2_warps(s);
+            a.E = col2_radix(s);
+            const int nt = mode == COL_INV_MASK ? max_kept_tiles(s) : s->ntiles;
+            if (timer) timer->begin(0, st);
+            cudaError_t e = launch_col2(a, nslots, nt, st);
+            if (timer) timer->begin(0, st);
+            s->launches++;
+            if (e != cudaSuccess) return cuda_fail(s, e, "k2_col launch");
+            return PSS_OK;
+        } else {
+            (void)mode;
+            return fail(s, PSS_EUNSUPPORTED, "the one-warp 2D path is FP32 only");
+        }
+    }
+
+    int row2(bool inc) {
+        if constexpr (std::is_same<T, float>::value) {
+            RowArgs<float> a{};
+            a.sp = sys_params<float>(s);
+            a.fps = (const FieldP<float> *)s->fps;
+            a.in = A();
+            a.out = B();
+            a.slot_stride = s->field_elems;
+            a.slot0 = slot0;
+            a.tw = (const float2 *)s->tw;
+            a.d_step = s->d_step;
+            a.d_status = s->d_status;
+            a.mode = ROW_FUSED;
+            a.G = row2_pairs(s);
+            a.E = row2_radix(s);
+            a.kx_cols_max = 0;
+            for (int i = 0; i < (int)s->fields.size(); ++i) a.kx_cols_max = std::max(a.kx_cols_max, kept_cols(s, i));
+            a.inc_step = inc ? 1 : 0;
+            if (timer) timer->begin(2, st);
+            cudaError_t e = launch_row2(a, nslots, st);
+            if (timer) timer->begin(2, st);
+            s->launches++;
+            if (e != cudaSuccess) return cuda_fail(s, e, "k2_row launch");
+            return PSS_OK;
+        } else {
+            (void)inc;
+            return fail(s, PSS_EUNSUPPORTED, "the one-warp 2D path is FP32 only");
+        }
+    }
+
     // B <- x-transformed product of the current state (start of a run)
     int prologue() {
         int rc;
+        if (fast2d(s)) {
+            if ((rc = col2(COL_INV_MASK))) return rc;                             // state -> A (column-major)
+            return row2(false);                                                    // A -> B (column-major)
+        }
         if ((rc = col(COL_INV_MASK, false, true))) return rc;                      // state -> A
         if (s->dim == 3) {
             if ((rc = mid(MID_INV_MASK, true, false))) return rc;                  // A -> B
@@ -407,6 +502,10 @@ template <typename T> struct Seq {
 
     int one_step() {
         int rc;
+        if (fast2d(s)) {
+            if ((rc = col2(COL_STEP))) return rc;                                 // B, state -> state, A
+            return row2(true);                                                     // A -> B, step++
+        }
         if ((rc = col(COL_STEP, true, true))) return rc;                           // B, state -> state, A
         if (s->dim == 3) {
             if ((rc = mid(MID_INV_MASK, true, false))) return rc;                  // A -> B
@@ -494,10 +593,11 @@ template <typename T> int run_prologue(pss_system *s) {
 }
 
 int prologue(pss_system *s) {
-    if (!s->stale) return PSS_OK;
+    if (!s->stale && s->b_fast == fast2d(s)) return PSS_OK;
     int rc = s->prec == PSS_F64 ? run_prologue<double>(s) : run_prologue<float>(s);
     if (rc) return rc;
     s->stale = false;
+    s->b_fast = fast2d(s);
     return PSS_OK;
 }
 
@@ -1166,6 +1266,16 @@ int pss_set_tuning(pss_system *s, const char *key, int value) {
     else if (k == "col_tiles") s->tune_col_tiles = value;
     else if (k == "mid_planes") s->tune_mid_planes = value;
     else if (k == "graph_steps") s->tune_graph_steps = value;
+    else if (k == "fast2d") s->tune_fast2d = value ? 1 : 0;
+    else if (k == "col2_warps") {
+        if (value > 24) return fail(s, PSS_EINVAL, "col2_warps is at most 24 (0 = automatic)");
+        s->tune_col2_warps = value;
+    }
+    else if (k == "row2_pairs") s->tune_row2_pairs = value;
+    else if (k == "col2_radix" || k == "row2_radix") {
+        if (value != 0 && value != 8 && value != 16) return fail(s, PSS_EINVAL, "radix 8 or 16 (0 = automatic)");
+        (k == "col2_radix" ? s->tune_col2_radix : s->tune_row2_radix) = value;
+    }
     else if (k == "col_radix" || k == "row_radix" || k == "mid_radix") {
         if (value != 0 && value != 8 && value != 16) return fail(s, PSS_EINVAL, "radix caps are 8 or 16 (0 = automatic)");
         (k == "col_radix" ? s->tune_col_radix : k == "row_radix" ? s->tune_row_radix : s->tune_mid_radix) = value;

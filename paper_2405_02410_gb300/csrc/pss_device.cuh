@@ -1,6 +1,6 @@
 // pss_device.cuh -- device building blocks of the sm_103a pseudo-spectral step:
 // complex arithmetic, the counter-based Philox4x32-10 generator, in-register
-// radix-2/4/8/16 DFTs, the shared-memory Stockham pass that strings them into
+// radix-2/4/8/16/32 DFTs, the shared-memory Stockham pass that strings them into
 // length-N FFTs (the F and F^-1 of Eq. cubicexample, arXiv:2405.02410), and
 // the TMA bulk-copy / mbarrier helpers that stage tiles into shared memory.
 #pragma once
@@ -74,27 +74,29 @@ __device__ __forceinline__ void box_muller(double u0, double u1, double &n1, dou
 }
 
 // ---------------------------------------------------------------------------
-// 16th roots of unity: cos(2 pi k / 16) from the exact first-quadrant values.
+// 32nd roots of unity: cos(2 pi k / 32) from the exact first-octant values
+// (cos(j pi / 16), j = 0..8) by quadrant symmetry.
 // ---------------------------------------------------------------------------
-__host__ __device__ constexpr double cos16(int k) {
-    k &= 15;
-    // cos(pi/8), cos(pi/4), cos(3 pi/8)
-    constexpr double c1 = 0.92387953251128675613, c2 = 0.70710678118654752440, c3 = 0.38268343236508977173;
-    return k == 0 ? 1.0 : k == 1 ? c1 : k == 2 ? c2 : k == 3 ? c3 : k == 4 ? 0.0 : k == 5 ? -c3 :
-           k == 6 ? -c2 : k == 7 ? -c1 : k == 8 ? -1.0 : k == 9 ? -c1 : k == 10 ? -c2 : k == 11 ? -c3 :
-           k == 12 ? 0.0 : k == 13 ? c3 : k == 14 ? c2 : c1;
+__host__ __device__ constexpr double cos_oct(int j) {
+    return j == 0 ? 1.0 : j == 1 ? 0.98078528040323044913 : j == 2 ? 0.92387953251128675613 :
+           j == 3 ? 0.83146961230254523708 : j == 4 ? 0.70710678118654752440 : j == 5 ? 0.55557023301960222474 :
+           j == 6 ? 0.38268343236508977173 : j == 7 ? 0.19509032201612826785 : 0.0;
 }
-__host__ __device__ constexpr double sin16(int k) { return cos16(k - 4); }
+__host__ __device__ constexpr double cos32(int k) {
+    k &= 31;
+    return k <= 8 ? cos_oct(k) : k <= 16 ? -cos_oct(16 - k) : k <= 24 ? -cos_oct(k - 16) : cos_oct(32 - k);
+}
+__host__ __device__ constexpr double sin32(int k) { return cos32(k - 8); }
 
-// b * exp(DIR 2 pi i e / 16) with e a compile-time constant after unrolling;
+// b * exp(DIR 2 pi i e / 32) with e a compile-time constant after unrolling;
 // the four axis-aligned roots cost no multiply.
-template <int DIR, typename T> __device__ __forceinline__ cplx<T> rot16(cplx<T> b, int e) {
-    e &= 15;
+template <int DIR, typename T> __device__ __forceinline__ cplx<T> rot32(cplx<T> b, int e) {
+    e &= 31;
     if (e == 0) return b;
-    if (e == 8) return mk<T>(-b.x, -b.y);
-    if (e == 4) return DIR > 0 ? mk<T>(-b.y, b.x) : mk<T>(b.y, -b.x);    // * (+-i)
-    if (e == 12) return DIR > 0 ? mk<T>(b.y, -b.x) : mk<T>(-b.y, b.x);
-    const T c = T(cos16(e)), s = T(DIR * sin16(e));
+    if (e == 16) return mk<T>(-b.x, -b.y);
+    if (e == 8) return DIR > 0 ? mk<T>(-b.y, b.x) : mk<T>(b.y, -b.x);    // * (+-i)
+    if (e == 24) return DIR > 0 ? mk<T>(b.y, -b.x) : mk<T>(-b.y, b.x);
+    const T c = T(cos32(e)), s = T(DIR * sin32(e));
     return mk<T>(b.x * c - b.y * s, b.x * s + b.y * c);
 }
 
@@ -104,7 +106,7 @@ __host__ __device__ constexpr int bitrev(int i, int n) {
     return r;
 }
 
-// In-register DFT of size R (1, 2, 4, 8 or 16): X_k = sum_j v_j exp(DIR 2 pi i jk/R),
+// In-register DFT of size R (1, 2, 4, 8, 16 or 32): X_k = sum_j v_j exp(DIR 2 pi i jk/R),
 // natural order in and out; iterative radix-2 decimation in time.
 template <int R, int DIR, typename T> __device__ __forceinline__ void dft_reg(cplx<T> *v) {
     if constexpr (R > 1) {
@@ -118,7 +120,7 @@ template <int R, int DIR, typename T> __device__ __forceinline__ void dft_reg(cp
 #pragma unroll
                 for (int m = 0; m < len / 2; ++m) {
                     const cplx<T> a = w[st + m];
-                    const cplx<T> b = rot16<DIR, T>(w[st + m + len / 2], m * (16 / len));
+                    const cplx<T> b = rot32<DIR, T>(w[st + m + len / 2], m * (32 / len));
                     w[st + m] = cadd<T>(a, b);
                     w[st + m + len / 2] = csub<T>(a, b);
                 }
@@ -315,6 +317,14 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t phase) {
         : "r"(smem_u32(bar)), "r"(phase)
         : "memory");
     return ok != 0;
+}
+
+// The calling thread alone polls phase `phase` of `bar`, at most kWaitLimit
+// times; false when the wait ran out.
+__device__ __forceinline__ bool mbar_poll(uint64_t *bar, uint32_t phase) {
+    for (int it = 0; it < kWaitLimit; ++it)
+        if (mbar_try_wait(bar, phase)) return true;
+    return false;
 }
 
 // All threads wait for phase `phase` of `bar`.  Returns true for the whole

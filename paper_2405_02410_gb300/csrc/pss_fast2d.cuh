@@ -1,0 +1,470 @@
+// pss_fast2d.cuh -- the FP32 2D step with one warp per transform
+// (arXiv:2405.02410, section "What cuPSS calculates", Eq. timeupdate).
+//
+// For a 2D field whose sides are 256, 512 or 1024 points, every length-N
+// transform of the step is run by a single warp in shared memory, so its
+// passes meet at __syncwarp instead of CTA barriers.  Two kernels per step,
+// with the same split of the work as the generic path:
+//
+//   k2_col (one CTA per tile of kTileW = 4 columns kx, all ky): four FFT warps
+//       (one per column) stage the state and the x-transformed product with
+//       TMA and run the forward y-FFT, while the remaining "noise" warps draw
+//       the Philox noise of the tile's modes into shared memory.  Then every
+//       warp updates the modes (Eq. timeupdate), the Hermitian part is taken on
+//       the kx = 0, Nx/2 planes, the state goes back with one bulk copy and the
+//       FFT warps transform the de-aliased, 1/N_sites-scaled kept columns back
+//       along y.
+//   k2_row (one CTA per NW pairs of rows): warp j takes rows r0 + 2j and
+//       r0 + 2j + 1 as one complex transform (z = a + i b): C2R of the kept
+//       columns, power p in real space, R2C, split into the two half spectra.
+//
+// Only forward transforms are coded: an inverse is conj(F(conj(x))).  The
+// column kernel stores the conjugate of its y-inverse (T1 = F(conj X)), which
+// the row kernel's staging and split absorb, so no pass body exists twice.
+// Each kernel runs its transforms from one inlined call site, and a pass
+// loops over its butterflies: the code a kernel streams through an SM stays
+// small (fully unrolled one-warp FFTs spent most of their time waiting for
+// instruction fetch).
+//
+// The two work arrays between the kernels are column-major, [kx][y] with
+// column kx contiguous: a column is one contiguous run for k2_col (one bulk
+// copy per tile, conflict-free reads along y, coalesced stores), and the NW
+// row pairs of a k2_row CTA are a 16 NW-byte run of every column.  The state
+// keeps the tiled layout of every other kernel.
+#pragma once
+
+#include "pss_kernels.cuh"
+
+namespace pss {
+
+// A group FFT of length N with radix-E passes (E = 8 or 16) and a last pass
+// of radix RL, run by TPF = N / E threads (GW = TPF / 32 warps) that meet at
+// a named barrier (at __syncwarp when the group is one warp).  A group's two
+// buffers hold BUF = N + N/16 points (room for the padded intermediate
+// results) and sit WS apart (the extra 4 staggers neighbouring groups over
+// the banks).
+template <int N, int E_> struct GShape {
+    static_assert(N == 256 || N == 512 || N == 1024, "group FFTs of 256, 512 or 1024 points");
+    static_assert(E_ == 8 || E_ == 16, "radix-8 or radix-16 passes");
+    static constexpr int E = E_;
+    static constexpr int TPF = N / E, GW = TPF / 32;
+    static_assert(TPF % 32 == 0 && TPF <= 128, "whole warps, at most four per transform");
+    static constexpr int LOG = ilog2(N), LOGE = ilog2(E);
+    static constexpr int LOGRL = LOG % LOGE == 0 ? LOGE : LOG % LOGE;
+    static constexpr int RL = 1 << LOGRL;
+    static constexpr int NPASS = (LOG - LOGRL) / LOGE + 1;
+    static constexpr int BUF = N + N / 16;
+    static constexpr int WS = 2 * BUF + 4;
+    // the buffer that holds a transform's result: the first pass writes b0,
+    // the passes alternate
+    static constexpr int OUT = NPASS % 2 == 1 ? 0 : 1;
+};
+
+// the group's barrier: named barrier `id` (1..15) over its TPF threads
+template <int TPF> __device__ __forceinline__ void group_sync(int id) {
+    if constexpr (TPF <= 32) {
+        __syncwarp();
+    } else {
+        asm volatile("bar.sync %0, %1;" ::"r"(id), "n"(TPF) : "memory");
+    }
+}
+
+// Intermediate pass results are padded: position p lives at p + p/16, which
+// keeps the stride-R stores of a pass and the strided loads of the next free
+// of bank conflicts, and which, with R and the pass strides known at compile
+// time, folds into constant address offsets.  Inputs and outputs of a
+// transform are in natural order.
+__device__ __forceinline__ int pad16(int p) { return p + (p >> 4); }
+
+__device__ __forceinline__ float pow_p(float x, int p) { return p == 3 ? x * x * x : ipow<float>(x, p); }
+
+// One forward Stockham pass of radix R after P = 2^logP points have been
+// combined (the pass structure of the generic kernels, butterfly
+// i = gl + TPF s): read x[i + r N/R], multiply by exp(-2 pi i r k / (P R)),
+// k = i mod P, transform over r, write y[(i - k) R + k + r P].  tw is the
+// (N, E) table; with power p > 0 (natural-order output only) an output
+// x + i y is stored as x^p + i (-y)^p: for z' = conj(z) that is
+// Re(z)^p + i Im(z)^p.
+template <int N, int E, int R, bool TWID, bool PADIN, bool PADOUT>
+__device__ __forceinline__ void fpass(const float2 *src, float2 *dst, int logP, int gl,
+                                      const float2 *__restrict__ tw, int power) {
+    constexpr int TPF = GShape<N, E>::TPF;
+    constexpr int STRIDE = N / R, BPT = STRIDE / TPF, LOGR = ilog2(R);
+    static_assert(STRIDE % TPF == 0, "every thread takes whole butterflies");
+    const int P = 1 << logP;
+#pragma unroll 1
+    for (int s = 0; s < BPT; ++s) {
+        const int i = gl + TPF * s, k = i & (P - 1);
+        float2 u[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int p = i + r * STRIDE;
+            u[r] = src[PADIN ? pad16(p) : p];
+        }
+        if constexpr (TWID) {
+            const float2 *__restrict__ twp = tw + (P - E) + k;
+#pragma unroll
+            for (int r = 1; r < R; ++r) u[r] = cmul<float>(u[r], twp[(r - 1) * P]);
+        }
+        dft_reg<R, -1, float>(u);
+        const int j = ((i - k) << LOGR) + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int q = j + r * P;
+            float2 v = u[r];
+            if (!PADOUT && power > 0) v = mk<float>(pow_p(v.x, power), pow_p(-v.y, power));
+            dst[PADOUT ? pad16(q) : q] = v;
+        }
+    }
+}
+
+// Unnormalised forward FFT (exponent -2 pi i) of length N by a group of TPF
+// threads (gl = 0..TPF-1, barrier `id`).  `in` holds the input in natural
+// order and may be b1, never b0; the result, in natural order, lands in b0 or
+// b1 (GShape::OUT).  b0 and b1 hold BUF points each.  The caller makes the
+// input visible to the group before the call; the result is visible to the
+// group on return.
+template <int N, int E>
+__device__ __forceinline__ float2 *fft_fwd_group(const float2 *in, float2 *b0, float2 *b1, int gl, int id,
+                                                 const float2 *__restrict__ tw, int power) {
+    using S = GShape<N, E>;
+    fpass<N, E, E, false, false, true>(in, b0, 0, gl, tw, 0);
+    group_sync<S::TPF>(id);
+    float2 *cur = b0, *nxt = b1;
+    int logP = S::LOGE;
+#pragma unroll 1
+    for (; logP + S::LOGRL < S::LOG; logP += S::LOGE) {
+        fpass<N, E, E, true, true, true>(cur, nxt, logP, gl, tw, 0);
+        group_sync<S::TPF>(id);
+        float2 *tmp = cur;
+        cur = nxt;
+        nxt = tmp;
+    }
+    fpass<N, E, S::RL, true, true, false>(cur, nxt, logP, gl, tw, power);
+    group_sync<S::TPF>(id);
+    return nxt;
+}
+
+// ---------------------------------------------------------------------------
+// k2_col: y transforms of one tile (4 columns) fused with the update.
+// Threads: four FFT groups of TPF threads (group c = column c, barrier 1 + c),
+// then the noise warps.  Shared memory (bytes): mbarrier | roots of unity (N)
+// | PHI: state chunk [pos][4] | XIN: product columns [c][pos] | XI: noise
+// [pos][4] | the four groups' buffer pairs.  A column's P lands in buffer OUT
+// of its group; the update writes the conjugated inverse input into the other.
+// ---------------------------------------------------------------------------
+template <int N, int E> struct Col2Smem {
+    using S = GShape<N, E>;
+    static constexpr size_t TW = 128;
+    static constexpr size_t PHI = TW + sizeof(float2) * N;
+    static constexpr size_t XIN = PHI + sizeof(float2) * 4 * N;
+    static constexpr size_t XI = XIN + sizeof(float2) * 4 * N;
+    static constexpr size_t WBUF = XI + sizeof(float2) * 4 * N;
+    static constexpr size_t BYTES = WBUF + sizeof(float2) * 4 * S::WS;
+    static constexpr int POFS = S::OUT * S::BUF;   // P (after the forward transform)
+    static constexpr int UOFS = S::BUF - POFS;     // the inverse's (conjugated) input
+};
+
+template <int N, int E>
+__global__ void __launch_bounds__(E == 8 ? 1024 : 768, 1) k2_col(const ColArgs<float> a) {
+    using C = float2;
+    using S = GShape<N, E>;
+    using L = Col2Smem<N, E>;
+    constexpr int TPF = S::TPF, NF = 4 * TPF;   // FFT threads of the CTA
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw);
+    C *TW = reinterpret_cast<C *>(smem_raw + L::TW);
+    C *PHI = reinterpret_cast<C *>(smem_raw + L::PHI);
+    C *XIN = reinterpret_cast<C *>(smem_raw + L::XIN);
+    C *XI = reinterpret_cast<C *>(smem_raw + L::XI);
+    C *WBUF = reinterpret_cast<C *>(smem_raw + L::WBUF);
+    __shared__ FieldP<float> sfp;
+    __shared__ uint32_t sstep;
+    const SysP<float> &sp = a.sp;
+    const FieldP<float> &fp = sfp;
+    const int t = threadIdx.x, nthr = blockDim.x;
+    const int g = t / TPF, gl = t - g * TPF;                                        // FFT group (column) and its thread
+    const int slot = a.slot0 + blockIdx.y;
+    const size_t sofs = (size_t)slot * a.slot_stride + (size_t)blockIdx.x * 4 * N;   // the tile's chunk / columns
+    const int kxt = blockIdx.x * 4;                                                  // first kx of the tile
+    const bool step_mode = a.mode == COL_STEP;
+    const uint32_t chunk = (uint32_t)(4 * N * sizeof(C));
+    pdl_wait();
+    pdl_trigger();
+    if (t == 0) {
+        mbar_init(bar, 1);
+        mbar_expect_tx(bar, (uint32_t)(N * sizeof(C)) + chunk * (step_mode ? 2u : 1u));
+        bulk_g2s(TW, a.tw + twiddle_offset(N, E), (uint32_t)(N * sizeof(C)), bar);
+        bulk_g2s(PHI, a.state + sofs, chunk, bar);
+        if (step_mode) bulk_g2s(XIN, a.in + sofs, chunk, bar);
+    }
+    static_assert(sizeof(FieldP<float>) % 4 == 0, "FieldP is copied as 32-bit words");
+    if (t < (int)(sizeof(FieldP<float>) / 4))
+        reinterpret_cast<uint32_t *>(&sfp)[t] = reinterpret_cast<const uint32_t *>(&a.fps[slot])[t];
+    if (t == 0) sstep = (uint32_t)(*a.d_step);
+    __syncthreads();   // the barrier is initialised, the parameters are in place
+
+    // ---- noise warps: the noise of every mode of the tile (pairs of
+    // neighbouring columns share one Philox call; two pairs in flight per thread)
+    if (t >= NF && step_mode && fp.noisy) {
+        const uint32_t step = sstep;
+        const int nt = t - NF, nn = nthr - NF;
+#pragma unroll 1
+        for (int i0 = nt; i0 < 2 * N; i0 += 2 * nn) {
+            C xa[2], xb[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int i = i0 + u * nn;
+                const int pos = i >> 1, kx0 = kxt + 2 * (i & 1);
+                xa[u] = mk<float>(0.f, 0.f);
+                xb[u] = xa[u];
+                if (i < 2 * N && kx0 < sp.hx) {
+                    const float qy = float(signed_k(pos, N)) * sp.gy;
+                    const float qx0 = float(kx0) * sp.gx, qx1 = float(kx0 + 1) * sp.gx;
+                    const float q2a = qx0 * qx0 + qy * qy, q2b = qx1 * qx1 + qy * qy;
+                    noise_pair<float>(kx0 == 0 || 2 * kx0 == sp.nx, kx0, pos, 0,
+                                      noise_amp<float>(fp.sigma0, fp.noise_pow, q2a),
+                                      noise_amp<float>(fp.sigma0, fp.noise_pow, q2b), kx0 + 1 < sp.hx, sp,
+                                      (uint32_t)fp.field_id, fp.seed_lo, fp.seed_hi, step, xa[u], xb[u]);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int i = i0 + u * nn;
+                if (i < 2 * N) st_pair<float>(XI + 4 * (i >> 1) + 2 * (i & 1), xa[u], xb[u]);
+            }
+        }
+    }
+    const bool ok = mbar_poll(bar, 0);
+
+    const int kmx = fp.kmax[0], kmy = fp.kmax[1];
+    const float scale = sp.inv_nsites;
+    C *gb = WBUF + (g & 3) * S::WS;
+    // Two transform phases from one call site: 0 = forward of the product
+    // column (step mode), 1 = inverse of the kept column, stored conjugated.
+#pragma unroll 1
+    for (int ph = 0; ph < 2; ++ph) {
+        const bool run = t < NF && (ph == 0 ? step_mode : kxt + g <= kmx);
+        if (run) {
+            const C *src = ph == 0 ? XIN + g * N : gb + L::UOFS;
+            C *o = fft_fwd_group<N, E>(src, ph == 0 ? gb : gb + L::POFS, ph == 0 ? gb + S::BUF : gb + L::UOFS, gl,
+                                       1 + g, TW, 0);
+            if (ph == 1) {
+                C *__restrict__ dst = a.out + sofs + (size_t)g * N;
+#pragma unroll 4
+                for (int p = gl; p < N; p += TPF) dst[p] = o[p];
+            }
+        }
+        if (ph == 1) break;
+        if (!__syncthreads_and(ok)) {
+            if (t == 0 && a.d_status) atomicOr(a.d_status, kStatusTimeout);
+            mbar_poll(bar, 0);   // copies still in flight land before the CTA's shared memory is released
+            __syncthreads();
+            return;
+        }
+        if (step_mode) {
+            // ---- update (Eq. timeupdate) of every mode, two neighbouring columns
+            // per thread and position, two positions in flight per thread
+            float dtO[kPolyTerms], dtM[kPolyTerms];
+#pragma unroll
+            for (int i = 0; i < kPolyTerms; ++i) {
+                dtO[i] = sp.dt * fp.O[i];
+                dtM[i] = sp.dt * fp.M[i];
+            }
+            const bool has_product = fp.power > 0, noisy = fp.noisy != 0;
+            bool bad = false;
+#pragma unroll 1
+            for (int i0 = t; i0 < 2 * N; i0 += 2 * nthr) {
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const int i = i0 + u * nthr;
+                    if (i >= 2 * N) break;
+                    const int pos = i >> 1, c0 = 2 * (i & 1), kx0 = kxt + c0;
+                    C f0, f1, x0 = mk<float>(0.f, 0.f), x1 = x0;
+                    ld_pair<float>(PHI + 4 * pos + c0, f0, f1);
+                    if (noisy) ld_pair<float>(XI + 4 * pos + c0, x0, x1);
+                    C *B0 = WBUF + c0 * S::WS;
+                    C v0 = B0[L::POFS + pos], v1 = B0[S::WS + L::POFS + pos];
+                    const float qy = float(signed_k(pos, N)) * sp.gy;
+                    const float qx0 = float(kx0) * sp.gx, qx1 = float(kx0 + 1) * sp.gx;
+                    const float q2a = qx0 * qx0 + qy * qy, q2b = qx1 * qx1 + qy * qy;
+                    v0 = update_mode<float>(f0, v0, x0, q2a, dtO, dtM, has_product);
+                    v1 = update_mode<float>(f1, v1, x1, q2b, dtO, dtM, has_product);
+                    if (kx0 >= sp.hx) v0 = mk<float>(0.f, 0.f);
+                    if (kx0 + 1 >= sp.hx) v1 = mk<float>(0.f, 0.f);
+                    bad |= !(fabsf(v0.x) + fabsf(v0.y) + fabsf(v1.x) + fabsf(v1.y) <= 3.0e38f);
+                    st_pair<float>(PHI + 4 * pos + c0, v0, v1);
+                    const bool ky_keep = abs(signed_k(pos, N)) <= kmy;
+                    const float s0 = (ky_keep && kx0 <= kmx) ? scale : 0.f;
+                    const float s1 = (ky_keep && kx0 + 1 <= kmx) ? scale : 0.f;
+                    B0[L::UOFS + pos] = mk<float>(v0.x * s0, -v0.y * s0);
+                    B0[S::WS + L::UOFS + pos] = mk<float>(v1.x * s1, -v1.y * s1);
+                }
+            }
+            if (bad && a.d_status) atomicOr(a.d_status, kStatusNonFinite);
+            __syncthreads();
+            // Hermitian part on the kx = 0 and kx = Nx/2 planes (the field is
+            // real): phi(kx, ky) <- (phi(kx, ky) + conj phi(kx, -ky)) / 2
+            const int kh = sp.nx / 2;
+            const int npl = (kxt == 0 ? 1 : 0) + ((kh >> 2) == (int)blockIdx.x ? 1 : 0);
+            if (npl > 0) {
+                const int cA = kxt == 0 ? 0 : (kh & 3), cB = kh & 3;
+                constexpr int HALF = N / 2 + 1;
+#pragma unroll 1
+                for (int i = t; i < npl * HALF; i += nthr) {
+                    const int j = i >= HALF ? 1 : 0, pos = i - j * HALF;
+                    const int c = j ? cB : cA;
+                    const int ppos = (N - pos) & (N - 1);
+                    const C u0 = PHI[4 * pos + c], u1 = PHI[4 * ppos + c];
+                    const C h = mk<float>(0.5f * (u0.x + u1.x), 0.5f * (u0.y - u1.y));
+                    PHI[4 * pos + c] = h;
+                    PHI[4 * ppos + c] = mk<float>(h.x, -h.y);
+                    const bool kxk = kxt + c <= kmx;
+                    C *U = WBUF + c * S::WS + L::UOFS;
+                    const float s0 = (kxk && abs(signed_k(pos, N)) <= kmy) ? scale : 0.f;
+                    const float s1 = (kxk && abs(signed_k(ppos, N)) <= kmy) ? scale : 0.f;
+                    U[pos] = mk<float>(h.x * s0, -h.y * s0);   // conj(h)
+                    U[ppos] = mk<float>(h.x * s1, h.y * s1);   // conj(conj(h))
+                }
+            }
+            // the state goes back with one bulk copy (its chunk is contiguous)
+            fence_proxy_async();
+            __syncthreads();
+            if (t == 0) {
+                C *sdst = a.state_out ? a.state_out : a.state;
+                bulk_s2g(sdst + sofs, PHI, chunk);
+                bulk_commit();
+            }
+        } else {
+            // start of a run: the inverse input is the de-aliased, scaled state
+#pragma unroll 1
+            for (int i = t; i < 4 * N; i += nthr) {
+                const int pos = i >> 2, c = i & 3;
+                const float sc = (kxt + c <= kmx && abs(signed_k(pos, N)) <= kmy) ? scale : 0.f;
+                const C v = PHI[i];
+                WBUF[c * S::WS + L::UOFS + pos] = mk<float>(v.x * sc, -v.y * sc);
+            }
+            __syncthreads();
+        }
+    }
+    if (step_mode && t == 0) bulk_wait_read();   // PHI outlives the state write-back
+}
+
+// ---------------------------------------------------------------------------
+// k2_row: x transforms of NW = blockDim / TPF pairs of rows, group j (barrier
+// 1 + j) on rows r0 + 2j, r0 + 2j + 1.  Shared memory: roots of unity (N) |
+// per group two buffers of BUF points, WS apart.
+// ---------------------------------------------------------------------------
+template <int N, int E> struct Row2Smem {
+    static size_t bytes(int nw) { return sizeof(float2) * ((size_t)N + (size_t)nw * GShape<N, E>::WS); }
+};
+
+template <int N, int E>
+__global__ void __launch_bounds__(512) k2_row(const RowArgs<float> a) {
+    using C = float2;
+    using S = GShape<N, E>;
+    constexpr int TPF = S::TPF;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    C *TW = reinterpret_cast<C *>(smem_raw);
+    C *WBUF = TW + N;
+    const SysP<float> &sp = a.sp;
+    const int NW = blockDim.x / TPF, logNW = __ffs(NW) - 1;   // NW a power of two
+    const int t = threadIdx.x, nthr = blockDim.x;
+    const int g = t / TPF, gl = t - g * TPF;
+    const int slot = a.slot0 + blockIdx.y;
+    const int rows = sp.rows;
+    const size_t sofs = (size_t)slot * a.slot_stride + (size_t)blockIdx.x * 2 * NW;   // first row of the CTA
+    constexpr int H = N / 2 + 1;
+    pdl_wait();
+    pdl_trigger();
+    {
+        const float4 *src = reinterpret_cast<const float4 *>(a.tw + twiddle_offset(N, E));
+        float4 *dst = reinterpret_cast<float4 *>(TW);
+        for (int i = t; i < N / 2; i += nthr) dst[i] = __ldg(src + i);
+    }
+    const int kc = a.fps[slot].kx_cols, power = a.fps[slot].power;
+    // ---- stage Y = conj(Z), Z_k = A_k + i B_k (k <= N/2), conj(A_{N-k}) +
+    // i conj(B_{N-k}) above, into the second buffer of group j.  T1 holds
+    // conj(A), conj(B): (ar, ai, br, bi) of rows r0 + 2j, r0 + 2j + 1 of column k.
+    {
+        const C *__restrict__ in = a.in + sofs;
+        const int total = H << logNW;
+#pragma unroll 1
+        for (int base = 0; base < total; base += 4 * nthr) {
+            float4 v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int idx = base + u * nthr + t;
+                const int k = idx >> logNW;
+                v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (idx < total && k < kc)
+                    v[u] = __ldcg(reinterpret_cast<const float4 *>(in + (size_t)k * rows + 2 * (idx & (NW - 1))));
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int idx = base + u * nthr + t;
+                if (idx >= total) break;
+                const int k = idx >> logNW;
+                C *Y = WBUF + (idx & (NW - 1)) * S::WS + S::BUF;
+                float ai = v[u].y, bi = v[u].w;
+                if (k == 0 || k == N / 2) { ai = 0.f; bi = 0.f; }   // the half spectra of real rows
+                Y[k] = mk<float>(v[u].x + bi, ai - v[u].z);
+                if (k > 0 && k < N / 2) Y[N - k] = mk<float>(v[u].x - bi, -ai - v[u].z);
+            }
+        }
+    }
+    __syncthreads();
+    // ---- z' = F(Y) = conj(z) = a - i b; its last pass stores u = a^p + i b^p,
+    // the product of both rows; then W = F(u).  Both results land in b1.
+    {
+        C *b0 = WBUF + g * S::WS, *b1 = b0 + S::BUF;
+        const C *src = b1;
+        C *p0 = b0, *p1 = b1;
+#pragma unroll 1
+        for (int it = 0; it < 2; ++it) {
+            C *o = fft_fwd_group<N, E>(src, p0, p1, gl, 1 + g, TW, it == 0 ? power : 0);
+            src = o;
+            p0 = o == b0 ? b1 : b0;
+            p1 = o;
+        }
+    }
+    __syncthreads();
+    // ---- split into the half spectra of the two rows:
+    // A_k = (W_k + conj W_{N-k}) / 2, B_k = (W_k - conj W_{N-k}) / 2i;
+    // (k, pair j) stored as 16 bytes
+    C *__restrict__ out = a.out + sofs;
+    const int total = H << logNW;
+#pragma unroll 1
+    for (int idx = t; idx < total; idx += nthr) {
+        const int k = idx >> logNW, j = idx & (NW - 1);
+        const C *Wj = WBUF + j * S::WS + S::BUF;
+        const C wk = Wj[k], wm = Wj[(N - k) & (N - 1)];
+        const float4 r = make_float4(0.5f * (wk.x + wm.x), 0.5f * (wk.y - wm.y), 0.5f * (wk.y + wm.y),
+                                     -0.5f * (wk.x - wm.x));
+        *reinterpret_cast<float4 *>(out + (size_t)k * rows + 2 * j) = r;
+    }
+    if (a.inc_step && blockIdx.x == 0 && blockIdx.y == 0 && t == 0) *a.d_step += 1;
+}
+
+// ---------------------------------------------------------------------------
+// launchers: E is the radix of the FFT passes (8 or 16; 8 only for N = 256)
+// ---------------------------------------------------------------------------
+template <int N, int E> cudaError_t launch_col2_ne(const ColArgs<float> &a, int nslots, int ntiles, cudaStream_t st) {
+    const int threads = 4 * GShape<N, E>::TPF + 32 * a.aux_warps;
+    if (a.aux_warps < 1 || threads > (E == 8 ? 1024 : 768)) return cudaErrorInvalidConfiguration;
+    cudaError_t e = ensure_smem(k2_col<N, E>, Col2Smem<N, E>::BYTES);
+    if (e != cudaSuccess) return e;
+    return launch_pdl(k2_col<N, E>, dim3(ntiles, nslots), threads, Col2Smem<N, E>::BYTES, st, a);
+}
+
+template <int N, int E> cudaError_t launch_row2_ne(const RowArgs<float> &a, int nslots, cudaStream_t st) {
+    const int nw = a.G, threads = nw * GShape<N, E>::TPF;
+    if (nw < 1 || nw > 8 || (nw & (nw - 1)) || a.sp.rows % (2 * nw) || threads > 512)
+        return cudaErrorInvalidConfiguration;
+    const size_t smem = Row2Smem<N, E>::bytes(nw);
+    cudaError_t e = ensure_smem(k2_row<N, E>, smem);
+    if (e != cudaSuccess) return e;
+    return launch_pdl(k2_row<N, E>, dim3(a.sp.rows / (2 * nw), nslots), threads, smem, st, a);
+}
+
+}  // namespace pss

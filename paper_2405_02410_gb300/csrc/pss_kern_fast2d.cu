@@ -1,0 +1,27 @@
+// FP32 2D step kernels with one FFT group per transform (sides of 256, 512 or 1024 points).
+#include "pss_fast2d.cuh"
+namespace pss {
+
+// a.E: radix of the FFT passes, 8 or 16 (sides of 256 take 8)
+cudaError_t launch_col2(const ColArgs<float> &a, int nslots, int ntiles, cudaStream_t st) {
+    const bool r16 = a.E == 16;
+    switch (a.sp.n_inner) {
+        case 256: return launch_col2_ne<256, 8>(a, nslots, ntiles, st);
+        case 512: return r16 ? launch_col2_ne<512, 16>(a, nslots, ntiles, st) : launch_col2_ne<512, 8>(a, nslots, ntiles, st);
+        case 1024:
+            return r16 ? launch_col2_ne<1024, 16>(a, nslots, ntiles, st) : launch_col2_ne<1024, 8>(a, nslots, ntiles, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_row2(const RowArgs<float> &a, int nslots, cudaStream_t st) {
+    const bool r16 = a.E == 16;
+    switch (a.sp.nx) {
+        case 256: return launch_row2_ne<256, 8>(a, nslots, st);
+        case 512: return r16 ? launch_row2_ne<512, 16>(a, nslots, st) : launch_row2_ne<512, 8>(a, nslots, st);
+        case 1024: return r16 ? launch_row2_ne<1024, 16>(a, nslots, st) : launch_row2_ne<1024, 8>(a, nslots, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace pss

@@ -1,9 +1,11 @@
 """Run a fixed number of Model B steps for profilers (ncu wraps this command).
 
     python -m paper_2405_02410_gb300.profile_run --shape 1024 1024 --steps 20 [--eager] [--fields 1|2]
+        [--tune key=value ...]
 
 --eager launches every step's kernels one by one (no CUDA graph); --fields 2
-adds a Model A field (the 3D Model A + B pair).
+adds a Model A field (the 3D Model A + B pair); --tune passes launch-shape
+settings to pss_set_tuning (e.g. fast2d=0 for the generic 2D kernels).
 """
 import argparse
 import os
@@ -19,6 +21,7 @@ def main():
     ap.add_argument("--fields", type=int, default=1)
     ap.add_argument("--precision", default="f32")
     ap.add_argument("--eager", action="store_true")
+    ap.add_argument("--tune", nargs="*", default=[], help="key=value launch-shape settings")
     args = ap.parse_args()
     import torch
     from paper_2405_02410_gb300 import build
@@ -34,6 +37,9 @@ def main():
         s = pss.model_b(shape, dt=0.01, a=-1, b=1, K=1, D=0.01, seed=2405, precision=args.precision)
         if args.fields == 2:
             pss.add_model_a_field(s, a=-1, b=1, K=1, D=0.05, name="psi")
+    for kv in args.tune:
+        k, v = kv.split("=")
+        s.set_tuning(k, int(v))
     for f in range(args.fields):
         s.init_uniform(f, -0.1, 0.1)
     if args.eager:
