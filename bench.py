@@ -471,10 +471,11 @@ def run_gpu(args):
     peaks, peak_kind = measured_peaks()
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     names = {0: "col", 2: "row"}
+    kernel_names = {0: "k2_col", 2: "k2_row"} if s.step_path == "fast2d" else {0: "k_col", 2: "k_row"}
     dom = max((0, 2), key=lambda k: kern_ms[k])
     dom_name = names[dom]
     achieved = ab[dom_name] / (kern_ms[dom] * 1e-3) / 1e9
-    traffic = recorded_traffic("k_col" if dom == 0 else "k_row")
+    traffic = recorded_traffic(kernel_names[dom])
 
     # end to end through the public API with host buffers: pinned upload of phi_0,
     # steps, S(q) to the host every INTERVAL steps, final field to the host
@@ -548,10 +549,10 @@ def run_gpu(args):
                    "global_batch": world, "seq_len": sites, "parallelism": "replicas" if world > 1 else "single",
                    "l2": "flushed (512 MiB write) before every 1000-step interval; the ~11 MB working set is "
                          "L2-resident inside an interval"},
-        "roofline": {"bound": "hbm", "kernel": "k_col" if dom == 0 else "k_row", "achieved": achieved,
+        "roofline": {"bound": "hbm", "kernel": kernel_names[dom], "achieved": achieved,
                      "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
                      "peak_source": f"{peak_kind} hbm_gbs", "step_frac": (ab["step"] / (ms_per_step * 1e-3) / 1e9) / hbm,
-                     "kernel_ms": {"col": kern_ms[0], "row": kern_ms[2]},
+                     "kernel_ms": {kernel_names[0]: kern_ms[0], kernel_names[2]: kern_ms[2]},
                      "algorithmic_bytes": {"col": ab["col"], "row": ab["row"], "step": ab["step"]}},
         "e2e": {"value": sites * K * world / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d / K,
                 "d2h_bytes_per_step": d2h / K},

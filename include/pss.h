@@ -177,9 +177,11 @@ int pss_time_kernels(pss_system *s, int64_t n, double *avg_ms);
  *   "fast2d"      FP32 2D systems whose sides are 256, 512 or 1024 points
  *                 run every transform in one warp (1, default) or take the
  *                 generic kernels (0); the two agree to FP32 rounding;
- *   "col2_warps"  noise warps beside the FFT warps of a column CTA of that
- *                 path (1..24);
+ *   "col2_warps"  warps beside the FFT groups of a column CTA of that path
+ *                 that join its update (1..24);
  *   "row2_pairs"  row pairs per row CTA of that path (power of two <= 8);
+ *   "row2_noise"  warps per row CTA of that path that draw the next step's
+ *                 noise (1..24);
  *   "col2_radix", "row2_radix"
  *                 radix of that path's FFT passes (8 or 16);
  * 0 restores the automatic choice.  Unknown keys return PSS_EINVAL. */
@@ -242,6 +244,13 @@ const char *pss_last_error(const pss_system *s);
 /* Number of kernel launches this handle has issued (a count kept by the
  * host; for measurement). */
 int64_t pss_launch_count(const pss_system *s);
+
+/* Which kernels a step of this system runs (for measurement and profiling):
+ * 1 = the FP32 2D kernels with one FFT group per transform (k2_col, k2_row:
+ * FP32 2D systems with sides of 256, 512 or 1024 points, unless the tuning
+ * key "fast2d" is 0), 0 = the generic kernels (k_col, k_mid, k_row).
+ * Returns PSS_EINVAL for a NULL handle. */
+int pss_step_path(const pss_system *s);
 
 #ifdef __cplusplus
 }

@@ -68,6 +68,7 @@ struct pss_system {
     long long nsites = 0;
     size_t field_elems = 0;                  // complex elements of one slot of one array
     void *state = nullptr, *A = nullptr, *B = nullptr;   // [slot][field_elems]
+    void *XI = nullptr;                      // fast 2D path: unit-amplitude noise of the next step [slot][field_elems]
     void *fps = nullptr;                     // FieldP<T>[slots] on the device
     bool fps_dirty = true;
     void *tw = nullptr;                      // roots of unity, precision of the system
@@ -88,6 +89,7 @@ struct pss_system {
     int tune_fast2d = 1;                     // FP32 2D sides of 256..1024: one warp per transform (0 = generic kernels)
     int tune_col2_warps = 0, tune_row2_pairs = 0;   // its noise warps per column CTA, row pairs per row CTA
     int tune_col2_radix = 0, tune_row2_radix = 0;   // its FFT pass radix (8 or 16; 0 = automatic)
+    int tune_row2_noise = 0;                 // noise warps per row CTA of that path (0 = automatic)
     int64_t launches = 0;
     std::string err;
     // adjoint: checkpoints of the last pss_adjoint_forward run
@@ -277,8 +279,18 @@ int col2_radix(const pss_system *s) { return s->ny >= 512 && s->tune_col2_radix 
 int row2_radix(const pss_system *s) { return s->nx >= 512 && s->tune_row2_radix != 8 ? 16 : 8; }
 int col2_warps(const pss_system *s) {
     const int fft_warps = 4 * s->ny / col2_radix(s) / 32;
-    const int want = s->tune_col2_warps > 0 ? s->tune_col2_warps : 16;
+    const int want = s->tune_col2_warps > 0 ? s->tune_col2_warps : 8;
     return std::min(want, (col2_radix(s) == 8 ? 32 : 24) - fft_warps);
+}
+int row2_noise_warps(const pss_system *s, int pairs) {
+    const int fft_warps = pairs * s->nx / row2_radix(s) / 32;
+    const int want = s->tune_row2_noise > 0 ? s->tune_row2_noise : 16;
+    return std::max(1, std::min(want, 32 - fft_warps));
+}
+bool any_noisy(const pss_system *s) {
+    for (const Field &f : s->fields)
+        if (f.noisy) return true;
+    return false;
 }
 // row pairs per CTA: a power of two with at most 512 threads per CTA
 int row2_pairs(const pss_system *s) {
@@ -441,6 +453,7 @@ template <typename T> struct Seq {
             a.mode = mode;
             a.aux_warps = col2_warps(s);
             a.E = col2_radix(s);
+            a.noise = any_noisy(s) ? (const float2 *)s->XI : nullptr;
             const int nt = mode == COL_INV_MASK ? max_kept_tiles(s) : s->ntiles;
             if (timer) timer->begin(0, st);
             cudaError_t e = launch_col2(a, nslots, nt, st);
@@ -454,6 +467,7 @@ template <typename T> struct Seq {
         }
     }
 
+    // (the step counter is advanced by k2_col; inc documents the caller's intent)
     int row2(bool inc) {
         if constexpr (std::is_same<T, float>::value) {
             RowArgs<float> a{};
@@ -471,7 +485,9 @@ template <typename T> struct Seq {
             a.E = row2_radix(s);
             a.kx_cols_max = 0;
             for (int i = 0; i < (int)s->fields.size(); ++i) a.kx_cols_max = std::max(a.kx_cols_max, kept_cols(s, i));
-            a.inc_step = inc ? 1 : 0;
+            a.inc_step = 0;   // k2_col advances the step counter
+            a.noise = any_noisy(s) ? (float2 *)s->XI : nullptr;
+            a.noise_warps = a.noise ? row2_noise_warps(s, a.G) : 0;
             if (timer) timer->begin(2, st);
             cudaError_t e = launch_row2(a, nslots, st);
             if (timer) timer->begin(2, st);
@@ -594,6 +610,11 @@ template <typename T> int run_prologue(pss_system *s) {
 
 int prologue(pss_system *s) {
     if (!s->stale && s->b_fast == fast2d(s)) return PSS_OK;
+    if (fast2d(s) && !s->XI) {
+        const size_t bytes = csize(s) * s->field_elems * (size_t)s->nslots();
+        CK(cudaMalloc(&s->XI, bytes));
+        CK(cudaMemset(s->XI, 0, bytes));
+    }
     int rc = s->prec == PSS_F64 ? run_prologue<double>(s) : run_prologue<float>(s);
     if (rc) return rc;
     s->stale = false;
@@ -738,6 +759,8 @@ int grow_arrays(pss_system *s, int old_nf) {
     }
     cudaFree(s->fps);
     s->fps = nullptr;
+    cudaFree(s->XI);   // drawn-ahead noise of the fast 2D path: reallocated for the new slot count
+    s->XI = nullptr;
     CK(cudaMalloc(&s->fps, fpsize(s) * (size_t)s->batch * nf));
     s->fps_dirty = true;
     return PSS_OK;
@@ -933,6 +956,7 @@ int pss_destroy_system(pss_system *s) {
     cudaFree(s->state);
     cudaFree(s->A);
     cudaFree(s->B);
+    cudaFree(s->XI);
     cudaFree(s->fps);
     cudaFree(s->tw);
     cudaFree(s->real);
@@ -1079,6 +1103,8 @@ int pss_set_noise(pss_system *s, int field_id, int D_param_id, int q2_pow) {
     f.noise_param = D_param_id;
     f.noise_pow = q2_pow;
     s->fps_dirty = true;
+    s->stale = true;   // the fast 2D path keeps the next step's noise drawn ahead
+    invalidate(s);
     return PSS_OK;
 }
 
@@ -1272,6 +1298,10 @@ int pss_set_tuning(pss_system *s, const char *key, int value) {
         s->tune_col2_warps = value;
     }
     else if (k == "row2_pairs") s->tune_row2_pairs = value;
+    else if (k == "row2_noise") {
+        if (value > 24) return fail(s, PSS_EINVAL, "row2_noise is at most 24 (0 = automatic)");
+        s->tune_row2_noise = value;
+    }
     else if (k == "col2_radix" || k == "row2_radix") {
         if (value != 0 && value != 8 && value != 16) return fail(s, PSS_EINVAL, "radix 8 or 16 (0 = automatic)");
         (k == "col2_radix" ? s->tune_col2_radix : s->tune_row2_radix) = value;
@@ -1298,6 +1328,7 @@ int pss_set_step(pss_system *s, int64_t step) {
     CK(cudaMemcpyAsync(s->d_step, &v, sizeof v, cudaMemcpyHostToDevice, s->stream));
     CK(cudaStreamSynchronize(s->stream));
     s->step = step;
+    s->stale = true;   // the fast 2D path keeps the next step's noise drawn ahead
     return PSS_OK;
 }
 
@@ -1460,5 +1491,7 @@ int pss_sync(pss_system *s) {
 const char *pss_last_error(const pss_system *s) { return s ? s->err.c_str() : g_create_err.c_str(); }
 
 int64_t pss_launch_count(const pss_system *s) { return s ? s->launches : 0; }
+
+int pss_step_path(const pss_system *s) { return s ? (fast2d(s) ? 1 : 0) : PSS_EINVAL; }
 
 }  // extern "C"

@@ -6,17 +6,20 @@
 // passes meet at __syncwarp instead of CTA barriers.  Two kernels per step,
 // with the same split of the work as the generic path:
 //
-//   k2_col (one CTA per tile of kTileW = 4 columns kx, all ky): four FFT warps
-//       (one per column) stage the state and the x-transformed product with
-//       TMA and run the forward y-FFT, while the remaining "noise" warps draw
-//       the Philox noise of the tile's modes into shared memory.  Then every
-//       warp updates the modes (Eq. timeupdate), the Hermitian part is taken on
-//       the kx = 0, Nx/2 planes, the state goes back with one bulk copy and the
-//       FFT warps transform the de-aliased, 1/N_sites-scaled kept columns back
-//       along y.
-//   k2_row (one CTA per NW pairs of rows): warp j takes rows r0 + 2j and
+//   k2_col (one CTA per tile of kTileW = 4 columns kx, all ky): the state,
+//       the x-transformed product and the step's noise are staged with TMA;
+//       four FFT groups (one per column) run the forward y-FFT; then every warp
+//       updates the modes (Eq. timeupdate), the Hermitian part is taken on the
+//       kx = 0, Nx/2 planes, the state goes back with one bulk copy and the FFT
+//       groups transform the de-aliased, 1/N_sites-scaled kept columns back
+//       along y.  Block 0 advances the step counter.
+//   k2_row (one CTA per NW pairs of rows): group j takes rows r0 + 2j and
 //       r0 + 2j + 1 as one complex transform (z = a + i b): C2R of the kept
 //       columns, power p in real space, R2C, split into the two half spectra.
+//       Beside the transform groups, "noise" warps draw the Philox noise of the
+//       next step (unit amplitude, tiled like the state) for the column kernel:
+//       the generator has no data dependence, so it fills the issue slots the
+//       latency-bound transforms leave idle.
 //
 // Only forward transforms are coded: an inverse is conj(F(conj(x))).  The
 // column kernel stores the conjugate of its y-inverse (T1 = F(conj X)), which
@@ -67,6 +70,21 @@ template <int TPF> __device__ __forceinline__ void group_sync(int id) {
     } else {
         asm volatile("bar.sync %0, %1;" ::"r"(id), "n"(TPF) : "memory");
     }
+}
+
+// The AND of `pred` over the `nthreads` threads meeting at named barrier `id`
+// (every one of them gets the same answer).
+__device__ __forceinline__ bool bar_and(int id, int nthreads, bool pred) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.and.pred q, %2, %3, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)pred), "r"(id), "r"(nthreads)
+        : "memory");
+    return r != 0;
 }
 
 // Intermediate pass results are padded: position p lives at p + p/16, which
@@ -148,10 +166,11 @@ __device__ __forceinline__ float2 *fft_fwd_group(const float2 *in, float2 *b0, f
 // ---------------------------------------------------------------------------
 // k2_col: y transforms of one tile (4 columns) fused with the update.
 // Threads: four FFT groups of TPF threads (group c = column c, barrier 1 + c),
-// then the noise warps.  Shared memory (bytes): mbarrier | roots of unity (N)
-// | PHI: state chunk [pos][4] | XIN: product columns [c][pos] | XI: noise
-// [pos][4] | the four groups' buffer pairs.  A column's P lands in buffer OUT
-// of its group; the update writes the conjugated inverse input into the other.
+// then helper warps that join the update.  Shared memory (bytes): mbarrier |
+// roots of unity (N) | PHI: state chunk [pos][4] | XIN: product columns
+// [c][pos] | XI: unit-amplitude noise [pos][4] | the four groups' buffer
+// pairs.  A column's P lands in buffer OUT of its group; the update writes
+// the conjugated inverse input into the other.
 // ---------------------------------------------------------------------------
 template <int N, int E> struct Col2Smem {
     using S = GShape<N, E>;
@@ -179,7 +198,6 @@ __global__ void __launch_bounds__(E == 8 ? 1024 : 768, 1) k2_col(const ColArgs<f
     C *XI = reinterpret_cast<C *>(smem_raw + L::XI);
     C *WBUF = reinterpret_cast<C *>(smem_raw + L::WBUF);
     __shared__ FieldP<float> sfp;
-    __shared__ uint32_t sstep;
     const SysP<float> &sp = a.sp;
     const FieldP<float> &fp = sfp;
     const int t = threadIdx.x, nthr = blockDim.x;
@@ -188,53 +206,22 @@ __global__ void __launch_bounds__(E == 8 ? 1024 : 768, 1) k2_col(const ColArgs<f
     const size_t sofs = (size_t)slot * a.slot_stride + (size_t)blockIdx.x * 4 * N;   // the tile's chunk / columns
     const int kxt = blockIdx.x * 4;                                                  // first kx of the tile
     const bool step_mode = a.mode == COL_STEP;
+    const bool with_noise = step_mode && a.noise != nullptr;
     const uint32_t chunk = (uint32_t)(4 * N * sizeof(C));
     pdl_wait();
     pdl_trigger();
     if (t == 0) {
         mbar_init(bar, 1);
-        mbar_expect_tx(bar, (uint32_t)(N * sizeof(C)) + chunk * (step_mode ? 2u : 1u));
+        mbar_expect_tx(bar, (uint32_t)(N * sizeof(C)) + chunk * (step_mode ? (with_noise ? 3u : 2u) : 1u));
         bulk_g2s(TW, a.tw + twiddle_offset(N, E), (uint32_t)(N * sizeof(C)), bar);
         bulk_g2s(PHI, a.state + sofs, chunk, bar);
         if (step_mode) bulk_g2s(XIN, a.in + sofs, chunk, bar);
+        if (with_noise) bulk_g2s(XI, a.noise + sofs, chunk, bar);
     }
     static_assert(sizeof(FieldP<float>) % 4 == 0, "FieldP is copied as 32-bit words");
     if (t < (int)(sizeof(FieldP<float>) / 4))
         reinterpret_cast<uint32_t *>(&sfp)[t] = reinterpret_cast<const uint32_t *>(&a.fps[slot])[t];
-    if (t == 0) sstep = (uint32_t)(*a.d_step);
     __syncthreads();   // the barrier is initialised, the parameters are in place
-
-    // ---- noise warps: the noise of every mode of the tile (pairs of
-    // neighbouring columns share one Philox call; two pairs in flight per thread)
-    if (t >= NF && step_mode && fp.noisy) {
-        const uint32_t step = sstep;
-        const int nt = t - NF, nn = nthr - NF;
-#pragma unroll 1
-        for (int i0 = nt; i0 < 2 * N; i0 += 2 * nn) {
-            C xa[2], xb[2];
-#pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                const int i = i0 + u * nn;
-                const int pos = i >> 1, kx0 = kxt + 2 * (i & 1);
-                xa[u] = mk<float>(0.f, 0.f);
-                xb[u] = xa[u];
-                if (i < 2 * N && kx0 < sp.hx) {
-                    const float qy = float(signed_k(pos, N)) * sp.gy;
-                    const float qx0 = float(kx0) * sp.gx, qx1 = float(kx0 + 1) * sp.gx;
-                    const float q2a = qx0 * qx0 + qy * qy, q2b = qx1 * qx1 + qy * qy;
-                    noise_pair<float>(kx0 == 0 || 2 * kx0 == sp.nx, kx0, pos, 0,
-                                      noise_amp<float>(fp.sigma0, fp.noise_pow, q2a),
-                                      noise_amp<float>(fp.sigma0, fp.noise_pow, q2b), kx0 + 1 < sp.hx, sp,
-                                      (uint32_t)fp.field_id, fp.seed_lo, fp.seed_hi, step, xa[u], xb[u]);
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                const int i = i0 + u * nn;
-                if (i < 2 * N) st_pair<float>(XI + 4 * (i >> 1) + 2 * (i & 1), xa[u], xb[u]);
-            }
-        }
-    }
     const bool ok = mbar_poll(bar, 0);
 
     const int kmx = fp.kmax[0], kmy = fp.kmax[1];
@@ -271,7 +258,8 @@ __global__ void __launch_bounds__(E == 8 ? 1024 : 768, 1) k2_col(const ColArgs<f
                 dtO[i] = sp.dt * fp.O[i];
                 dtM[i] = sp.dt * fp.M[i];
             }
-            const bool has_product = fp.power > 0, noisy = fp.noisy != 0;
+            const bool has_product = fp.power > 0, noisy = with_noise && fp.noisy != 0;
+            const float sigma0 = fp.sigma0;
             bool bad = false;
 #pragma unroll 1
             for (int i0 = t; i0 < 2 * N; i0 += 2 * nthr) {
@@ -282,7 +270,11 @@ __global__ void __launch_bounds__(E == 8 ? 1024 : 768, 1) k2_col(const ColArgs<f
                     const int pos = i >> 1, c0 = 2 * (i & 1), kx0 = kxt + c0;
                     C f0, f1, x0 = mk<float>(0.f, 0.f), x1 = x0;
                     ld_pair<float>(PHI + 4 * pos + c0, f0, f1);
-                    if (noisy) ld_pair<float>(XI + 4 * pos + c0, x0, x1);
+                    if (noisy) {
+                        ld_pair<float>(XI + 4 * pos + c0, x0, x1);
+                        x0 = cscale<float>(x0, sigma0);
+                        x1 = cscale<float>(x1, sigma0);
+                    }
                     C *B0 = WBUF + c0 * S::WS;
                     C v0 = B0[L::POFS + pos], v1 = B0[S::WS + L::POFS + pos];
                     const float qy = float(signed_k(pos, N)) * sp.gy;
@@ -347,29 +339,68 @@ __global__ void __launch_bounds__(E == 8 ? 1024 : 768, 1) k2_col(const ColArgs<f
             __syncthreads();
         }
     }
-    if (step_mode && t == 0) bulk_wait_read();   // PHI outlives the state write-back
+    if (step_mode && t == 0) {
+        bulk_wait_read();   // PHI outlives the state write-back
+        if (blockIdx.x == 0 && blockIdx.y == 0) *a.d_step += 1;   // no CTA of this kernel reads it
+    }
 }
 
 // ---------------------------------------------------------------------------
-// k2_row: x transforms of NW = blockDim / TPF pairs of rows, group j (barrier
-// 1 + j) on rows r0 + 2j, r0 + 2j + 1.  Shared memory: roots of unity (N) |
-// per group two buffers of BUF points, WS apart.
+// k2_row: x transforms of NW = a.G pairs of rows, group j (barrier 1 + j) on
+// rows r0 + 2j, r0 + 2j + 1, then the noise warps.  The transform threads
+// meet at barrier 15.  Shared memory: mbarrier | roots of unity (N) | per
+// group two buffers of BUF points, WS apart.
 // ---------------------------------------------------------------------------
 template <int N, int E> struct Row2Smem {
-    static size_t bytes(int nw) { return sizeof(float2) * ((size_t)N + (size_t)nw * GShape<N, E>::WS); }
+    static size_t bytes(int nw) { return 128 + sizeof(float2) * ((size_t)N + (size_t)nw * GShape<N, E>::WS); }
 };
 
+// Unit-amplitude noise (sigma0 = 1) of pairs q0, q0 + stride, ... < q1 of one
+// slot, step `step`; pair q = (tile ny + pos) 2 + cp covers columns
+// 4 tile + 2 cp, 4 tile + 2 cp + 1 at ky = pos and is stored as 16 bytes at
+// element 2 q of the slot's tiled array.  Two pairs in flight per thread.
+__device__ __forceinline__ void noise_range(const SysP<float> &sp, const FieldP<float> &fp, uint32_t step,
+                                            float2 *__restrict__ out, int q0, int q1, int stride) {
+    const int logny = __ffs(sp.ny) - 1;
+#pragma unroll 1
+    for (int qa = q0; qa < q1; qa += 2 * stride) {
+        float2 xa[2], xb[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int q = qa + u * stride;
+            const int rest = q >> 1, pos = rest & (sp.ny - 1), kx0 = ((rest >> logny) << 2) + 2 * (q & 1);
+            xa[u] = mk<float>(0.f, 0.f);
+            xb[u] = xa[u];
+            if (q < q1 && kx0 < sp.hx) {
+                const float qy = float(signed_k(pos, sp.ny)) * sp.gy;
+                const float qx0 = float(kx0) * sp.gx, qx1 = float(kx0 + 1) * sp.gx;
+                const float q2a = qx0 * qx0 + qy * qy, q2b = qx1 * qx1 + qy * qy;
+                noise_pair<float>(kx0 == 0 || 2 * kx0 == sp.nx, kx0, pos, 0, noise_amp<float>(1.f, fp.noise_pow, q2a),
+                                  noise_amp<float>(1.f, fp.noise_pow, q2b), kx0 + 1 < sp.hx, sp, (uint32_t)fp.field_id,
+                                  fp.seed_lo, fp.seed_hi, step, xa[u], xb[u]);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int q = qa + u * stride;
+            if (q < q1) st_pair<float>(out + 2 * (size_t)q, xa[u], xb[u]);
+        }
+    }
+}
+
 template <int N, int E>
-__global__ void __launch_bounds__(512) k2_row(const RowArgs<float> a) {
+__global__ void __launch_bounds__(1024) k2_row(const RowArgs<float> a) {
     using C = float2;
     using S = GShape<N, E>;
     constexpr int TPF = S::TPF;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    C *TW = reinterpret_cast<C *>(smem_raw);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw);
+    C *TW = reinterpret_cast<C *>(smem_raw + 128);
     C *WBUF = TW + N;
     const SysP<float> &sp = a.sp;
-    const int NW = blockDim.x / TPF, logNW = __ffs(NW) - 1;   // NW a power of two
-    const int t = threadIdx.x, nthr = blockDim.x;
+    const int NW = a.G, logNW = __ffs(NW) - 1;   // NW a power of two
+    const int nf = NW * TPF;                     // transform threads
+    const int t = threadIdx.x;
     const int g = t / TPF, gl = t - g * TPF;
     const int slot = a.slot0 + blockIdx.y;
     const int rows = sp.rows;
@@ -377,43 +408,65 @@ __global__ void __launch_bounds__(512) k2_row(const RowArgs<float> a) {
     constexpr int H = N / 2 + 1;
     pdl_wait();
     pdl_trigger();
-    {
-        const float4 *src = reinterpret_cast<const float4 *>(a.tw + twiddle_offset(N, E));
-        float4 *dst = reinterpret_cast<float4 *>(TW);
-        for (int i = t; i < N / 2; i += nthr) dst[i] = __ldg(src + i);
+    if (t >= nf) {
+        // ---- noise warps: this CTA's share of the next step's noise
+        const FieldP<float> &fp = a.fps[slot];
+        if (a.noise && fp.noisy) {
+            const int Q = sp.ntiles * sp.ny * 2, nb = gridDim.x, b = blockIdx.x;
+            noise_range(sp, fp, (uint32_t)(*a.d_step), a.noise + (size_t)slot * a.slot_stride,
+                        (int)((long long)Q * b / nb) + (t - nf), (int)((long long)Q * (b + 1) / nb),
+                        (int)blockDim.x - nf);
+        }
+        return;
     }
-    const int kc = a.fps[slot].kx_cols, power = a.fps[slot].power;
+    // roots of unity: one bulk copy, in flight while the rows are loaded
+    if (t == 0) {
+        mbar_init(bar, 1);
+        mbar_expect_tx(bar, (uint32_t)(N * sizeof(C)));
+        bulk_g2s(TW, a.tw + twiddle_offset(N, E), (uint32_t)(N * sizeof(C)), bar);
+    }
     // ---- stage Y = conj(Z), Z_k = A_k + i B_k (k <= N/2), conj(A_{N-k}) +
     // i conj(B_{N-k}) above, into the second buffer of group j.  T1 holds
     // conj(A), conj(B): (ar, ai, br, bi) of rows r0 + 2j, r0 + 2j + 1 of column k.
+    // All of a thread's loads are issued before the first use.
+    const int kcm = a.kx_cols_max;
     {
         const C *__restrict__ in = a.in + sofs;
         const int total = H << logNW;
 #pragma unroll 1
-        for (int base = 0; base < total; base += 4 * nthr) {
-            float4 v[4];
+        for (int base = 0; base < total; base += 8 * nf) {
+            float4 v[8];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int idx = base + u * nthr + t;
+            for (int u = 0; u < 8; ++u) {
+                const int idx = base + u * nf + t;
                 const int k = idx >> logNW;
                 v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (idx < total && k < kc)
+                if (idx < total && k < kcm)
                     v[u] = __ldcg(reinterpret_cast<const float4 *>(in + (size_t)k * rows + 2 * (idx & (NW - 1))));
             }
+            const int kc = a.fps[slot].kx_cols;
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int idx = base + u * nthr + t;
+            for (int u = 0; u < 8; ++u) {
+                const int idx = base + u * nf + t;
                 if (idx >= total) break;
                 const int k = idx >> logNW;
                 C *Y = WBUF + (idx & (NW - 1)) * S::WS + S::BUF;
-                float ai = v[u].y, bi = v[u].w;
+                float ar = v[u].x, ai = v[u].y, br = v[u].z, bi = v[u].w;
+                if (k >= kc) { ar = 0.f; ai = 0.f; br = 0.f; bi = 0.f; }
                 if (k == 0 || k == N / 2) { ai = 0.f; bi = 0.f; }   // the half spectra of real rows
-                Y[k] = mk<float>(v[u].x + bi, ai - v[u].z);
-                if (k > 0 && k < N / 2) Y[N - k] = mk<float>(v[u].x - bi, -ai - v[u].z);
+                Y[k] = mk<float>(ar + bi, ai - br);
+                if (k > 0 && k < N / 2) Y[N - k] = mk<float>(ar - bi, -ai - br);
             }
         }
     }
-    __syncthreads();
+    const int power = a.fps[slot].power;
+    asm volatile("bar.sync 15, %0;" ::"r"(nf) : "memory");   // the mbarrier is initialised; Y is staged
+    if (!bar_and(15, nf, mbar_poll(bar, 0))) {
+        // the copy did not land in time: record it, wait (bounded) for it and leave together
+        if (t == 0 && a.d_status) atomicOr(a.d_status, kStatusTimeout);
+        mbar_poll(bar, 0);
+        return;
+    }
     // ---- z' = F(Y) = conj(z) = a - i b; its last pass stores u = a^p + i b^p,
     // the product of both rows; then W = F(u).  Both results land in b1.
     {
@@ -428,14 +481,14 @@ __global__ void __launch_bounds__(512) k2_row(const RowArgs<float> a) {
             p1 = o;
         }
     }
-    __syncthreads();
+    asm volatile("bar.sync 15, %0;" ::"r"(nf) : "memory");
     // ---- split into the half spectra of the two rows:
     // A_k = (W_k + conj W_{N-k}) / 2, B_k = (W_k - conj W_{N-k}) / 2i;
     // (k, pair j) stored as 16 bytes
     C *__restrict__ out = a.out + sofs;
     const int total = H << logNW;
 #pragma unroll 1
-    for (int idx = t; idx < total; idx += nthr) {
+    for (int idx = t; idx < total; idx += nf) {
         const int k = idx >> logNW, j = idx & (NW - 1);
         const C *Wj = WBUF + j * S::WS + S::BUF;
         const C wk = Wj[k], wm = Wj[(N - k) & (N - 1)];
@@ -443,7 +496,6 @@ __global__ void __launch_bounds__(512) k2_row(const RowArgs<float> a) {
                                      -0.5f * (wk.x - wm.x));
         *reinterpret_cast<float4 *>(out + (size_t)k * rows + 2 * j) = r;
     }
-    if (a.inc_step && blockIdx.x == 0 && blockIdx.y == 0 && t == 0) *a.d_step += 1;
 }
 
 // ---------------------------------------------------------------------------
@@ -458,8 +510,8 @@ template <int N, int E> cudaError_t launch_col2_ne(const ColArgs<float> &a, int 
 }
 
 template <int N, int E> cudaError_t launch_row2_ne(const RowArgs<float> &a, int nslots, cudaStream_t st) {
-    const int nw = a.G, threads = nw * GShape<N, E>::TPF;
-    if (nw < 1 || nw > 8 || (nw & (nw - 1)) || a.sp.rows % (2 * nw) || threads > 512)
+    const int nw = a.G, threads = nw * GShape<N, E>::TPF + 32 * a.noise_warps;
+    if (nw < 1 || nw > 8 || (nw & (nw - 1)) || a.sp.rows % (2 * nw) || a.noise_warps < 0 || threads > 1024)
         return cudaErrorInvalidConfiguration;
     const size_t smem = Row2Smem<N, E>::bytes(nw);
     cudaError_t e = ensure_smem(k2_row<N, E>, smem);

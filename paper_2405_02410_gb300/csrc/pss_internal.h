@@ -89,7 +89,7 @@ template <typename T> struct ColArgs {
     size_t slot_stride;
     int slot0;
     const cplx<T> *tw;
-    const long long *d_step;
+    long long *d_step;    // step counter (k2_col advances it)
     int *d_status;
     int mode, tiles_per_cta, n_tiles;
     int E;                // FFT radix cap (8 or 16), chosen by the host
@@ -100,7 +100,8 @@ template <typename T> struct ColArgs {
     long long adj_step;
     const long long *d_adj_base;   // if set, the noise step is adj_step + *d_adj_base
     double *grad;
-    int aux_warps;        // k2_col: warps that draw the noise beside the four FFT warps
+    int aux_warps;        // k2_col: warps that join the update beside the FFT warps
+    const cplx<T> *noise; // k2_col: unit-amplitude noise of this step (tiled like the state)
 };
 
 template <typename T> struct RowArgs {
@@ -118,6 +119,8 @@ template <typename T> struct RowArgs {
     int mode, G, inc_step;
     int E;                // FFT radix cap (8 or 16)
     int kx_cols_max;      // largest kept half-spectrum column count over the launch's slots
+    cplx<T> *noise;       // k2_row: where the unit-amplitude noise of step *d_step goes (null: none)
+    int noise_warps;      // k2_row: warps that draw it beside the transform warps
 };
 
 template <typename T> struct MidArgs {

@@ -29,7 +29,7 @@ EXPORTS = [
     "pss_set_spectrum", "pss_structure_factor", "pss_sync", "pss_last_error", "pss_launch_count",
     "pss_time_kernels", "pss_set_tuning", "pss_create_batch", "pss_batch_size", "pss_select_instance",
     "pss_set_param_batch", "pss_step_many", "pss_adjoint_forward", "pss_adjoint_backward",
-    "pss_structure_factor_noalloc",
+    "pss_structure_factor_noalloc", "pss_step_path",
 ]
 
 
@@ -69,6 +69,7 @@ def _load():
         "pss_sync": ([vp], i32),
         "pss_last_error": ([vp], ctypes.c_char_p),
         "pss_launch_count": ([vp], i64),
+        "pss_step_path": ([vp], i32),
         "pss_time_kernels": ([vp, i64, P(d)], i32),
         "pss_set_tuning": ([vp, ctypes.c_char_p, i32], i32),
         "pss_create_batch": ([P(vp), i32, i32, i32, i32, i32, d, d, d, d, P(u64), i32], i32),
@@ -266,7 +267,8 @@ class System:
 
     def set_tuning(self, key: str, value: int):
         """Launch-shape knob ("pdl", "row_pairs", "col_tiles", "mid_planes", "graph_steps", "col_radix",
-        "row_radix", "mid_radix"); 0 = automatic."""
+        "row_radix", "mid_radix", "fast2d", "col2_warps", "row2_pairs", "row2_noise", "col2_radix",
+        "row2_radix"); 0 = automatic (for "fast2d": the generic kernels)."""
         self._ck(lib.pss_set_tuning(self._h, key.encode(), int(value)))
 
     def adjoint_forward(self, n: int):
@@ -289,6 +291,11 @@ class System:
     @property
     def launch_count(self) -> int:
         return int(lib.pss_launch_count(self._h))
+
+    @property
+    def step_path(self) -> str:
+        """'fast2d' (k2_col, k2_row: FP32 2D, sides 256..1024) or 'generic' (k_col, k_mid, k_row)."""
+        return "fast2d" if lib.pss_step_path(self._h) == 1 else "generic"
 
 
 def step_many(systems: Sequence[System], n: int):
