@@ -30,16 +30,42 @@ template <typename T> __device__ __forceinline__ cplx<T> cscale(cplx<T> a, T s) 
 // ---------------------------------------------------------------------------
 struct u32x4 { uint32_t x, y, z, w; };
 
+constexpr uint32_t kPhiloxMulA = 0xD2511F53u, kPhiloxMulB = 0xCD9E8D57u;
+constexpr uint32_t kPhiloxWeylA = 0x9E3779B9u, kPhiloxWeylB = 0xBB67AE85u;
+
 __device__ __forceinline__ u32x4 philox4x32_10(u32x4 c, uint32_t k0, uint32_t k1) {
-    constexpr uint32_t kMulA = 0xD2511F53u, kMulB = 0xCD9E8D57u;
-    constexpr uint32_t kWeylA = 0x9E3779B9u, kWeylB = 0xBB67AE85u;
 #pragma unroll
     for (int round = 0; round < 10; ++round) {
-        const uint32_t hiA = __umulhi(kMulA, c.x), loA = kMulA * c.x;
-        const uint32_t hiB = __umulhi(kMulB, c.z), loB = kMulB * c.z;
+        const uint32_t hiA = __umulhi(kPhiloxMulA, c.x), loA = kPhiloxMulA * c.x;
+        const uint32_t hiB = __umulhi(kPhiloxMulB, c.z), loB = kPhiloxMulB * c.z;
         c = u32x4{hiB ^ c.y ^ k0, loB, hiA ^ c.w ^ k1, loA};
-        k0 += kWeylA;
-        k1 += kWeylB;
+        k0 += kPhiloxWeylA;
+        k1 += kPhiloxWeylB;
+    }
+    return c;
+}
+
+// The ten round keys of one key (k + r W mod 2^32): a thread that draws many
+// numbers under one key computes them once, and each round then costs two
+// wide multiplies and two three-input XORs.
+struct PhiloxKey { uint32_t k0[10], k1[10]; };
+
+__device__ __forceinline__ PhiloxKey philox_key(uint32_t k0, uint32_t k1) {
+    PhiloxKey K;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        K.k0[r] = k0 + (uint32_t)r * kPhiloxWeylA;
+        K.k1[r] = k1 + (uint32_t)r * kPhiloxWeylB;
+    }
+    return K;
+}
+
+__device__ __forceinline__ u32x4 philox4x32_10(u32x4 c, const PhiloxKey &K) {
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        const uint32_t hiA = __umulhi(kPhiloxMulA, c.x), loA = kPhiloxMulA * c.x;
+        const uint32_t hiB = __umulhi(kPhiloxMulB, c.z), loB = kPhiloxMulB * c.z;
+        c = u32x4{hiB ^ c.y ^ K.k0[round], loB, hiA ^ c.w ^ K.k1[round], loA};
     }
     return c;
 }

@@ -362,6 +362,7 @@ template <int N, int E> struct Row2Smem {
 __device__ __forceinline__ void noise_range(const SysP<float> &sp, const FieldP<float> &fp, uint32_t step,
                                             float2 *__restrict__ out, int q0, int q1, int stride) {
     const int logny = __ffs(sp.ny) - 1;
+    const PhiloxKey key = philox_key(fp.seed_lo, fp.seed_hi);
 #pragma unroll 1
     for (int qa = q0; qa < q1; qa += 2 * stride) {
         float2 xa[2], xb[2];
@@ -377,7 +378,7 @@ __device__ __forceinline__ void noise_range(const SysP<float> &sp, const FieldP<
                 const float q2a = qx0 * qx0 + qy * qy, q2b = qx1 * qx1 + qy * qy;
                 noise_pair<float>(kx0 == 0 || 2 * kx0 == sp.nx, kx0, pos, 0, noise_amp<float>(1.f, fp.noise_pow, q2a),
                                   noise_amp<float>(1.f, fp.noise_pow, q2b), kx0 + 1 < sp.hx, sp, (uint32_t)fp.field_id,
-                                  fp.seed_lo, fp.seed_hi, step, xa[u], xb[u]);
+                                  key, step, xa[u], xb[u]);
             }
         }
 #pragma unroll

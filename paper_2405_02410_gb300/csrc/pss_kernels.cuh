@@ -50,7 +50,7 @@ __device__ __forceinline__ int signed_k(int k, int n) { return k < (n + 1) / 2 ?
 // on_plane: kx0 is 0 or Nx/2 (its partner is (kx0, -ky, -kz)).
 template <typename T>
 __device__ __forceinline__ void noise_pair(bool on_plane, int kx0, int ky, int kz, T amp0, T amp1, bool has1,
-                                           const SysP<T> &sp, uint32_t fid, uint32_t seed_lo, uint32_t seed_hi,
+                                           const SysP<T> &sp, uint32_t fid, const PhiloxKey &key,
                                            uint32_t step, cplx<T> &xi0, cplx<T> &xi1) {
     const uint32_t row = (uint32_t)(kz * sp.ny + ky);
     uint32_t crow = row;
@@ -60,14 +60,14 @@ __device__ __forceinline__ void noise_pair(bool on_plane, int kx0, int ky, int k
         selfc = prow == row;
         if (prow < row) { crow = prow; cj = true; }
     }
-    u32x4 r = philox4x32_10(u32x4{(crow * (uint32_t)sp.hxe + (uint32_t)kx0) >> 1, step, fid, 0u}, seed_lo, seed_hi);
+    u32x4 r = philox4x32_10(u32x4{(crow * (uint32_t)sp.hxe + (uint32_t)kx0) >> 1, step, fid, 0u}, key);
     T n1, n2;
     box_muller(uniform24<T>(r.x), uniform24<T>(r.y), n1, n2);
     xi0 = selfc ? mk<T>(T(1.4142135623730951) * amp0 * n1, T(0)) : mk<T>(amp0 * n1, cj ? -amp0 * n2 : amp0 * n2);
     if (has1) {
         // kx1 is odd, so it is never 0 or Nx/2: it is its own canonical member
         if (crow != row)
-            r = philox4x32_10(u32x4{(row * (uint32_t)sp.hxe + (uint32_t)kx0) >> 1, step, fid, 0u}, seed_lo, seed_hi);
+            r = philox4x32_10(u32x4{(row * (uint32_t)sp.hxe + (uint32_t)kx0) >> 1, step, fid, 0u}, key);
         box_muller(uniform24<T>(r.z), uniform24<T>(r.w), n1, n2);
         xi1 = mk<T>(amp1 * n1, amp1 * n2);
     }
@@ -161,6 +161,7 @@ __device__ __forceinline__ void col_adjoint(const ColArgs<T> &a, const FieldP<T>
 #pragma unroll
     for (int i = 0; i < 11; ++i) acc[i] = 0.0;
     const uint32_t step = (uint32_t)(a.adj_step + (a.d_adj_base ? *a.d_adj_base : 0));
+    const PhiloxKey key = philox_key(fp.seed_lo, fp.seed_hi);
 #pragma unroll 1
     for (int i = t; i < N * F; i += nthr) {
         const int pos = i >> (__ffs(F) - 1), ff = i & (F - 1);
@@ -202,7 +203,7 @@ __device__ __forceinline__ void col_adjoint(const ColArgs<T> &a, const FieldP<T>
                     C xi0 = mk<T>(0, 0), xi1 = mk<T>(0, 0);
                     noise_pair<T>(kx0 == 0 || 2 * kx0 == sp.nx, kx0, ky, kz, noise_amp<T>(fp.sigma0, fp.noise_pow, q2e),
                                   noise_amp<T>(fp.sigma0, fp.noise_pow, q2o), kx0 + 1 < sp.hx, sp,
-                                  (uint32_t)fp.field_id, fp.seed_lo, fp.seed_hi, step, xi0, xi1);
+                                  (uint32_t)fp.field_id, key, step, xi0, xi1);
                     const C xi = (kx & 1) ? xi1 : xi0;
                     acc[10] += wgt * ((double)mu.x * xi.x + (double)mu.y * xi.y);
                 }
@@ -397,7 +398,7 @@ __global__ void __launch_bounds__(512, N >= 512 ? 1 : 2) k_col(const ColArgs<T> 
         const bool has_product = fp.power > 0, noisy = fp.noisy != 0;
         const int noise_pow = fp.noise_pow, fid = fp.field_id;
         const T sigma0 = fp.sigma0;
-        const uint32_t seed_lo = fp.seed_lo, seed_hi = fp.seed_hi;
+        const PhiloxKey key = philox_key(fp.seed_lo, fp.seed_hi);
         if (tile < a.n_tiles) {
 #pragma unroll 1
             for (int pos = t >> (1 + lognch); pos < N; pos += pos_step) {
@@ -414,7 +415,7 @@ __global__ void __launch_bounds__(512, N >= 512 ? 1 : 2) k_col(const ColArgs<T> 
                     C xi0 = mk<T>(0, 0), xi1 = mk<T>(0, 0);
                     if (noisy)
                         noise_pair<T>(on_plane, kx0, ky, kz, noise_amp<T>(sigma0, noise_pow, q2a),
-                                      noise_amp<T>(sigma0, noise_pow, q2b), has1, sp, (uint32_t)fid, seed_lo, seed_hi,
+                                      noise_amp<T>(sigma0, noise_pow, q2b), has1, sp, (uint32_t)fid, key,
                                       step, xi0, xi1);
                     v0 = update_mode<T>(f0, v0, xi0, q2a, dtO, dtM, has_product);
                     v1 = update_mode<T>(f1, v1, xi1, q2b, dtO, dtM, has_product);
