@@ -182,6 +182,9 @@ int pss_time_kernels(pss_system *s, int64_t n, double *avg_ms);
  *   "row2_pairs"  row pairs per row CTA of that path (power of two <= 8);
  *   "row2_noise"  warps per row CTA of that path that draw the next step's
  *                 noise (1..24);
+ *   "fast3d"      FP32 3D systems whose x side is 256, 512 or 1024 points
+ *                 run their x pass on FFT groups (1, default) or on the
+ *                 generic row kernel (0);
  *   "col2_radix", "row2_radix"
  *                 radix of that path's FFT passes (8 or 16);
  * 0 restores the automatic choice.  Unknown keys return PSS_EINVAL. */
@@ -248,8 +251,10 @@ int64_t pss_launch_count(const pss_system *s);
 /* Which kernels a step of this system runs (for measurement and profiling):
  * 1 = the FP32 2D kernels with one FFT group per transform (k2_col, k2_row:
  * FP32 2D systems with sides of 256, 512 or 1024 points, unless the tuning
- * key "fast2d" is 0), 0 = the generic kernels (k_col, k_mid, k_row).
- * Returns PSS_EINVAL for a NULL handle. */
+ * key "fast2d" is 0); 2 = the generic 3D kernels with the x pass on FFT
+ * groups (k_col, k_mid, k2_row: FP32 3D systems whose x side is 256, 512 or
+ * 1024 points, unless "fast3d" is 0); 0 = the generic kernels (k_col,
+ * k_mid, k_row).  Returns PSS_EINVAL for a NULL handle. */
 int pss_step_path(const pss_system *s);
 
 #ifdef __cplusplus

@@ -90,6 +90,7 @@ struct pss_system {
     int tune_col2_warps = 0, tune_row2_pairs = 0;   // its noise warps per column CTA, row pairs per row CTA
     int tune_col2_radix = 0, tune_row2_radix = 0;   // its FFT pass radix (8 or 16; 0 = automatic)
     int tune_row2_noise = 0;                 // noise warps per row CTA of that path (0 = automatic)
+    int tune_fast3d = 1;                     // FP32 3D x pass with one FFT group per row pair (0 = generic k_row)
     int64_t launches = 0;
     std::string err;
     // adjoint: checkpoints of the last pss_adjoint_forward run
@@ -301,6 +302,12 @@ int row2_pairs(const pss_system *s) {
     return p;
 }
 
+// The FP32 3D step runs its x pass (rows of 256, 512 or 1024 points) with
+// the FFT groups of the fast path, on the tiled arrays of the generic kernels.
+bool fast3d_rows(const pss_system *s) {
+    return s->tune_fast3d && s->prec == PSS_F32 && s->dim == 3 && (s->nx == 256 || s->nx == 512 || s->nx == 1024);
+}
+
 int max_kept_tiles(const pss_system *s) {
     int m = 0;
     for (int i = 0; i < (int)s->fields.size(); ++i) m = std::max(m, (kept_cols(s, i) + kTileW - 1) / kTileW);
@@ -489,7 +496,7 @@ template <typename T> struct Seq {
             a.noise = any_noisy(s) ? (float2 *)s->XI : nullptr;
             a.noise_warps = a.noise ? row2_noise_warps(s, a.G) : 0;
             if (timer) timer->begin(2, st);
-            cudaError_t e = launch_row2(a, nslots, st);
+            cudaError_t e = launch_row2(a, nslots, st, false);
             if (timer) timer->begin(2, st);
             s->launches++;
             if (e != cudaSuccess) return cuda_fail(s, e, "k2_row launch");
@@ -499,6 +506,40 @@ template <typename T> struct Seq {
             return fail(s, PSS_EUNSUPPORTED, "the one-warp 2D path is FP32 only");
         }
     }
+
+    // the 3D x pass with FFT groups (FP32): B -> A, tiled arrays
+    int row3() {
+        if constexpr (std::is_same<T, float>::value) {
+            RowArgs<float> a{};
+            a.sp = sys_params<float>(s);
+            a.fps = (const FieldP<float> *)s->fps;
+            a.in = B();
+            a.out = A();
+            a.slot_stride = s->field_elems;
+            a.slot0 = slot0;
+            a.tw = (const float2 *)s->tw;
+            a.d_step = s->d_step;
+            a.d_status = s->d_status;
+            a.mode = ROW_FUSED;
+            a.E = row2_radix(s);
+            a.G = std::min(8, 256 / (s->nx / a.E));   // row pairs per CTA: 256 threads
+            a.kx_cols_max = 0;
+            for (int i = 0; i < (int)s->fields.size(); ++i) a.kx_cols_max = std::max(a.kx_cols_max, kept_cols(s, i));
+            a.inc_step = 0;
+            a.noise = nullptr;
+            a.noise_warps = 0;
+            if (timer) timer->begin(2, st);
+            cudaError_t e = launch_row2(a, nslots, st, true);
+            if (timer) timer->begin(2, st);
+            s->launches++;
+            if (e != cudaSuccess) return cuda_fail(s, e, "k2_row (3D x pass) launch");
+            return PSS_OK;
+        } else {
+            return fail(s, PSS_EUNSUPPORTED, "the FFT-group x pass is FP32 only");
+        }
+    }
+
+    int x_pass_3d() { return fast3d_rows(s) ? row3() : row(ROW_FUSED, false, false, false, nullptr, 0); }  // B -> A
 
     // B <- x-transformed product of the current state (start of a run)
     int prologue() {
@@ -510,7 +551,7 @@ template <typename T> struct Seq {
         if ((rc = col(COL_INV_MASK, false, true))) return rc;                      // state -> A
         if (s->dim == 3) {
             if ((rc = mid(MID_INV_MASK, true, false))) return rc;                  // A -> B
-            if ((rc = row(ROW_FUSED, false, false, false, nullptr, 0))) return rc;  // B -> A
+            if ((rc = x_pass_3d())) return rc;                                     // B -> A
             return mid(MID_FWD, true, false);                                      // A -> B
         }
         return row(ROW_FUSED, true, true, false, nullptr, 0);                       // A -> B
@@ -525,7 +566,7 @@ template <typename T> struct Seq {
         if ((rc = col(COL_STEP, true, true))) return rc;                           // B, state -> state, A
         if (s->dim == 3) {
             if ((rc = mid(MID_INV_MASK, true, false))) return rc;                  // A -> B
-            if ((rc = row(ROW_FUSED, false, false, false, nullptr, 0))) return rc;  // B -> A
+            if ((rc = x_pass_3d())) return rc;                                     // B -> A
             return mid(MID_FWD, true, true);                                       // A -> B, step++
         }
         return row(ROW_FUSED, true, true, true, nullptr, 0);                        // A -> B, step++
@@ -1293,6 +1334,7 @@ int pss_set_tuning(pss_system *s, const char *key, int value) {
     else if (k == "mid_planes") s->tune_mid_planes = value;
     else if (k == "graph_steps") s->tune_graph_steps = value;
     else if (k == "fast2d") s->tune_fast2d = value ? 1 : 0;
+    else if (k == "fast3d") s->tune_fast3d = value ? 1 : 0;
     else if (k == "col2_warps") {
         if (value > 24) return fail(s, PSS_EINVAL, "col2_warps is at most 24 (0 = automatic)");
         s->tune_col2_warps = value;
@@ -1492,6 +1534,6 @@ const char *pss_last_error(const pss_system *s) { return s ? s->err.c_str() : g_
 
 int64_t pss_launch_count(const pss_system *s) { return s ? s->launches : 0; }
 
-int pss_step_path(const pss_system *s) { return s ? (fast2d(s) ? 1 : 0) : PSS_EINVAL; }
+int pss_step_path(const pss_system *s) { return s ? (fast2d(s) ? 1 : fast3d_rows(s) ? 2 : 0) : PSS_EINVAL; }
 
 }  // extern "C"

@@ -350,6 +350,11 @@ __global__ void __launch_bounds__(E == 8 ? 1024 : 768, 1) k2_col(const ColArgs<f
 // rows r0 + 2j, r0 + 2j + 1, then the noise warps.  The transform threads
 // meet at barrier 15.  Shared memory: mbarrier | roots of unity (N) | per
 // group two buffers of BUF points, WS apart.
+//
+// TILED = false: the 2D step's column-major work arrays, the input holding
+// the conjugated y-inverse.  TILED = true: the tiled arrays of the generic
+// kernels ([tile][row][4], input as it is), as the x pass of the 3D step; the
+// CTA's rows of one tile are a 64 NW-byte run, moved as 16-byte pieces.
 // ---------------------------------------------------------------------------
 template <int N, int E> struct Row2Smem {
     static size_t bytes(int nw) { return 128 + sizeof(float2) * ((size_t)N + (size_t)nw * GShape<N, E>::WS); }
@@ -389,7 +394,7 @@ __device__ __forceinline__ void noise_range(const SysP<float> &sp, const FieldP<
     }
 }
 
-template <int N, int E>
+template <int N, int E, bool TILED>
 __global__ void __launch_bounds__(1024) k2_row(const RowArgs<float> a) {
     using C = float2;
     using S = GShape<N, E>;
@@ -405,7 +410,8 @@ __global__ void __launch_bounds__(1024) k2_row(const RowArgs<float> a) {
     const int g = t / TPF, gl = t - g * TPF;
     const int slot = a.slot0 + blockIdx.y;
     const int rows = sp.rows;
-    const size_t sofs = (size_t)slot * a.slot_stride + (size_t)blockIdx.x * 2 * NW;   // first row of the CTA
+    const int r0 = blockIdx.x * 2 * NW;                                                  // first row of the CTA
+    const size_t sofs = (size_t)slot * a.slot_stride + (size_t)r0 * (TILED ? 4 : 1);
     constexpr int H = N / 2 + 1;
     pdl_wait();
     pdl_trigger();
@@ -427,11 +433,23 @@ __global__ void __launch_bounds__(1024) k2_row(const RowArgs<float> a) {
         bulk_g2s(TW, a.tw + twiddle_offset(N, E), (uint32_t)(N * sizeof(C)), bar);
     }
     // ---- stage Y = conj(Z), Z_k = A_k + i B_k (k <= N/2), conj(A_{N-k}) +
-    // i conj(B_{N-k}) above, into the second buffer of group j.  T1 holds
-    // conj(A), conj(B): (ar, ai, br, bi) of rows r0 + 2j, r0 + 2j + 1 of column k.
-    // All of a thread's loads are issued before the first use.
+    // i conj(B_{N-k}) above, into the second buffer of group j.  With
+    // (ar, ai, br, bi) the values of rows r0 + 2j, r0 + 2j + 1 at column k:
+    // Y_k = (ar - bi, -ai - br), Y_{N-k} = (ar + bi, ai - br) for the values
+    // as they are (TILED), and the two swapped when the input holds their
+    // conjugates (the 2D path).  All of a thread's loads are issued before the
+    // first use.
     const int kcm = a.kx_cols_max;
-    {
+    const int kc = a.fps[slot].kx_cols;
+    auto stage = [&](int k, int j, float ar, float ai, float br, float bi) {
+        C *Y = WBUF + j * S::WS + S::BUF;
+        if (k >= kc) { ar = 0.f; ai = 0.f; br = 0.f; bi = 0.f; }
+        if (k == 0 || k == N / 2) { ai = 0.f; bi = 0.f; }   // the half spectra of real rows
+        const C lo = mk<float>(ar - bi, -ai - br), hi = mk<float>(ar + bi, ai - br);
+        Y[k] = TILED ? lo : hi;
+        if (k > 0 && k < N / 2) Y[N - k] = TILED ? hi : lo;
+    };
+    if constexpr (!TILED) {
         const C *__restrict__ in = a.in + sofs;
         const int total = H << logNW;
 #pragma unroll 1
@@ -445,20 +463,47 @@ __global__ void __launch_bounds__(1024) k2_row(const RowArgs<float> a) {
                 if (idx < total && k < kcm)
                     v[u] = __ldcg(reinterpret_cast<const float4 *>(in + (size_t)k * rows + 2 * (idx & (NW - 1))));
             }
-            const int kc = a.fps[slot].kx_cols;
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
                 const int idx = base + u * nf + t;
                 if (idx >= total) break;
-                const int k = idx >> logNW;
-                C *Y = WBUF + (idx & (NW - 1)) * S::WS + S::BUF;
-                float ar = v[u].x, ai = v[u].y, br = v[u].z, bi = v[u].w;
-                if (k >= kc) { ar = 0.f; ai = 0.f; br = 0.f; bi = 0.f; }
-                if (k == 0 || k == N / 2) { ai = 0.f; bi = 0.f; }   // the half spectra of real rows
-                Y[k] = mk<float>(ar + bi, ai - br);
-                if (k > 0 && k < N / 2) Y[N - k] = mk<float>(ar - bi, -ai - br);
+                stage(idx >> logNW, idx & (NW - 1), v[u].x, v[u].y, v[u].z, v[u].w);
             }
         }
+    } else {
+        // item (tile, pair j): the 64 bytes of rows r0 + 2j, r0 + 2j + 1 of the tile
+        const float4 *__restrict__ in = reinterpret_cast<const float4 *>(a.in + sofs);
+        const int ntl = (kcm + 3) >> 2;
+        const int total = ntl << logNW;
+#pragma unroll 1
+        for (int base = 0; base < total; base += 2 * nf) {
+            float4 v[2][4];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int idx = base + u * nf + t;
+                const float4 *p = in + ((size_t)(idx >> logNW) * rows + 2 * (idx & (NW - 1))) * 2;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) v[u][q] = idx < total ? __ldcg(p + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int idx = base + u * nf + t;
+                if (idx >= total) break;
+                const int k0 = (idx >> logNW) << 2, j = idx & (NW - 1);
+                // row a: (c0, c1) (c2, c3) in v[0], v[1]; row b in v[2], v[3]
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const float4 va = v[u][c >> 1], vb = v[u][2 + (c >> 1)];
+                    if (k0 + c <= N / 2)
+                        stage(k0 + c, j, (c & 1) ? va.z : va.x, (c & 1) ? va.w : va.y, (c & 1) ? vb.z : vb.x,
+                              (c & 1) ? vb.w : vb.y);
+                }
+            }
+        }
+        // the columns past the staged tiles are zero
+        const int kz = ntl << 2, nz = H - kz;
+        for (int idx = t; idx < (nz > 0 ? nz << logNW : 0); idx += nf)
+            stage(kz + (idx >> logNW), idx & (NW - 1), 0.f, 0.f, 0.f, 0.f);
     }
     const int power = a.fps[slot].power;
     asm volatile("bar.sync 15, %0;" ::"r"(nf) : "memory");   // the mbarrier is initialised; Y is staged
@@ -484,18 +529,37 @@ __global__ void __launch_bounds__(1024) k2_row(const RowArgs<float> a) {
     }
     asm volatile("bar.sync 15, %0;" ::"r"(nf) : "memory");
     // ---- split into the half spectra of the two rows:
-    // A_k = (W_k + conj W_{N-k}) / 2, B_k = (W_k - conj W_{N-k}) / 2i;
-    // (k, pair j) stored as 16 bytes
-    C *__restrict__ out = a.out + sofs;
-    const int total = H << logNW;
-#pragma unroll 1
-    for (int idx = t; idx < total; idx += nf) {
-        const int k = idx >> logNW, j = idx & (NW - 1);
+    // A_k = (W_k + conj W_{N-k}) / 2, B_k = (W_k - conj W_{N-k}) / 2i
+    auto split = [&](int k, int j) {
         const C *Wj = WBUF + j * S::WS + S::BUF;
         const C wk = Wj[k], wm = Wj[(N - k) & (N - 1)];
-        const float4 r = make_float4(0.5f * (wk.x + wm.x), 0.5f * (wk.y - wm.y), 0.5f * (wk.y + wm.y),
-                                     -0.5f * (wk.x - wm.x));
-        *reinterpret_cast<float4 *>(out + (size_t)k * rows + 2 * j) = r;
+        return make_float4(0.5f * (wk.x + wm.x), 0.5f * (wk.y - wm.y), 0.5f * (wk.y + wm.y), -0.5f * (wk.x - wm.x));
+    };
+    if constexpr (!TILED) {
+        // (k, pair j) stored as 16 bytes
+        C *__restrict__ out = a.out + sofs;
+        const int total = H << logNW;
+#pragma unroll 1
+        for (int idx = t; idx < total; idx += nf) {
+            const int k = idx >> logNW, j = idx & (NW - 1);
+            *reinterpret_cast<float4 *>(out + (size_t)k * rows + 2 * j) = split(k, j);
+        }
+    } else {
+        // (tile, pair j) stored as the 64 bytes of its two rows (zero past Nx/2)
+        float4 *__restrict__ out = reinterpret_cast<float4 *>(a.out + sofs);
+        const int total = sp.ntiles << logNW;
+#pragma unroll 1
+        for (int idx = t; idx < total; idx += nf) {
+            const int k0 = (idx >> logNW) << 2, j = idx & (NW - 1);
+            float4 ab[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) ab[c] = k0 + c <= N / 2 ? split(k0 + c, j) : make_float4(0.f, 0.f, 0.f, 0.f);
+            float4 *p = out + ((size_t)(idx >> logNW) * rows + 2 * j) * 2;
+            p[0] = make_float4(ab[0].x, ab[0].y, ab[1].x, ab[1].y);   // row a
+            p[1] = make_float4(ab[2].x, ab[2].y, ab[3].x, ab[3].y);
+            p[2] = make_float4(ab[0].z, ab[0].w, ab[1].z, ab[1].w);   // row b
+            p[3] = make_float4(ab[2].z, ab[2].w, ab[3].z, ab[3].w);
+        }
     }
 }
 
@@ -510,14 +574,16 @@ template <int N, int E> cudaError_t launch_col2_ne(const ColArgs<float> &a, int 
     return launch_pdl(k2_col<N, E>, dim3(ntiles, nslots), threads, Col2Smem<N, E>::BYTES, st, a);
 }
 
-template <int N, int E> cudaError_t launch_row2_ne(const RowArgs<float> &a, int nslots, cudaStream_t st) {
+template <int N, int E, bool TILED>
+cudaError_t launch_row2_ne(const RowArgs<float> &a, int nslots, cudaStream_t st) {
     const int nw = a.G, threads = nw * GShape<N, E>::TPF + 32 * a.noise_warps;
-    if (nw < 1 || nw > 8 || (nw & (nw - 1)) || a.sp.rows % (2 * nw) || a.noise_warps < 0 || threads > 1024)
+    if (nw < 1 || nw > 8 || (nw & (nw - 1)) || a.sp.rows % (2 * nw) || a.noise_warps < 0 || threads > 1024 ||
+        (TILED && a.noise))
         return cudaErrorInvalidConfiguration;
     const size_t smem = Row2Smem<N, E>::bytes(nw);
-    cudaError_t e = ensure_smem(k2_row<N, E>, smem);
+    cudaError_t e = ensure_smem(k2_row<N, E, TILED>, smem);
     if (e != cudaSuccess) return e;
-    return launch_pdl(k2_row<N, E>, dim3(a.sp.rows / (2 * nw), nslots), threads, smem, st, a);
+    return launch_pdl(k2_row<N, E, TILED>, dim3(a.sp.rows / (2 * nw), nslots), threads, smem, st, a);
 }
 
 }  // namespace pss

@@ -158,11 +158,13 @@ template <typename T> inline cudaError_t launch_row(const RowArgs<T> &a, int nsl
 template <typename T> inline cudaError_t launch_mid(const MidArgs<T> &a, int nslots, int n_tiles, cudaStream_t st) {
     return a.E == 16 ? launch_mid_e<T, 16>(a, nslots, n_tiles, st) : launch_mid_e<T, 8>(a, nslots, n_tiles, st);
 }
-// The FP32 2D step with one warp per transform (sides 256, 512 or 1024):
-// k2_col over `ntiles` tiles of every slot, k2_row over all row pairs.  The
-// work arrays they exchange are column-major ([kx][y] per slot).
+// The FP32 path with one FFT group per transform (sides 256, 512 or 1024):
+// k2_col over `ntiles` tiles of every slot, k2_row over all row pairs.  In
+// the 2D step the work arrays they exchange are column-major ([kx][y] per
+// slot); with tiled = true k2_row reads and writes the tiled arrays of the
+// generic kernels (the x pass of the 3D step).
 cudaError_t launch_col2(const ColArgs<float> &a, int nslots, int ntiles, cudaStream_t st);
-cudaError_t launch_row2(const RowArgs<float> &a, int nslots, cudaStream_t st);
+cudaError_t launch_row2(const RowArgs<float> &a, int nslots, cudaStream_t st, bool tiled);
 template <typename T> cudaError_t launch_init_uniform(T *real, long long nsites, double lo, double hi,
                                                       uint64_t seed, int field_id, cudaStream_t st);
 template <typename T> cudaError_t launch_tiles_to_half(const SysP<T> &sp, const cplx<T> *tiles,

@@ -14,14 +14,16 @@ cudaError_t launch_col2(const ColArgs<float> &a, int nslots, int ntiles, cudaStr
     }
 }
 
-cudaError_t launch_row2(const RowArgs<float> &a, int nslots, cudaStream_t st) {
+cudaError_t launch_row2(const RowArgs<float> &a, int nslots, cudaStream_t st, bool tiled) {
     const bool r16 = a.E == 16;
+#define PSS_ROW2(N, E) (tiled ? launch_row2_ne<N, E, true>(a, nslots, st) : launch_row2_ne<N, E, false>(a, nslots, st))
     switch (a.sp.nx) {
-        case 256: return launch_row2_ne<256, 8>(a, nslots, st);
-        case 512: return r16 ? launch_row2_ne<512, 16>(a, nslots, st) : launch_row2_ne<512, 8>(a, nslots, st);
-        case 1024: return r16 ? launch_row2_ne<1024, 16>(a, nslots, st) : launch_row2_ne<1024, 8>(a, nslots, st);
+        case 256: return PSS_ROW2(256, 8);
+        case 512: return r16 ? PSS_ROW2(512, 16) : PSS_ROW2(512, 8);
+        case 1024: return r16 ? PSS_ROW2(1024, 16) : PSS_ROW2(1024, 8);
         default: return cudaErrorInvalidValue;
     }
+#undef PSS_ROW2
 }
 
 }  // namespace pss

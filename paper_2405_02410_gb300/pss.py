@@ -267,8 +267,8 @@ class System:
 
     def set_tuning(self, key: str, value: int):
         """Launch-shape knob ("pdl", "row_pairs", "col_tiles", "mid_planes", "graph_steps", "col_radix",
-        "row_radix", "mid_radix", "fast2d", "col2_warps", "row2_pairs", "row2_noise", "col2_radix",
-        "row2_radix"); 0 = automatic (for "fast2d": the generic kernels)."""
+        "row_radix", "mid_radix", "fast2d", "fast3d", "col2_warps", "row2_pairs", "row2_noise", "col2_radix",
+        "row2_radix"); 0 = automatic (for "fast2d" / "fast3d": the generic kernels)."""
         self._ck(lib.pss_set_tuning(self._h, key.encode(), int(value)))
 
     def adjoint_forward(self, n: int):
@@ -294,8 +294,9 @@ class System:
 
     @property
     def step_path(self) -> str:
-        """'fast2d' (k2_col, k2_row: FP32 2D, sides 256..1024) or 'generic' (k_col, k_mid, k_row)."""
-        return "fast2d" if lib.pss_step_path(self._h) == 1 else "generic"
+        """'fast2d' (k2_col, k2_row: FP32 2D, sides 256..1024), 'fast3d_rows' (k_col, k_mid and the
+        FFT-group x pass k2_row: FP32 3D, x side 256..1024) or 'generic' (k_col, k_mid, k_row)."""
+        return {1: "fast2d", 2: "fast3d_rows"}.get(lib.pss_step_path(self._h), "generic")
 
 
 def step_many(systems: Sequence[System], n: int):

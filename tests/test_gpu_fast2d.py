@@ -156,3 +156,42 @@ def test_nonfinite_is_reported_on_the_fast_path():
     with pytest.raises(P.PssError) as ei:
         s.sync()
     assert ei.value.code == P.PSS_ENONFINITE
+
+
+# ---------------------------------------------------------------------------
+# the 3D x pass on FFT groups (tiled arrays, tuning key "fast3d")
+# ---------------------------------------------------------------------------
+def _pair_3d(shape, fast, order=2, seed=8):
+    P = pss()
+    s = P.System(shape, dt=0.005, seed=seed, precision="f32")
+    P.add_model_a_field(s, a=-1, b=1, K=1, D=0.05, name="psi", dealias_order=order)
+    P.add_model_b_field(s, a=-1, b=1, K=1, D=0.05, name="phi", dealias_order=order)
+    s.set_tuning("fast3d", 1 if fast else 0)
+    s.init_uniform(0, -0.05, 0.05)
+    s.init_uniform(1, -0.05, 0.05)
+    return s
+
+
+@pytest.mark.parametrize("shape,order", [((8, 16, 256), 2), ((4, 8, 256), 0), ((4, 4, 512), 3)])
+def test_3d_x_pass_matches_oracle(shape, order):
+    steps = 16
+    s = _pair_3d(shape, True, order)
+    assert s.step_path == "fast3d_rows"
+    s.step(steps)
+    ma = O.model_a(shape, dt=0.005, a=-1, b=1, K=1, D=0.05, seed=8, field_id=0, dealias_order=order)
+    mb = O.model_b(shape, dt=0.005, a=-1, b=1, K=1, D=0.05, seed=8, field_id=1, dealias_order=order)
+    for fid, m in ((0, ma), (1, mb)):
+        ref = O.half(O.run(m, O.to_spectrum(m, O.init_uniform(m, -0.05, 0.05)), 0, steps))
+        err = rel(s.get_spectrum(fid), ref)
+        assert err < 1e-4, (fid, err)
+
+
+@pytest.mark.parametrize("shape", [(16, 32, 512), (32, 32, 1024), (64, 64, 256)])
+def test_3d_x_pass_matches_generic_kernels(shape):
+    fast, gen = _pair_3d(shape, True), _pair_3d(shape, False)
+    assert gen.step_path == "generic"
+    for s in (fast, gen):
+        s.step(30)
+    for fid in (0, 1):
+        err = rel(fast.get_spectrum(fid), gen.get_spectrum(fid))
+        assert err < 1e-5, (fid, err)
