@@ -272,12 +272,20 @@ bool fast2d(const pss_system *s) {
     auto side = [](int n) { return n == 256 || n == 512 || n == 1024; };
     return s->tune_fast2d && s->prec == PSS_F32 && s->dim == 2 && side(s->nx) && side(s->ny);
 }
-// Launch shape of the fast path.  Measured on GB300 at 1024 x 1024: radix-16
-// passes (two warps per 1024-point transform, three passes) in both kernels,
-// 16 noise warps per column CTA and 4 row pairs per row CTA; sides of 256
-// always take radix 8 (one warp per transform).
-int col2_radix(const pss_system *s) { return s->ny >= 512 && s->tune_col2_radix != 8 ? 16 : 8; }
-int row2_radix(const pss_system *s) { return s->nx >= 512 && s->tune_row2_radix != 8 ? 16 : 8; }
+// Launch shape of the fast path, measured on GB300.  2D: radix-16 passes for
+// sides of 512 and 1024 (two warps per 1024-point transform, three passes),
+// radix 8 for 256 (one warp per transform: the 256^2 step is latency-bound,
+// 7.9 us against 9.7 us with radix 16), 4 row pairs per row CTA.  The 3D x
+// pass takes radix 16 at every side: at 256 points that is half a warp per
+// transform and two passes instead of three, and there the passes are bound
+// by shared-memory bandwidth (x pass of the 256^3 pair 130 -> 113 us).
+int col2_radix(const pss_system *s) {
+    return s->tune_col2_radix ? s->tune_col2_radix : (s->ny >= 512 ? 16 : 8);
+}
+int row2_radix(const pss_system *s) {
+    if (s->tune_row2_radix) return s->tune_row2_radix;
+    return (s->dim == 3 || s->nx >= 512) ? 16 : 8;
+}
 int col2_warps(const pss_system *s) {
     const int fft_warps = 4 * s->ny / col2_radix(s) / 32;
     const int want = s->tune_col2_warps > 0 ? s->tune_col2_warps : 8;
@@ -298,6 +306,7 @@ int row2_pairs(const pss_system *s) {
     const int tpf = s->nx / row2_radix(s);
     const int nw = s->tune_row2_pairs > 0 ? s->tune_row2_pairs : 4;
     int p = 1;
+    while (p * tpf < 32) p *= 2;   // whole warps of transform threads
     while (p * 2 <= nw && p * 2 <= 8 && p * 2 * tpf <= 512) p *= 2;
     return p;
 }

@@ -41,17 +41,17 @@
 namespace pss {
 
 // A group FFT of length N with radix-E passes (E = 8 or 16) and a last pass
-// of radix RL, run by TPF = N / E threads (GW = TPF / 32 warps) that meet at
-// a named barrier (at __syncwarp when the group is one warp).  A group's two
-// buffers hold BUF = N + N/16 points (room for the padded intermediate
-// results) and sit WS apart (the extra 4 staggers neighbouring groups over
-// the banks).
+// of radix RL, run by TPF = N / E threads: whole warps that meet at a named
+// barrier, one warp (__syncwarp), or half a warp (N = 256, E = 16: two
+// groups per warp, each synchronising its own half).  A group's two buffers
+// hold BUF = N + N/16 points (room for the padded intermediate results) and
+// sit WS apart (the extra 4 staggers neighbouring groups over the banks).
 template <int N, int E_> struct GShape {
     static_assert(N == 256 || N == 512 || N == 1024, "group FFTs of 256, 512 or 1024 points");
     static_assert(E_ == 8 || E_ == 16, "radix-8 or radix-16 passes");
     static constexpr int E = E_;
-    static constexpr int TPF = N / E, GW = TPF / 32;
-    static_assert(TPF % 32 == 0 && TPF <= 128, "whole warps, at most four per transform");
+    static constexpr int TPF = N / E;
+    static_assert((TPF % 32 == 0 && TPF <= 128) || TPF == 16, "half a warp or up to four warps per transform");
     static constexpr int LOG = ilog2(N), LOGE = ilog2(E);
     static constexpr int LOGRL = LOG % LOGE == 0 ? LOGE : LOG % LOGE;
     static constexpr int RL = 1 << LOGRL;
@@ -65,7 +65,9 @@ template <int N, int E_> struct GShape {
 
 // the group's barrier: named barrier `id` (1..15) over its TPF threads
 template <int TPF> __device__ __forceinline__ void group_sync(int id) {
-    if constexpr (TPF <= 32) {
+    if constexpr (TPF == 16) {
+        __syncwarp(0xFFFFu << (threadIdx.x & 16));   // this half of the warp
+    } else if constexpr (TPF == 32) {
         __syncwarp();
     } else {
         asm volatile("bar.sync %0, %1;" ::"r"(id), "n"(TPF) : "memory");

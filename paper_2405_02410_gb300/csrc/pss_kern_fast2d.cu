@@ -2,11 +2,11 @@
 #include "pss_fast2d.cuh"
 namespace pss {
 
-// a.E: radix of the FFT passes, 8 or 16 (sides of 256 take 8)
+// a.E: radix of the FFT passes, 8 or 16
 cudaError_t launch_col2(const ColArgs<float> &a, int nslots, int ntiles, cudaStream_t st) {
     const bool r16 = a.E == 16;
     switch (a.sp.n_inner) {
-        case 256: return launch_col2_ne<256, 8>(a, nslots, ntiles, st);
+        case 256: return r16 ? launch_col2_ne<256, 16>(a, nslots, ntiles, st) : launch_col2_ne<256, 8>(a, nslots, ntiles, st);
         case 512: return r16 ? launch_col2_ne<512, 16>(a, nslots, ntiles, st) : launch_col2_ne<512, 8>(a, nslots, ntiles, st);
         case 1024:
             return r16 ? launch_col2_ne<1024, 16>(a, nslots, ntiles, st) : launch_col2_ne<1024, 8>(a, nslots, ntiles, st);
@@ -18,7 +18,7 @@ cudaError_t launch_row2(const RowArgs<float> &a, int nslots, cudaStream_t st, bo
     const bool r16 = a.E == 16;
 #define PSS_ROW2(N, E) (tiled ? launch_row2_ne<N, E, true>(a, nslots, st) : launch_row2_ne<N, E, false>(a, nslots, st))
     switch (a.sp.nx) {
-        case 256: return PSS_ROW2(256, 8);
+        case 256: return r16 ? PSS_ROW2(256, 16) : PSS_ROW2(256, 8);
         case 512: return r16 ? PSS_ROW2(512, 16) : PSS_ROW2(512, 8);
         case 1024: return r16 ? PSS_ROW2(1024, 16) : PSS_ROW2(1024, 8);
         default: return cudaErrorInvalidValue;
