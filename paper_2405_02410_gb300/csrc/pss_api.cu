@@ -280,21 +280,28 @@ bool fast2d(const pss_system *s) {
 // transform and two passes instead of three, and there the passes are bound
 // by shared-memory bandwidth (x pass of the 256^3 pair 130 -> 113 us).
 int col2_radix(const pss_system *s) {
-    return s->tune_col2_radix ? s->tune_col2_radix : (s->ny >= 512 ? 16 : 8);
+    const int r = s->tune_col2_radix ? s->tune_col2_radix : (s->ny >= 512 ? 16 : 8);
+    return r == 32 && s->ny != 1024 ? 16 : r;   // radix-32 passes serve 1024 points only
 }
 int row2_radix(const pss_system *s) {
-    if (s->tune_row2_radix) return s->tune_row2_radix;
-    return (s->dim == 3 || s->nx >= 512) ? 16 : 8;
+    const int r = s->tune_row2_radix ? s->tune_row2_radix : ((s->dim == 3 || s->nx >= 512) ? 16 : 8);
+    return r == 32 && s->nx != 1024 ? 16 : r;
 }
+// CTA size limits of the two kernels (their launch bounds leave radix-32
+// passes 128 registers per thread)
+int col2_max_threads(int E) { return E == 8 ? 1024 : E == 16 ? 768 : 512; }
+int row2_max_threads(int E) { return E == 32 ? 512 : 1024; }
 int col2_warps(const pss_system *s) {
-    const int fft_warps = 4 * s->ny / col2_radix(s) / 32;
+    const int E = col2_radix(s);
+    const int fft_warps = 4 * s->ny / E / 32;
     const int want = s->tune_col2_warps > 0 ? s->tune_col2_warps : 8;
-    return std::min(want, (col2_radix(s) == 8 ? 32 : 24) - fft_warps);
+    return std::max(1, std::min(want, col2_max_threads(E) / 32 - fft_warps));
 }
 int row2_noise_warps(const pss_system *s, int pairs) {
-    const int fft_warps = pairs * s->nx / row2_radix(s) / 32;
+    const int E = row2_radix(s);
+    const int fft_warps = pairs * s->nx / E / 32;
     const int want = s->tune_row2_noise > 0 ? s->tune_row2_noise : 16;
-    return std::max(1, std::min(want, 32 - fft_warps));
+    return std::max(1, std::min(want, row2_max_threads(E) / 32 - fft_warps));
 }
 bool any_noisy(const pss_system *s) {
     for (const Field &f : s->fields)
@@ -854,7 +861,7 @@ int do_create(pss_system **out, int batch, int dim, int nx, int ny, int nz, doub
     if (e == cudaSuccess) {
         const int total = kTwiddleEntries;
         std::vector<double2> h(total, make_double2(0.0, 0.0));
-        for (int emax : {8, 16})
+        for (int emax : {8, 16, 32})
             for (int n = 2; n <= kMaxFftN; n *= 2) {
                 const int E = fft_E(n, emax);
                 for (int P = E, R = std::min(E, n / P); P < n; P *= R, R = std::min(E, n / P))
@@ -1354,7 +1361,8 @@ int pss_set_tuning(pss_system *s, const char *key, int value) {
         s->tune_row2_noise = value;
     }
     else if (k == "col2_radix" || k == "row2_radix") {
-        if (value != 0 && value != 8 && value != 16) return fail(s, PSS_EINVAL, "radix 8 or 16 (0 = automatic)");
+        if (value != 0 && value != 8 && value != 16 && value != 32)
+            return fail(s, PSS_EINVAL, "radix 8, 16 or 32 (0 = automatic; 32 for sides of 1024 only)");
         (k == "col2_radix" ? s->tune_col2_radix : s->tune_row2_radix) = value;
     }
     else if (k == "col_radix" || k == "row_radix" || k == "mid_radix") {

@@ -40,15 +40,16 @@
 
 namespace pss {
 
-// A group FFT of length N with radix-E passes (E = 8 or 16) and a last pass
-// of radix RL, run by TPF = N / E threads: whole warps that meet at a named
-// barrier, one warp (__syncwarp), or half a warp (N = 256, E = 16: two
-// groups per warp, each synchronising its own half).  A group's two buffers
-// hold BUF = N + N/16 points (room for the padded intermediate results) and
-// sit WS apart (the extra 4 staggers neighbouring groups over the banks).
+// A group FFT of length N with radix-E passes (E = 8, 16, or 32 for N = 1024)
+// and a last pass of radix RL, run by TPF = N / E threads: whole warps that
+// meet at a named barrier, one warp (__syncwarp), or half a warp (N = 256,
+// E = 16: two groups per warp, each synchronising its own half).  A group's
+// two buffers hold BUF = N + N / 2^PS points (room for the padded
+// intermediate results) and sit WS apart (the extra 4 staggers neighbouring
+// groups over the banks).
 template <int N, int E_> struct GShape {
     static_assert(N == 256 || N == 512 || N == 1024, "group FFTs of 256, 512 or 1024 points");
-    static_assert(E_ == 8 || E_ == 16, "radix-8 or radix-16 passes");
+    static_assert(E_ == 8 || E_ == 16 || (E_ == 32 && N == 1024), "radix-8, -16 or (1024 points) -32 passes");
     static constexpr int E = E_;
     static constexpr int TPF = N / E;
     static_assert((TPF % 32 == 0 && TPF <= 128) || TPF == 16, "half a warp or up to four warps per transform");
@@ -56,7 +57,8 @@ template <int N, int E_> struct GShape {
     static constexpr int LOGRL = LOG % LOGE == 0 ? LOGE : LOG % LOGE;
     static constexpr int RL = 1 << LOGRL;
     static constexpr int NPASS = (LOG - LOGRL) / LOGE + 1;
-    static constexpr int BUF = N + N / 16;
+    static constexpr int PS = E == 32 ? 5 : 4;     // one pad slot per 2^PS points
+    static constexpr int BUF = N + (N >> PS);
     static constexpr int WS = 2 * BUF + 4;
     // the buffer that holds a transform's result: the first pass writes b0,
     // the passes alternate
@@ -89,12 +91,13 @@ __device__ __forceinline__ bool bar_and(int id, int nthreads, bool pred) {
     return r != 0;
 }
 
-// Intermediate pass results are padded: position p lives at p + p/16, which
-// keeps the stride-R stores of a pass and the strided loads of the next free
-// of bank conflicts, and which, with R and the pass strides known at compile
-// time, folds into constant address offsets.  Inputs and outputs of a
-// transform are in natural order.
-__device__ __forceinline__ int pad16(int p) { return p + (p >> 4); }
+// Intermediate pass results are padded: position p lives at p + p / 2^PS
+// (one slot per 16 points, per 32 for radix-32 passes), which keeps the
+// stride-R stores of a pass and the strided loads of the next free of bank
+// conflicts, and which, with R and the pass strides known at compile time,
+// folds into constant address offsets.  Inputs and outputs of a transform are
+// in natural order.
+template <int PS> __device__ __forceinline__ int padp(int p) { return p + (p >> PS); }
 
 __device__ __forceinline__ float pow_p(float x, int p) { return p == 3 ? x * x * x : ipow<float>(x, p); }
 
@@ -119,7 +122,7 @@ __device__ __forceinline__ void fpass(const float2 *src, float2 *dst, int logP, 
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const int p = i + r * STRIDE;
-            u[r] = src[PADIN ? pad16(p) : p];
+            u[r] = src[PADIN ? padp<GShape<N, E>::PS>(p) : p];
         }
         if constexpr (TWID) {
             const float2 *__restrict__ twp = tw + (P - E) + k;
@@ -133,7 +136,7 @@ __device__ __forceinline__ void fpass(const float2 *src, float2 *dst, int logP, 
             const int q = j + r * P;
             float2 v = u[r];
             if (!PADOUT && power > 0) v = mk<float>(pow_p(v.x, power), pow_p(-v.y, power));
-            dst[PADOUT ? pad16(q) : q] = v;
+            dst[PADOUT ? padp<GShape<N, E>::PS>(q) : q] = v;
         }
     }
 }
@@ -187,7 +190,7 @@ template <int N, int E> struct Col2Smem {
 };
 
 template <int N, int E>
-__global__ void __launch_bounds__(E == 8 ? 1024 : 768, 1) k2_col(const ColArgs<float> a) {
+__global__ void __launch_bounds__(E == 8 ? 1024 : E == 16 ? 768 : 512, 1) k2_col(const ColArgs<float> a) {
     using C = float2;
     using S = GShape<N, E>;
     using L = Col2Smem<N, E>;
@@ -397,7 +400,7 @@ __device__ __forceinline__ void noise_range(const SysP<float> &sp, const FieldP<
 }
 
 template <int N, int E, bool TILED>
-__global__ void __launch_bounds__(1024) k2_row(const RowArgs<float> a) {
+__global__ void __launch_bounds__(E == 32 ? 512 : 1024) k2_row(const RowArgs<float> a) {
     using C = float2;
     using S = GShape<N, E>;
     constexpr int TPF = S::TPF;
@@ -570,7 +573,7 @@ __global__ void __launch_bounds__(1024) k2_row(const RowArgs<float> a) {
 // ---------------------------------------------------------------------------
 template <int N, int E> cudaError_t launch_col2_ne(const ColArgs<float> &a, int nslots, int ntiles, cudaStream_t st) {
     const int threads = 4 * GShape<N, E>::TPF + 32 * a.aux_warps;
-    if (a.aux_warps < 1 || threads > (E == 8 ? 1024 : 768)) return cudaErrorInvalidConfiguration;
+    if (a.aux_warps < 1 || threads > (E == 8 ? 1024 : E == 16 ? 768 : 512)) return cudaErrorInvalidConfiguration;
     cudaError_t e = ensure_smem(k2_col<N, E>, Col2Smem<N, E>::BYTES);
     if (e != cudaSuccess) return e;
     return launch_pdl(k2_col<N, E>, dim3(ntiles, nslots), threads, Col2Smem<N, E>::BYTES, st, a);
@@ -579,8 +582,8 @@ template <int N, int E> cudaError_t launch_col2_ne(const ColArgs<float> &a, int 
 template <int N, int E, bool TILED>
 cudaError_t launch_row2_ne(const RowArgs<float> &a, int nslots, cudaStream_t st) {
     const int nw = a.G, threads = nw * GShape<N, E>::TPF + 32 * a.noise_warps;
-    if (nw < 1 || nw > 8 || (nw & (nw - 1)) || a.sp.rows % (2 * nw) || a.noise_warps < 0 || threads > 1024 ||
-        (TILED && a.noise))
+    if (nw < 1 || nw > 8 || (nw & (nw - 1)) || a.sp.rows % (2 * nw) || a.noise_warps < 0 ||
+        threads > (E == 32 ? 512 : 1024) || (TILED && a.noise))
         return cudaErrorInvalidConfiguration;
     const size_t smem = Row2Smem<N, E>::bytes(nw);
     cudaError_t e = ensure_smem(k2_row<N, E, TILED>, smem);

@@ -13,7 +13,7 @@ template <> struct CplxOf<double> { using type = double2; };
 template <typename T> using cplx = typename CplxOf<T>::type;
 
 // Twiddle factors: the host builds, in FP64, one table per transform length
-// n = 2, 4, ..., kMaxFftN and radix cap emax (8 or 16).  A length-n FFT runs
+// n = 2, 4, ..., kMaxFftN and radix cap emax (8, 16 or 32).  A length-n FFT runs
 // radix-E passes (E = min(n, emax)) and a last pass of radix n / P (<= E).
 // The pass that follows P > 1 points already transformed, of radix
 // R = min(E, n / P), needs exp(-2 pi i r k / (P R)) for 1 <= r < R, k < P,
@@ -22,8 +22,10 @@ template <typename T> using cplx = typename CplxOf<T>::type;
 // (16-byte aligned, room for n entries), so kernels stage it with one bulk
 // copy.
 constexpr int kMaxFftN = 1024;
-__host__ __device__ constexpr int twiddle_offset(int n, int emax) { return (emax == 16 ? 2 * kMaxFftN : 0) + n; }
-constexpr int kTwiddleEntries = 4 * kMaxFftN;
+__host__ __device__ constexpr int twiddle_offset(int n, int emax) {
+    return (emax == 32 ? 4 * kMaxFftN : emax == 16 ? 2 * kMaxFftN : 0) + n;
+}
+constexpr int kTwiddleEntries = 6 * kMaxFftN;
 
 constexpr int kTileW = 4;       // kx columns per tile of every spectral array
 constexpr int kMaxFields = 4;

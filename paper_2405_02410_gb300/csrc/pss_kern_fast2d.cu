@@ -2,14 +2,17 @@
 #include "pss_fast2d.cuh"
 namespace pss {
 
-// a.E: radix of the FFT passes, 8 or 16
+// a.E: radix of the FFT passes, 8 or 16 (or 32 for sides of 1024); a radix a
+// side does not take falls back to 16
 cudaError_t launch_col2(const ColArgs<float> &a, int nslots, int ntiles, cudaStream_t st) {
     const bool r16 = a.E == 16;
     switch (a.sp.n_inner) {
         case 256: return r16 ? launch_col2_ne<256, 16>(a, nslots, ntiles, st) : launch_col2_ne<256, 8>(a, nslots, ntiles, st);
         case 512: return r16 ? launch_col2_ne<512, 16>(a, nslots, ntiles, st) : launch_col2_ne<512, 8>(a, nslots, ntiles, st);
         case 1024:
-            return r16 ? launch_col2_ne<1024, 16>(a, nslots, ntiles, st) : launch_col2_ne<1024, 8>(a, nslots, ntiles, st);
+            return a.E == 32 ? launch_col2_ne<1024, 32>(a, nslots, ntiles, st)
+                 : r16       ? launch_col2_ne<1024, 16>(a, nslots, ntiles, st)
+                             : launch_col2_ne<1024, 8>(a, nslots, ntiles, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -20,7 +23,7 @@ cudaError_t launch_row2(const RowArgs<float> &a, int nslots, cudaStream_t st, bo
     switch (a.sp.nx) {
         case 256: return r16 ? PSS_ROW2(256, 16) : PSS_ROW2(256, 8);
         case 512: return r16 ? PSS_ROW2(512, 16) : PSS_ROW2(512, 8);
-        case 1024: return r16 ? PSS_ROW2(1024, 16) : PSS_ROW2(1024, 8);
+        case 1024: return a.E == 32 ? PSS_ROW2(1024, 32) : r16 ? PSS_ROW2(1024, 16) : PSS_ROW2(1024, 8);
         default: return cudaErrorInvalidValue;
     }
 #undef PSS_ROW2

@@ -85,14 +85,16 @@ def test_launch_shapes_do_not_change_bits(knobs):
 
 @pytest.mark.parametrize("shape", [(1024, 1024), (512, 1024), (1024, 512)])
 def test_fft_radix_changes_only_rounding(shape):
-    # radix-8 and radix-16 passes order the sums differently: FP32 rounding apart
+    # radix-8, -16 and -32 passes order the sums differently: FP32 rounding apart
+    # (radix 32 serves sides of 1024; other sides fall back to 16)
     kw = dict(dt=0.01, a=-1, b=1, K=1, D=0.01, seed=9)
     runs = []
-    for radix in (8, 16):
+    for radix in (8, 16, 32):
         s = _model_b(shape, knobs=dict(col2_radix=radix, row2_radix=radix), **kw)
         s.step(50)
         runs.append(s.get_spectrum(0))
     assert rel(runs[1], runs[0]) < 1e-5
+    assert rel(runs[2], runs[0]) < 1e-5
 
 
 def test_switching_paths_mid_run():
