@@ -378,6 +378,7 @@ template <typename T> struct Seq {
         a.adj_step = adj_step;
         a.d_adj_base = (mode == COL_ADJ_A || mode == COL_ADJ_B) ? s->d_seg + 1 : nullptr;
         a.grad = s->d_grad;
+        a.in_colmajor = (mode == COL_ADJ_A && fast2d(s)) ? 1 : 0;   // the product the fast path recomputed
         a.slot_stride = s->field_elems;
         a.slot0 = slot0;
         a.tw = (const cplx<T> *)s->tw;
@@ -460,14 +461,17 @@ template <typename T> struct Seq {
     }
 
     // the fast 2D path (FP32 only): k2_col, then k2_row
-    int col2(int mode) {
+    int col2(int mode) { return col2_ptrs(mode, state(), B(), A(), nullptr); }
+
+    int col2_ptrs(int mode, cplx<T> *st_ptr, const cplx<T> *in_ptr, cplx<T> *out_ptr, cplx<T> *st_out) {
         if constexpr (std::is_same<T, float>::value) {
             ColArgs<float> a{};
             a.sp = sys_params<float>(s);
             a.fps = (const FieldP<float> *)s->fps;
-            a.in = B();
-            a.out = A();
-            a.state = state();
+            a.in = in_ptr;
+            a.out = out_ptr;
+            a.state = st_ptr;
+            a.state_out = st_out;
             a.slot_stride = s->field_elems;
             a.slot0 = slot0;
             a.tw = (const float2 *)s->tw;
@@ -485,19 +489,23 @@ template <typename T> struct Seq {
             if (e != cudaSuccess) return cuda_fail(s, e, "k2_col launch");
             return PSS_OK;
         } else {
-            (void)mode;
-            return fail(s, PSS_EUNSUPPORTED, "the one-warp 2D path is FP32 only");
+            (void)mode; (void)st_ptr; (void)in_ptr; (void)out_ptr; (void)st_out;
+            return fail(s, PSS_EUNSUPPORTED, "the FFT-group 2D path is FP32 only");
         }
     }
 
     // (the step counter is advanced by k2_col; inc documents the caller's intent)
-    int row2(bool inc) {
+    int row2(bool inc) { (void)inc; return row2_ptrs(A(), B(), nullptr); }
+
+    int row2_ptrs(const cplx<T> *in_ptr, cplx<T> *out_ptr, T *real_out) {
         if constexpr (std::is_same<T, float>::value) {
             RowArgs<float> a{};
             a.sp = sys_params<float>(s);
             a.fps = (const FieldP<float> *)s->fps;
-            a.in = A();
-            a.out = B();
+            a.in = in_ptr;
+            a.out = out_ptr;
+            a.real_out = real_out;
+            a.real_stride = 0;   // one slot (the adjoint's recompute)
             a.slot_stride = s->field_elems;
             a.slot0 = slot0;
             a.tw = (const float2 *)s->tw;
@@ -518,8 +526,8 @@ template <typename T> struct Seq {
             if (e != cudaSuccess) return cuda_fail(s, e, "k2_row launch");
             return PSS_OK;
         } else {
-            (void)inc;
-            return fail(s, PSS_EUNSUPPORTED, "the one-warp 2D path is FP32 only");
+            (void)in_ptr; (void)out_ptr; (void)real_out;
+            return fail(s, PSS_EUNSUPPORTED, "the FFT-group 2D path is FP32 only");
         }
     }
 
@@ -617,6 +625,10 @@ template <typename T> struct Seq {
     // r_n+1 = F^-1[m phi_n+1] (real_out), which the adjoint step needs.
     int recompute_step(cplx<T> *st_in, cplx<T> *st_out, const cplx<T> *prod_in, cplx<T> *prod_out, T *real_out) {
         int rc;
+        if (fast2d(s)) {   // the kernels (and the column-major product) of the forward run
+            if ((rc = col2_ptrs(COL_STEP, st_in, prod_in, A(), st_out))) return rc;          // -> A, step++
+            return row2_ptrs(A(), prod_out, real_out);                                       // A -> prod, r, noise
+        }
         if ((rc = col_ptrs(COL_STEP, st_in, prod_in, A(), nullptr, 0, st_out))) return rc;  // -> A
         if (s->dim == 3) {
             if ((rc = mid(MID_INV_MASK, true, false))) return rc;                            // A -> B
@@ -629,6 +641,10 @@ template <typename T> struct Seq {
     // The product and real field of the state st (start of a recomputed segment).
     int recompute_prologue(cplx<T> *st, cplx<T> *prod_out, T *real_out) {
         int rc;
+        if (fast2d(s)) {
+            if ((rc = col2_ptrs(COL_INV_MASK, st, nullptr, A(), nullptr))) return rc;         // st -> A
+            return row2_ptrs(A(), prod_out, real_out);                                       // A -> prod, r, noise
+        }
         if ((rc = col_ptrs(COL_INV_MASK, st, nullptr, A(), nullptr, 0))) return rc;           // st -> A
         if (s->dim == 3) {
             if ((rc = mid(MID_INV_MASK, true, false))) return rc;                            // A -> B

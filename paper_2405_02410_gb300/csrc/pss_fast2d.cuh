@@ -15,7 +15,9 @@
 //       along y.  Block 0 advances the step counter.
 //   k2_row (one CTA per NW pairs of rows): group j takes rows r0 + 2j and
 //       r0 + 2j + 1 as one complex transform (z = a + i b): C2R of the kept
-//       columns, power p in real space, R2C, split into the two half spectra.
+//       columns, power p in real space, R2C, split into the two half spectra
+//       (with real_out, the de-aliased real rows are stored too: the adjoint's
+//       recomputed forward steps keep them).
 //       Beside the transform groups, "noise" warps draw the Philox noise of the
 //       next step (unit amplitude, tiled like the state) for the column kernel:
 //       the generator has no data dependence, so it fills the issue slots the
@@ -107,10 +109,12 @@ __device__ __forceinline__ float pow_p(float x, int p) { return p == 3 ? x * x *
 // k = i mod P, transform over r, write y[(i - k) R + k + r P].  tw is the
 // (N, E) table; with power p > 0 (natural-order output only) an output
 // x + i y is stored as x^p + i (-y)^p: for z' = conj(z) that is
-// Re(z)^p + i Im(z)^p.
+// Re(z)^p + i Im(z)^p; with ra, rb set (natural-order output only) x and -y
+// also go to ra[q], rb[q] (the real rows Re z, Im z themselves).
 template <int N, int E, int R, bool TWID, bool PADIN, bool PADOUT>
 __device__ __forceinline__ void fpass(const float2 *src, float2 *dst, int logP, int gl,
-                                      const float2 *__restrict__ tw, int power) {
+                                      const float2 *__restrict__ tw, int power, float *ra = nullptr,
+                                      float *rb = nullptr) {
     constexpr int TPF = GShape<N, E>::TPF;
     constexpr int STRIDE = N / R, BPT = STRIDE / TPF, LOGR = ilog2(R);
     static_assert(STRIDE % TPF == 0, "every thread takes whole butterflies");
@@ -135,6 +139,10 @@ __device__ __forceinline__ void fpass(const float2 *src, float2 *dst, int logP, 
         for (int r = 0; r < R; ++r) {
             const int q = j + r * P;
             float2 v = u[r];
+            if (!PADOUT && ra) {
+                ra[q] = v.x;
+                rb[q] = -v.y;
+            }
             if (!PADOUT && power > 0) v = mk<float>(pow_p(v.x, power), pow_p(-v.y, power));
             dst[PADOUT ? padp<GShape<N, E>::PS>(q) : q] = v;
         }
@@ -146,10 +154,11 @@ __device__ __forceinline__ void fpass(const float2 *src, float2 *dst, int logP, 
 // order and may be b1, never b0; the result, in natural order, lands in b0 or
 // b1 (GShape::OUT).  b0 and b1 hold BUF points each.  The caller makes the
 // input visible to the group before the call; the result is visible to the
-// group on return.
+// group on return.  power, ra, rb: see fpass (applied on the last pass).
 template <int N, int E>
 __device__ __forceinline__ float2 *fft_fwd_group(const float2 *in, float2 *b0, float2 *b1, int gl, int id,
-                                                 const float2 *__restrict__ tw, int power) {
+                                                 const float2 *__restrict__ tw, int power, float *ra = nullptr,
+                                                 float *rb = nullptr) {
     using S = GShape<N, E>;
     fpass<N, E, E, false, false, true>(in, b0, 0, gl, tw, 0);
     group_sync<S::TPF>(id);
@@ -163,7 +172,7 @@ __device__ __forceinline__ float2 *fft_fwd_group(const float2 *in, float2 *b0, f
         cur = nxt;
         nxt = tmp;
     }
-    fpass<N, E, S::RL, true, true, false>(cur, nxt, logP, gl, tw, power);
+    fpass<N, E, S::RL, true, true, false>(cur, nxt, logP, gl, tw, power, ra, rb);
     group_sync<S::TPF>(id);
     return nxt;
 }
@@ -519,14 +528,21 @@ __global__ void __launch_bounds__(E == 32 ? 512 : 1024) k2_row(const RowArgs<flo
         return;
     }
     // ---- z' = F(Y) = conj(z) = a - i b; its last pass stores u = a^p + i b^p,
-    // the product of both rows; then W = F(u).  Both results land in b1.
+    // the product of both rows (and, with real_out, the rows a and b
+    // themselves); then W = F(u).  Both results land in b1.
     {
         C *b0 = WBUF + g * S::WS, *b1 = b0 + S::BUF;
         const C *src = b1;
         C *p0 = b0, *p1 = b1;
+        float *ra = nullptr, *rb = nullptr;
+        if (!TILED && a.real_out) {
+            ra = a.real_out + (size_t)slot * a.real_stride + (size_t)(r0 + 2 * g) * N;
+            rb = ra + N;
+        }
 #pragma unroll 1
         for (int it = 0; it < 2; ++it) {
-            C *o = fft_fwd_group<N, E>(src, p0, p1, gl, 1 + g, TW, it == 0 ? power : 0);
+            C *o = fft_fwd_group<N, E>(src, p0, p1, gl, 1 + g, TW, it == 0 ? power : 0, it == 0 ? ra : nullptr,
+                                       it == 0 ? rb : nullptr);
             src = o;
             p0 = o == b0 ? b1 : b0;
             p1 = o;

@@ -103,6 +103,8 @@ template <typename T> struct ColArgs {
     const long long *d_adj_base;   // if set, the noise step is adj_step + *d_adj_base
     double *grad;
     int aux_warps;        // k2_col: warps that join the update beside the FFT warps
+    int in_colmajor;      // k_col: `in` holds each tile's columns one after another ([c][pos]), as the
+                          // FP32 2D path writes its product (the adjoint reads it)
     const cplx<T> *noise; // k2_col: unit-amplitude noise of this step (tiled like the state)
 };
 

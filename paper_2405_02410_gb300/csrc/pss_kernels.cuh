@@ -363,9 +363,11 @@ __global__ void __launch_bounds__(512, N >= 512 ? 1 : 2) k_col(const ColArgs<T> 
     const int kx = my_tile * W + c;
 
     if (need_in) {
-        // forward transform along this axis: P_q
-        const C *xb = X + ch * CS + c;
-        const int which = fft_run<T, N, EMAX, -1>([&](int p) { return xb[p * W]; },
+        // forward transform along this axis: P_q (the staged chunk is [pos][W],
+        // or [W][pos] for a column-major input)
+        const int xstride = a.in_colmajor ? 1 : W;
+        const C *xb = X + ch * CS + (a.in_colmajor ? c * N : c);
+        const int which = fft_run<T, N, EMAX, -1>([&](int p) { return xb[p * xstride]; },
                                             [&](int p, C v, C *fr) { fr[spad(p)] = v; },
                                             Y + f * SF, X + f * SF, lane, active, tw);
         __syncthreads();

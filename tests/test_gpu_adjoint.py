@@ -140,3 +140,32 @@ def test_torch_autograd_function_matches_finite_differences():
     fd = (loss(h0.detach() + eps * d, params.detach()) - loss(h0.detach() - eps * d, params.detach())) / (2 * eps)
     ad = torch.real(torch.vdot(h0.grad.reshape(-1), d.reshape(-1)))
     assert abs(ad.item() - fd.item()) <= 1e-6 * abs(fd.item())
+
+
+@pytest.mark.parametrize("shape", [(256, 256), (256, 512)])
+def test_adjoint_on_the_fft_group_path(shape):
+    # FP32 2D sides of 256..1024: the forward run and the backward pass's
+    # recomputed steps take the FFT-group kernels (column-major product read
+    # by the adjoint's column kernel); 13 steps = three segments of 4 and one
+    # of 1, so the captured segment graph is replayed
+    dt, seed, n = 0.02, 23, 13
+    m = O.model_b(shape, dt=dt, seed=seed, **PARAMS)
+    phi0 = O.to_spectrum(m, O.init_uniform(m, -0.3, 0.3))
+    c = _weights(shape)
+    lamT = 2.0 * c * O.run(m, phi0, 0, n) / m.n_sites
+    lam0, g = O.adjoint(m, phi0, 0, n, lamT)
+    ref = np.array([g[1], -g[6], g[2], g[10]])
+    runs = {}
+    for fast in (1, 0):
+        s = _gpu_system(shape, "f32", dt, seed)
+        s.set_tuning("fast2d", fast)
+        assert s.step_path == ("fast2d" if fast else "generic")
+        s.adjoint_forward(n)
+        grads, lam0_gpu = s.adjoint_backward(O.half(lamT), 4)
+        assert rel(lam0_gpu, O.half(lam0)) < 1e-3
+        assert np.max(np.abs(grads - ref) / np.abs(ref)) < 1e-3, (fast, grads, ref)
+        assert s.get_step() == n
+        runs[fast] = (grads, lam0_gpu)
+    # the two paths agree to FP32 rounding
+    assert rel(runs[1][1], runs[0][1]) < 1e-4
+    assert np.max(np.abs(runs[1][0] - runs[0][0]) / np.abs(runs[0][0])) < 1e-4
