@@ -157,9 +157,12 @@ __device__ __forceinline__ void col_adjoint(const ColArgs<T> &a, const FieldP<T>
     auto gofs = [&](int q) { return ((size_t)(chunk_tile(q) * sp.n_outer + chunk_o(q)) * N) * W; };
     // ADJ_A writes nu into the work buffer that does not hold P
     C *NU = which == 0 ? X : Y;
-    double acc[11];
+    // a thread's partial sums over its few modes are in the working precision;
+    // the sums over threads, CTAs and time steps are FP64
+    using Acc = T;
+    Acc acc[11];
 #pragma unroll
-    for (int i = 0; i < 11; ++i) acc[i] = 0.0;
+    for (int i = 0; i < 11; ++i) acc[i] = Acc(0);
     const uint32_t step = (uint32_t)(a.adj_step + (a.d_adj_base ? *a.d_adj_base : 0));
     const PhiloxKey key = philox_key(fp.seed_lo, fp.seed_hi);
 #pragma unroll 1
@@ -184,16 +187,16 @@ __device__ __forceinline__ void col_adjoint(const ColArgs<T> &a, const FieldP<T>
             NU[ff * SF + spad(pos)] = cscale<T>(mu, dtM);
             // the duplicate pencil of a self-paired 3D CTA does not count twice
             if (valid && chunk_writes(chq)) {
-                const double wgt = (kx == 0 || 2 * kx == sp.nx) ? 1.0 : 2.0;
+                const Acc wgt = (kx == 0 || 2 * kx == sp.nx) ? Acc(1) : Acc(2);
                 const C phin = a.aux[sofs + gofs(chq) + pos * W + cc];
-                const double a_phi = wgt * ((double)mu.x * phin.x + (double)mu.y * phin.y);
-                const double a_P = wgt * ((double)mu.x * pv.x + (double)mu.y * pv.y);
-                double q2k = 1.0;
+                const Acc a_phi = wgt * sp.dt * (mu.x * phin.x + mu.y * phin.y);
+                const Acc a_P = wgt * sp.dt * (mu.x * pv.x + mu.y * pv.y);
+                Acc q2k = Acc(1);
 #pragma unroll
                 for (int k = 0; k < 5; ++k) {
-                    acc[k] += -(double)sp.dt * q2k * a_phi;
-                    acc[5 + k] += (double)sp.dt * q2k * a_P;
-                    q2k *= (double)q2;
+                    acc[k] -= q2k * a_phi;
+                    acc[5 + k] += q2k * a_P;
+                    q2k *= q2;
                 }
                 if (fp.noisy) {
                     // the noise of this mode (one draw per pair of kx columns; use the even member's)
@@ -205,7 +208,7 @@ __device__ __forceinline__ void col_adjoint(const ColArgs<T> &a, const FieldP<T>
                                   noise_amp<T>(fp.sigma0, fp.noise_pow, q2o), kx0 + 1 < sp.hx, sp,
                                   (uint32_t)fp.field_id, key, step, xi0, xi1);
                     const C xi = (kx & 1) ? xi1 : xi0;
-                    acc[10] += wgt * ((double)mu.x * xi.x + (double)mu.y * xi.y);
+                    acc[10] += wgt * (mu.x * xi.x + mu.y * xi.y);
                 }
             }
         } else {
@@ -223,7 +226,7 @@ __device__ __forceinline__ void col_adjoint(const ColArgs<T> &a, const FieldP<T>
         __syncthreads();
 #pragma unroll
         for (int k = 0; k < 11; ++k) {
-            double v = acc[k];
+            double v = (double)acc[k];
             for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
             if ((t & 31) == 0 && v != 0.0) atomicAdd(&red[k], v);
         }
@@ -287,7 +290,7 @@ template <typename T, int N> struct ColSmem {
 };
 
 template <typename T, int N, int EMAX, bool ADJ>
-__global__ void __launch_bounds__(512, N >= 512 ? 1 : 2) k_col(const ColArgs<T> a) {
+__global__ void __launch_bounds__(512, (N >= 512 || ADJ) ? 1 : 2) k_col(const ColArgs<T> a) {
     using C = cplx<T>;
     using L = ColSmem<T, N>;
     constexpr int TPF = FftShape<N, EMAX>::TPF;
