@@ -563,6 +563,37 @@ template <typename T> struct Seq {
         }
     }
 
+    // the 2D adjoint's x pass on FFT groups (FP32): A -> B (tiled), times p r^(p-1)
+    int row2_adj(const T *real_r) {
+        if constexpr (std::is_same<T, float>::value) {
+            RowArgs<float> a{};
+            a.sp = sys_params<float>(s);
+            a.fps = (const FieldP<float> *)s->fps;
+            a.in = A();
+            a.out = B();
+            a.real_in = real_r;
+            a.real_stride = 0;
+            a.slot_stride = s->field_elems;
+            a.slot0 = slot0;
+            a.tw = (const float2 *)s->tw;
+            a.d_step = s->d_step;
+            a.d_status = s->d_status;
+            a.mode = ROW_ADJ;
+            a.E = row2_radix(s);
+            a.G = row2_pairs(s);
+            a.kx_cols_max = s->hx;
+            if (timer) timer->begin(2, st);
+            cudaError_t e = launch_row2(a, nslots, st, true);
+            if (timer) timer->begin(2, st);
+            s->launches++;
+            if (e != cudaSuccess) return cuda_fail(s, e, "k2_row (adjoint x pass) launch");
+            return PSS_OK;
+        } else {
+            (void)real_r;
+            return fail(s, PSS_EUNSUPPORTED, "the FFT-group x pass is FP32 only");
+        }
+    }
+
     int x_pass_3d() { return fast3d_rows(s) ? row3() : row(ROW_FUSED, false, false, false, nullptr, 0); }  // B -> A
 
     // B <- x-transformed product of the current state (start of a run)
@@ -668,6 +699,8 @@ template <typename T> struct Seq {
             if ((rc = mid(MID_INV_FULL, true, false))) return rc;                            // A -> B
             if ((rc = row_ptrs(ROW_ADJ, B(), A(), false, real_r, nullptr, 0))) return rc;     // B -> A
             if ((rc = mid(MID_FWD, true, false))) return rc;                                 // A -> B
+        } else if (fast2d(s)) {
+            if ((rc = row2_adj(real_r))) return rc;                                          // A -> B
         } else {
             if ((rc = row_ptrs(ROW_ADJ, A(), B(), false, real_r, nullptr, 0))) return rc;     // A -> B
         }

@@ -110,11 +110,13 @@ __device__ __forceinline__ float pow_p(float x, int p) { return p == 3 ? x * x *
 // (N, E) table; with power p > 0 (natural-order output only) an output
 // x + i y is stored as x^p + i (-y)^p: for z' = conj(z) that is
 // Re(z)^p + i Im(z)^p; with ra, rb set (natural-order output only) x and -y
-// also go to ra[q], rb[q] (the real rows Re z, Im z themselves).
+// also go to ra[q], rb[q] (the real rows Re z, Im z themselves); with ma, mb
+// set (natural-order output only, instead of the power) the output is
+// p ma[q]^(p-1) x + i p mb[q]^(p-1) (-y), the adjoint's linearised power.
 template <int N, int E, int R, bool TWID, bool PADIN, bool PADOUT>
 __device__ __forceinline__ void fpass(const float2 *src, float2 *dst, int logP, int gl,
                                       const float2 *__restrict__ tw, int power, float *ra = nullptr,
-                                      float *rb = nullptr) {
+                                      float *rb = nullptr, const float *ma = nullptr, const float *mb = nullptr) {
     constexpr int TPF = GShape<N, E>::TPF;
     constexpr int STRIDE = N / R, BPT = STRIDE / TPF, LOGR = ilog2(R);
     static_assert(STRIDE % TPF == 0, "every thread takes whole butterflies");
@@ -143,7 +145,12 @@ __device__ __forceinline__ void fpass(const float2 *src, float2 *dst, int logP, 
                 ra[q] = v.x;
                 rb[q] = -v.y;
             }
-            if (!PADOUT && power > 0) v = mk<float>(pow_p(v.x, power), pow_p(-v.y, power));
+            if (!PADOUT && ma) {
+                v = mk<float>(float(power) * ipow<float>(ma[q], power - 1) * v.x,
+                              float(power) * ipow<float>(mb[q], power - 1) * (-v.y));
+            } else if (!PADOUT && power > 0) {
+                v = mk<float>(pow_p(v.x, power), pow_p(-v.y, power));
+            }
             dst[PADOUT ? padp<GShape<N, E>::PS>(q) : q] = v;
         }
     }
@@ -154,11 +161,13 @@ __device__ __forceinline__ void fpass(const float2 *src, float2 *dst, int logP, 
 // order and may be b1, never b0; the result, in natural order, lands in b0 or
 // b1 (GShape::OUT).  b0 and b1 hold BUF points each.  The caller makes the
 // input visible to the group before the call; the result is visible to the
-// group on return.  power, ra, rb: see fpass (applied on the last pass).
+// group on return.  power, ra, rb, ma, mb: see fpass (applied on the last
+// pass).
 template <int N, int E>
 __device__ __forceinline__ float2 *fft_fwd_group(const float2 *in, float2 *b0, float2 *b1, int gl, int id,
                                                  const float2 *__restrict__ tw, int power, float *ra = nullptr,
-                                                 float *rb = nullptr) {
+                                                 float *rb = nullptr, const float *ma = nullptr,
+                                                 const float *mb = nullptr) {
     using S = GShape<N, E>;
     fpass<N, E, E, false, false, true>(in, b0, 0, gl, tw, 0);
     group_sync<S::TPF>(id);
@@ -172,7 +181,7 @@ __device__ __forceinline__ float2 *fft_fwd_group(const float2 *in, float2 *b0, f
         cur = nxt;
         nxt = tmp;
     }
-    fpass<N, E, S::RL, true, true, false>(cur, nxt, logP, gl, tw, power, ra, rb);
+    fpass<N, E, S::RL, true, true, false>(cur, nxt, logP, gl, tw, power, ra, rb, ma, mb);
     group_sync<S::TPF>(id);
     return nxt;
 }
@@ -367,8 +376,10 @@ __global__ void __launch_bounds__(E == 8 ? 1024 : E == 16 ? 768 : 512, 1) k2_col
 //
 // TILED = false: the 2D step's column-major work arrays, the input holding
 // the conjugated y-inverse.  TILED = true: the tiled arrays of the generic
-// kernels ([tile][row][4], input as it is), as the x pass of the 3D step; the
-// CTA's rows of one tile are a 64 NW-byte run, moved as 16-byte pieces.
+// kernels ([tile][row][4], input as it is), as the x pass of the 3D step and
+// of the 2D adjoint step (mode ROW_ADJ: C2R of all columns, times
+// p r^(p-1) with r the stored real rows, R2C); the CTA's rows of one tile are
+// a 64 NW-byte run, moved as 16-byte pieces.
 // ---------------------------------------------------------------------------
 template <int N, int E> struct Row2Smem {
     static size_t bytes(int nw) { return 128 + sizeof(float2) * ((size_t)N + (size_t)nw * GShape<N, E>::WS); }
@@ -453,8 +464,9 @@ __global__ void __launch_bounds__(E == 32 ? 512 : 1024) k2_row(const RowArgs<flo
     // as they are (TILED), and the two swapped when the input holds their
     // conjugates (the 2D path).  All of a thread's loads are issued before the
     // first use.
-    const int kcm = a.kx_cols_max;
-    const int kc = a.fps[slot].kx_cols;
+    const bool adj = TILED && a.mode == ROW_ADJ;
+    const int kcm = adj ? sp.hx : a.kx_cols_max;
+    const int kc = adj ? sp.hx : a.fps[slot].kx_cols;
     auto stage = [&](int k, int j, float ar, float ai, float br, float bi) {
         C *Y = WBUF + j * S::WS + S::BUF;
         if (k >= kc) { ar = 0.f; ai = 0.f; br = 0.f; bi = 0.f; }
@@ -535,14 +547,19 @@ __global__ void __launch_bounds__(E == 32 ? 512 : 1024) k2_row(const RowArgs<flo
         const C *src = b1;
         C *p0 = b0, *p1 = b1;
         float *ra = nullptr, *rb = nullptr;
+        const float *ma = nullptr, *mb = nullptr;
         if (!TILED && a.real_out) {
             ra = a.real_out + (size_t)slot * a.real_stride + (size_t)(r0 + 2 * g) * N;
             rb = ra + N;
         }
+        if (adj) {
+            ma = a.real_in + (size_t)slot * a.real_stride + (size_t)(r0 + 2 * g) * N;
+            mb = ma + N;
+        }
 #pragma unroll 1
         for (int it = 0; it < 2; ++it) {
             C *o = fft_fwd_group<N, E>(src, p0, p1, gl, 1 + g, TW, it == 0 ? power : 0, it == 0 ? ra : nullptr,
-                                       it == 0 ? rb : nullptr);
+                                       it == 0 ? rb : nullptr, it == 0 ? ma : nullptr, it == 0 ? mb : nullptr);
             src = o;
             p0 = o == b0 ? b1 : b0;
             p1 = o;

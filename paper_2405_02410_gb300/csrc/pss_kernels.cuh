@@ -165,57 +165,62 @@ __device__ __forceinline__ void col_adjoint(const ColArgs<T> &a, const FieldP<T>
     for (int i = 0; i < 11; ++i) acc[i] = Acc(0);
     const uint32_t step = (uint32_t)(a.adj_step + (a.d_adj_base ? *a.d_adj_base : 0));
     const PhiloxKey key = philox_key(fp.seed_lo, fp.seed_hi);
+    // one iteration per pair of neighbouring columns at one position: a single
+    // Philox draw serves both modes of the pair
+    const int logF = __ffs(F) - 1;
 #pragma unroll 1
-    for (int i = t; i < N * F; i += nthr) {
-        const int pos = i >> (__ffs(F) - 1), ff = i & (F - 1);
-        const int chq = ff >> 2, cc = ff & 3;
+    for (int j = t; j < (N * F) >> 1; j += nthr) {
+        const int pos = j >> (logF - 1), ff0 = (j & ((F >> 1) - 1)) << 1;
+        const int chq = ff0 >> 2, cc0 = ff0 & 3;
         const int tile = chunk_tile(chq);
-        const int kx = tile * W + cc;
+        const int kx0 = tile * W + cc0;
         const int o = chunk_o(chq);
         const int ky = sp.dim == 3 ? o : (sp.dim == 2 ? pos : 0);
         const int kz = sp.dim == 3 ? pos : 0;
-        const bool valid = tile < a.n_tiles && kx < sp.hx;
-        const T qx = T(kx) * sp.gx, qy = T(signed_k(ky, sp.ny)) * sp.gy, qz = T(signed_k(kz, sp.nz)) * sp.gz;
-        const T q2 = qx * qx + qy * qy + qz * qz;
-        C *ph = &PHI[chq * CS + pos * W + cc];
-        const C pv = P[ff * SF + spad(pos)];
-        if (mode_a) {
-            const T g = T(1) / (T(1) + sp.dt * poly5<T>(fp.O, q2));
-            const C mu = valid ? cscale<T>(*ph, g) : mk<T>(0, 0);
-            *ph = mu;
-            const T dtM = fp.power > 0 ? sp.dt * poly5<T>(fp.M, q2) : T(0);
-            NU[ff * SF + spad(pos)] = cscale<T>(mu, dtM);
-            // the duplicate pencil of a self-paired 3D CTA does not count twice
-            if (valid && chunk_writes(chq)) {
-                const Acc wgt = (kx == 0 || 2 * kx == sp.nx) ? Acc(1) : Acc(2);
-                const C phin = a.aux[sofs + gofs(chq) + pos * W + cc];
-                const Acc a_phi = wgt * sp.dt * (mu.x * phin.x + mu.y * phin.y);
-                const Acc a_P = wgt * sp.dt * (mu.x * pv.x + mu.y * pv.y);
-                Acc q2k = Acc(1);
+        const T qy = T(signed_k(ky, sp.ny)) * sp.gy, qz = T(signed_k(kz, sp.nz)) * sp.gz;
+        C xin[2] = {mk<T>(0, 0), mk<T>(0, 0)};
+        if (mode_a && fp.noisy && tile < a.n_tiles && kx0 < sp.hx && chunk_writes(chq)) {
+            const T qe = T(kx0) * sp.gx, qo = T(kx0 + 1) * sp.gx;
+            const T q2e = qe * qe + qy * qy + qz * qz, q2o = qo * qo + qy * qy + qz * qz;
+            noise_pair<T>(kx0 == 0 || 2 * kx0 == sp.nx, kx0, ky, kz, noise_amp<T>(fp.sigma0, fp.noise_pow, q2e),
+                          noise_amp<T>(fp.sigma0, fp.noise_pow, q2o), kx0 + 1 < sp.hx, sp, (uint32_t)fp.field_id, key,
+                          step, xin[0], xin[1]);
+        }
 #pragma unroll
-                for (int k = 0; k < 5; ++k) {
-                    acc[k] -= q2k * a_phi;
-                    acc[5 + k] += q2k * a_P;
-                    q2k *= q2;
+        for (int u = 0; u < 2; ++u) {
+            const int ff = ff0 + u, cc = cc0 + u, kx = kx0 + u;
+            const bool valid = tile < a.n_tiles && kx < sp.hx;
+            const T qx = T(kx) * sp.gx;
+            const T q2 = qx * qx + qy * qy + qz * qz;
+            C *ph = &PHI[chq * CS + pos * W + cc];
+            const C pv = P[ff * SF + spad(pos)];
+            if (mode_a) {
+                const T g = T(1) / (T(1) + sp.dt * poly5<T>(fp.O, q2));
+                const C mu = valid ? cscale<T>(*ph, g) : mk<T>(0, 0);
+                *ph = mu;
+                const T dtM = fp.power > 0 ? sp.dt * poly5<T>(fp.M, q2) : T(0);
+                NU[ff * SF + spad(pos)] = cscale<T>(mu, dtM);
+                // the duplicate pencil of a self-paired 3D CTA does not count twice
+                if (valid && chunk_writes(chq)) {
+                    const Acc wgt = (kx == 0 || 2 * kx == sp.nx) ? Acc(1) : Acc(2);
+                    const C phin = a.aux[sofs + gofs(chq) + pos * W + cc];
+                    const Acc a_phi = wgt * sp.dt * (mu.x * phin.x + mu.y * phin.y);
+                    const Acc a_P = wgt * sp.dt * (mu.x * pv.x + mu.y * pv.y);
+                    Acc q2k = Acc(1);
+    #pragma unroll
+                    for (int k = 0; k < 5; ++k) {
+                        acc[k] -= q2k * a_phi;
+                        acc[5 + k] += q2k * a_P;
+                        q2k *= q2;
+                    }
+                    if (fp.noisy) acc[10] += wgt * (mu.x * xin[u].x + mu.y * xin[u].y);
                 }
-                if (fp.noisy) {
-                    // the noise of this mode (one draw per pair of kx columns; use the even member's)
-                    const int kx0 = kx & ~1;
-                    const T qe = T(kx0) * sp.gx, qo = T(kx0 + 1) * sp.gx;
-                    const T q2e = qe * qe + qy * qy + qz * qz, q2o = qo * qo + qy * qy + qz * qz;
-                    C xi0 = mk<T>(0, 0), xi1 = mk<T>(0, 0);
-                    noise_pair<T>(kx0 == 0 || 2 * kx0 == sp.nx, kx0, ky, kz, noise_amp<T>(fp.sigma0, fp.noise_pow, q2e),
-                                  noise_amp<T>(fp.sigma0, fp.noise_pow, q2o), kx0 + 1 < sp.hx, sp,
-                                  (uint32_t)fp.field_id, key, step, xi0, xi1);
-                    const C xi = (kx & 1) ? xi1 : xi0;
-                    acc[10] += wgt * (mu.x * xi.x + mu.y * xi.y);
-                }
+            } else {
+                bool keep = valid && kx <= fp.kmax[0] && abs(signed_k(ky, sp.ny)) <= fp.kmax[1] &&
+                            abs(signed_k(kz, sp.nz)) <= fp.kmax[2];
+                const C mu = *ph;
+                *ph = keep ? mk<T>(mu.x + pv.x * sp.inv_nsites, mu.y + pv.y * sp.inv_nsites) : (valid ? mu : mk<T>(0, 0));
             }
-        } else {
-            bool keep = valid && kx <= fp.kmax[0] && abs(signed_k(ky, sp.ny)) <= fp.kmax[1] &&
-                        abs(signed_k(kz, sp.nz)) <= fp.kmax[2];
-            const C mu = *ph;
-            *ph = keep ? mk<T>(mu.x + pv.x * sp.inv_nsites, mu.y + pv.y * sp.inv_nsites) : (valid ? mu : mk<T>(0, 0));
         }
     }
     __syncthreads();
