@@ -113,7 +113,9 @@ __device__ __forceinline__ float pow_p(float x, int p) { return p == 3 ? x * x *
 // also go to ra[q], rb[q] (the real rows Re z, Im z themselves); with ma, mb
 // set (natural-order output only, instead of the power) the output is
 // p ma[q]^(p-1) x + i p mb[q]^(p-1) (-y), the adjoint's linearised power.
-template <int N, int E, int R, bool TWID, bool PADIN, bool PADOUT>
+// VAR selects which of these the pass is compiled with (0 none, 1 power and
+// real rows, 2 the linearised power), so each kernel carries only its own.
+template <int N, int E, int R, bool TWID, bool PADIN, bool PADOUT, int VAR = 0>
 __device__ __forceinline__ void fpass(const float2 *src, float2 *dst, int logP, int gl,
                                       const float2 *__restrict__ tw, int power, float *ra = nullptr,
                                       float *rb = nullptr, const float *ma = nullptr, const float *mb = nullptr) {
@@ -141,15 +143,17 @@ __device__ __forceinline__ void fpass(const float2 *src, float2 *dst, int logP, 
         for (int r = 0; r < R; ++r) {
             const int q = j + r * P;
             float2 v = u[r];
-            if (!PADOUT && ra) {
-                ra[q] = v.x;
-                rb[q] = -v.y;
+            if constexpr (!PADOUT && VAR == 1) {
+                if (ra) {
+                    ra[q] = v.x;
+                    rb[q] = -v.y;
+                }
+                if (power > 0) v = mk<float>(pow_p(v.x, power), pow_p(-v.y, power));
             }
-            if (!PADOUT && ma) {
-                v = mk<float>(float(power) * ipow<float>(ma[q], power - 1) * v.x,
-                              float(power) * ipow<float>(mb[q], power - 1) * (-v.y));
-            } else if (!PADOUT && power > 0) {
-                v = mk<float>(pow_p(v.x, power), pow_p(-v.y, power));
+            if constexpr (!PADOUT && VAR == 2) {
+                if (ma)
+                    v = mk<float>(float(power) * ipow<float>(ma[q], power - 1) * v.x,
+                                  float(power) * ipow<float>(mb[q], power - 1) * (-v.y));
             }
             dst[PADOUT ? padp<GShape<N, E>::PS>(q) : q] = v;
         }
@@ -161,9 +165,9 @@ __device__ __forceinline__ void fpass(const float2 *src, float2 *dst, int logP, 
 // order and may be b1, never b0; the result, in natural order, lands in b0 or
 // b1 (GShape::OUT).  b0 and b1 hold BUF points each.  The caller makes the
 // input visible to the group before the call; the result is visible to the
-// group on return.  power, ra, rb, ma, mb: see fpass (applied on the last
-// pass).
-template <int N, int E>
+// group on return.  power, ra, rb, ma, mb, VAR: see fpass (applied on the
+// last pass).
+template <int N, int E, int VAR = 0>
 __device__ __forceinline__ float2 *fft_fwd_group(const float2 *in, float2 *b0, float2 *b1, int gl, int id,
                                                  const float2 *__restrict__ tw, int power, float *ra = nullptr,
                                                  float *rb = nullptr, const float *ma = nullptr,
@@ -181,7 +185,7 @@ __device__ __forceinline__ float2 *fft_fwd_group(const float2 *in, float2 *b0, f
         cur = nxt;
         nxt = tmp;
     }
-    fpass<N, E, S::RL, true, true, false>(cur, nxt, logP, gl, tw, power, ra, rb, ma, mb);
+    fpass<N, E, S::RL, true, true, false, VAR>(cur, nxt, logP, gl, tw, power, ra, rb, ma, mb);
     group_sync<S::TPF>(id);
     return nxt;
 }
@@ -381,8 +385,20 @@ __global__ void __launch_bounds__(E == 8 ? 1024 : E == 16 ? 768 : 512, 1) k2_col
 // p r^(p-1) with r the stored real rows, R2C); the CTA's rows of one tile are
 // a 64 NW-byte run, moved as 16-byte pieces.
 // ---------------------------------------------------------------------------
+// A row group's buffer pair: WS apart in the 2D mapping (element (k, pair j)
+// by consecutive threads: the extra 4 of WS puts the four pairs of a
+// half-warp on distinct banks), WST apart plus a shift in the tiled mapping
+// (element (tile, pair j): a half-warp covers 8 pairs of 2 tiles, 4 columns
+// apart; the shifts (j & 3) + 8 ((j >> 2) & 1) spread them over all 16 bank
+// pairs).
 template <int N, int E> struct Row2Smem {
-    static size_t bytes(int nw) { return 128 + sizeof(float2) * ((size_t)N + (size_t)nw * GShape<N, E>::WS); }
+    static constexpr int WST = 2 * GShape<N, E>::BUF + 16;
+    static size_t bytes(int nw, bool tiled) {
+        return 128 + sizeof(float2) * ((size_t)N + (size_t)nw * (tiled ? WST : GShape<N, E>::WS));
+    }
+    __device__ static int base(int j, bool tiled) {
+        return tiled ? j * WST + (j & 3) + 8 * ((j >> 2) & 1) : j * GShape<N, E>::WS;
+    }
 };
 
 // Unit-amplitude noise (sigma0 = 1) of pairs q0, q0 + stride, ... < q1 of one
@@ -419,7 +435,7 @@ __device__ __forceinline__ void noise_range(const SysP<float> &sp, const FieldP<
     }
 }
 
-template <int N, int E, bool TILED>
+template <int N, int E, bool TILED, bool ADJ>
 __global__ void __launch_bounds__(E == 32 ? 512 : 1024) k2_row(const RowArgs<float> a) {
     using C = float2;
     using S = GShape<N, E>;
@@ -464,11 +480,11 @@ __global__ void __launch_bounds__(E == 32 ? 512 : 1024) k2_row(const RowArgs<flo
     // as they are (TILED), and the two swapped when the input holds their
     // conjugates (the 2D path).  All of a thread's loads are issued before the
     // first use.
-    const bool adj = TILED && a.mode == ROW_ADJ;
+    constexpr bool adj = TILED && ADJ;   // mode ROW_ADJ
     const int kcm = adj ? sp.hx : a.kx_cols_max;
     const int kc = adj ? sp.hx : a.fps[slot].kx_cols;
     auto stage = [&](int k, int j, float ar, float ai, float br, float bi) {
-        C *Y = WBUF + j * S::WS + S::BUF;
+        C *Y = WBUF + Row2Smem<N, E>::base(j, TILED) + S::BUF;
         if (k >= kc) { ar = 0.f; ai = 0.f; br = 0.f; bi = 0.f; }
         if (k == 0 || k == N / 2) { ai = 0.f; bi = 0.f; }   // the half spectra of real rows
         const C lo = mk<float>(ar - bi, -ai - br), hi = mk<float>(ar + bi, ai - br);
@@ -543,7 +559,7 @@ __global__ void __launch_bounds__(E == 32 ? 512 : 1024) k2_row(const RowArgs<flo
     // the product of both rows (and, with real_out, the rows a and b
     // themselves); then W = F(u).  Both results land in b1.
     {
-        C *b0 = WBUF + g * S::WS, *b1 = b0 + S::BUF;
+        C *b0 = WBUF + Row2Smem<N, E>::base(g, TILED), *b1 = b0 + S::BUF;
         const C *src = b1;
         C *p0 = b0, *p1 = b1;
         float *ra = nullptr, *rb = nullptr;
@@ -558,8 +574,9 @@ __global__ void __launch_bounds__(E == 32 ? 512 : 1024) k2_row(const RowArgs<flo
         }
 #pragma unroll 1
         for (int it = 0; it < 2; ++it) {
-            C *o = fft_fwd_group<N, E>(src, p0, p1, gl, 1 + g, TW, it == 0 ? power : 0, it == 0 ? ra : nullptr,
-                                       it == 0 ? rb : nullptr, it == 0 ? ma : nullptr, it == 0 ? mb : nullptr);
+            C *o = fft_fwd_group<N, E, adj ? 2 : 1>(src, p0, p1, gl, 1 + g, TW, it == 0 ? power : 0,
+                                                    it == 0 ? ra : nullptr, it == 0 ? rb : nullptr,
+                                                    it == 0 ? ma : nullptr, it == 0 ? mb : nullptr);
             src = o;
             p0 = o == b0 ? b1 : b0;
             p1 = o;
@@ -569,7 +586,7 @@ __global__ void __launch_bounds__(E == 32 ? 512 : 1024) k2_row(const RowArgs<flo
     // ---- split into the half spectra of the two rows:
     // A_k = (W_k + conj W_{N-k}) / 2, B_k = (W_k - conj W_{N-k}) / 2i
     auto split = [&](int k, int j) {
-        const C *Wj = WBUF + j * S::WS + S::BUF;
+        const C *Wj = WBUF + Row2Smem<N, E>::base(j, TILED) + S::BUF;
         const C wk = Wj[k], wm = Wj[(N - k) & (N - 1)];
         return make_float4(0.5f * (wk.x + wm.x), 0.5f * (wk.y - wm.y), 0.5f * (wk.y + wm.y), -0.5f * (wk.x - wm.x));
     };
@@ -612,16 +629,16 @@ template <int N, int E> cudaError_t launch_col2_ne(const ColArgs<float> &a, int 
     return launch_pdl(k2_col<N, E>, dim3(ntiles, nslots), threads, Col2Smem<N, E>::BYTES, st, a);
 }
 
-template <int N, int E, bool TILED>
+template <int N, int E, bool TILED, bool ADJ>
 cudaError_t launch_row2_ne(const RowArgs<float> &a, int nslots, cudaStream_t st) {
     const int nw = a.G, threads = nw * GShape<N, E>::TPF + 32 * a.noise_warps;
     if (nw < 1 || nw > 8 || (nw & (nw - 1)) || a.sp.rows % (2 * nw) || a.noise_warps < 0 ||
         threads > (E == 32 ? 512 : 1024) || (TILED && a.noise))
         return cudaErrorInvalidConfiguration;
-    const size_t smem = Row2Smem<N, E>::bytes(nw);
-    cudaError_t e = ensure_smem(k2_row<N, E, TILED>, smem);
+    const size_t smem = Row2Smem<N, E>::bytes(nw, TILED);
+    cudaError_t e = ensure_smem(k2_row<N, E, TILED, ADJ>, smem);
     if (e != cudaSuccess) return e;
-    return launch_pdl(k2_row<N, E, TILED>, dim3(a.sp.rows / (2 * nw), nslots), threads, smem, st, a);
+    return launch_pdl(k2_row<N, E, TILED, ADJ>, dim3(a.sp.rows / (2 * nw), nslots), threads, smem, st, a);
 }
 
 }  // namespace pss

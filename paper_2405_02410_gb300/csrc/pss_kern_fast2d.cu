@@ -19,7 +19,10 @@ cudaError_t launch_col2(const ColArgs<float> &a, int nslots, int ntiles, cudaStr
 
 cudaError_t launch_row2(const RowArgs<float> &a, int nslots, cudaStream_t st, bool tiled) {
     const bool r16 = a.E == 16;
-#define PSS_ROW2(N, E) (tiled ? launch_row2_ne<N, E, true>(a, nslots, st) : launch_row2_ne<N, E, false>(a, nslots, st))
+#define PSS_ROW2(N, E)                                                                                    \
+    (!tiled ? launch_row2_ne<N, E, false, false>(a, nslots, st)                                           \
+            : (a.mode == ROW_ADJ ? launch_row2_ne<N, E, true, true>(a, nslots, st)                        \
+                                 : launch_row2_ne<N, E, true, false>(a, nslots, st)))
     switch (a.sp.nx) {
         case 256: return r16 ? PSS_ROW2(256, 16) : PSS_ROW2(256, 8);
         case 512: return r16 ? PSS_ROW2(512, 16) : PSS_ROW2(512, 8);
