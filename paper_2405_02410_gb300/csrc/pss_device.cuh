@@ -296,9 +296,14 @@ __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.lau
 // ---------------------------------------------------------------------------
 // TMA bulk copies (cp.async.bulk, no tensor map) completing on an mbarrier.
 // Every wait is bounded: after kWaitLimit polls the kernel records
-// PSS_STATUS_TIMEOUT and takes its early exit.
+// PSS_STATUS_TIMEOUT and takes its early exit.  A poll lets the hardware
+// suspend the waiting thread for up to kWaitSuspendNs (it resumes as soon as
+// the phase completes), so waiting warps leave the issue slots to the other
+// CTAs of the SM instead of spinning; the total wait stays bounded (at most
+// kWaitLimit x kWaitSuspendNs, about 2 s).
 // ---------------------------------------------------------------------------
-constexpr int kWaitLimit = 1 << 22;
+constexpr int kWaitLimit = 1 << 20;
+constexpr uint32_t kWaitSuspendNs = 2000;
 constexpr int kStatusNonFinite = 1;
 constexpr int kStatusTimeout = 2;
 
@@ -337,10 +342,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t phase) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(phase)
+        : "r"(smem_u32(bar)), "r"(phase), "r"(kWaitSuspendNs)
         : "memory");
     return ok != 0;
 }
