@@ -182,6 +182,8 @@ int pss_time_kernels(pss_system *s, int64_t n, double *avg_ms);
  *   "row2_pairs"  row pairs per row CTA of that path (power of two <= 8);
  *   "row2_noise"  warps per row CTA of that path that draw the next step's
  *                 noise (1..24);
+ *   "row2_share"  percentage (0..100) of that noise drawn by extra CTAs on
+ *                 the SMs the row CTAs leave idle (default 0: none);
  *   "fast3d"      FP32 3D systems whose x side is 256, 512 or 1024 points
  *                 run their x pass on FFT groups (1, default) or on the
  *                 generic row kernel (0);

@@ -90,6 +90,8 @@ struct pss_system {
     int tune_col2_warps = 0, tune_row2_pairs = 0;   // its noise warps per column CTA, row pairs per row CTA
     int tune_col2_radix = 0, tune_row2_radix = 0;   // its FFT pass radix (8 or 16; 0 = automatic)
     int tune_row2_noise = 0;                 // noise warps per row CTA of that path (0 = automatic)
+    int tune_row2_share = -1;                // % of the noise drawn by extra CTAs on idle SMs (-1 = automatic: 0)
+    int num_sms = 0;
     int tune_fast3d = 1;                     // FP32 3D x pass with one FFT group per row pair (0 = generic k_row)
     int64_t launches = 0;
     std::string err;
@@ -519,6 +521,13 @@ template <typename T> struct Seq {
             a.inc_step = 0;   // k2_col advances the step counter
             a.noise = any_noisy(s) ? (float2 *)s->XI : nullptr;
             a.noise_warps = a.noise ? row2_noise_warps(s, a.G) : 0;
+            // optionally, SMs the row CTAs leave idle draw part of the noise in
+            // extra CTAs (measured at 1024^2: slower than spreading the noise
+            // over the row CTAs, 19.0 against 16.0 us/step at 75 %, so off by default)
+            const int row_ctas = s->rows / (2 * a.G) * nslots;
+            const int share = s->tune_row2_share >= 0 ? s->tune_row2_share : 0;
+            a.noise_ctas = (a.noise && share > 0 && nslots == 1) ? std::max(0, s->num_sms - row_ctas) : 0;
+            a.noise_share = a.noise_ctas > 0 ? std::min(64, share * 64 / 100) : 0;
             if (timer) timer->begin(2, st);
             cudaError_t e = launch_row2(a, nslots, st, false);
             if (timer) timer->begin(2, st);
@@ -901,6 +910,7 @@ int do_create(pss_system **out, int batch, int dim, int nx, int ny, int nz, doub
     s->nsites = (long long)nx * ny * nz;
     s->field_elems = (size_t)s->ntiles * s->rows * kTileW;
     cudaError_t e = cudaGetDevice(&s->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, s->device);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMalloc(&s->d_step, sizeof(long long));
     if (e == cudaSuccess) e = cudaMalloc(&s->d_status, sizeof(int));
@@ -1405,6 +1415,10 @@ int pss_set_tuning(pss_system *s, const char *key, int value) {
         s->tune_col2_warps = value;
     }
     else if (k == "row2_pairs") s->tune_row2_pairs = value;
+    else if (k == "row2_share") {
+        if (value > 100) return fail(s, PSS_EINVAL, "row2_share is a percentage");
+        s->tune_row2_share = value;
+    }
     else if (k == "row2_noise") {
         if (value > 24) return fail(s, PSS_EINVAL, "row2_noise is at most 24 (0 = automatic)");
         s->tune_row2_noise = value;

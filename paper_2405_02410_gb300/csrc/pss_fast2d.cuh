@@ -456,14 +456,30 @@ __global__ void __launch_bounds__(E == 32 ? 512 : 1024) k2_row(const RowArgs<flo
     constexpr int H = N / 2 + 1;
     pdl_wait();
     pdl_trigger();
-    if (t >= nf) {
-        // ---- noise warps: this CTA's share of the next step's noise
+    // ---- noise: the next step's, split between the extra noise CTAs (the
+    // first noise_share/64 of the pairs, every thread) and the noise warps of
+    // the row CTAs (the rest)
+    const int nrow_cta = (int)gridDim.x - a.noise_ctas;
+    if ((int)blockIdx.x >= nrow_cta || t >= nf) {
         const FieldP<float> &fp = a.fps[slot];
         if (a.noise && fp.noisy) {
-            const int Q = sp.ntiles * sp.ny * 2, nb = gridDim.x, b = blockIdx.x;
-            noise_range(sp, fp, (uint32_t)(*a.d_step), a.noise + (size_t)slot * a.slot_stride,
-                        (int)((long long)Q * b / nb) + (t - nf), (int)((long long)Q * (b + 1) / nb),
-                        (int)blockDim.x - nf);
+            const int Q = sp.ntiles * sp.ny * 2;
+            const int Qn = a.noise_ctas > 0 ? (int)((long long)Q * a.noise_share / 64) : 0;
+            int q0, q1, i, n;
+            if ((int)blockIdx.x >= nrow_cta) {
+                const int b = blockIdx.x - nrow_cta;
+                q0 = (int)((long long)Qn * b / a.noise_ctas);
+                q1 = (int)((long long)Qn * (b + 1) / a.noise_ctas);
+                i = t;
+                n = blockDim.x;
+            } else {
+                const int b = blockIdx.x;
+                q0 = Qn + (int)((long long)(Q - Qn) * b / nrow_cta);
+                q1 = Qn + (int)((long long)(Q - Qn) * (b + 1) / nrow_cta);
+                i = t - nf;
+                n = (int)blockDim.x - nf;
+            }
+            if (n > 0) noise_range(sp, fp, (uint32_t)(*a.d_step), a.noise + (size_t)slot * a.slot_stride, q0 + i, q1, n);
         }
         return;
     }
@@ -633,12 +649,14 @@ template <int N, int E, bool TILED, bool ADJ>
 cudaError_t launch_row2_ne(const RowArgs<float> &a, int nslots, cudaStream_t st) {
     const int nw = a.G, threads = nw * GShape<N, E>::TPF + 32 * a.noise_warps;
     if (nw < 1 || nw > 8 || (nw & (nw - 1)) || a.sp.rows % (2 * nw) || a.noise_warps < 0 ||
-        threads > (E == 32 ? 512 : 1024) || (TILED && a.noise))
+        threads > (E == 32 ? 512 : 1024) || (TILED && a.noise) || a.noise_ctas < 0 ||
+        (a.noise_ctas > 0 && !a.noise) || a.noise_share < 0 || a.noise_share > 64)
         return cudaErrorInvalidConfiguration;
     const size_t smem = Row2Smem<N, E>::bytes(nw, TILED);
     cudaError_t e = ensure_smem(k2_row<N, E, TILED, ADJ>, smem);
     if (e != cudaSuccess) return e;
-    return launch_pdl(k2_row<N, E, TILED, ADJ>, dim3(a.sp.rows / (2 * nw), nslots), threads, smem, st, a);
+    return launch_pdl(k2_row<N, E, TILED, ADJ>, dim3(a.sp.rows / (2 * nw) + a.noise_ctas, nslots), threads, smem,
+                      st, a);
 }
 
 }  // namespace pss

@@ -125,6 +125,8 @@ template <typename T> struct RowArgs {
     int kx_cols_max;      // largest kept half-spectrum column count over the launch's slots
     cplx<T> *noise;       // k2_row: where the unit-amplitude noise of step *d_step goes (null: none)
     int noise_warps;      // k2_row: warps that draw it beside the transform warps
+    int noise_ctas;       // k2_row: extra CTAs (past the row CTAs) that only draw noise
+    int noise_share;      // k2_row: the pairs those CTAs draw, out of 64 (the row CTAs draw the rest)
 };
 
 template <typename T> struct MidArgs {
