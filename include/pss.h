@@ -189,6 +189,11 @@ int pss_time_kernels(pss_system *s, int64_t n, double *avg_ms);
  *                 generic row kernel (0);
  *   "col2_radix", "row2_radix"
  *                 radix of that path's FFT passes (8 or 16);
+ *   "fuse_adjoint" the backward pass runs the last column part of one
+ *                 adjoint step and the first of the step before it in one
+ *                 launch (1, default, where its shared memory fits) or in
+ *                 two (0); the adjoint fields agree bit for bit, the
+ *                 gradients to the order of their FP64 atomic sums;
  * 0 restores the automatic choice.  Unknown keys return PSS_EINVAL. */
 int pss_set_tuning(pss_system *s, const char *key, int value);
 

@@ -90,6 +90,7 @@ struct pss_system {
     int tune_col2_warps = 0, tune_row2_pairs = 0;   // its noise warps per column CTA, row pairs per row CTA
     int tune_col2_radix = 0, tune_row2_radix = 0;   // its FFT pass radix (8 or 16; 0 = automatic)
     int tune_row2_noise = 0;                 // noise warps per row CTA of that path (0 = automatic)
+    int tune_fuse_adj = 1;                   // adjoint: one launch for part B of a step and part A of the one before
     int tune_row2_share = -1;                // % of the noise drawn by extra CTAs on idle SMs (-1 = automatic: 0)
     int num_sms = 0;
     int tune_fast3d = 1;                     // FP32 3D x pass with one FFT group per row pair (0 = generic k_row)
@@ -368,7 +369,7 @@ template <typename T> struct Seq {
     }
 
     int col_ptrs(int mode, cplx<T> *st_ptr, const cplx<T> *in_ptr, cplx<T> *out_ptr, const cplx<T> *aux,
-                 long long adj_step, cplx<T> *st_out = nullptr) {
+                 long long adj_step, cplx<T> *st_out = nullptr, const cplx<T> *in2 = nullptr) {
         ColArgs<T> a{};
         a.sp = sys_params<T>(s);
         a.fps = (const FieldP<T> *)s->fps;
@@ -378,9 +379,11 @@ template <typename T> struct Seq {
         a.state_out = st_out;
         a.aux = aux;
         a.adj_step = adj_step;
-        a.d_adj_base = (mode == COL_ADJ_A || mode == COL_ADJ_B) ? s->d_seg + 1 : nullptr;
+        a.d_adj_base = (mode == COL_ADJ_A || mode == COL_ADJ_B || mode == COL_ADJ_BA) ? s->d_seg + 1 : nullptr;
         a.grad = s->d_grad;
         a.in_colmajor = (mode == COL_ADJ_A && fast2d(s)) ? 1 : 0;   // the product the fast path recomputed
+        a.in2 = in2;
+        a.in2_colmajor = fast2d(s) ? 1 : 0;
         a.slot_stride = s->field_elems;
         a.slot0 = slot0;
         a.tw = (const cplx<T> *)s->tw;
@@ -698,12 +701,30 @@ template <typename T> struct Seq {
     // with s->L holding lambda_{n+1} on entry, lambda_n on exit; prod is the
     // x(y)-transformed product of phi_n and real_r its de-aliased real field
     // (see the adjoint recursion in COL_ADJ_A / COL_ADJ_B).
-    int adjoint_step(const cplx<T> *phi_n1, const cplx<T> *prod, const T *real_r, long long n_step) {
+    //   part A: mu = g lambda, gradients, nu = dt M mu back along the slowest axis -> A
+    //   x(y) part: w = p r^(p-1) N F^-1[nu] in real space, then its x(y) transform -> B
+    //   part B: lambda_n = mu + m F[w] / N
+    // Over a run of steps, part B of one step and part A of the step before it
+    // share one launch (COL_ADJ_BA) where its shared memory fits.
+    bool fused_adjoint() const {
+        const int F = col_tiles_per_cta(s) * kTileW * (s->dim == 3 ? 2 : 1);
+        const size_t need = col_smem_bytes<T>(s->n_inner, F, col_emax(s), COL_ADJ_BA);
+        return s->tune_fuse_adj && need > 0 && need <= 227 * 1024;
+    }
+
+    int adjoint_part_a(const cplx<T> *phi_n1, const cplx<T> *prod, long long n_step) {
+        return col_ptrs(COL_ADJ_A, (cplx<T> *)s->L, prod, A(), phi_n1, n_step);
+    }
+
+    int adjoint_part_b(long long n_step) { return col_ptrs(COL_ADJ_B, (cplx<T> *)s->L, B(), A(), nullptr, n_step); }
+
+    // part B of step n, then part A of step n - 1 (phi_n, prod_{n-1}, noise step n - 1)
+    int adjoint_part_ba(const cplx<T> *phi_n, const cplx<T> *prod_prev, long long n_step) {
+        return col_ptrs(COL_ADJ_BA, (cplx<T> *)s->L, B(), A(), phi_n, n_step - 1, nullptr, prod_prev);
+    }
+
+    int adjoint_x_part(const T *real_r) {
         int rc;
-        cplx<T> *Lb = (cplx<T> *)s->L;
-        // mu = g lambda, gradients, nu = dt M mu back along the slowest axis -> A
-        if ((rc = col_ptrs(COL_ADJ_A, Lb, prod, A(), phi_n1, n_step))) return rc;
-        // w = p r^(p-1) N F^-1[nu] in real space, then its x(y) transform -> B
         if (s->dim == 3) {
             if ((rc = mid(MID_INV_FULL, true, false))) return rc;                            // A -> B
             if ((rc = row_ptrs(ROW_ADJ, B(), A(), false, real_r, nullptr, 0))) return rc;     // B -> A
@@ -713,8 +734,14 @@ template <typename T> struct Seq {
         } else {
             if ((rc = row_ptrs(ROW_ADJ, A(), B(), false, real_r, nullptr, 0))) return rc;     // A -> B
         }
-        // lambda_n = mu + m F[w] / N
-        return col_ptrs(COL_ADJ_B, Lb, B(), A(), nullptr, n_step);
+        return PSS_OK;
+    }
+
+    int adjoint_step(const cplx<T> *phi_n1, const cplx<T> *prod, const T *real_r, long long n_step) {
+        int rc;
+        if ((rc = adjoint_part_a(phi_n1, prod, n_step))) return rc;
+        if ((rc = adjoint_x_part(real_r))) return rc;
+        return adjoint_part_b(n_step);
     }
 };
 
@@ -1011,9 +1038,18 @@ template <typename T> int record_adjoint_segment(pss_system *s, cudaStream_t str
     if (rc) return rc;
     for (int64_t i = 0; i < len; ++i)
         if ((rc = q.recompute_step(st(i), st(i + 1), prod(i), prod(i + 1), real(i + 1)))) return rc;
-    for (int64_t i = len - 1; i >= 0; --i)
-        if ((rc = q.adjoint_step(st(i + 1), prod(i), real(i), i))) return rc;
-    return PSS_OK;
+    if (len < 1 || !q.fused_adjoint()) {
+        for (int64_t i = len - 1; i >= 0; --i)
+            if ((rc = q.adjoint_step(st(i + 1), prod(i), real(i), i))) return rc;
+        return PSS_OK;
+    }
+    if ((rc = q.adjoint_part_a(st(len), prod(len - 1), len - 1))) return rc;
+    for (int64_t i = len - 1; i >= 1; --i) {
+        if ((rc = q.adjoint_x_part(real(i)))) return rc;
+        if ((rc = q.adjoint_part_ba(st(i), prod(i - 1), i))) return rc;
+    }
+    if ((rc = q.adjoint_x_part(real(0)))) return rc;
+    return q.adjoint_part_b(0);
 }
 
 template <typename T> int adjoint_backward_t(pss_system *s) {
@@ -1410,6 +1446,7 @@ int pss_set_tuning(pss_system *s, const char *key, int value) {
     else if (k == "graph_steps") s->tune_graph_steps = value;
     else if (k == "fast2d") s->tune_fast2d = value ? 1 : 0;
     else if (k == "fast3d") s->tune_fast3d = value ? 1 : 0;
+    else if (k == "fuse_adjoint") s->tune_fuse_adj = value ? 1 : 0;
     else if (k == "col2_warps") {
         if (value > 24) return fail(s, PSS_EINVAL, "col2_warps is at most 24 (0 = automatic)");
         s->tune_col2_warps = value;

@@ -68,7 +68,8 @@ template <typename T> struct SysP {
 enum ColMode {
     COL_STEP = 0, COL_FWD = 1, COL_INV_MASK = 2, COL_INV_FULL = 3,
     COL_ADJ_A = 4,   // adjoint: mu = g lambda, coefficient gradients, inverse of nu = dt M mu (all columns)
-    COL_ADJ_B = 5    // adjoint: lambda = mu + m F[w] / N
+    COL_ADJ_B = 5,   // adjoint: lambda = mu + m F[w] / N
+    COL_ADJ_BA = 6   // adjoint: COL_ADJ_B of one step, then COL_ADJ_A of the step before it
 };
 enum RowMode {
     ROW_FUSED = 0,      // C2R of the kept columns, power p, R2C (real_out: also store the real field)
@@ -106,6 +107,10 @@ template <typename T> struct ColArgs {
     int in_colmajor;      // k_col: `in` holds each tile's columns one after another ([c][pos]), as the
                           // FP32 2D path writes its product (the adjoint reads it)
     const cplx<T> *noise; // k2_col: unit-amplitude noise of this step (tiled like the state)
+    // COL_ADJ_BA: the product of the earlier step (the A part's input; `in` is the
+    // B part's), column-major like `in_colmajor` says
+    const cplx<T> *in2;
+    int in2_colmajor;
 };
 
 template <typename T> struct RowArgs {
@@ -154,6 +159,11 @@ template <typename T, int EMAX>
 cudaError_t launch_col_e(const ColArgs<T> &a, int nslots, int grid_x, int grid_y, cudaStream_t st);
 template <typename T, int EMAX> cudaError_t launch_row_e(const RowArgs<T> &a, int nslots, cudaStream_t st);
 template <typename T, int EMAX> cudaError_t launch_mid_e(const MidArgs<T> &a, int nslots, int n_tiles, cudaStream_t st);
+// dynamic shared memory of one column-kernel CTA (0: side not supported)
+template <typename T, int EMAX> size_t col_smem_bytes_e(int n_inner, int F, int mode);
+template <typename T> inline size_t col_smem_bytes(int n_inner, int F, int E, int mode) {
+    return E == 16 ? col_smem_bytes_e<T, 16>(n_inner, F, mode) : col_smem_bytes_e<T, 8>(n_inner, F, mode);
+}
 template <typename T>
 inline cudaError_t launch_col(const ColArgs<T> &a, int nslots, int grid_x, int grid_y, cudaStream_t st) {
     return a.E == 16 ? launch_col_e<T, 16>(a, nslots, grid_x, grid_y, st) : launch_col_e<T, 8>(a, nslots, grid_x, grid_y, st);

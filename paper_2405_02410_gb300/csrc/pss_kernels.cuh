@@ -138,112 +138,54 @@ __device__ __forceinline__ cplx<T> update_mode(cplx<T> phi, cplx<T> P, cplx<T> x
 //       this axis (all columns, unscaled) -> out.
 //   COL_ADJ_B: PHI = mu, P = F[w]: lambda = mu + m F[w] / N (stored back),
 //       Hermitian part on the kx = 0, Nx/2 planes.
+//   COL_ADJ_BA: the B part of step n, then the A part of step n - 1 on the
+//       lambda_n it left in PHI, with P = the forward transform of Z (the
+//       product of step n - 1, staged beside X): lambda_n never goes through
+//       global memory, and only mu_{n-1} is stored.
 // Inner products run over the full Hermitian set: weight 2 for 0 < kx < Nx/2.
 // ---------------------------------------------------------------------------
 template <typename T, int N, int EMAX>
 __device__ __forceinline__ void col_adjoint(const ColArgs<T> &a, const FieldP<T> &fp, cplx<T> *PHI, const cplx<T> *P,
-                                            cplx<T> *X, cplx<T> *Y, int which, int F, int SF, int nchunks,
-                                            int lognch, int first_tile, int op, int opp, int logNP, size_t sofs,
-                                            int ch, int c, int f, int lane, bool active,
+                                            cplx<T> *X, cplx<T> *Y, const cplx<T> *Z, int which, int F, int SF,
+                                            int nchunks, int lognch, int first_tile, int op, int opp, int logNP,
+                                            size_t sofs, int ch, int c, int f, int lane, bool active,
                                             const cplx<T> *__restrict__ tw) {
     using C = cplx<T>;
     constexpr int CS = N * W + 8;
     const SysP<T> &sp = a.sp;
     const int t = threadIdx.x, nthr = blockDim.x;
-    const bool mode_a = a.mode == COL_ADJ_A;
+    const bool do_b = a.mode != COL_ADJ_A, do_a = a.mode != COL_ADJ_B;
     auto chunk_tile = [&](int q) { return first_tile + (q >> logNP); };
     auto chunk_o = [&](int q) { return (q & logNP) ? opp : op; };
     auto chunk_writes = [&](int q) { return chunk_tile(q) < a.n_tiles && !((q & logNP) && opp == op); };
     auto gofs = [&](int q) { return ((size_t)(chunk_tile(q) * sp.n_outer + chunk_o(q)) * N) * W; };
-    // ADJ_A writes nu into the work buffer that does not hold P
-    C *NU = which == 0 ? X : Y;
-    // a thread's partial sums over its few modes are in the working precision;
-    // the sums over threads, CTAs and time steps are FP64
-    using Acc = T;
-    Acc acc[11];
-#pragma unroll
-    for (int i = 0; i < 11; ++i) acc[i] = Acc(0);
-    const uint32_t step = (uint32_t)(a.adj_step + (a.d_adj_base ? *a.d_adj_base : 0));
-    const PhiloxKey key = philox_key(fp.seed_lo, fp.seed_hi);
-    // one iteration per pair of neighbouring columns at one position: a single
-    // Philox draw serves both modes of the pair
     const int logF = __ffs(F) - 1;
+
+    if (do_b) {
+        // lambda = mu + m F[w] / N on the kept modes
 #pragma unroll 1
-    for (int j = t; j < (N * F) >> 1; j += nthr) {
-        const int pos = j >> (logF - 1), ff0 = (j & ((F >> 1) - 1)) << 1;
-        const int chq = ff0 >> 2, cc0 = ff0 & 3;
-        const int tile = chunk_tile(chq);
-        const int kx0 = tile * W + cc0;
-        const int o = chunk_o(chq);
-        const int ky = sp.dim == 3 ? o : (sp.dim == 2 ? pos : 0);
-        const int kz = sp.dim == 3 ? pos : 0;
-        const T qy = T(signed_k(ky, sp.ny)) * sp.gy, qz = T(signed_k(kz, sp.nz)) * sp.gz;
-        C xin[2] = {mk<T>(0, 0), mk<T>(0, 0)};
-        if (mode_a && fp.noisy && tile < a.n_tiles && kx0 < sp.hx && chunk_writes(chq)) {
-            const T qe = T(kx0) * sp.gx, qo = T(kx0 + 1) * sp.gx;
-            const T q2e = qe * qe + qy * qy + qz * qz, q2o = qo * qo + qy * qy + qz * qz;
-            noise_pair<T>(kx0 == 0 || 2 * kx0 == sp.nx, kx0, ky, kz, noise_amp<T>(fp.sigma0, fp.noise_pow, q2e),
-                          noise_amp<T>(fp.sigma0, fp.noise_pow, q2o), kx0 + 1 < sp.hx, sp, (uint32_t)fp.field_id, key,
-                          step, xin[0], xin[1]);
-        }
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-            const int ff = ff0 + u, cc = cc0 + u, kx = kx0 + u;
+        for (int i = t; i < N * F; i += nthr) {
+            const int pos = i >> logF, ff = i & (F - 1);
+            const int chq = ff >> 2, cc = ff & 3;
+            const int tile = chunk_tile(chq), kx = tile * W + cc;
+            const int o = chunk_o(chq);
+            const int ky = sp.dim == 3 ? o : (sp.dim == 2 ? pos : 0);
+            const int kz = sp.dim == 3 ? pos : 0;
             const bool valid = tile < a.n_tiles && kx < sp.hx;
-            const T qx = T(kx) * sp.gx;
-            const T q2 = qx * qx + qy * qy + qz * qz;
+            const bool keep = valid && kx <= fp.kmax[0] && abs(signed_k(ky, sp.ny)) <= fp.kmax[1] &&
+                              abs(signed_k(kz, sp.nz)) <= fp.kmax[2];
             C *ph = &PHI[chq * CS + pos * W + cc];
             const C pv = P[ff * SF + spad(pos)];
-            if (mode_a) {
-                const T g = T(1) / (T(1) + sp.dt * poly5<T>(fp.O, q2));
-                const C mu = valid ? cscale<T>(*ph, g) : mk<T>(0, 0);
-                *ph = mu;
-                const T dtM = fp.power > 0 ? sp.dt * poly5<T>(fp.M, q2) : T(0);
-                NU[ff * SF + spad(pos)] = cscale<T>(mu, dtM);
-                // the duplicate pencil of a self-paired 3D CTA does not count twice
-                if (valid && chunk_writes(chq)) {
-                    const Acc wgt = (kx == 0 || 2 * kx == sp.nx) ? Acc(1) : Acc(2);
-                    const C phin = a.aux[sofs + gofs(chq) + pos * W + cc];
-                    const Acc a_phi = wgt * sp.dt * (mu.x * phin.x + mu.y * phin.y);
-                    const Acc a_P = wgt * sp.dt * (mu.x * pv.x + mu.y * pv.y);
-                    Acc q2k = Acc(1);
-    #pragma unroll
-                    for (int k = 0; k < 5; ++k) {
-                        acc[k] -= q2k * a_phi;
-                        acc[5 + k] += q2k * a_P;
-                        q2k *= q2;
-                    }
-                    if (fp.noisy) acc[10] += wgt * (mu.x * xin[u].x + mu.y * xin[u].y);
-                }
-            } else {
-                bool keep = valid && kx <= fp.kmax[0] && abs(signed_k(ky, sp.ny)) <= fp.kmax[1] &&
-                            abs(signed_k(kz, sp.nz)) <= fp.kmax[2];
-                const C mu = *ph;
-                *ph = keep ? mk<T>(mu.x + pv.x * sp.inv_nsites, mu.y + pv.y * sp.inv_nsites) : (valid ? mu : mk<T>(0, 0));
-            }
-        }
-    }
-    __syncthreads();
-    if (mode_a) {
-        // CTA reduction of the gradient sums, one FP64 atomic per value
-        __shared__ double red[11];
-        if (t < 11) red[t] = 0.0;
-        __syncthreads();
-#pragma unroll
-        for (int k = 0; k < 11; ++k) {
-            double v = (double)acc[k];
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if ((t & 31) == 0 && v != 0.0) atomicAdd(&red[k], v);
+            const C mu = *ph;
+            *ph = keep ? mk<T>(mu.x + pv.x * sp.inv_nsites, mu.y + pv.y * sp.inv_nsites) : (valid ? mu : mk<T>(0, 0));
         }
         __syncthreads();
-        if (t < 11 && red[t] != 0.0) atomicAdd(&a.grad[(size_t)(a.slot0 + blockIdx.z) * 11 + t], red[t]);
-    } else {
         // Hermitian part of lambda on the kx = 0, Nx/2 planes
         const int last_tile = first_tile + a.tiles_per_cta;
         if (first_tile == 0 || (first_tile * W <= sp.nx / 2 && sp.nx / 2 < last_tile * W)) {
 #pragma unroll 1
             for (int i = t; i < N * F; i += nthr) {
-                const int pos = i >> (__ffs(F) - 1), ff = i & (F - 1);
+                const int pos = i >> logF, ff = i & (F - 1);
                 const int cq = ff >> 2, cc = ff & 3;
                 const int kq = chunk_tile(cq) * W + cc;
                 if (!(kq == 0 || 2 * kq == sp.nx) || (cq & logNP) != 0) continue;
@@ -258,6 +200,92 @@ __device__ __forceinline__ void col_adjoint(const ColArgs<T> &a, const FieldP<T>
             }
             __syncthreads();
         }
+        if (a.mode == COL_ADJ_BA) {
+            // the A part's P: forward transform of the earlier step's product
+            const int zstride = a.in2_colmajor ? 1 : W;
+            const C *zb = Z + ch * CS + (a.in2_colmajor ? c * N : c);
+            which = fft_run<T, N, EMAX, -1>([&](int p) { return zb[p * zstride]; },
+                                            [&](int p, C v, C *fr) { fr[spad(p)] = v; },
+                                            Y + f * SF, X + f * SF, lane, active, tw);
+            __syncthreads();
+            P = which == 0 ? Y : X;
+        }
+    }
+
+    // A part: nu goes into the work buffer that does not hold P
+    C *NU = which == 0 ? X : Y;
+    // a thread's partial sums over its few modes are in the working precision;
+    // the sums over threads, CTAs and time steps are FP64
+    using Acc = T;
+    Acc acc[11];
+#pragma unroll
+    for (int i = 0; i < 11; ++i) acc[i] = Acc(0);
+    if (do_a) {
+        const uint32_t step = (uint32_t)(a.adj_step + (a.d_adj_base ? *a.d_adj_base : 0));
+        const PhiloxKey key = philox_key(fp.seed_lo, fp.seed_hi);
+        // one iteration per pair of neighbouring columns at one position: a single
+        // Philox draw serves both modes of the pair
+#pragma unroll 1
+        for (int j = t; j < (N * F) >> 1; j += nthr) {
+            const int pos = j >> (logF - 1), ff0 = (j & ((F >> 1) - 1)) << 1;
+            const int chq = ff0 >> 2, cc0 = ff0 & 3;
+            const int tile = chunk_tile(chq);
+            const int kx0 = tile * W + cc0;
+            const int o = chunk_o(chq);
+            const int ky = sp.dim == 3 ? o : (sp.dim == 2 ? pos : 0);
+            const int kz = sp.dim == 3 ? pos : 0;
+            const T qy = T(signed_k(ky, sp.ny)) * sp.gy, qz = T(signed_k(kz, sp.nz)) * sp.gz;
+            C xin[2] = {mk<T>(0, 0), mk<T>(0, 0)};
+            if (fp.noisy && tile < a.n_tiles && kx0 < sp.hx && chunk_writes(chq)) {
+                const T qe = T(kx0) * sp.gx, qo = T(kx0 + 1) * sp.gx;
+                const T q2e = qe * qe + qy * qy + qz * qz, q2o = qo * qo + qy * qy + qz * qz;
+                noise_pair<T>(kx0 == 0 || 2 * kx0 == sp.nx, kx0, ky, kz, noise_amp<T>(fp.sigma0, fp.noise_pow, q2e),
+                              noise_amp<T>(fp.sigma0, fp.noise_pow, q2o), kx0 + 1 < sp.hx, sp, (uint32_t)fp.field_id,
+                              key, step, xin[0], xin[1]);
+            }
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int ff = ff0 + u, cc = cc0 + u, kx = kx0 + u;
+                const bool valid = tile < a.n_tiles && kx < sp.hx;
+                const T qx = T(kx) * sp.gx;
+                const T q2 = qx * qx + qy * qy + qz * qz;
+                C *ph = &PHI[chq * CS + pos * W + cc];
+                const C pv = P[ff * SF + spad(pos)];
+                const T g = T(1) / (T(1) + sp.dt * poly5<T>(fp.O, q2));
+                const C mu = valid ? cscale<T>(*ph, g) : mk<T>(0, 0);
+                *ph = mu;
+                const T dtM = fp.power > 0 ? sp.dt * poly5<T>(fp.M, q2) : T(0);
+                NU[ff * SF + spad(pos)] = cscale<T>(mu, dtM);
+                // the duplicate pencil of a self-paired 3D CTA does not count twice
+                if (valid && chunk_writes(chq)) {
+                    const Acc wgt = (kx == 0 || 2 * kx == sp.nx) ? Acc(1) : Acc(2);
+                    const C phin = a.aux[sofs + gofs(chq) + pos * W + cc];
+                    const Acc a_phi = wgt * sp.dt * (mu.x * phin.x + mu.y * phin.y);
+                    const Acc a_P = wgt * sp.dt * (mu.x * pv.x + mu.y * pv.y);
+                    Acc q2k = Acc(1);
+#pragma unroll
+                    for (int k = 0; k < 5; ++k) {
+                        acc[k] -= q2k * a_phi;
+                        acc[5 + k] += q2k * a_P;
+                        q2k *= q2;
+                    }
+                    if (fp.noisy) acc[10] += wgt * (mu.x * xin[u].x + mu.y * xin[u].y);
+                }
+            }
+        }
+        __syncthreads();
+        // CTA reduction of the gradient sums, one FP64 atomic per value
+        __shared__ double red[11];
+        if (t < 11) red[t] = 0.0;
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < 11; ++k) {
+            double v = (double)acc[k];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if ((t & 31) == 0 && v != 0.0) atomicAdd(&red[k], v);
+        }
+        __syncthreads();
+        if (t < 11 && red[t] != 0.0) atomicAdd(&a.grad[(size_t)(a.slot0 + blockIdx.z) * 11 + t], red[t]);
     }
     // store PHI (mu or lambda) back with one bulk copy per chunk
     fence_proxy_async();
@@ -268,7 +296,7 @@ __device__ __forceinline__ void col_adjoint(const ColArgs<T> &a, const FieldP<T>
             if (chunk_writes(q)) bulk_s2g(a.state + sofs + gofs(q), PHI + q * CS, chunk_bytes);
         bulk_commit();
     }
-    if (mode_a) {
+    if (do_a) {
         // nu back along this axis (all columns), stored straight from the last pass
         C *__restrict__ dst = a.out + sofs + gofs(ch) + c;
         const bool writes = chunk_writes(ch);
@@ -292,6 +320,8 @@ template <typename T, int N> struct ColSmem {
     __host__ __device__ static size_t bytes(int F) {
         return 128 + sizeof(cplx<T>) * ((size_t)twiddle_elems<N>() + (size_t)(F / W) * CS + 2 * (size_t)xs(F));
     }
+    // the adjoint instantiation also stages COL_ADJ_BA's second product (Z, after Y)
+    __host__ __device__ static size_t bytes_adj(int F) { return bytes(F) + sizeof(cplx<T>) * (size_t)(F / W) * CS; }
 };
 
 template <typename T, int N, int EMAX, bool ADJ>
@@ -311,6 +341,7 @@ __global__ void __launch_bounds__(512, (N >= 512 || ADJ) ? 1 : 2) k_col(const Co
     C *PHI = TW + twiddle_elems<N>();
     C *X = PHI + nchunks * CS;
     C *Y = X + L::xs(F);
+    C *Z = Y + L::xs(F);                                          // COL_ADJ_BA only
     const SysP<T> &sp = a.sp;
     const int slot = a.slot0 + blockIdx.z;
     // the slot's parameters and the step number, fetched into shared memory
@@ -337,6 +368,7 @@ __global__ void __launch_bounds__(512, (N >= 512 || ADJ) ? 1 : 2) k_col(const Co
     constexpr bool adj = ADJ;   // the adjoint modes are a separate instantiation
     const bool need_in = mode == COL_STEP || mode == COL_FWD || adj;
     const bool need_phi = mode != COL_FWD;
+    const bool need_in2 = adj && mode == COL_ADJ_BA;
     const uint32_t chunk_bytes = (uint32_t)(N * W * sizeof(C));
     int nvalid = 0;                                              // chunks 0..nvalid-1 lie inside the grid
     for (int ch = 0; ch < nchunks; ++ch) nvalid += chunk_ok(ch) ? 1 : 0;
@@ -344,11 +376,13 @@ __global__ void __launch_bounds__(512, (N >= 512 || ADJ) ? 1 : 2) k_col(const Co
     pdl_trigger();
     if (t == 0) {
         mbar_init(bar, 1);
-        mbar_expect_tx(bar, chunk_bytes * nvalid * ((need_in ? 1 : 0) + (need_phi ? 1 : 0)) + twiddle_bytes<C, N>());
+        mbar_expect_tx(bar, chunk_bytes * nvalid * ((need_in ? 1 : 0) + (need_phi ? 1 : 0) + (need_in2 ? 1 : 0)) +
+                                twiddle_bytes<C, N>());
         if (twiddle_bytes<C, N>()) bulk_g2s(TW, a.tw + twiddle_offset(N, EMAX), twiddle_bytes<C, N>(), bar);
         for (int ch = 0; ch < nvalid; ++ch) {
             if (need_phi) bulk_g2s(PHI + ch * CS, a.state + sofs + gofs(ch), chunk_bytes, bar);
             if (need_in) bulk_g2s(X + ch * CS, a.in + sofs + gofs(ch), chunk_bytes, bar);
+            if (need_in2) bulk_g2s(Z + ch * CS, a.in2 + sofs + gofs(ch), chunk_bytes, bar);
         }
     }
     static_assert(sizeof(FieldP<T>) % 4 == 0, "FieldP is copied as 32-bit words");
@@ -360,6 +394,7 @@ __global__ void __launch_bounds__(512, (N >= 512 || ADJ) ? 1 : 2) k_col(const Co
         const int ch = i >> LOGNW, r = i & (N * W - 1);
         PHI[ch * CS + r] = mk<T>(0, 0);
         X[ch * CS + r] = mk<T>(0, 0);
+        if (need_in2) Z[ch * CS + r] = mk<T>(0, 0);
     }
     if (!mbar_wait_all(bar, 0, a.d_status)) return;
 
@@ -381,8 +416,8 @@ __global__ void __launch_bounds__(512, (N >= 512 || ADJ) ? 1 : 2) k_col(const Co
         __syncthreads();
         const C *P = which == 0 ? Y : X;
         if constexpr (ADJ) {
-            col_adjoint<T, N, EMAX>(a, fp, PHI, P, X, Y, which, F, SF, nchunks, lognch, first_tile, op, opp, logNP, sofs,
-                              ch, c, f, lane, active, tw);
+            col_adjoint<T, N, EMAX>(a, fp, PHI, P, X, Y, Z, which, F, SF, nchunks, lognch, first_tile, op, opp, logNP,
+                                    sofs, ch, c, f, lane, active, tw);
             return;
         }
         const uint32_t step = sstep;
@@ -904,10 +939,10 @@ template <class K> cudaError_t ensure_smem(K kernel, size_t smem) {
 template <typename T, int N, int EMAX>
 cudaError_t launch_col_n(const ColArgs<T> &a, int nf, int gx, int gy, cudaStream_t st) {
     const int threads = col_threads(N, EMAX, a.F);
-    const size_t smem = ColSmem<T, N>::bytes(a.F);
+    const bool adj = a.mode == COL_ADJ_A || a.mode == COL_ADJ_B || a.mode == COL_ADJ_BA;
+    const size_t smem = a.mode == COL_ADJ_BA ? ColSmem<T, N>::bytes_adj(a.F) : ColSmem<T, N>::bytes(a.F);
     if (a.F * FftShape<N, EMAX>::TPF > 512 || (a.F & (a.F - 1)) != 0 || a.F % W != 0)
         return cudaErrorInvalidConfiguration;
-    const bool adj = a.mode == COL_ADJ_A || a.mode == COL_ADJ_B;
     cudaError_t e = adj ? ensure_smem(k_col<T, N, EMAX, true>, smem) : ensure_smem(k_col<T, N, EMAX, false>, smem);
     if (e != cudaSuccess) return e;
     if (adj) return launch_pdl(k_col<T, N, EMAX, true>, dim3(gx, gy, nf), threads, smem, st, a);
@@ -928,6 +963,17 @@ cudaError_t launch_col_e(const ColArgs<T> &a, int nf, int gx, int gy, cudaStream
         case 512: return launch_col_n<T, 512, EMAX>(a, nf, gx, gy, st);
         case 1024: return launch_col_n<T, 1024, EMAX>(a, nf, gx, gy, st);
         default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename T, int EMAX> size_t col_smem_bytes_e(int n_inner, int F, int mode) {
+    const bool two = mode == COL_ADJ_BA;
+    switch (n_inner) {
+#define PSS_COL_SMEM(n) case n: return two ? ColSmem<T, n>::bytes_adj(F) : ColSmem<T, n>::bytes(F);
+        PSS_COL_SMEM(1) PSS_COL_SMEM(4) PSS_COL_SMEM(8) PSS_COL_SMEM(16) PSS_COL_SMEM(32) PSS_COL_SMEM(64)
+        PSS_COL_SMEM(128) PSS_COL_SMEM(256) PSS_COL_SMEM(512) PSS_COL_SMEM(1024)
+#undef PSS_COL_SMEM
+        default: return 0;
     }
 }
 
@@ -1029,6 +1075,7 @@ cudaError_t launch_structure_factor(const SysP<T> &sp, const double dx[3], const
 // the step kernels of one precision and FFT radix cap
 #define PSS_INSTANTIATE_STEP(T, EMAX)                                                                       \
     template cudaError_t launch_col_e<T, EMAX>(const ColArgs<T> &, int, int, int, cudaStream_t);           \
+    template size_t col_smem_bytes_e<T, EMAX>(int, int, int);                                              \
     template cudaError_t launch_row_e<T, EMAX>(const RowArgs<T> &, int, cudaStream_t);                     \
     template cudaError_t launch_mid_e<T, EMAX>(const MidArgs<T> &, int, int, cudaStream_t);
 

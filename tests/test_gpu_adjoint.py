@@ -169,3 +169,31 @@ def test_adjoint_on_the_fft_group_path(shape):
     # the two paths agree to FP32 rounding
     assert rel(runs[1][1], runs[0][1]) < 1e-4
     assert np.max(np.abs(runs[1][0] - runs[0][0]) / np.abs(runs[0][0])) < 1e-4
+
+
+@pytest.mark.parametrize("shape,prec", [((32, 32), "f64"), ((64,), "f64"), ((16, 16, 16), "f32"),
+                                        ((8, 16, 8), "f64"), ((256, 256), "f32"), ((1024, 16), "f64")])
+def test_fused_adjoint_launch_changes_no_field_bit(shape, prec):
+    # part B of one adjoint step and part A of the step before it in one launch
+    # (the default) or in two: the adjoint fields are the same bits, the FP64
+    # gradient sums the same up to the order of their atomic additions; 11 steps
+    # = segments of 4, 4 and 3
+    dt, seed, n = 0.02, 29, 11
+    m = O.model_b(shape, dt=dt, seed=seed, **PARAMS)
+    lamT = 2.0 * _weights(shape) * O.run(m, O.to_spectrum(m, O.init_uniform(m, -0.3, 0.3)), 0, n) / m.n_sites
+    out = {}
+    for fuse in (1, 0):
+        s = _gpu_system(shape, prec, dt, seed)
+        s.set_tuning("fuse_adjoint", fuse)
+        s.adjoint_forward(n)
+        l0 = s.launch_count
+        grads, lam0 = s.adjoint_backward(O.half(lamT), 4)
+        out[fuse] = (grads, lam0, s.launch_count - l0)
+    np.testing.assert_array_equal(out[1][1], out[0][1])
+    np.testing.assert_allclose(out[1][0], out[0][0], rtol=1e-12 if prec == "f64" else 1e-9)
+    # the fused launch fits in shared memory everywhere but the FP64 1024-point column
+    fits = not (prec == "f64" and shape[0] == 1024)
+    if fits:
+        assert out[1][2] < out[0][2], out
+    else:
+        assert out[1][2] == out[0][2], out
