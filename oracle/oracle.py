@@ -265,6 +265,23 @@ def run(m: Model, phi: np.ndarray, step0: int, nsteps: int) -> np.ndarray:
     return out
 
 
+def run_framed(m: Model, phi: np.ndarray, step0: int, nsteps: int, width: int, lo: float, hi: float) -> np.ndarray:
+    """``nsteps`` steps of Eq. timeupdate, each followed by a boundary frame
+    (section "Callback functions"): the real field at the end of the step takes
+    ``lo`` on the sites x < width and ``hi`` on the sites x >= Nx - width (every
+    y and z), and the spectrum is taken again from that real field.
+    ``width = 0`` is ``run``."""
+    out = np.array(phi, dtype=np.complex128, copy=True)
+    for k in range(nsteps):
+        out = run(m, out, step0 + k, 1)
+        if width > 0:
+            r = to_real(m, out)
+            r[..., :width] = lo
+            r[..., r.shape[-1] - width:] = hi
+            out = to_spectrum(m, r)
+    return out
+
+
 def init_uniform(m: Model, lo: float, hi: float) -> np.ndarray:
     s = m.c_struct()
     out = np.zeros(m.shape, dtype=np.float64)
