@@ -357,6 +357,57 @@ def oracle_all_cores(shape, budget_s=10.0):
     return sum(r[0] for r in rates), ncores, n
 
 
+def _timed_steps(torch, stream, s, n, warm=20):
+    with torch.cuda.stream(stream):
+        s.step(warm)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.step(n)
+        e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / n
+
+
+def variants_measurement(pss, torch, stream, ms_default_1024):
+    """The de-aliasing order rule of the paper for the cubic term (order 3:
+    keep (3+1)|k| < N per axis) at 1024^2 and for the 256^3 pair, and the
+    ablation that takes every field to real space and back at the end of each
+    step (the paper keeps both spaces; four transforms per step instead of two)."""
+    w = WORKLOAD
+    out = {}
+    s = pss.model_b((1024, 1024), dt=w["dt"], a=w["a"], b=w["b"], K=w["K"], D=w["D"], seed=w["seed"],
+                    precision="f32", dealias_order=3)
+    s.set_stream(stream)
+    s.init_uniform(0, w["lo"], w["hi"])
+    ms = _timed_steps(torch, stream, s, 2000)
+    out["order3_1024"] = {"ms_per_step": ms, "site_steps_per_s": 1024 ** 2 / (ms * 1e-3),
+                          "speedup_over_order2": ms_default_1024 / ms, "path": s.step_path}
+    s.close()
+    s = make_system(pss, (1024, 1024))
+    s.set_stream(stream)
+    s.set_tuning("real_state", 1)
+    s.init_uniform(0, w["lo"], w["hi"])
+    ms = _timed_steps(torch, stream, s, 500)
+    out["real_state_1024"] = {"ms_per_step": ms, "site_steps_per_s": 1024 ** 2 / (ms * 1e-3),
+                              "slowdown_over_spectral_state": ms / ms_default_1024}
+    s.close()
+    res = {}
+    for order in (2, 3):
+        s3 = pss.System((256, 256, 256), dt=0.005, seed=w["seed"], precision="f32")
+        pss.add_model_a_field(s3, a=-1, b=1, K=1, D=0.05, name="psi", dealias_order=order)
+        pss.add_model_b_field(s3, a=-1, b=1, K=1, D=0.05, name="phi", dealias_order=order)
+        s3.set_stream(stream)
+        s3.init_uniform(0, -0.05, 0.05)
+        s3.init_uniform(1, -0.05, 0.05)
+        res[order] = _timed_steps(torch, stream, s3, 100)
+        s3.close()
+    out["order3_256cubed_pair"] = {"ms_per_step_two_fields": res[3],
+                                   "site_steps_per_s_per_field": 256 ** 3 * 2 / (res[3] * 1e-3),
+                                   "speedup_over_order2": res[2] / res[3]}
+    return out
+
+
 def adjoint_measurement(pss, torch, stream, n=2000, shape=(256, 256), nbins=64):
     """The adjoint workload: 2D Model B 256^2, FP32, n steps with a fixed noise realisation and sqrt(n)
     checkpoints; loss = mean over the 64 S(q) bins of (S - S*)^2 with S* from (a, b, K) = (-0.8, 1.2, 0.9)."""
@@ -547,6 +598,8 @@ def run_gpu(args):
         extra["ensemble_512"] = ensemble_measurement(pss, torch, stream)
     if not args.no_adjoint:
         extra["adjoint_256"] = adjoint_measurement(pss, torch, stream)
+    if not args.no_variants:
+        extra["variants"] = variants_measurement(pss, torch, stream, ms_per_step)
     if not args.no_cufft:
         cf = cufft_comparison(torch, stream)
         cf["ours_over_cufft"] = value / cf["site_steps_per_s"]
@@ -604,6 +657,8 @@ def main(argv=None):
     ap.add_argument("--no-ensemble", action="store_true", help="skip the 512-instance ensemble measurement")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint measurement")
     ap.add_argument("--no-cufft", action="store_true", help="skip the cuFFT + torch comparison step")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the order-3 de-aliasing and real-space round-trip measurements")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

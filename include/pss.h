@@ -125,6 +125,17 @@ int pss_set_noise(pss_system *s, int field_id, int D_param_id, int q2_pow);
  * (the two-thirds rule); 0 keeps every mode. */
 int pss_set_dealias(pss_system *s, int field_id, int order);
 
+/* Boundary frame of field_id along x (section "Callback functions": a
+ * callback that sets the real field near the boundary at the end of every
+ * step).  At the end of every step the sites with x < width take lo_value
+ * and the sites with x >= Nx - width take hi_value (every y and z, every
+ * instance), and the field's spectrum is taken again from that real field.
+ * width = 0 removes the frame; 0 <= width <= Nx/2, values finite, else
+ * PSS_EINVAL.  While a field has a frame, every step of the system ends with
+ * each field taken to real space and back (four transforms per step instead
+ * of two), and the adjoint returns PSS_EUNSUPPORTED. */
+int pss_set_frame(pss_system *s, int field_id, int width, double lo_value, double hi_value);
+
 /* Copy a real field [nz][ny][nx] in (and transform it). */
 int pss_set_field(pss_system *s, int field_id, const void *real, int where);
 /* Set a real field to lo + (hi - lo) u, u = ((x >> 8) + 0.5) / 2^24 with x the
@@ -189,6 +200,10 @@ int pss_time_kernels(pss_system *s, int64_t n, double *avg_ms);
  *                 generic row kernel (0);
  *   "col2_radix", "row2_radix"
  *                 radix of that path's FFT passes (8 or 16);
+ *   "real_state"  every step ends with each field taken to real space and
+ *                 back, as with a boundary frame of width 0 (1; an ablation
+ *                 of keeping the state in Fourier space, 0, default); the
+ *                 two agree to rounding;
  *   "fuse_adjoint" the backward pass runs the last column part of one
  *                 adjoint step and the first of the step before it in one
  *                 launch (1, default, where its shared memory fits) or in

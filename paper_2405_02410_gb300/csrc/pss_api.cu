@@ -42,6 +42,8 @@ struct Field {
     int noise_param = -1;
     int noise_pow = 0;
     int dealias = 2;
+    int frame_w = 0;                   // boundary frame along x (0: none)
+    double frame_lo = 0, frame_hi = 0;
 };
 
 constexpr int kDefaultGraphSteps = 16;
@@ -90,6 +92,7 @@ struct pss_system {
     int tune_col2_warps = 0, tune_row2_pairs = 0;   // its noise warps per column CTA, row pairs per row CTA
     int tune_col2_radix = 0, tune_row2_radix = 0;   // its FFT pass radix (8 or 16; 0 = automatic)
     int tune_row2_noise = 0;                 // noise warps per row CTA of that path (0 = automatic)
+    int tune_real_state = 0;                 // every step ends in real space and comes back (ablation)
     int tune_fuse_adj = 1;                   // adjoint: one launch for part B of a step and part A of the one before
     int tune_row2_share = -1;                // % of the noise drawn by extra CTAs on idle SMs (-1 = automatic: 0)
     int num_sms = 0;
@@ -111,6 +114,7 @@ struct pss_system {
     int64_t adj_graph_launches = 0;
 
     int nslots() const { return batch * (int)fields.size(); }
+    int64_t graph_launches = 0;              // launches per step of the captured step graph
 };
 
 namespace {
@@ -764,10 +768,40 @@ int prologue(pss_system *s) {
     return PSS_OK;
 }
 
+// Every step ends in real space when a field has a boundary frame (section
+// "Callback functions": the frame is set on the real field at the end of a
+// step) or when the round trip is asked for as an ablation.
+bool round_trip(const pss_system *s) {
+    if (s->tune_real_state) return true;
+    for (const Field &f : s->fields)
+        if (f.frame_w > 0) return true;
+    return false;
+}
+
+template <typename T> int step_once(pss_system *s, cudaStream_t st) {
+    int rc = Seq<T>{s, st, 0, s->nslots()}.one_step();
+    if (rc || !round_trip(s)) return rc;
+    // per slot: the full real field, its frame, and back to the spectrum
+    const int nf = (int)s->fields.size();
+    for (int slot = 0; slot < s->nslots(); ++slot) {
+        Seq<T> q{s, st, slot, 1};
+        if ((rc = q.inverse_to_real())) return rc;
+        const Field &f = s->fields[slot % nf];
+        if (f.frame_w > 0) {
+            cudaError_t e = launch_frame<T>((T *)s->real, s->nx, (long long)s->ny * s->nz, f.frame_w, f.frame_lo,
+                                            f.frame_hi, st);
+            s->launches++;
+            if (e != cudaSuccess) return cuda_fail(s, e, "frame kernel");
+        }
+        if ((rc = q.forward_from_real())) return rc;
+    }
+    // the product (and on the FP32 2D path the noise) of the new state
+    return Seq<T>{s, st, 0, s->nslots()}.prologue();
+}
+
 int record_steps(pss_system *s, cudaStream_t st, int64_t n) {
     for (int64_t k = 0; k < n; ++k) {
-        int rc = s->prec == PSS_F64 ? Seq<double>{s, st, 0, s->nslots()}.one_step()
-                                    : Seq<float>{s, st, 0, s->nslots()}.one_step();
+        int rc = s->prec == PSS_F64 ? step_once<double>(s, st) : step_once<float>(s, st);
         if (rc) return rc;
     }
     return PSS_OK;
@@ -785,7 +819,10 @@ int capture_graph(pss_system **sys, int n, int steps, cudaGraphExec_t *out) {
             rc = record_steps(sys[i], s->cap_stream, 1);
             if (rc && i != 0) s->err = sys[i]->err;
         }
-    for (int i = 0; i < n; ++i) sys[i]->launches = before[i];
+    for (int i = 0; i < n; ++i) {
+        sys[i]->graph_launches = steps > 0 ? (sys[i]->launches - before[i]) / steps : 0;
+        sys[i]->launches = before[i];
+    }
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(s->cap_stream, &g);
     if (rc) { if (g) cudaGraphDestroy(g); return rc; }
@@ -806,10 +843,9 @@ int run_steps(pss_system *s, int64_t n) {
             if (rc) return rc;
             s->graph_valid = true;
         }
-        const int per_step = s->dim == 3 ? 4 : 2;
         while (n - done >= chunk) {
             CK(cudaGraphLaunch(s->graph, s->stream));
-            s->launches += (int64_t)chunk * per_step;
+            s->launches += (int64_t)chunk * s->graph_launches;
             done += chunk;
         }
     }
@@ -1271,6 +1307,19 @@ int pss_set_dealias(pss_system *s, int field_id, int order) {
     return PSS_OK;
 }
 
+int pss_set_frame(pss_system *s, int field_id, int width, double lo_value, double hi_value) {
+    int rc = check_field(s, field_id);
+    if (rc) return rc;
+    if (width < 0 || 2 * width > s->nx) return fail(s, PSS_EINVAL, "frame width must be in [0, Nx/2]");
+    if (!std::isfinite(lo_value) || !std::isfinite(hi_value)) return fail(s, PSS_EINVAL, "frame values must be finite");
+    Field &f = s->fields[field_id];
+    f.frame_w = width;
+    f.frame_lo = lo_value;
+    f.frame_hi = hi_value;
+    invalidate(s);
+    return PSS_OK;
+}
+
 int pss_set_field(pss_system *s, int field_id, const void *real, int where) {
     int rc = check_field(s, field_id);
     if (rc) return rc;
@@ -1302,6 +1351,7 @@ int pss_step(pss_system *s, int64_t n) {
     if (n == 0) return PSS_OK;
     int rc = upload_params(s);
     if (rc) return rc;
+    if (round_trip(s) && (rc = ensure_real(s))) return rc;
     if ((rc = prologue(s))) return rc;
     if ((rc = run_steps(s, n))) return rc;
     s->step += n;
@@ -1321,6 +1371,7 @@ int pss_step_many(pss_system **systems, int n, int64_t steps) {
             if (rc) return fail(s0, rc, "%s", s->err.c_str());
         }
         int rc = upload_params(s);
+        if (!rc && round_trip(s)) rc = ensure_real(s);
         if (!rc) rc = prologue(s);
         if (rc) return i == 0 ? rc : fail(s0, rc, "%s", s->err.c_str());
     }
@@ -1335,7 +1386,7 @@ int pss_step_many(pss_system **systems, int n, int64_t steps) {
         for (; steps - done >= chunk && e == cudaSuccess; done += chunk) e = cudaGraphLaunch(ge, s0->stream);
         cudaGraphExecDestroy(ge);
         if (e != cudaSuccess) return cuda_fail(s0, e, "cudaGraphLaunch");
-        for (int i = 0; i < n; ++i) systems[i]->launches += done * (systems[i]->dim == 3 ? 4 : 2);
+        for (int i = 0; i < n; ++i) systems[i]->launches += done * systems[i]->graph_launches;
     }
     for (; done < steps; ++done)
         for (int i = 0; i < n; ++i) {
@@ -1350,6 +1401,7 @@ int pss_adjoint_forward(pss_system *s, int64_t n) {
     if (!s) return PSS_EINVAL;
     if (n < 1) return fail(s, PSS_EINVAL, "n must be >= 1");
     if (s->nslots() != 1) return fail(s, PSS_EUNSUPPORTED, "the adjoint needs one field and batch 1 in this build");
+    if (round_trip(s)) return fail(s, PSS_EUNSUPPORTED, "the adjoint has no boundary frames or real-space round trip");
     int64_t K = (int64_t)std::ceil(std::sqrt((double)n));
     const int64_t nck = (n + K - 1) / K;
     int rc = adj_alloc(s, nck, K);
@@ -1447,6 +1499,7 @@ int pss_set_tuning(pss_system *s, const char *key, int value) {
     else if (k == "fast2d") s->tune_fast2d = value ? 1 : 0;
     else if (k == "fast3d") s->tune_fast3d = value ? 1 : 0;
     else if (k == "fuse_adjoint") s->tune_fuse_adj = value ? 1 : 0;
+    else if (k == "real_state") s->tune_real_state = value ? 1 : 0;
     else if (k == "col2_warps") {
         if (value > 24) return fail(s, PSS_EINVAL, "col2_warps is at most 24 (0 = automatic)");
         s->tune_col2_warps = value;

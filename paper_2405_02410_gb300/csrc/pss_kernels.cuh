@@ -820,6 +820,18 @@ __global__ void k_init_uniform(T *real, long long nsites, T lo, T hi, uint32_t s
     }
 }
 
+// Boundary frame along x of a real field [rows][nx]: x < w takes lo, x >= nx - w takes hi.
+template <typename T> __global__ void k_frame(T *real, int nx, long long rows, int w, T lo, T hi) {
+    const long long n = rows * (2LL * w);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long r = i / (2 * w);
+        const int j = (int)(i - r * (2 * w));
+        const int x = j < w ? j : nx - 2 * w + j;
+        real[r * nx + x] = j < w ? lo : hi;
+    }
+}
+
 template <typename T>
 __global__ void k_tiles_half(SysP<T> sp, cplx<T> *tiles, cplx<T> *half, int to_half) {
     const long long n = (long long)sp.nz * sp.ny * sp.hx;
@@ -1042,6 +1054,16 @@ cudaError_t launch_init_uniform(T *real, long long nsites, double lo, double hi,
 }
 
 template <typename T>
+cudaError_t launch_frame(T *real, int nx, long long rows, int width, double lo, double hi, cudaStream_t st) {
+    if (width < 1 || 2 * width > nx) return cudaErrorInvalidValue;
+    const long long n = rows * 2LL * width;
+    long long blocks = (n + 255) / 256;
+    if (blocks > 65535) blocks = 65535;
+    k_frame<T><<<(int)blocks, 256, 0, st>>>(real, nx, rows, width, T(lo), T(hi));
+    return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_tiles_to_half(const SysP<T> &sp, const cplx<T> *tiles, cplx<T> *half, cudaStream_t st) {
     const long long n = (long long)sp.nz * sp.ny * sp.hx;
     long long blocks = (n + 255) / 256;
@@ -1083,6 +1105,7 @@ cudaError_t launch_structure_factor(const SysP<T> &sp, const double dx[3], const
 #define PSS_INSTANTIATE_AUX(T)                                                                               \
     template cudaError_t launch_init_uniform<T>(T *, long long, double, double, uint64_t, int, cudaStream_t); \
     template cudaError_t launch_tiles_to_half<T>(const SysP<T> &, const cplx<T> *, cplx<T> *, cudaStream_t); \
+    template cudaError_t launch_frame<T>(T *, int, long long, int, double, double, cudaStream_t);              \
     template cudaError_t launch_half_to_tiles<T>(const SysP<T> &, const cplx<T> *, cplx<T> *, cudaStream_t); \
     template cudaError_t launch_segment_begin<T>(cplx<T> *, const cplx<T> *, size_t, const long long *, long long, \
                                                  long long, long long *, long long *, cudaStream_t);             \

@@ -29,7 +29,7 @@ EXPORTS = [
     "pss_set_spectrum", "pss_structure_factor", "pss_sync", "pss_last_error", "pss_launch_count",
     "pss_time_kernels", "pss_set_tuning", "pss_create_batch", "pss_batch_size", "pss_select_instance",
     "pss_set_param_batch", "pss_step_many", "pss_adjoint_forward", "pss_adjoint_backward",
-    "pss_structure_factor_noalloc", "pss_step_path",
+    "pss_structure_factor_noalloc", "pss_step_path", "pss_set_frame",
 ]
 
 
@@ -56,6 +56,7 @@ def _load():
         "pss_add_term": ([vp, i32, i32, i32, P(i32), P(d), P(i32), i32, P(i32), P(i32)], i32),
         "pss_set_noise": ([vp, i32, i32, i32], i32),
         "pss_set_dealias": ([vp, i32, i32], i32),
+        "pss_set_frame": ([vp, i32, i32, d, d], i32),
         "pss_set_field": ([vp, i32, vp, i32], i32),
         "pss_init_uniform": ([vp, i32, d, d], i32),
         "pss_step": ([vp, i64], i32),
@@ -190,6 +191,10 @@ class System:
 
     def set_dealias(self, field: int, order: int):
         self._ck(lib.pss_set_dealias(self._h, field, order))
+
+    def set_frame(self, field: int, width: int, lo: float, hi: float):
+        """Boundary frame along x: after every step x < width takes lo and x >= Nx - width takes hi."""
+        self._ck(lib.pss_set_frame(self._h, field, width, float(lo), float(hi)))
 
     # -- data ----------------------------------------------------------------
     def set_field(self, field: int, data):
