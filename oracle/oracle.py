@@ -64,6 +64,7 @@ class _Field(ctypes.Structure):
         ("noise_pow", ctypes.c_int),
         ("dealias_order", ctypes.c_int),
         ("transform", ctypes.c_int),
+        ("grad2", ctypes.c_int),
     ]
 
 
@@ -118,6 +119,7 @@ class Model:
     field_id: int = 0
     dx: Sequence[float] = (1.0, 1.0, 1.0)     # (dx, dy, dz)
     transform: int = 0
+    grad2: bool = False                       # product |grad(m phi)|^2 (KPZ) instead of (m phi)^power
 
     @property
     def dim(self) -> int:
@@ -152,6 +154,7 @@ class Model:
         s.noise_pow = int(self.noise_pow)
         s.dealias_order = int(self.dealias_order)
         s.transform = int(self.transform)
+        s.grad2 = int(bool(self.grad2))
         return s
 
 
@@ -161,6 +164,16 @@ def model_b(shape, dt=0.01, a=-1.0, b=1.0, K=1.0, D=0.01, noisy=True, seed=2405,
     conserved noise D q^2."""
     return Model(shape=shape, dt=dt, lhs=[(a, 1), (K, 2)], rhs=[(-b, 1)], power=3,
                  noise_D=D, noise_pow=1, noisy=noisy, dealias_order=dealias_order,
+                 seed=seed, field_id=field_id, dx=dx)
+
+
+def kpz(shape, dt=0.01, sigma=1.0, lam=1.0, D=0.01, noisy=True, seed=2405, dealias_order=2, field_id=0,
+        dx=(1.0, 1.0, 1.0)) -> Model:
+    """KPZ (section "Writing models"): dt phi = sigma lap phi + lambda (grad phi)^2 + noise, i.e.
+    dt phi + sigma q^2 phi = lambda F[|grad(m phi)|^2], non-conserved noise D (the quadratic
+    term takes the two-thirds rule, order 2)."""
+    return Model(shape=shape, dt=dt, lhs=[(sigma, 1)], rhs=[(lam, 0)], power=2, grad2=True,
+                 noise_D=D, noise_pow=0, noisy=noisy, dealias_order=dealias_order,
                  seed=seed, field_id=field_id, dx=dx)
 
 

@@ -243,12 +243,53 @@ static double poly_q2(int nm, const double *coef, const int *pw, double q2)
 /* ------------------------------------------------------------------------ */
 /* Step pieces                                                              */
 /* ------------------------------------------------------------------------ */
+/* q_j of unsigned index k on axis j for an odd (first-derivative) operator:
+ * the Nyquist index of an even axis has q_j = 0 */
+static double q_axis(const orc_field *f, int j, int k, int n)
+{
+    if (n % 2 == 0 && k == n / 2) return 0.0;
+    return 2.0 * M_PI * (double)signed_k(k, n) / ((double)n * f->dx[j]);
+}
+
+/* |grad(m phi)|^2 in real space, back to Fourier space (section "Writing
+ * models", the KPZ example: the nonlinearity lambda psi^2 with psi = grad phi) */
+static int nonlinear_grad2(const orc_field *f, const double *phi, double *P)
+{
+    int N[3];
+    dims(f, N);
+    long ns = n_sites(f);
+    int method = transform_method(f);
+    double *D = malloc(sizeof(double) * (size_t)(2 * ns));
+    if (!D) return -2;
+    for (long i = 0; i < 2 * ns; ++i) P[i] = 0.0;
+    for (int j = 0; j < f->dim; ++j) {
+        /* psi_j = F^-1[i q_j m phi] */
+        for (int kz = 0; kz < N[2]; ++kz)
+            for (int ky = 0; ky < N[1]; ++ky)
+                for (int kx = 0; kx < N[0]; ++kx) {
+                    long i = ((long)kz * N[1] + ky) * N[0] + kx;
+                    int k[3] = {kx, ky, kz};
+                    double q = orc_mask(f, kx, ky, kz) ? q_axis(f, j, k[j], N[j]) : 0.0;
+                    D[2 * i] = -q * phi[2 * i + 1];
+                    D[2 * i + 1] = q * phi[2 * i];
+                }
+        if (orc_dft(f->dim, f->n, D, +1, method)) { free(D); return -1; }
+        for (long i = 0; i < ns; ++i) {
+            double r = D[2 * i] / (double)ns;
+            P[2 * i] += r * r;
+        }
+    }
+    free(D);
+    return orc_dft(f->dim, f->n, P, -1, method);
+}
+
 int orc_nonlinear(const orc_field *f, const double *phi, double *P)
 {
     int N[3];
     dims(f, N);
     long ns = n_sites(f);
     int method = transform_method(f);
+    if (f->grad2) return nonlinear_grad2(f, phi, P);
     /* step 2: de-alias, d = m phi */
     for (int kz = 0; kz < N[2]; ++kz)
         for (int ky = 0; ky < N[1]; ++ky)
@@ -462,6 +503,7 @@ int orc_structure_factor(const orc_field *f, const double *phi, int nbins,
 int orc_adjoint(const orc_field *f, const double *phi0, int64_t step0, int64_t nsteps, double *lambda,
                 double *grad)
 {
+    if (f->grad2) return -3;   /* the adjoint covers power products only */
     int N[3];
     dims(f, N);
     long ns = n_sites(f);

@@ -46,6 +46,9 @@ typedef struct {
     int noise_pow;
     int dealias_order;      /* n_d: keep iff (n_d+1)|k_j| < N_j on every axis; 0 keeps all */
     int transform;          /* 0: auto (naive DFT for N_sites <= 256), 1: naive DFT, 2: radix-2 FFT */
+    int grad2;              /* 1: the product is |grad(m phi)|^2 = sum_j (F^-1[i q_j m phi])^2 (the KPZ
+                               nonlinearity with psi = grad phi) instead of (F^-1[m phi])^power; power = 2.
+                               q_j of a Nyquist index is 0 (the derivative of a real field stays real) */
 } orc_field;
 
 /* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11). */
@@ -68,7 +71,8 @@ int orc_mask(const orc_field *f, int kx, int ky, int kz);
 /* q^2 of full-spectrum mode (kx, ky, kz). */
 double orc_q2(const orc_field *f, int kx, int ky, int kz);
 
-/* P_q = F[ (F^-1[m phi])^p ] for a full spectrum phi (Eq. nonlin_general without M). */
+/* P_q = F[ (F^-1[m phi])^p ] for a full spectrum phi (Eq. nonlin_general without M),
+ * or F[ sum_j (F^-1[i q_j m phi])^2 ] when grad2 is set. */
 int orc_nonlinear(const orc_field *f, const double *phi, double *P);
 /* Noise increment xi_q of time step `step` (full spectrum), i.e. sqrt(dt) eta~_q of Eq. timeupdate.
  * Counter (((kz Ny + ky) Hxe + kx) / 2, step, field_id, 0) of the canonical
@@ -89,7 +93,7 @@ int orc_structure_factor(const orc_field *f, const double *phi, int nbins,
  * lambda holds dJ/dphi_T, on exit dJ/dphi_0, both for the inner product
  * <a, b> = Re sum conj(a) b over the full spectrum.  grad[0..4] receives
  * dJ/dO_k (the implicit coefficient of (q^2)^k), grad[5..9] dJ/dM_k, grad[10]
- * dJ/dD.  Keeps every intermediate state (nsteps + 1 spectra). */
+ * dJ/dD.  Power products only (grad2 = 0; else returns -3).  Keeps every intermediate state (nsteps + 1 spectra). */
 int orc_adjoint(const orc_field *f, const double *phi0, int64_t step0, int64_t nsteps, double *lambda,
                 double *grad);
 
