@@ -392,6 +392,16 @@ def variants_measurement(pss, torch, stream, ms_default_1024):
     out["real_state_1024"] = {"ms_per_step": ms, "site_steps_per_s": 1024 ** 2 / (ms * 1e-3),
                               "slowdown_over_spectral_state": ms / ms_default_1024}
     s.close()
+    # the second workload of the paper's examples: KPZ at 1024^2 (generic kernels,
+    # the gradient product per axis through real space)
+    s = pss.kpz((1024, 1024), dt=0.01, sigma=1.0, lam=0.5, D=0.01, seed=w["seed"], precision="f32")
+    s.set_stream(stream)
+    s.init_uniform(0, -0.5, 0.5)
+    l0 = s.launch_count
+    ms = _timed_steps(torch, stream, s, 300)
+    out["kpz_1024"] = {"ms_per_step": ms, "site_steps_per_s": 1024 ** 2 / (ms * 1e-3),
+                       "launches_per_step": (s.launch_count - l0) / 320, "path": s.step_path}
+    s.close()
     res = {}
     for order in (2, 3):
         s3 = pss.System((256, 256, 256), dt=0.005, seed=w["seed"], precision="f32")

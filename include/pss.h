@@ -116,6 +116,18 @@ int pss_add_term(pss_system *s, int field_id, int implicit,
                  int n_mono, const int *param_ids, const double *scales, const int *q2_pows,
                  int n_factors, const int *factor_fields, const int *powers);
 
+/* Add the rhs term  M(q) F[ |grad(m phi)|^2 ]  to the equation of field_id,
+ * M(q) = sum_{m < n_mono} scales[m] * param[param_ids[m]] * (q^2)^q2_pows[m]
+ * as in pss_add_term.  This is the KPZ nonlinearity lambda (grad phi)^2 of
+ * section "Writing models", written there as lambda psi^2 with psi = grad phi:
+ * each derivative i q_j m phi (q_j = 0 at a Nyquist index) goes to real
+ * space, their squares add up, and the sum goes back to Fourier space.  A
+ * field takes either this term (several add up their operators) or a power
+ * product (PSS_EUNSUPPORTED otherwise).  Such a system runs the generic
+ * kernels, and the adjoint returns PSS_EUNSUPPORTED for it. */
+int pss_add_grad_sq_term(pss_system *s, int field_id, int n_mono, const int *param_ids, const double *scales,
+                         const int *q2_pows);
+
 /* Noise of strength D~(q) = param[D_param_id] * (q^2)^q2_pow on field_id
  * ("addNoise(phi, D*q^2)", section "Adding noise").  q2_pow in [0, 4]. */
 int pss_set_noise(pss_system *s, int field_id, int D_param_id, int q2_pow);

@@ -42,6 +42,7 @@ struct Field {
     int noise_param = -1;
     int noise_pow = 0;
     int dealias = 2;
+    bool grad2 = false;                // rhs product |grad(m phi)|^2 (KPZ) instead of phi^power
     int frame_w = 0;                   // boundary frame along x (0: none)
     double frame_lo = 0, frame_hi = 0;
 };
@@ -75,6 +76,8 @@ struct pss_system {
     bool fps_dirty = true;
     void *tw = nullptr;                      // roots of unity, precision of the system
     void *real = nullptr;                    // real scratch [nz][ny][nx] (one slot)
+    void *GS = nullptr;                      // KPZ-type terms: derivative spectrum [slot][field_elems]
+    void *real_acc = nullptr;                // KPZ-type terms: |grad(m phi)|^2 in real space (one slot)
     void *half = nullptr;                    // half-spectrum scratch (one slot)
     double *sq = nullptr;                    // structure-factor accumulator
     int sq_cap = 0;
@@ -275,9 +278,15 @@ int mid_PZ(const pss_system *s) {
 
 // The FP32 2D path with one warp per transform serves sides of 256, 512 and
 // 1024 points; everything else runs the generic kernels.
+bool any_grad2(const pss_system *s) {
+    for (const Field &f : s->fields)
+        if (f.grad2) return true;
+    return false;
+}
+
 bool fast2d(const pss_system *s) {
     auto side = [](int n) { return n == 256 || n == 512 || n == 1024; };
-    return s->tune_fast2d && s->prec == PSS_F32 && s->dim == 2 && side(s->nx) && side(s->ny);
+    return s->tune_fast2d && s->prec == PSS_F32 && s->dim == 2 && side(s->nx) && side(s->ny) && !any_grad2(s);
 }
 // Launch shape of the fast path, measured on GB300.  2D: radix-16 passes for
 // sides of 512 and 1024 (two warps per 1024-point transform, three passes),
@@ -612,6 +621,38 @@ template <typename T> struct Seq {
 
     int x_pass_3d() { return fast3d_rows(s) ? row3() : row(ROW_FUSED, false, false, false, nullptr, 0); }  // B -> A
 
+    // The product of a KPZ-type term for the sequence's one slot (section
+    // "Writing models": lambda psi^2 with psi = grad phi): per axis j the
+    // derivative i q_j m phi back to real space, the sum of their squares,
+    // and its transform along x (and y in 3D) -> B, where the column kernel
+    // takes the product from.  Replaces the power product the fused kernels
+    // wrote into B for this slot.
+    int grad_sq_product() {
+        int rc;
+        cplx<T> *G = (cplx<T> *)s->GS;
+        for (int j = 0; j < s->dim; ++j) {
+            cudaError_t e = launch_grad_spectrum<T>(sys_params<T>(s), (const FieldP<T> *)s->fps, slot0,
+                                                    s->field_elems, state(), G, j, st);
+            s->launches++;
+            if (e != cudaSuccess) return cuda_fail(s, e, "derivative kernel");
+            if ((rc = col_ptrs(COL_INV_FULL, G, nullptr, A(), nullptr, 0))) return rc;        // G -> A
+            if (s->dim == 3) {
+                if ((rc = mid(MID_INV_FULL, true, false))) return rc;                         // A -> B
+                if ((rc = row(ROW_C2R, false, false, false, s->real, 0))) return rc;          // B -> real
+            } else if ((rc = row(ROW_C2R, true, false, false, s->real, 0))) {                 // A -> real
+                return rc;
+            }
+            e = launch_square_acc<T>((T *)s->real_acc, (const T *)s->real, s->nsites, j == 0 ? 1 : 0, st);
+            s->launches++;
+            if (e != cudaSuccess) return cuda_fail(s, e, "square kernel");
+        }
+        if (s->dim == 3) {
+            if ((rc = row(ROW_R2C, true, false, false, s->real_acc, 0))) return rc;           // -> A
+            return mid(MID_FWD, true, false);                                                 // A -> B
+        }
+        return row(ROW_R2C, true, true, false, s->real_acc, 0);                               // -> B
+    }
+
     // B <- x-transformed product of the current state (start of a run)
     int prologue() {
         int rc;
@@ -749,12 +790,35 @@ template <typename T> struct Seq {
     }
 };
 
-template <typename T> int run_prologue(pss_system *s) {
-    Seq<T> q{s, s->stream, 0, s->nslots()};
-    return q.prologue();
+// the products of the KPZ-type slots, over the power products the fused kernels wrote
+template <typename T> int grad_sq_products(pss_system *s, cudaStream_t st) {
+    const int nf = (int)s->fields.size();
+    for (int slot = 0; slot < s->nslots(); ++slot)
+        if (s->fields[slot % nf].grad2) {
+            int rc = Seq<T>{s, st, slot, 1}.grad_sq_product();
+            if (rc) return rc;
+        }
+    return PSS_OK;
+}
+
+template <typename T> int full_prologue(pss_system *s, cudaStream_t st) {
+    int rc = Seq<T>{s, st, 0, s->nslots()}.prologue();
+    if (rc || !any_grad2(s)) return rc;
+    return grad_sq_products<T>(s, st);
+}
+
+template <typename T> int run_prologue(pss_system *s) { return full_prologue<T>(s, s->stream); }
+
+int alloc_term_scratch(pss_system *s) {
+    if (!any_grad2(s)) return PSS_OK;
+    if (!s->GS) CK(cudaMalloc(&s->GS, csize(s) * s->field_elems * (size_t)s->nslots()));
+    if (!s->real) CK(cudaMalloc(&s->real, rsize(s) * (size_t)s->nsites));
+    if (!s->real_acc) CK(cudaMalloc(&s->real_acc, rsize(s) * (size_t)s->nsites));
+    return PSS_OK;
 }
 
 int prologue(pss_system *s) {
+    if (int rc = alloc_term_scratch(s)) return rc;
     if (!s->stale && s->b_fast == fast2d(s)) return PSS_OK;
     if (fast2d(s) && !s->XI) {
         const size_t bytes = csize(s) * s->field_elems * (size_t)s->nslots();
@@ -780,7 +844,8 @@ bool round_trip(const pss_system *s) {
 
 template <typename T> int step_once(pss_system *s, cudaStream_t st) {
     int rc = Seq<T>{s, st, 0, s->nslots()}.one_step();
-    if (rc || !round_trip(s)) return rc;
+    if (rc) return rc;
+    if (!round_trip(s)) return any_grad2(s) ? grad_sq_products<T>(s, st) : PSS_OK;
     // per slot: the full real field, its frame, and back to the spectrum
     const int nf = (int)s->fields.size();
     for (int slot = 0; slot < s->nslots(); ++slot) {
@@ -796,7 +861,7 @@ template <typename T> int step_once(pss_system *s, cudaStream_t st) {
         if ((rc = q.forward_from_real())) return rc;
     }
     // the product (and on the FP32 2D path the noise) of the new state
-    return Seq<T>{s, st, 0, s->nslots()}.prologue();
+    return full_prologue<T>(s, st);
 }
 
 int record_steps(pss_system *s, cudaStream_t st, int64_t n) {
@@ -939,6 +1004,8 @@ int grow_arrays(pss_system *s, int old_nf) {
     s->fps = nullptr;
     cudaFree(s->XI);   // drawn-ahead noise of the fast 2D path: reallocated for the new slot count
     s->XI = nullptr;
+    cudaFree(s->GS);
+    s->GS = nullptr;
     CK(cudaMalloc(&s->fps, fpsize(s) * (size_t)s->batch * nf));
     s->fps_dirty = true;
     return PSS_OK;
@@ -1145,6 +1212,8 @@ int pss_destroy_system(pss_system *s) {
     cudaFree(s->A);
     cudaFree(s->B);
     cudaFree(s->XI);
+    cudaFree(s->GS);
+    cudaFree(s->real_acc);
     cudaFree(s->fps);
     cudaFree(s->tw);
     cudaFree(s->real);
@@ -1271,12 +1340,34 @@ int pss_add_term(pss_system *s, int field_id, int implicit, int n_mono, const in
         for (int m = 0; m < n_mono; ++m) f.lhs.push_back({param_ids ? param_ids[m] : -1, scales[m], q2_pows[m]});
     } else {
         if (p < 1 || p > 3) return fail(s, PSS_EUNSUPPORTED, "explicit products must be a power 1..3");
+        if (f.grad2) return fail(s, PSS_EUNSUPPORTED, "a field with a |grad phi|^2 term takes no power product");
         if (f.power != 0 && f.power != p) return fail(s, PSS_EUNSUPPORTED, "explicit terms of a field share one power");
         f.power = p;
         for (int m = 0; m < n_mono; ++m) f.rhs.push_back({param_ids ? param_ids[m] : -1, scales[m], q2_pows[m]});
     }
     s->stale = true;
     s->fps_dirty = true;
+    return PSS_OK;
+}
+
+int pss_add_grad_sq_term(pss_system *s, int field_id, int n_mono, const int *param_ids, const double *scales,
+                         const int *q2_pows) {
+    int rc = check_field(s, field_id);
+    if (rc) return rc;
+    if (n_mono < 1 || n_mono > 8 || !scales || !q2_pows) return fail(s, PSS_EINVAL, "need 1..8 monomials");
+    for (int m = 0; m < n_mono; ++m) {
+        if (q2_pows[m] < 0 || q2_pows[m] >= kPolyTerms) return fail(s, PSS_EINVAL, "q^2 power must be in [0, 4]");
+        const int pid = param_ids ? param_ids[m] : -1;
+        if (pid >= (int)s->param_names.size()) return fail(s, PSS_EINVAL, "no parameter %d", pid);
+    }
+    Field &f = s->fields[field_id];
+    if (f.power != 0 && !f.grad2) return fail(s, PSS_EUNSUPPORTED, "the field already has a power product");
+    f.grad2 = true;
+    f.power = 2;
+    for (int m = 0; m < n_mono; ++m) f.rhs.push_back({param_ids ? param_ids[m] : -1, scales[m], q2_pows[m]});
+    s->stale = true;
+    s->fps_dirty = true;
+    invalidate(s);
     return PSS_OK;
 }
 
@@ -1402,6 +1493,7 @@ int pss_adjoint_forward(pss_system *s, int64_t n) {
     if (n < 1) return fail(s, PSS_EINVAL, "n must be >= 1");
     if (s->nslots() != 1) return fail(s, PSS_EUNSUPPORTED, "the adjoint needs one field and batch 1 in this build");
     if (round_trip(s)) return fail(s, PSS_EUNSUPPORTED, "the adjoint has no boundary frames or real-space round trip");
+    if (any_grad2(s)) return fail(s, PSS_EUNSUPPORTED, "the adjoint covers power products only");
     int64_t K = (int64_t)std::ceil(std::sqrt((double)n));
     const int64_t nck = (n + K - 1) / K;
     int rc = adj_alloc(s, nck, K);

@@ -183,6 +183,10 @@ cudaError_t launch_col2(const ColArgs<float> &a, int nslots, int ntiles, cudaStr
 cudaError_t launch_row2(const RowArgs<float> &a, int nslots, cudaStream_t st, bool tiled);
 template <typename T> cudaError_t launch_init_uniform(T *real, long long nsites, double lo, double hi,
                                                       uint64_t seed, int field_id, cudaStream_t st);
+template <typename T>
+cudaError_t launch_grad_spectrum(const SysP<T> &sp, const FieldP<T> *fps, int slot, size_t slot_stride,
+                                 const cplx<T> *in, cplx<T> *out, int axis, cudaStream_t st);
+template <typename T> cudaError_t launch_square_acc(T *acc, const T *r, long long n, int first, cudaStream_t st);
 template <typename T> cudaError_t launch_frame(T *real, int nx, long long rows, int width, double lo, double hi,
                                                cudaStream_t st);
 template <typename T> cudaError_t launch_tiles_to_half(const SysP<T> &sp, const cplx<T> *tiles,

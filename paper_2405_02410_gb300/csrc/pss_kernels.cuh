@@ -820,6 +820,44 @@ __global__ void k_init_uniform(T *real, long long nsites, T lo, T hi, uint32_t s
     }
 }
 
+// i q_j m phi of one slot (tiled in, tiled out): the derivative along axis j of
+// the de-aliased field, one factor psi_j of a KPZ-type term |grad(m phi)|^2.
+// q_j of a Nyquist index is 0, so that the derivative of a real field is real.
+template <typename T>
+__global__ void k_grad_spectrum(const SysP<T> sp, const FieldP<T> *fps, int slot, size_t slot_stride,
+                                const cplx<T> *in, cplx<T> *out, int axis) {
+    const FieldP<T> &fp = fps[slot];
+    const long long n = (long long)sp.ntiles * sp.rows * W;
+    const cplx<T> *src = in + (size_t)slot * slot_stride;
+    cplx<T> *dst = out + (size_t)slot * slot_stride;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(i % W);
+        const long long tr = i / W;
+        const int row = (int)(tr % sp.rows), tile = (int)(tr / sp.rows);
+        const int kx = tile * W + c;
+        const int ky = sp.dim == 3 ? row / sp.nz : (sp.dim == 2 ? row : 0);
+        const int kz = sp.dim == 3 ? row % sp.nz : 0;
+        const int sky = signed_k(ky, sp.ny), skz = signed_k(kz, sp.nz);
+        const bool keep = kx < sp.hx && kx <= fp.kmax[0] && abs(sky) <= fp.kmax[1] && abs(skz) <= fp.kmax[2];
+        T q;
+        if (axis == 0) q = 2 * kx == sp.nx ? T(0) : T(kx) * sp.gx;
+        else if (axis == 1) q = 2 * ky == sp.ny ? T(0) : T(sky) * sp.gy;
+        else q = 2 * kz == sp.nz ? T(0) : T(skz) * sp.gz;
+        const cplx<T> v = src[i];
+        dst[i] = keep ? mk<T>(-q * v.y, q * v.x) : mk<T>(0, 0);
+    }
+}
+
+// acc = (first ? 0 : acc) + r^2 over a real field
+template <typename T> __global__ void k_square_acc(T *acc, const T *r, long long n, int first) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const T v = r[i];
+        acc[i] = first ? v * v : acc[i] + v * v;
+    }
+}
+
 // Boundary frame along x of a real field [rows][nx]: x < w takes lo, x >= nx - w takes hi.
 template <typename T> __global__ void k_frame(T *real, int nx, long long rows, int w, T lo, T hi) {
     const long long n = rows * (2LL * w);
@@ -1054,6 +1092,23 @@ cudaError_t launch_init_uniform(T *real, long long nsites, double lo, double hi,
 }
 
 template <typename T>
+cudaError_t launch_grad_spectrum(const SysP<T> &sp, const FieldP<T> *fps, int slot, size_t slot_stride,
+                                 const cplx<T> *in, cplx<T> *out, int axis, cudaStream_t st) {
+    const long long n = (long long)sp.ntiles * sp.rows * W;
+    long long blocks = (n + 255) / 256;
+    if (blocks > 65535) blocks = 65535;
+    k_grad_spectrum<T><<<(int)blocks, 256, 0, st>>>(sp, fps, slot, slot_stride, in, out, axis);
+    return cudaGetLastError();
+}
+
+template <typename T> cudaError_t launch_square_acc(T *acc, const T *r, long long n, int first, cudaStream_t st) {
+    long long blocks = (n + 255) / 256;
+    if (blocks > 65535) blocks = 65535;
+    k_square_acc<T><<<(int)blocks, 256, 0, st>>>(acc, r, n, first);
+    return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_frame(T *real, int nx, long long rows, int width, double lo, double hi, cudaStream_t st) {
     if (width < 1 || 2 * width > nx) return cudaErrorInvalidValue;
     const long long n = rows * 2LL * width;
@@ -1106,6 +1161,9 @@ cudaError_t launch_structure_factor(const SysP<T> &sp, const double dx[3], const
     template cudaError_t launch_init_uniform<T>(T *, long long, double, double, uint64_t, int, cudaStream_t); \
     template cudaError_t launch_tiles_to_half<T>(const SysP<T> &, const cplx<T> *, cplx<T> *, cudaStream_t); \
     template cudaError_t launch_frame<T>(T *, int, long long, int, double, double, cudaStream_t);              \
+    template cudaError_t launch_grad_spectrum<T>(const SysP<T> &, const FieldP<T> *, int, size_t, const cplx<T> *, \
+                                                 cplx<T> *, int, cudaStream_t);                                  \
+    template cudaError_t launch_square_acc<T>(T *, const T *, long long, int, cudaStream_t);                  \
     template cudaError_t launch_half_to_tiles<T>(const SysP<T> &, const cplx<T> *, cplx<T> *, cudaStream_t); \
     template cudaError_t launch_segment_begin<T>(cplx<T> *, const cplx<T> *, size_t, const long long *, long long, \
                                                  long long, long long *, long long *, cudaStream_t);             \

@@ -29,7 +29,7 @@ EXPORTS = [
     "pss_set_spectrum", "pss_structure_factor", "pss_sync", "pss_last_error", "pss_launch_count",
     "pss_time_kernels", "pss_set_tuning", "pss_create_batch", "pss_batch_size", "pss_select_instance",
     "pss_set_param_batch", "pss_step_many", "pss_adjoint_forward", "pss_adjoint_backward",
-    "pss_structure_factor_noalloc", "pss_step_path", "pss_set_frame",
+    "pss_structure_factor_noalloc", "pss_step_path", "pss_set_frame", "pss_add_grad_sq_term",
 ]
 
 
@@ -54,6 +54,7 @@ def _load():
         "pss_get_param": ([vp, i32, P(d)], i32),
         "pss_add_field": ([vp, ctypes.c_char_p, i32, P(i32)], i32),
         "pss_add_term": ([vp, i32, i32, i32, P(i32), P(d), P(i32), i32, P(i32), P(i32)], i32),
+        "pss_add_grad_sq_term": ([vp, i32, i32, P(i32), P(d), P(i32)], i32),
         "pss_set_noise": ([vp, i32, i32, i32], i32),
         "pss_set_dealias": ([vp, i32, i32], i32),
         "pss_set_frame": ([vp, i32, i32, d, d], i32),
@@ -185,6 +186,14 @@ class System:
                                   _arr(ctypes.c_double, [float(m[1]) for m in mono]),
                                   _arr(ctypes.c_int, [m[2] for m in mono]), len(fac),
                                   _arr(ctypes.c_int, [f[0] for f in fac]), _arr(ctypes.c_int, [f[1] for f in fac])))
+
+    def add_grad_sq_term(self, field: int, monomials: Iterable):
+        """rhs term M(q) F[|grad(m phi)|^2]; monomials: (param_id or -1, scale, q2_power)."""
+        mono = list(monomials)
+        self._ck(lib.pss_add_grad_sq_term(self._h, field, len(mono),
+                                          _arr(ctypes.c_int, [m[0] for m in mono]),
+                                          _arr(ctypes.c_double, [float(m[1]) for m in mono]),
+                                          _arr(ctypes.c_int, [int(m[2]) for m in mono])))
 
     def set_noise(self, field: int, D_param: int, q2_pow: int = 0):
         self._ck(lib.pss_set_noise(self._h, field, D_param, q2_pow))
@@ -336,6 +345,26 @@ def add_model_b_field(s: System, a=-1.0, b=1.0, K=1.0, D=0.01, noisy=True, deali
         s.set_noise(f, pD, 1)
     s.set_dealias(f, dealias_order)
     return f
+
+
+def add_kpz_field(s: System, sigma=1.0, lam=1.0, D=0.01, noisy=True, dealias_order=2, name="h"):
+    """KPZ (section "Writing models"): dt h = sigma lap h + lambda (grad h)^2 + noise D,
+    i.e. dt h + sigma q^2 h = lambda F[|grad(m h)|^2]."""
+    f = s.add_field(name)
+    ps, pl, pD = (s.add_param(f"{name}.{k}", v) for k, v in (("sigma", sigma), ("lambda", lam), ("D", D)))
+    s.add_term(f, True, [(ps, 1.0, 1)], [(f, 1)])
+    s.add_grad_sq_term(f, [(pl, 1.0, 0)])
+    if noisy:
+        s.set_noise(f, pD, 0)
+    s.set_dealias(f, dealias_order)
+    return f
+
+
+def kpz(shape, dt=0.01, sigma=1.0, lam=1.0, D=0.01, noisy=True, seed=2405, precision="f32", dealias_order=2,
+        dx=(1.0, 1.0, 1.0), system: Optional[System] = None) -> System:
+    s = system or System(shape, dt=dt, dx=dx, seed=seed, precision=precision)
+    add_kpz_field(s, sigma=sigma, lam=lam, D=D, noisy=noisy, dealias_order=dealias_order)
+    return s
 
 
 def add_model_a_field(s: System, a=-1.0, b=1.0, K=1.0, D=0.05, noisy=True, dealias_order=2, name="psi"):
