@@ -418,6 +418,30 @@ def variants_measurement(pss, torch, stream, ms_default_1024):
     return out
 
 
+def example_measurement(pss, torch, stream):
+    """The paper's Model B example: 256^2, dt = 0.1, -a = b = 1, k = 4, no noise,
+    to t = 5000 (50,000 steps) with L(t) from S(q) at its snapshot times."""
+    import math
+    import numpy as np
+    s = pss.model_b((256, 256), dt=0.1, a=-1.0, b=1.0, K=4.0, D=0.0, noisy=False, seed=2405, precision="f32")
+    s.set_stream(stream)
+    s.init_uniform(0, -0.1, 0.1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    L, t = {}, 0
+    for T in (10, 100, 1000, 5000):
+        s.step(int(round((T - t) / 0.1)))
+        t = T
+        L[T] = s.structure_factor(0, 64)[2]
+    wall = time.perf_counter() - t0
+    r = s.get_field(0)
+    s.close()
+    return {"workload": "Model B example, 256x256, dt=0.1, a=-1, b=1, k=4, no noise, t = 0..5000",
+            "wall_s_to_t5000": wall, "L_at_t": {str(k): v for k, v in L.items()},
+            "growth_exponent_1000_5000": math.log(L[5000] / L[1000]) / math.log(5.0),
+            "phases_p3_p97": [float(np.percentile(r, 3)), float(np.percentile(r, 97))]}
+
+
 def adjoint_measurement(pss, torch, stream, n=2000, shape=(256, 256), nbins=64):
     """The adjoint workload: 2D Model B 256^2, FP32, n steps with a fixed noise realisation and sqrt(n)
     checkpoints; loss = mean over the 64 S(q) bins of (S - S*)^2 with S* from (a, b, K) = (-0.8, 1.2, 0.9)."""
@@ -610,6 +634,7 @@ def run_gpu(args):
         extra["adjoint_256"] = adjoint_measurement(pss, torch, stream)
     if not args.no_variants:
         extra["variants"] = variants_measurement(pss, torch, stream, ms_per_step)
+        extra["model_b_example_256"] = example_measurement(pss, torch, stream)
     if not args.no_cufft:
         cf = cufft_comparison(torch, stream)
         cf["ours_over_cufft"] = value / cf["site_steps_per_s"]
