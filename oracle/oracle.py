@@ -295,6 +295,87 @@ def run_framed(m: Model, phi: np.ndarray, step0: int, nsteps: int, width: int, l
     return out
 
 
+@dataclass
+class Factor:
+    """One factor psi^power of a product term, psi = F^-1[op(q) m phi_field] with
+    op(q) = (i q_deriv if deriv >= 0) * (-q^2)^lap (section "Writing models": the
+    fields psi_k are the fields phi_i acted on by differential operators)."""
+    field: int
+    power: int = 1
+    deriv: int = -1           # -1: none; 0, 1, 2: i q_x, i q_y, i q_z (q = 0 at a Nyquist index)
+    lap: int = 0
+
+
+@dataclass
+class Term:
+    """M(q) F[prod_k psi_k^n_k] on the rhs of the equation of field ``target``;
+    ``M`` is a list of (coef, q2_power)."""
+    target: int
+    M: list
+    factors: list
+
+
+def _q_axis(m: Model, axis: int) -> np.ndarray:
+    """q_axis of every full-spectrum mode, 0 at a Nyquist index (odd operator)."""
+    n = m.shape[m.dim - 1 - axis]
+    k = np.arange(n)
+    kk = np.where(k < (n + 1) // 2, k, k - n).astype(float)
+    q = 2 * np.pi * kk / (n * m.dx[axis])
+    if n % 2 == 0:
+        q[n // 2] = 0.0
+    shp = [1] * m.dim
+    shp[m.dim - 1 - axis] = n
+    return np.broadcast_to(q.reshape(shp), m.shape)
+
+
+def term_products(models, terms, phis):
+    """The explicit part P_i = sum_{terms of i} M_t(q) F[prod_k psi_k^n_k] of every
+    field (Eq. basefourier with the nonlinearities written as in "Writing models"):
+    each factor is taken to real space from its field's de-aliased spectrum, the
+    factors multiply in real space, the product goes back to Fourier space."""
+    m0 = models[0]
+    method = 1 if m0.n_sites <= 256 else 2
+    masks = [mask(m) for m in models]
+    q2s = q2(m0)
+    P = [np.zeros(m0.shape, dtype=np.complex128) for _ in models]
+    for t in terms:
+        prod = np.ones(m0.shape)
+        for fct in t.factors:
+            op = np.ones(m0.shape, dtype=np.complex128)
+            if fct.deriv >= 0:
+                op = op * 1j * _q_axis(m0, fct.deriv)
+            op = op * (-q2s) ** fct.lap
+            psi = dft(op * masks[fct.field] * phis[fct.field], +1, method).real / m0.n_sites
+            prod = prod * psi ** fct.power
+        Mq = sum(c * q2s ** p for c, p in t.M)
+        P[t.target] = P[t.target] + Mq * dft(prod, -1, method)
+    return P
+
+
+def hermitian(phi: np.ndarray) -> np.ndarray:
+    """The Hermitian part (phi_k + conj phi_-k) / 2 of a full spectrum."""
+    flip = np.conj(np.roll(np.flip(phi), 1, axis=tuple(range(phi.ndim))))
+    return 0.5 * (phi + flip)
+
+
+def run_coupled(models, terms, phis, step0: int, nsteps: int):
+    """Coupled fields (Eq. basefourier): every field i takes
+    phi_i <- H[(phi_i + dt P_i + xi_i) / (1 + dt O_i(q))] with P_i from
+    ``term_products`` of all fields at the same time step, O_i and the noise
+    from ``models[i]`` (its own rhs and power are not used)."""
+    phis = [np.array(p, dtype=np.complex128, copy=True) for p in phis]
+    q2s = q2(models[0])
+    for k in range(nsteps):
+        P = term_products(models, terms, phis)
+        nxt = []
+        for i, m in enumerate(models):
+            O = sum(c * q2s ** p for c, p in m.lhs) if m.lhs else np.zeros(m.shape)
+            xi = noise(m, step0 + k) if m.noisy else 0.0
+            nxt.append(hermitian((phis[i] + m.dt * P[i] + xi) / (1 + m.dt * O)))
+        phis = nxt
+    return phis
+
+
 def init_uniform(m: Model, lo: float, hi: float) -> np.ndarray:
     s = m.c_struct()
     out = np.zeros(m.shape, dtype=np.float64)
