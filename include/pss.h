@@ -116,15 +116,32 @@ int pss_add_term(pss_system *s, int field_id, int implicit,
                  int n_mono, const int *param_ids, const double *scales, const int *q2_pows,
                  int n_factors, const int *factor_fields, const int *powers);
 
+/* Add a product term  M(q) F[ prod_k psi_k^powers[k] ]  to the rhs of the
+ * equation of field_id (Eq. basefourier; section "Writing models": a
+ * nonlinearity M prod_k psi_k^n_k whose factors psi_k are fields acted on by
+ * differential operators).  M(q) is built from the monomials as in
+ * pss_add_term.  Factor k is psi_k = F^-1[op_k(q) m phi_{factor_fields[k]}]
+ * with the de-alias mask m of that field and
+ *     op_k(q) = (i q_{derivs[k]} if derivs[k] >= 0) * (-q^2)^laps[k],
+ * derivs[k] in -1 (none), 0..dim-1 (x, y, z; q = 0 at a Nyquist index),
+ * laps[k] in 0..2, powers[k] in 1..4, 1..8 factors; derivs or laps NULL
+ * means all -1 or all 0.  Factors may name any field of the system (of the
+ * same instance).  A field with product terms evaluates all its explicit
+ * terms (its power product from pss_add_term too) through real space: per
+ * factor its transform back, then the products, the sums of the terms that
+ * share one operator, and the transforms forward.  Such systems run the
+ * generic kernels; the adjoint returns PSS_EUNSUPPORTED for them. */
+int pss_add_product_term(pss_system *s, int field_id, int n_mono, const int *param_ids, const double *scales,
+                         const int *q2_pows, int n_factors, const int *factor_fields, const int *powers,
+                         const int *derivs, const int *laps);
+
 /* Add the rhs term  M(q) F[ |grad(m phi)|^2 ]  to the equation of field_id,
  * M(q) = sum_{m < n_mono} scales[m] * param[param_ids[m]] * (q^2)^q2_pows[m]
  * as in pss_add_term.  This is the KPZ nonlinearity lambda (grad phi)^2 of
  * section "Writing models", written there as lambda psi^2 with psi = grad phi:
  * each derivative i q_j m phi (q_j = 0 at a Nyquist index) goes to real
- * space, their squares add up, and the sum goes back to Fourier space.  A
- * field takes either this term (several add up their operators) or a power
- * product (PSS_EUNSUPPORTED otherwise).  Such a system runs the generic
- * kernels, and the adjoint returns PSS_EUNSUPPORTED for it. */
+ * space, their squares add up, and the sum goes back to Fourier space: the
+ * product terms M (d_j phi)^2 of every axis j (pss_add_product_term). */
 int pss_add_grad_sq_term(pss_system *s, int field_id, int n_mono, const int *param_ids, const double *scales,
                          const int *q2_pows);
 

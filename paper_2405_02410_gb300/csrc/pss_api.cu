@@ -42,9 +42,21 @@ struct Field {
     int noise_param = -1;
     int noise_pow = 0;
     int dealias = 2;
-    bool grad2 = false;                // rhs product |grad(m phi)|^2 (KPZ) instead of phi^power
+    bool general = false;              // has product terms (evaluated through real space)
     int frame_w = 0;                   // boundary frame along x (0: none)
     double frame_lo = 0, frame_hi = 0;
+};
+
+// One factor psi^power of a product term: psi = F^-1[op(q) m phi_field],
+// op(q) = (i q_deriv if deriv >= 0) (-q^2)^lap.
+struct GFactor {
+    int field, power, deriv, lap;
+};
+// M(q) F[prod_k psi_k^n_k] on the rhs of field `target`.
+struct GTerm {
+    int target;
+    std::vector<Mono> M;
+    std::vector<GFactor> factors;
 };
 
 constexpr int kDefaultGraphSteps = 16;
@@ -66,6 +78,7 @@ struct pss_system {
     std::vector<std::string> param_names;
     std::vector<double> param_values;        // [instance][param]
     std::vector<Field> fields;
+    std::vector<GTerm> gterms;               // product terms (pss_add_product_term, pss_add_grad_sq_term)
     int cur = 0;                             // instance addressed by the per-field calls
     int hx = 0, ntiles = 0, rows = 0, n_outer = 1, n_inner = 1;
     long long nsites = 0;
@@ -76,8 +89,9 @@ struct pss_system {
     bool fps_dirty = true;
     void *tw = nullptr;                      // roots of unity, precision of the system
     void *real = nullptr;                    // real scratch [nz][ny][nx] (one slot)
-    void *GS = nullptr;                      // KPZ-type terms: derivative spectrum [slot][field_elems]
-    void *real_acc = nullptr;                // KPZ-type terms: |grad(m phi)|^2 in real space (one slot)
+    void *GS = nullptr;                      // product terms: factor / product spectrum [slot][field_elems]
+    void *real_acc = nullptr;                // product terms: sum of the products in real space (one slot)
+    void *real_tp = nullptr;                 // product terms: running product of one term (one slot)
     void *half = nullptr;                    // half-spectrum scratch (one slot)
     double *sq = nullptr;                    // structure-factor accumulator
     int sq_cap = 0;
@@ -183,12 +197,59 @@ double pval(const pss_system *s, int inst, int id) {
     return id < 0 ? 1.0 : s->param_values[(size_t)inst * s->param_names.size() + id];
 }
 
+bool any_general(const pss_system *s) {
+    for (const Field &f : s->fields)
+        if (f.general) return true;
+    return false;
+}
+
+bool same_mono(const std::vector<Mono> &a, const std::vector<Mono> &b) {
+    if (a.size() != b.size()) return false;
+    for (size_t i = 0; i < a.size(); ++i)
+        if (a[i].param != b[i].param || a[i].scale != b[i].scale || a[i].pow != b[i].pow) return false;
+    return true;
+}
+
+// The product terms of field fi (its power product, if any, among them),
+// grouped by operator: a group's products add up in real space and take one
+// transform.
+std::vector<std::vector<GTerm>> term_groups(const pss_system *s, int fi) {
+    std::vector<GTerm> terms;
+    const Field &f = s->fields[fi];
+    if (f.power > 0) terms.push_back({fi, f.rhs, {{fi, f.power, -1, 0}}});
+    for (const GTerm &t : s->gterms)
+        if (t.target == fi) terms.push_back(t);
+    std::vector<std::vector<GTerm>> groups;
+    for (const GTerm &t : terms) {
+        bool placed = false;
+        for (auto &g : groups)
+            if (same_mono(g[0].M, t.M)) { g.push_back(t); placed = true; break; }
+        if (!placed) groups.push_back({t});
+    }
+    return groups;
+}
+
 template <typename T> FieldP<T> field_params(const pss_system *s, int inst, int fi) {
     const Field &f = s->fields[fi];
     FieldP<T> p{};
     double O[kPolyTerms] = {0}, M[kPolyTerms] = {0};
     for (const Mono &m : f.lhs) O[m.pow] += m.scale * pval(s, inst, m.param);
-    for (const Mono &m : f.rhs) M[m.pow] += m.scale * pval(s, inst, m.param);
+    p.power = f.power;
+    p.spectral = 0;
+    if (f.general) {
+        // one operator: the column kernel applies it after its own transform;
+        // several: the products arrive summed in Fourier space with theirs
+        const auto groups = term_groups(s, fi);
+        p.power = 1;
+        if (groups.size() == 1) {
+            for (const Mono &m : groups[0][0].M) M[m.pow] += m.scale * pval(s, inst, m.param);
+        } else {
+            M[0] = 1.0;
+            p.spectral = 1;
+        }
+    } else {
+        for (const Mono &m : f.rhs) M[m.pow] += m.scale * pval(s, inst, m.param);
+    }
     for (int i = 0; i < kPolyTerms; ++i) { p.O[i] = T(O[i]); p.M[i] = T(M[i]); }
     double dV = 1.0;
     for (int j = 0; j < s->dim; ++j) dV *= s->dx[j];
@@ -196,7 +257,6 @@ template <typename T> FieldP<T> field_params(const pss_system *s, int inst, int 
     p.sigma0 = f.noisy ? T(std::sqrt(std::max(0.0, (double)s->nsites * pval(s, inst, f.noise_param) * s->dt / dV)))
                        : T(0);
     p.noise_pow = f.noise_pow;
-    p.power = f.power;
     p.kmax[0] = kmax_axis(s->nx, f.dealias);
     p.kmax[1] = kmax_axis(s->ny, f.dealias);
     p.kmax[2] = kmax_axis(s->nz, f.dealias);
@@ -278,15 +338,10 @@ int mid_PZ(const pss_system *s) {
 
 // The FP32 2D path with one warp per transform serves sides of 256, 512 and
 // 1024 points; everything else runs the generic kernels.
-bool any_grad2(const pss_system *s) {
-    for (const Field &f : s->fields)
-        if (f.grad2) return true;
-    return false;
-}
 
 bool fast2d(const pss_system *s) {
     auto side = [](int n) { return n == 256 || n == 512 || n == 1024; };
-    return s->tune_fast2d && s->prec == PSS_F32 && s->dim == 2 && side(s->nx) && side(s->ny) && !any_grad2(s);
+    return s->tune_fast2d && s->prec == PSS_F32 && s->dim == 2 && side(s->nx) && side(s->ny) && !any_general(s);
 }
 // Launch shape of the fast path, measured on GB300.  2D: radix-16 passes for
 // sides of 512 and 1024 (two warps per 1024-point transform, three passes),
@@ -621,36 +676,74 @@ template <typename T> struct Seq {
 
     int x_pass_3d() { return fast3d_rows(s) ? row3() : row(ROW_FUSED, false, false, false, nullptr, 0); }  // B -> A
 
-    // The product of a KPZ-type term for the sequence's one slot (section
-    // "Writing models": lambda psi^2 with psi = grad phi): per axis j the
-    // derivative i q_j m phi back to real space, the sum of their squares,
-    // and its transform along x (and y in 3D) -> B, where the column kernel
-    // takes the product from.  Replaces the power product the fused kernels
-    // wrote into B for this slot.
-    int grad_sq_product() {
+    // The explicit part of general field fi of instance inst, for the
+    // sequence's one slot (section "Writing models": N = M prod_k psi_k^n_k,
+    // psi_k a field acted on by a differential operator): every factor goes
+    // to real space from op(q) m phi of its field, the factors multiply and
+    // the terms of a group (one operator M) add up there; the sum goes back
+    // along x (and y in 3D) into B, where the column kernel transforms it
+    // the rest of the way and applies M.  With several groups each sum is
+    // transformed completely and B takes sum_g M_g(q) F[sum_g] instead.
+    // Replaces what the fused kernels wrote into B for this slot.
+    int general_product(int inst, int fi) {
         int rc;
+        cudaError_t e;
+        const int nf = (int)s->fields.size();
+        const auto groups = term_groups(s, fi);
+        const bool spectral = groups.size() > 1;
+        const size_t stride = s->field_elems;
         cplx<T> *G = (cplx<T> *)s->GS;
-        for (int j = 0; j < s->dim; ++j) {
-            cudaError_t e = launch_grad_spectrum<T>(sys_params<T>(s), (const FieldP<T> *)s->fps, slot0,
-                                                    s->field_elems, state(), G, j, st);
-            s->launches++;
-            if (e != cudaSuccess) return cuda_fail(s, e, "derivative kernel");
-            if ((rc = col_ptrs(COL_INV_FULL, G, nullptr, A(), nullptr, 0))) return rc;        // G -> A
-            if (s->dim == 3) {
-                if ((rc = mid(MID_INV_FULL, true, false))) return rc;                         // A -> B
-                if ((rc = row(ROW_C2R, false, false, false, s->real, 0))) return rc;          // B -> real
-            } else if ((rc = row(ROW_C2R, true, false, false, s->real, 0))) {                 // A -> real
-                return rc;
+        T *acc = (T *)s->real_acc, *tp = (T *)s->real_tp, *r = (T *)s->real;
+        for (size_t gi = 0; gi < groups.size(); ++gi) {
+            const auto &g = groups[gi];
+            for (size_t ti = 0; ti < g.size(); ++ti) {
+                const auto &fac = g[ti].factors;
+                for (size_t k = 0; k < fac.size(); ++k) {
+                    const int src = inst * nf + fac[k].field;
+                    e = launch_op_spectrum<T>(sys_params<T>(s), (const FieldP<T> *)s->fps, src,
+                                              state() + (size_t)src * stride, G + (size_t)slot0 * stride,
+                                              fac[k].deriv, fac[k].lap, st);
+                    s->launches++;
+                    if (e != cudaSuccess) return cuda_fail(s, e, "factor spectrum kernel");
+                    if ((rc = col_ptrs(COL_INV_FULL, G, nullptr, A(), nullptr, 0))) return rc;      // G -> A
+                    if (s->dim == 3) {
+                        if ((rc = mid_ptrs(MID_INV_FULL, A(), G, false))) return rc;              // A -> G
+                        if ((rc = row_ptrs(ROW_C2R, G, A(), false, nullptr, r, 0))) return rc;   // G -> real
+                    } else if ((rc = row_ptrs(ROW_C2R, A(), B(), false, nullptr, r, 0))) {       // A -> real
+                        return rc;
+                    }
+                    e = launch_factor<T>(acc, tp, r, s->nsites, fac[k].power, k == 0, k + 1 == fac.size(), ti == 0,
+                                         st);
+                    s->launches++;
+                    if (e != cudaSuccess) return cuda_fail(s, e, "factor kernel");
+                }
             }
-            e = launch_square_acc<T>((T *)s->real_acc, (const T *)s->real, s->nsites, j == 0 ? 1 : 0, st);
+            if (!spectral) {
+                if (s->dim == 3) {
+                    if ((rc = row_ptrs(ROW_R2C, A(), A(), false, acc, nullptr, 0))) return rc;   // -> A
+                    return mid_ptrs(MID_FWD, A(), B(), false);                                 // A -> B
+                }
+                return row_ptrs(ROW_R2C, A(), B(), false, acc, nullptr, 0);                      // -> B
+            }
+            // the group's sum transformed along every axis, times M_g, into B
+            cplx<T> *full;
+            if ((rc = row_ptrs(ROW_R2C, A(), A(), false, acc, nullptr, 0))) return rc;           // -> A
+            if (s->dim == 3) {
+                if ((rc = mid_ptrs(MID_FWD, A(), G, false))) return rc;                         // A -> G
+                if ((rc = col_ptrs(COL_FWD, A(), G, B(), nullptr, 0))) return rc;                // G -> A
+                full = A();
+            } else {
+                if ((rc = col_ptrs(COL_FWD, G, A(), B(), nullptr, 0))) return rc;                // A -> G
+                full = G;
+            }
+            double m[kPolyTerms] = {0};
+            for (const Mono &mo : g[0].M) m[mo.pow] += mo.scale * pval(s, inst, mo.param);
+            e = launch_combine<T>(sys_params<T>(s), B() + (size_t)slot0 * stride, full + (size_t)slot0 * stride, m,
+                                  gi == 0, st);
             s->launches++;
-            if (e != cudaSuccess) return cuda_fail(s, e, "square kernel");
+            if (e != cudaSuccess) return cuda_fail(s, e, "combine kernel");
         }
-        if (s->dim == 3) {
-            if ((rc = row(ROW_R2C, true, false, false, s->real_acc, 0))) return rc;           // -> A
-            return mid(MID_FWD, true, false);                                                 // A -> B
-        }
-        return row(ROW_R2C, true, true, false, s->real_acc, 0);                               // -> B
+        return PSS_OK;
     }
 
     // B <- x-transformed product of the current state (start of a run)
@@ -790,12 +883,12 @@ template <typename T> struct Seq {
     }
 };
 
-// the products of the KPZ-type slots, over the power products the fused kernels wrote
-template <typename T> int grad_sq_products(pss_system *s, cudaStream_t st) {
+// the products of the general fields' slots, over what the fused kernels wrote
+template <typename T> int general_products(pss_system *s, cudaStream_t st) {
     const int nf = (int)s->fields.size();
     for (int slot = 0; slot < s->nslots(); ++slot)
-        if (s->fields[slot % nf].grad2) {
-            int rc = Seq<T>{s, st, slot, 1}.grad_sq_product();
+        if (s->fields[slot % nf].general) {
+            int rc = Seq<T>{s, st, slot, 1}.general_product(slot / nf, slot % nf);
             if (rc) return rc;
         }
     return PSS_OK;
@@ -803,17 +896,18 @@ template <typename T> int grad_sq_products(pss_system *s, cudaStream_t st) {
 
 template <typename T> int full_prologue(pss_system *s, cudaStream_t st) {
     int rc = Seq<T>{s, st, 0, s->nslots()}.prologue();
-    if (rc || !any_grad2(s)) return rc;
-    return grad_sq_products<T>(s, st);
+    if (rc || !any_general(s)) return rc;
+    return general_products<T>(s, st);
 }
 
 template <typename T> int run_prologue(pss_system *s) { return full_prologue<T>(s, s->stream); }
 
 int alloc_term_scratch(pss_system *s) {
-    if (!any_grad2(s)) return PSS_OK;
+    if (!any_general(s)) return PSS_OK;
     if (!s->GS) CK(cudaMalloc(&s->GS, csize(s) * s->field_elems * (size_t)s->nslots()));
     if (!s->real) CK(cudaMalloc(&s->real, rsize(s) * (size_t)s->nsites));
     if (!s->real_acc) CK(cudaMalloc(&s->real_acc, rsize(s) * (size_t)s->nsites));
+    if (!s->real_tp) CK(cudaMalloc(&s->real_tp, rsize(s) * (size_t)s->nsites));
     return PSS_OK;
 }
 
@@ -845,7 +939,7 @@ bool round_trip(const pss_system *s) {
 template <typename T> int step_once(pss_system *s, cudaStream_t st) {
     int rc = Seq<T>{s, st, 0, s->nslots()}.one_step();
     if (rc) return rc;
-    if (!round_trip(s)) return any_grad2(s) ? grad_sq_products<T>(s, st) : PSS_OK;
+    if (!round_trip(s)) return any_general(s) ? general_products<T>(s, st) : PSS_OK;
     // per slot: the full real field, its frame, and back to the spectrum
     const int nf = (int)s->fields.size();
     for (int slot = 0; slot < s->nslots(); ++slot) {
@@ -1214,6 +1308,7 @@ int pss_destroy_system(pss_system *s) {
     cudaFree(s->XI);
     cudaFree(s->GS);
     cudaFree(s->real_acc);
+    cudaFree(s->real_tp);
     cudaFree(s->fps);
     cudaFree(s->tw);
     cudaFree(s->real);
@@ -1272,6 +1367,12 @@ int pss_set_param(pss_system *s, int id, double value) {
     if (id < 0 || id >= (int)s->param_names.size()) return fail(s, PSS_EINVAL, "no parameter %d", id);
     for (int b = 0; b < s->batch; ++b) s->param_values[(size_t)b * s->param_names.size() + id] = value;
     s->fps_dirty = true;
+    if (!s->gterms.empty()) {
+        // product-term operators are launch arguments, and a field with several
+        // of them holds its next product with the operators applied
+        invalidate(s);
+        s->stale = true;
+    }
     return PSS_OK;
 }
 
@@ -1280,6 +1381,10 @@ int pss_set_param_batch(pss_system *s, int id, const double *values) {
     if (id < 0 || id >= (int)s->param_names.size()) return fail(s, PSS_EINVAL, "no parameter %d", id);
     for (int b = 0; b < s->batch; ++b) s->param_values[(size_t)b * s->param_names.size() + id] = values[b];
     s->fps_dirty = true;
+    if (!s->gterms.empty()) {
+        invalidate(s);
+        s->stale = true;
+    }
     return PSS_OK;
 }
 
@@ -1340,7 +1445,6 @@ int pss_add_term(pss_system *s, int field_id, int implicit, int n_mono, const in
         for (int m = 0; m < n_mono; ++m) f.lhs.push_back({param_ids ? param_ids[m] : -1, scales[m], q2_pows[m]});
     } else {
         if (p < 1 || p > 3) return fail(s, PSS_EUNSUPPORTED, "explicit products must be a power 1..3");
-        if (f.grad2) return fail(s, PSS_EUNSUPPORTED, "a field with a |grad phi|^2 term takes no power product");
         if (f.power != 0 && f.power != p) return fail(s, PSS_EUNSUPPORTED, "explicit terms of a field share one power");
         f.power = p;
         for (int m = 0; m < n_mono; ++m) f.rhs.push_back({param_ids ? param_ids[m] : -1, scales[m], q2_pows[m]});
@@ -1350,24 +1454,57 @@ int pss_add_term(pss_system *s, int field_id, int implicit, int n_mono, const in
     return PSS_OK;
 }
 
-int pss_add_grad_sq_term(pss_system *s, int field_id, int n_mono, const int *param_ids, const double *scales,
-                         const int *q2_pows) {
-    int rc = check_field(s, field_id);
-    if (rc) return rc;
+int check_monos(pss_system *s, int n_mono, const int *param_ids, const double *scales, const int *q2_pows) {
     if (n_mono < 1 || n_mono > 8 || !scales || !q2_pows) return fail(s, PSS_EINVAL, "need 1..8 monomials");
     for (int m = 0; m < n_mono; ++m) {
         if (q2_pows[m] < 0 || q2_pows[m] >= kPolyTerms) return fail(s, PSS_EINVAL, "q^2 power must be in [0, 4]");
         const int pid = param_ids ? param_ids[m] : -1;
         if (pid >= (int)s->param_names.size()) return fail(s, PSS_EINVAL, "no parameter %d", pid);
     }
-    Field &f = s->fields[field_id];
-    if (f.power != 0 && !f.grad2) return fail(s, PSS_EUNSUPPORTED, "the field already has a power product");
-    f.grad2 = true;
-    f.power = 2;
-    for (int m = 0; m < n_mono; ++m) f.rhs.push_back({param_ids ? param_ids[m] : -1, scales[m], q2_pows[m]});
+    return PSS_OK;
+}
+
+int add_gterm(pss_system *s, GTerm t) {
+    s->gterms.push_back(std::move(t));
+    s->fields[s->gterms.back().target].general = true;
     s->stale = true;
     s->fps_dirty = true;
     invalidate(s);
+    return PSS_OK;
+}
+
+int pss_add_product_term(pss_system *s, int field_id, int n_mono, const int *param_ids, const double *scales,
+                         const int *q2_pows, int n_factors, const int *factor_fields, const int *powers,
+                         const int *derivs, const int *laps) {
+    int rc = check_field(s, field_id);
+    if (rc) return rc;
+    if ((rc = check_monos(s, n_mono, param_ids, scales, q2_pows))) return rc;
+    if (n_factors < 1 || n_factors > 8 || !factor_fields || !powers)
+        return fail(s, PSS_EINVAL, "need 1..8 factors");
+    GTerm t{field_id, {}, {}};
+    for (int m = 0; m < n_mono; ++m) t.M.push_back({param_ids ? param_ids[m] : -1, scales[m], q2_pows[m]});
+    for (int k = 0; k < n_factors; ++k) {
+        const int fld = factor_fields[k], pw = powers[k], d = derivs ? derivs[k] : -1, l = laps ? laps[k] : 0;
+        if (fld < 0 || fld >= (int)s->fields.size()) return fail(s, PSS_EINVAL, "no field %d", fld);
+        if (pw < 1 || pw > 4) return fail(s, PSS_EINVAL, "factor powers are 1..4");
+        if (d < -1 || d >= s->dim) return fail(s, PSS_EINVAL, "derivative axis must be -1 or 0..dim-1");
+        if (l < 0 || l > 2) return fail(s, PSS_EINVAL, "Laplacian powers are 0..2");
+        t.factors.push_back({fld, pw, d, l});
+    }
+    return add_gterm(s, std::move(t));
+}
+
+int pss_add_grad_sq_term(pss_system *s, int field_id, int n_mono, const int *param_ids, const double *scales,
+                         const int *q2_pows) {
+    int rc = check_field(s, field_id);
+    if (rc) return rc;
+    if ((rc = check_monos(s, n_mono, param_ids, scales, q2_pows))) return rc;
+    // sum_j (d_j phi)^2: one term per axis, all with the same operator
+    for (int j = 0; j < s->dim; ++j) {
+        GTerm t{field_id, {}, {{field_id, 2, j, 0}}};
+        for (int m = 0; m < n_mono; ++m) t.M.push_back({param_ids ? param_ids[m] : -1, scales[m], q2_pows[m]});
+        add_gterm(s, std::move(t));
+    }
     return PSS_OK;
 }
 
@@ -1493,7 +1630,7 @@ int pss_adjoint_forward(pss_system *s, int64_t n) {
     if (n < 1) return fail(s, PSS_EINVAL, "n must be >= 1");
     if (s->nslots() != 1) return fail(s, PSS_EUNSUPPORTED, "the adjoint needs one field and batch 1 in this build");
     if (round_trip(s)) return fail(s, PSS_EUNSUPPORTED, "the adjoint has no boundary frames or real-space round trip");
-    if (any_grad2(s)) return fail(s, PSS_EUNSUPPORTED, "the adjoint covers power products only");
+    if (any_general(s)) return fail(s, PSS_EUNSUPPORTED, "the adjoint covers power products only");
     int64_t K = (int64_t)std::ceil(std::sqrt((double)n));
     const int64_t nck = (n + K - 1) / K;
     int rc = adj_alloc(s, nck, K);

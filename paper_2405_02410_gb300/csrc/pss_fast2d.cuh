@@ -246,8 +246,8 @@ __global__ void __launch_bounds__(E == 8 ? 1024 : E == 16 ? 768 : 512, 1) k2_col
         if (with_noise) bulk_g2s(XI, a.noise + sofs, chunk, bar);
     }
     static_assert(sizeof(FieldP<float>) % 4 == 0, "FieldP is copied as 32-bit words");
-    if (t < (int)(sizeof(FieldP<float>) / 4))
-        reinterpret_cast<uint32_t *>(&sfp)[t] = reinterpret_cast<const uint32_t *>(&a.fps[slot])[t];
+    for (int i = t; i < (int)(sizeof(FieldP<float>) / 4); i += (int)blockDim.x)   // CTAs may be smaller than FieldP
+        reinterpret_cast<uint32_t *>(&sfp)[i] = reinterpret_cast<const uint32_t *>(&a.fps[slot])[i];
     __syncthreads();   // the barrier is initialised, the parameters are in place
     const bool ok = mbar_poll(bar, 0);
 

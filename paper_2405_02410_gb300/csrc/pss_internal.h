@@ -49,6 +49,7 @@ template <typename T> struct FieldP {
     int noise_pow;        // D~ = D (q^2)^noise_pow
     int noisy;
     int power;            // product (phi^d)^power; 0 = no explicit term
+    int spectral;         // the column kernel gets the product transformed along every axis (product terms)
     int kmax[3];          // largest kept |k| per axis of the de-alias mask
     int kx_cols;          // kept half-spectrum columns (kmax[0] + 1, at most Nx/2 + 1)
     int field_id;         // Philox counter word 2
@@ -183,10 +184,17 @@ cudaError_t launch_col2(const ColArgs<float> &a, int nslots, int ntiles, cudaStr
 cudaError_t launch_row2(const RowArgs<float> &a, int nslots, cudaStream_t st, bool tiled);
 template <typename T> cudaError_t launch_init_uniform(T *real, long long nsites, double lo, double hi,
                                                       uint64_t seed, int field_id, cudaStream_t st);
+// product terms through real space: op(q) m phi of one slot, one real factor,
+// and Q += M(q) Pt (m[0..4] the coefficients of M in q^2)
 template <typename T>
-cudaError_t launch_grad_spectrum(const SysP<T> &sp, const FieldP<T> *fps, int slot, size_t slot_stride,
-                                 const cplx<T> *in, cplx<T> *out, int axis, cudaStream_t st);
-template <typename T> cudaError_t launch_square_acc(T *acc, const T *r, long long n, int first, cudaStream_t st);
+cudaError_t launch_op_spectrum(const SysP<T> &sp, const FieldP<T> *fps, int mask_slot, const cplx<T> *src,
+                               cplx<T> *dst, int deriv, int lap, cudaStream_t st);
+template <typename T>
+cudaError_t launch_factor(T *acc, T *tp, const T *r, long long n, int power, int first_factor, int last_factor,
+                          int first_term, cudaStream_t st);
+template <typename T>
+cudaError_t launch_combine(const SysP<T> &sp, cplx<T> *Q, const cplx<T> *Pt, const double *m, int first,
+                           cudaStream_t st);
 template <typename T> cudaError_t launch_frame(T *real, int nx, long long rows, int width, double lo, double hi,
                                                cudaStream_t st);
 template <typename T> cudaError_t launch_tiles_to_half(const SysP<T> &sp, const cplx<T> *tiles,

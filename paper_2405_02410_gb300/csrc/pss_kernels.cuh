@@ -386,8 +386,8 @@ __global__ void __launch_bounds__(512, (N >= 512 || ADJ) ? 1 : 2) k_col(const Co
         }
     }
     static_assert(sizeof(FieldP<T>) % 4 == 0, "FieldP is copied as 32-bit words");
-    if (t < (int)(sizeof(FieldP<T>) / 4))
-        reinterpret_cast<uint32_t *>(&sfp)[t] = reinterpret_cast<const uint32_t *>(&a.fps[slot])[t];
+    for (int i = t; i < (int)(sizeof(FieldP<T>) / 4); i += (int)blockDim.x)   // CTAs may be smaller than FieldP
+        reinterpret_cast<uint32_t *>(&sfp)[i] = reinterpret_cast<const uint32_t *>(&a.fps[slot])[i];
     if (t == 0) sstep = (uint32_t)(*a.d_step);
     __syncthreads();   // the barrier is initialised before anyone polls it
     for (int i = nvalid * (N * W) + t; i < nchunks * (N * W); i += nthr) {   // chunks past the last tile read as zero
@@ -410,9 +410,21 @@ __global__ void __launch_bounds__(512, (N >= 512 || ADJ) ? 1 : 2) k_col(const Co
         // or [W][pos] for a column-major input)
         const int xstride = a.in_colmajor ? 1 : W;
         const C *xb = X + ch * CS + (a.in_colmajor ? c * N : c);
-        const int which = fft_run<T, N, EMAX, -1>([&](int p) { return xb[p * xstride]; },
+        int which = 0;
+        if (!ADJ && mode == COL_STEP && fp.spectral) {
+            // the product arrives transformed along every axis (several product
+            // terms with different operators, summed in Fourier space): only
+            // its layout changes
+#pragma unroll 1
+            for (int i = t; i < N * F; i += nthr) {
+                const int ff = i & (F - 1), pos = i >> logF;
+                Y[ff * SF + spad(pos)] = X[(ff >> 2) * CS + pos * W + (ff & 3)];
+            }
+        } else {
+            which = fft_run<T, N, EMAX, -1>([&](int p) { return xb[p * xstride]; },
                                             [&](int p, C v, C *fr) { fr[spad(p)] = v; },
                                             Y + f * SF, X + f * SF, lane, active, tw);
+        }
         __syncthreads();
         const C *P = which == 0 ? Y : X;
         if constexpr (ADJ) {
@@ -820,16 +832,16 @@ __global__ void k_init_uniform(T *real, long long nsites, T lo, T hi, uint32_t s
     }
 }
 
-// i q_j m phi of one slot (tiled in, tiled out): the derivative along axis j of
-// the de-aliased field, one factor psi_j of a KPZ-type term |grad(m phi)|^2.
-// q_j of a Nyquist index is 0, so that the derivative of a real field is real.
+// op(q) m phi of one slot (tiled in, tiled out), op(q) = (i q_deriv if deriv >=
+// 0) (-q^2)^lap: one factor psi of a product term (the field acted on by a
+// differential operator), with the mask of the source field's slot.  q of a
+// Nyquist index is 0 in the first derivative, so that a real field's
+// derivative stays real.
 template <typename T>
-__global__ void k_grad_spectrum(const SysP<T> sp, const FieldP<T> *fps, int slot, size_t slot_stride,
-                                const cplx<T> *in, cplx<T> *out, int axis) {
-    const FieldP<T> &fp = fps[slot];
+__global__ void k_op_spectrum(const SysP<T> sp, const FieldP<T> *fps, int mask_slot, const cplx<T> *src,
+                              cplx<T> *dst, int deriv, int lap) {
+    const FieldP<T> &fp = fps[mask_slot];
     const long long n = (long long)sp.ntiles * sp.rows * W;
-    const cplx<T> *src = in + (size_t)slot * slot_stride;
-    cplx<T> *dst = out + (size_t)slot * slot_stride;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
         const int c = (int)(i % W);
@@ -840,21 +852,59 @@ __global__ void k_grad_spectrum(const SysP<T> sp, const FieldP<T> *fps, int slot
         const int kz = sp.dim == 3 ? row % sp.nz : 0;
         const int sky = signed_k(ky, sp.ny), skz = signed_k(kz, sp.nz);
         const bool keep = kx < sp.hx && kx <= fp.kmax[0] && abs(sky) <= fp.kmax[1] && abs(skz) <= fp.kmax[2];
-        T q;
-        if (axis == 0) q = 2 * kx == sp.nx ? T(0) : T(kx) * sp.gx;
-        else if (axis == 1) q = 2 * ky == sp.ny ? T(0) : T(sky) * sp.gy;
-        else q = 2 * kz == sp.nz ? T(0) : T(skz) * sp.gz;
+        const T qx = T(kx) * sp.gx, qy = T(sky) * sp.gy, qz = T(skz) * sp.gz;
+        T f = T(1);
+        for (int l = 0; l < lap; ++l) f *= -(qx * qx + qy * qy + qz * qz);
         const cplx<T> v = src[i];
-        dst[i] = keep ? mk<T>(-q * v.y, q * v.x) : mk<T>(0, 0);
+        cplx<T> o;
+        if (deriv >= 0) {
+            T q;
+            if (deriv == 0) q = 2 * kx == sp.nx ? T(0) : qx;
+            else if (deriv == 1) q = 2 * ky == sp.ny ? T(0) : qy;
+            else q = 2 * kz == sp.nz ? T(0) : qz;
+            o = mk<T>(-q * f * v.y, q * f * v.x);
+        } else {
+            o = mk<T>(f * v.x, f * v.y);
+        }
+        dst[i] = keep ? o : mk<T>(0, 0);
     }
 }
 
-// acc = (first ? 0 : acc) + r^2 over a real field
-template <typename T> __global__ void k_square_acc(T *acc, const T *r, long long n, int first) {
+// One factor psi^power of a product term in real space: the running product tp
+// (the first factor starts it); the last factor adds the term to acc (the
+// first term of a sum starts it).
+template <typename T>
+__global__ void k_factor(T *acc, T *tp, const T *r, long long n, int power, int first_factor, int last_factor,
+                         int first_term) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
-        const T v = r[i];
-        acc[i] = first ? v * v : acc[i] + v * v;
+        const T x = r[i];
+        T v = x;
+        for (int p = 1; p < power; ++p) v *= x;
+        const T t = first_factor ? v : tp[i] * v;
+        if (last_factor) acc[i] = first_term ? t : acc[i] + t;
+        else tp[i] = t;
+    }
+}
+
+// Q = (first ? 0 : Q) + M(q) Pt over one slot's tiled spectrum, M(q) = sum_p m_p (q^2)^p
+template <typename T>
+__global__ void k_combine(const SysP<T> sp, cplx<T> *Q, const cplx<T> *Pt, T m0, T m1, T m2, T m3, T m4, int first) {
+    const long long n = (long long)sp.ntiles * sp.rows * W;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(i % W);
+        const long long tr = i / W;
+        const int row = (int)(tr % sp.rows), tile = (int)(tr / sp.rows);
+        const int kx = tile * W + c;
+        const int ky = sp.dim == 3 ? row / sp.nz : (sp.dim == 2 ? row : 0);
+        const int kz = sp.dim == 3 ? row % sp.nz : 0;
+        const T qx = T(kx) * sp.gx, qy = T(signed_k(ky, sp.ny)) * sp.gy, qz = T(signed_k(kz, sp.nz)) * sp.gz;
+        const T q2 = qx * qx + qy * qy + qz * qz;
+        const T M = m0 + q2 * (m1 + q2 * (m2 + q2 * (m3 + q2 * m4)));
+        const cplx<T> p = Pt[i];
+        const cplx<T> base = first ? mk<T>(0, 0) : Q[i];
+        Q[i] = kx < sp.hx ? mk<T>(base.x + M * p.x, base.y + M * p.y) : mk<T>(0, 0);
     }
 }
 
@@ -1091,20 +1141,31 @@ cudaError_t launch_init_uniform(T *real, long long nsites, double lo, double hi,
     return cudaGetLastError();
 }
 
-template <typename T>
-cudaError_t launch_grad_spectrum(const SysP<T> &sp, const FieldP<T> *fps, int slot, size_t slot_stride,
-                                 const cplx<T> *in, cplx<T> *out, int axis, cudaStream_t st) {
-    const long long n = (long long)sp.ntiles * sp.rows * W;
+static inline int aux_blocks(long long n) {
     long long blocks = (n + 255) / 256;
-    if (blocks > 65535) blocks = 65535;
-    k_grad_spectrum<T><<<(int)blocks, 256, 0, st>>>(sp, fps, slot, slot_stride, in, out, axis);
+    return (int)(blocks > 65535 ? 65535 : (blocks < 1 ? 1 : blocks));
+}
+
+template <typename T>
+cudaError_t launch_op_spectrum(const SysP<T> &sp, const FieldP<T> *fps, int mask_slot, const cplx<T> *src,
+                               cplx<T> *dst, int deriv, int lap, cudaStream_t st) {
+    k_op_spectrum<T><<<aux_blocks((long long)sp.ntiles * sp.rows * W), 256, 0, st>>>(sp, fps, mask_slot, src, dst,
+                                                                                       deriv, lap);
     return cudaGetLastError();
 }
 
-template <typename T> cudaError_t launch_square_acc(T *acc, const T *r, long long n, int first, cudaStream_t st) {
-    long long blocks = (n + 255) / 256;
-    if (blocks > 65535) blocks = 65535;
-    k_square_acc<T><<<(int)blocks, 256, 0, st>>>(acc, r, n, first);
+template <typename T>
+cudaError_t launch_factor(T *acc, T *tp, const T *r, long long n, int power, int first_factor, int last_factor,
+                          int first_term, cudaStream_t st) {
+    k_factor<T><<<aux_blocks(n), 256, 0, st>>>(acc, tp, r, n, power, first_factor, last_factor, first_term);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_combine(const SysP<T> &sp, cplx<T> *Q, const cplx<T> *Pt, const double *m, int first,
+                           cudaStream_t st) {
+    k_combine<T><<<aux_blocks((long long)sp.ntiles * sp.rows * W), 256, 0, st>>>(
+        sp, Q, Pt, T(m[0]), T(m[1]), T(m[2]), T(m[3]), T(m[4]), first);
     return cudaGetLastError();
 }
 
@@ -1161,9 +1222,11 @@ cudaError_t launch_structure_factor(const SysP<T> &sp, const double dx[3], const
     template cudaError_t launch_init_uniform<T>(T *, long long, double, double, uint64_t, int, cudaStream_t); \
     template cudaError_t launch_tiles_to_half<T>(const SysP<T> &, const cplx<T> *, cplx<T> *, cudaStream_t); \
     template cudaError_t launch_frame<T>(T *, int, long long, int, double, double, cudaStream_t);              \
-    template cudaError_t launch_grad_spectrum<T>(const SysP<T> &, const FieldP<T> *, int, size_t, const cplx<T> *, \
-                                                 cplx<T> *, int, cudaStream_t);                                  \
-    template cudaError_t launch_square_acc<T>(T *, const T *, long long, int, cudaStream_t);                  \
+    template cudaError_t launch_op_spectrum<T>(const SysP<T> &, const FieldP<T> *, int, const cplx<T> *,       \
+                                               cplx<T> *, int, int, cudaStream_t);                              \
+    template cudaError_t launch_factor<T>(T *, T *, const T *, long long, int, int, int, int, cudaStream_t);   \
+    template cudaError_t launch_combine<T>(const SysP<T> &, cplx<T> *, const cplx<T> *, const double *, int,  \
+                                           cudaStream_t);                                                   \
     template cudaError_t launch_half_to_tiles<T>(const SysP<T> &, const cplx<T> *, cplx<T> *, cudaStream_t); \
     template cudaError_t launch_segment_begin<T>(cplx<T> *, const cplx<T> *, size_t, const long long *, long long, \
                                                  long long, long long *, long long *, cudaStream_t);             \

@@ -30,6 +30,7 @@ EXPORTS = [
     "pss_time_kernels", "pss_set_tuning", "pss_create_batch", "pss_batch_size", "pss_select_instance",
     "pss_set_param_batch", "pss_step_many", "pss_adjoint_forward", "pss_adjoint_backward",
     "pss_structure_factor_noalloc", "pss_step_path", "pss_set_frame", "pss_add_grad_sq_term",
+    "pss_add_product_term",
 ]
 
 
@@ -55,6 +56,7 @@ def _load():
         "pss_add_field": ([vp, ctypes.c_char_p, i32, P(i32)], i32),
         "pss_add_term": ([vp, i32, i32, i32, P(i32), P(d), P(i32), i32, P(i32), P(i32)], i32),
         "pss_add_grad_sq_term": ([vp, i32, i32, P(i32), P(d), P(i32)], i32),
+        "pss_add_product_term": ([vp, i32, i32, P(i32), P(d), P(i32), i32, P(i32), P(i32), P(i32), P(i32)], i32),
         "pss_set_noise": ([vp, i32, i32, i32], i32),
         "pss_set_dealias": ([vp, i32, i32], i32),
         "pss_set_frame": ([vp, i32, i32, d, d], i32),
@@ -194,6 +196,20 @@ class System:
                                           _arr(ctypes.c_int, [m[0] for m in mono]),
                                           _arr(ctypes.c_double, [float(m[1]) for m in mono]),
                                           _arr(ctypes.c_int, [int(m[2]) for m in mono])))
+
+    def add_product_term(self, field: int, monomials: Iterable, factors: Iterable):
+        """rhs term M(q) F[prod_k psi_k^n_k]; monomials: (param_id or -1, scale, q2_power);
+        factors: (field_id, power[, deriv axis or -1[, laplacian power]])."""
+        mono = list(monomials)
+        fac = [tuple(f) + (-1, 0)[len(f) - 2:] if len(f) < 4 else tuple(f) for f in factors]
+        self._ck(lib.pss_add_product_term(self._h, field, len(mono),
+                                          _arr(ctypes.c_int, [m[0] for m in mono]),
+                                          _arr(ctypes.c_double, [float(m[1]) for m in mono]),
+                                          _arr(ctypes.c_int, [int(m[2]) for m in mono]),
+                                          len(fac), _arr(ctypes.c_int, [f[0] for f in fac]),
+                                          _arr(ctypes.c_int, [f[1] for f in fac]),
+                                          _arr(ctypes.c_int, [f[2] for f in fac]),
+                                          _arr(ctypes.c_int, [f[3] for f in fac])))
 
     def set_noise(self, field: int, D_param: int, q2_pow: int = 0):
         self._ck(lib.pss_set_noise(self._h, field, D_param, q2_pow))

@@ -111,6 +111,19 @@ def test_kpz_launches_and_limits():
     with pytest.raises(P.PssError) as ei:
         s.adjoint_forward(4)
     assert ei.value.code == P.PSS_EUNSUPPORTED
-    with pytest.raises(P.PssError) as ei:
-        s.add_term(0, False, [(-1, 1.0, 0)], [(0, 3)])
-    assert ei.value.code == P.PSS_EUNSUPPORTED
+
+
+
+def test_kpz_with_a_cubic_term():
+    # a power product beside the gradient square: both go through real space,
+    # in two operator groups
+    shape, steps = (64, 64), 25
+    s = pss().kpz(shape, seed=8, precision="f64", **KW)
+    s.add_term(0, False, [(-1, -0.3, 0)], [(0, 3)])
+    s.init_uniform(0, -0.5, 0.5)
+    s.step(steps)
+    m = O.kpz(shape, seed=8, **KW)
+    terms = [O.Term(0, [(KW["lam"], 0)], [O.Factor(0, 2, deriv=j)]) for j in (0, 1)]
+    terms.append(O.Term(0, [(-0.3, 0)], [O.Factor(0, 3)]))
+    ref = O.run_coupled([m], terms, [O.to_spectrum(m, O.init_uniform(m, -0.5, 0.5))], 0, steps)[0]
+    assert rel(s.get_spectrum(0), O.half(ref)) < 1e-10
