@@ -402,6 +402,29 @@ def variants_measurement(pss, torch, stream, ms_default_1024):
     out["kpz_1024"] = {"ms_per_step": ms, "site_steps_per_s": 1024 ** 2 / (ms * 1e-3),
                        "launches_per_step": (s.launch_count - l0) / 320, "path": s.step_path}
     s.close()
+    # general product terms: a conserved field phi and a non-conserved psi coupled
+    # by phi psi^2 and phi^2 psi (two operators on phi), 1024^2, FP32
+    s = pss.System((1024, 1024), dt=0.01, seed=w["seed"], precision="f32")
+    f0, f1 = s.add_field("phi"), s.add_field("psi")
+    pa, pK, pb, pg, pc, pL, ph, pD0, pD1 = (s.add_param(k, v) for k, v in (
+        ("a", -1.0), ("K", 1.0), ("b", 1.0), ("g", 0.5), ("c", 0.3), ("L", 1.0), ("h", 0.7), ("D0", 0.01),
+        ("D1", 0.01)))
+    s.add_term(f0, True, [(pa, 1.0, 1), (pK, 1.0, 2)], [(f0, 1)])
+    s.add_term(f0, False, [(pb, -1.0, 1)], [(f0, 3)])
+    s.add_product_term(f0, [(pg, -1.0, 1)], [(f0, 1), (f1, 2)])
+    s.add_term(f1, True, [(pc, 1.0, 0), (pL, 1.0, 1)], [(f1, 1)])
+    s.add_product_term(f1, [(ph, -1.0, 0)], [(f0, 2), (f1, 1)])
+    s.set_noise(f0, pD0, 1)
+    s.set_noise(f1, pD1, 0)
+    s.set_stream(stream)
+    s.init_uniform(0, -0.1, 0.1)
+    s.init_uniform(1, -0.1, 0.1)
+    l0 = s.launch_count
+    ms = _timed_steps(torch, stream, s, 200)
+    out["coupled_pair_1024"] = {"ms_per_step_two_fields": ms,
+                                "site_steps_per_s_per_field": 2 * 1024 ** 2 / (ms * 1e-3),
+                                "launches_per_step": (s.launch_count - l0) / 220}
+    s.close()
     res = {}
     for order in (2, 3):
         s3 = pss.System((256, 256, 256), dt=0.005, seed=w["seed"], precision="f32")
