@@ -235,19 +235,24 @@ __global__ void __launch_bounds__(E == 8 ? 1024 : E == 16 ? 768 : 512, 1) k2_col
     const bool step_mode = a.mode == COL_STEP;
     const bool with_noise = step_mode && a.noise != nullptr;
     const uint32_t chunk = (uint32_t)(4 * N * sizeof(C));
-    pdl_wait();
-    pdl_trigger();
+    // what no earlier kernel writes (roots of unity, parameters) is fetched
+    // before the wait on the previous launch, so that with programmatic
+    // dependent launch it overlaps that launch's tail
     if (t == 0) {
         mbar_init(bar, 1);
         mbar_expect_tx(bar, (uint32_t)(N * sizeof(C)) + chunk * (step_mode ? (with_noise ? 3u : 2u) : 1u));
         bulk_g2s(TW, a.tw + twiddle_offset(N, E), (uint32_t)(N * sizeof(C)), bar);
-        bulk_g2s(PHI, a.state + sofs, chunk, bar);
-        if (step_mode) bulk_g2s(XIN, a.in + sofs, chunk, bar);
-        if (with_noise) bulk_g2s(XI, a.noise + sofs, chunk, bar);
     }
     static_assert(sizeof(FieldP<float>) % 4 == 0, "FieldP is copied as 32-bit words");
     for (int i = t; i < (int)(sizeof(FieldP<float>) / 4); i += (int)blockDim.x)   // CTAs may be smaller than FieldP
         reinterpret_cast<uint32_t *>(&sfp)[i] = reinterpret_cast<const uint32_t *>(&a.fps[slot])[i];
+    pdl_wait();
+    pdl_trigger();
+    if (t == 0) {
+        bulk_g2s(PHI, a.state + sofs, chunk, bar);
+        if (step_mode) bulk_g2s(XIN, a.in + sofs, chunk, bar);
+        if (with_noise) bulk_g2s(XI, a.noise + sofs, chunk, bar);
+    }
     __syncthreads();   // the barrier is initialised, the parameters are in place
     const bool ok = mbar_poll(bar, 0);
 
@@ -454,13 +459,21 @@ __global__ void __launch_bounds__(E == 32 ? 512 : 1024) k2_row(const RowArgs<flo
     const int r0 = blockIdx.x * 2 * NW;                                                  // first row of the CTA
     const size_t sofs = (size_t)slot * a.slot_stride + (size_t)r0 * (TILED ? 4 : 1);
     constexpr int H = N / 2 + 1;
+    const int nrow_cta = (int)gridDim.x - a.noise_ctas;
+    const bool noise_thread = (int)blockIdx.x >= nrow_cta || t >= nf;
+    // roots of unity: one bulk copy, issued before the wait on the previous
+    // launch (no kernel writes them) and in flight while the rows are loaded
+    if (!noise_thread && t == 0) {
+        mbar_init(bar, 1);
+        mbar_expect_tx(bar, (uint32_t)(N * sizeof(C)));
+        bulk_g2s(TW, a.tw + twiddle_offset(N, E), (uint32_t)(N * sizeof(C)), bar);
+    }
     pdl_wait();
     pdl_trigger();
     // ---- noise: the next step's, split between the extra noise CTAs (the
     // first noise_share/64 of the pairs, every thread) and the noise warps of
     // the row CTAs (the rest)
-    const int nrow_cta = (int)gridDim.x - a.noise_ctas;
-    if ((int)blockIdx.x >= nrow_cta || t >= nf) {
+    if (noise_thread) {
         const FieldP<float> &fp = a.fps[slot];
         if (a.noise && fp.noisy) {
             const int Q = sp.ntiles * sp.ny * 2;
@@ -482,12 +495,6 @@ __global__ void __launch_bounds__(E == 32 ? 512 : 1024) k2_row(const RowArgs<flo
             if (n > 0) noise_range(sp, fp, (uint32_t)(*a.d_step), a.noise + (size_t)slot * a.slot_stride, q0 + i, q1, n);
         }
         return;
-    }
-    // roots of unity: one bulk copy, in flight while the rows are loaded
-    if (t == 0) {
-        mbar_init(bar, 1);
-        mbar_expect_tx(bar, (uint32_t)(N * sizeof(C)));
-        bulk_g2s(TW, a.tw + twiddle_offset(N, E), (uint32_t)(N * sizeof(C)), bar);
     }
     // ---- stage Y = conj(Z), Z_k = A_k + i B_k (k <= N/2), conj(A_{N-k}) +
     // i conj(B_{N-k}) above, into the second buffer of group j.  With

@@ -73,7 +73,7 @@ def test_matches_generic_kernels(shape):
 
 @pytest.mark.parametrize("knobs", [dict(col2_warps=1), dict(col2_warps=4), dict(col2_warps=16),
                                    dict(row2_pairs=1), dict(row2_pairs=4), dict(row2_pairs=8),
-                                   dict(pdl=1), dict(graph_steps=3, row2_pairs=1, col2_warps=2),
+                                   dict(pdl=1), dict(pdl=0), dict(graph_steps=3, row2_pairs=1, col2_warps=2),
                                    dict(row2_share=0), dict(row2_share=100), dict(row2_share=30, row2_noise=2)])
 def test_launch_shapes_do_not_change_bits(knobs):
     shape = (512, 256)
