@@ -433,6 +433,11 @@ template <typename T> struct Seq {
     cudaStream_t st;
     int slot0, nslots;
     Timer *timer = nullptr;
+    // a product-term factor in flight: the column inverse applies op(q), the
+    // row inverse folds r^n into the term's product instead of storing r
+    int op_on = 0, op_deriv = -1, op_lap = 0;
+    T *fac_acc = nullptr, *fac_tp = nullptr;
+    int fac_power = 1, fac_first_factor = 1, fac_last_factor = 1, fac_first_term = 1;
 
     cplx<T> *state() const { return (cplx<T> *)s->state; }
     cplx<T> *A() const { return (cplx<T> *)s->A; }
@@ -458,6 +463,9 @@ template <typename T> struct Seq {
         a.in_colmajor = (mode == COL_ADJ_A && fast2d(s)) ? 1 : 0;   // the product the fast path recomputed
         a.in2 = in2;
         a.in2_colmajor = fast2d(s) ? 1 : 0;
+        a.op_on = op_on;
+        a.op_deriv = op_deriv;
+        a.op_lap = op_lap;
         a.slot_stride = s->field_elems;
         a.slot0 = slot0;
         a.tw = (const cplx<T> *)s->tw;
@@ -504,6 +512,12 @@ template <typename T> struct Seq {
         a.kx_cols_max = 0;
         for (int i = 0; i < (int)s->fields.size(); ++i) a.kx_cols_max = std::max(a.kx_cols_max, kept_cols(s, i));
         a.inc_step = inc ? 1 : 0;
+        a.fac_acc = fac_acc;
+        a.fac_tp = fac_tp;
+        a.fac_power = fac_power;
+        a.fac_first_factor = fac_first_factor;
+        a.fac_last_factor = fac_last_factor;
+        a.fac_first_term = fac_first_term;
         if (timer) timer->begin(2, st);
         cudaError_t e = launch_row<T>(a, nslots, st);
         if (timer) timer->begin(2, st);
@@ -699,29 +713,31 @@ template <typename T> struct Seq {
         const bool spectral = groups.size() > 1;
         const size_t stride = s->field_elems;
         cplx<T> *G = (cplx<T> *)s->GS;
-        T *acc = (T *)s->real_acc, *tp = (T *)s->real_tp, *r = (T *)s->real;
+        T *acc = (T *)s->real_acc, *tp = (T *)s->real_tp;
         for (size_t gi = 0; gi < groups.size(); ++gi) {
             const auto &g = groups[gi];
             for (size_t ti = 0; ti < g.size(); ++ti) {
                 const auto &fac = g[ti].factors;
                 for (size_t k = 0; k < fac.size(); ++k) {
-                    const int src = inst * nf + fac[k].field;
-                    e = launch_op_spectrum<T>(sys_params<T>(s), (const FieldP<T> *)s->fps, src,
-                                              state() + (size_t)src * stride, G + (size_t)slot0 * stride,
-                                              fac[k].deriv, fac[k].lap, st);
-                    s->launches++;
-                    if (e != cudaSuccess) return cuda_fail(s, e, "factor spectrum kernel");
-                    if ((rc = col_ptrs(COL_INV_FULL, G, nullptr, A(), nullptr, 0))) return rc;      // G -> A
+                    // the factor's field (same instance), kept modes times op(q), to
+                    // real space; its own slot of A (and of G in 3D) is scratch
+                    Seq<T> q{s, st, inst * nf + fac[k].field, 1};
+                    q.op_on = 1;
+                    q.op_deriv = fac[k].deriv;
+                    q.op_lap = fac[k].lap;
+                    q.fac_acc = acc;
+                    q.fac_tp = tp;
+                    q.fac_power = fac[k].power;
+                    q.fac_first_factor = k == 0;
+                    q.fac_last_factor = k + 1 == fac.size();
+                    q.fac_first_term = ti == 0;
+                    if ((rc = q.col_ptrs(COL_INV_MASK, q.state(), nullptr, q.A(), nullptr, 0))) return rc;   // -> A
                     if (s->dim == 3) {
-                        if ((rc = mid_ptrs(MID_INV_FULL, A(), G, false))) return rc;              // A -> G
-                        if ((rc = row_ptrs(ROW_C2R, G, A(), false, nullptr, r, 0))) return rc;   // G -> real
-                    } else if ((rc = row_ptrs(ROW_C2R, A(), B(), false, nullptr, r, 0))) {       // A -> real
+                        if ((rc = q.mid_ptrs(MID_INV_MASK, q.A(), G, false))) return rc;                   // A -> G
+                        if ((rc = q.row_ptrs(ROW_C2R_KEPT, G, q.A(), false, nullptr, nullptr, 0))) return rc;
+                    } else if ((rc = q.row_ptrs(ROW_C2R_KEPT, q.A(), q.B(), false, nullptr, nullptr, 0))) {
                         return rc;
                     }
-                    e = launch_factor<T>(acc, tp, r, s->nsites, fac[k].power, k == 0, k + 1 == fac.size(), ti == 0,
-                                         st);
-                    s->launches++;
-                    if (e != cudaSuccess) return cuda_fail(s, e, "factor kernel");
                 }
             }
             if (!spectral) {

@@ -112,6 +112,9 @@ template <typename T> struct ColArgs {
     // B part's), column-major like `in_colmajor` says
     const cplx<T> *in2;
     int in2_colmajor;
+    // COL_INV_MASK of a product-term factor: the kept modes times
+    // op(q) = (i q_op_deriv if op_deriv >= 0) (-q^2)^op_lap (op_on = 1)
+    int op_on, op_deriv, op_lap;
 };
 
 template <typename T> struct RowArgs {
@@ -133,6 +136,12 @@ template <typename T> struct RowArgs {
     int noise_warps;      // k2_row: warps that draw it beside the transform warps
     int noise_ctas;       // k2_row: extra CTAs (past the row CTAs) that only draw noise
     int noise_share;      // k2_row: the pairs those CTAs draw, out of 64 (the row CTAs draw the rest)
+    // ROW_C2R_KEPT of a product-term factor (fac_acc set): instead of storing
+    // the real rows r, fold r^fac_power into the running product fac_tp (the
+    // first factor starts it) and, at the term's last factor, add the
+    // product to fac_acc (the first term of a sum starts it)
+    T *fac_acc, *fac_tp;
+    int fac_power, fac_first_factor, fac_last_factor, fac_first_term;
 };
 
 template <typename T> struct MidArgs {
@@ -184,14 +193,8 @@ cudaError_t launch_col2(const ColArgs<float> &a, int nslots, int ntiles, cudaStr
 cudaError_t launch_row2(const RowArgs<float> &a, int nslots, cudaStream_t st, bool tiled);
 template <typename T> cudaError_t launch_init_uniform(T *real, long long nsites, double lo, double hi,
                                                       uint64_t seed, int field_id, cudaStream_t st);
-// product terms through real space: op(q) m phi of one slot, one real factor,
-// and Q += M(q) Pt (m[0..4] the coefficients of M in q^2)
-template <typename T>
-cudaError_t launch_op_spectrum(const SysP<T> &sp, const FieldP<T> *fps, int mask_slot, const cplx<T> *src,
-                               cplx<T> *dst, int deriv, int lap, cudaStream_t st);
-template <typename T>
-cudaError_t launch_factor(T *acc, T *tp, const T *r, long long n, int power, int first_factor, int last_factor,
-                          int first_term, cudaStream_t st);
+// product terms with several operators: Q = (first ? 0 : Q) + M(q) Pt over one
+// slot (m[0..4] the coefficients of M in q^2)
 template <typename T>
 cudaError_t launch_combine(const SysP<T> &sp, cplx<T> *Q, const cplx<T> *Pt, const double *m, int first,
                            cudaStream_t st);

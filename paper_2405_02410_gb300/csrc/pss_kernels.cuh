@@ -548,8 +548,28 @@ __global__ void __launch_bounds__(512, (N >= 512 || ADJ) ? 1 : 2) k_col(const Co
         const C *pb = PHI + ch * CS + c;
         const bool writes = chunk_writes(ch) && (full || my_tile * W <= fp.kmax[0]);
         C *__restrict__ dst = a.out + sofs + gofs(ch) + c;
+        // a product-term factor: op(q) = (i q_d) (-q^2)^l, q_d = 0 at a Nyquist index
+        const T gpos = sp.dim == 3 ? sp.gz : sp.gy;
+        const T qx = T(kx) * sp.gx, qo = sp.dim == 3 ? T(signed_k(my_o, sp.ny)) * sp.gy : T(0);
+        const int dpos = sp.dim == 3 ? 2 : 1;                    // the axis of this kernel's transform
+        auto op = [&](int p, C v) {
+            const T qp = T(signed_k(p, N)) * gpos;
+            const T qy = sp.dim == 3 ? qo : qp, qz = sp.dim == 3 ? qp : T(0);
+            T f = T(1);
+            for (int l = 0; l < a.op_lap; ++l) f *= -(qx * qx + qy * qy + qz * qz);
+            if (a.op_deriv < 0) return cscale<T>(v, f);
+            T q;
+            if (a.op_deriv == 0) q = 2 * kx == sp.nx ? T(0) : qx;
+            else if (a.op_deriv == dpos) q = 2 * p == N ? T(0) : qp;
+            else q = 2 * my_o == sp.ny ? T(0) : qo;              // y in 3D
+            return mk<T>(-q * f * v.y, q * f * v.x);
+        };
         fft_run<T, N, EMAX, +1>(
-            [&](int p) { return abs(signed_k(p, N)) <= kmax_pos ? cscale<T>(pb[p * W], scale) : mk<T>(0, 0); },
+            [&](int p) {
+                if (abs(signed_k(p, N)) > kmax_pos) return mk<T>(0, 0);
+                const C v = cscale<T>(pb[p * W], scale);
+                return a.op_on ? op(p, v) : v;
+            },
             [&](int p, C v, C *) {
                 if (writes) dst[p * W] = v;
             },
@@ -688,6 +708,21 @@ __global__ void __launch_bounds__(256) k_row(const RowArgs<T> a) {
         __syncthreads();
         C *Z = which == 0 ? B0 : B1;
         if (mode == ROW_C2R || mode == ROW_C2R_KEPT) {
+            if (a.fac_acc) {
+                // a product-term factor: r^n folded into the term's running product
+                const size_t ro = (size_t)slot * a.real_stride;
+#pragma unroll 1
+                for (int i = t; i < nrow * N; i += nthr) {
+                    const int rl = i / N, x = i - rl * N;
+                    const C z = Z[(rl & (G - 1)) * SF + spad(x)];
+                    const size_t idx = ro + real_row_offset(sp, r0 + rl) + x;
+                    const T v = ipow<T>(rl < G ? z.x : z.y, a.fac_power);
+                    const T tp = a.fac_first_factor ? v : a.fac_tp[idx] * v;
+                    if (a.fac_last_factor) a.fac_acc[idx] = a.fac_first_term ? tp : a.fac_acc[idx] + tp;
+                    else a.fac_tp[idx] = tp;
+                }
+                return;
+            }
             T *__restrict__ dst = a.real_out + (size_t)slot * a.real_stride;
 #pragma unroll 1
             for (int i = t; i < nrow * N; i += nthr) {
@@ -829,61 +864,6 @@ __global__ void k_init_uniform(T *real, long long nsites, T lo, T hi, uint32_t s
          i += (long long)gridDim.x * blockDim.x) {
         const u32x4 r = philox4x32_10(u32x4{(uint32_t)i, 0u, (uint32_t)field_id, 1u}, s0, s1);
         real[i] = lo + (hi - lo) * uniform24<T>(r.x);
-    }
-}
-
-// op(q) m phi of one slot (tiled in, tiled out), op(q) = (i q_deriv if deriv >=
-// 0) (-q^2)^lap: one factor psi of a product term (the field acted on by a
-// differential operator), with the mask of the source field's slot.  q of a
-// Nyquist index is 0 in the first derivative, so that a real field's
-// derivative stays real.
-template <typename T>
-__global__ void k_op_spectrum(const SysP<T> sp, const FieldP<T> *fps, int mask_slot, const cplx<T> *src,
-                              cplx<T> *dst, int deriv, int lap) {
-    const FieldP<T> &fp = fps[mask_slot];
-    const long long n = (long long)sp.ntiles * sp.rows * W;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
-        const int c = (int)(i % W);
-        const long long tr = i / W;
-        const int row = (int)(tr % sp.rows), tile = (int)(tr / sp.rows);
-        const int kx = tile * W + c;
-        const int ky = sp.dim == 3 ? row / sp.nz : (sp.dim == 2 ? row : 0);
-        const int kz = sp.dim == 3 ? row % sp.nz : 0;
-        const int sky = signed_k(ky, sp.ny), skz = signed_k(kz, sp.nz);
-        const bool keep = kx < sp.hx && kx <= fp.kmax[0] && abs(sky) <= fp.kmax[1] && abs(skz) <= fp.kmax[2];
-        const T qx = T(kx) * sp.gx, qy = T(sky) * sp.gy, qz = T(skz) * sp.gz;
-        T f = T(1);
-        for (int l = 0; l < lap; ++l) f *= -(qx * qx + qy * qy + qz * qz);
-        const cplx<T> v = src[i];
-        cplx<T> o;
-        if (deriv >= 0) {
-            T q;
-            if (deriv == 0) q = 2 * kx == sp.nx ? T(0) : qx;
-            else if (deriv == 1) q = 2 * ky == sp.ny ? T(0) : qy;
-            else q = 2 * kz == sp.nz ? T(0) : qz;
-            o = mk<T>(-q * f * v.y, q * f * v.x);
-        } else {
-            o = mk<T>(f * v.x, f * v.y);
-        }
-        dst[i] = keep ? o : mk<T>(0, 0);
-    }
-}
-
-// One factor psi^power of a product term in real space: the running product tp
-// (the first factor starts it); the last factor adds the term to acc (the
-// first term of a sum starts it).
-template <typename T>
-__global__ void k_factor(T *acc, T *tp, const T *r, long long n, int power, int first_factor, int last_factor,
-                         int first_term) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
-        const T x = r[i];
-        T v = x;
-        for (int p = 1; p < power; ++p) v *= x;
-        const T t = first_factor ? v : tp[i] * v;
-        if (last_factor) acc[i] = first_term ? t : acc[i] + t;
-        else tp[i] = t;
     }
 }
 
@@ -1147,21 +1127,6 @@ static inline int aux_blocks(long long n) {
 }
 
 template <typename T>
-cudaError_t launch_op_spectrum(const SysP<T> &sp, const FieldP<T> *fps, int mask_slot, const cplx<T> *src,
-                               cplx<T> *dst, int deriv, int lap, cudaStream_t st) {
-    k_op_spectrum<T><<<aux_blocks((long long)sp.ntiles * sp.rows * W), 256, 0, st>>>(sp, fps, mask_slot, src, dst,
-                                                                                       deriv, lap);
-    return cudaGetLastError();
-}
-
-template <typename T>
-cudaError_t launch_factor(T *acc, T *tp, const T *r, long long n, int power, int first_factor, int last_factor,
-                          int first_term, cudaStream_t st) {
-    k_factor<T><<<aux_blocks(n), 256, 0, st>>>(acc, tp, r, n, power, first_factor, last_factor, first_term);
-    return cudaGetLastError();
-}
-
-template <typename T>
 cudaError_t launch_combine(const SysP<T> &sp, cplx<T> *Q, const cplx<T> *Pt, const double *m, int first,
                            cudaStream_t st) {
     k_combine<T><<<aux_blocks((long long)sp.ntiles * sp.rows * W), 256, 0, st>>>(
@@ -1222,9 +1187,6 @@ cudaError_t launch_structure_factor(const SysP<T> &sp, const double dx[3], const
     template cudaError_t launch_init_uniform<T>(T *, long long, double, double, uint64_t, int, cudaStream_t); \
     template cudaError_t launch_tiles_to_half<T>(const SysP<T> &, const cplx<T> *, cplx<T> *, cudaStream_t); \
     template cudaError_t launch_frame<T>(T *, int, long long, int, double, double, cudaStream_t);              \
-    template cudaError_t launch_op_spectrum<T>(const SysP<T> &, const FieldP<T> *, int, const cplx<T> *,       \
-                                               cplx<T> *, int, int, cudaStream_t);                              \
-    template cudaError_t launch_factor<T>(T *, T *, const T *, long long, int, int, int, int, cudaStream_t);   \
     template cudaError_t launch_combine<T>(const SysP<T> &, cplx<T> *, const cplx<T> *, const double *, int,  \
                                            cudaStream_t);                                                   \
     template cudaError_t launch_half_to_tiles<T>(const SysP<T> &, const cplx<T> *, cplx<T> *, cudaStream_t); \

@@ -105,9 +105,10 @@ def test_kpz_launches_and_limits():
     s.step(1)
     l0 = s.launch_count
     s.step(40)
-    # column + row kernels (2), then per axis: derivative, column inverse,
-    # row inverse, square (4 x 2), and the row transform of the sum (1)
-    assert s.launch_count - l0 == 40 * 11
+    # column + row kernels (2), then per axis the column inverse of i q_j m h
+    # and the row inverse that adds its square (2 x 2), and the row transform
+    # of the sum (1)
+    assert s.launch_count - l0 == 40 * 7
     with pytest.raises(P.PssError) as ei:
         s.adjoint_forward(4)
     assert ei.value.code == P.PSS_EUNSUPPORTED
