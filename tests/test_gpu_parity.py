@@ -225,6 +225,27 @@ def test_model_b_1024_sampled_against_oracle():
     assert rel(s.get_spectrum(0), ref) < 1e-4
 
 
+def test_model_ab_256cubed_against_oracle():
+    # the 256^3 Model A + B pair in its timed launch configuration (FFT-group x
+    # pass), two steps, every mode of both fields checked
+    shape, steps = (256, 256, 256), 2
+    P = pss()
+    s = P.System(shape, dt=0.005, seed=2405, precision="f32")
+    P.add_model_a_field(s, a=-1, b=1, K=1, D=0.05, name="psi")
+    P.add_model_b_field(s, a=-1, b=1, K=1, D=0.05, name="phi")
+    assert s.step_path == "fast3d_rows"
+    s.init_uniform(0, -0.05, 0.05)
+    s.init_uniform(1, -0.05, 0.05)
+    s.step(steps)
+    ma = O.model_a(shape, dt=0.005, a=-1, b=1, K=1, D=0.05, seed=2405, field_id=0)
+    mb = O.model_b(shape, dt=0.005, a=-1, b=1, K=1, D=0.05, seed=2405, field_id=1)
+    for fid, m in ((0, ma), (1, mb)):
+        ref = O.half(O.run(m, O.to_spectrum(m, O.init_uniform(m, -0.05, 0.05)), 0, steps))
+        err = rel(s.get_spectrum(fid), ref)
+        assert err < 1e-4, (fid, err)
+        del ref
+
+
 @pytest.mark.parametrize("knobs", [
     dict(row_pairs=1), dict(row_pairs=2), dict(row_pairs=4), dict(row_pairs=8),
     dict(mid_planes=1), dict(mid_planes=2), dict(mid_planes=4), dict(col_tiles=2), dict(col_tiles=4),
