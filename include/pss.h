@@ -206,8 +206,9 @@ int pss_time_kernels(pss_system *s, int64_t n, double *avg_ms);
 
 /* Launch-shape tuning (results do not depend on it).  key / value:
  *   "pdl"         1 = launch the step kernels with programmatic dependent
- *                 launch, 0 = plain stream order; by default on for the FP32
- *                 2D path below ("fast2d"), off elsewhere;
+ *                 launch, 0 = plain stream order; by default on for the
+ *                 kernels of the FP32 2D step below ("fast2d"), off for the
+ *                 rest;
  *   "row_pairs"   row pairs per CTA of the x-transform kernel (power of two);
  *   "col_tiles"   column tiles per CTA of the fused column kernel;
  *   "mid_planes"  z planes per CTA of the 3D y-transform kernel;

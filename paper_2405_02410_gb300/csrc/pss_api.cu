@@ -176,8 +176,6 @@ int kmax_axis(int n, int order) {
 // kept half-spectrum columns kx = 0..kmax (never more than the nx/2+1 stored)
 int kept_cols(const pss_system *s, int fi) { return std::min(kmax_axis(s->nx, s->fields[fi].dealias) + 1, s->hx); }
 
-bool fast2d(const pss_system *s);
-
 template <typename T> SysP<T> sys_params(const pss_system *s) {
     SysP<T> p{};
     p.dim = s->dim;
@@ -191,13 +189,18 @@ template <typename T> SysP<T> sys_params(const pss_system *s) {
     p.gz = s->nz > 1 ? T(two_pi / (s->nz * s->dx[2])) : T(0);
     p.dt = T(s->dt);
     p.inv_nsites = T(1.0 / (double)s->nsites);
-    // programmatic dependent launch: measured on GB300, the FP32 2D path gains
-    // (1024^2 15.7 -> 15.3, 512^2 11.4 -> 10.2, 256^2 7.8 -> 6.7 us/step: its
-    // kernels fetch their roots of unity and parameters before the wait), the
-    // 3D pair loses (360 -> 378 us), so it is on for the former only
-    p.pdl = s->tune_pdl >= 0 ? s->tune_pdl : (fast2d(s) ? 1 : 0);
+    // programmatic dependent launch (tuning key "pdl"; by default only the
+    // FFT-group kernels k2_col / k2_row take it, see pdl_fast)
+    p.pdl = s->tune_pdl >= 0 ? s->tune_pdl : 0;
     return p;
 }
+
+// Programmatic dependent launch of the FFT-group kernels, measured on GB300:
+// the FP32 2D step gains (1024^2 15.7 -> 15.3, 512^2 11.4 -> 10.2, 256^2
+// 7.8 -> 6.7 us/step; those kernels fetch their roots of unity and parameters
+// before the wait), while the generic kernels lose (3D pair 360 -> 378 us,
+// the adjoint's column kernels), so by default it is on for the former only.
+int pdl_fast(const pss_system *s) { return s->tune_pdl >= 0 ? s->tune_pdl : 1; }
 
 double pval(const pss_system *s, int inst, int id) {
     return id < 0 ? 1.0 : s->param_values[(size_t)inst * s->param_names.size() + id];
@@ -560,6 +563,7 @@ template <typename T> struct Seq {
         if constexpr (std::is_same<T, float>::value) {
             ColArgs<float> a{};
             a.sp = sys_params<float>(s);
+            a.sp.pdl = pdl_fast(s);
             a.fps = (const FieldP<float> *)s->fps;
             a.in = in_ptr;
             a.out = out_ptr;
@@ -594,6 +598,7 @@ template <typename T> struct Seq {
         if constexpr (std::is_same<T, float>::value) {
             RowArgs<float> a{};
             a.sp = sys_params<float>(s);
+            a.sp.pdl = pdl_fast(s);
             a.fps = (const FieldP<float> *)s->fps;
             a.in = in_ptr;
             a.out = out_ptr;

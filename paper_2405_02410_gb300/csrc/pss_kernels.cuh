@@ -564,16 +564,20 @@ __global__ void __launch_bounds__(512, (N >= 512 || ADJ) ? 1 : 2) k_col(const Co
             else q = 2 * my_o == sp.ny ? T(0) : qo;              // y in 3D
             return mk<T>(-q * f * v.y, q * f * v.x);
         };
-        fft_run<T, N, EMAX, +1>(
-            [&](int p) {
-                if (abs(signed_k(p, N)) > kmax_pos) return mk<T>(0, 0);
-                const C v = cscale<T>(pb[p * W], scale);
-                return a.op_on ? op(p, v) : v;
-            },
-            [&](int p, C v, C *) {
-                if (writes) dst[p * W] = v;
-            },
-            X + f * SF, Y + f * SF, lane, active, tw);
+        auto sink = [&](int p, C v, C *) {
+            if (writes) dst[p * W] = v;
+        };
+        // two call sites, so that the step's inverse carries no per-element test
+        if (a.op_on)
+            fft_run<T, N, EMAX, +1>(
+                [&](int p) {
+                    return abs(signed_k(p, N)) <= kmax_pos ? op(p, cscale<T>(pb[p * W], scale)) : mk<T>(0, 0);
+                },
+                sink, X + f * SF, Y + f * SF, lane, active, tw);
+        else
+            fft_run<T, N, EMAX, +1>(
+                [&](int p) { return abs(signed_k(p, N)) <= kmax_pos ? cscale<T>(pb[p * W], scale) : mk<T>(0, 0); },
+                sink, X + f * SF, Y + f * SF, lane, active, tw);
     }
     if (need_in && t == 0) bulk_wait_read();   // PHI must outlive the state write-back
 }
