@@ -175,6 +175,13 @@ def max_over_ranks(x, world):
     return float(t.item())
 
 
+def whole_job_rate(units_per_rank, local_ms, world):
+    """(units of all ranks per second over the slowest rank's time, that time in ms): every rank
+    runs the same replica workload, so the job's units are world x one rank's."""
+    t_max = max_over_ranks(local_ms, world)
+    return units_per_rank * world / (t_max * 1e-3), t_max
+
+
 # ---------------------------------------------------------------------------
 # the CPU oracle leg
 # ---------------------------------------------------------------------------
@@ -254,10 +261,13 @@ def ensemble_systems(pss, n=512, gen_seed=2405, base_seed=10000):
     return systems, sites, {int(k): int((sizes == k).sum()) for k in (64, 128, 256, 512)}
 
 
-def ensemble_measurement(pss, torch, stream, steps=200):
+def ensemble_measurement(pss, torch, stream, steps=200, tune=True):
     systems, sites, counts = ensemble_systems(pss)
+    tuning = {}
     for s in systems:
         s.set_stream(stream)
+        if tune:
+            tuning[s.shape[0]] = s.autotune(16)
     pss.step_many(systems, 32)
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
@@ -276,6 +286,8 @@ def ensemble_measurement(pss, torch, stream, steps=200):
         one = pss.model_b((sz, sz), seed=1)
         one.set_stream(stream)
         one.init_uniform(0, -0.1, 0.1)
+        if tune:
+            one.autotune(16)
         one.step(32)
         f0 = torch.cuda.Event(enable_timing=True)
         f1 = torch.cuda.Event(enable_timing=True)
@@ -288,7 +300,8 @@ def ensemble_measurement(pss, torch, stream, steps=200):
     return {"instances": 512, "size_counts": counts, "sites": sites, "ms_per_step": ms,
             "site_steps_per_s": sites / (ms * 1e-3),
             "sequential_single_system_ms_per_step": seq_ms,
-            "speedup_vs_sequential": seq_ms / ms}
+            "speedup_vs_sequential": seq_ms / ms,
+            "autotuned": {str(k): v for k, v in tuning.items()} if tune else None}
 
 
 def cufft_comparison(torch, stream, shape=(1024, 1024), steps=2000, graph_steps=20):
@@ -538,6 +551,13 @@ def run_gpu(args):
     s.set_stream(stream)
     s.init_uniform(0, w["lo"], w["hi"])
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    # launch shapes chosen by the library's autotuner (state and step counter are left as they were),
+    # or given on the command line (to repeat a tuned run, e.g. under a profiler)
+    if args.tuning is not None:
+        tuning = {k: int(v) for k, v in (kv.split("=") for kv in args.tuning)}
+        s.set_tunings(tuning)
+    else:
+        tuning = None if args.no_autotune else s.autotune(64)
 
     # warm-up (graph capture, clocks)
     with torch.cuda.stream(stream):
@@ -569,8 +589,7 @@ def run_gpu(args):
     barrier(world)
     launches = s.launch_count - launches0
     s.sync()
-    t_max = max_over_ranks(total_ms, world)
-    value = sites * K * world / (t_max * 1e-3)
+    value, t_max = whole_job_rate(sites * K, total_ms, world)
     ms_per_step = t_max / K
 
     # per-kernel durations (CUDA events around each launch, same stream)
@@ -604,6 +623,8 @@ def run_gpu(args):
     host_out = torch.empty(shape, dtype=torch.float32).pin_memory()
     s2 = make_system(pss, shape)
     s2.set_stream(stream)
+    if tuning:
+        s2.set_tunings(tuning)
     s2.set_field(0, host_in.numpy())
     with torch.cuda.stream(stream):
         s2.step(args.warmup)
@@ -630,6 +651,7 @@ def run_gpu(args):
         s3.set_stream(stream)
         s3.init_uniform(0, -0.05, 0.05)
         s3.init_uniform(1, -0.05, 0.05)
+        tuning3 = None if args.no_autotune else s3.autotune(16)
         with torch.cuda.stream(stream):
             s3.step(20)
             n3 = 200
@@ -648,11 +670,12 @@ def run_gpu(args):
             "algorithmic_bytes_per_field_step": ab3["step"],
             "hbm_frac_of_measured": (2 * ab3["step"] / (ms3 * 1e-3) / 1e9) / hbm,
             "kernel_ms_two_fields": {"col": k3[0], "mid_inv": k3[1], "row": k3[2], "mid_fwd": k3[3]},
+            "autotuned": tuning3,
         }
         s3.close()
 
     if not args.no_ensemble:
-        extra["ensemble_512"] = ensemble_measurement(pss, torch, stream)
+        extra["ensemble_512"] = ensemble_measurement(pss, torch, stream, tune=not args.no_autotune)
     if not args.no_adjoint:
         extra["adjoint_256"] = adjoint_measurement(pss, torch, stream)
     if not args.no_variants:
@@ -671,7 +694,8 @@ def run_gpu(args):
                                "2/3 de-aliasing, output every 1000 steps",
                    "global_batch": world, "seq_len": sites, "parallelism": "replicas" if world > 1 else "single",
                    "l2": "flushed (512 MiB write) before every 1000-step interval; the ~11 MB working set is "
-                         "L2-resident inside an interval"},
+                         "L2-resident inside an interval",
+                   "autotuned": tuning},
         "roofline": {"bound": "hbm", "kernel": kernel_names[dom], "achieved": achieved,
                      "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
                      "peak_source": f"{peak_kind} hbm_gbs", "step_frac": (ab["step"] / (ms_per_step * 1e-3) / 1e9) / hbm,
@@ -715,6 +739,10 @@ def main(argv=None):
     ap.add_argument("--no-ensemble", action="store_true", help="skip the 512-instance ensemble measurement")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint measurement")
     ap.add_argument("--no-cufft", action="store_true", help="skip the cuFFT + torch comparison step")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the library's default launch shapes (no pss_autotune before timing)")
+    ap.add_argument("--tuning", nargs="*", default=None, metavar="KEY=VALUE",
+                    help="launch-shape settings of the 1024x1024 system instead of the autotuner's")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the order-3 de-aliasing and real-space round-trip measurements")
     args = ap.parse_args(argv)

@@ -243,6 +243,35 @@ int pss_time_kernels(pss_system *s, int64_t n, double *avg_ms);
  * 0 restores the automatic choice.  Unknown keys return PSS_EINVAL. */
 int pss_set_tuning(pss_system *s, const char *key, int value);
 
+/* Launch-shape autotuner: chooses the FFT pass radices, CTA tilings, noise
+ * warps, programmatic dependent launch and steps per graph of this system's
+ * step path by timing them on the GPU (the paper leaves launch shapes to the
+ * library; they do not change results beyond the rounding order of the FFT
+ * radix).  Coordinate descent: every knob of the path in turn takes each
+ * value of its list with the others at their best so far, and a value is
+ * kept only if its run is more than 1 % faster; each trial times at least
+ * steps_per_trial steps (a whole number of graph replays) three times and
+ * keeps the fastest.  Finally the starting settings and the result are
+ * timed back to back; the result is kept only if it is faster there too.
+ *
+ * The trials advance the system: its spectral state and step counter are
+ * saved first (one temporary device copy of the state, allocated and freed
+ * here) and restored afterwards, so the run continues as if the call had not
+ * been made (the next step's product and noise are recomputed from the
+ * restored state).  Cost: about 4 + (sum of the list lengths) trials of
+ * (3 steps_per_trial + one graph) steps; synchronises.
+ *
+ * The chosen settings stay in force as pss_set_tuning values.  If report is
+ * not NULL, a text of at most report_len bytes (NUL-terminated) describes
+ * the outcome: "path=P trials=T skipped=S initial_ms=X tuned_ms=Y
+ * key=value ...", with T the timed trials, S the values skipped because the
+ * launcher refused them for this system (shared memory that would not fit),
+ * X and Y the milliseconds per step of the starting and the chosen settings
+ * and every knob of the path as its pss_set_tuning value (0 = automatic;
+ * for "pdl", -1 = automatic).  Errors: PSS_EINVAL (NULL handle, no fields,
+ * steps_per_trial < 1), a failing trial's status (state still restored). */
+int pss_autotune(pss_system *s, int64_t steps_per_trial, char *report, size_t report_len);
+
 /* Steps taken so far (the next step's noise index). */
 int pss_get_step(pss_system *s, int64_t *step);
 int pss_set_step(pss_system *s, int64_t step);

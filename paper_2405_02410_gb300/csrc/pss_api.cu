@@ -1783,6 +1783,191 @@ int pss_set_tuning(pss_system *s, const char *key, int value) {
     return PSS_OK;
 }
 
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Launch-shape autotuner.  Coordinate descent over the knobs of the system's
+// step path: each knob in turn takes every value of its list with the others
+// held at their best so far, and keeps the value whose timed run of steps is
+// fastest (by more than 1 %, so that timing noise does not move it).  The
+// lists hold only values the launch-shape tests run (the helpers above clamp
+// them to the kernels' thread limits).
+// ---------------------------------------------------------------------------
+namespace {
+
+struct TuneKnob {
+    const char *name;
+    int pss_system::*field;
+    std::vector<int> values;
+};
+
+std::vector<TuneKnob> tune_space(const pss_system *s) {
+    std::vector<TuneKnob> k;
+    const auto radix_list = [](int side) { return side == 1024 ? std::vector<int>{8, 16, 32} : std::vector<int>{8, 16}; };
+    if (fast2d(s)) {
+        k.push_back({"col2_radix", &pss_system::tune_col2_radix, radix_list(s->ny)});
+        k.push_back({"row2_radix", &pss_system::tune_row2_radix, radix_list(s->nx)});
+        k.push_back({"row2_pairs", &pss_system::tune_row2_pairs, {1, 2, 4, 8}});
+        k.push_back({"col2_warps", &pss_system::tune_col2_warps, {4, 8, 16}});
+        if (any_noisy(s)) k.push_back({"row2_noise", &pss_system::tune_row2_noise, {8, 16}});
+    } else {
+        k.push_back({"col_radix", &pss_system::tune_col_radix, {8, 16}});
+        if (fast3d_rows(s)) k.push_back({"row2_radix", &pss_system::tune_row2_radix, {8, 16}});
+        else k.push_back({"row_radix", &pss_system::tune_row_radix, {8, 16}});
+        if (s->dim == 3) {
+            k.push_back({"mid_radix", &pss_system::tune_mid_radix, {8, 16}});
+            k.push_back({"mid_planes", &pss_system::tune_mid_planes, {1, 2, 4}});
+        }
+        if (!fast3d_rows(s)) k.push_back({"row_pairs", &pss_system::tune_row_pairs, {1, 2, 4, 8}});
+        k.push_back({"col_tiles", &pss_system::tune_col_tiles, {1, 2, 4}});
+    }
+    k.push_back({"pdl", &pss_system::tune_pdl, {0, 1}});
+    k.push_back({"graph_steps", &pss_system::tune_graph_steps, {8, 16, 32}});
+    return k;
+}
+
+// Milliseconds per step: the fastest of `reps` timed runs of at least `n`
+// steps (a whole number of graph replays), after one replay of warm-up that
+// also captures the graph of the current launch shape.
+int tune_trial(pss_system *s, int64_t n, int reps, cudaEvent_t e0, cudaEvent_t e1, double *ms) {
+    const int chunk = s->tune_graph_steps > 0 ? s->tune_graph_steps : kDefaultGraphSteps;
+    const int64_t m = (n + chunk - 1) / chunk * chunk;
+    int rc = pss_step(s, chunk);
+    if (rc) return rc;
+    double best = 1e300;
+    for (int r = 0; r < reps; ++r) {
+        CK(cudaEventRecord(e0, s->stream));
+        if ((rc = pss_step(s, m))) return rc;
+        CK(cudaEventRecord(e1, s->stream));
+        CK(cudaEventSynchronize(e1));
+        float t = 0;
+        CK(cudaEventElapsedTime(&t, e0, e1));
+        best = std::min(best, (double)t / (double)m);
+    }
+    *ms = best;
+    return PSS_OK;
+}
+
+int autotune_search(pss_system *s, int64_t n, const std::vector<TuneKnob> &space, const std::vector<int> &initial,
+                    double *ms_initial, double *ms_tuned, int *trials, int *skipped) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0));
+    cudaError_t ce = cudaEventCreate(&e1);
+    if (ce != cudaSuccess) { cudaEventDestroy(e0); return cuda_fail(s, ce, "cudaEventCreate"); }
+    const int reps = 3;
+    int rc = PSS_OK;
+    double best = 0;
+    *trials = 0;
+    *skipped = 0;
+    if ((rc = tune_trial(s, n, reps, e0, e1, &best)) == PSS_OK) {
+        ++*trials;
+        for (const TuneKnob &k : space) {
+            const int keep = s->*k.field;
+            int arg = keep;
+            for (int v : k.values) {
+                if (v == keep) continue;
+                s->*k.field = v;
+                invalidate(s);
+                double t = 0;
+                const int trc = tune_trial(s, n, reps, e0, e1, &t);
+                if (trc) {
+                    // a shape the launcher refuses for this system (its shared memory
+                    // would not fit): skip it, as long as the stream is unharmed
+                    cudaGetLastError();
+                    if (cudaStreamSynchronize(s->stream) != cudaSuccess) { rc = trc; break; }
+                    ++*skipped;
+                    continue;
+                }
+                ++*trials;
+                if (t < 0.99 * best) { best = t; arg = v; }
+            }
+            s->*k.field = arg;
+            invalidate(s);
+            if (rc) break;
+        }
+    }
+    // the starting shape and the result, timed back to back twice over; the
+    // result stands only if it is faster there too
+    std::vector<int> tuned(space.size());
+    for (size_t i = 0; i < space.size(); ++i) tuned[i] = s->*space[i].field;
+    double t_init = 1e300, t_tuned = 1e300;
+    for (int round = 0; round < 2 && rc == PSS_OK; ++round)
+        for (int which = 0; which < 2 && rc == PSS_OK; ++which) {
+            const std::vector<int> &set = which == 0 ? initial : tuned;
+            for (size_t i = 0; i < space.size(); ++i) s->*space[i].field = set[i];
+            invalidate(s);
+            double t = 0;
+            if ((rc = tune_trial(s, n, reps, e0, e1, &t))) break;
+            ++*trials;
+            (which == 0 ? t_init : t_tuned) = std::min(which == 0 ? t_init : t_tuned, t);
+        }
+    const std::vector<int> &final_set = (rc == PSS_OK && t_tuned <= t_init) ? tuned : initial;
+    for (size_t i = 0; i < space.size(); ++i) s->*space[i].field = final_set[i];
+    invalidate(s);
+    *ms_initial = t_init;
+    *ms_tuned = std::min(t_init, t_tuned);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pss_autotune(pss_system *s, int64_t steps_per_trial, char *report, size_t report_len) {
+    if (!s) return PSS_EINVAL;
+    if (steps_per_trial < 1) return fail(s, PSS_EINVAL, "steps_per_trial must be >= 1");
+    if (s->fields.empty()) return fail(s, PSS_EINVAL, "no fields");
+    if (report && report_len) report[0] = '\0';
+    int rc = upload_params(s);
+    if (rc) return rc;
+    if (round_trip(s) && (rc = ensure_real(s))) return rc;
+    if ((rc = prologue(s))) return rc;
+    // keep the state and the step counter: the trials advance the system
+    const size_t bytes = csize(s) * s->field_elems * (size_t)s->nslots();
+    void *saved = nullptr;
+    CK(cudaMalloc(&saved, bytes));
+    const int64_t step0 = s->step;
+    cudaError_t e = cudaMemcpyAsync(saved, s->state, bytes, cudaMemcpyDeviceToDevice, s->stream);
+    if (e != cudaSuccess) { cudaFree(saved); return cuda_fail(s, e, "saving the state"); }
+
+    const std::vector<TuneKnob> space = tune_space(s);
+    std::vector<int> initial(space.size());
+    for (size_t i = 0; i < space.size(); ++i) initial[i] = s->*space[i].field;
+    double ms_init = 0, ms_tuned = 0;
+    int trials = 0, skipped = 0;
+    rc = autotune_search(s, steps_per_trial, space, initial, &ms_init, &ms_tuned, &trials, &skipped);
+    const std::string search_err = s->err;
+
+    // put the state, the step counter and the next step's product and noise back
+    long long v = step0;
+    e = cudaMemcpyAsync(s->state, saved, bytes, cudaMemcpyDeviceToDevice, s->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->d_step, &v, sizeof v, cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    cudaFree(saved);
+    s->step = step0;
+    s->stale = true;
+    invalidate(s);
+    if (rc) { s->err = search_err; return rc; }
+    if (e != cudaSuccess) return cuda_fail(s, e, "restoring the state");
+    if ((rc = device_errors(s))) return rc;
+
+    if (report && report_len) {
+        std::string r;
+        char buf[160];
+        snprintf(buf, sizeof buf, "path=%d trials=%d skipped=%d initial_ms=%.6g tuned_ms=%.6g", pss_step_path(s), trials,
+                 skipped, ms_init, ms_tuned);
+        r = buf;
+        for (size_t i = 0; i < space.size(); ++i) {
+            snprintf(buf, sizeof buf, " %s=%d", space[i].name, s->*space[i].field);
+            r += buf;
+        }
+        snprintf(report, report_len, "%s", r.c_str());
+    }
+    return PSS_OK;
+}
+
 int pss_get_step(pss_system *s, int64_t *step) {
     if (!s || !step) return PSS_EINVAL;
     *step = s->step;

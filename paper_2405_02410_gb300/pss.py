@@ -30,7 +30,7 @@ EXPORTS = [
     "pss_time_kernels", "pss_set_tuning", "pss_create_batch", "pss_batch_size", "pss_select_instance",
     "pss_set_param_batch", "pss_step_many", "pss_adjoint_forward", "pss_adjoint_backward",
     "pss_structure_factor_noalloc", "pss_step_path", "pss_set_frame", "pss_add_grad_sq_term",
-    "pss_add_product_term",
+    "pss_add_product_term", "pss_autotune",
 ]
 
 
@@ -76,6 +76,7 @@ def _load():
         "pss_step_path": ([vp], i32),
         "pss_time_kernels": ([vp, i64, P(d)], i32),
         "pss_set_tuning": ([vp, ctypes.c_char_p, i32], i32),
+        "pss_autotune": ([vp, i64, ctypes.c_char_p, ctypes.c_size_t], i32),
         "pss_create_batch": ([P(vp), i32, i32, i32, i32, i32, d, d, d, d, P(u64), i32], i32),
         "pss_batch_size": ([vp], i32),
         "pss_select_instance": ([vp, i32], i32),
@@ -301,6 +302,22 @@ class System:
         "row2_radix"); 0 = automatic (for "fast2d" / "fast3d": the generic kernels)."""
         self._ck(lib.pss_set_tuning(self._h, key.encode(), int(value)))
 
+    def autotune(self, steps_per_trial: int = 64) -> dict:
+        """Time the launch-shape knobs of this system's step path on the GPU and keep the
+        fastest settings (pss_autotune); the state and step counter are left as they were.
+        Returns the report as a dict: path, trials, initial_ms / tuned_ms per step, and each
+        knob's pss_set_tuning value (0 = automatic, -1 = automatic for "pdl")."""
+        buf = ctypes.create_string_buffer(1024)
+        self._ck(lib.pss_autotune(self._h, int(steps_per_trial), buf, len(buf)))
+        return parse_tune_report(buf.value.decode())
+
+    def set_tunings(self, report: dict):
+        """Apply the knob settings of an autotune report (other keys are ignored)."""
+        for key, val in report.items():
+            if key in ("path", "trials", "skipped", "initial_ms", "tuned_ms") or (key == "pdl" and val < 0):
+                continue
+            self.set_tuning(key, val)
+
     def adjoint_forward(self, n: int):
         """Advance n steps keeping sqrt(n)-spaced checkpoints for adjoint_backward."""
         self._ck(lib.pss_adjoint_forward(self._h, int(n)))
@@ -327,6 +344,15 @@ class System:
         """'fast2d' (k2_col, k2_row: FP32 2D, sides 256..1024), 'fast3d_rows' (k_col, k_mid and the
         FFT-group x pass k2_row: FP32 3D, x side 256..1024) or 'generic' (k_col, k_mid, k_row)."""
         return {1: "fast2d", 2: "fast3d_rows"}.get(lib.pss_step_path(self._h), "generic")
+
+
+def parse_tune_report(text: str) -> dict:
+    """'path=1 trials=9 initial_ms=0.0153 tuned_ms=0.0151 pdl=-1 ...' -> dict (ints, and floats for *_ms)."""
+    out = {}
+    for item in text.split():
+        key, _, val = item.partition("=")
+        out[key] = float(val) if key.endswith("_ms") else int(val)
+    return out
 
 
 def step_many(systems: Sequence[System], n: int):
