@@ -185,8 +185,9 @@ def whole_job_rate(units_per_rank, local_ms, world):
 # ---------------------------------------------------------------------------
 # the CPU oracle leg
 # ---------------------------------------------------------------------------
-def oracle_rate(shape, steps, budget_s=20.0):
-    """Site-steps/s of the FP64 oracle (one thread) on the Model B workload, bounded to ~budget_s."""
+def oracle_rate(shape, steps, budget_s=20.0, keep_state=False):
+    """Site-steps/s of the FP64 oracle (one thread) on the Model B workload, bounded to ~budget_s
+    (with keep_state, also the oracle's spectrum after its 1 + n steps)."""
     from oracle import oracle as O
     w = WORKLOAD
     m = O.model_b(shape, dt=w["dt"], a=w["a"], b=w["b"], K=w["K"], D=w["D"], seed=w["seed"])
@@ -197,12 +198,80 @@ def oracle_rate(shape, steps, budget_s=20.0):
     per = t1 - t0
     n = max(1, min(steps, int(budget_s / max(per, 1e-9))))
     t0 = time.perf_counter()
-    O.run(m, phi, 1, n)
+    phi = O.run(m, phi, 1, n)
     dt = time.perf_counter() - t0
     sites = 1
     for s in shape:
         sites *= s
-    return sites * n / dt, n, dt
+    return (sites * n / dt, n, dt, phi) if keep_state else (sites * n / dt, n, dt)
+
+
+def _oracle_3d_field(field_id, steps):
+    """Half spectrum of one field of the 256^3 Model A + B pair after `steps` oracle steps (worker)."""
+    from oracle import oracle as O
+    shape = (256, 256, 256)
+    mk = O.model_a if field_id == 0 else O.model_b
+    m = mk(shape, dt=0.005, a=-1, b=1, K=1, D=0.05, seed=WORKLOAD["seed"], field_id=field_id)
+    return O.half(O.run(m, O.to_spectrum(m, O.init_uniform(m, -0.05, 0.05)), 0, steps))
+
+
+def _rel_l2(a, b):
+    import numpy as np
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def oracle_parity(pss, stream, phi_1024, steps_1024, tuning, tuning3, probes, do_3d=True, steps_3d=2):
+    """The oracle leg's accuracy check: relative L2 error of each timed workload's GPU spectrum against
+    the FP64 oracle on the same inputs and noise (the 1024^2 run of the CPU baseline, the 64^2 parity
+    workload in FP32 and FP64, the first steps of the 256^3 pair, instance 0 of the 64^2 and 128^2
+    classes of the ensemble)."""
+    import multiprocessing as mp
+    from oracle import oracle as O
+    w = WORKLOAD
+    out = {}
+    pool = None
+    if do_3d:   # the two 3D oracle fields start first (spawned workers) and run beside the rest
+        pool = mp.get_context("spawn").Pool(2)
+        fut3 = pool.starmap_async(_oracle_3d_field, [(0, steps_3d), (1, steps_3d)])
+    s = make_system(pss, w["shape"])
+    s.set_stream(stream)
+    if tuning:
+        s.set_tunings(tuning)
+    s.init_uniform(0, w["lo"], w["hi"])
+    s.step(steps_1024)
+    out["model_b_1024_f32"] = {"steps": steps_1024, "rel_l2": _rel_l2(s.get_spectrum(0), O.half(phi_1024))}
+    s.close()
+    m = O.model_b((64, 64), dt=w["dt"], a=w["a"], b=w["b"], K=w["K"], D=w["D"], seed=w["seed"])
+    ref = O.half(O.run(m, O.to_spectrum(m, O.init_uniform(m, w["lo"], w["hi"])), 0, 100))
+    for prec in ("f32", "f64"):
+        g = make_system(pss, (64, 64), prec)
+        g.set_stream(stream)
+        g.init_uniform(0, w["lo"], w["hi"])
+        g.step(100)
+        out[f"model_b_64_{prec}"] = {"steps": 100, "rel_l2": _rel_l2(g.get_spectrum(0), ref)}
+        g.close()
+    for sz, (seed, a, steps, spec) in sorted(probes.items()):
+        m = O.model_b((sz, sz), dt=0.01, a=a, b=1.0, K=1.0, D=0.01, seed=seed)
+        ref = O.half(O.run(m, O.to_spectrum(m, O.init_uniform(m, -0.1, 0.1)), 0, steps))
+        out[f"ensemble_{sz}_instance0_f32"] = {"steps": steps, "rel_l2": _rel_l2(spec, ref)}
+    if pool is not None:
+        g = pss.System((256, 256, 256), dt=0.005, seed=w["seed"], precision="f32")
+        pss.add_model_a_field(g, a=-1, b=1, K=1, D=0.05, name="psi")
+        pss.add_model_b_field(g, a=-1, b=1, K=1, D=0.05, name="phi")
+        g.set_stream(stream)
+        if tuning3:
+            g.set_tunings(tuning3)
+        g.init_uniform(0, -0.05, 0.05)
+        g.init_uniform(1, -0.05, 0.05)
+        g.step(steps_3d)
+        got = [g.get_spectrum(0), g.get_spectrum(1)]
+        g.close()
+        refs = fut3.get()
+        pool.close()
+        pool.join()
+        out["model_ab_256cubed_f32"] = {"steps": steps_3d, "rel_l2_model_a": _rel_l2(got[0], refs[0]),
+                                        "rel_l2_model_b": _rel_l2(got[1], refs[1])}
+    return out
 
 
 def run_reference(args):
@@ -246,6 +315,7 @@ def ensemble_systems(pss, n=512, gen_seed=2405, base_seed=10000):
     sizes = g.choice([64, 128, 256, 512], size=n)
     a_vals = g.uniform(-1.5, -0.5, size=n)
     systems, sites = [], 0
+    first = {}
     for sz in (64, 128, 256, 512):
         idx = np.nonzero(sizes == sz)[0]
         if len(idx) == 0:
@@ -258,6 +328,8 @@ def ensemble_systems(pss, n=512, gen_seed=2405, base_seed=10000):
             s.init_uniform(0, -0.1, 0.1)
         systems.append(s)
         sites += len(idx) * int(sz) * int(sz)
+        first[int(sz)] = (base_seed + int(idx[0]), float(a_vals[idx[0]]))
+    ensemble_systems.first = first          # instance 0 of each size class: (seed, a)
     return systems, sites, {int(k): int((sizes == k).sum()) for k in (64, 128, 256, 512)}
 
 
@@ -277,8 +349,13 @@ def ensemble_measurement(pss, torch, stream, steps=200, tune=True):
     e1.record(stream)
     e1.synchronize()
     ms = e0.elapsed_time(e1) / steps
+    probes = {}
     for s in systems:
         s.sync()
+        if s.shape[0] in (64, 128):        # instance 0 of the small classes, for the oracle leg
+            s.select_instance(0)
+            seed, a = ensemble_systems.first[s.shape[0]]
+            probes[s.shape[0]] = (seed, a, s.get_step(), s.get_spectrum(0))
         s.close()
     # the plain single-system path on the same instances: one system per instance, run one after another
     seq_ms = 0.0
@@ -301,7 +378,8 @@ def ensemble_measurement(pss, torch, stream, steps=200, tune=True):
             "site_steps_per_s": sites / (ms * 1e-3),
             "sequential_single_system_ms_per_step": seq_ms,
             "speedup_vs_sequential": seq_ms / ms,
-            "autotuned": {str(k): v for k, v in tuning.items()} if tune else None}
+            "autotuned": {str(k): v for k, v in tuning.items()} if tune else None,
+            "_probes": probes}
 
 
 def cufft_comparison(torch, stream, shape=(1024, 1024), steps=2000, graph_steps=20):
@@ -478,7 +556,7 @@ def example_measurement(pss, torch, stream):
             "phases_p3_p97": [float(np.percentile(r, 3)), float(np.percentile(r, 97))]}
 
 
-def adjoint_measurement(pss, torch, stream, n=2000, shape=(256, 256), nbins=64):
+def adjoint_measurement(pss, torch, stream, n=2000, shape=(256, 256), nbins=64, tune=True):
     """The adjoint workload: 2D Model B 256^2, FP32, n steps with a fixed noise realisation and sqrt(n)
     checkpoints; loss = mean over the 64 S(q) bins of (S - S*)^2 with S* from (a, b, K) = (-0.8, 1.2, 0.9)."""
     import numpy as np
@@ -489,11 +567,15 @@ def adjoint_measurement(pss, torch, stream, n=2000, shape=(256, 256), nbins=64):
         s.init_uniform(0, -0.1, 0.1)
         return s
 
+    tuning = None
+
     tgt = system(-0.8, 1.2, 0.9)
     tgt.step(n)
     S_star, cnt, _ = tgt.structure_factor(0, nbins)
     tgt.close()
     plain = system(-1.0, 1.0, 1.0)
+    if tune:   # the forward step's launch shapes, for the plain run and the adjoint's recomputed steps
+        tuning = plain.autotune(16)
     plain.step(32)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -502,6 +584,8 @@ def adjoint_measurement(pss, torch, stream, n=2000, shape=(256, 256), nbins=64):
     t_plain = time.perf_counter() - t0
     plain.close()
     s = system(-1.0, 1.0, 1.0)
+    if tuning:
+        s.set_tunings(tuning)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     s.adjoint_forward(n)
@@ -529,7 +613,7 @@ def adjoint_measurement(pss, torch, stream, n=2000, shape=(256, 256), nbins=64):
     return {"workload": "2D Model B 256x256 FP32, 2000 steps, sqrt(n) checkpoints, binned-S(q) loss",
             "steps": n, "loss": loss, "dJ_d(a,b,K,D)": [float(x) for x in grads],
             "forward_plain_ms": t_plain * 1e3, "forward_with_checkpoints_ms": t_fwd * 1e3,
-            "adjoint_ms": t_bwd * 1e3, "adjoint_over_forward": t_bwd / t_plain}
+            "adjoint_ms": t_bwd * 1e3, "adjoint_over_forward": t_bwd / t_plain, "autotuned": tuning}
 
 
 def run_gpu(args):
@@ -644,6 +728,7 @@ def run_gpu(args):
 
     # secondary: 3D 256^3 Model A + Model B pair (two fields), FP32
     extra = {}
+    tuning3 = None
     if not args.no_3d:
         s3 = pss.System((256, 256, 256), dt=0.005, seed=w["seed"], precision="f32")
         pss.add_model_a_field(s3, a=-1, b=1, K=1, D=0.05, name="psi")
@@ -676,8 +761,9 @@ def run_gpu(args):
 
     if not args.no_ensemble:
         extra["ensemble_512"] = ensemble_measurement(pss, torch, stream, tune=not args.no_autotune)
+    probes = extra["ensemble_512"].pop("_probes") if "ensemble_512" in extra else {}
     if not args.no_adjoint:
-        extra["adjoint_256"] = adjoint_measurement(pss, torch, stream)
+        extra["adjoint_256"] = adjoint_measurement(pss, torch, stream, tune=not args.no_autotune)
     if not args.no_variants:
         extra["variants"] = variants_measurement(pss, torch, stream, ms_per_step)
         extra["model_b_example_256"] = example_measurement(pss, torch, stream)
@@ -711,13 +797,17 @@ def run_gpu(args):
         "extra": extra,
     }
     if rank == 0 and not args.no_cpu_baseline:
-        rate, n, dt = oracle_rate(shape, 1000, budget_s=float(os.environ.get("PSS_CPU_BUDGET_S", "15")))
+        rate, n, dt, phi_o = oracle_rate(shape, 1000, budget_s=float(os.environ.get("PSS_CPU_BUDGET_S", "15")),
+                                         keep_state=True)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": f"{n} steps of the 1024x1024 Model B workload, FP64 C oracle, 1 thread"}
         all_rate, ncores, n_all = oracle_all_cores(shape, budget_s=float(os.environ.get("PSS_CPU_BUDGET_S", "15")) / 2)
         line["cpu_baseline"]["all_cores"] = {
             "value": all_rate, "unit": UNIT, "cores": ncores,
             "sample": f"{ncores} independent oracle runs of {n_all} steps each (spawned processes, one per core)"}
+        # the same oracle runs as the accuracy reference of the timed workloads
+        line["parity_vs_fp64_oracle"] = oracle_parity(pss, stream, phi_o, n + 1, tuning, tuning3, probes,
+                                                      do_3d=not args.no_3d)
     s.close()
     s2.close()
     if rank == 0:

@@ -222,6 +222,9 @@ int pss_time_kernels(pss_system *s, int64_t n, double *avg_ms);
  *   "col2_warps"  warps beside the FFT groups of a column CTA of that path
  *                 that join its update (1..24);
  *   "row2_pairs"  row pairs per row CTA of that path (power of two <= 8);
+ *   "adj_row_pairs" row pairs per CTA of the adjoint's x pass on that path
+ *                 (power of two <= 8; automatic: the largest that still
+ *                 gives every SM a CTA); the adjoint is the same bits;
  *   "row2_noise"  warps per row CTA of that path that draw the next step's
  *                 noise (1..24);
  *   "row2_share"  percentage (0..100) of that noise drawn by extra CTAs on

@@ -109,6 +109,7 @@ struct pss_system {
     int tune_col2_warps = 0, tune_row2_pairs = 0;   // its noise warps per column CTA, row pairs per row CTA
     int tune_col2_radix = 0, tune_row2_radix = 0;   // its FFT pass radix (8 or 16; 0 = automatic)
     int tune_row2_noise = 0;                 // noise warps per row CTA of that path (0 = automatic)
+    int tune_adj_row_pairs = 0;              // row pairs per CTA of the adjoint's FFT-group x pass (0 = automatic)
     int tune_real_state = 0;                 // every step ends in real space and comes back (ablation)
     int tune_fuse_adj = 1;                   // adjoint: one launch for part B of a step and part A of the one before
     int tune_row2_share = -1;                // % of the noise drawn by extra CTAs on idle SMs (-1 = automatic: 0)
@@ -395,6 +396,23 @@ int row2_pairs(const pss_system *s) {
     int p = 1;
     while (p * tpf < 32) p *= 2;   // whole warps of transform threads
     while (p * 2 <= nw && p * 2 <= 8 && p * 2 * tpf <= 512) p *= 2;
+    return p;
+}
+
+// row pairs per CTA of the adjoint's x pass on FFT groups.  It has no noise
+// warps, so a CTA is just its transform groups: the pairs are spread so that
+// every SM gets a CTA (at 256^2 the step's 4 pairs would leave 32 CTAs of
+// four warps on 152 SMs), with whole warps of transform threads.
+int row2_adj_pairs(const pss_system *s, int nslots) {
+    const int tpf = s->nx / row2_radix(s);
+    const int maxp = std::min(8, row2_max_threads(row2_radix(s)) / tpf);
+    int p = 1;
+    while (p * tpf < 32) p *= 2;
+    if (s->tune_adj_row_pairs > 0) {
+        while (p * 2 <= s->tune_adj_row_pairs && p * 2 <= maxp) p *= 2;
+        return p;
+    }
+    while (p * 2 <= maxp && (long long)s->rows / (4 * p) * nslots >= s->num_sms) p *= 2;
     return p;
 }
 
@@ -685,7 +703,7 @@ template <typename T> struct Seq {
             a.d_status = s->d_status;
             a.mode = ROW_ADJ;
             a.E = row2_radix(s);
-            a.G = row2_pairs(s);
+            a.G = row2_adj_pairs(s, nslots);
             a.kx_cols_max = s->hx;
             if (timer) timer->begin(2, st);
             cudaError_t e = launch_row2(a, nslots, st, true);
@@ -1761,6 +1779,7 @@ int pss_set_tuning(pss_system *s, const char *key, int value) {
         s->tune_col2_warps = value;
     }
     else if (k == "row2_pairs") s->tune_row2_pairs = value;
+    else if (k == "adj_row_pairs") s->tune_adj_row_pairs = value;
     else if (k == "row2_share") {
         if (value > 100) return fail(s, PSS_EINVAL, "row2_share is a percentage");
         s->tune_row2_share = value;

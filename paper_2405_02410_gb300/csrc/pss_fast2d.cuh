@@ -398,7 +398,7 @@ __global__ void __launch_bounds__(E == 8 ? 1024 : E == 16 ? 768 : 512, 1) k2_col
 // pairs).
 template <int N, int E> struct Row2Smem {
     static constexpr int WST = 2 * GShape<N, E>::BUF + 16;
-    static size_t bytes(int nw, bool tiled) {
+    __host__ __device__ static size_t bytes(int nw, bool tiled) {
         return 128 + sizeof(float2) * ((size_t)N + (size_t)nw * (tiled ? WST : GShape<N, E>::WS));
     }
     __device__ static int base(int j, bool tiled) {
@@ -504,6 +504,27 @@ __global__ void __launch_bounds__(E == 32 ? 512 : 1024) k2_row(const RowArgs<flo
     // conjugates (the 2D path).  All of a thread's loads are issued before the
     // first use.
     constexpr bool adj = TILED && ADJ;   // mode ROW_ADJ
+    // ROW_ADJ: the real rows r0 .. r0 + 2 NW - 1 (one contiguous run), which the
+    // first transform's last pass multiplies in, go to shared memory behind the
+    // group buffers now, all of a thread's loads in flight together, instead of
+    // being read from global memory inside that pass
+    float *MS = nullptr;
+    if constexpr (adj) {
+        MS = reinterpret_cast<float *>(smem_raw + Row2Smem<N, E>::bytes(NW, true));
+        constexpr int PER = N / (2 * TPF), CH = PER < 4 ? PER : 4;   // float4 per thread, per batch of loads
+        static_assert(PER % CH == 0, "whole batches");
+        const float4 *__restrict__ src =
+            reinterpret_cast<const float4 *>(a.real_in + (size_t)slot * a.real_stride + (size_t)r0 * N);
+        float4 *ms4 = reinterpret_cast<float4 *>(MS);
+#pragma unroll 1
+        for (int p0 = 0; p0 < PER; p0 += CH) {
+            float4 v[CH];
+#pragma unroll
+            for (int c = 0; c < CH; ++c) v[c] = __ldcg(src + t + (p0 + c) * nf);
+#pragma unroll
+            for (int c = 0; c < CH; ++c) ms4[t + (p0 + c) * nf] = v[c];
+        }
+    }
     const int kcm = adj ? sp.hx : a.kx_cols_max;
     const int kc = adj ? sp.hx : a.fps[slot].kx_cols;
     auto stage = [&](int k, int j, float ar, float ai, float br, float bi) {
@@ -592,7 +613,7 @@ __global__ void __launch_bounds__(E == 32 ? 512 : 1024) k2_row(const RowArgs<flo
             rb = ra + N;
         }
         if (adj) {
-            ma = a.real_in + (size_t)slot * a.real_stride + (size_t)(r0 + 2 * g) * N;
+            ma = MS + (size_t)(2 * g) * N;
             mb = ma + N;
         }
 #pragma unroll 1
@@ -659,7 +680,8 @@ cudaError_t launch_row2_ne(const RowArgs<float> &a, int nslots, cudaStream_t st)
         threads > (E == 32 ? 512 : 1024) || (TILED && a.noise) || a.noise_ctas < 0 ||
         (a.noise_ctas > 0 && !a.noise) || a.noise_share < 0 || a.noise_share > 64)
         return cudaErrorInvalidConfiguration;
-    const size_t smem = Row2Smem<N, E>::bytes(nw, TILED);
+    // ROW_ADJ also stages the CTA's 2 nw real rows
+    const size_t smem = Row2Smem<N, E>::bytes(nw, TILED) + (TILED && ADJ ? sizeof(float) * 2 * nw * N : 0);
     cudaError_t e = ensure_smem(k2_row<N, E, TILED, ADJ>, smem);
     if (e != cudaSuccess) return e;
     return launch_pdl(k2_row<N, E, TILED, ADJ>, dim3(a.sp.rows / (2 * nw) + a.noise_ctas, nslots), threads, smem,

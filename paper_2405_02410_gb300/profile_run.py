@@ -1,11 +1,13 @@
 """Run a fixed number of Model B steps for profilers (ncu wraps this command).
 
     python -m paper_2405_02410_gb300.profile_run --shape 1024 1024 --steps 20 [--eager] [--fields 1|2]
-        [--tune key=value ...]
+        [--tune key=value ...] [--adjoint]
 
 --eager launches every step's kernels one by one (no CUDA graph); --fields 2
 adds a Model A field (the 3D Model A + B pair); --tune passes launch-shape
-settings to pss_set_tuning (e.g. fast2d=0 for the generic 2D kernels).
+settings to pss_set_tuning (e.g. fast2d=0 for the generic 2D kernels);
+--adjoint runs the steps with checkpoints (pss_adjoint_forward) and then the
+backward pass of J = |phi_T|^2 / 2 (pss_adjoint_backward) instead.
 """
 import argparse
 import os
@@ -22,6 +24,7 @@ def main():
     ap.add_argument("--precision", default="f32")
     ap.add_argument("--eager", action="store_true")
     ap.add_argument("--tune", nargs="*", default=[], help="key=value launch-shape settings")
+    ap.add_argument("--adjoint", action="store_true", help="forward with checkpoints, then the backward pass")
     args = ap.parse_args()
     import torch
     from paper_2405_02410_gb300 import build
@@ -42,7 +45,10 @@ def main():
         s.set_tuning(k, int(v))
     for f in range(args.fields):
         s.init_uniform(f, -0.1, 0.1)
-    if args.eager:
+    if args.adjoint:
+        s.adjoint_forward(args.steps)
+        s.adjoint_backward(s.get_spectrum(0), 4)
+    elif args.eager:
         for _ in range(args.steps):
             s.step(1)
     else:

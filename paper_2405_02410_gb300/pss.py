@@ -299,7 +299,7 @@ class System:
     def set_tuning(self, key: str, value: int):
         """Launch-shape knob ("pdl", "row_pairs", "col_tiles", "mid_planes", "graph_steps", "col_radix",
         "row_radix", "mid_radix", "fast2d", "fast3d", "col2_warps", "row2_pairs", "row2_noise", "col2_radix",
-        "row2_radix"); 0 = automatic (for "fast2d" / "fast3d": the generic kernels)."""
+        "row2_radix", "adj_row_pairs", ...; see pss_set_tuning in include/pss.h); 0 = automatic (for "fast2d" / "fast3d": the generic kernels)."""
         self._ck(lib.pss_set_tuning(self._h, key.encode(), int(value)))
 
     def autotune(self, steps_per_trial: int = 64) -> dict:

@@ -171,6 +171,25 @@ def test_adjoint_on_the_fft_group_path(shape):
     assert np.max(np.abs(runs[1][0] - runs[0][0]) / np.abs(runs[0][0])) < 1e-4
 
 
+@pytest.mark.parametrize("shape", [(256, 256), (512, 256), (256, 1024)])
+def test_adjoint_x_pass_row_pairs_change_no_bit(shape):
+    # the adjoint's x pass on FFT groups transforms each row pair on its own:
+    # any number of pairs per CTA gives the same bits (automatic = spread over the SMs)
+    dt, seed, n = 0.02, 31, 9
+    m = O.model_b(shape, dt=dt, seed=seed, **PARAMS)
+    lamT = 2.0 * _weights(shape) * O.run(m, O.to_spectrum(m, O.init_uniform(m, -0.3, 0.3)), 0, n) / m.n_sites
+    out = {}
+    for pairs in (0, 1, 2, 4, 8):
+        s = _gpu_system(shape, "f32", dt, seed)
+        assert s.step_path == "fast2d"
+        s.set_tuning("adj_row_pairs", pairs)
+        s.adjoint_forward(n)
+        out[pairs] = s.adjoint_backward(O.half(lamT), 4)
+    for pairs in (1, 2, 4, 8):
+        np.testing.assert_array_equal(out[pairs][1], out[0][1])
+        np.testing.assert_allclose(out[pairs][0], out[0][0], rtol=1e-9)
+
+
 @pytest.mark.parametrize("shape,prec", [((32, 32), "f64"), ((64,), "f64"), ((16, 16, 16), "f32"),
                                         ((8, 16, 8), "f64"), ((256, 256), "f32"), ((1024, 16), "f64")])
 def test_fused_adjoint_launch_changes_no_field_bit(shape, prec):
