@@ -1011,24 +1011,60 @@ int record_steps(pss_system *s, cudaStream_t st, int64_t n) {
     return PSS_OK;
 }
 
-// capture `steps` steps of every system into one graph (on systems[0]'s capture stream)
+// capture `steps` steps of every system into one graph (on systems[0]'s
+// capture stream).  Distinct systems share no buffers, so each one's steps
+// form a branch of its own (forked from and joined to the capture stream by
+// events, recorded on the system's own capture stream) and the GPU runs the
+// branches side by side; a system listed twice keeps the serial order.
 int capture_graph(pss_system **sys, int n, int steps, cudaGraphExec_t *out) {
     pss_system *s = sys[0];
-    CK(cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal));
+    bool branches = n > 1;
+    for (int i = 0; i < n && branches; ++i)
+        for (int j = 0; j < i; ++j)
+            if (sys[i] == sys[j] || sys[i]->cap_stream == sys[j]->cap_stream) branches = false;
+    std::vector<cudaEvent_t> ev(branches ? n + 1 : 0, nullptr);
+    for (auto &x : ev) {
+        cudaError_t e = cudaEventCreateWithFlags(&x, cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            for (auto &y : ev) if (y) cudaEventDestroy(y);
+            return cuda_fail(s, e, "cudaEventCreateWithFlags");
+        }
+    }
+    auto destroy_events = [&]() { for (auto &x : ev) if (x) cudaEventDestroy(x); };
+    cudaError_t e = cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) { destroy_events(); return cuda_fail(s, e, "cudaStreamBeginCapture"); }
     int rc = PSS_OK;
     std::vector<int64_t> before(n);
     for (int i = 0; i < n; ++i) before[i] = sys[i]->launches;
-    for (int k = 0; k < steps && rc == PSS_OK; ++k)
+    if (branches) {
+        e = cudaEventRecord(ev[n], s->cap_stream);                               // fork
+        int forked = 1;
+        for (; forked < n && e == cudaSuccess; ++forked) e = cudaStreamWaitEvent(sys[forked]->cap_stream, ev[n], 0);
+        if (e != cudaSuccess) { rc = cuda_fail(s, e, "forking the capture"); --forked; }
         for (int i = 0; i < n && rc == PSS_OK; ++i) {
-            rc = record_steps(sys[i], s->cap_stream, 1);
+            rc = record_steps(sys[i], sys[i]->cap_stream, steps);
             if (rc && i != 0) s->err = sys[i]->err;
         }
+        // join every forked stream, also after a failure, so that the capture ends cleanly
+        for (int i = 1; i < forked; ++i) {
+            e = cudaEventRecord(ev[i], sys[i]->cap_stream);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(s->cap_stream, ev[i], 0);
+            if (e != cudaSuccess && rc == PSS_OK) rc = cuda_fail(s, e, "joining the capture");
+        }
+    } else {
+        for (int k = 0; k < steps && rc == PSS_OK; ++k)
+            for (int i = 0; i < n && rc == PSS_OK; ++i) {
+                rc = record_steps(sys[i], s->cap_stream, 1);
+                if (rc && i != 0) s->err = sys[i]->err;
+            }
+    }
     for (int i = 0; i < n; ++i) {
         sys[i]->graph_launches = steps > 0 ? (sys[i]->launches - before[i]) / steps : 0;
         sys[i]->launches = before[i];
     }
     cudaGraph_t g = nullptr;
-    cudaError_t e = cudaStreamEndCapture(s->cap_stream, &g);
+    e = cudaStreamEndCapture(s->cap_stream, &g);
+    destroy_events();
     if (rc) { if (g) cudaGraphDestroy(g); return rc; }
     if (e != cudaSuccess) return cuda_fail(s, e, "cudaStreamEndCapture");
     e = cudaGraphInstantiate(out, g, 0);

@@ -81,6 +81,21 @@ def test_step_many_mixed_sizes_equal_separate_runs():
         assert systems[j].get_step() == 37
 
 
+def test_step_many_runs_a_system_listed_twice_in_order():
+    # distinct systems run as parallel branches of the captured graph; a system
+    # listed twice keeps the serial order: two steps per step of the call
+    P = pss()
+    a = _batch((64, 64), [5, 6], [-1.0, -0.9])
+    b = _batch((64, 64), [5, 6], [-1.0, -0.9])
+    P.step_many([a, a], 20)           # one graph replay of 16 (32 steps) + 4 eager (8 steps)
+    b.step(40)
+    assert a.get_step() == 40
+    for i in range(2):
+        a.select_instance(i)
+        b.select_instance(i)
+        np.testing.assert_array_equal(a.get_spectrum(0), b.get_spectrum(0))
+
+
 def test_param_change_between_graph_replays():
     # parameters live on the device: a change between runs applies without re-capture
     P = pss()
