@@ -1,13 +1,15 @@
 """Run a fixed number of Model B steps for profilers (ncu wraps this command).
 
     python -m paper_2405_02410_gb300.profile_run --shape 1024 1024 --steps 20 [--eager] [--fields 1|2]
-        [--tune key=value ...] [--adjoint]
+        [--tune key=value ...] [--adjoint] [--batch B]
 
 --eager launches every step's kernels one by one (no CUDA graph); --fields 2
 adds a Model A field (the 3D Model A + B pair); --tune passes launch-shape
 settings to pss_set_tuning (e.g. fast2d=0 for the generic 2D kernels);
 --adjoint runs the steps with checkpoints (pss_adjoint_forward) and then the
-backward pass of J = |phi_T|^2 / 2 (pss_adjoint_backward) instead.
+backward pass of J = |phi_T|^2 / 2 (pss_adjoint_backward) instead; --batch B
+runs B independent 2D Model B instances in one batched system (seeds
+2405 + i, the ensemble workload's parameters).
 """
 import argparse
 import os
@@ -25,6 +27,7 @@ def main():
     ap.add_argument("--eager", action="store_true")
     ap.add_argument("--tune", nargs="*", default=[], help="key=value launch-shape settings")
     ap.add_argument("--adjoint", action="store_true", help="forward with checkpoints, then the backward pass")
+    ap.add_argument("--batch", type=int, default=1, help="independent 2D Model B instances in one batched system")
     args = ap.parse_args()
     import torch
     from paper_2405_02410_gb300 import build
@@ -36,6 +39,10 @@ def main():
         if args.fields == 2:
             pss.add_model_a_field(s, a=-1, b=1, K=1, D=0.05, name="psi")
         pss.add_model_b_field(s, a=-1, b=1, K=1, D=0.05, name="phi")
+    elif args.batch > 1:
+        s = pss.System(shape, dt=0.01, batch=args.batch, seeds=[2405 + i for i in range(args.batch)],
+                       precision=args.precision)
+        pss.add_model_b_field(s, a=-1.0, b=1.0, K=1.0, D=0.01)
     else:
         s = pss.model_b(shape, dt=0.01, a=-1, b=1, K=1, D=0.01, seed=2405, precision=args.precision)
         if args.fields == 2:
@@ -43,8 +50,11 @@ def main():
     for kv in args.tune:
         k, v = kv.split("=")
         s.set_tuning(k, int(v))
-    for f in range(args.fields):
-        s.init_uniform(f, -0.1, 0.1)
+    for b in range(args.batch):
+        if args.batch > 1:
+            s.select_instance(b)
+        for f in range(args.fields):
+            s.init_uniform(f, -0.1, 0.1)
     if args.adjoint:
         s.adjoint_forward(args.steps)
         s.adjoint_backward(s.get_spectrum(0), 4)
