@@ -207,12 +207,16 @@ def oracle_rate(shape, steps, budget_s=20.0, keep_state=False):
 
 
 def _oracle_3d_field(field_id, steps):
-    """Half spectrum of one field of the 256^3 Model A + B pair after `steps` oracle steps (worker)."""
+    """Half spectrum of one field of the 256^3 Model A + B pair after `steps` oracle steps, and the
+    seconds those steps took (worker, one thread)."""
     from oracle import oracle as O
     shape = (256, 256, 256)
     mk = O.model_a if field_id == 0 else O.model_b
     m = mk(shape, dt=0.005, a=-1, b=1, K=1, D=0.05, seed=WORKLOAD["seed"], field_id=field_id)
-    return O.half(O.run(m, O.to_spectrum(m, O.init_uniform(m, -0.05, 0.05)), 0, steps))
+    phi = O.to_spectrum(m, O.init_uniform(m, -0.05, 0.05))
+    t0 = time.perf_counter()
+    phi = O.run(m, phi, 0, steps)
+    return O.half(phi), time.perf_counter() - t0
 
 
 def _rel_l2(a, b):
@@ -266,11 +270,12 @@ def oracle_parity(pss, stream, phi_1024, steps_1024, tuning, tuning3, probes, do
         g.step(steps_3d)
         got = [g.get_spectrum(0), g.get_spectrum(1)]
         g.close()
-        refs = fut3.get()
+        res = fut3.get()
         pool.close()
         pool.join()
-        out["model_ab_256cubed_f32"] = {"steps": steps_3d, "rel_l2_model_a": _rel_l2(got[0], refs[0]),
-                                        "rel_l2_model_b": _rel_l2(got[1], refs[1])}
+        out["model_ab_256cubed_f32"] = {"steps": steps_3d, "rel_l2_model_a": _rel_l2(got[0], res[0][0]),
+                                        "rel_l2_model_b": _rel_l2(got[1], res[1][0]),
+                                        "oracle_seconds_per_field": [res[0][1], res[1][1]]}
     return out
 
 
@@ -431,6 +436,22 @@ def cufft_comparison(torch, stream, shape=(1024, 1024), steps=2000, graph_steps=
     ms = e0.elapsed_time(e1) / (reps * graph_steps)
     return {"what": "cuFFT R2C/C2R (torch.fft) + torch element-wise ops, CUDA-graph replay, FP32, same GPU",
             "ms_per_step": ms, "site_steps_per_s": nx * ny / (ms * 1e-3)}
+
+
+def oracle_by_size(rate_1024, n_1024, parity):
+    """Single-thread oracle site-steps/s of Model B at 64^2 and 256^2 (bounded samples), at 1024^2 (the
+    cpu_baseline run) and of one field of the 256^3 pair (the parity leg's workers, one thread each)."""
+    by = {}
+    for shape, steps, budget in (((64, 64), 1000, 2.0), ((256, 256), 100, 4.0)):
+        r, n, _ = oracle_rate(shape, steps, budget_s=budget)
+        by["x".join(str(v) for v in shape)] = {"value": r, "steps": n}
+    by["1024x1024"] = {"value": rate_1024, "steps": n_1024}
+    p3 = parity.get("model_ab_256cubed_f32")
+    if p3:
+        secs = p3["oracle_seconds_per_field"]
+        by["256x256x256_per_field"] = {"value": 256 ** 3 * p3["steps"] / (sum(secs) / len(secs)),
+                                       "steps": p3["steps"]}
+    return by
 
 
 def oracle_all_cores(shape, budget_s=10.0):
@@ -808,6 +829,7 @@ def run_gpu(args):
         # the same oracle runs as the accuracy reference of the timed workloads
         line["parity_vs_fp64_oracle"] = oracle_parity(pss, stream, phi_o, n + 1, tuning, tuning3, probes,
                                                       do_3d=not args.no_3d)
+        line["cpu_baseline"]["by_size"] = oracle_by_size(rate, n, line["parity_vs_fp64_oracle"])
     s.close()
     s2.close()
     if rank == 0:
