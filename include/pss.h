@@ -176,8 +176,10 @@ int pss_init_uniform(pss_system *s, int field_id, double lo, double hi);
 int pss_step(pss_system *s, int64_t n);
 /* Advance n systems (for instance the size classes of an ensemble) by
  * `steps` steps each, replayed from one captured CUDA graph on systems[0]'s
- * stream (the other systems are moved to that stream).  Errors are reported
- * on systems[0]. */
+ * stream (the other systems are moved to that stream).  Distinct systems
+ * are independent branches of the graph, which the GPU may run side by
+ * side; a system listed more than once takes its steps in list order.
+ * Errors are reported on systems[0]. */
 int pss_step_many(pss_system **systems, int n, int64_t steps);
 /* Gradients by the hand-written adjoint of the step (single field, batch 1).
  * Inner product: dJ = Re sum_q conj(lambda_q) dphi_q over the full spectrum,

@@ -1,0 +1,58 @@
+"""Host-side logic that needs no GPU: the roofline byte counts of bench.py
+against their closed forms, the autotuner's report format, and the argument
+checks of the entry points that return before any CUDA call."""
+import ctypes
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _bench():
+    sys.path.insert(0, ROOT)
+    import bench
+    return bench
+
+
+def test_algorithmic_bytes_2d_1024():
+    # kept columns under the two-thirds rule: 3 |k| < 1024 -> kx = 0..341 (342 of the 513
+    # half-spectrum columns); per step 8 bytes x M modes x (4 + 2 f), M = 513 x 1024
+    b = _bench().algorithmic_bytes_2d(1024, 1024)
+    M = 513 * 1024
+    assert b["step"] == pytest.approx(8 * M * (4 + 2 * 342 / 513))
+    assert b["col"] + b["row"] == pytest.approx(b["step"])
+    assert round(b["step"] / 1e6, 2) == 22.41
+
+
+def test_algorithmic_bytes_3d_256():
+    # per field-step 8 M (6 + 2 fx fy + 2 fx), fx = 86/129 kept kx, fy = 171/256 kept ky
+    b = _bench().algorithmic_bytes_3d(256, 256, 256)
+    M = 129 * 256 * 256
+    fx, fy = 86 / 129, 171 / 256
+    assert b["step"] == pytest.approx(8 * M * (6 + 2 * fx * fy + 2 * fx))
+    assert round(b["step"] / 1e6, 1) == 556.2
+
+
+def test_whole_job_rate_single_rank():
+    value, t = _bench().whole_job_rate(1_000_000, 250.0, 1)
+    assert t == 250.0 and value == pytest.approx(4e6)
+
+
+def test_tune_report_parsing():
+    from paper_2405_02410_gb300 import pss
+    rep = pss.parse_tune_report("path=1 trials=25 skipped=0 initial_ms=0.015071 tuned_ms=0.0149 "
+                                "col2_radix=16 row2_pairs=0 pdl=-1 graph_steps=32")
+    assert rep == {"path": 1, "trials": 25, "skipped": 0, "initial_ms": 0.015071, "tuned_ms": 0.0149,
+                   "col2_radix": 16, "row2_pairs": 0, "pdl": -1, "graph_steps": 32}
+
+
+def test_null_handles_are_rejected_without_a_gpu():
+    from paper_2405_02410_gb300 import pss
+    lib = pss.lib
+    buf = ctypes.create_string_buffer(64)
+    assert lib.pss_autotune(None, 16, buf, len(buf)) == pss.PSS_EINVAL
+    assert lib.pss_set_tuning(None, b"pdl", 1) == pss.PSS_EINVAL
+    assert lib.pss_step(None, 1) == pss.PSS_EINVAL
+    assert lib.pss_step_path(None) == pss.PSS_EINVAL
