@@ -274,15 +274,37 @@ __device__ __forceinline__ void col_adjoint(const ColArgs<T> &a, const FieldP<T>
             }
         }
         __syncthreads();
-        // CTA reduction of the gradient sums, one FP64 atomic per value
+        // CTA reduction of the gradient sums, one FP64 atomic per value.  In
+        // FP32 the warp sum is compensated (TwoSum: hi + lo holds it to about
+        // the square of FP32 rounding) and only its result goes to FP64, once
+        // per warp: FP64 arithmetic runs at a small fraction of the FP32 rate
+        // on this GPU, and a butterfly of FP64 adds on every lane cost more
+        // than the rest of the update
         __shared__ double red[11];
         if (t < 11) red[t] = 0.0;
         __syncthreads();
 #pragma unroll
         for (int k = 0; k < 11; ++k) {
-            double v = (double)acc[k];
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if ((t & 31) == 0 && v != 0.0) atomicAdd(&red[k], v);
+            double v;
+            if constexpr (std::is_same<Acc, float>::value) {
+                float hi = acc[k], lo = 0.f;
+                for (int o = 16; o > 0; o >>= 1) {
+                    const float ohi = __shfl_xor_sync(0xffffffffu, hi, o);
+                    const float olo = __shfl_xor_sync(0xffffffffu, lo, o);
+                    const float s = __fadd_rn(hi, ohi), bp = __fsub_rn(s, hi);
+                    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(ohi, bp));
+                    hi = s;
+                    lo = __fadd_rn(__fadd_rn(lo, olo), err);
+                }
+                if ((t & 31) == 0) {
+                    v = (double)hi + (double)lo;
+                    if (v != 0.0) atomicAdd(&red[k], v);
+                }
+            } else {
+                v = (double)acc[k];
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if ((t & 31) == 0 && v != 0.0) atomicAdd(&red[k], v);
+            }
         }
         __syncthreads();
         if (t < 11 && red[t] != 0.0) atomicAdd(&a.grad[(size_t)(a.slot0 + blockIdx.z) * 11 + t], red[t]);
