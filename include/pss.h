@@ -257,7 +257,8 @@ int pss_set_tuning(pss_system *s, const char *key, int value);
  * kept only if its run is more than 1 % faster; each trial times at least
  * steps_per_trial steps (a whole number of graph replays) three times and
  * keeps the fastest.  Finally the starting settings and the result are
- * timed back to back; the result is kept only if it is faster there too.
+ * timed back to back, twice each; the result is kept only if it is not
+ * slower there.
  *
  * The trials advance the system: its spectral state and step counter are
  * saved first (one temporary device copy of the state, allocated and freed
