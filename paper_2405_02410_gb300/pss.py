@@ -101,8 +101,9 @@ def _arr(ctype, vals):
 
 
 class System:
-    """One lattice system: ``System(dim, shape, dx, dt, seed, precision)``; shape is
-    (nx,), (ny, nx) or (nz, ny, nx) like numpy arrays of the real field."""
+    """One lattice system (pss_create_system / pss_create_batch): ``System(shape, dt, dx, seed,
+    precision, batch, seeds)``; shape is (nx,), (ny, nx) or (nz, ny, nx) like numpy arrays of the
+    real field; batch > 1 (or seeds) makes independent instances keyed by seeds[i] (default seed + i)."""
 
     def __init__(self, shape: Sequence[int], dt: float, dx: Sequence[float] = (1.0, 1.0, 1.0),
                  seed: int = 0, precision: str = "f32", batch: int = 1, seeds: Optional[Sequence[int]] = None):
