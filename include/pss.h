@@ -245,6 +245,12 @@ int pss_time_kernels(pss_system *s, int64_t n, double *avg_ms);
  *                 launch (1, default, where its shared memory fits) or in
  *                 two (0); the adjoint fields agree bit for bit, the
  *                 gradients to the order of their FP64 atomic sums;
+ *   "test_timeout" a check of the bounded device waits, for tests: with 1,
+ *                 the first CTA of the generic column kernel expects 16
+ *                 bytes more than its bulk copies deliver and its waits give
+ *                 up after 1024 polls (a few milliseconds), so the next
+ *                 synchronising call returns PSS_ETIMEOUT; results of the
+ *                 steps taken meanwhile are wrong; 0 (default) turns it off;
  * 0 restores the automatic choice.  Unknown keys return PSS_EINVAL. */
 int pss_set_tuning(pss_system *s, const char *key, int value);
 
@@ -287,6 +293,26 @@ int pss_get_field(pss_system *s, int field_id, void *real_out, int where);
 /* Half spectrum [nz][ny][nx/2+1] out / in. */
 int pss_get_spectrum(pss_system *s, int field_id, void *half_out, int where);
 int pss_set_spectrum(pss_system *s, int field_id, const void *half_in, int where);
+
+/* Checkpoint and resume (the paper's runs write their state out at output
+ * steps, section "Example"; this is the whole state a step reads).
+ * pss_save_state writes into the host buffer buf: a header (format tag,
+ * lattice, precision, batch, number of fields and parameters, step counter),
+ * the parameter values of every instance [batch][nparams] (double), the
+ * per-instance seeds [batch] (uint64) and the half spectrum of every field of
+ * every instance [batch][nfields][nz][ny][nx/2+1] (the system's precision).
+ * With buf == NULL only *len is set to the size needed; with *len smaller
+ * than that, PSS_EINVAL and *len set to the size.  On success *len is the
+ * size written.  Synchronises.
+ * pss_load_state restores such a buffer into a system built the same way
+ * (same lattice, precision, batch, number of fields and parameters; else
+ * PSS_EINVAL and nothing changes): spectra, step counter, parameter values
+ * and seeds.  The next step's nonlinear product and noise are recomputed
+ * from the loaded state, so a resumed run takes the same steps, bit for bit,
+ * as one that was never interrupted.  Launch-shape settings (pss_set_tuning)
+ * are not part of the state.  Synchronises. */
+int pss_save_state(pss_system *s, void *buf, size_t *len);
+int pss_load_state(pss_system *s, const void *buf, size_t len);
 
 /* Radially binned structure factor S(q) = |phi_q|^2 / N_sites over
  * 0 < |q| <= pi/dx, nbins equal bins (b = ceil(|q| nbins dx / pi) - 1), over

@@ -19,40 +19,54 @@ import torch
 from . import pss as _pss
 
 
-def _weights(system: "_pss.System") -> np.ndarray:
-    w = np.full(system.nx // 2 + 1, 2.0)
+def _weights(system: "_pss.System", device, dtype) -> torch.Tensor:
+    w = torch.full((system.nx // 2 + 1,), 2.0, dtype=dtype, device=device)
     w[0] = 1.0
     w[-1] = 1.0
     return w
 
 
+def _cdtype(system: "_pss.System"):
+    return torch.complex128 if system.precision == "f64" else torch.complex64
+
+
 class PSSRun(torch.autograd.Function):
+    """The spectra stay on the device: h0, h_T, dJ/dh_T and dJ/dh0 are passed to the
+    library as device pointers on PyTorch's current stream (the system is moved to
+    that stream), so the run is ordered after the work that produced h0.  Only the
+    parameter values (host doubles of the C ABI) cross to the host."""
+
     @staticmethod
     def forward(ctx, h0, params, system, param_ids, nsteps, step0):
+        if not h0.is_cuda:
+            raise ValueError("h0 must be a CUDA tensor (the half spectrum stays on the device)")
         sys_ = system
+        sys_.set_stream(torch.cuda.current_stream(h0.device))
         for i, pid in enumerate(param_ids):
             sys_.set_param(pid, float(params[i]))
         sys_.set_step(step0)
-        sys_.set_spectrum(0, h0.detach().cpu().numpy().astype(sys_.cdtype))
+        sys_.set_spectrum(0, h0.detach().to(_cdtype(sys_)).contiguous())
         sys_.adjoint_forward(int(nsteps))
-        hT = torch.from_numpy(sys_.get_spectrum(0)).to(h0.device)
+        hT = torch.empty(sys_.half_shape, dtype=_cdtype(sys_), device=h0.device)
+        sys_.get_spectrum(0, out=hT)
         ctx.system = sys_
-        ctx.n_params = len(param_ids)
         ctx.param_ids = list(param_ids)
-        ctx.device = h0.device
         ctx.pdtype = params.dtype
-        return hT
+        ctx.hdtype = h0.dtype
+        return hT.to(h0.dtype)
 
     @staticmethod
     def backward(ctx, grad_hT):
         sys_ = ctx.system
-        w = _weights(sys_)
-        lam_T = grad_hT.detach().cpu().numpy() / w
+        sys_.set_stream(torch.cuda.current_stream(grad_hT.device))
+        rdt = torch.float64 if sys_.precision == "f64" else torch.float32
+        w = _weights(sys_, grad_hT.device, rdt)
+        lam_T = (grad_hT.detach().to(_cdtype(sys_)) / w).contiguous()
         n_all = len(sys_._param_names) if hasattr(sys_, "_param_names") else max(ctx.param_ids) + 1
         g_all, lam0 = sys_.adjoint_backward(lam_T, max(n_all, max(ctx.param_ids) + 1))
-        g = np.array([g_all[pid] for pid in ctx.param_ids])
-        grad_h0 = torch.from_numpy(lam0 * w).to(ctx.device)
-        return grad_h0, torch.from_numpy(g).to(dtype=ctx.pdtype, device=ctx.device), None, None, None, None
+        g = torch.tensor([g_all[pid] for pid in ctx.param_ids], dtype=ctx.pdtype, device=grad_hT.device)
+        grad_h0 = (lam0 * w).to(ctx.hdtype)
+        return grad_h0, g, None, None, None, None
 
 
 def run(h0: torch.Tensor, params: torch.Tensor, system: "_pss.System", param_ids, nsteps: int, step0: int = 0):

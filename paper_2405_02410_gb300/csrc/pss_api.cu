@@ -16,6 +16,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <mutex>
 #include <string>
 #include <type_traits>
@@ -60,6 +61,7 @@ struct GTerm {
 };
 
 constexpr int kDefaultGraphSteps = 16;
+constexpr int kTestWaitLimit = 1024;   // polls of a wait under the "test_timeout" check (a few ms)
 constexpr int kMaxBatch = 65535 / kMaxFields;
 constexpr double kPi = 3.14159265358979323846;
 
@@ -100,8 +102,22 @@ struct pss_system {
     int64_t step = 0;
     bool stale = true;                       // B does not hold the product of the current state
     bool b_fast = false;                     // B is in the column-major layout of the fast 2D path
-    cudaGraphExec_t graph = nullptr;
+    // captured step graphs by length (graphs[n]: n steps); all of them are
+    // dropped when the launches they hold change (invalidate)
+    std::vector<cudaGraphExec_t> graphs;
     bool graph_valid = false;
+    uint64_t gen = 0;                        // bumped by every invalidation (pss_step_many's cache)
+    uint64_t uid = 0;                        // unique per handle of the process (never reused)
+    // pss_step_many's graphs with this system first: the systems (by uid and
+    // generation at capture) and the number of steps of each
+    struct Many {
+        std::vector<uint64_t> uids, gens;
+        int len = 0;
+        cudaGraphExec_t exec = nullptr;
+        int64_t stamp = 0;
+    };
+    std::vector<Many> many;
+    int64_t many_clock = 0;
     // launch-shape tuning (pss_set_tuning); 0 = automatic
     int tune_pdl = -1, tune_row_pairs = 0, tune_col_tiles = 0, tune_graph_steps = 0, tune_mid_planes = 0;
     int tune_col_radix = 0, tune_row_radix = 0, tune_mid_radix = 0;   // FFT radix caps (8 or 16; 0 = automatic)
@@ -115,6 +131,7 @@ struct pss_system {
     int tune_row2_share = -1;                // % of the noise drawn by extra CTAs on idle SMs (-1 = automatic: 0)
     int num_sms = 0;
     int tune_fast3d = 1;                     // FP32 3D x pass with one FFT group per row pair (0 = generic k_row)
+    int tune_test_timeout = 0;               // check of the bounded waits: one CTA's wait runs out (tests)
     int64_t launches = 0;
     std::string err;
     // adjoint: checkpoints of the last pss_adjoint_forward run
@@ -193,6 +210,8 @@ template <typename T> SysP<T> sys_params(const pss_system *s) {
     // programmatic dependent launch (tuning key "pdl"; by default only the
     // FFT-group kernels k2_col / k2_row take it, see pdl_fast)
     p.pdl = s->tune_pdl >= 0 ? s->tune_pdl : 0;
+    p.wait_limit = s->tune_test_timeout ? kTestWaitLimit : 0;
+    p.tx_extra = s->tune_test_timeout ? 16u : 0u;
     return p;
 }
 
@@ -1073,23 +1092,39 @@ int capture_graph(pss_system **sys, int n, int steps, cudaGraphExec_t *out) {
     return PSS_OK;
 }
 
+void drop_graphs(pss_system *s) {
+    for (cudaGraphExec_t &g : s->graphs)
+        if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+}
+
+// Every run of steps replays captured graphs: whole graphs of `graph_steps`
+// steps, then one graph of the remaining length (captured on its first use
+// and kept), so that the launches per step do not depend on n.
 int run_steps(pss_system *s, int64_t n) {
     const int chunk = s->tune_graph_steps > 0 ? s->tune_graph_steps : kDefaultGraphSteps;
-    int64_t done = 0;
-    if (n >= chunk) {
-        if (!s->graph_valid) {
-            if (s->graph) { cudaGraphExecDestroy(s->graph); s->graph = nullptr; }
-            int rc = capture_graph(&s, 1, chunk, &s->graph);
-            if (rc) return rc;
-            s->graph_valid = true;
-        }
-        while (n - done >= chunk) {
-            CK(cudaGraphLaunch(s->graph, s->stream));
-            s->launches += (int64_t)chunk * s->graph_launches;
-            done += chunk;
-        }
+    if (!s->graph_valid) {
+        drop_graphs(s);
+        s->graph_valid = true;
     }
-    return record_steps(s, s->stream, n - done);
+    if ((int)s->graphs.size() < chunk + 1) s->graphs.resize(chunk + 1, nullptr);
+    auto graph_of = [&](int len, cudaGraphExec_t *g) -> int {
+        if (!s->graphs[len]) {
+            int rc = capture_graph(&s, 1, len, &s->graphs[len]);
+            if (rc) { s->graphs[len] = nullptr; return rc; }
+        }
+        *g = s->graphs[len];
+        return PSS_OK;
+    };
+    int64_t done = 0;
+    while (done < n) {
+        const int len = (int)std::min<int64_t>(chunk, n - done);
+        cudaGraphExec_t g = nullptr;
+        if (int rc = graph_of(len, &g)) return rc;
+        CK(cudaGraphLaunch(g, s->stream));
+        s->launches += (int64_t)len * s->graph_launches;
+        done += len;
+    }
+    return PSS_OK;
 }
 
 template <typename T> int timed_steps(pss_system *s, int64_t n, double *avg_ms) {
@@ -1156,7 +1191,9 @@ int device_errors(pss_system *s) {
 void invalidate(pss_system *s) {
     s->graph_valid = false;
     s->adj_graph_valid = false;
+    s->gen++;
 }
+
 
 // (re)allocate the slot arrays for the current number of slots, keeping the
 // data of the slots that exist
@@ -1202,6 +1239,8 @@ int do_create(pss_system **out, int batch, int dim, int nx, int ny, int nz, doub
     if (precision != PSS_F32 && precision != PSS_F64) return fail(nullptr, PSS_EINVAL, "precision");
     if ((long long)nx * ny * nz > (1ll << 30)) return fail(nullptr, PSS_EUNSUPPORTED, "lattice too large");
     pss_system *s = new pss_system();
+    static std::atomic<uint64_t> next_uid{1};
+    s->uid = next_uid++;
     s->dim = dim; s->nx = nx; s->ny = ny; s->nz = nz;
     s->dx[0] = dx; s->dx[1] = dim >= 2 ? dy : 1.0; s->dx[2] = dim == 3 ? dz : 1.0;
     s->dt = dt; s->prec = precision;
@@ -1382,7 +1421,8 @@ int pss_create_batch(pss_system **out, int batch, int dim, int nx, int ny, int n
 
 int pss_destroy_system(pss_system *s) {
     if (!s) return PSS_OK;
-    if (s->graph) cudaGraphExecDestroy(s->graph);
+    drop_graphs(s);
+    for (auto &m : s->many) if (m.exec) cudaGraphExecDestroy(m.exec);
     cudaFree(s->state);
     cudaFree(s->A);
     cudaFree(s->B);
@@ -1686,22 +1726,48 @@ int pss_step_many(pss_system **systems, int n, int64_t steps) {
     }
     if (steps == 0) return PSS_OK;
     const int chunk = s0->tune_graph_steps > 0 ? s0->tune_graph_steps : kDefaultGraphSteps;
-    int64_t done = 0;
-    if (steps >= chunk) {
+    // graphs of whole chunks and of the remainder, kept on systems[0] for this
+    // list of systems as long as none of them changed its launches
+    auto graph_of = [&](int len, cudaGraphExec_t *out) -> int {
+        std::vector<uint64_t> uids(n), gens(n);
+        for (int i = 0; i < n; ++i) { uids[i] = systems[i]->uid; gens[i] = systems[i]->gen; }
+        for (auto &m : s0->many)
+            if (m.len == len && m.uids == uids && m.gens == gens) {
+                m.stamp = ++s0->many_clock;
+                *out = m.exec;
+                return PSS_OK;
+            }
         cudaGraphExec_t ge = nullptr;
-        int rc = capture_graph(systems, n, chunk, &ge);
+        int rc = capture_graph(systems, n, len, &ge);
         if (rc) return rc;
-        cudaError_t e = cudaSuccess;
-        for (; steps - done >= chunk && e == cudaSuccess; done += chunk) e = cudaGraphLaunch(ge, s0->stream);
-        cudaGraphExecDestroy(ge);
-        if (e != cudaSuccess) return cuda_fail(s0, e, "cudaGraphLaunch");
-        for (int i = 0; i < n; ++i) systems[i]->launches += done * systems[i]->graph_launches;
-    }
-    for (; done < steps; ++done)
-        for (int i = 0; i < n; ++i) {
-            int rc = record_steps(systems[i], s0->stream, 1);
-            if (rc) return i == 0 ? rc : fail(s0, rc, "%s", systems[i]->err.c_str());
+        constexpr size_t kKeep = 8;
+        if (s0->many.size() >= kKeep) {   // the least recently used entry goes
+            size_t old = 0;
+            for (size_t k = 1; k < s0->many.size(); ++k)
+                if (s0->many[k].stamp < s0->many[old].stamp) old = k;
+            cudaGraphExecDestroy(s0->many[old].exec);
+            s0->many.erase(s0->many.begin() + (long)old);
         }
+        pss_system::Many m;
+        m.uids = uids;
+        m.gens = gens;
+        m.len = len;
+        m.exec = ge;
+        m.stamp = ++s0->many_clock;
+        s0->many.push_back(m);
+        *out = ge;
+        return PSS_OK;
+    };
+    int64_t done = 0;
+    while (done < steps) {
+        const int len = (int)std::min<int64_t>(chunk, steps - done);
+        cudaGraphExec_t ge = nullptr;
+        if (int rc = graph_of(len, &ge)) return rc;
+        cudaError_t e = cudaGraphLaunch(ge, s0->stream);
+        if (e != cudaSuccess) return cuda_fail(s0, e, "cudaGraphLaunch");
+        for (int i = 0; i < n; ++i) systems[i]->launches += (int64_t)len * systems[i]->graph_launches;
+        done += len;
+    }
     for (int i = 0; i < n; ++i) systems[i]->step += steps;
     return PSS_OK;
 }
@@ -1810,6 +1876,7 @@ int pss_set_tuning(pss_system *s, const char *key, int value) {
     else if (k == "fast3d") s->tune_fast3d = value ? 1 : 0;
     else if (k == "fuse_adjoint") s->tune_fuse_adj = value ? 1 : 0;
     else if (k == "real_state") s->tune_real_state = value ? 1 : 0;
+    else if (k == "test_timeout") s->tune_test_timeout = value ? 1 : 0;
     else if (k == "col2_warps") {
         if (value > 24) return fail(s, PSS_EINVAL, "col2_warps is at most 24 (0 = automatic)");
         s->tune_col2_warps = value;
@@ -2095,6 +2162,127 @@ int pss_set_spectrum(pss_system *s, int field_id, const void *half_in, int where
     return PSS_OK;
 }
 
+// ---- checkpoint / resume -------------------------------------------------
+// The saved state is everything a step reads that the caller can change:
+// the half spectra of every field of every instance (in the exchange layout
+// [nz][ny][nx/2+1], independent of the device layout), the step counter (the
+// next step's noise index), the parameter values of every instance and the
+// per-instance seeds.  The next step's product and drawn-ahead noise are not
+// saved: both are functions of the state and the step counter, recomputed
+// before the first step after a load.
+namespace {
+struct StateHeader {
+    char magic[8];
+    uint32_t version, header_bytes;
+    int32_t dim, nx, ny, nz, precision, batch, nfields, nparams;
+    int64_t step;
+    uint64_t payload_bytes;
+};
+constexpr char kStateMagic[8] = {'P', 'S', 'S', 'S', 'T', 'A', 'T', 'E'};
+
+size_t state_payload(const pss_system *s) {
+    const size_t half = csize(s) * (size_t)s->hx * s->ny * s->nz;
+    return sizeof(double) * (size_t)s->batch * s->param_names.size() + sizeof(uint64_t) * (size_t)s->batch +
+           half * (size_t)s->nslots();
+}
+}  // namespace
+
+int pss_save_state(pss_system *s, void *buf, size_t *len) {
+    if (!s || !len) return PSS_EINVAL;
+    if (s->fields.empty()) return fail(s, PSS_EINVAL, "no fields");
+    const size_t need = sizeof(StateHeader) + state_payload(s);
+    if (!buf) {
+        *len = need;
+        return PSS_OK;
+    }
+    if (*len < need) {
+        *len = need;
+        return fail(s, PSS_EINVAL, "buffer too small: %zu bytes needed", need);
+    }
+    int rc = ensure_half(s);
+    if (rc) return rc;
+    StateHeader h{};
+    std::memcpy(h.magic, kStateMagic, 8);
+    h.version = 1;
+    h.header_bytes = sizeof(StateHeader);
+    h.dim = s->dim; h.nx = s->nx; h.ny = s->ny; h.nz = s->nz;
+    h.precision = s->prec;
+    h.batch = s->batch;
+    h.nfields = (int)s->fields.size();
+    h.nparams = (int)s->param_names.size();
+    h.step = s->step;
+    h.payload_bytes = state_payload(s);
+    char *p = (char *)buf;
+    std::memcpy(p, &h, sizeof h);
+    p += sizeof h;
+    const size_t pv = sizeof(double) * s->param_values.size();
+    if (pv) std::memcpy(p, s->param_values.data(), pv);
+    p += pv;
+    std::memcpy(p, s->seeds.data(), sizeof(uint64_t) * (size_t)s->batch);
+    p += sizeof(uint64_t) * (size_t)s->batch;
+    const size_t half = csize(s) * (size_t)s->hx * s->ny * s->nz;
+    for (int slot = 0; slot < s->nslots(); ++slot, p += half) {
+        const size_t ofs = csize(s) * s->field_elems * (size_t)slot;
+        cudaError_t e = s->prec == PSS_F64
+            ? launch_tiles_to_half<double>(sys_params<double>(s), (const double2 *)((char *)s->state + ofs),
+                                           (double2 *)s->half, s->stream)
+            : launch_tiles_to_half<float>(sys_params<float>(s), (const float2 *)((char *)s->state + ofs),
+                                          (float2 *)s->half, s->stream);
+        s->launches++;
+        if (e != cudaSuccess) return cuda_fail(s, e, "layout kernel");
+        CK(cudaMemcpyAsync(p, s->half, half, cudaMemcpyDeviceToHost, s->stream));
+        CK(cudaStreamSynchronize(s->stream));   // s->half is reused by the next slot
+    }
+    *len = need;
+    return device_errors(s);
+}
+
+int pss_load_state(pss_system *s, const void *buf, size_t len) {
+    if (!s || !buf) return PSS_EINVAL;
+    if (s->fields.empty()) return fail(s, PSS_EINVAL, "no fields");
+    StateHeader h{};
+    if (len < sizeof h) return fail(s, PSS_EINVAL, "not a saved state: %zu bytes", len);
+    std::memcpy(&h, buf, sizeof h);
+    if (std::memcmp(h.magic, kStateMagic, 8) != 0 || h.version != 1 || h.header_bytes != sizeof h)
+        return fail(s, PSS_EINVAL, "not a saved state of this format");
+    if (h.dim != s->dim || h.nx != s->nx || h.ny != s->ny || h.nz != s->nz || h.precision != s->prec ||
+        h.batch != s->batch || h.nfields != (int)s->fields.size() || h.nparams != (int)s->param_names.size())
+        return fail(s, PSS_EINVAL,
+                    "saved state of a different system (dim %d, %dx%dx%d, precision %d, batch %d, %d fields, "
+                    "%d parameters)", h.dim, h.nx, h.ny, h.nz, h.precision, h.batch, h.nfields, h.nparams);
+    if (h.payload_bytes != state_payload(s) || len < sizeof h + h.payload_bytes || h.step < 0)
+        return fail(s, PSS_EINVAL, "saved state is truncated or inconsistent");
+    int rc = ensure_half(s);
+    if (rc) return rc;
+    const char *p = (const char *)buf + sizeof h;
+    const size_t pv = sizeof(double) * s->param_values.size();
+    if (pv) std::memcpy(s->param_values.data(), p, pv);
+    p += pv;
+    std::memcpy(s->seeds.data(), p, sizeof(uint64_t) * (size_t)s->batch);
+    p += sizeof(uint64_t) * (size_t)s->batch;
+    s->fps_dirty = true;
+    const size_t half = csize(s) * (size_t)s->hx * s->ny * s->nz;
+    for (int slot = 0; slot < s->nslots(); ++slot, p += half) {
+        CK(cudaMemcpyAsync(s->half, p, half, cudaMemcpyHostToDevice, s->stream));
+        const size_t ofs = csize(s) * s->field_elems * (size_t)slot;
+        cudaError_t e = s->prec == PSS_F64
+            ? launch_half_to_tiles<double>(sys_params<double>(s), (const double2 *)s->half,
+                                           (double2 *)((char *)s->state + ofs), s->stream)
+            : launch_half_to_tiles<float>(sys_params<float>(s), (const float2 *)s->half,
+                                          (float2 *)((char *)s->state + ofs), s->stream);
+        s->launches++;
+        if (e != cudaSuccess) return cuda_fail(s, e, "layout kernel");
+        CK(cudaStreamSynchronize(s->stream));   // the host buffer and s->half are reused
+    }
+    long long v = h.step;
+    CK(cudaMemcpyAsync(s->d_step, &v, sizeof v, cudaMemcpyHostToDevice, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    s->step = h.step;
+    s->stale = true;   // the next step's product and noise come from the loaded state
+    if (!s->gterms.empty()) invalidate(s);   // product-term operators are launch arguments
+    return device_errors(s);
+}
+
 int pss_structure_factor(pss_system *s, int field_id, int nbins, double *S_out, double *count_out, double *L_out) {
     int rc = check_field(s, field_id);
     if (rc) return rc;
@@ -2103,6 +2291,7 @@ int pss_structure_factor(pss_system *s, int field_id, int nbins, double *S_out, 
     if (s->sq_cap < need) {
         cudaFree(s->sq);
         s->sq = nullptr;
+        s->sq_cap = 0;   // a failed allocation below leaves no capacity behind
         CK(cudaMalloc(&s->sq, sizeof(double) * need));
         s->sq_cap = need;
     }

@@ -358,15 +358,17 @@ __device__ __forceinline__ bool mbar_poll(uint64_t *bar, uint32_t phase) {
     return false;
 }
 
-// All threads wait for phase `phase` of `bar`.  Returns true for the whole
-// CTA when the copies landed; false (for the whole CTA) when a bounded wait
-// ran out, after a second bounded wait for the copies still in flight.
-__device__ __forceinline__ bool mbar_wait_all(uint64_t *bar, uint32_t phase, int *status) {
+// All threads wait for phase `phase` of `bar` (at most `limit` polls each,
+// 0: kWaitLimit).  Returns true for the whole CTA when the copies landed;
+// false (for the whole CTA) when a bounded wait ran out, after a second
+// bounded wait for the copies still in flight.
+__device__ __forceinline__ bool mbar_wait_all(uint64_t *bar, uint32_t phase, int *status, int limit = kWaitLimit) {
     bool ok = false;
-    for (int it = 0; it < kWaitLimit && !ok; ++it) ok = mbar_try_wait(bar, phase);
+    if (limit <= 0) limit = kWaitLimit;
+    for (int it = 0; it < limit && !ok; ++it) ok = mbar_try_wait(bar, phase);
     if (__syncthreads_and(ok)) return true;
     if (threadIdx.x == 0 && status) atomicOr(status, kStatusTimeout);
-    for (int it = 0; it < kWaitLimit && !ok; ++it) ok = mbar_try_wait(bar, phase);
+    for (int it = 0; it < limit && !ok; ++it) ok = mbar_try_wait(bar, phase);
     __syncthreads();
     return false;
 }

@@ -64,6 +64,11 @@ template <typename T> struct SysP {
     T gx, gy, gz;         // 2 pi / (N dx) per axis (0 for unused axes)
     T dt, inv_nsites;
     int pdl;              // launch with programmatic stream serialisation
+    // bounded-wait check (tuning key "test_timeout"): polls before a wait of
+    // the generic column kernel gives up (0: the default limit), and bytes
+    // its first CTA's mbarrier expects beyond what its copies deliver
+    int wait_limit;
+    uint32_t tx_extra;
 };
 
 enum ColMode {

@@ -398,8 +398,11 @@ __global__ void __launch_bounds__(512, (N >= 512 || ADJ) ? 1 : 2) k_col(const Co
     pdl_trigger();
     if (t == 0) {
         mbar_init(bar, 1);
+        // (tx_extra: the bounded-wait check makes the first CTA expect more
+        // bytes than its copies deliver, so that its wait runs out)
+        const uint32_t extra = (blockIdx.x | blockIdx.y | blockIdx.z) == 0 ? sp.tx_extra : 0u;
         mbar_expect_tx(bar, chunk_bytes * nvalid * ((need_in ? 1 : 0) + (need_phi ? 1 : 0) + (need_in2 ? 1 : 0)) +
-                                twiddle_bytes<C, N>());
+                                twiddle_bytes<C, N>() + extra);
         if (twiddle_bytes<C, N>()) bulk_g2s(TW, a.tw + twiddle_offset(N, EMAX), twiddle_bytes<C, N>(), bar);
         for (int ch = 0; ch < nvalid; ++ch) {
             if (need_phi) bulk_g2s(PHI + ch * CS, a.state + sofs + gofs(ch), chunk_bytes, bar);
@@ -418,7 +421,7 @@ __global__ void __launch_bounds__(512, (N >= 512 || ADJ) ? 1 : 2) k_col(const Co
         X[ch * CS + r] = mk<T>(0, 0);
         if (need_in2) Z[ch * CS + r] = mk<T>(0, 0);
     }
-    if (!mbar_wait_all(bar, 0, a.d_status)) return;
+    if (!mbar_wait_all(bar, 0, a.d_status, sp.wait_limit)) return;
 
     // this thread's FFT: column c of chunk ch
     const int f = t & (F - 1), lane = t >> logF;

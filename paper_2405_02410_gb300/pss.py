@@ -30,7 +30,7 @@ EXPORTS = [
     "pss_time_kernels", "pss_set_tuning", "pss_create_batch", "pss_batch_size", "pss_select_instance",
     "pss_set_param_batch", "pss_step_many", "pss_adjoint_forward", "pss_adjoint_backward",
     "pss_structure_factor_noalloc", "pss_step_path", "pss_set_frame", "pss_add_grad_sq_term",
-    "pss_add_product_term", "pss_autotune",
+    "pss_add_product_term", "pss_autotune", "pss_save_state", "pss_load_state",
 ]
 
 
@@ -84,6 +84,8 @@ def _load():
         "pss_step_many": ([P(vp), i32, i64], i32),
         "pss_adjoint_forward": ([vp, i64], i32),
         "pss_adjoint_backward": ([vp, vp, i32, P(d), vp, i32], i32),
+        "pss_save_state": ([vp, vp, P(ctypes.c_size_t)], i32),
+        "pss_load_state": ([vp, vp, ctypes.c_size_t], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -270,6 +272,20 @@ class System:
             a = np.ascontiguousarray(half, dtype=self.cdtype).reshape(self.half_shape)
             self._ck(lib.pss_set_spectrum(self._h, field, a.ctypes.data_as(ctypes.c_void_p), PSS_HOST))
 
+    def save_state(self) -> bytes:
+        """The whole state (spectra of every field and instance, step counter, parameters, seeds)
+        as bytes (pss_save_state)."""
+        n = ctypes.c_size_t(0)
+        self._ck(lib.pss_save_state(self._h, None, ctypes.byref(n)))
+        buf = ctypes.create_string_buffer(n.value)
+        self._ck(lib.pss_save_state(self._h, ctypes.cast(buf, ctypes.c_void_p), ctypes.byref(n)))
+        return buf.raw[: n.value]
+
+    def load_state(self, blob: bytes):
+        """Restore a state written by save_state into a system built the same way (pss_load_state)."""
+        buf = ctypes.create_string_buffer(bytes(blob), len(blob))
+        self._ck(lib.pss_load_state(self._h, ctypes.cast(buf, ctypes.c_void_p), len(blob)))
+
     def structure_factor(self, field: int, nbins: int = 64):
         S = np.zeros(nbins)
         cnt = np.zeros(nbins)
@@ -324,10 +340,22 @@ class System:
         self._ck(lib.pss_adjoint_forward(self._h, int(n)))
 
     def adjoint_backward(self, lambda_T, n_params: int):
-        """dJ/dphi_T (half spectrum, numpy) -> (dJ/dparams[n_params], dJ/dphi_0 half spectrum)."""
+        """dJ/dphi_T (half spectrum) -> (dJ/dparams[n_params] numpy, dJ/dphi_0 half spectrum).
+        lambda_T a numpy array: dJ/dphi_0 comes back as numpy; a torch CUDA tensor of the
+        system's complex dtype (contiguous, used on the system's stream): it comes back as a
+        new CUDA tensor, and the spectra never leave the device."""
+        g = np.zeros(max(1, n_params))
+        if _is_cuda_tensor(lambda_T):
+            import torch
+            assert lambda_T.is_contiguous() and tuple(lambda_T.shape) == self.half_shape
+            assert lambda_T.dtype == (torch.complex128 if self.precision == "f64" else torch.complex64)
+            out = torch.empty_like(lambda_T)
+            self._ck(lib.pss_adjoint_backward(self._h, ctypes.c_void_p(lambda_T.data_ptr()), PSS_DEVICE,
+                                              g.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                              ctypes.c_void_p(out.data_ptr()), PSS_DEVICE))
+            return g[:n_params], out
         lam = np.ascontiguousarray(lambda_T, dtype=self.cdtype).reshape(self.half_shape)
         out = np.empty(self.half_shape, dtype=self.cdtype)
-        g = np.zeros(max(1, n_params))
         self._ck(lib.pss_adjoint_backward(self._h, lam.ctypes.data_as(ctypes.c_void_p), PSS_HOST,
                                           g.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                           out.ctypes.data_as(ctypes.c_void_p), PSS_HOST))

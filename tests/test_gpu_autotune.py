@@ -13,6 +13,8 @@ import pytest
 
 from oracle import oracle as O
 
+from tests.parity import check_spectrum  # noqa: E402
+
 pytestmark = pytest.mark.gpu
 
 
@@ -133,10 +135,10 @@ def test_autotune_batch_and_step_many():
         one.init_uniform(0, -0.1, 0.1)
         one.step(40)
         s.select_instance(i)
-        assert rel(s.get_spectrum(0), one.get_spectrum(0)) < 1e-5
+        check_spectrum(s.get_spectrum(0), one.get_spectrum(0), 1e-5)
     ref = O.model_b((64, 64), dt=0.01, a=-1.0, b=1.0, K=1.0, D=0.01, seed=7)
     want = O.half(O.run(ref, O.to_spectrum(ref, O.init_uniform(ref, -0.1, 0.1)), 0, 40))
-    assert rel(other.get_spectrum(0), want) < 1e-4
+    check_spectrum(other.get_spectrum(0), want, 1e-4)
 
 
 def test_autotune_rejects_bad_arguments():

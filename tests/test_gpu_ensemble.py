@@ -6,6 +6,8 @@ import pytest
 
 from oracle import oracle as O
 
+from tests.parity import check_spectrum  # noqa: E402
+
 pytestmark = pytest.mark.gpu
 
 
@@ -63,7 +65,7 @@ def test_batch_matches_oracle(prec, tol):
         m = O.model_b(shape, dt=0.01, a=av, b=1.0, K=1.0, D=0.01, seed=sd)
         ref = O.half(O.run(m, O.to_spectrum(m, O.init_uniform(m, -0.1, 0.1)), 0, steps))
         s.select_instance(i)
-        assert rel(s.get_spectrum(0), ref) < tol
+        check_spectrum(s.get_spectrum(0), ref, tol)
 
 
 def test_step_many_mixed_sizes_equal_separate_runs():

@@ -5,6 +5,8 @@ import pytest
 
 from oracle import oracle as O
 
+from tests.parity import check_spectrum  # noqa: E402
+
 pytestmark = pytest.mark.gpu
 
 
@@ -42,7 +44,7 @@ def test_heat_bath(prec, tol):
     s.set_field(0, np.full(n, 5.0))
     s.set_frame(0, w, t1, t2)
     s.step(steps)
-    assert rel(s.get_spectrum(0), O.half(ref)) < tol
+    check_spectrum(s.get_spectrum(0), O.half(ref), tol)
     r = s.get_field(0)
     np.testing.assert_allclose(r[:w], t1, atol=1e-9 if prec == "f64" else 1e-4)
     np.testing.assert_allclose(r[n - w:], t2, atol=1e-9 if prec == "f64" else 1e-4)
@@ -58,7 +60,7 @@ def test_model_b_with_a_frame(shape, prec, tol, steps):
     s.init_uniform(0, -0.2, 0.2)
     s.set_frame(0, 4, 0.3, -0.3)
     s.step(steps)
-    assert rel(s.get_spectrum(0), O.half(ref)) < tol
+    check_spectrum(s.get_spectrum(0), O.half(ref), tol)
 
 
 def test_3d_pair_with_a_frame_on_one_field():
@@ -76,7 +78,7 @@ def test_3d_pair_with_a_frame_on_one_field():
     refs = [O.run(ma, O.to_spectrum(ma, O.init_uniform(ma, -0.05, 0.05)), 0, steps),
             O.run_framed(mb, O.to_spectrum(mb, O.init_uniform(mb, -0.05, 0.05)), 0, steps, 3, 0.1, -0.2)]
     for fid in (0, 1):
-        assert rel(s.get_spectrum(fid), O.half(refs[fid])) < 1e-10, fid
+        check_spectrum(s.get_spectrum(fid), O.half(refs[fid]), 1e-10, what=str(fid))
 
 
 @pytest.mark.parametrize("shape,prec,tol", [((128, 128), "f64", 1e-12), ((256, 256), "f32", 1e-5),
@@ -107,7 +109,7 @@ def test_batched_instances_each_take_the_frame():
         m = O.model_b(shape, dt=0.01, a=-1.0, b=1.0, K=1.0, D=0.05, seed=seeds[i])
         ref = O.run_framed(m, O.to_spectrum(m, O.init_uniform(m, -0.1, 0.1)), 0, 10, 2, 0.25, -0.25)
         s.select_instance(i)
-        assert rel(s.get_spectrum(0), O.half(ref)) < 1e-10, i
+        check_spectrum(s.get_spectrum(0), O.half(ref), 1e-10, what=str(i))
 
 
 def test_launches_per_framed_step_and_graph_bookkeeping():

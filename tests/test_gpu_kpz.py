@@ -5,6 +5,8 @@ import pytest
 
 from oracle import oracle as O
 
+from tests.parity import check_spectrum  # noqa: E402
+
 pytestmark = pytest.mark.gpu
 
 
@@ -43,7 +45,7 @@ def test_kpz_matches_oracle(shape, prec, tol, steps):
     s.init_uniform(0, -0.5, 0.5)
     s.step(steps)
     _, ref = _oracle(shape, steps, 41)
-    assert rel(s.get_spectrum(0), O.half(ref)) < tol
+    check_spectrum(s.get_spectrum(0), O.half(ref), tol)
 
 
 def test_kpz_order_zero_and_three():
@@ -52,7 +54,7 @@ def test_kpz_order_zero_and_three():
         s.init_uniform(0, -0.5, 0.5)
         s.step(25)
         _, ref = _oracle((64, 64), 25, 9, order=order)
-        assert rel(s.get_spectrum(0), O.half(ref)) < 1e-10, order
+        check_spectrum(s.get_spectrum(0), O.half(ref), 1e-10, what=str(order))
 
 
 def test_kpz_beside_a_model_b_field():
@@ -68,8 +70,8 @@ def test_kpz_beside_a_model_b_field():
     _, ref_h = _oracle(shape, steps, 13, field_id=0)
     mb = O.model_b(shape, dt=0.02, a=-1, b=1, K=1, D=0.05, seed=13, field_id=1)
     ref_b = O.run(mb, O.to_spectrum(mb, O.init_uniform(mb, -0.1, 0.1)), 0, steps)
-    assert rel(s.get_spectrum(0), O.half(ref_h)) < 1e-10
-    assert rel(s.get_spectrum(1), O.half(ref_b)) < 1e-10
+    check_spectrum(s.get_spectrum(0), O.half(ref_h), 1e-10)
+    check_spectrum(s.get_spectrum(1), O.half(ref_b), 1e-10)
 
 
 def test_kpz_batched_instances():
@@ -84,7 +86,7 @@ def test_kpz_batched_instances():
     for i in range(3):
         _, ref = _oracle(shape, 20, seeds[i])
         s.select_instance(i)
-        assert rel(s.get_spectrum(0), O.half(ref)) < 1e-10, i
+        check_spectrum(s.get_spectrum(0), O.half(ref), 1e-10, what=str(i))
 
 
 def test_kpz_with_a_frame():
@@ -95,7 +97,7 @@ def test_kpz_with_a_frame():
     s.step(steps)
     m = O.kpz((n,), seed=2, **KW)
     ref = O.run_framed(m, O.to_spectrum(m, O.init_uniform(m, -0.5, 0.5)), 0, steps, 5, 1.0, -1.0)
-    assert rel(s.get_spectrum(0), O.half(ref)) < 1e-10
+    check_spectrum(s.get_spectrum(0), O.half(ref), 1e-10)
 
 
 def test_kpz_launches_and_limits():
@@ -127,4 +129,4 @@ def test_kpz_with_a_cubic_term():
     terms = [O.Term(0, [(KW["lam"], 0)], [O.Factor(0, 2, deriv=j)]) for j in (0, 1)]
     terms.append(O.Term(0, [(-0.3, 0)], [O.Factor(0, 3)]))
     ref = O.run_coupled([m], terms, [O.to_spectrum(m, O.init_uniform(m, -0.5, 0.5))], 0, steps)[0]
-    assert rel(s.get_spectrum(0), O.half(ref)) < 1e-10
+    check_spectrum(s.get_spectrum(0), O.half(ref), 1e-10)

@@ -8,6 +8,8 @@ import pytest
 
 from oracle import oracle as O
 
+from tests.parity import check_spectrum  # noqa: E402
+
 pytestmark = pytest.mark.gpu
 
 
@@ -77,7 +79,7 @@ def test_coupled_pair_matches_oracle(shape, prec, tol, steps):
     ms, terms = _pair_oracle(shape, dt, seed)
     ref = O.run_coupled(ms, terms, _init_oracle(ms), 0, steps)
     for fid in (0, 1):
-        assert rel(s.get_spectrum(fid), O.half(ref[fid])) < tol, fid
+        check_spectrum(s.get_spectrum(fid), O.half(ref[fid]), tol, what=str(fid))
 
 
 def test_batched_coupling_parameters():
@@ -95,7 +97,7 @@ def test_batched_coupling_parameters():
         ref = O.run_coupled(ms, terms, _init_oracle(ms), 0, 20)
         s.select_instance(i)
         for fid in (0, 1):
-            assert rel(s.get_spectrum(fid), O.half(ref[fid])) < 1e-10, (i, fid)
+            check_spectrum(s.get_spectrum(fid), O.half(ref[fid]), 1e-10, what=str((i, fid)))
 
 
 def test_changing_a_coupling_between_runs():
@@ -112,7 +114,7 @@ def test_changing_a_coupling_between_runs():
     ms2, terms2 = _pair_oracle(shape, dt, 9, p={**P0, "g": 1.4, "h": 0.1})
     ref = O.run_coupled(ms2, terms2, mid, 17, 17)
     for fid in (0, 1):
-        assert rel(s.get_spectrum(fid), O.half(ref[fid])) < 1e-10, fid
+        check_spectrum(s.get_spectrum(fid), O.half(ref[fid]), 1e-10, what=str(fid))
 
 
 def test_linear_coupling_rotates_uniform_fields():
@@ -150,7 +152,7 @@ def test_burgers_and_a_laplacian_factor(shape, prec, tol):
     terms = [O.Term(0, [(-1.0, 0)], [O.Factor(0), O.Factor(0, deriv=0)]),
              O.Term(0, [(0.1, 0)], [O.Factor(0), O.Factor(0, lap=1)])]
     ref = O.run_coupled([m], terms, [O.to_spectrum(m, O.init_uniform(m, -0.5, 0.5))], 0, steps)[0]
-    assert rel(s.get_spectrum(0), O.half(ref)) < tol
+    check_spectrum(s.get_spectrum(0), O.half(ref), tol)
 
 
 def test_product_terms_with_a_frame_and_argument_checks():
@@ -169,7 +171,7 @@ def test_product_terms_with_a_frame_and_argument_checks():
         r[:3], r[-3:] = 0.2, -0.2
         phis[1] = O.to_spectrum(ms[1], r)
     for fid in (0, 1):
-        assert rel(s.get_spectrum(fid), O.half(phis[fid])) < 1e-10, fid
+        check_spectrum(s.get_spectrum(fid), O.half(phis[fid]), 1e-10, what=str(fid))
     for bad in ([(5, 1)], [(0, 0)], [(0, 1, 3)], [(0, 1, -1, 3)]):
         with pytest.raises(P.PssError) as ei:
             s.add_product_term(0, [(-1, 1.0, 0)], bad)
