@@ -132,6 +132,11 @@ struct pss_system {
     int num_sms = 0;
     int tune_fast3d = 1;                     // FP32 3D x pass with one FFT group per row pair (0 = generic k_row)
     int tune_test_timeout = 0;               // check of the bounded waits: one CTA's wait runs out (tests)
+    int tune_persist = 1;                    // square FP32 2D systems: a run of steps as one persistent launch
+    int tune_persist_blocks = 0;             // its CTAs (0: every SM, at most one CTA per column pair or row pair)
+    int coop = 0;                            // the device takes cooperative launches
+    GridSync *gs = nullptr;                  // grid-barrier words of the persistent step
+    unsigned long long bar_base = 0;         // their arrival count after every launch so far
     int64_t launches = 0;
     std::string err;
     // adjoint: checkpoints of the last pss_adjoint_forward run
@@ -379,6 +384,29 @@ bool fast2d(const pss_system *s) {
 // pass takes radix 16 at every side: at 256 points that is half a warp per
 // transform and two passes instead of three, and there the passes are bound
 // by shared-memory bandwidth (x pass of the 256^3 pair 130 -> 113 us).
+bool round_trip(const pss_system *s);
+
+// A run of steps of a square FP32 2D system with one field and one instance
+// on the FFT-group path is one persistent launch (k2p_step), where the
+// device takes cooperative launches.
+bool persist2d_ok(const pss_system *s) {
+    return fast2d(s) && s->nx == s->ny && s->batch == 1 && s->fields.size() == 1 && s->coop && !round_trip(s);
+}
+bool persist2d(const pss_system *s) { return s->tune_persist && persist2d_ok(s); }
+int p2_radix(const pss_system *s) {
+    const int r = s->tune_col2_radix ? s->tune_col2_radix : (s->ny >= 512 ? 16 : 8);
+    return r == 32 ? (s->ny == 1024 ? 32 : 16) : r == 16 ? 16 : 8;
+}
+// CTAs of the persistent step: every SM (one CTA each), but no more than the
+// column pairs or row pairs to hand out, and at least enough to hold them (2
+// column pairs and 4 row pairs per CTA)
+int p2_blocks(const pss_system *s) {
+    const int n = s->nx, uc = (n / 2 + 2) / 2;
+    const int lo = std::max((uc + 1) / 2, n / 8);
+    const int want = s->tune_persist_blocks > 0 ? s->tune_persist_blocks : std::min(s->num_sms, std::max(uc, n / 2));
+    return std::max(lo, want);
+}
+
 int col2_radix(const pss_system *s) {
     const int r = s->tune_col2_radix ? s->tune_col2_radix : (s->ny >= 512 ? 16 : 8);
     return r == 32 && s->ny != 1024 ? 16 : r;   // radix-32 passes serve 1024 points only
@@ -1097,10 +1125,47 @@ void drop_graphs(pss_system *s) {
         if (g) { cudaGraphExecDestroy(g); g = nullptr; }
 }
 
+// The persistent path: runs of at most kMaxPersistSteps steps, one
+// cooperative launch each.  The launch reads the product of the current state
+// (array B, column-major, as the prologue or the previous launch left it) and
+// leaves the state, the product of the new state and the next step's noise
+// (XI) as the two-kernel path would, so the paths may alternate.
+constexpr int64_t kMaxPersistSteps = 4096;
+
+P2Args p2_args(pss_system *s, int nsteps) {
+    P2Args a{};
+    a.sp = sys_params<float>(s);
+    a.fps = (const FieldP<float> *)s->fps;
+    a.state = (float2 *)s->state;
+    a.P = (float2 *)s->B;
+    a.T1 = (float2 *)s->A;
+    a.xi = any_noisy(s) ? (float2 *)s->XI : nullptr;
+    a.tw = (const float2 *)s->tw;
+    a.d_step = s->d_step;
+    a.d_status = s->d_status;
+    a.gs = s->gs;
+    a.bar_base = s->bar_base;
+    a.nsteps = nsteps;
+    return a;
+}
+
+int run_persist(pss_system *s, int64_t n, cudaStream_t st) {
+    for (int64_t done = 0; done < n;) {
+        const int len = (int)std::min<int64_t>(kMaxPersistSteps, n - done);
+        cudaError_t e = launch_p2(p2_args(s, len), s->nx, p2_radix(s), p2_blocks(s), st);
+        s->launches++;
+        if (e != cudaSuccess) return cuda_fail(s, e, "k2p_step launch");
+        s->bar_base += (unsigned long long)(2 * len - 1) * (unsigned long long)p2_blocks(s);
+        done += len;
+    }
+    return PSS_OK;
+}
+
 // Every run of steps replays captured graphs: whole graphs of `graph_steps`
 // steps, then one graph of the remaining length (captured on its first use
 // and kept), so that the launches per step do not depend on n.
 int run_steps(pss_system *s, int64_t n) {
+    if (persist2d(s)) return run_persist(s, n, s->stream);
     const int chunk = s->tune_graph_steps > 0 ? s->tune_graph_steps : kDefaultGraphSteps;
     if (!s->graph_valid) {
         drop_graphs(s);
@@ -1182,7 +1247,13 @@ int device_errors(pss_system *s) {
     CK(cudaStreamSynchronize(s->stream));
     if (st) {
         CK(cudaMemsetAsync(s->d_status, 0, sizeof(int), s->stream));
-        if (st & 2) return fail(s, PSS_ETIMEOUT, "a bounded device wait ran out");
+        if (st & 2) {
+            // a persistent launch that gave up leaves its barrier words behind
+            CK(cudaMemsetAsync(s->gs, 0, sizeof(GridSync), s->stream));
+            CK(cudaStreamSynchronize(s->stream));
+            s->bar_base = 0;
+            return fail(s, PSS_ETIMEOUT, "a bounded device wait ran out");
+        }
         return fail(s, PSS_ENONFINITE, "a field became NaN or Inf");
     }
     return PSS_OK;
@@ -1260,6 +1331,9 @@ int do_create(pss_system **out, int batch, int dim, int nx, int ny, int nz, doub
     if (e == cudaSuccess) e = cudaMalloc(&s->d_status, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(s->d_step, 0, sizeof(long long));
     if (e == cudaSuccess) e = cudaMemset(s->d_status, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&s->coop, cudaDevAttrCooperativeLaunch, s->device);
+    if (e == cudaSuccess) e = cudaMalloc(&s->gs, sizeof(GridSync));
+    if (e == cudaSuccess) e = cudaMemset(s->gs, 0, sizeof(GridSync));
     // twiddle tables of every transform length and radix cap, built in FP64 on the host
     if (e == cudaSuccess) {
         const int total = kTwiddleEntries;
@@ -1437,6 +1511,7 @@ int pss_destroy_system(pss_system *s) {
     cudaFree(s->sq);
     cudaFree(s->d_step);
     cudaFree(s->d_status);
+    cudaFree(s->gs);
     cudaFree(s->L);
     cudaFree(s->ck);
     cudaFree(s->seg);
@@ -1857,8 +1932,32 @@ int pss_time_kernels(pss_system *s, int64_t n, double *avg_ms) {
     int rc = upload_params(s);
     if (rc) return rc;
     if ((rc = prologue(s))) return rc;
-    rc = s->prec == PSS_F64 ? timed_steps<double>(s, n, avg_ms) : timed_steps<float>(s, n, avg_ms);
-    if (rc) return rc;
+    if (persist2d(s)) {
+        // one launch of n steps between two events: its duration per step
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        CK(cudaEventCreate(&e0));
+        cudaError_t e = cudaEventCreate(&e1);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, s->stream);
+        if (e == cudaSuccess) {
+            const int len = (int)std::min<int64_t>(n, kMaxPersistSteps);
+            e = launch_p2(p2_args(s, len), s->nx, p2_radix(s), p2_blocks(s), s->stream);
+            s->launches++;
+            if (e == cudaSuccess) s->bar_base += (unsigned long long)(2 * len - 1) * (unsigned long long)p2_blocks(s);
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(e1, s->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        if (e != cudaSuccess) return cuda_fail(s, e, "timed persistent launch");
+        n = std::min<int64_t>(n, kMaxPersistSteps);
+        avg_ms[0] = ms / (double)n;
+        avg_ms[1] = avg_ms[2] = avg_ms[3] = 0.0;
+    } else {
+        rc = s->prec == PSS_F64 ? timed_steps<double>(s, n, avg_ms) : timed_steps<float>(s, n, avg_ms);
+        if (rc) return rc;
+    }
     s->step += n;
     return device_errors(s);
 }
@@ -1877,6 +1976,11 @@ int pss_set_tuning(pss_system *s, const char *key, int value) {
     else if (k == "fuse_adjoint") s->tune_fuse_adj = value ? 1 : 0;
     else if (k == "real_state") s->tune_real_state = value ? 1 : 0;
     else if (k == "test_timeout") s->tune_test_timeout = value ? 1 : 0;
+    else if (k == "persist") s->tune_persist = value ? 1 : 0;
+    else if (k == "persist_blocks") {
+        if (value > 1024) return fail(s, PSS_EINVAL, "persist_blocks is at most 1024 (0 = automatic)");
+        s->tune_persist_blocks = value;
+    }
     else if (k == "col2_warps") {
         if (value > 24) return fail(s, PSS_EINVAL, "col2_warps is at most 24 (0 = automatic)");
         s->tune_col2_warps = value;
@@ -1927,6 +2031,8 @@ std::vector<TuneKnob> tune_space(const pss_system *s) {
     std::vector<TuneKnob> k;
     const auto radix_list = [](int side) { return side == 1024 ? std::vector<int>{8, 16, 32} : std::vector<int>{8, 16}; };
     if (fast2d(s)) {
+        // the persistent launch against the two-kernel step, where the system qualifies
+        if (persist2d_ok(s)) k.push_back({"persist", &pss_system::tune_persist, {1, 0}});
         k.push_back({"col2_radix", &pss_system::tune_col2_radix, radix_list(s->ny)});
         k.push_back({"row2_radix", &pss_system::tune_row2_radix, radix_list(s->nx)});
         k.push_back({"row2_pairs", &pss_system::tune_row2_pairs, {1, 2, 4, 8}});
@@ -2389,6 +2495,8 @@ const char *pss_last_error(const pss_system *s) { return s ? s->err.c_str() : g_
 
 int64_t pss_launch_count(const pss_system *s) { return s ? s->launches : 0; }
 
-int pss_step_path(const pss_system *s) { return s ? (fast2d(s) ? 1 : fast3d_rows(s) ? 2 : 0) : PSS_EINVAL; }
+int pss_step_path(const pss_system *s) {
+    return s ? (persist2d(s) ? 3 : fast2d(s) ? 1 : fast3d_rows(s) ? 2 : 0) : PSS_EINVAL;
+}
 
 }  // extern "C"

@@ -18,10 +18,24 @@ namespace pss {
 template <typename T> __device__ __forceinline__ cplx<T> mk(T x, T y) { cplx<T> r; r.x = x; r.y = y; return r; }
 template <typename T> __device__ __forceinline__ cplx<T> cadd(cplx<T> a, cplx<T> b) { return mk<T>(a.x + b.x, a.y + b.y); }
 template <typename T> __device__ __forceinline__ cplx<T> csub(cplx<T> a, cplx<T> b) { return mk<T>(a.x - b.x, a.y - b.y); }
+// Products and sums that several kernels must round alike are written with
+// explicit round-to-nearest intrinsics: the compiler never contracts them into
+// fused multiply-adds of its own choosing, so two kernels that run the same
+// formula give the same bits whatever code surrounds it.
+__device__ __forceinline__ float fmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double fmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float fadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double fadd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float ffma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double ffma(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// a b = (a.x b.x - a.y b.y) + i (a.x b.y + a.y b.x): one product rounded, the other fused
 template <typename T> __device__ __forceinline__ cplx<T> cmul(cplx<T> a, cplx<T> b) {
-    return mk<T>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+    return mk<T>(ffma(a.x, b.x, -fmul(a.y, b.y)), ffma(a.x, b.y, fmul(a.y, b.x)));
 }
-template <typename T> __device__ __forceinline__ cplx<T> cscale(cplx<T> a, T s) { return mk<T>(a.x * s, a.y * s); }
+template <typename T> __device__ __forceinline__ cplx<T> cscale(cplx<T> a, T s) { return mk<T>(fmul(a.x, s), fmul(a.y, s)); }
+// q^2 = qx^2 + qy^2 with the same rounding in every kernel
+template <typename T> __device__ __forceinline__ T q2sum(T qx, T qy) { return ffma(qx, qx, fmul(qy, qy)); }
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as
@@ -123,7 +137,7 @@ template <int DIR, typename T> __device__ __forceinline__ cplx<T> rot32(cplx<T> 
     if (e == 8) return DIR > 0 ? mk<T>(-b.y, b.x) : mk<T>(b.y, -b.x);    // * (+-i)
     if (e == 24) return DIR > 0 ? mk<T>(b.y, -b.x) : mk<T>(-b.y, b.x);
     const T c = T(cos32(e)), s = T(DIR * sin32(e));
-    return mk<T>(b.x * c - b.y * s, b.x * s + b.y * c);
+    return mk<T>(ffma(b.x, c, -fmul(b.y, s)), ffma(b.x, s, fmul(b.y, c)));
 }
 
 __host__ __device__ constexpr int bitrev(int i, int n) {

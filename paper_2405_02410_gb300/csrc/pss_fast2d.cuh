@@ -309,9 +309,9 @@ __global__ void __launch_bounds__(E == 8 ? 1024 : E == 16 ? 768 : 512, 1) k2_col
                     }
                     C *B0 = WBUF + c0 * S::WS;
                     C v0 = B0[L::POFS + pos], v1 = B0[S::WS + L::POFS + pos];
-                    const float qy = float(signed_k(pos, N)) * sp.gy;
-                    const float qx0 = float(kx0) * sp.gx, qx1 = float(kx0 + 1) * sp.gx;
-                    const float q2a = qx0 * qx0 + qy * qy, q2b = qx1 * qx1 + qy * qy;
+                    const float qy = fmul(float(signed_k(pos, N)), sp.gy);
+                    const float qx0 = fmul(float(kx0), sp.gx), qx1 = fmul(float(kx0 + 1), sp.gx);
+                    const float q2a = q2sum(qx0, qy), q2b = q2sum(qx1, qy);
                     v0 = update_mode<float>(f0, v0, x0, q2a, dtO, dtM, has_product);
                     v1 = update_mode<float>(f1, v1, x1, q2b, dtO, dtM, has_product);
                     if (kx0 >= sp.hx) v0 = mk<float>(0.f, 0.f);
@@ -424,9 +424,9 @@ __device__ __forceinline__ void noise_range(const SysP<float> &sp, const FieldP<
             xa[u] = mk<float>(0.f, 0.f);
             xb[u] = xa[u];
             if (q < q1 && kx0 < sp.hx) {
-                const float qy = float(signed_k(pos, sp.ny)) * sp.gy;
-                const float qx0 = float(kx0) * sp.gx, qx1 = float(kx0 + 1) * sp.gx;
-                const float q2a = qx0 * qx0 + qy * qy, q2b = qx1 * qx1 + qy * qy;
+                const float qy = fmul(float(signed_k(pos, sp.ny)), sp.gy);
+                const float qx0 = fmul(float(kx0), sp.gx), qx1 = fmul(float(kx0 + 1), sp.gx);
+                const float q2a = q2sum(qx0, qy), q2b = q2sum(qx1, qy);
                 noise_pair<float>(kx0 == 0 || 2 * kx0 == sp.nx, kx0, pos, 0, noise_amp<float>(1.f, fp.noise_pow, q2a),
                                   noise_amp<float>(1.f, fp.noise_pow, q2b), kx0 + 1 < sp.hx, sp, (uint32_t)fp.field_id,
                                   key, step, xa[u], xb[u]);

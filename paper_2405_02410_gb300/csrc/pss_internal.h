@@ -196,6 +196,32 @@ template <typename T> inline cudaError_t launch_mid(const MidArgs<T> &a, int nsl
 // generic kernels (the x pass of the 3D step).
 cudaError_t launch_col2(const ColArgs<float> &a, int nslots, int ntiles, cudaStream_t st);
 cudaError_t launch_row2(const RowArgs<float> &a, int nslots, cudaStream_t st, bool tiled);
+// The persistent FP32 2D step (k2p_step: square sides of 256, 512 or 1024
+// points, one field, one instance): grid-barrier words of one system
+// (16 bytes, zero-initialised) and the launch arguments.  Barrier i of a
+// launch (0-based) completes when gs->count reaches bar_base + (i + 1)
+// gridDim.x; the host advances bar_base by the arrivals of every launch.
+struct GridSync {
+    unsigned long long count;   // CTA arrivals at grid barriers since the last reset
+    unsigned int abort;         // a CTA gave up waiting: the others leave too
+    unsigned int pad;
+};
+struct P2Args {
+    SysP<float> sp;
+    const FieldP<float> *fps;   // the field's parameters (one slot)
+    float2 *state;              // tiled [tile][ny][4]
+    float2 *P;                  // x-transformed product, column-major [kx][ny]
+    float2 *T1;                 // conjugated y-inverse of the kept columns, column-major [kx][ny]
+    float2 *xi;                 // unit-amplitude noise of the step after the run, tiled (written at the end)
+    const float2 *tw;
+    long long *d_step;
+    int *d_status;
+    GridSync *gs;
+    unsigned long long bar_base;   // gs->count when the launch starts (every earlier barrier complete)
+    int nsteps;
+};
+// n steps in one cooperative launch of nblocks CTAs (E: FFT pass radix, 8 or 16)
+cudaError_t launch_p2(const P2Args &a, int n, int E, int nblocks, cudaStream_t st);
 template <typename T> cudaError_t launch_init_uniform(T *real, long long nsites, double lo, double hi,
                                                       uint64_t seed, int field_id, cudaStream_t st);
 // product terms with several operators: Q = (first ? 0 : Q) + M(q) Pt over one

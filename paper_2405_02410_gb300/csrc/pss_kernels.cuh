@@ -34,7 +34,7 @@ template <typename C, int N> __host__ __device__ constexpr uint32_t twiddle_byte
 template <int N> __host__ __device__ constexpr int twiddle_elems() { return N >= 16 ? N : 0; }
 
 template <typename T> __device__ __forceinline__ T poly5(const T *c, T x) {
-    return (((c[4] * x + c[3]) * x + c[2]) * x + c[1]) * x + c[0];
+    return ffma(ffma(ffma(ffma(c[4], x, c[3]), x, c[2]), x, c[1]), x, c[0]);
 }
 
 __device__ __forceinline__ int signed_k(int k, int n) { return k < (n + 1) / 2 ? k : k - n; }
@@ -103,19 +103,30 @@ template <typename T> __device__ __forceinline__ T noise_amp(T sigma0, int p, T 
     return amp;
 }
 
-// Eq. (timeupdate): (phi + dt M P + xi) / (1 + dt O), O = -L~; dtO, dtM are
-// dt times the operator coefficients
+// Eq. (timeupdate) with the mode's factors given: g (phi + xi + m P), where
+// m = dt M(q) and g = 1 / (1 + dt O(q)) (update_factors)
+template <typename T>
+__device__ __forceinline__ cplx<T> update_pre(cplx<T> phi, cplx<T> P, cplx<T> xi, T m, T g, bool has_product) {
+    T nx = fadd(phi.x, xi.x), ny = fadd(phi.y, xi.y);
+    if (has_product) {
+        nx = ffma(m, P.x, nx);
+        ny = ffma(m, P.y, ny);
+    }
+    return mk<T>(fmul(nx, g), fmul(ny, g));
+}
+// the factors m = dt M(q), g = 1 / (1 + dt O(q)) of a mode; dtO, dtM are dt
+// times the operator coefficients (O = -L~)
+template <typename T> __device__ __forceinline__ void update_factors(T q2, const T *dtO, const T *dtM, T &m, T &g) {
+    m = poly5<T>(dtM, q2);
+    g = fast_rcp(fadd(T(1), poly5<T>(dtO, q2)));
+}
+// Eq. (timeupdate): (phi + dt M P + xi) / (1 + dt O)
 template <typename T>
 __device__ __forceinline__ cplx<T> update_mode(cplx<T> phi, cplx<T> P, cplx<T> xi, T q2, const T *dtO, const T *dtM,
                                                bool has_product) {
-    T nx = phi.x + xi.x, ny = phi.y + xi.y;
-    if (has_product) {
-        const T m = poly5<T>(dtM, q2);
-        nx += m * P.x;
-        ny += m * P.y;
-    }
-    const T g = fast_rcp(T(1) + poly5<T>(dtO, q2));
-    return mk<T>(nx * g, ny * g);
+    T m, g;
+    update_factors<T>(q2, dtO, dtM, m, g);
+    return update_pre<T>(phi, P, xi, m, g, has_product);
 }
 
 // ---------------------------------------------------------------------------

@@ -1,0 +1,435 @@
+// pss_persist2d.cuh -- the FP32 2D step as one persistent launch
+// (arXiv:2405.02410, section "What cuPSS calculates", Eq. timeupdate).
+//
+// k2p_step runs n steps of a square FP32 2D field (sides 256, 512, 1024) in
+// one cooperative launch of at most one CTA per SM.  Each CTA owns a fixed
+// set of half-spectrum columns (pairs kx = 2u, 2u + 1: one Philox call draws
+// the noise of both) and a fixed block of rows.  The state phi_q of its
+// columns stays in shared memory for the whole launch; only the two work
+// arrays of the FFT-group path move through L2 between the phases:
+//
+//   column phase (step n): P column (x-transformed product) -> forward
+//       y-FFT -> update (Eq. timeupdate, noise of step n) -> Hermitian part
+//       on kx = 0, Nx/2 -> de-aliased, 1/N_sites-scaled, conjugated kept
+//       columns -> y-FFT -> T1 (column-major)
+//   grid barrier A
+//   row phase: T1 rows of the CTA's row pairs -> C2R along x (two rows as
+//       one complex transform) -> power p -> R2C -> P (column-major)
+//   grid barrier B
+//
+// The barriers replace the two kernel boundaries of the two-kernel path.
+// The transform warps of a CTA meet at named barrier 15; beside them, noise
+// warps draw the Philox noise of the CTA's columns one step ahead into two
+// shared-memory buffers (the generator has no data dependence, so it fills
+// the issue slots the latency-bound transforms leave idle).  A buffer is
+// handed over through two mbarriers: "full" (the noise warps have drawn it)
+// and "empty" (the update has read it); every wait on them is bounded.  The
+// per-mode factors of the update, g = 1 / (1 + dt O(q)) and dt M(q), are
+// computed once per launch.
+// Every arithmetic operation on the data is the one k2_col / k2_row perform
+// (same transforms, same update and noise calls), so the two paths give the
+// same bits at the same FFT radix.
+//
+// The grid barrier is one 64-bit arrival counter in global memory: after a
+// CTA barrier of the transform warps, one thread adds 1 with release
+// semantics, and all of them poll it with acquire loads until it reaches the
+// barrier's target.  The counter is never reset inside a launch; the host
+// knows how many arrivals each launch makes and passes the count at the
+// launch's start.  Every wait is bounded; a CTA whose wait runs out records
+// PSS_STATUS_TIMEOUT, raises the abort word (so that no other CTA waits out
+// its own limit) and leaves.  The host clears both words after it has
+// reported the error.
+#pragma once
+
+#include "pss_fast2d.cuh"
+
+namespace pss {
+
+constexpr int kGridWaitLimit = 1 << 23;   // polls of one grid-barrier wait (about 1 s)
+
+__device__ __forceinline__ unsigned long long ld_acquire_gpu_u64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned ld_relaxed_gpu(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void red_release_gpu_add(unsigned long long *p, unsigned long long v) {
+    asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Arrive at a grid barrier: after the CTA's global writes of the phase, the
+// NMAIN transform threads meet at named barrier 15 and thread 0 adds the
+// CTA's arrival (release: it orders the CTA's writes before it).
+template <int NMAIN> __device__ __forceinline__ void grid_arrive(GridSync *gs) {
+    asm volatile("bar.sync 15, %0;" ::"n"(NMAIN) : "memory");
+    if (threadIdx.x == 0) red_release_gpu_add(&gs->count, 1ull);
+}
+
+// Wait until the arrival counter reaches `target` (at most `limit` polls; 0:
+// kGridWaitLimit).  Every transform thread calls it; all get the same answer.
+// A wait that runs out records the timeout, raises the grid's abort word and
+// the CTA's *cta_abort.
+template <int NMAIN>
+__device__ __forceinline__ bool grid_wait(GridSync *gs, unsigned long long target, int *status, int limit,
+                                          volatile int *cta_abort) {
+    __shared__ int s_ok;
+    if (threadIdx.x == 0) {
+        int ok = 0;
+        if (limit <= 0) limit = kGridWaitLimit;
+        for (int it = 0; it < limit; ++it) {
+            if (ld_acquire_gpu_u64(&gs->count) >= target) { ok = 1; break; }
+            if ((it & 63) == 63 && (ld_relaxed_gpu(&gs->abort) || *cta_abort)) break;
+        }
+        if (!ok) {
+            if (status) atomicOr(status, kStatusTimeout);
+            atomicExch(&gs->abort, 1u);
+            *cta_abort = 1;
+        }
+        s_ok = ok;
+    }
+    asm volatile("bar.sync 15, %0;" ::"n"(NMAIN) : "memory");
+    return s_ok != 0;
+}
+
+// CTAs, threads and shared memory of the persistent step.  The transform
+// warps are NG = 4 FFT groups of TPF = N / E threads and NHW helper warps that
+// join the element-wise loops; beside them run NNW noise warps.  A CTA owns at
+// most NG / 2 column pairs and NG row pairs.  Shared memory: mbarriers | roots
+// of unity | state [NG][N] | update factors (m, g) [NG][N] | noise, two
+// buffers [2][NG][N] | the groups' buffer pairs.
+template <int N, int E, int NNW, int NHW> struct P2Shape {
+    using S = GShape<N, E>;
+    static constexpr int NG = 4;
+    static constexpr int NF = NG * S::TPF;             // FFT-group threads
+    static constexpr int NMAIN = NF + 32 * NHW;        // transform warps
+    static constexpr int THREADS = NMAIN + 32 * NNW;
+    static constexpr size_t BAR = 0;                                    // full[2], empty[2]
+    static constexpr size_t TW = 128;
+    static constexpr size_t ST = TW + sizeof(float2) * N;
+    static constexpr size_t MG = ST + sizeof(float2) * NG * N;
+    static constexpr size_t NZ = MG + sizeof(float2) * NG * N;
+    static constexpr size_t WB = NZ + 2 * sizeof(float2) * NG * N;
+    static constexpr size_t BYTES = WB + sizeof(float2) * NG * S::WS;
+    static constexpr int POFS = S::OUT * S::BUF;
+    static constexpr int UOFS = S::BUF - POFS;
+};
+
+// the CTA's share of `total` units when they are cut into `nb` contiguous blocks
+__device__ __forceinline__ void block_range(int total, int nb, int b, int &lo, int &hi) {
+    lo = (int)((long long)total * b / nb);
+    hi = (int)((long long)total * (b + 1) / nb);
+}
+
+// the transform warps' CTA barrier (named barrier 15)
+template <int NMAIN> __device__ __forceinline__ void main_sync() {
+    asm volatile("bar.sync 15, %0;" ::"n"(NMAIN) : "memory");
+}
+
+// mbarrier arrive (release at CTA scope) by the calling thread
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// bounded wait of one thread for phase `parity` of `bar`; gives up early when
+// *abort is raised
+__device__ __forceinline__ bool mbar_wait_abortable(uint64_t *bar, uint32_t parity, const volatile int *abort) {
+    for (int it = 0; it < kWaitLimit; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (*abort) return false;
+    }
+    return false;
+}
+
+template <int N, int E, int NNW, int NHW>
+__global__ void __launch_bounds__(P2Shape<N, E, NNW, NHW>::THREADS, 1) k2p_step(const P2Args a) {
+    using C = float2;
+    using S = GShape<N, E>;
+    using L = P2Shape<N, E, NNW, NHW>;
+    constexpr int TPF = S::TPF, NG = L::NG, NF = L::NF, NMAIN = L::NMAIN, H = N / 2 + 1, UC = (H + 1) / 2;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw + L::BAR);     // full[0], full[1]
+    uint64_t *empty = full + 2;                                            // empty[0], empty[1]
+    C *TW = reinterpret_cast<C *>(smem_raw + L::TW);
+    C *ST = reinterpret_cast<C *>(smem_raw + L::ST);   // state of column slot c: ST[c N + ky]
+    float2 *MG = reinterpret_cast<float2 *>(smem_raw + L::MG);   // (m, g) of the update per mode
+    C *NZ = reinterpret_cast<C *>(smem_raw + L::NZ);   // noise buffer b of column slot c: NZ[(b NG + c) N + ky]
+    C *WB = reinterpret_cast<C *>(smem_raw + L::WB);
+    __shared__ FieldP<float> sfp;
+    __shared__ unsigned s_step0;
+    __shared__ volatile int s_abort;   // a wait gave up: every role leaves
+    const SysP<float> &sp = a.sp;
+    const FieldP<float> &fp = sfp;
+    const int t = threadIdx.x;
+    const unsigned nb = gridDim.x;
+    (void)NF;
+    // this CTA's column pairs [u0, u1) (column slot c = 2 (u - u0) + j holds kx = 2u + j)
+    // and row pairs [p0, p1)
+    int u0, u1, p0, p1;
+    block_range(UC, (int)nb, blockIdx.x, u0, u1);
+    block_range(N / 2, (int)nb, blockIdx.x, p0, p1);
+    const int ncs = 2 * (u1 - u0);   // column slots in use (the last may lie past Nx/2)
+    const int npr = p1 - p0;
+    auto kx_of = [&](int c) { return 2 * u0 + c; };
+
+    // ---- set-up (every thread): parameters, step counter, mbarriers
+    for (int i = t; i < (int)(sizeof(FieldP<float>) / 4); i += L::THREADS)
+        reinterpret_cast<uint32_t *>(&sfp)[i] = reinterpret_cast<const uint32_t *>(a.fps)[i];
+    if (t == 0) {
+        s_step0 = (unsigned)(*a.d_step);
+        s_abort = 0;
+        mbar_init(full, 32 * NNW);
+        mbar_init(full + 1, 32 * NNW);
+        mbar_init(empty, 1);
+        mbar_init(empty + 1, 1);
+    }
+    __syncthreads();   // the only CTA-wide barrier: from here on the two roles run apart
+    const bool noisy = fp.noisy != 0;
+
+    if (t >= NMAIN) {
+        // ================= noise warps =================
+        // unit-amplitude noise (times |q|^noise_pow) of steps step0 .. step0 + nsteps,
+        // one Philox call per (column pair, ky), as noise_range draws it
+        const int tn = t - NMAIN;
+        const PhiloxKey key = philox_key(fp.seed_lo, fp.seed_hi);
+        const int npairs = (u1 - u0) * N;
+        for (int n = 0; n <= a.nsteps; ++n) {
+            const int b = n & 1;
+            if (n >= 2 && !mbar_wait_abortable(empty + b, ((n >> 1) - 1) & 1, &s_abort)) {
+                if (!s_abort && a.d_status) atomicOr(a.d_status, kStatusTimeout);
+                s_abort = 1;
+                return;
+            }
+            if (noisy) {
+                C *nz = NZ + (size_t)b * NG * N;
+                const unsigned step = s_step0 + (unsigned)n;
+                for (int i = tn; i < npairs; i += 32 * NNW) {
+                    const int uu = i >> ilog2(N), ky = i & (N - 1), kx0 = 2 * (u0 + uu);
+                    C xa = mk<float>(0.f, 0.f), xb = xa;
+                    const float qy = fmul(float(signed_k(ky, N)), sp.gy);
+                    const float qx0 = fmul(float(kx0), sp.gx), qx1 = fmul(float(kx0 + 1), sp.gx);
+                    const float q2a = q2sum(qx0, qy), q2b = q2sum(qx1, qy);
+                    noise_pair<float>(kx0 == 0 || 2 * kx0 == sp.nx, kx0, ky, 0, noise_amp<float>(1.f, fp.noise_pow, q2a),
+                                      noise_amp<float>(1.f, fp.noise_pow, q2b), kx0 + 1 < sp.hx, sp,
+                                      (uint32_t)fp.field_id, key, step, xa, xb);
+                    nz[(2 * uu) * N + ky] = xa;
+                    nz[(2 * uu + 1) * N + ky] = xb;
+                }
+            }
+            mbar_arrive(full + b);
+        }
+        return;
+    }
+
+    // ================= transform warps =================
+    const int g = t < NF ? t / TPF : NG, gl = t - g * TPF;   // FFT group (NG: a helper thread)
+    for (int i = t; i < N; i += NMAIN) TW[i] = a.tw[twiddle_offset(N, E) + i];
+    const int kmx = fp.kmax[0], kmy = fp.kmax[1];
+    const float scale = sp.inv_nsites;
+    const bool has_product = fp.power > 0;
+    {
+        float dtO[kPolyTerms], dtM[kPolyTerms];
+#pragma unroll
+        for (int i = 0; i < kPolyTerms; ++i) {
+            dtO[i] = sp.dt * fp.O[i];
+            dtM[i] = sp.dt * fp.M[i];
+        }
+        for (int c = 0; c < ncs; ++c) {
+            const int kx = kx_of(c);
+            const float qx = fmul(float(kx), sp.gx);
+            for (int ky = t; ky < N; ky += NMAIN) {
+                ST[c * N + ky] =
+                    kx < sp.hx ? a.state[((size_t)(kx >> 2) * N + ky) * 4 + (kx & 3)] : mk<float>(0.f, 0.f);
+                float m, gg;
+                update_factors<float>(q2sum(qx, fmul(float(signed_k(ky, N)), sp.gy)), dtO, dtM, m, gg);
+                MG[c * N + ky] = make_float2(m, gg);
+            }
+        }
+    }
+    main_sync<NMAIN>();
+    const float sigma0 = fp.sigma0;
+    C *gb = WB + (g < NG ? g : 0) * S::WS;   // this thread's group buffers
+    bool alive = true;
+    // every transform thread waits for phase `parity` of the noise buffer's
+    // "full" mbarrier; the warps agree on the outcome
+    auto wait_full = [&](int b, uint32_t parity) {
+        if (!mbar_wait_abortable(full + b, parity, &s_abort)) {
+            if (!s_abort && a.d_status) atomicOr(a.d_status, kStatusTimeout);
+            s_abort = 1;
+        }
+        main_sync<NMAIN>();
+        return !s_abort;
+    };
+    unsigned long long target = a.bar_base;   // the arrival count that ends the next grid barrier
+
+#pragma unroll 1
+    for (int n = 0; n < a.nsteps && alive; ++n) {
+        // ================= column phase =================
+        // the x-transformed product of the CTA's columns into the second buffer
+        // of each group: 16-byte asynchronous copies, all in flight together
+        for (int i = t; i < ncs * (N / 2); i += NMAIN) {
+            const int c = i >> ilog2(N / 2), p = i & (N / 2 - 1), kx = kx_of(c);
+            float4 *dst = reinterpret_cast<float4 *>(WB + c * S::WS + S::BUF + 2 * p);
+            if (kx < sp.hx) {
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)),
+                             "l"(reinterpret_cast<const float4 *>(a.P + (size_t)kx * N) + p)
+                             : "memory");
+            } else {
+                *dst = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        }
+        asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+        main_sync<NMAIN>();
+        if (g < ncs) fft_fwd_group<N, E>(gb + S::BUF, gb, gb + S::BUF, gl, 1 + g, TW, 0);
+        const int b = n & 1;
+        if (!wait_full(b, (n >> 1) & 1)) { alive = false; break; }   // also orders the transforms before the update
+        // update (Eq. timeupdate) of every mode of the CTA's columns
+        const C *nz = NZ + (size_t)b * NG * N;
+        for (int c = 0; c < ncs; ++c) {
+            const int kx = kx_of(c);
+            C *B0 = WB + c * S::WS;
+            const bool kxk = kx <= kmx, live = kx < sp.hx;
+            for (int ky = t; ky < N; ky += NMAIN) {
+                const int i = c * N + ky;
+                const C x = noisy ? cscale<float>(nz[i], sigma0) : mk<float>(0.f, 0.f);
+                const float2 mg = MG[i];
+                C v = update_pre<float>(ST[i], B0[L::POFS + ky], x, mg.x, mg.y, has_product);
+                if (!live) v = mk<float>(0.f, 0.f);
+                ST[i] = v;
+                const float sc = (kxk && abs(signed_k(ky, N)) <= kmy) ? scale : 0.f;
+                B0[L::UOFS + ky] = mk<float>(v.x * sc, -v.y * sc);
+            }
+        }
+        main_sync<NMAIN>();
+        if (t == 0) mbar_arrive(empty + b);   // noise buffer b is read: the noise warps may refill it
+        // Hermitian part on the kx = 0 and kx = Nx/2 columns (the field is real)
+        for (int c = 0; c < ncs; ++c) {
+            const int kx = kx_of(c);
+            if (kx != 0 && kx != N / 2) continue;
+            C *Sc = ST + c * N, *U = WB + c * S::WS + L::UOFS;
+            const bool kxk = kx <= kmx;
+            for (int pos = t; pos < N / 2 + 1; pos += NMAIN) {
+                const int ppos = (N - pos) & (N - 1);
+                const C v0 = Sc[pos], v1 = Sc[ppos];
+                const C h = mk<float>(0.5f * (v0.x + v1.x), 0.5f * (v0.y - v1.y));
+                Sc[pos] = h;
+                Sc[ppos] = mk<float>(h.x, -h.y);
+                const float s0 = (kxk && abs(signed_k(pos, N)) <= kmy) ? scale : 0.f;
+                const float s1 = (kxk && abs(signed_k(ppos, N)) <= kmy) ? scale : 0.f;
+                U[pos] = mk<float>(h.x * s0, -h.y * s0);
+                U[ppos] = mk<float>(h.x * s1, h.y * s1);
+            }
+        }
+        main_sync<NMAIN>();
+        // y-inverse of the kept columns (stored conjugated: T1 = F(conj X))
+        if (g < ncs && kx_of(g) <= kmx) {
+            C *o = fft_fwd_group<N, E>(gb + L::UOFS, gb + L::POFS, gb + L::UOFS, gl, 1 + g, TW, 0);
+            C *__restrict__ dst = a.T1 + (size_t)kx_of(g) * N;
+#pragma unroll 4
+            for (int p = gl; p < N; p += TPF) dst[p] = o[p];
+        }
+        // ---- grid barrier A
+        target += nb;
+        if (sp.tx_extra && n == 0 && blockIdx.x == 0) {
+            // the bounded-wait check (tuning key "test_timeout"): this CTA never
+            // arrives, so the first barrier cannot complete and every wait runs out
+            main_sync<NMAIN>();
+        } else {
+            grid_arrive<NMAIN>(a.gs);
+        }
+        alive = grid_wait<NMAIN>(a.gs, target, a.d_status, sp.wait_limit, &s_abort);
+        if (!alive) break;
+        // ================= row phase =================
+        // stage Y = conj(Z) of each row pair from the conjugated y-inverse (as k2_row)
+        const int kc = fp.kx_cols;
+        auto stage = [&](int k, int j, float ar, float ai, float br, float bi) {
+            C *Y = WB + j * S::WS + S::BUF;
+            if (k >= kc) { ar = 0.f; ai = 0.f; br = 0.f; bi = 0.f; }
+            if (k == 0 || k == N / 2) { ai = 0.f; bi = 0.f; }
+            const C lo = mk<float>(ar - bi, -ai - br), hi = mk<float>(ar + bi, ai - br);
+            Y[k] = hi;
+            if (k > 0 && k < N / 2) Y[N - k] = lo;
+        };
+        {
+            const C *__restrict__ in = a.T1 + 2 * p0;
+            constexpr int total = H * NG;
+#pragma unroll 1
+            for (int base = 0; base < total; base += 4 * NMAIN) {
+                float4 v[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int idx = base + q * NMAIN + t, k = idx >> 2, j = idx & 3;
+                    v[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (idx < total && j < npr && k < kc)
+                        v[q] = __ldcg(reinterpret_cast<const float4 *>(in + (size_t)k * N + 2 * j));
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int idx = base + q * NMAIN + t, k = idx >> 2, j = idx & 3;
+                    if (idx < total && j < npr) stage(k, j, v[q].x, v[q].y, v[q].z, v[q].w);
+                }
+            }
+        }
+        main_sync<NMAIN>();
+        if (g < npr) {
+            C *b0 = gb, *b1 = gb + S::BUF;
+            const C *src = b1;
+            C *q0 = b0, *q1 = b1;
+#pragma unroll 1
+            for (int it = 0; it < 2; ++it) {
+                C *o = fft_fwd_group<N, E, 1>(src, q0, q1, gl, 1 + g, TW, it == 0 ? fp.power : 0);
+                src = o;
+                q0 = o == b0 ? b1 : b0;
+                q1 = o;
+            }
+        }
+        main_sync<NMAIN>();
+        // split into the half spectra of the two rows, stored column-major
+        {
+            C *__restrict__ out = a.P + 2 * p0;
+            constexpr int total = H * NG;
+            for (int idx = t; idx < total; idx += NMAIN) {
+                const int k = idx >> 2, j = idx & 3;
+                if (j >= npr) continue;
+                const C *Wj = WB + j * S::WS + S::BUF;
+                const C wk = Wj[k], wm = Wj[(N - k) & (N - 1)];
+                *reinterpret_cast<float4 *>(out + (size_t)k * N + 2 * j) =
+                    make_float4(0.5f * (wk.x + wm.x), 0.5f * (wk.y - wm.y), 0.5f * (wk.y + wm.y), -0.5f * (wk.x - wm.x));
+            }
+        }
+        // ---- grid barrier B (not after the last step)
+        if (n + 1 < a.nsteps) {
+            target += nb;
+            grid_arrive<NMAIN>(a.gs);
+            alive = grid_wait<NMAIN>(a.gs, target, a.d_status, sp.wait_limit, &s_abort);
+        }
+    }
+    if (!alive) {
+        s_abort = 1;   // the noise warps stop too
+        return;
+    }
+    // ---- the state, and the next step's unit noise (as the two-kernel path keeps it), back to the
+    // tiled arrays; a non-finite mode of the state is reported (it spreads to every mode in a step)
+    const int bl = a.nsteps & 1;
+    if (!wait_full(bl, (a.nsteps >> 1) & 1)) return;
+    const C *nz = NZ + (size_t)bl * NG * N;
+    bool bad = false;
+    for (int c = 0; c < ncs; ++c) {
+        const int kx = kx_of(c);
+        if (kx >= sp.hx) continue;
+        for (int ky = t; ky < N; ky += NMAIN) {
+            const size_t o = ((size_t)(kx >> 2) * N + ky) * 4 + (kx & 3);
+            const C v = ST[c * N + ky];
+            bad |= !(fabsf(v.x) + fabsf(v.y) <= 3.0e38f);
+            a.state[o] = v;
+            if (a.xi) a.xi[o] = noisy ? nz[c * N + ky] : mk<float>(0.f, 0.f);
+        }
+    }
+    if (bad && a.d_status) atomicOr(a.d_status, kStatusNonFinite);
+    if (blockIdx.x == 0 && t == 0) *a.d_step = (long long)s_step0 + a.nsteps;
+}
+
+}  // namespace pss

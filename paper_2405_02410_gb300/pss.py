@@ -370,9 +370,11 @@ class System:
 
     @property
     def step_path(self) -> str:
-        """'fast2d' (k2_col, k2_row: FP32 2D, sides 256..1024), 'fast3d_rows' (k_col, k_mid and the
-        FFT-group x pass k2_row: FP32 3D, x side 256..1024) or 'generic' (k_col, k_mid, k_row)."""
-        return {1: "fast2d", 2: "fast3d_rows"}.get(lib.pss_step_path(self._h), "generic")
+        """'persist2d' (k2p_step: a run of steps in one persistent launch; square FP32 2D, sides
+        256..1024, one field), 'fast2d' (k2_col, k2_row: FP32 2D, sides 256..1024), 'fast3d_rows'
+        (k_col, k_mid and the FFT-group x pass k2_row: FP32 3D, x side 256..1024) or 'generic'
+        (k_col, k_mid, k_row)."""
+        return {1: "fast2d", 2: "fast3d_rows", 3: "persist2d"}.get(lib.pss_step_path(self._h), "generic")
 
 
 def parse_tune_report(text: str) -> dict:

@@ -40,6 +40,8 @@ KNOBS = {
     "fast3d_rows": {"col_radix", "row2_radix", "mid_radix", "mid_planes", "col_tiles", "pdl", "graph_steps"},
     "generic": {"col_radix", "row_radix", "row_pairs", "col_tiles", "pdl", "graph_steps"},   # 3D: also mid_radix, mid_planes
 }
+# a system that qualifies for the persistent step also times it against the two-kernel step
+KNOBS["persist2d"] = KNOBS["fast2d"] | {"persist"}
 
 
 def _pair(shape, seed=8):
@@ -62,7 +64,10 @@ def _oracle_pair(shape, steps, seed=8):
 
 
 def _check_report(rep, path, dim=2):
-    assert rep["path"] == {"generic": 0, "fast2d": 1, "fast3d_rows": 2}[path]
+    if path == "persist2d":
+        assert rep["path"] in (3, 1) and rep["persist"] == (1 if rep["path"] == 3 else 0)   # either step may win
+    else:
+        assert rep["path"] == {"generic": 0, "fast2d": 1, "fast3d_rows": 2}[path]
     knobs = set(rep) - {"path", "trials", "skipped", "initial_ms", "tuned_ms"}
     want = KNOBS[path] | ({"mid_radix", "mid_planes"} if path == "generic" and dim == 3 else set())
     assert knobs == want, knobs
@@ -70,7 +75,8 @@ def _check_report(rep, path, dim=2):
     assert 0 < rep["tuned_ms"] <= rep["initial_ms"]
 
 
-@pytest.mark.parametrize("shape,path", [((256, 256), "fast2d"), ((64, 64), "generic"), ((8, 16, 256), "fast3d_rows"),
+@pytest.mark.parametrize("shape,path", [((256, 256), "persist2d"), ((512, 256), "fast2d"), ((64, 64), "generic"),
+                                        ((8, 16, 256), "fast3d_rows"),
                                         ((16, 32, 32), "generic")])
 def test_autotune_keeps_the_run(shape, path):
     steps0, steps1 = 10, 20

@@ -55,7 +55,7 @@ def test_matches_oracle(shape, order, noisy, steps):
     kw = dict(dt=0.01, a=-1, b=1, K=1, D=0.05, seed=17, dealias_order=order, noisy=noisy)
     s = _model_b(shape, **kw)
     s.step(steps)
-    check_spectrum(s.get_spectrum(0), _oracle_b(shape, steps, **kw), 1e-4, what=str(err))
+    check_spectrum(s.get_spectrum(0), _oracle_b(shape, steps, **kw), 1e-4)
     # the real field too (generic inverse of the state the fast path wrote)
     assert rel(s.get_field(0), np.fft.irfftn(_oracle_b(shape, steps, **kw), s=shape, axes=(0, 1))) < 1e-3
 
@@ -125,7 +125,7 @@ def test_model_a_and_b_pair():
     mb = O.model_b(shape, dt=0.005, a=-1, b=1, K=1, D=0.05, seed=21, field_id=1, dealias_order=3)
     for fid, m in ((0, ma), (1, mb)):
         ref = O.half(O.run(m, O.to_spectrum(m, O.init_uniform(m, -0.05, 0.05)), 0, steps))
-        check_spectrum(s.get_spectrum(fid), ref, 1e-4, what=str((fid, err)))
+        check_spectrum(s.get_spectrum(fid), ref, 1e-4, what=f"field {fid}")
 
 
 def test_batched_instances_match_single_runs():
@@ -185,7 +185,7 @@ def test_3d_x_pass_matches_oracle(shape, order):
     mb = O.model_b(shape, dt=0.005, a=-1, b=1, K=1, D=0.05, seed=8, field_id=1, dealias_order=order)
     for fid, m in ((0, ma), (1, mb)):
         ref = O.half(O.run(m, O.to_spectrum(m, O.init_uniform(m, -0.05, 0.05)), 0, steps))
-        check_spectrum(s.get_spectrum(fid), ref, 1e-4, what=str((fid, err)))
+        check_spectrum(s.get_spectrum(fid), ref, 1e-4, what=f"field {fid}")
 
 
 @pytest.mark.parametrize("shape", [(16, 32, 512), (32, 32, 1024), (64, 64, 256)])
@@ -195,4 +195,4 @@ def test_3d_x_pass_matches_generic_kernels(shape):
     for s in (fast, gen):
         s.step(30)
     for fid in (0, 1):
-        check_spectrum(fast.get_spectrum(fid), gen.get_spectrum(fid), 1e-5, what=str((fid, err)))
+        check_spectrum(fast.get_spectrum(fid), gen.get_spectrum(fid), 1e-5, what=f"field {fid}")

@@ -41,7 +41,8 @@ def _model_b(shape, prec="f32", batch=1, seed=2405):
 
 
 @pytest.mark.parametrize("shape,prec,path", [
-    ((256, 256), "f32", "fast2d"),
+    ((256, 256), "f32", "persist2d"),
+    ((512, 256), "f32", "fast2d"),
     ((64, 64), "f32", "generic"),
     ((8, 16, 32), "f64", "generic"),
     ((1024,), "f32", "generic"),
