@@ -47,11 +47,19 @@ struct u32x4 { uint32_t x, y, z, w; };
 constexpr uint32_t kPhiloxMulA = 0xD2511F53u, kPhiloxMulB = 0xCD9E8D57u;
 constexpr uint32_t kPhiloxWeylA = 0x9E3779B9u, kPhiloxWeylB = 0xBB67AE85u;
 
+// one 32 x 32 -> 64-bit product gives both halves a round needs
+__device__ __forceinline__ void mul_wide(uint32_t a, uint32_t b, uint32_t &hi, uint32_t &lo) {
+    const uint64_t p = (uint64_t)a * (uint64_t)b;
+    hi = (uint32_t)(p >> 32);
+    lo = (uint32_t)p;
+}
+
 __device__ __forceinline__ u32x4 philox4x32_10(u32x4 c, uint32_t k0, uint32_t k1) {
 #pragma unroll
     for (int round = 0; round < 10; ++round) {
-        const uint32_t hiA = __umulhi(kPhiloxMulA, c.x), loA = kPhiloxMulA * c.x;
-        const uint32_t hiB = __umulhi(kPhiloxMulB, c.z), loB = kPhiloxMulB * c.z;
+        uint32_t hiA, loA, hiB, loB;
+        mul_wide(kPhiloxMulA, c.x, hiA, loA);
+        mul_wide(kPhiloxMulB, c.z, hiB, loB);
         c = u32x4{hiB ^ c.y ^ k0, loB, hiA ^ c.w ^ k1, loA};
         k0 += kPhiloxWeylA;
         k1 += kPhiloxWeylB;
@@ -77,8 +85,9 @@ __device__ __forceinline__ PhiloxKey philox_key(uint32_t k0, uint32_t k1) {
 __device__ __forceinline__ u32x4 philox4x32_10(u32x4 c, const PhiloxKey &K) {
 #pragma unroll
     for (int round = 0; round < 10; ++round) {
-        const uint32_t hiA = __umulhi(kPhiloxMulA, c.x), loA = kPhiloxMulA * c.x;
-        const uint32_t hiB = __umulhi(kPhiloxMulB, c.z), loB = kPhiloxMulB * c.z;
+        uint32_t hiA, loA, hiB, loB;
+        mul_wide(kPhiloxMulA, c.x, hiA, loA);
+        mul_wide(kPhiloxMulB, c.z, hiB, loB);
         c = u32x4{hiB ^ c.y ^ K.k0[round], loB, hiA ^ c.w ^ K.k1[round], loA};
     }
     return c;

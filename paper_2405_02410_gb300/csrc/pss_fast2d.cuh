@@ -123,7 +123,11 @@ __device__ __forceinline__ void fpass(const float2 *src, float2 *dst, int logP, 
     constexpr int STRIDE = N / R, BPT = STRIDE / TPF, LOGR = ilog2(R);
     static_assert(STRIDE % TPF == 0, "every thread takes whole butterflies");
     const int P = 1 << logP;
-#pragma unroll 1
+    // a thread's butterflies of a small-radix pass (at most 16 values in all)
+    // run unrolled, so that their loads and arithmetic overlap; larger passes
+    // keep the loop rolled (code size)
+    constexpr bool UNROLL = R * BPT <= 16;
+#pragma unroll (UNROLL ? BPT : 1)
     for (int s = 0; s < BPT; ++s) {
         const int i = gl + TPF * s, k = i & (P - 1);
         float2 u[R];
@@ -188,6 +192,61 @@ __device__ __forceinline__ float2 *fft_fwd_group(const float2 *in, float2 *b0, f
     fpass<N, E, S::RL, true, true, false, VAR>(cur, nxt, logP, gl, tw, power, ra, rb, ma, mb);
     group_sync<S::TPF>(id);
     return nxt;
+}
+
+// The last pass of a group FFT with its natural-order outputs handed to
+// sink(q, value) instead of stored (same butterflies and arithmetic as fpass).
+template <int N, int E, int R, class Sink>
+__device__ __forceinline__ void fpass_sink(const float2 *src, int logP, int gl, const float2 *__restrict__ tw,
+                                           Sink &&sink) {
+    constexpr int TPF = GShape<N, E>::TPF;
+    constexpr int STRIDE = N / R, BPT = STRIDE / TPF, LOGR = ilog2(R);
+    static_assert(STRIDE % TPF == 0, "every thread takes whole butterflies");
+    const int P = 1 << logP;
+    constexpr bool UNROLL = R * BPT <= 16;
+#pragma unroll (UNROLL ? BPT : 1)
+    for (int s = 0; s < BPT; ++s) {
+        const int i = gl + TPF * s, k = i & (P - 1);
+        float2 u[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) u[r] = src[padp<GShape<N, E>::PS>(i + r * STRIDE)];
+        const float2 *__restrict__ twp = tw + (P - E) + k;
+#pragma unroll
+        for (int r = 1; r < R; ++r) u[r] = cmul<float>(u[r], twp[(r - 1) * P]);
+        dft_reg<R, -1, float>(u);
+        const int j = ((i - k) << LOGR) + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) sink(j + r * P, u[r]);
+    }
+}
+
+// fft_fwd_group whose last pass hands each output to sink(q, value).  The
+// input is in b1 (natural order); the last pass reads b1 when the transform
+// has an odd number of passes, else b0, so the other buffer (SinkShape::FREE)
+// is free for the sink to write.  No barrier follows the last pass.
+template <int N, int E> struct SinkShape {
+    static constexpr bool LAST_READS_B1 = (GShape<N, E>::NPASS - 1) % 2 == 0;
+};
+template <int N, int E, class Sink>
+__device__ __forceinline__ void fft_fwd_group_sink(float2 *b0, float2 *b1, int gl, int id,
+                                                   const float2 *__restrict__ tw, Sink &&sink) {
+    using S = GShape<N, E>;
+    static_assert(S::NPASS >= 2, "the sink pass reads padded intermediate results");
+    {
+        fpass<N, E, E, false, false, true>(b1, b0, 0, gl, tw, 0);
+        group_sync<S::TPF>(id);
+        float2 *cur = b0, *nxt = b1;
+        int logP = S::LOGE;
+#pragma unroll 1
+        for (; logP + S::LOGRL < S::LOG; logP += S::LOGE) {
+            fpass<N, E, E, true, true, true>(cur, nxt, logP, gl, tw, 0);
+            group_sync<S::TPF>(id);
+            float2 *tmp = cur;
+            cur = nxt;
+            nxt = tmp;
+        }
+        fpass_sink<N, E, S::RL>(cur, logP, gl, tw, sink);
+    }
 }
 
 // ---------------------------------------------------------------------------

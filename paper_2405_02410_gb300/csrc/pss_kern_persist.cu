@@ -25,15 +25,15 @@ cudaError_t launch_p2(const P2Args &a, int n, int E, int nblocks, cudaStream_t s
     // a CTA holds at most 2 of the (n / 2 + 2) / 2 column pairs and 4 of the n / 2 row pairs
     const int uc = (n / 2 + 2) / 2;
     if (nblocks < (uc + 1) / 2 || nblocks < n / 8 || a.nsteps < 1) return cudaErrorInvalidConfiguration;
-    // beside the FFT groups: 8 noise warps and 8 helper warps with radix-16
-    // passes, 4 noise warps and no helpers with radix 8 (twice the FFT threads)
+    // beside the FFT groups: 8 noise warps with radix-16 passes, 4 with radix 8
+    // (twice the FFT threads)
     switch (n) {
-        case 256: return E == 16 ? launch_p2_ne<256, 16, 8, 8>(a, nblocks, st) : launch_p2_ne<256, 8, 4, 0>(a, nblocks, st);
-        case 512: return E == 16 ? launch_p2_ne<512, 16, 8, 8>(a, nblocks, st) : launch_p2_ne<512, 8, 4, 0>(a, nblocks, st);
+        case 256: return E == 16 ? launch_p2_ne<256, 16, 8, 0>(a, nblocks, st) : launch_p2_ne<256, 8, 4, 0>(a, nblocks, st);
+        case 512: return E == 16 ? launch_p2_ne<512, 16, 8, 0>(a, nblocks, st) : launch_p2_ne<512, 8, 4, 0>(a, nblocks, st);
         case 1024:
-            // radix 32: one warp per transform, two passes; 4 helper and 8 noise warps
-            return E == 32 ? launch_p2_ne<1024, 32, 8, 4>(a, nblocks, st)
-                 : E == 16 ? launch_p2_ne<1024, 16, 8, 8>(a, nblocks, st)
+            // radix 32: one warp per transform, two passes; 8 noise warps
+            return E == 32 ? launch_p2_ne<1024, 32, 8, 0>(a, nblocks, st)
+                 : E == 16 ? launch_p2_ne<1024, 16, 8, 0>(a, nblocks, st)
                            : launch_p2_ne<1024, 8, 4, 0>(a, nblocks, st);
         default: return cudaErrorInvalidValue;
     }

@@ -80,7 +80,9 @@ __device__ __forceinline__ bool grid_wait(GridSync *gs, unsigned long long targe
     if (threadIdx.x == 0) {
         int ok = 0;
         if (limit <= 0) limit = kGridWaitLimit;
-        for (int it = 0; it < limit; ++it) {
+        // a wait of this CTA that gave up earlier (noise hand-over) ends the launch here,
+        // at a point every transform thread reaches
+        for (int it = 0; it < limit && !*cta_abort; ++it) {
             if (ld_acquire_gpu_u64(&gs->count) >= target) { ok = 1; break; }
             if ((it & 63) == 63 && (ld_relaxed_gpu(&gs->abort) || *cta_abort)) break;
         }
@@ -268,70 +270,70 @@ __global__ void __launch_bounds__(P2Shape<N, E, NNW, NHW>::THREADS, 1) k2p_step(
 #pragma unroll 1
     for (int n = 0; n < a.nsteps && alive; ++n) {
         // ================= column phase =================
-        // the x-transformed product of the CTA's columns into the second buffer
-        // of each group: 16-byte asynchronous copies, all in flight together
-        for (int i = t; i < ncs * (N / 2); i += NMAIN) {
-            const int c = i >> ilog2(N / 2), p = i & (N / 2 - 1), kx = kx_of(c);
-            float4 *dst = reinterpret_cast<float4 *>(WB + c * S::WS + S::BUF + 2 * p);
-            if (kx < sp.hx) {
-                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)),
-                             "l"(reinterpret_cast<const float4 *>(a.P + (size_t)kx * N) + p)
-                             : "memory");
-            } else {
-                *dst = make_float4(0.f, 0.f, 0.f, 0.f);
-            }
-        }
-        asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
-        main_sync<NMAIN>();
-        if (g < ncs) fft_fwd_group<N, E>(gb + S::BUF, gb, gb + S::BUF, gl, 1 + g, TW, 0);
+        // Each FFT group runs its column on its own: the x-transformed product
+        // (16-byte asynchronous copies into b1), the forward y-FFT whose last
+        // pass applies the update (Eq. timeupdate) mode by mode and writes the
+        // de-aliased, scaled, conjugated inverse input into the free buffer, the
+        // Hermitian part on the kx = 0, Nx/2 columns, and the y-inverse whose
+        // last pass stores T1 (column-major) straight to global memory.
         const int b = n & 1;
-        if (!wait_full(b, (n >> 1) & 1)) { alive = false; break; }   // also orders the transforms before the update
-        // update (Eq. timeupdate) of every mode of the CTA's columns
-        const C *nz = NZ + (size_t)b * NG * N;
-        for (int c = 0; c < ncs; ++c) {
-            const int kx = kx_of(c);
-            C *B0 = WB + c * S::WS;
+        if (g < ncs) {
+            const int kx = kx_of(g);
+            C *b0 = gb, *b1 = gb + S::BUF;
+            C *U = SinkShape<N, E>::LAST_READS_B1 ? b0 : b1;   // the buffer the last pass does not read
+            for (int p = gl; p < N / 2; p += TPF) {
+                float4 *dst = reinterpret_cast<float4 *>(b1 + 2 * p);
+                if (kx < sp.hx) {
+                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)),
+                                 "l"(reinterpret_cast<const float4 *>(a.P + (size_t)kx * N) + p)
+                                 : "memory");
+                } else {
+                    *dst = make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+            }
+            asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+            // the noise of this step (every thread of the group waits; bounded)
+            if (!mbar_wait_abortable(full + b, (n >> 1) & 1, &s_abort)) {
+                if (!s_abort && a.d_status) atomicOr(a.d_status, kStatusTimeout);
+                s_abort = 1;
+            }
+            group_sync<TPF>(1 + g);
+            const C *nzc = NZ + ((size_t)b * NG + g) * N;
+            C *STc = ST + g * N;
+            const float2 *MGc = MG + g * N;
             const bool kxk = kx <= kmx, live = kx < sp.hx;
-            for (int ky = t; ky < N; ky += NMAIN) {
-                const int i = c * N + ky;
-                const C x = noisy ? cscale<float>(nz[i], sigma0) : mk<float>(0.f, 0.f);
-                const float2 mg = MG[i];
-                C v = update_pre<float>(ST[i], B0[L::POFS + ky], x, mg.x, mg.y, has_product);
+            fft_fwd_group_sink<N, E>(b0, b1, gl, 1 + g, TW, [&](int ky, C pq) {
+                const C x = noisy ? cscale<float>(nzc[ky], sigma0) : mk<float>(0.f, 0.f);
+                const float2 mg = MGc[ky];
+                C v = update_pre<float>(STc[ky], pq, x, mg.x, mg.y, has_product);
                 if (!live) v = mk<float>(0.f, 0.f);
-                ST[i] = v;
+                STc[ky] = v;
                 const float sc = (kxk && abs(signed_k(ky, N)) <= kmy) ? scale : 0.f;
-                B0[L::UOFS + ky] = mk<float>(v.x * sc, -v.y * sc);
+                U[ky] = mk<float>(v.x * sc, -v.y * sc);
+            });
+            group_sync<TPF>(1 + g);
+            if (kx == 0 || kx == N / 2) {
+                // Hermitian part (the field is real): phi(kx, ky) <- (phi(kx, ky) + conj phi(kx, -ky)) / 2
+                for (int pos = gl; pos < N / 2 + 1; pos += TPF) {
+                    const int ppos = (N - pos) & (N - 1);
+                    const C v0 = STc[pos], v1 = STc[ppos];
+                    const C h = mk<float>(0.5f * (v0.x + v1.x), 0.5f * (v0.y - v1.y));
+                    STc[pos] = h;
+                    STc[ppos] = mk<float>(h.x, -h.y);
+                    const float s0 = (kxk && abs(signed_k(pos, N)) <= kmy) ? scale : 0.f;
+                    const float s1 = (kxk && abs(signed_k(ppos, N)) <= kmy) ? scale : 0.f;
+                    U[pos] = mk<float>(h.x * s0, -h.y * s0);
+                    U[ppos] = mk<float>(h.x * s1, h.y * s1);
+                }
+                group_sync<TPF>(1 + g);
+            }
+            if (kxk) {
+                // y-inverse (T1 = F(conj X)): input in U, the other buffer for the passes
+                C *__restrict__ dst = a.T1 + (size_t)kx * N;
+                fft_fwd_group_sink<N, E>(U == b0 ? b1 : b0, U, gl, 1 + g, TW, [&](int q, C v) { dst[q] = v; });
             }
         }
-        main_sync<NMAIN>();
-        if (t == 0) mbar_arrive(empty + b);   // noise buffer b is read: the noise warps may refill it
-        // Hermitian part on the kx = 0 and kx = Nx/2 columns (the field is real)
-        for (int c = 0; c < ncs; ++c) {
-            const int kx = kx_of(c);
-            if (kx != 0 && kx != N / 2) continue;
-            C *Sc = ST + c * N, *U = WB + c * S::WS + L::UOFS;
-            const bool kxk = kx <= kmx;
-            for (int pos = t; pos < N / 2 + 1; pos += NMAIN) {
-                const int ppos = (N - pos) & (N - 1);
-                const C v0 = Sc[pos], v1 = Sc[ppos];
-                const C h = mk<float>(0.5f * (v0.x + v1.x), 0.5f * (v0.y - v1.y));
-                Sc[pos] = h;
-                Sc[ppos] = mk<float>(h.x, -h.y);
-                const float s0 = (kxk && abs(signed_k(pos, N)) <= kmy) ? scale : 0.f;
-                const float s1 = (kxk && abs(signed_k(ppos, N)) <= kmy) ? scale : 0.f;
-                U[pos] = mk<float>(h.x * s0, -h.y * s0);
-                U[ppos] = mk<float>(h.x * s1, h.y * s1);
-            }
-        }
-        main_sync<NMAIN>();
-        // y-inverse of the kept columns (stored conjugated: T1 = F(conj X))
-        if (g < ncs && kx_of(g) <= kmx) {
-            C *o = fft_fwd_group<N, E>(gb + L::UOFS, gb + L::POFS, gb + L::UOFS, gl, 1 + g, TW, 0);
-            C *__restrict__ dst = a.T1 + (size_t)kx_of(g) * N;
-#pragma unroll 4
-            for (int p = gl; p < N; p += TPF) dst[p] = o[p];
-        }
-        // ---- grid barrier A
+        // ---- grid barrier A (its CTA barrier also ends the column phase's reads of noise buffer b)
         target += nb;
         if (sp.tx_extra && n == 0 && blockIdx.x == 0) {
             // the bounded-wait check (tuning key "test_timeout"): this CTA never
@@ -340,63 +342,44 @@ __global__ void __launch_bounds__(P2Shape<N, E, NNW, NHW>::THREADS, 1) k2p_step(
         } else {
             grid_arrive<NMAIN>(a.gs);
         }
+        if (t == 0) mbar_arrive(empty + b);   // noise buffer b is read: the noise warps may refill it
         alive = grid_wait<NMAIN>(a.gs, target, a.d_status, sp.wait_limit, &s_abort);
         if (!alive) break;
         // ================= row phase =================
-        // stage Y = conj(Z) of each row pair from the conjugated y-inverse (as k2_row)
-        const int kc = fp.kx_cols;
-        auto stage = [&](int k, int j, float ar, float ai, float br, float bi) {
-            C *Y = WB + j * S::WS + S::BUF;
-            if (k >= kc) { ar = 0.f; ai = 0.f; br = 0.f; bi = 0.f; }
-            if (k == 0 || k == N / 2) { ai = 0.f; bi = 0.f; }
-            const C lo = mk<float>(ar - bi, -ai - br), hi = mk<float>(ar + bi, ai - br);
-            Y[k] = hi;
-            if (k > 0 && k < N / 2) Y[N - k] = lo;
-        };
-        {
-            const C *__restrict__ in = a.T1 + 2 * p0;
-            constexpr int total = H * NG;
-#pragma unroll 1
-            for (int base = 0; base < total; base += 4 * NMAIN) {
-                float4 v[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int idx = base + q * NMAIN + t, k = idx >> 2, j = idx & 3;
-                    v[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (idx < total && j < npr && k < kc)
-                        v[q] = __ldcg(reinterpret_cast<const float4 *>(in + (size_t)k * N + 2 * j));
-                }
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int idx = base + q * NMAIN + t, k = idx >> 2, j = idx & 3;
-                    if (idx < total && j < npr) stage(k, j, v[q].x, v[q].y, v[q].z, v[q].w);
-                }
-            }
-        }
-        main_sync<NMAIN>();
+        // Each FFT group runs one row pair on its own: Y = conj(Z) staged from the
+        // conjugated y-inverse (as k2_row), C2R with the power on its last pass,
+        // R2C, and the split into the two rows' half spectra, stored column-major.
         if (g < npr) {
+            const int r0 = 2 * (p0 + g);   // the pair's first row
+            const int kc = fp.kx_cols;
             C *b0 = gb, *b1 = gb + S::BUF;
-            const C *src = b1;
-            C *q0 = b0, *q1 = b1;
-#pragma unroll 1
-            for (int it = 0; it < 2; ++it) {
-                C *o = fft_fwd_group<N, E, 1>(src, q0, q1, gl, 1 + g, TW, it == 0 ? fp.power : 0);
-                src = o;
-                q0 = o == b0 ? b1 : b0;
-                q1 = o;
+            constexpr int PER = (H + TPF - 1) / TPF;   // columns per thread
+            float4 v[PER];
+#pragma unroll
+            for (int q = 0; q < PER; ++q) {
+                const int k = gl + q * TPF;
+                v[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (k < kc) v[q] = __ldcg(reinterpret_cast<const float4 *>(a.T1 + (size_t)k * N + r0));
             }
-        }
-        main_sync<NMAIN>();
-        // split into the half spectra of the two rows, stored column-major
-        {
-            C *__restrict__ out = a.P + 2 * p0;
-            constexpr int total = H * NG;
-            for (int idx = t; idx < total; idx += NMAIN) {
-                const int k = idx >> 2, j = idx & 3;
-                if (j >= npr) continue;
-                const C *Wj = WB + j * S::WS + S::BUF;
-                const C wk = Wj[k], wm = Wj[(N - k) & (N - 1)];
-                *reinterpret_cast<float4 *>(out + (size_t)k * N + 2 * j) =
+#pragma unroll
+            for (int q = 0; q < PER; ++q) {
+                const int k = gl + q * TPF;
+                if (k < H) {
+                    float ar = v[q].x, ai = v[q].y, br = v[q].z, bi = v[q].w;
+                    if (k == 0 || k == N / 2) { ai = 0.f; bi = 0.f; }   // the half spectra of real rows
+                    const C lo = mk<float>(ar - bi, -ai - br), hi = mk<float>(ar + bi, ai - br);
+                    b1[k] = hi;
+                    if (k > 0 && k < N / 2) b1[N - k] = lo;
+                }
+            }
+            group_sync<TPF>(1 + g);
+            C *o = fft_fwd_group<N, E, 1>(b1, b0, b1, gl, 1 + g, TW, fp.power);
+            C *o2 = fft_fwd_group<N, E, 1>(o, o == b0 ? b1 : b0, o, gl, 1 + g, TW, 0);
+            C *__restrict__ out = a.P + r0;
+#pragma unroll 4
+            for (int k = gl; k < H; k += TPF) {
+                const C wk = o2[k], wm = o2[(N - k) & (N - 1)];
+                *reinterpret_cast<float4 *>(out + (size_t)k * N) =
                     make_float4(0.5f * (wk.x + wm.x), 0.5f * (wk.y - wm.y), 0.5f * (wk.y + wm.y), -0.5f * (wk.x - wm.x));
             }
         }
