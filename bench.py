@@ -78,8 +78,9 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kernel):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on the current kernels."""
+def recorded_traffic(kernel, steps_per_launch=None):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the current kernels
+    (and, for the persistent step, on launches of the same number of steps)."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
             rec = json.load(fh)
@@ -87,7 +88,10 @@ def recorded_traffic(kernel):
         return None
     if rec.get("source_hash") != kernel_source_hash():
         return None
-    return rec.get("kernels", {}).get(kernel)
+    v = rec.get("kernels", {}).get(kernel)
+    if isinstance(v, dict):   # per launch length
+        return v.get(str(steps_per_launch)) if steps_per_launch is not None else None
+    return v
 
 
 class ClockSampler:
@@ -512,6 +516,19 @@ def variants_measurement(pss, torch, stream, tuning=None):
                           "baseline_ms_per_step": base, "speedup_over_order2": base / ms, "path": s.step_path,
                           "timed": "2000 steps after 20 warm-up steps, beside the order-2 baseline timed alike"}
     s.close()
+    # the two-kernel step (k2_col, k2_row from CUDA graphs) that the persistent launch replaces
+    s = make_system(pss, (1024, 1024))
+    s.set_stream(stream)
+    if tuning:
+        s.set_tunings(tuning)
+    s.set_tuning("persist", 0)
+    s.init_uniform(0, w["lo"], w["hi"])
+    ms = _timed_steps(torch, stream, s, 2000)
+    base = baseline_1024(pss, torch, stream, 2000, tuning)
+    out["two_kernel_1024"] = {"ms_per_step": ms, "site_steps_per_s": 1024 ** 2 / (ms * 1e-3), "path": s.step_path,
+                              "baseline_ms_per_step": base, "baseline_path": "persist2d",
+                              "slowdown_over_baseline": ms / base}
+    s.close()
     s = make_system(pss, (1024, 1024))
     s.set_stream(stream)
     s.set_tuning("real_state", 1)
@@ -700,6 +717,7 @@ def run_gpu(args):
     warm_steps = args.warmup + sum(sorted(set(chunks)))
     launches0 = s.launch_count
     total_ms = 0.0
+    chunk_ms = []
     barrier(world)
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
@@ -712,7 +730,8 @@ def run_gpu(args):
                 s.step(c)
                 e1.record(stream)
             e1.synchronize()
-            total_ms += e0.elapsed_time(e1)
+            chunk_ms.append(e0.elapsed_time(e1))
+            total_ms += chunk_ms[-1]
     torch.cuda.synchronize()
     barrier(world)
     launches = s.launch_count - launches0
@@ -720,29 +739,49 @@ def run_gpu(args):
     value, t_max = whole_job_rate(sites * K, total_ms, world)
     ms_per_step = t_max / K
 
-    # per-kernel durations (CUDA events around each launch, same stream)
-    kern_ms = s.time_kernels(200)
     ab = algorithmic_bytes_2d(shape[1], shape[0])
     peaks, peak_kind = measured_peaks()
     hbm = float(peaks.get("hbm_gbs", 6800.0))
-    names = {0: "col", 2: "row"}
-    kernel_names = {0: "k2_col", 2: "k2_row"} if s.step_path == "fast2d" else {0: "k_col", 2: "k_row"}
-    # An event pair around every launch puts event nodes between the kernels,
-    # and each adds its own gap (the brackets sum to more than the step): the
-    # brackets give each kernel's share of the step, and the live step time
-    # (events around the timed replays) splits by those shares.
-    bracket_sum = kern_ms[0] + kern_ms[2]
-    live_ms = {k: ms_per_step * kern_ms[k] / bracket_sum for k in (0, 2)}
-    dom = max((0, 2), key=lambda k: live_ms[k])
-    dom_name = names[dom]
-    achieved = ab[dom_name] / (live_ms[dom] * 1e-3) / 1e9
-    per_kernel = {kernel_names[k]: {"ms": live_ms[k], "share": kern_ms[k] / bracket_sum,
-                                    "algorithmic_bytes": ab[names[k]],
-                                    "achieved_gbs": ab[names[k]] / (live_ms[k] * 1e-3) / 1e9,
-                                    "frac": ab[names[k]] / (live_ms[k] * 1e-3) / 1e9 / hbm,
-                                    "event_bracket_ms": kern_ms[k],
-                                    "traffic": recorded_traffic(kernel_names[k])} for k in (0, 2)}
-    traffic = recorded_traffic(kernel_names[dom])
+    if s.step_path == "persist2d":
+        # one kernel: each timed interval of c steps is one launch of k2p_step with a CUDA
+        # event pair around it, so the launch duration is the interval's event time
+        spl = chunks[0]
+        launch_ms = chunk_ms[0] if len(chunk_ms) == 1 else float(np.mean([m for m, c in zip(chunk_ms, chunks) if c == spl]))
+        achieved = ab["step"] * spl / (launch_ms * 1e-3) / 1e9
+        traffic = recorded_traffic("k2p_step", spl)
+        dom_kernel = "k2p_step"
+        kernel_ms = {"k2p_step": launch_ms / spl}
+        per_kernel = {"k2p_step": {"ms_per_launch": launch_ms, "steps_per_launch": spl, "share": 1.0,
+                                   "algorithmic_bytes_per_launch": ab["step"] * spl, "achieved_gbs": achieved,
+                                   "frac": achieved / hbm, "traffic": traffic}}
+        duration_method = ("CUDA events around each timed launch of k2p_step (one launch per interval of "
+                           f"{spl} steps), on the launching stream")
+        algo = {"step": ab["step"], "per_launch": ab["step"] * spl, "col_phase": ab["col"], "row_phase": ab["row"]}
+    else:
+        # per-kernel durations (CUDA events around each launch, same stream)
+        kern_ms = s.time_kernels(200)
+        names = {0: "col", 2: "row"}
+        kernel_names = {0: "k2_col", 2: "k2_row"} if s.step_path == "fast2d" else {0: "k_col", 2: "k_row"}
+        # An event pair around every launch puts event nodes between the kernels,
+        # and each adds its own gap (the brackets sum to more than the step): the
+        # brackets give each kernel's share of the step, and the live step time
+        # (events around the timed replays) splits by those shares.
+        bracket_sum = kern_ms[0] + kern_ms[2]
+        live_ms = {k: ms_per_step * kern_ms[k] / bracket_sum for k in (0, 2)}
+        dom = max((0, 2), key=lambda k: live_ms[k])
+        achieved = ab[names[dom]] / (live_ms[dom] * 1e-3) / 1e9
+        per_kernel = {kernel_names[k]: {"ms": live_ms[k], "share": kern_ms[k] / bracket_sum,
+                                        "algorithmic_bytes": ab[names[k]],
+                                        "achieved_gbs": ab[names[k]] / (live_ms[k] * 1e-3) / 1e9,
+                                        "frac": ab[names[k]] / (live_ms[k] * 1e-3) / 1e9 / hbm,
+                                        "event_bracket_ms": kern_ms[k],
+                                        "traffic": recorded_traffic(kernel_names[k])} for k in (0, 2)}
+        traffic = recorded_traffic(kernel_names[dom])
+        dom_kernel = kernel_names[dom]
+        kernel_ms = {kernel_names[0]: live_ms[0], kernel_names[2]: live_ms[2]}
+        duration_method = ("live step time (CUDA events around the timed graph replays) split by each kernel's "
+                           "share of per-launch CUDA-event brackets (200 steps)")
+        algo = {"col": ab["col"], "row": ab["row"], "step": ab["step"]}
 
     # end to end through the public API with host buffers: pinned upload of phi_0,
     # steps, S(q) to the host every INTERVAL steps, final field to the host
@@ -831,14 +870,14 @@ def run_gpu(args):
                               "length: every graph the timed region replays is captured before it)",
                    "graph_steps": ((tuning or {}).get("graph_steps") or 16),
                    "autotuned": tuning},
-        "roofline": {"bound": "hbm", "kernel": kernel_names[dom], "achieved": achieved,
+        "roofline": {"bound": "hbm", "kernel": dom_kernel, "achieved": achieved,
                      "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
                      "peak_source": f"{peak_kind} hbm_gbs", "step_frac": (ab["step"] / (ms_per_step * 1e-3) / 1e9) / hbm,
-                     "kernel_ms": {kernel_names[0]: live_ms[0], kernel_names[2]: live_ms[2]},
-                     "duration_method": "live step time (CUDA events around the timed graph replays) split by "
-                                        "each kernel's share of per-launch CUDA-event brackets (200 steps)",
+                     "kernel_ms": kernel_ms,
+                     "duration_method": duration_method,
                      "per_kernel": per_kernel,
-                     "algorithmic_bytes": {"col": ab["col"], "row": ab["row"], "step": ab["step"]}},
+                     "algorithmic_bytes": algo},
+        "step_path": s.step_path,
         "e2e": {"value": sites * K * world / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d / K,
                 "d2h_bytes_per_step": d2h / K},
         "gpu_launches": launches,

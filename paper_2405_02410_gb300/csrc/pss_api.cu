@@ -135,8 +135,11 @@ struct pss_system {
     int tune_persist = 1;                    // square FP32 2D systems: a run of steps as one persistent launch
     int tune_persist_blocks = 0;             // its CTAs (0: every SM, at most one CTA per column pair or row pair)
     int coop = 0;                            // the device takes cooperative launches
+    // captured persistent launches by run length (one kernel node each); p2_capture < 0: capture
+    // of the cooperative launch is refused here, launch directly
+    std::vector<std::pair<int, cudaGraphExec_t>> p2_graphs;
+    int p2_capture = 1;
     GridSync *gs = nullptr;                  // grid-barrier words of the persistent step
-    unsigned long long bar_base = 0;         // their arrival count after every launch so far
     int64_t launches = 0;
     std::string err;
     // adjoint: checkpoints of the last pss_adjoint_forward run
@@ -1126,6 +1129,8 @@ int capture_graph(pss_system **sys, int n, int steps, cudaGraphExec_t *out) {
 void drop_graphs(pss_system *s) {
     for (cudaGraphExec_t &g : s->graphs)
         if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+    for (auto &pg : s->p2_graphs) cudaGraphExecDestroy(pg.second);
+    s->p2_graphs.clear();
 }
 
 // The persistent path: runs of at most kMaxPersistSteps steps, one
@@ -1147,18 +1152,55 @@ P2Args p2_args(pss_system *s, int nsteps) {
     a.d_step = s->d_step;
     a.d_status = s->d_status;
     a.gs = s->gs;
-    a.bar_base = s->bar_base;
     a.nsteps = nsteps;
     return a;
 }
 
+// The launch of a run of `len` steps, captured once into a graph of one
+// kernel node and replayed (a graph launch costs the host less than a
+// cooperative launch); the arguments depend only on len and the system's
+// buffers and launch shape, so a graph stays valid until the system's
+// launches change (invalidate).  If the capture is refused, every run
+// launches directly.
+constexpr size_t kMaxP2Graphs = 8;
+
+cudaGraphExec_t p2_graph(pss_system *s, int len) {
+    if (s->p2_capture <= 0) return nullptr;
+    for (auto &pg : s->p2_graphs)
+        if (pg.first == len) return pg.second;
+    cudaError_t e = cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) { cudaGetLastError(); s->p2_capture = -1; return nullptr; }
+    cudaError_t el = launch_p2(p2_args(s, len), s->nx, p2_radix(s), p2_blocks(s), s->cap_stream);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(s->cap_stream, &g);
+    cudaGraphExec_t ge = nullptr;
+    if (el == cudaSuccess && e == cudaSuccess) e = cudaGraphInstantiate(&ge, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (el != cudaSuccess || e != cudaSuccess || !ge) {
+        cudaGetLastError();   // a refused capture leaves no error behind: launch directly from now on
+        if (ge) cudaGraphExecDestroy(ge);
+        s->p2_capture = -1;
+        return nullptr;
+    }
+    if (s->p2_graphs.size() >= kMaxP2Graphs) {
+        cudaGraphExecDestroy(s->p2_graphs.front().second);
+        s->p2_graphs.erase(s->p2_graphs.begin());
+    }
+    s->p2_graphs.emplace_back(len, ge);
+    return ge;
+}
+
 int run_persist(pss_system *s, int64_t n, cudaStream_t st) {
+    if (!s->graph_valid) {
+        drop_graphs(s);
+        s->graph_valid = true;
+    }
     for (int64_t done = 0; done < n;) {
         const int len = (int)std::min<int64_t>(kMaxPersistSteps, n - done);
-        cudaError_t e = launch_p2(p2_args(s, len), s->nx, p2_radix(s), p2_blocks(s), st);
+        cudaGraphExec_t g = p2_graph(s, len);
+        cudaError_t e = g ? cudaGraphLaunch(g, st) : launch_p2(p2_args(s, len), s->nx, p2_radix(s), p2_blocks(s), st);
         s->launches++;
         if (e != cudaSuccess) return cuda_fail(s, e, "k2p_step launch");
-        s->bar_base += (unsigned long long)(2 * len - 1) * (unsigned long long)p2_blocks(s);
         done += len;
     }
     return PSS_OK;
@@ -1254,7 +1296,6 @@ int device_errors(pss_system *s) {
             // a persistent launch that gave up leaves its barrier words behind
             CK(cudaMemsetAsync(s->gs, 0, sizeof(GridSync), s->stream));
             CK(cudaStreamSynchronize(s->stream));
-            s->bar_base = 0;
             return fail(s, PSS_ETIMEOUT, "a bounded device wait ran out");
         }
         return fail(s, PSS_ENONFINITE, "a field became NaN or Inf");
@@ -1945,7 +1986,6 @@ int pss_time_kernels(pss_system *s, int64_t n, double *avg_ms) {
             const int len = (int)std::min<int64_t>(n, kMaxPersistSteps);
             e = launch_p2(p2_args(s, len), s->nx, p2_radix(s), p2_blocks(s), s->stream);
             s->launches++;
-            if (e == cudaSuccess) s->bar_base += (unsigned long long)(2 * len - 1) * (unsigned long long)p2_blocks(s);
         }
         if (e == cudaSuccess) e = cudaEventRecord(e1, s->stream);
         if (e == cudaSuccess) e = cudaEventSynchronize(e1);

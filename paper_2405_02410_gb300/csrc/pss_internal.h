@@ -199,12 +199,12 @@ cudaError_t launch_row2(const RowArgs<float> &a, int nslots, cudaStream_t st, bo
 // The persistent FP32 2D step (k2p_step: square sides of 256, 512 or 1024
 // points, one field, one instance): grid-barrier words of one system
 // (16 bytes, zero-initialised) and the launch arguments.  Barrier i of a
-// launch (0-based) completes when gs->count reaches bar_base + (i + 1)
-// gridDim.x; the host advances bar_base by the arrivals of every launch.
+// launch (0-based) completes when gs->count reaches (i + 1) gridDim.x; the
+// last CTA to finish a launch sets count back to 0.
 struct GridSync {
-    unsigned long long count;   // CTA arrivals at grid barriers since the last reset
+    unsigned long long count;   // CTA arrivals at the launch's grid barriers so far
     unsigned int abort;         // a CTA gave up waiting: the others leave too
-    unsigned int pad;
+    unsigned int done;          // CTAs finished (the last one resets count and done)
 };
 struct P2Args {
     SysP<float> sp;
@@ -212,12 +212,11 @@ struct P2Args {
     float2 *state;              // tiled [tile][ny][4]
     float2 *P;                  // x-transformed product, column-major [kx][ny]
     float2 *T1;                 // conjugated y-inverse of the kept columns, column-major [kx][ny]
-    float2 *xi;                 // unit-amplitude noise of the step after the run, tiled (written at the end)
+    float2 *xi;                 // unit-amplitude noise of the next step, tiled: read at the start, written at the end
     const float2 *tw;
     long long *d_step;
     int *d_status;
     GridSync *gs;
-    unsigned long long bar_base;   // gs->count when the launch starts (every earlier barrier complete)
     int nsteps;
 };
 // n steps in one cooperative launch of nblocks CTAs (E: FFT pass radix, 8 or 16)

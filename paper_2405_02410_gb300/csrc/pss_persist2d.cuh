@@ -24,6 +24,9 @@
 // the issue slots the latency-bound transforms leave idle).  A buffer is
 // handed over through two mbarriers: "full" (the noise warps have drawn it)
 // and "empty" (the update has read it); every wait on them is bounded.  The
+// first step's noise is the one the previous launch (or the two-kernel
+// path) left drawn ahead in the noise array, and the launch leaves the next
+// step's there in turn.  The
 // per-mode factors of the update, g = 1 / (1 + dt O(q)) and dt M(q), are
 // computed once per launch.
 // Every arithmetic operation on the data is the one k2_col / k2_row perform
@@ -182,13 +185,15 @@ __global__ void __launch_bounds__(P2Shape<N, E, NNW, NHW>::THREADS, 1) k2p_step(
         reinterpret_cast<uint32_t *>(&sfp)[i] = reinterpret_cast<const uint32_t *>(a.fps)[i];
     if (t == 0) {
         s_step0 = (unsigned)(*a.d_step);
-        s_abort = 0;
+        // an earlier launch gave up (its barrier words are not yet cleared): leave at once
+        s_abort = ld_relaxed_gpu(&a.gs->abort) ? 1 : 0;
         mbar_init(full, 32 * NNW);
         mbar_init(full + 1, 32 * NNW);
         mbar_init(empty, 1);
         mbar_init(empty + 1, 1);
     }
     __syncthreads();   // the only CTA-wide barrier: from here on the two roles run apart
+    if (s_abort) return;
     const bool noisy = fp.noisy != 0;
 
     if (t >= NMAIN) {
@@ -198,9 +203,13 @@ __global__ void __launch_bounds__(P2Shape<N, E, NNW, NHW>::THREADS, 1) k2p_step(
         const int tn = t - NMAIN;
         const PhiloxKey key = philox_key(fp.seed_lo, fp.seed_hi);
         const int npairs = (u1 - u0) * N;
-        for (int n = 0; n <= a.nsteps; ++n) {
+        // draw n (the noise of step step0 + n) goes to buffer n & 1; the first
+        // step's (n = 0) comes from the noise array.  Before draw n >= 2 the
+        // buffer's last reader, step n - 2, must have released it: release
+        // number (n - 2 - b) / 2 of that buffer.
+        for (int n = 1; n <= a.nsteps; ++n) {
             const int b = n & 1;
-            if (n >= 2 && !mbar_wait_abortable(empty + b, ((n >> 1) - 1) & 1, &s_abort)) {
+            if (n >= 2 && !mbar_wait_abortable(empty + b, ((n - 2 - b) >> 1) & 1, &s_abort)) {
                 if (!s_abort && a.d_status) atomicOr(a.d_status, kStatusTimeout);
                 s_abort = 1;
                 return;
@@ -239,12 +248,22 @@ __global__ void __launch_bounds__(P2Shape<N, E, NNW, NHW>::THREADS, 1) k2p_step(
             dtO[i] = sp.dt * fp.O[i];
             dtM[i] = sp.dt * fp.M[i];
         }
+        // the state and the first step's noise of each column pair: 16 bytes per
+        // (pair, ky) of the tiled arrays (the pair's two columns are neighbours)
+        for (int i = t; i < (u1 - u0) * N; i += NMAIN) {
+            const int uu = i >> ilog2(N), ky = i & (N - 1), kx0 = 2 * (u0 + uu);
+            const size_t o = ((size_t)(kx0 >> 2) * N + ky) * 4 + (kx0 & 3);
+            float4 v = __ldcg(reinterpret_cast<const float4 *>(a.state + o));
+            float4 x = noisy ? __ldcg(reinterpret_cast<const float4 *>(a.xi + o)) : make_float4(0.f, 0.f, 0.f, 0.f);
+            if (kx0 + 1 >= sp.hx) { v.z = 0.f; v.w = 0.f; x.z = 0.f; x.w = 0.f; }   // past Nx/2
+            ST[(2 * uu) * N + ky] = mk<float>(v.x, v.y);
+            ST[(2 * uu + 1) * N + ky] = mk<float>(v.z, v.w);
+            NZ[(2 * uu) * N + ky] = mk<float>(x.x, x.y);
+            NZ[(2 * uu + 1) * N + ky] = mk<float>(x.z, x.w);
+        }
         for (int c = 0; c < ncs; ++c) {
-            const int kx = kx_of(c);
-            const float qx = fmul(float(kx), sp.gx);
+            const float qx = fmul(float(kx_of(c)), sp.gx);
             for (int ky = t; ky < N; ky += NMAIN) {
-                ST[c * N + ky] =
-                    kx < sp.hx ? a.state[((size_t)(kx >> 2) * N + ky) * 4 + (kx & 3)] : mk<float>(0.f, 0.f);
                 float m, gg;
                 update_factors<float>(q2sum(qx, fmul(float(signed_k(ky, N)), sp.gy)), dtO, dtM, m, gg);
                 MG[c * N + ky] = make_float2(m, gg);
@@ -265,7 +284,7 @@ __global__ void __launch_bounds__(P2Shape<N, E, NNW, NHW>::THREADS, 1) k2p_step(
         main_sync<NMAIN>();
         return !s_abort;
     };
-    unsigned long long target = a.bar_base;   // the arrival count that ends the next grid barrier
+    unsigned long long target = 0;   // the arrival count that ends the next grid barrier
 
 #pragma unroll 1
     for (int n = 0; n < a.nsteps && alive; ++n) {
@@ -292,8 +311,9 @@ __global__ void __launch_bounds__(P2Shape<N, E, NNW, NHW>::THREADS, 1) k2p_step(
                 }
             }
             asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
-            // the noise of this step (every thread of the group waits; bounded)
-            if (!mbar_wait_abortable(full + b, (n >> 1) & 1, &s_abort)) {
+            // the noise of this step (every thread of the group waits; bounded): draw
+            // number (n - 2 + b) / 2 into buffer b; step 0's came with the set-up
+            if (n > 0 && !mbar_wait_abortable(full + b, ((n - 2 + b) >> 1) & 1, &s_abort)) {
                 if (!s_abort && a.d_status) atomicOr(a.d_status, kStatusTimeout);
                 s_abort = 1;
             }
@@ -397,22 +417,29 @@ __global__ void __launch_bounds__(P2Shape<N, E, NNW, NHW>::THREADS, 1) k2p_step(
     // ---- the state, and the next step's unit noise (as the two-kernel path keeps it), back to the
     // tiled arrays; a non-finite mode of the state is reported (it spreads to every mode in a step)
     const int bl = a.nsteps & 1;
-    if (!wait_full(bl, (a.nsteps >> 1) & 1)) return;
+    if (!wait_full(bl, ((a.nsteps - 2 + bl) >> 1) & 1)) return;
     const C *nz = NZ + (size_t)bl * NG * N;
     bool bad = false;
-    for (int c = 0; c < ncs; ++c) {
-        const int kx = kx_of(c);
-        if (kx >= sp.hx) continue;
-        for (int ky = t; ky < N; ky += NMAIN) {
-            const size_t o = ((size_t)(kx >> 2) * N + ky) * 4 + (kx & 3);
-            const C v = ST[c * N + ky];
-            bad |= !(fabsf(v.x) + fabsf(v.y) <= 3.0e38f);
-            a.state[o] = v;
-            if (a.xi) a.xi[o] = noisy ? nz[c * N + ky] : mk<float>(0.f, 0.f);
+    for (int i = t; i < (u1 - u0) * N; i += NMAIN) {
+        const int uu = i >> ilog2(N), ky = i & (N - 1), kx0 = 2 * (u0 + uu);
+        const size_t o = ((size_t)(kx0 >> 2) * N + ky) * 4 + (kx0 & 3);
+        const C v0 = ST[(2 * uu) * N + ky], v1 = ST[(2 * uu + 1) * N + ky];   // zero past Nx/2
+        bad |= !(fabsf(v0.x) + fabsf(v0.y) + fabsf(v1.x) + fabsf(v1.y) <= 3.0e38f);
+        *reinterpret_cast<float4 *>(a.state + o) = make_float4(v0.x, v0.y, v1.x, v1.y);
+        if (a.xi) {
+            const C x0 = noisy ? nz[(2 * uu) * N + ky] : mk<float>(0.f, 0.f);
+            const C x1 = noisy ? nz[(2 * uu + 1) * N + ky] : mk<float>(0.f, 0.f);
+            *reinterpret_cast<float4 *>(a.xi + o) = make_float4(x0.x, x0.y, x1.x, x1.y);
         }
     }
     if (bad && a.d_status) atomicOr(a.d_status, kStatusNonFinite);
     if (blockIdx.x == 0 && t == 0) *a.d_step = (long long)s_step0 + a.nsteps;
+    // the last CTA to finish sets the barrier words back for the next launch
+    // (the kernel boundary orders this before that launch's first arrival)
+    if (t == 0 && atomicAdd(&a.gs->done, 1u) == nb - 1) {
+        a.gs->count = 0ull;
+        a.gs->done = 0u;
+    }
 }
 
 }  // namespace pss
