@@ -258,10 +258,10 @@ def oracle_parity(pss, stream, phi_1024, steps_1024, tuning, tuning3, probes, do
         g.step(100)
         out[f"model_b_64_{prec}"] = {"steps": 100, "rel_l2": _rel_l2(g.get_spectrum(0), ref)}
         g.close()
-    for sz, (seed, a, steps, spec) in sorted(probes.items()):
+    for sz, (seed, a, steps, spec, inst) in sorted(probes.items()):
         m = O.model_b((sz, sz), dt=0.01, a=a, b=1.0, K=1.0, D=0.01, seed=seed)
         ref = O.half(O.run(m, O.to_spectrum(m, O.init_uniform(m, -0.1, 0.1)), 0, steps))
-        out[f"ensemble_{sz}_instance0_f32"] = {"steps": steps, "rel_l2": _rel_l2(spec, ref)}
+        out[f"ensemble_{sz}_first_instance_f32"] = {"instance": inst, "steps": steps, "rel_l2": _rel_l2(spec, ref)}
     if pool is not None:
         g = pss.System((256, 256, 256), dt=0.005, seed=w["seed"], precision="f32")
         pss.add_model_a_field(g, a=-1, b=1, K=1, D=0.05, name="psi")
@@ -316,79 +316,77 @@ def make_system(pss, shape, precision="f32"):
     return s
 
 
-def ensemble_systems(pss, n=512, gen_seed=2405, base_seed=10000):
-    """512 independent 2D Model B instances, sizes drawn uniformly from {64, 128, 256, 512}^2, per-instance
-    seeds base + i and a ~ U[-1.5, -0.5], grouped into one batched system per size class."""
-    import numpy as np
-    g = np.random.default_rng(gen_seed)
-    sizes = g.choice([64, 128, 256, 512], size=n)
-    a_vals = g.uniform(-1.5, -0.5, size=n)
-    systems, sites = [], 0
-    first = {}
-    for sz in (64, 128, 256, 512):
-        idx = np.nonzero(sizes == sz)[0]
-        if len(idx) == 0:
-            continue
-        s = pss.System((int(sz), int(sz)), dt=0.01, batch=len(idx), seeds=[base_seed + int(i) for i in idx])
-        pss.add_model_b_field(s, a=-1.0, b=1.0, K=1.0, D=0.01)
-        s.set_param_batch(0, a_vals[idx])
-        for j in range(len(idx)):
-            s.select_instance(j)
-            s.init_uniform(0, -0.1, 0.1)
-        systems.append(s)
-        sites += len(idx) * int(sz) * int(sz)
-        first[int(sz)] = (base_seed + int(idx[0]), float(a_vals[idx[0]]))
-    ensemble_systems.first = first          # instance 0 of each size class: (seed, a)
-    return systems, sites, {int(k): int((sizes == k).sum()) for k in (64, 128, 256, 512)}
-
-
-def ensemble_measurement(pss, torch, stream, steps=200, tune=True):
-    systems, sites, counts = ensemble_systems(pss)
+def ensemble_measurement(pss, torch, stream, steps=200, tune=True, rank=0, world=1):
+    """The 512-instance ensemble (paper_2405_02410_gb300.ensemble.recipe: sides uniform over
+    {64, 128, 256, 512}^2, seeds 10000 + i, a ~ U[-1.5, -0.5]), one batched system per side, all
+    stepped from one CUDA graph.  With world > 1 the instances are split over the ranks by cost
+    (sites x steps); each rank runs its share, the time is the slowest rank's, and the per-instance
+    S(q) (64 bins, FP64) are gathered and averaged per side in instance order."""
+    from paper_2405_02410_gb300 import ensemble as E
+    spec = E.recipe(n=512, steps=steps)
+    idx = E.share(spec, rank, world)
+    groups = E.build_systems(pss, spec, idx)
+    systems = [g[1] for g in groups]
     tuning = {}
-    for s in systems:
+    for sz, s, _ in groups:
         s.set_stream(stream)
         if tune:
-            tuning[s.shape[0]] = s.autotune(16)
-    pss.step_many(systems, 32)
+            tuning[sz] = s.autotune(16)
+    warm = 32
+    if systems:
+        pss.step_many(systems, warm)
     torch.cuda.synchronize()
+    barrier(world)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    pss.step_many(systems, steps)
+    if systems:
+        pss.step_many(systems, steps)
     e1.record(stream)
     e1.synchronize()
-    ms = e0.elapsed_time(e1) / steps
+    local_ms = e0.elapsed_time(e1)
+    t_max = max_over_ranks(local_ms, world)
+    ms = t_max / steps
+    sites_all = sum(int(n) ** 2 for n in spec.side)
+    per_inst = E.structure_factors(groups, spec.nbins)
+    merged = E.merge(spec, E.gather(per_inst, world))
     probes = {}
-    for s in systems:
+    for sz, s, ix in groups:
         s.sync()
-        if s.shape[0] in (64, 128):        # instance 0 of the small classes, for the oracle leg
+        if sz in (64, 128):        # the first instance of the small sides on this rank, for the oracle leg
             s.select_instance(0)
-            seed, a = ensemble_systems.first[s.shape[0]]
-            probes[s.shape[0]] = (seed, a, s.get_step(), s.get_spectrum(0))
+            probes[sz] = (spec.seed[ix[0]], spec.a[ix[0]], s.get_step(), s.get_spectrum(0), ix[0])
         s.close()
-    # the plain single-system path on the same instances: one system per instance, run one after another
-    seq_ms = 0.0
-    for sz, cnt in counts.items():
-        one = pss.model_b((sz, sz), seed=1)
-        one.set_stream(stream)
-        one.init_uniform(0, -0.1, 0.1)
-        if tune:
-            one.autotune(16)
-        one.step(32)
-        f0 = torch.cuda.Event(enable_timing=True)
-        f1 = torch.cuda.Event(enable_timing=True)
-        f0.record(stream)
-        one.step(steps)
-        f1.record(stream)
-        f1.synchronize()
-        seq_ms += cnt * f0.elapsed_time(f1) / steps
-        one.close()
-    return {"instances": 512, "size_counts": counts, "sites": sites, "ms_per_step": ms,
-            "site_steps_per_s": sites / (ms * 1e-3),
-            "sequential_single_system_ms_per_step": seq_ms,
-            "speedup_vs_sequential": seq_ms / ms,
-            "autotuned": {str(k): v for k, v in tuning.items()} if tune else None,
-            "_probes": probes}
+    counts = {int(k): int(sum(1 for n in spec.side if n == k)) for k in E.SIZES}
+    out = {"instances": len(spec), "size_counts": counts, "sites": sites_all, "ms_per_step": ms,
+           "site_steps_per_s": sites_all / (ms * 1e-3), "ranks": world,
+           "partition": "instances split by sites x steps, longest first onto the least-loaded rank",
+           "instances_per_rank": [len(x) for x in E.partition([spec.cost(i) for i in range(len(spec))], world)],
+           "this_rank_ms": local_ms / steps,
+           "S_q_mean_by_side": {str(k): v.tolist() for k, v in merged.items()},
+           "S_q_after_steps": warm + steps,
+           "autotuned": {str(k): v for k, v in tuning.items()} if tune else None,
+           "_probes": probes}
+    if world == 1:
+        # the plain single-system path on the same instances: one system per instance, run one after another
+        seq_ms = 0.0
+        for sz, cnt in counts.items():
+            one = pss.model_b((sz, sz), seed=1)
+            one.set_stream(stream)
+            one.init_uniform(0, -0.1, 0.1)
+            if tune:
+                one.autotune(16)
+            one.step(32)
+            f0 = torch.cuda.Event(enable_timing=True)
+            f1 = torch.cuda.Event(enable_timing=True)
+            f0.record(stream)
+            one.step(steps)
+            f1.record(stream)
+            f1.synchronize()
+            seq_ms += cnt * f0.elapsed_time(f1) / steps
+            one.close()
+        out.update({"sequential_single_system_ms_per_step": seq_ms, "speedup_vs_sequential": seq_ms / ms})
+    return out
 
 
 def cufft_comparison(torch, stream, shape=(1024, 1024), steps=2000, graph_steps=20):
@@ -843,7 +841,8 @@ def run_gpu(args):
         s3.close()
 
     if not args.no_ensemble:
-        extra["ensemble_512"] = ensemble_measurement(pss, torch, stream, tune=not args.no_autotune)
+        extra["ensemble_512"] = ensemble_measurement(pss, torch, stream, tune=not args.no_autotune, rank=rank,
+                                                     world=world)
     probes = extra["ensemble_512"].pop("_probes") if "ensemble_512" in extra else {}
     if not args.no_adjoint:
         extra["adjoint_256"] = adjoint_measurement(pss, torch, stream, tune=not args.no_autotune)

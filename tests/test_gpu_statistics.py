@@ -108,3 +108,34 @@ def test_ensemble_of_mixed_sizes_structure_factor_by_size():
     for shape, seeds, a_values, s in groups:
         _compare(_gpu_sq(s, per_size), ref[k:k + per_size])
         k += per_size
+
+
+def test_ensemble_recipe_structure_factor_all_four_sides():
+    # instances of the 512-instance ensemble recipe (their own side, seed and a), built
+    # and stepped through the ensemble module (one batched system per side, one graph);
+    # the S(q) averaged over the instances of each side of 64, 128, 256 and 512 points
+    # against the oracle's (4 instances of the small sides, 2 of the large ones)
+    from paper_2405_02410_gb300 import ensemble as E
+    P = pss()
+    steps = 300
+    full = E.recipe(n=512, steps=steps)
+    want = {64: 4, 128: 4, 256: 2, 512: 2}
+    pick = []
+    for i in range(len(full)):
+        if want.get(full.side[i], 0) > 0:
+            pick.append(i)
+            want[full.side[i]] -= 1
+    spec = E.Spec(side=[full.side[i] for i in pick], seed=[full.seed[i] for i in pick],
+                  a=[full.a[i] for i in pick], steps=steps, nbins=NBINS)
+    groups = E.build_systems(P, spec, list(range(len(spec))))
+    P.step_many([g[1] for g in groups], steps)
+    per = E.structure_factors(groups, NBINS)
+    ref = _oracle_pool([((spec.side[i],) * 2, spec.a[i], spec.seed[i], steps) for i in range(len(spec))])
+    got_by_side = E.merge(spec, per)
+    ref_by_side = E.merge(spec, {i: r[0] for i, r in enumerate(ref)})
+    assert set(got_by_side) == {64, 128, 256, 512}
+    for side in got_by_side:
+        counts = ref[spec.side.index(side)][1]
+        filled = counts > 0
+        dev = np.abs(got_by_side[side][filled] - ref_by_side[side][filled]) / ref_by_side[side][filled]
+        assert dev.max() <= TOL, (side, dev.max())
