@@ -1,6 +1,6 @@
 """Build libpss.so (the sm_103a kernels and the C ABI of include/pss.h) in-tree.
 
-nvcc compiles the seven translation units in parallel (one -gencode, sm_103a)
+nvcc compiles the eight translation units in parallel (one -gencode, sm_103a)
 and links them into paper_2405_02410_gb300/_lib/libpss.so.
 """
 from __future__ import annotations
@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libpss.so")
 SOURCES = ["pss_api.cu", "pss_kern_f32.cu", "pss_kern_f64.cu", "pss_kern_f32_r16.cu", "pss_kern_f64_r16.cu",
-           "pss_kern_fast2d.cu", "pss_kern_persist.cu"]
+           "pss_kern_fast2d.cu", "pss_kern_persist.cu", "pss_kern_persist_kpz.cu"]
 HEADERS = ["pss_device.cuh", "pss_internal.h", "pss_kernels.cuh", "pss_fast2d.cuh", "pss_persist2d.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fno-strict-aliasing",

@@ -392,10 +392,26 @@ bool round_trip(const pss_system *s);
 // A run of steps of a square FP32 2D system with one field and one instance
 // on the FFT-group path is one persistent launch (k2p_step), where the
 // device takes cooperative launches.
+// The KPZ field of pss_add_grad_sq_term alone: one field whose explicit terms
+// are M (d_x h)^2 + M (d_y h)^2 with one operator M (no power term).
+bool kpz2d_shape(const pss_system *s) {
+    if (s->dim != 2 || s->fields.size() != 1 || s->fields[0].power != 0 || s->gterms.size() != 2) return false;
+    bool axis[2] = {false, false};
+    for (const GTerm &t : s->gterms) {
+        if (t.target != 0 || t.factors.size() != 1 || !same_mono(t.M, s->gterms[0].M)) return false;
+        const GFactor &f = t.factors[0];
+        if (f.field != 0 || f.power != 2 || f.lap != 0 || f.deriv < 0 || f.deriv > 1) return false;
+        axis[f.deriv] = true;
+    }
+    return axis[0] && axis[1];
+}
 bool persist2d_ok(const pss_system *s) {
-    return fast2d(s) && s->nx == s->ny && s->batch == 1 && s->fields.size() == 1 && s->coop && !round_trip(s);
+    auto side = [](int n) { return n == 256 || n == 512 || n == 1024; };
+    return s->tune_fast2d && s->prec == PSS_F32 && s->dim == 2 && side(s->nx) && s->nx == s->ny && s->batch == 1 &&
+           s->fields.size() == 1 && s->coop && !round_trip(s) && (!any_general(s) || kpz2d_shape(s));
 }
 bool persist2d(const pss_system *s) { return s->tune_persist && persist2d_ok(s); }
+int p2_mode(const pss_system *s) { return any_general(s) ? 1 : 0; }
 // FFT pass radix of the persistent step: 16 at 1024 points (three passes of
 // two warps per transform), 8 below (measured faster at 512: 6.2 against 8.3
 // us per step)
@@ -1009,8 +1025,20 @@ int alloc_term_scratch(pss_system *s) {
     return PSS_OK;
 }
 
-int prologue(pss_system *s) {
+// Makes B hold the product of the current state (and, on the FP32 2D path, XI
+// the current step's noise) for the step kernels.  With for_persist the run
+// that follows is a persistent launch, which computes both itself when they
+// are stale (its prologue flag): only the arrays are allocated here.
+int prologue(pss_system *s, bool for_persist = false) {
     if (int rc = alloc_term_scratch(s)) return rc;
+    if (for_persist) {
+        if (!s->XI) {
+            const size_t bytes = csize(s) * s->field_elems * (size_t)s->nslots();
+            CK(cudaMalloc(&s->XI, bytes));
+            CK(cudaMemset(s->XI, 0, bytes));
+        }
+        return PSS_OK;
+    }
     if (!s->stale && s->b_fast == fast2d(s)) return PSS_OK;
     if (fast2d(s) && !s->XI) {
         const size_t bytes = csize(s) * s->field_elems * (size_t)s->nslots();
@@ -1147,12 +1175,14 @@ P2Args p2_args(pss_system *s, int nsteps) {
     a.state = (float2 *)s->state;
     a.P = (float2 *)s->B;
     a.T1 = (float2 *)s->A;
+    a.T1a = (float2 *)s->GS;
     a.xi = any_noisy(s) ? (float2 *)s->XI : nullptr;
     a.tw = (const float2 *)s->tw;
     a.d_step = s->d_step;
     a.d_status = s->d_status;
     a.gs = s->gs;
     a.nsteps = nsteps;
+    a.prologue = (s->stale || !s->b_fast) ? 1 : 0;
     return a;
 }
 
@@ -1166,11 +1196,13 @@ constexpr size_t kMaxP2Graphs = 8;
 
 cudaGraphExec_t p2_graph(pss_system *s, int len) {
     if (s->p2_capture <= 0) return nullptr;
+    const P2Args args = p2_args(s, len);
+    const int key = 2 * len + args.prologue;
     for (auto &pg : s->p2_graphs)
-        if (pg.first == len) return pg.second;
+        if (pg.first == key) return pg.second;
     cudaError_t e = cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) { cudaGetLastError(); s->p2_capture = -1; return nullptr; }
-    cudaError_t el = launch_p2(p2_args(s, len), s->nx, p2_radix(s), p2_blocks(s), s->cap_stream);
+    cudaError_t el = launch_p2(args, s->nx, p2_radix(s), p2_blocks(s), p2_mode(s), s->cap_stream);
     cudaGraph_t g = nullptr;
     e = cudaStreamEndCapture(s->cap_stream, &g);
     cudaGraphExec_t ge = nullptr;
@@ -1186,7 +1218,7 @@ cudaGraphExec_t p2_graph(pss_system *s, int len) {
         cudaGraphExecDestroy(s->p2_graphs.front().second);
         s->p2_graphs.erase(s->p2_graphs.begin());
     }
-    s->p2_graphs.emplace_back(len, ge);
+    s->p2_graphs.emplace_back(key, ge);
     return ge;
 }
 
@@ -1198,9 +1230,14 @@ int run_persist(pss_system *s, int64_t n, cudaStream_t st) {
     for (int64_t done = 0; done < n;) {
         const int len = (int)std::min<int64_t>(kMaxPersistSteps, n - done);
         cudaGraphExec_t g = p2_graph(s, len);
-        cudaError_t e = g ? cudaGraphLaunch(g, st) : launch_p2(p2_args(s, len), s->nx, p2_radix(s), p2_blocks(s), st);
+        cudaError_t e = g ? cudaGraphLaunch(g, st)
+                          : launch_p2(p2_args(s, len), s->nx, p2_radix(s), p2_blocks(s), p2_mode(s), st);
         s->launches++;
         if (e != cudaSuccess) return cuda_fail(s, e, "k2p_step launch");
+        // the launch leaves the product of its last state in B (column-major) and the
+        // next step's noise in XI, as the FP32 2D path keeps them
+        s->stale = false;
+        s->b_fast = true;
         done += len;
     }
     return PSS_OK;
@@ -1820,7 +1857,7 @@ int pss_step(pss_system *s, int64_t n) {
     int rc = upload_params(s);
     if (rc) return rc;
     if (round_trip(s) && (rc = ensure_real(s))) return rc;
-    if ((rc = prologue(s))) return rc;
+    if ((rc = prologue(s, persist2d(s)))) return rc;
     if ((rc = run_steps(s, n))) return rc;
     s->step += n;
     return PSS_OK;
@@ -1975,7 +2012,7 @@ int pss_time_kernels(pss_system *s, int64_t n, double *avg_ms) {
     if (s->fields.empty()) return fail(s, PSS_EINVAL, "no fields");
     int rc = upload_params(s);
     if (rc) return rc;
-    if ((rc = prologue(s))) return rc;
+    if ((rc = prologue(s, persist2d(s)))) return rc;
     if (persist2d(s)) {
         // one launch of n steps between two events: its duration per step
         cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -1984,8 +2021,9 @@ int pss_time_kernels(pss_system *s, int64_t n, double *avg_ms) {
         if (e == cudaSuccess) e = cudaEventRecord(e0, s->stream);
         if (e == cudaSuccess) {
             const int len = (int)std::min<int64_t>(n, kMaxPersistSteps);
-            e = launch_p2(p2_args(s, len), s->nx, p2_radix(s), p2_blocks(s), s->stream);
+            e = launch_p2(p2_args(s, len), s->nx, p2_radix(s), p2_blocks(s), p2_mode(s), s->stream);
             s->launches++;
+            if (e == cudaSuccess) { s->stale = false; s->b_fast = true; }
         }
         if (e == cudaSuccess) e = cudaEventRecord(e1, s->stream);
         if (e == cudaSuccess) e = cudaEventSynchronize(e1);
@@ -2194,7 +2232,7 @@ int pss_autotune(pss_system *s, int64_t steps_per_trial, char *report, size_t re
     int rc = upload_params(s);
     if (rc) return rc;
     if (round_trip(s) && (rc = ensure_real(s))) return rc;
-    if ((rc = prologue(s))) return rc;
+    if ((rc = prologue(s, persist2d(s)))) return rc;
     // keep the state and the step counter: the trials advance the system
     const size_t bytes = csize(s) * s->field_elems * (size_t)s->nslots();
     void *saved = nullptr;

@@ -212,15 +212,19 @@ struct P2Args {
     float2 *state;              // tiled [tile][ny][4]
     float2 *P;                  // x-transformed product, column-major [kx][ny]
     float2 *T1;                 // conjugated y-inverse of the kept columns, column-major [kx][ny]
+    float2 *T1a;                // KPZ (mode 1): the same of i q_y times the field
     float2 *xi;                 // unit-amplitude noise of the next step, tiled: read at the start, written at the end
     const float2 *tw;
     long long *d_step;
     int *d_status;
     GridSync *gs;
     int nsteps;
+    int prologue;               // P does not hold the product of the state yet: compute it first
 };
-// n steps in one cooperative launch of nblocks CTAs (E: FFT pass radix, 8 or 16)
-cudaError_t launch_p2(const P2Args &a, int n, int E, int nblocks, cudaStream_t st);
+// n steps in one cooperative launch of nblocks CTAs (E: FFT pass radix, 8 or 16;
+// mode 0: a power of the field, 1: the KPZ gradient square)
+cudaError_t launch_p2(const P2Args &a, int n, int E, int nblocks, int mode, cudaStream_t st);
+cudaError_t launch_p2_kpz(const P2Args &a, int n, int E, int nblocks, cudaStream_t st);
 template <typename T> cudaError_t launch_init_uniform(T *real, long long nsites, double lo, double hi,
                                                       uint64_t seed, int field_id, cudaStream_t st);
 // product terms with several operators: Q = (first ? 0 : Q) + M(q) Pt over one

@@ -2,7 +2,9 @@
 // (arXiv:2405.02410, section "What cuPSS calculates", Eq. timeupdate).
 //
 // k2p_step runs n steps of a square FP32 2D field (sides 256, 512, 1024) in
-// one cooperative launch of at most one CTA per SM.  Each CTA owns a fixed
+// one cooperative launch of at most one CTA per SM.  Two kinds of field:
+// MODE 0, an explicit term M(q) F[(F^-1 m phi)^p] (Models A and B), and
+// MODE 1, the KPZ term M(q) F[|grad(F^-1 m h)|^2] (section "Writing models").  Each CTA owns a fixed
 // set of half-spectrum columns (pairs kx = 2u, 2u + 1: one Philox call draws
 // the noise of both) and a fixed block of rows.  The state phi_q of its
 // columns stays in shared memory for the whole launch; only the two work
@@ -16,6 +18,16 @@
 //   row phase: T1 rows of the CTA's row pairs -> C2R along x (two rows as
 //       one complex transform) -> power p -> R2C -> P (column-major)
 //   grid barrier B
+//
+// MODE 1 (KPZ): the column phase also transforms i q_y m h back along y (a
+// second inverse, array T1a); in the row phase one complex C2R of the two
+// rows' i q_x m h and one of their i q_y m h give (d_x h, d_y h) of both rows,
+// whose squares, added, are the two rows' products, packed for one R2C.  Three
+// transforms per row pair and three per kept column instead of two.
+//
+// A launch whose product is not in P yet (a fresh state, a new parameter of
+// the operators) starts with a prologue: the inverse transforms of the state
+// and the row phase, without an update.
 //
 // The barriers replace the two kernel boundaries of the two-kernel path.
 // The transform warps of a CTA meet at named barrier 15; beside them, noise
@@ -101,26 +113,23 @@ __device__ __forceinline__ bool grid_wait(GridSync *gs, unsigned long long targe
 }
 
 // CTAs, threads and shared memory of the persistent step.  The transform
-// warps are NG = 4 FFT groups of TPF = N / E threads and NHW helper warps that
-// join the element-wise loops; beside them run NNW noise warps.  A CTA owns at
-// most NG / 2 column pairs and NG row pairs.  Shared memory: mbarriers | roots
-// of unity | state [NG][N] | update factors (m, g) [NG][N] | noise, two
-// buffers [2][NG][N] | the groups' buffer pairs.
-template <int N, int E, int NNW, int NHW> struct P2Shape {
+// warps are NG = 4 FFT groups of TPF = N / E threads; beside them run NNW
+// noise warps.  A CTA owns at most NG / 2 column pairs and NG row pairs.
+// Shared memory: mbarriers | roots of unity | state [NG][N] | update factors
+// (m, g) [NG][N] (MODE 0) or a third buffer of N points per group (MODE 1) |
+// noise, two buffers [2][NG][N] | the groups' buffer pairs.
+template <int N, int E, int NNW> struct P2Shape {
     using S = GShape<N, E>;
     static constexpr int NG = 4;
-    static constexpr int NF = NG * S::TPF;             // FFT-group threads
-    static constexpr int NMAIN = NF + 32 * NHW;        // transform warps
+    static constexpr int NMAIN = NG * S::TPF;         // transform threads
     static constexpr int THREADS = NMAIN + 32 * NNW;
-    static constexpr size_t BAR = 0;                                    // full[2], empty[2]
+    static constexpr size_t BAR = 0;                   // full[2], empty[2]
     static constexpr size_t TW = 128;
     static constexpr size_t ST = TW + sizeof(float2) * N;
     static constexpr size_t MG = ST + sizeof(float2) * NG * N;
     static constexpr size_t NZ = MG + sizeof(float2) * NG * N;
     static constexpr size_t WB = NZ + 2 * sizeof(float2) * NG * N;
     static constexpr size_t BYTES = WB + sizeof(float2) * NG * S::WS;
-    static constexpr int POFS = S::OUT * S::BUF;
-    static constexpr int UOFS = S::BUF - POFS;
 };
 
 // the CTA's share of `total` units when they are cut into `nb` contiguous blocks
@@ -149,18 +158,33 @@ __device__ __forceinline__ bool mbar_wait_abortable(uint64_t *bar, uint32_t pari
     return false;
 }
 
-template <int N, int E, int NNW, int NHW>
-__global__ void __launch_bounds__(P2Shape<N, E, NNW, NHW>::THREADS, 1) k2p_step(const P2Args a) {
+// The noise hand-over.  Draw n (the noise of step step0 + n) goes to buffer
+// n & 1; draws start at n = first (0 after a prologue, else 1: step 0's
+// noise comes from the noise array).  The j-th draw into buffer b completes
+// phase j of full[b]; step n's update releases its buffer (empty[b]), and
+// draw n >= 2 waits for release number (n - 2 - b) / 2 of its buffer.
+__device__ __forceinline__ uint32_t full_parity(int n, int first) {
+    const int b = n & 1;
+    return (uint32_t)(((n - (b ? 1 : (first ? 2 : 0))) >> 1) & 1);
+}
+__device__ __forceinline__ uint32_t empty_parity(int n) { return (uint32_t)(((n - 2 - (n & 1)) >> 1) & 1); }
+
+// derivative factor i q of a mode (q = 0 at a Nyquist index, reading R14)
+__device__ __forceinline__ float dq(int k, int n, float g) { return 2 * k == n ? 0.f : fmul(float(signed_k(k, n)), g); }
+
+template <int N, int E, int NNW, int MODE>
+__global__ void __launch_bounds__(P2Shape<N, E, NNW>::THREADS, 1) k2p_step(const P2Args a) {
     using C = float2;
     using S = GShape<N, E>;
-    using L = P2Shape<N, E, NNW, NHW>;
-    constexpr int TPF = S::TPF, NG = L::NG, NF = L::NF, NMAIN = L::NMAIN, H = N / 2 + 1, UC = (H + 1) / 2;
+    using L = P2Shape<N, E, NNW>;
+    constexpr int TPF = S::TPF, NG = L::NG, NMAIN = L::NMAIN, H = N / 2 + 1, UC = (H + 1) / 2;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw + L::BAR);     // full[0], full[1]
     uint64_t *empty = full + 2;                                            // empty[0], empty[1]
     C *TW = reinterpret_cast<C *>(smem_raw + L::TW);
     C *ST = reinterpret_cast<C *>(smem_raw + L::ST);   // state of column slot c: ST[c N + ky]
-    float2 *MG = reinterpret_cast<float2 *>(smem_raw + L::MG);   // (m, g) of the update per mode
+    float2 *MG = reinterpret_cast<float2 *>(smem_raw + L::MG);   // MODE 0: (m, g) of the update per mode
+    C *X3 = reinterpret_cast<C *>(smem_raw + L::MG);   // MODE 1: group g's third buffer X3[g N + x]
     C *NZ = reinterpret_cast<C *>(smem_raw + L::NZ);   // noise buffer b of column slot c: NZ[(b NG + c) N + ky]
     C *WB = reinterpret_cast<C *>(smem_raw + L::WB);
     __shared__ FieldP<float> sfp;
@@ -170,7 +194,7 @@ __global__ void __launch_bounds__(P2Shape<N, E, NNW, NHW>::THREADS, 1) k2p_step(
     const FieldP<float> &fp = sfp;
     const int t = threadIdx.x;
     const unsigned nb = gridDim.x;
-    (void)NF;
+    const int first = a.prologue ? 0 : 1;   // the first noise draw of the launch
     // this CTA's column pairs [u0, u1) (column slot c = 2 (u - u0) + j holds kx = 2u + j)
     // and row pairs [p0, p1)
     int u0, u1, p0, p1;
@@ -198,18 +222,14 @@ __global__ void __launch_bounds__(P2Shape<N, E, NNW, NHW>::THREADS, 1) k2p_step(
 
     if (t >= NMAIN) {
         // ================= noise warps =================
-        // unit-amplitude noise (times |q|^noise_pow) of steps step0 .. step0 + nsteps,
+        // unit-amplitude noise (times |q|^noise_pow) of steps step0 + first .. step0 + nsteps,
         // one Philox call per (column pair, ky), as noise_range draws it
         const int tn = t - NMAIN;
         const PhiloxKey key = philox_key(fp.seed_lo, fp.seed_hi);
         const int npairs = (u1 - u0) * N;
-        // draw n (the noise of step step0 + n) goes to buffer n & 1; the first
-        // step's (n = 0) comes from the noise array.  Before draw n >= 2 the
-        // buffer's last reader, step n - 2, must have released it: release
-        // number (n - 2 - b) / 2 of that buffer.
-        for (int n = 1; n <= a.nsteps; ++n) {
+        for (int n = first; n <= a.nsteps; ++n) {
             const int b = n & 1;
-            if (n >= 2 && !mbar_wait_abortable(empty + b, ((n - 2 - b) >> 1) & 1, &s_abort)) {
+            if (n >= 2 && !mbar_wait_abortable(empty + b, empty_parity(n), &s_abort)) {
                 if (!s_abort && a.d_status) atomicOr(a.d_status, kStatusTimeout);
                 s_abort = 1;
                 return;
@@ -236,31 +256,34 @@ __global__ void __launch_bounds__(P2Shape<N, E, NNW, NHW>::THREADS, 1) k2p_step(
     }
 
     // ================= transform warps =================
-    const int g = t < NF ? t / TPF : NG, gl = t - g * TPF;   // FFT group (NG: a helper thread)
+    const int g = t / TPF, gl = t - g * TPF;   // FFT group and its thread
     for (int i = t; i < N; i += NMAIN) TW[i] = a.tw[twiddle_offset(N, E) + i];
     const int kmx = fp.kmax[0], kmy = fp.kmax[1];
     const float scale = sp.inv_nsites;
     const bool has_product = fp.power > 0;
-    {
-        float dtO[kPolyTerms], dtM[kPolyTerms];
+    float dtO[kPolyTerms], dtM[kPolyTerms];
 #pragma unroll
-        for (int i = 0; i < kPolyTerms; ++i) {
-            dtO[i] = sp.dt * fp.O[i];
-            dtM[i] = sp.dt * fp.M[i];
-        }
-        // the state and the first step's noise of each column pair: 16 bytes per
-        // (pair, ky) of the tiled arrays (the pair's two columns are neighbours)
-        for (int i = t; i < (u1 - u0) * N; i += NMAIN) {
-            const int uu = i >> ilog2(N), ky = i & (N - 1), kx0 = 2 * (u0 + uu);
-            const size_t o = ((size_t)(kx0 >> 2) * N + ky) * 4 + (kx0 & 3);
-            float4 v = __ldcg(reinterpret_cast<const float4 *>(a.state + o));
-            float4 x = noisy ? __ldcg(reinterpret_cast<const float4 *>(a.xi + o)) : make_float4(0.f, 0.f, 0.f, 0.f);
-            if (kx0 + 1 >= sp.hx) { v.z = 0.f; v.w = 0.f; x.z = 0.f; x.w = 0.f; }   // past Nx/2
-            ST[(2 * uu) * N + ky] = mk<float>(v.x, v.y);
-            ST[(2 * uu + 1) * N + ky] = mk<float>(v.z, v.w);
+    for (int i = 0; i < kPolyTerms; ++i) {
+        dtO[i] = sp.dt * fp.O[i];
+        dtM[i] = sp.dt * fp.M[i];
+    }
+    // the state (and, without a prologue, the first step's noise) of each column
+    // pair: 16 bytes per (pair, ky) of the tiled arrays (the two columns are neighbours)
+    for (int i = t; i < (u1 - u0) * N; i += NMAIN) {
+        const int uu = i >> ilog2(N), ky = i & (N - 1), kx0 = 2 * (u0 + uu);
+        const size_t o = ((size_t)(kx0 >> 2) * N + ky) * 4 + (kx0 & 3);
+        float4 v = __ldcg(reinterpret_cast<const float4 *>(a.state + o));
+        if (kx0 + 1 >= sp.hx) { v.z = 0.f; v.w = 0.f; }   // past Nx/2
+        ST[(2 * uu) * N + ky] = mk<float>(v.x, v.y);
+        ST[(2 * uu + 1) * N + ky] = mk<float>(v.z, v.w);
+        if (first == 1 && noisy) {
+            float4 x = __ldcg(reinterpret_cast<const float4 *>(a.xi + o));
+            if (kx0 + 1 >= sp.hx) { x.z = 0.f; x.w = 0.f; }
             NZ[(2 * uu) * N + ky] = mk<float>(x.x, x.y);
             NZ[(2 * uu + 1) * N + ky] = mk<float>(x.z, x.w);
         }
+    }
+    if constexpr (MODE == 0) {
         for (int c = 0; c < ncs; ++c) {
             const float qx = fmul(float(kx_of(c)), sp.gx);
             for (int ky = t; ky < N; ky += NMAIN) {
@@ -272,7 +295,7 @@ __global__ void __launch_bounds__(P2Shape<N, E, NNW, NHW>::THREADS, 1) k2p_step(
     }
     main_sync<NMAIN>();
     const float sigma0 = fp.sigma0;
-    C *gb = WB + (g < NG ? g : 0) * S::WS;   // this thread's group buffers
+    C *gb = WB + g * S::WS;   // this thread's group buffers
     bool alive = true;
     // every transform thread waits for phase `parity` of the noise buffer's
     // "full" mbarrier; the warps agree on the outcome
@@ -287,63 +310,82 @@ __global__ void __launch_bounds__(P2Shape<N, E, NNW, NHW>::THREADS, 1) k2p_step(
     unsigned long long target = 0;   // the arrival count that ends the next grid barrier
 
 #pragma unroll 1
-    for (int n = 0; n < a.nsteps && alive; ++n) {
+    for (int n = a.prologue ? -1 : 0; n < a.nsteps && alive; ++n) {
+        const bool pro = n < 0;   // the prologue: inverse transforms and row phase of the state, no update
+        const int b = n & 1;
         // ================= column phase =================
         // Each FFT group runs its column on its own: the x-transformed product
         // (16-byte asynchronous copies into b1), the forward y-FFT whose last
         // pass applies the update (Eq. timeupdate) mode by mode and writes the
         // de-aliased, scaled, conjugated inverse input into the free buffer, the
         // Hermitian part on the kx = 0, Nx/2 columns, and the y-inverse whose
-        // last pass stores T1 (column-major) straight to global memory.
-        const int b = n & 1;
+        // last pass stores T1 (column-major) straight to global memory (MODE 1:
+        // then the y-inverse of i q_y times the same input, T1a).
         if (g < ncs) {
             const int kx = kx_of(g);
             C *b0 = gb, *b1 = gb + S::BUF;
             C *U = SinkShape<N, E>::LAST_READS_B1 ? b0 : b1;   // the buffer the last pass does not read
-            for (int p = gl; p < N / 2; p += TPF) {
-                float4 *dst = reinterpret_cast<float4 *>(b1 + 2 * p);
-                if (kx < sp.hx) {
-                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)),
-                                 "l"(reinterpret_cast<const float4 *>(a.P + (size_t)kx * N) + p)
-                                 : "memory");
-                } else {
-                    *dst = make_float4(0.f, 0.f, 0.f, 0.f);
-                }
-            }
-            asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
-            // the noise of this step (every thread of the group waits; bounded): draw
-            // number (n - 2 + b) / 2 into buffer b; step 0's came with the set-up
-            if (n > 0 && !mbar_wait_abortable(full + b, ((n - 2 + b) >> 1) & 1, &s_abort)) {
-                if (!s_abort && a.d_status) atomicOr(a.d_status, kStatusTimeout);
-                s_abort = 1;
-            }
-            group_sync<TPF>(1 + g);
-            const C *nzc = NZ + ((size_t)b * NG + g) * N;
             C *STc = ST + g * N;
-            const float2 *MGc = MG + g * N;
             const bool kxk = kx <= kmx, live = kx < sp.hx;
-            fft_fwd_group_sink<N, E>(b0, b1, gl, 1 + g, TW, [&](int ky, C pq) {
-                const C x = noisy ? cscale<float>(nzc[ky], sigma0) : mk<float>(0.f, 0.f);
-                const float2 mg = MGc[ky];
-                C v = update_pre<float>(STc[ky], pq, x, mg.x, mg.y, has_product);
-                if (!live) v = mk<float>(0.f, 0.f);
-                STc[ky] = v;
-                const float sc = (kxk && abs(signed_k(ky, N)) <= kmy) ? scale : 0.f;
-                U[ky] = mk<float>(v.x * sc, -v.y * sc);
-            });
-            group_sync<TPF>(1 + g);
-            if (kx == 0 || kx == N / 2) {
-                // Hermitian part (the field is real): phi(kx, ky) <- (phi(kx, ky) + conj phi(kx, -ky)) / 2
-                for (int pos = gl; pos < N / 2 + 1; pos += TPF) {
-                    const int ppos = (N - pos) & (N - 1);
-                    const C v0 = STc[pos], v1 = STc[ppos];
-                    const C h = mk<float>(0.5f * (v0.x + v1.x), 0.5f * (v0.y - v1.y));
-                    STc[pos] = h;
-                    STc[ppos] = mk<float>(h.x, -h.y);
-                    const float s0 = (kxk && abs(signed_k(pos, N)) <= kmy) ? scale : 0.f;
-                    const float s1 = (kxk && abs(signed_k(ppos, N)) <= kmy) ? scale : 0.f;
-                    U[pos] = mk<float>(h.x * s0, -h.y * s0);
-                    U[ppos] = mk<float>(h.x * s1, h.y * s1);
+            if (!pro) {
+                for (int p = gl; p < N / 2; p += TPF) {
+                    float4 *dst = reinterpret_cast<float4 *>(b1 + 2 * p);
+                    if (live) {
+                        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)),
+                                     "l"(reinterpret_cast<const float4 *>(a.P + (size_t)kx * N) + p)
+                                     : "memory");
+                    } else {
+                        *dst = make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
+                }
+                asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+                // the noise of this step (every thread of the group waits; bounded)
+                if (!(n == 0 && first == 1) && !mbar_wait_abortable(full + b, full_parity(n, first), &s_abort)) {
+                    if (!s_abort && a.d_status) atomicOr(a.d_status, kStatusTimeout);
+                    s_abort = 1;
+                }
+                group_sync<TPF>(1 + g);
+                const C *nzc = NZ + ((size_t)b * NG + g) * N;
+                const float2 *MGc = MG + g * N;
+                const float qx = fmul(float(kx), sp.gx);
+                fft_fwd_group_sink<N, E>(b0, b1, gl, 1 + g, TW, [&](int ky, C pq) {
+                    const C x = noisy ? cscale<float>(nzc[ky], sigma0) : mk<float>(0.f, 0.f);
+                    float m, gg;
+                    if constexpr (MODE == 0) {
+                        const float2 mg = MGc[ky];
+                        m = mg.x;
+                        gg = mg.y;
+                    } else {
+                        update_factors<float>(q2sum(qx, fmul(float(signed_k(ky, N)), sp.gy)), dtO, dtM, m, gg);
+                    }
+                    C v = update_pre<float>(STc[ky], pq, x, m, gg, has_product);
+                    if (!live) v = mk<float>(0.f, 0.f);
+                    STc[ky] = v;
+                    const float sc = (kxk && abs(signed_k(ky, N)) <= kmy) ? scale : 0.f;
+                    U[ky] = mk<float>(v.x * sc, -v.y * sc);
+                });
+                group_sync<TPF>(1 + g);
+                if (kx == 0 || kx == N / 2) {
+                    // Hermitian part (the field is real): phi(kx, ky) <- (phi(kx, ky) + conj phi(kx, -ky)) / 2
+                    for (int pos = gl; pos < N / 2 + 1; pos += TPF) {
+                        const int ppos = (N - pos) & (N - 1);
+                        const C v0 = STc[pos], v1 = STc[ppos];
+                        const C h = mk<float>(0.5f * (v0.x + v1.x), 0.5f * (v0.y - v1.y));
+                        STc[pos] = h;
+                        STc[ppos] = mk<float>(h.x, -h.y);
+                        const float s0 = (kxk && abs(signed_k(pos, N)) <= kmy) ? scale : 0.f;
+                        const float s1 = (kxk && abs(signed_k(ppos, N)) <= kmy) ? scale : 0.f;
+                        U[pos] = mk<float>(h.x * s0, -h.y * s0);
+                        U[ppos] = mk<float>(h.x * s1, h.y * s1);
+                    }
+                    group_sync<TPF>(1 + g);
+                }
+            } else {
+                // the inverse input from the state as it is
+                for (int ky = gl; ky < N; ky += TPF) {
+                    const C v = STc[ky];
+                    const float sc = (kxk && abs(signed_k(ky, N)) <= kmy) ? scale : 0.f;
+                    U[ky] = mk<float>(v.x * sc, -v.y * sc);
                 }
                 group_sync<TPF>(1 + g);
             }
@@ -351,6 +393,19 @@ __global__ void __launch_bounds__(P2Shape<N, E, NNW, NHW>::THREADS, 1) k2p_step(
                 // y-inverse (T1 = F(conj X)): input in U, the other buffer for the passes
                 C *__restrict__ dst = a.T1 + (size_t)kx * N;
                 fft_fwd_group_sink<N, E>(U == b0 ? b1 : b0, U, gl, 1 + g, TW, [&](int q, C v) { dst[q] = v; });
+                if constexpr (MODE == 1) {
+                    // the y-inverse of i q_y X (T1a): its input from the state, into b1
+                    group_sync<TPF>(1 + g);
+                    for (int ky = gl; ky < N; ky += TPF) {
+                        const C v = STc[ky];
+                        const float sc = (kxk && abs(signed_k(ky, N)) <= kmy) ? scale : 0.f;
+                        const float qd = dq(ky, N, sp.gy);
+                        b1[ky] = mk<float>(-qd * v.y * sc, -qd * v.x * sc);   // conj(sc i q_y v)
+                    }
+                    group_sync<TPF>(1 + g);
+                    C *__restrict__ dsta = a.T1a + (size_t)kx * N;
+                    fft_fwd_group_sink<N, E>(b0, b1, gl, 1 + g, TW, [&](int q, C v) { dsta[q] = v; });
+                }
             }
         }
         // ---- grid barrier A (its CTA barrier also ends the column phase's reads of noise buffer b)
@@ -362,39 +417,65 @@ __global__ void __launch_bounds__(P2Shape<N, E, NNW, NHW>::THREADS, 1) k2p_step(
         } else {
             grid_arrive<NMAIN>(a.gs);
         }
-        if (t == 0) mbar_arrive(empty + b);   // noise buffer b is read: the noise warps may refill it
+        if (!pro && t == 0) mbar_arrive(empty + b);   // noise buffer b is read: the noise warps may refill it
         alive = grid_wait<NMAIN>(a.gs, target, a.d_status, sp.wait_limit, &s_abort);
         if (!alive) break;
         // ================= row phase =================
-        // Each FFT group runs one row pair on its own: Y = conj(Z) staged from the
-        // conjugated y-inverse (as k2_row), C2R with the power on its last pass,
-        // R2C, and the split into the two rows' half spectra, stored column-major.
+        // Each FFT group runs one row pair on its own (rows r0, r0 + 1), from the
+        // conjugated y-inverse(s), and stores the two rows' half spectra of the
+        // product column-major.
         if (g < npr) {
-            const int r0 = 2 * (p0 + g);   // the pair's first row
+            const int r0 = 2 * (p0 + g);
             const int kc = fp.kx_cols;
             C *b0 = gb, *b1 = gb + S::BUF;
             constexpr int PER = (H + TPF - 1) / TPF;   // columns per thread
-            float4 v[PER];
+            // stage Y = conj(Z) of the rows' spectra (as k2_row) into b1; deriv: times -i q_x
+            // first (the conjugate of i q_x)
+            auto stage_from = [&](const C *src, bool deriv) {
+                float4 v[PER];
 #pragma unroll
-            for (int q = 0; q < PER; ++q) {
-                const int k = gl + q * TPF;
-                v[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (k < kc) v[q] = __ldcg(reinterpret_cast<const float4 *>(a.T1 + (size_t)k * N + r0));
-            }
-#pragma unroll
-            for (int q = 0; q < PER; ++q) {
-                const int k = gl + q * TPF;
-                if (k < H) {
-                    float ar = v[q].x, ai = v[q].y, br = v[q].z, bi = v[q].w;
-                    if (k == 0 || k == N / 2) { ai = 0.f; bi = 0.f; }   // the half spectra of real rows
-                    const C lo = mk<float>(ar - bi, -ai - br), hi = mk<float>(ar + bi, ai - br);
-                    b1[k] = hi;
-                    if (k > 0 && k < N / 2) b1[N - k] = lo;
+                for (int q = 0; q < PER; ++q) {
+                    const int k = gl + q * TPF;
+                    v[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (k < kc) v[q] = __ldcg(reinterpret_cast<const float4 *>(src + (size_t)k * N + r0));
                 }
+#pragma unroll
+                for (int q = 0; q < PER; ++q) {
+                    const int k = gl + q * TPF;
+                    if (k < H) {
+                        float ar = v[q].x, ai = v[q].y, br = v[q].z, bi = v[q].w;
+                        if (deriv) {
+                            const float qd = dq(k, N, sp.gx);
+                            const float t0 = qd * ai, t1 = -qd * ar, t2 = qd * bi, t3 = -qd * br;
+                            ar = t0; ai = t1; br = t2; bi = t3;
+                        }
+                        if (k == 0 || k == N / 2) { ai = 0.f; bi = 0.f; }   // the half spectra of real rows
+                        const C lo = mk<float>(ar - bi, -ai - br), hi = mk<float>(ar + bi, ai - br);
+                        b1[k] = hi;
+                        if (k > 0 && k < N / 2) b1[N - k] = lo;
+                    }
+                }
+                group_sync<TPF>(1 + g);
+            };
+            C *o2;
+            if constexpr (MODE == 0) {
+                stage_from(a.T1, false);
+                C *o = fft_fwd_group<N, E, 1>(b1, b0, b1, gl, 1 + g, TW, fp.power);
+                o2 = fft_fwd_group<N, E, 1>(o, o == b0 ? b1 : b0, o, gl, 1 + g, TW, 0);
+            } else {
+                // (d_x h) of both rows as one complex C2R; squares of the two real parts to X3
+                C *X = X3 + g * N;
+                stage_from(a.T1, true);
+                fft_fwd_group_sink<N, E>(b0, b1, gl, 1 + g, TW, [&](int q, C v) { X[q] = mk<float>(v.x * v.x, v.y * v.y); });
+                group_sync<TPF>(1 + g);
+                // (d_y h) of both rows; the sum of squares packs the two rows' products
+                stage_from(a.T1a, false);
+                C *F = SinkShape<N, E>::LAST_READS_B1 ? b0 : b1;
+                fft_fwd_group_sink<N, E>(b0, b1, gl, 1 + g, TW,
+                                         [&](int q, C v) { F[q] = mk<float>(fadd(X[q].x, v.x * v.x), fadd(X[q].y, v.y * v.y)); });
+                group_sync<TPF>(1 + g);
+                o2 = fft_fwd_group<N, E, 1>(F, F == b0 ? b1 : b0, F, gl, 1 + g, TW, 0);
             }
-            group_sync<TPF>(1 + g);
-            C *o = fft_fwd_group<N, E, 1>(b1, b0, b1, gl, 1 + g, TW, fp.power);
-            C *o2 = fft_fwd_group<N, E, 1>(o, o == b0 ? b1 : b0, o, gl, 1 + g, TW, 0);
             C *__restrict__ out = a.P + r0;
 #pragma unroll 4
             for (int k = gl; k < H; k += TPF) {
@@ -417,7 +498,7 @@ __global__ void __launch_bounds__(P2Shape<N, E, NNW, NHW>::THREADS, 1) k2p_step(
     // ---- the state, and the next step's unit noise (as the two-kernel path keeps it), back to the
     // tiled arrays; a non-finite mode of the state is reported (it spreads to every mode in a step)
     const int bl = a.nsteps & 1;
-    if (!wait_full(bl, ((a.nsteps - 2 + bl) >> 1) & 1)) return;
+    if (!wait_full(bl, full_parity(a.nsteps, first))) return;
     const C *nz = NZ + (size_t)bl * NG * N;
     bool bad = false;
     for (int i = t; i < (u1 - u0) * N; i += NMAIN) {

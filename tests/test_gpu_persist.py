@@ -155,3 +155,71 @@ def test_launches_per_run():
     n0 = s.launch_count
     s.step(1000)
     assert s.launch_count - n0 == 1
+
+
+# ---------------------------------------------------------------------------
+# KPZ (the gradient-square term) on the persistent step
+# ---------------------------------------------------------------------------
+KPZ = dict(dt=0.02, sigma=1.0, lam=0.6, D=0.02)
+
+
+def _kpz(shape, knobs=None, order=2, seed=41):
+    s = pss().kpz(shape, seed=seed, precision="f32", dealias_order=order, **KPZ)
+    for k, v in (knobs or {}).items():
+        s.set_tuning(k, v)
+    s.init_uniform(0, -0.5, 0.5)
+    return s
+
+
+def _oracle_kpz(shape, steps, order=2, seed=41):
+    m = O.kpz(shape, seed=seed, dealias_order=order, **KPZ)
+    return O.half(O.run(m, O.to_spectrum(m, O.init_uniform(m, -0.5, 0.5)), 0, steps))
+
+
+@pytest.mark.parametrize("shape,order,steps", [((256, 256), 2, 40), ((512, 512), 2, 20), ((256, 256), 0, 30),
+                                               ((256, 256), 3, 30), ((1024, 1024), 2, 8)])
+def test_kpz_matches_oracle(shape, order, steps):
+    s = _kpz(shape, order=order)
+    assert s.step_path == "persist2d"
+    s.step(steps)
+    check_spectrum(s.get_spectrum(0), _oracle_kpz(shape, steps, order), 1e-4, order=order)
+
+
+@pytest.mark.parametrize("radix", [8, 16])
+def test_kpz_matches_the_generic_kernels_and_takes_one_launch(radix):
+    shape = (512, 512)
+    p = _kpz(shape, knobs=dict(col2_radix=radix, row2_radix=radix))
+    q = _kpz(shape, knobs=dict(persist=0))
+    assert q.step_path == "generic"
+    p.step(3)
+    q.step(3)
+    n0 = p.launch_count
+    p.step(30)
+    assert p.launch_count - n0 == 1
+    q.step(30)
+    check_spectrum(p.get_spectrum(0), q.get_spectrum(0), 1e-5)
+    # switching between the paths mid-run recomputes the product in each layout
+    p.set_tuning("persist", 0)
+    p.step(5)
+    p.set_tuning("persist", 1)
+    p.step(5)
+    q.step(10)
+    check_spectrum(p.get_spectrum(0), q.get_spectrum(0), 1e-5)
+
+
+def test_kpz_parameter_change_and_resume():
+    shape = (256, 256)
+    s = _kpz(shape)
+    s.step(10)
+    blob = s.save_state()
+    s.set_param(1, 0.3)        # lambda (parameters: sigma, lambda, D)
+    s.step(10)
+    m1 = O.kpz(shape, seed=41, **KPZ)
+    phi = O.run(m1, O.to_spectrum(m1, O.init_uniform(m1, -0.5, 0.5)), 0, 10)
+    m2 = O.kpz(shape, seed=41, **dict(KPZ, lam=0.3))
+    check_spectrum(s.get_spectrum(0), O.half(O.run(m2, phi, 10, 10)), 1e-4)
+    r = _kpz(shape, seed=99)
+    r.load_state(blob)
+    r.set_param(1, 0.3)
+    r.step(10)
+    assert r.get_spectrum(0).tobytes() == s.get_spectrum(0).tobytes()
