@@ -133,6 +133,7 @@ struct pss_system {
     int tune_fast3d = 1;                     // FP32 3D x pass with one FFT group per row pair (0 = generic k_row)
     int tune_test_timeout = 0;               // check of the bounded waits: one CTA's wait runs out (tests)
     int tune_persist = 1;                    // square FP32 2D systems: a run of steps as one persistent launch
+    int tune_adj_col2 = 1;                   // FP32 2D adjoint: column parts on FFT groups (0: generic kernel)
     int tune_persist_blocks = 0;             // its CTAs (0: every SM, at most one CTA per column pair or row pair)
     int coop = 0;                            // the device takes cooperative launches
     // captured persistent launches by run length (one kernel node each); p2_capture < 0: capture
@@ -568,6 +569,19 @@ template <typename T> struct Seq {
         a.n_tiles = mode == COL_INV_MASK ? max_kept_tiles(s) : s->ntiles;
         const int gx = (a.n_tiles + a.tiles_per_cta - 1) / a.tiles_per_cta;
         const int gy = s->dim == 3 ? s->ny / 2 + 1 : 1;
+        if constexpr (std::is_same<T, float>::value) {
+            // the adjoint's column part of the FP32 2D path on FFT groups: one
+            // column pair per CTA
+            if ((mode == COL_ADJ_A || mode == COL_ADJ_B || mode == COL_ADJ_BA) && fast2d(s) && s->tune_adj_col2) {
+                a.E = col2_radix(s) == 16 ? 16 : 8;
+                if (timer) timer->begin(0, st);
+                cudaError_t e = launch_col2_adj(a, nslots, st);
+                if (timer) timer->begin(0, st);
+                s->launches++;
+                if (e != cudaSuccess) return cuda_fail(s, e, "k2_col_adj launch");
+                return PSS_OK;
+            }
+        }
         if (timer) timer->begin(0, st);
         cudaError_t e = launch_col<T>(a, nslots, gx, gy, st);
         if (timer) timer->begin(0, st);
@@ -1506,10 +1520,28 @@ template <typename T> int record_adjoint_segment(pss_system *s, cudaStream_t str
                                             stream);
     s->launches++;
     if (e != cudaSuccess) return cuda_fail(s, e, "segment start kernel");
-    int rc = q.recompute_prologue(st(0), prod(0), real(0));
-    if (rc) return rc;
-    for (int64_t i = 0; i < len; ++i)
-        if ((rc = q.recompute_step(st(i), st(i + 1), prod(i), prod(i + 1), real(i + 1)))) return rc;
+    int rc;
+    if (persist2d(s) && len >= 1) {
+        // the segment's forward steps as one persistent launch that writes every
+        // step's state, product and de-aliased real field (segment mode)
+        P2Args a = p2_args(s, (int)len);
+        a.state = (float2 *)st(0);
+        a.P = nullptr;
+        a.xi = nullptr;
+        a.prologue = 1;
+        a.seg_state = (float2 *)st(0);
+        a.seg_prod = (float2 *)prod(0);
+        a.seg_real = (float *)real(0);
+        a.seg_cstride = s->field_elems;
+        a.seg_rstride = (size_t)s->nsites;
+        e = launch_p2(a, s->nx, p2_radix(s), p2_blocks(s), 0, stream);
+        s->launches++;
+        if (e != cudaSuccess) return cuda_fail(s, e, "k2p_step launch (recomputed segment)");
+    } else {
+        if ((rc = q.recompute_prologue(st(0), prod(0), real(0)))) return rc;
+        for (int64_t i = 0; i < len; ++i)
+            if ((rc = q.recompute_step(st(i), st(i + 1), prod(i), prod(i + 1), real(i + 1)))) return rc;
+    }
     if (len < 1 || !q.fused_adjoint()) {
         for (int64_t i = len - 1; i >= 0; --i)
             if ((rc = q.adjoint_step(st(i + 1), prod(i), real(i), i))) return rc;
@@ -2058,6 +2090,7 @@ int pss_set_tuning(pss_system *s, const char *key, int value) {
     else if (k == "real_state") s->tune_real_state = value ? 1 : 0;
     else if (k == "test_timeout") s->tune_test_timeout = value ? 1 : 0;
     else if (k == "persist") s->tune_persist = value ? 1 : 0;
+    else if (k == "adj_col2") s->tune_adj_col2 = value ? 1 : 0;
     else if (k == "persist_blocks") {
         if (value > 1024) return fail(s, PSS_EINVAL, "persist_blocks is at most 1024 (0 = automatic)");
         s->tune_persist_blocks = value;

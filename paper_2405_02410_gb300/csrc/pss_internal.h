@@ -196,6 +196,9 @@ template <typename T> inline cudaError_t launch_mid(const MidArgs<T> &a, int nsl
 // generic kernels (the x pass of the 3D step).
 cudaError_t launch_col2(const ColArgs<float> &a, int nslots, int ntiles, cudaStream_t st);
 cudaError_t launch_row2(const RowArgs<float> &a, int nslots, cudaStream_t st, bool tiled);
+// the adjoint's column part (COL_ADJ_A / _B / _BA) of an FP32 2D system with
+// 256..1024-point columns on FFT groups, one column pair per CTA
+cudaError_t launch_col2_adj(const ColArgs<float> &a, int nslots, cudaStream_t st);
 // The persistent FP32 2D step (k2p_step: square sides of 256, 512 or 1024
 // points, one field, one instance): grid-barrier words of one system
 // (16 bytes, zero-initialised) and the launch arguments.  Barrier i of a
@@ -220,6 +223,15 @@ struct P2Args {
     GridSync *gs;
     int nsteps;
     int prologue;               // P does not hold the product of the state yet: compute it first
+    // segment mode (the adjoint's recomputed segments; seg_state != nullptr): the
+    // state of step 0 is read from seg_state, and the states of steps 1..nsteps
+    // (tiled), the products of steps 0..nsteps (column-major) and their
+    // de-aliased real fields ([ny][nx]) are written at seg_state + i seg_cstride,
+    // seg_prod + i seg_cstride, seg_real + i seg_rstride; P, xi and the state
+    // write-back at the end are not used
+    float2 *seg_state, *seg_prod;
+    float *seg_real;
+    size_t seg_cstride, seg_rstride;
 };
 // n steps in one cooperative launch of nblocks CTAs (E: FFT pass radix, 8 or 16;
 // mode 0: a power of the field, 1: the KPZ gradient square)

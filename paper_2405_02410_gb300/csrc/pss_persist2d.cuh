@@ -195,6 +195,7 @@ __global__ void __launch_bounds__(P2Shape<N, E, NNW>::THREADS, 1) k2p_step(const
     const int t = threadIdx.x;
     const unsigned nb = gridDim.x;
     const int first = a.prologue ? 0 : 1;   // the first noise draw of the launch
+    const bool seg = MODE == 0 && a.seg_state != nullptr;   // segment mode
     // this CTA's column pairs [u0, u1) (column slot c = 2 (u - u0) + j holds kx = 2u + j)
     // and row pairs [p0, p1)
     int u0, u1, p0, p1;
@@ -331,8 +332,9 @@ __global__ void __launch_bounds__(P2Shape<N, E, NNW>::THREADS, 1) k2p_step(const
                 for (int p = gl; p < N / 2; p += TPF) {
                     float4 *dst = reinterpret_cast<float4 *>(b1 + 2 * p);
                     if (live) {
+                        const C *Pin = seg ? a.seg_prod + (size_t)n * a.seg_cstride : a.P;
                         asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)),
-                                     "l"(reinterpret_cast<const float4 *>(a.P + (size_t)kx * N) + p)
+                                     "l"(reinterpret_cast<const float4 *>(Pin + (size_t)kx * N) + p)
                                      : "memory");
                     } else {
                         *dst = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -379,6 +381,11 @@ __global__ void __launch_bounds__(P2Shape<N, E, NNW>::THREADS, 1) k2p_step(const
                         U[ppos] = mk<float>(h.x * s1, h.y * s1);
                     }
                     group_sync<TPF>(1 + g);
+                }
+                if (seg && live) {
+                    // the state after step n, tiled, for the adjoint's segment
+                    C *so = a.seg_state + (size_t)(n + 1) * a.seg_cstride;
+                    for (int ky = gl; ky < N; ky += TPF) so[((size_t)(kx >> 2) * N + ky) * 4 + (kx & 3)] = STc[ky];
                 }
             } else {
                 // the inverse input from the state as it is
@@ -460,7 +467,9 @@ __global__ void __launch_bounds__(P2Shape<N, E, NNW>::THREADS, 1) k2p_step(const
             C *o2;
             if constexpr (MODE == 0) {
                 stage_from(a.T1, false);
-                C *o = fft_fwd_group<N, E, 1>(b1, b0, b1, gl, 1 + g, TW, fp.power);
+                // segment mode: the de-aliased real rows of the state too
+                float *ra = seg ? a.seg_real + (size_t)(n + 1) * a.seg_rstride + (size_t)r0 * N : nullptr;
+                C *o = fft_fwd_group<N, E, 1>(b1, b0, b1, gl, 1 + g, TW, fp.power, ra, ra ? ra + N : nullptr);
                 o2 = fft_fwd_group<N, E, 1>(o, o == b0 ? b1 : b0, o, gl, 1 + g, TW, 0);
             } else {
                 // (d_x h) of both rows as one complex C2R; squares of the two real parts to X3
@@ -476,7 +485,7 @@ __global__ void __launch_bounds__(P2Shape<N, E, NNW>::THREADS, 1) k2p_step(const
                 group_sync<TPF>(1 + g);
                 o2 = fft_fwd_group<N, E, 1>(F, F == b0 ? b1 : b0, F, gl, 1 + g, TW, 0);
             }
-            C *__restrict__ out = a.P + r0;
+            C *__restrict__ out = (seg ? a.seg_prod + (size_t)(n + 1) * a.seg_cstride : a.P) + r0;
 #pragma unroll 4
             for (int k = gl; k < H; k += TPF) {
                 const C wk = o2[k], wm = o2[(N - k) & (N - 1)];
@@ -501,7 +510,7 @@ __global__ void __launch_bounds__(P2Shape<N, E, NNW>::THREADS, 1) k2p_step(const
     if (!wait_full(bl, full_parity(a.nsteps, first))) return;
     const C *nz = NZ + (size_t)bl * NG * N;
     bool bad = false;
-    for (int i = t; i < (u1 - u0) * N; i += NMAIN) {
+    for (int i = t; i < (seg ? 0 : (u1 - u0) * N); i += NMAIN) {
         const int uu = i >> ilog2(N), ky = i & (N - 1), kx0 = 2 * (u0 + uu);
         const size_t o = ((size_t)(kx0 >> 2) * N + ky) * 4 + (kx0 & 3);
         const C v0 = ST[(2 * uu) * N + ky], v1 = ST[(2 * uu + 1) * N + ky];   // zero past Nx/2

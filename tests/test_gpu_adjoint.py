@@ -290,3 +290,33 @@ def test_adjoint_workload_recipe_at_64():
         fd = (4.0 * central(name, h / 2) - central(name, h)) / 3.0
         assert abs(grads64[i] - fd) <= 1e-6 * abs(fd), (name, grads64[i], fd)
     np.testing.assert_allclose(grads64, ref, rtol=1e-8)
+
+
+@pytest.mark.parametrize("shape", [(256, 256), (512, 256), (256, 1024)])
+def test_adjoint_column_parts_on_fft_groups_match_the_generic_kernel(shape):
+    # the column parts of the adjoint step (A, B and the fused B + A) on FFT groups,
+    # one column per group, against the generic column kernel in its adjoint modes:
+    # the same recursion, transforms of another radix layout, so FP32 rounding apart
+    dt, seed, n = 0.02, 19, 11
+    m = O.model_b(shape, dt=dt, seed=seed, **PARAMS)
+    phi0 = O.to_spectrum(m, O.init_uniform(m, -0.3, 0.3))
+    c = _weights(shape)
+    lamT = 2.0 * c * O.run(m, phi0, 0, n) / m.n_sites
+    lam0, g = O.adjoint(m, phi0, 0, n, lamT)
+    ref = np.array([g[1], -g[6], g[2], g[10]])
+    out = {}
+    for groups in (1, 0):
+        for fuse in (1, 0):
+            s = _gpu_system(shape, "f32", dt, seed)
+            s.set_tuning("adj_col2", groups)
+            s.set_tuning("fuse_adjoint", fuse)
+            s.adjoint_forward(n)
+            out[groups, fuse] = s.adjoint_backward(O.half(lamT), 4)
+            grads, lam0_gpu = out[groups, fuse]
+            assert rel(lam0_gpu, O.half(lam0)) < 1e-3
+            assert np.max(np.abs(grads - ref) / np.abs(ref)) < 1e-3, (groups, fuse, grads, ref)
+    # the fused and separate launches give the same adjoint field bits
+    np.testing.assert_array_equal(out[1, 1][1], out[1, 0][1])
+    np.testing.assert_allclose(out[1, 1][0], out[1, 0][0], rtol=1e-9)
+    assert rel(out[1, 1][1], out[0, 1][1]) < 1e-4
+    assert np.max(np.abs(out[1, 1][0] - out[0, 1][0]) / np.abs(out[0, 1][0])) < 1e-4
