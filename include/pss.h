@@ -245,11 +245,26 @@ int pss_time_kernels(pss_system *s, int64_t n, double *avg_ms);
  *                 launch (1, default, where its shared memory fits) or in
  *                 two (0); the adjoint fields agree bit for bit, the
  *                 gradients to the order of their FP64 atomic sums;
+ *   "persist"     FP32 2D square systems of side 256, 512 or 1024 with
+ *                 Model A/B or KPZ terms take a run of steps as one
+ *                 cooperative launch with grid barriers between the column
+ *                 and row phases (1, default) or as two launches a step on
+ *                 the "fast2d" kernels (0); the same bits at the same FFT
+ *                 radix;
+ *   "persist_blocks" CTAs of that launch (0: automatic, one per SM and at
+ *                 most one per column pair or row pair; values below the
+ *                 smallest count that keeps every column and row pair in
+ *                 shared memory are raised to it; at most the SMs);
+ *   "adj_col2"    the column parts of the FP32 2D adjoint run on FFT groups,
+ *                 one column pair per CTA (1, default) or on the generic
+ *                 column kernel (0); they agree to FP32 rounding;
  *   "test_timeout" a check of the bounded device waits, for tests: with 1,
  *                 the first CTA of the generic column kernel expects 16
- *                 bytes more than its bulk copies deliver and its waits give
- *                 up after 1024 polls (a few milliseconds), so the next
- *                 synchronising call returns PSS_ETIMEOUT; results of the
+ *                 bytes more than its bulk copies deliver, and the first
+ *                 CTA of the persistent step never arrives at its first
+ *                 grid barrier; every wait gives up after 1024 polls (a few
+ *                 milliseconds), so the next synchronising call returns
+ *                 PSS_ETIMEOUT and clears the barrier words; results of the
  *                 steps taken meanwhile are wrong; 0 (default) turns it off;
  * 0 restores the automatic choice.  Unknown keys return PSS_EINVAL. */
 int pss_set_tuning(pss_system *s, const char *key, int value);

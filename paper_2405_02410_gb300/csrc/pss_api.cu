@@ -408,8 +408,13 @@ bool kpz2d_shape(const pss_system *s) {
 }
 bool persist2d_ok(const pss_system *s) {
     auto side = [](int n) { return n == 256 || n == 512 || n == 1024; };
-    return s->tune_fast2d && s->prec == PSS_F32 && s->dim == 2 && side(s->nx) && s->nx == s->ny && s->batch == 1 &&
-           s->fields.size() == 1 && s->coop && !round_trip(s) && (!any_general(s) || kpz2d_shape(s));
+    if (!(s->tune_fast2d && s->prec == PSS_F32 && s->dim == 2 && side(s->nx) && s->nx == s->ny && s->batch == 1 &&
+          s->fields.size() == 1 && s->coop && !round_trip(s) && (!any_general(s) || kpz2d_shape(s))))
+        return false;
+    // every CTA resident at once, and few enough column and row pairs per CTA
+    // for its shared memory
+    const int n = s->nx, uc = (n / 2 + 2) / 2;
+    return std::max((uc + 1) / 2, n / 8) <= s->num_sms;
 }
 bool persist2d(const pss_system *s) { return s->tune_persist && persist2d_ok(s); }
 int p2_mode(const pss_system *s) { return any_general(s) ? 1 : 0; }
@@ -418,7 +423,7 @@ int p2_mode(const pss_system *s) { return any_general(s) ? 1 : 0; }
 // us per step)
 int p2_radix(const pss_system *s) {
     const int r = s->tune_col2_radix ? s->tune_col2_radix : (s->ny >= 1024 ? 16 : 8);
-    return r == 32 ? (s->ny == 1024 ? 32 : 16) : r == 16 ? 16 : 8;
+    return r >= 16 ? 16 : 8;   // no radix-32 variant: it was slower than radix 16
 }
 // CTAs of the persistent step: every SM (one CTA each), but no more than the
 // column pairs or row pairs to hand out, and at least enough to hold them (2
@@ -427,7 +432,7 @@ int p2_blocks(const pss_system *s) {
     const int n = s->nx, uc = (n / 2 + 2) / 2;
     const int lo = std::max((uc + 1) / 2, n / 8);
     const int want = s->tune_persist_blocks > 0 ? s->tune_persist_blocks : std::min(s->num_sms, std::max(uc, n / 2));
-    return std::max(lo, want);
+    return std::min(s->num_sms, std::max(lo, want));
 }
 
 int col2_radix(const pss_system *s) {

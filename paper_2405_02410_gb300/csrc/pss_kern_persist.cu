@@ -26,13 +26,13 @@ cudaError_t launch_p2(const P2Args &a, int n, int E, int nblocks, int mode, cuda
     const int uc = (n / 2 + 2) / 2;
     if (nblocks < (uc + 1) / 2 || nblocks < n / 8 || a.nsteps < 1) return cudaErrorInvalidConfiguration;
     if (mode == 1) return launch_p2_kpz(a, n, E, nblocks, st);
-    // beside the FFT groups: 8 noise warps with radix-16 passes, 4 with radix 8
-    // (twice the FFT threads)
+    // beside the FFT groups, 4 noise warps (the register budget of 168 per
+    // thread that leaves the radix-16 transforms measured faster than 8 warps)
     switch (n) {
-        case 256: return E == 16 ? launch_p2_ne<256, 16, 8, 0>(a, nblocks, st) : launch_p2_ne<256, 8, 4, 0>(a, nblocks, st);
-        case 512: return E == 16 ? launch_p2_ne<512, 16, 8, 0>(a, nblocks, st) : launch_p2_ne<512, 8, 4, 0>(a, nblocks, st);
+        case 256: return E == 16 ? launch_p2_ne<256, 16, 4, 0>(a, nblocks, st) : launch_p2_ne<256, 8, 4, 0>(a, nblocks, st);
+        case 512: return E == 16 ? launch_p2_ne<512, 16, 4, 0>(a, nblocks, st) : launch_p2_ne<512, 8, 4, 0>(a, nblocks, st);
         case 1024:
-            return E == 16 ? launch_p2_ne<1024, 16, 8, 0>(a, nblocks, st) : launch_p2_ne<1024, 8, 4, 0>(a, nblocks, st);
+            return E == 16 ? launch_p2_ne<1024, 16, 4, 0>(a, nblocks, st) : launch_p2_ne<1024, 8, 4, 0>(a, nblocks, st);
         default: return cudaErrorInvalidValue;
     }
 }

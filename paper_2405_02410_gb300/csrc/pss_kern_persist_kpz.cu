@@ -23,10 +23,10 @@ cudaError_t launch_p2k_ne(const P2Args &a, int nblocks, cudaStream_t st) {
 
 cudaError_t launch_p2_kpz(const P2Args &a, int n, int E, int nblocks, cudaStream_t st) {
     switch (n) {
-        case 256: return E == 16 ? launch_p2k_ne<256, 16, 8>(a, nblocks, st) : launch_p2k_ne<256, 8, 4>(a, nblocks, st);
-        case 512: return E == 16 ? launch_p2k_ne<512, 16, 8>(a, nblocks, st) : launch_p2k_ne<512, 8, 4>(a, nblocks, st);
+        case 256: return E == 16 ? launch_p2k_ne<256, 16, 4>(a, nblocks, st) : launch_p2k_ne<256, 8, 4>(a, nblocks, st);
+        case 512: return E == 16 ? launch_p2k_ne<512, 16, 4>(a, nblocks, st) : launch_p2k_ne<512, 8, 4>(a, nblocks, st);
         case 1024:
-            return E == 16 ? launch_p2k_ne<1024, 16, 8>(a, nblocks, st) : launch_p2k_ne<1024, 8, 4>(a, nblocks, st);
+            return E == 16 ? launch_p2k_ne<1024, 16, 4>(a, nblocks, st) : launch_p2k_ne<1024, 8, 4>(a, nblocks, st);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -172,6 +172,118 @@ __device__ __forceinline__ uint32_t empty_parity(int n) { return (uint32_t)(((n 
 // derivative factor i q of a mode (q = 0 at a Nyquist index, reading R14)
 __device__ __forceinline__ float dq(int k, int n, float g) { return 2 * k == n ? 0.f : fmul(float(signed_k(k, n)), g); }
 
+// ---- group FFTs with their first or last pass on registers ----------------
+// Thread gl of a group takes input points gl + TPF m (m = 0..E-1) in the first
+// pass of a transform, and the last pass leaves it with output points
+// gl + TPF (s + BPT r) of its butterflies s and outputs r: the same set.  So
+// a transform can start from values loaded from global memory, or from the
+// outputs of the transform before it, without a round trip through shared
+// memory: x[m] holds point gl + TPF m.  The butterflies and their arithmetic
+// are those of fpass, so the results are the same bits.
+
+// first pass (radix E, no twiddles) from x[] into dst (padded), as fpass<N, E, E, false, false, true>
+template <int N, int E>
+__device__ __forceinline__ void fpass_first_regs(float2 (&x)[E], float2 *dst, int gl) {
+    using S = GShape<N, E>;
+    dft_reg<E, -1, float>(x);
+    const int j = gl << S::LOGE;
+#pragma unroll
+    for (int r = 0; r < E; ++r) dst[padp<S::PS>(j + r)] = x[r];
+}
+
+// the middle passes (radix E, twiddled, padded in and out) after the first
+// pass wrote cur; on return cur is the buffer the last pass reads and nxt
+// the other one.  Returns log2 of the points combined so far.
+template <int N, int E>
+__device__ __forceinline__ int fpass_middle(float2 *&cur, float2 *&nxt, int gl, int id,
+                                            const float2 *__restrict__ tw) {
+    using S = GShape<N, E>;
+    int logP = S::LOGE;
+#pragma unroll 1
+    for (; logP + S::LOGRL < S::LOG; logP += S::LOGE) {
+        fpass<N, E, E, true, true, true>(cur, nxt, logP, gl, tw, 0);
+        group_sync<S::TPF>(id);
+        float2 *tmp = cur;
+        cur = nxt;
+        nxt = tmp;
+    }
+    return logP;
+}
+
+// last pass (radix RL, twiddled) into x[]: x[m] = f(q, X_q), q = gl + TPF m
+template <int N, int E, class F>
+__device__ __forceinline__ void fpass_last_regs(const float2 *src, int logP, int gl, const float2 *__restrict__ tw,
+                                                float2 (&x)[E], F &&f) {
+    using S = GShape<N, E>;
+    constexpr int R = S::RL, TPF = S::TPF, STRIDE = N / R, BPT = STRIDE / TPF, LOGR = ilog2(R);
+    static_assert(BPT * R == E, "a thread's last-pass outputs are its first-pass inputs");
+    const int P = 1 << logP;
+#pragma unroll
+    for (int s = 0; s < BPT; ++s) {
+        const int i = gl + TPF * s, k = i & (P - 1);
+        float2 u[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) u[r] = src[padp<S::PS>(i + r * STRIDE)];
+        const float2 *__restrict__ twp = tw + (P - E) + k;
+#pragma unroll
+        for (int r = 1; r < R; ++r) u[r] = cmul<float>(u[r], twp[(r - 1) * P]);
+        dft_reg<R, -1, float>(u);
+        const int j = ((i - k) << LOGR) + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) x[s + BPT * r] = f(j + r * P, u[r]);
+    }
+}
+
+// A group FFT from x[] (its first pass writes b0, which must be free) whose
+// last pass hands its outputs to sink(q, value) (no barrier after it).
+template <int N, int E, class Sink>
+__device__ __forceinline__ void fft_regs_sink(float2 (&x)[E], float2 *b0, float2 *b1, int gl, int id,
+                                              const float2 *__restrict__ tw, Sink &&sink) {
+    fpass_first_regs<N, E>(x, b0, gl);
+    group_sync<GShape<N, E>::TPF>(id);
+    float2 *cur = b0, *nxt = b1;
+    const int logP = fpass_middle<N, E>(cur, nxt, gl, id, tw);
+    fpass_sink<N, E, GShape<N, E>::RL>(cur, logP, gl, tw, sink);
+}
+
+// A group FFT from x[] back into x[] (x[m] = f(q, X_q)); the last pass reads
+// b1 when the transform has an odd number of passes, else b0 (no barrier after it).
+template <int N, int E, class F>
+__device__ __forceinline__ void fft_regs_regs(float2 (&x)[E], float2 *b0, float2 *b1, int gl, int id,
+                                              const float2 *__restrict__ tw, F &&f) {
+    fpass_first_regs<N, E>(x, b0, gl);
+    group_sync<GShape<N, E>::TPF>(id);
+    float2 *cur = b0, *nxt = b1;
+    const int logP = fpass_middle<N, E>(cur, nxt, gl, id, tw);
+    fpass_last_regs<N, E>(cur, logP, gl, tw, x, f);
+}
+
+// A group FFT of the natural-order input in b1 into x[] (x[m] = f(q, X_q));
+// the last pass reads the same buffer as fft_regs_regs's (no barrier after it).
+template <int N, int E, class F>
+__device__ __forceinline__ void fft_smem_regs(float2 *b0, float2 *b1, int gl, int id, const float2 *__restrict__ tw,
+                                              float2 (&x)[E], F &&f) {
+    fpass<N, E, E, false, false, true>(b1, b0, 0, gl, tw, 0);
+    group_sync<GShape<N, E>::TPF>(id);
+    float2 *cur = b0, *nxt = b1;
+    const int logP = fpass_middle<N, E>(cur, nxt, gl, id, tw);
+    fpass_last_regs<N, E>(cur, logP, gl, tw, x, f);
+}
+
+// A group FFT from x[] (first pass into b0, which must be free) whose result,
+// in natural order, is returned in one of the two buffers, visible to the group.
+template <int N, int E>
+__device__ __forceinline__ float2 *fft_regs_smem(float2 (&x)[E], float2 *b0, float2 *b1, int gl, int id,
+                                                 const float2 *__restrict__ tw) {
+    fpass_first_regs<N, E>(x, b0, gl);
+    group_sync<GShape<N, E>::TPF>(id);
+    float2 *cur = b0, *nxt = b1;
+    const int logP = fpass_middle<N, E>(cur, nxt, gl, id, tw);
+    fpass<N, E, GShape<N, E>::RL, true, true, false>(cur, nxt, logP, gl, tw, 0);
+    group_sync<GShape<N, E>::TPF>(id);
+    return nxt;
+}
+
 template <int N, int E, int NNW, int MODE>
 __global__ void __launch_bounds__(P2Shape<N, E, NNW>::THREADS, 1) k2p_step(const P2Args a) {
     using C = float2;
@@ -189,6 +301,7 @@ __global__ void __launch_bounds__(P2Shape<N, E, NNW>::THREADS, 1) k2p_step(const
     C *WB = reinterpret_cast<C *>(smem_raw + L::WB);
     __shared__ FieldP<float> sfp;
     __shared__ unsigned s_step0;
+    __shared__ int s_o2;   // offset of the row transforms' results in a group's buffers
     __shared__ volatile int s_abort;   // a wait gave up: every role leaves
     const SysP<float> &sp = a.sp;
     const FieldP<float> &fp = sfp;
@@ -328,30 +441,28 @@ __global__ void __launch_bounds__(P2Shape<N, E, NNW>::THREADS, 1) k2p_step(const
             C *U = SinkShape<N, E>::LAST_READS_B1 ? b0 : b1;   // the buffer the last pass does not read
             C *STc = ST + g * N;
             const bool kxk = kx <= kmx, live = kx < sp.hx;
+            const bool herm = kx == 0 || kx == N / 2;   // columns whose modes pair up (the field is real)
+            C x[E];   // point gl + TPF m of the current transform
             if (!pro) {
-                for (int p = gl; p < N / 2; p += TPF) {
-                    float4 *dst = reinterpret_cast<float4 *>(b1 + 2 * p);
-                    if (live) {
-                        const C *Pin = seg ? a.seg_prod + (size_t)n * a.seg_cstride : a.P;
-                        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)),
-                                     "l"(reinterpret_cast<const float4 *>(Pin + (size_t)kx * N) + p)
-                                     : "memory");
-                    } else {
-                        *dst = make_float4(0.f, 0.f, 0.f, 0.f);
-                    }
+                // the x-transformed product of the column straight into the forward
+                // transform's first-pass registers
+                {
+                    const C *Pin = (seg ? a.seg_prod + (size_t)n * a.seg_cstride : a.P) + (size_t)kx * N + gl;
+#pragma unroll
+                    for (int m = 0; m < E; ++m) x[m] = live ? __ldcg(Pin + m * TPF) : mk<float>(0.f, 0.f);
                 }
-                asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
                 // the noise of this step (every thread of the group waits; bounded)
                 if (!(n == 0 && first == 1) && !mbar_wait_abortable(full + b, full_parity(n, first), &s_abort)) {
                     if (!s_abort && a.d_status) atomicOr(a.d_status, kStatusTimeout);
                     s_abort = 1;
                 }
-                group_sync<TPF>(1 + g);
                 const C *nzc = NZ + ((size_t)b * NG + g) * N;
                 const float2 *MGc = MG + g * N;
                 const float qx = fmul(float(kx), sp.gx);
-                fft_fwd_group_sink<N, E>(b0, b1, gl, 1 + g, TW, [&](int ky, C pq) {
-                    const C x = noisy ? cscale<float>(nzc[ky], sigma0) : mk<float>(0.f, 0.f);
+                // forward y-FFT; its last pass applies the update (Eq. timeupdate) mode by
+                // mode and keeps the de-aliased, scaled, conjugated inverse input in x[]
+                fft_regs_regs<N, E>(x, b0, b1, gl, 1 + g, TW, [&](int ky, C pq) {
+                    const C xi = noisy ? cscale<float>(nzc[ky], sigma0) : mk<float>(0.f, 0.f);
                     float m, gg;
                     if constexpr (MODE == 0) {
                         const float2 mg = MGc[ky];
@@ -360,15 +471,18 @@ __global__ void __launch_bounds__(P2Shape<N, E, NNW>::THREADS, 1) k2p_step(const
                     } else {
                         update_factors<float>(q2sum(qx, fmul(float(signed_k(ky, N)), sp.gy)), dtO, dtM, m, gg);
                     }
-                    C v = update_pre<float>(STc[ky], pq, x, m, gg, has_product);
+                    C v = update_pre<float>(STc[ky], pq, xi, m, gg, has_product);
                     if (!live) v = mk<float>(0.f, 0.f);
                     STc[ky] = v;
                     const float sc = (kxk && abs(signed_k(ky, N)) <= kmy) ? scale : 0.f;
-                    U[ky] = mk<float>(v.x * sc, -v.y * sc);
+                    return mk<float>(v.x * sc, -v.y * sc);
                 });
-                group_sync<TPF>(1 + g);
-                if (kx == 0 || kx == N / 2) {
-                    // Hermitian part (the field is real): phi(kx, ky) <- (phi(kx, ky) + conj phi(kx, -ky)) / 2
+                if (herm) {
+                    // Hermitian part: phi(kx, ky) <- (phi(kx, ky) + conj phi(kx, -ky)) / 2, with
+                    // the inverse input through shared memory (partner modes sit with other threads)
+#pragma unroll
+                    for (int m = 0; m < E; ++m) U[gl + m * TPF] = x[m];
+                    group_sync<TPF>(1 + g);
                     for (int pos = gl; pos < N / 2 + 1; pos += TPF) {
                         const int ppos = (N - pos) & (N - 1);
                         const C v0 = STc[pos], v1 = STc[ppos];
@@ -383,9 +497,14 @@ __global__ void __launch_bounds__(P2Shape<N, E, NNW>::THREADS, 1) k2p_step(const
                     group_sync<TPF>(1 + g);
                 }
                 if (seg && live) {
-                    // the state after step n, tiled, for the adjoint's segment
+                    // the state after step n, tiled, for the adjoint's segment (a thread's own
+                    // modes, or any after the Hermitian part's barrier)
                     C *so = a.seg_state + (size_t)(n + 1) * a.seg_cstride;
-                    for (int ky = gl; ky < N; ky += TPF) so[((size_t)(kx >> 2) * N + ky) * 4 + (kx & 3)] = STc[ky];
+#pragma unroll 4
+                    for (int m = 0; m < E; ++m) {
+                        const int ky = gl + m * TPF;
+                        so[((size_t)(kx >> 2) * N + ky) * 4 + (kx & 3)] = STc[ky];
+                    }
                 }
             } else {
                 // the inverse input from the state as it is
@@ -397,9 +516,15 @@ __global__ void __launch_bounds__(P2Shape<N, E, NNW>::THREADS, 1) k2p_step(const
                 group_sync<TPF>(1 + g);
             }
             if (kxk) {
-                // y-inverse (T1 = F(conj X)): input in U, the other buffer for the passes
+                // y-inverse (T1 = F(conj X)), its last pass storing T1 (column-major): from
+                // x[] (its first pass into the buffer the forward's last pass did not read),
+                // or from U
                 C *__restrict__ dst = a.T1 + (size_t)kx * N;
-                fft_fwd_group_sink<N, E>(U == b0 ? b1 : b0, U, gl, 1 + g, TW, [&](int q, C v) { dst[q] = v; });
+                auto to_t1 = [&](int q, C v) { dst[q] = v; };
+                if (!pro && !herm)
+                    fft_regs_sink<N, E>(x, U, U == b0 ? b1 : b0, gl, 1 + g, TW, to_t1);
+                else
+                    fft_fwd_group_sink<N, E>(U == b0 ? b1 : b0, U, gl, 1 + g, TW, to_t1);
                 if constexpr (MODE == 1) {
                     // the y-inverse of i q_y X (T1a): its input from the state, into b1
                     group_sync<TPF>(1 + g);
@@ -428,28 +553,31 @@ __global__ void __launch_bounds__(P2Shape<N, E, NNW>::THREADS, 1) k2p_step(const
         alive = grid_wait<NMAIN>(a.gs, target, a.d_status, sp.wait_limit, &s_abort);
         if (!alive) break;
         // ================= row phase =================
-        // Each FFT group runs one row pair on its own (rows r0, r0 + 1), from the
-        // conjugated y-inverse(s), and stores the two rows' half spectra of the
-        // product column-major.
-        if (g < npr) {
-            const int r0 = 2 * (p0 + g);
+        // Each FFT group runs one row pair (rows r0 + 2 g, r0 + 2 g + 1) on its own,
+        // from the conjugated y-inverse(s), and the two rows' half spectra of the
+        // product go to P (column-major).  The staging of the inputs and the
+        // store of the products are shared by the CTA's transform threads: one
+        // thread per (column k, row pair j), so that the CTA's rows of a column
+        // (2 npr consecutive points of T1 and of P) move as one run.
+        if (npr > 0) {
+            const int r0 = 2 * p0;   // the CTA's first row
             const int kc = fp.kx_cols;
             C *b0 = gb, *b1 = gb + S::BUF;
-            constexpr int PER = (H + TPF - 1) / TPF;   // columns per thread
-            // stage Y = conj(Z) of the rows' spectra (as k2_row) into b1; deriv: times -i q_x
-            // first (the conjugate of i q_x)
+            constexpr int PERC = (NG * H + NMAIN - 1) / NMAIN;   // (column, row pair) items per thread
+            // stage Y = conj(Z) of every group's rows (as k2_row) into its b1; deriv:
+            // times -i q_x first (the conjugate of i q_x)
             auto stage_from = [&](const C *src, bool deriv) {
-                float4 v[PER];
+                float4 v[PERC];
 #pragma unroll
-                for (int q = 0; q < PER; ++q) {
-                    const int k = gl + q * TPF;
+                for (int q = 0; q < PERC; ++q) {
+                    const int i = t + q * NMAIN, k = i / NG, j = i % NG;
                     v[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (k < kc) v[q] = __ldcg(reinterpret_cast<const float4 *>(src + (size_t)k * N + r0));
+                    if (k < kc && j < npr) v[q] = __ldcg(reinterpret_cast<const float4 *>(src + (size_t)k * N + r0 + 2 * j));
                 }
 #pragma unroll
-                for (int q = 0; q < PER; ++q) {
-                    const int k = gl + q * TPF;
-                    if (k < H) {
+                for (int q = 0; q < PERC; ++q) {
+                    const int i = t + q * NMAIN, k = i / NG, j = i % NG;
+                    if (k < H && j < npr) {
                         float ar = v[q].x, ai = v[q].y, br = v[q].z, bi = v[q].w;
                         if (deriv) {
                             const float qd = dq(k, N, sp.gx);
@@ -458,39 +586,67 @@ __global__ void __launch_bounds__(P2Shape<N, E, NNW>::THREADS, 1) k2p_step(const
                         }
                         if (k == 0 || k == N / 2) { ai = 0.f; bi = 0.f; }   // the half spectra of real rows
                         const C lo = mk<float>(ar - bi, -ai - br), hi = mk<float>(ar + bi, ai - br);
-                        b1[k] = hi;
-                        if (k > 0 && k < N / 2) b1[N - k] = lo;
+                        C *bj = WB + j * S::WS + S::BUF;   // group j's b1
+                        bj[k] = hi;
+                        if (k > 0 && k < N / 2) bj[N - k] = lo;
                     }
                 }
-                group_sync<TPF>(1 + g);
+                main_sync<NMAIN>();
             };
-            C *o2;
+            // the C2R's last pass hands its outputs to the R2C's first pass in registers
+            // (the R2C's first pass writes the buffer that last pass did not read)
+            constexpr bool LB1 = SinkShape<N, E>::LAST_READS_B1;
+            C *o2 = nullptr;
             if constexpr (MODE == 0) {
                 stage_from(a.T1, false);
-                // segment mode: the de-aliased real rows of the state too
-                float *ra = seg ? a.seg_real + (size_t)(n + 1) * a.seg_rstride + (size_t)r0 * N : nullptr;
-                C *o = fft_fwd_group<N, E, 1>(b1, b0, b1, gl, 1 + g, TW, fp.power, ra, ra ? ra + N : nullptr);
-                o2 = fft_fwd_group<N, E, 1>(o, o == b0 ? b1 : b0, o, gl, 1 + g, TW, 0);
+                if (g < npr) {
+                    // segment mode: the de-aliased real rows of the state too
+                    float *ra = seg ? a.seg_real + (size_t)(n + 1) * a.seg_rstride + (size_t)(r0 + 2 * g) * N : nullptr;
+                    float *rb = ra ? ra + N : nullptr;
+                    const int pw = fp.power;
+                    C x[E];
+                    fft_smem_regs<N, E>(b0, b1, gl, 1 + g, TW, x, [&](int q, C v) {
+                        if (ra) {
+                            ra[q] = v.x;
+                            rb[q] = -v.y;
+                        }
+                        if (pw > 0) v = mk<float>(pow_p(v.x, pw), pow_p(-v.y, pw));
+                        return v;
+                    });
+                    o2 = fft_regs_smem<N, E>(x, LB1 ? b0 : b1, LB1 ? b1 : b0, gl, 1 + g, TW);
+                }
             } else {
                 // (d_x h) of both rows as one complex C2R; squares of the two real parts to X3
                 C *X = X3 + g * N;
                 stage_from(a.T1, true);
-                fft_fwd_group_sink<N, E>(b0, b1, gl, 1 + g, TW, [&](int q, C v) { X[q] = mk<float>(v.x * v.x, v.y * v.y); });
-                group_sync<TPF>(1 + g);
+                if (g < npr)
+                    fft_fwd_group_sink<N, E>(b0, b1, gl, 1 + g, TW,
+                                             [&](int q, C v) { X[q] = mk<float>(v.x * v.x, v.y * v.y); });
+                main_sync<NMAIN>();
                 // (d_y h) of both rows; the sum of squares packs the two rows' products
                 stage_from(a.T1a, false);
-                C *F = SinkShape<N, E>::LAST_READS_B1 ? b0 : b1;
-                fft_fwd_group_sink<N, E>(b0, b1, gl, 1 + g, TW,
-                                         [&](int q, C v) { F[q] = mk<float>(fadd(X[q].x, v.x * v.x), fadd(X[q].y, v.y * v.y)); });
-                group_sync<TPF>(1 + g);
-                o2 = fft_fwd_group<N, E, 1>(F, F == b0 ? b1 : b0, F, gl, 1 + g, TW, 0);
+                if (g < npr) {
+                    C x[E];
+                    fft_smem_regs<N, E>(b0, b1, gl, 1 + g, TW, x, [&](int q, C v) {
+                        return mk<float>(fadd(X[q].x, v.x * v.x), fadd(X[q].y, v.y * v.y));
+                    });
+                    o2 = fft_regs_smem<N, E>(x, LB1 ? b0 : b1, LB1 ? b1 : b0, gl, 1 + g, TW);
+                }
             }
+            // every group's result lies at the same offset of its buffers (group 0 always runs)
+            if (t == 0) s_o2 = (int)(o2 - gb);
+            main_sync<NMAIN>();
+            const C *o2w = WB + s_o2;
             C *__restrict__ out = (seg ? a.seg_prod + (size_t)(n + 1) * a.seg_cstride : a.P) + r0;
-#pragma unroll 4
-            for (int k = gl; k < H; k += TPF) {
-                const C wk = o2[k], wm = o2[(N - k) & (N - 1)];
-                *reinterpret_cast<float4 *>(out + (size_t)k * N) =
-                    make_float4(0.5f * (wk.x + wm.x), 0.5f * (wk.y - wm.y), 0.5f * (wk.y + wm.y), -0.5f * (wk.x - wm.x));
+#pragma unroll
+            for (int q = 0; q < PERC; ++q) {
+                const int i = t + q * NMAIN, k = i / NG, j = i % NG;
+                if (k < H && j < npr) {
+                    const C *oj = o2w + j * S::WS;
+                    const C wk = oj[k], wm = oj[(N - k) & (N - 1)];
+                    *reinterpret_cast<float4 *>(out + (size_t)k * N + 2 * j) =
+                        make_float4(0.5f * (wk.x + wm.x), 0.5f * (wk.y - wm.y), 0.5f * (wk.y + wm.y), -0.5f * (wk.x - wm.x));
+                }
             }
         }
         // ---- grid barrier B (not after the last step)
