@@ -16,8 +16,8 @@ CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libpss.so")
 SOURCES = ["pss_api.cu", "pss_kern_f32.cu", "pss_kern_f64.cu", "pss_kern_f32_r16.cu", "pss_kern_f64_r16.cu",
-           "pss_kern_fast2d.cu", "pss_kern_persist.cu", "pss_kern_persist_kpz.cu"]
-HEADERS = ["pss_device.cuh", "pss_internal.h", "pss_kernels.cuh", "pss_fast2d.cuh", "pss_persist2d.cuh", "pss_adj2d.cuh"]
+           "pss_kern_fast2d.cu", "pss_kern_persist.cu", "pss_kern_persist_kpz.cu", "pss_kern_persist_adj.cu"]
+HEADERS = ["pss_device.cuh", "pss_internal.h", "pss_kernels.cuh", "pss_fast2d.cuh", "pss_persist2d.cuh", "pss_adj2d.cuh", "pss_persist_adj.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fno-strict-aliasing",
               "--expt-relaxed-constexpr"]

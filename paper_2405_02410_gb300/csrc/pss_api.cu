@@ -133,7 +133,8 @@ struct pss_system {
     int tune_fast3d = 1;                     // FP32 3D x pass with one FFT group per row pair (0 = generic k_row)
     int tune_test_timeout = 0;               // check of the bounded waits: one CTA's wait runs out (tests)
     int tune_persist = 1;                    // square FP32 2D systems: a run of steps as one persistent launch
-    int tune_adj_col2 = 1;                   // FP32 2D adjoint: column parts on FFT groups (0: generic kernel)
+    int tune_adj_col2 = 1;
+    int tune_persist_adj = 1;                // FP32 2D adjoint on the persistent path: a segment's backward pass in one launch                   // FP32 2D adjoint: column parts on FFT groups (0: generic kernel)
     int tune_persist_blocks = 0;             // its CTAs (0: every SM, at most one CTA per column pair or row pair)
     int coop = 0;                            // the device takes cooperative launches
     // captured persistent launches by run length (one kernel node each); p2_capture < 0: capture
@@ -149,6 +150,7 @@ struct pss_system {
     void *seg = nullptr;                     // recomputed states of one segment [K + 1][slot]
     void *seg_prod = nullptr;                // their x(y)-transformed products [K + 1][slot]
     void *seg_real = nullptr;                // their de-aliased real fields [K + 1][nsites]
+    void *seg_noise = nullptr;               // their unit noise [K + 1][slot] (the persistent path)
     double *d_grad = nullptr;                // [11]
     long long *d_seg = nullptr;              // [2]: segment index, step of its first step (device)
     int64_t adj_n = 0, adj_step0 = 0, adj_K = 0, adj_nck = 0;
@@ -1490,11 +1492,13 @@ int adj_alloc(pss_system *s, int64_t nck, int64_t K) {
     cudaFree(s->seg);
     cudaFree(s->seg_prod);
     cudaFree(s->seg_real);
-    s->ck = s->seg = s->seg_prod = s->seg_real = nullptr;
+    cudaFree(s->seg_noise);
+    s->ck = s->seg = s->seg_prod = s->seg_real = s->seg_noise = nullptr;
     CK(cudaMalloc(&s->ck, slot_bytes * (size_t)(nck + 1)));
     CK(cudaMalloc(&s->seg, slot_bytes * (size_t)(K + 1)));
     CK(cudaMalloc(&s->seg_prod, slot_bytes * (size_t)(K + 1)));
     CK(cudaMalloc(&s->seg_real, rsize(s) * (size_t)s->nsites * (size_t)(K + 1)));
+    if (persist2d_ok(s)) CK(cudaMalloc(&s->seg_noise, slot_bytes * (size_t)(K + 1)));
     if (!s->L) CK(cudaMalloc(&s->L, slot_bytes));
     if (!s->d_grad) CK(cudaMalloc(&s->d_grad, sizeof(double) * 11));
     if (!s->d_seg) CK(cudaMalloc(&s->d_seg, sizeof(long long) * 2));
@@ -1537,11 +1541,37 @@ template <typename T> int record_adjoint_segment(pss_system *s, cudaStream_t str
         a.seg_state = (float2 *)st(0);
         a.seg_prod = (float2 *)prod(0);
         a.seg_real = (float *)real(0);
+        a.seg_noise = s->tune_persist_adj ? (float2 *)s->seg_noise : nullptr;
         a.seg_cstride = s->field_elems;
         a.seg_rstride = (size_t)s->nsites;
         e = launch_p2(a, s->nx, p2_radix(s), p2_blocks(s), 0, stream);
         s->launches++;
         if (e != cudaSuccess) return cuda_fail(s, e, "k2p_step launch (recomputed segment)");
+        if (s->tune_persist_adj && s->seg_noise) {
+            // the segment's backward pass as one persistent launch (k2p_adj): the adjoint
+            // field from L and back, nu and w through A and B
+            P2AdjArgs b{};
+            b.sp = a.sp;
+            b.fps = a.fps;
+            b.tw = a.tw;
+            b.L = (float2 *)s->L;
+            b.NU = (float2 *)s->A;
+            b.W = (float2 *)s->B;
+            b.seg_state = (const float2 *)st(0);
+            b.seg_prod = (const float2 *)prod(0);
+            b.seg_real = (const float *)real(0);
+            b.seg_noise = (const float2 *)s->seg_noise;
+            b.cstride = s->field_elems;
+            b.rstride = (size_t)s->nsites;
+            b.grad = s->d_grad;
+            b.d_status = s->d_status;
+            b.gs = s->gs;
+            b.len = (int)len;
+            e = launch_p2_adj(b, s->nx, p2_radix(s), p2_blocks(s), stream);
+            s->launches++;
+            if (e != cudaSuccess) return cuda_fail(s, e, "k2p_adj launch");
+            return PSS_OK;
+        }
     } else {
         if ((rc = q.recompute_prologue(st(0), prod(0), real(0)))) return rc;
         for (int64_t i = 0; i < len; ++i)
@@ -1635,6 +1665,7 @@ int pss_destroy_system(pss_system *s) {
     cudaFree(s->seg);
     cudaFree(s->seg_prod);
     cudaFree(s->seg_real);
+    cudaFree(s->seg_noise);
     cudaFree(s->d_grad);
     cudaFree(s->d_seg);
     if (s->adj_graph) cudaGraphExecDestroy(s->adj_graph);
@@ -2096,6 +2127,7 @@ int pss_set_tuning(pss_system *s, const char *key, int value) {
     else if (k == "test_timeout") s->tune_test_timeout = value ? 1 : 0;
     else if (k == "persist") s->tune_persist = value ? 1 : 0;
     else if (k == "adj_col2") s->tune_adj_col2 = value ? 1 : 0;
+    else if (k == "persist_adj") s->tune_persist_adj = value ? 1 : 0;
     else if (k == "persist_blocks") {
         if (value > 1024) return fail(s, PSS_EINVAL, "persist_blocks is at most 1024 (0 = automatic)");
         s->tune_persist_blocks = value;

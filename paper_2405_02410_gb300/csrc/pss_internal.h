@@ -232,11 +232,31 @@ struct P2Args {
     float2 *seg_state, *seg_prod;
     float *seg_real;
     size_t seg_cstride, seg_rstride;
+    float2 *seg_noise;          // segment mode: the unit noise of steps 0..nsteps-1 (tiled), if not null
 };
 // n steps in one cooperative launch of nblocks CTAs (E: FFT pass radix, 8 or 16;
 // mode 0: a power of the field, 1: the KPZ gradient square)
 cudaError_t launch_p2(const P2Args &a, int n, int E, int nblocks, int mode, cudaStream_t st);
 cudaError_t launch_p2_kpz(const P2Args &a, int n, int E, int nblocks, cudaStream_t st);
+// The backward pass of one recomputed segment of the FP32 2D adjoint (k2p_adj)
+struct P2AdjArgs {
+    SysP<float> sp;
+    const FieldP<float> *fps;   // the field's parameters (one slot)
+    const float2 *tw;
+    float2 *L;                  // adjoint field, tiled: of the segment's last step on entry, of its first on exit
+    float2 *NU;                 // work array, tiled: nu transformed back along y
+    float2 *W;                  // work array, tiled: the x pass's result
+    const float2 *seg_state;    // states after steps 0..len, tiled, cstride apart
+    const float2 *seg_prod;     // products of steps 0..len-1, column-major, cstride apart
+    const float *seg_real;      // de-aliased real fields of steps 0..len-1 ([ny][nx]), rstride apart
+    const float2 *seg_noise;    // unit noise of steps 0..len-1, tiled, cstride apart (noisy fields)
+    size_t cstride, rstride;
+    double *grad;               // 11 gradient sums, added to
+    int *d_status;
+    GridSync *gs;
+    int len;                    // steps of the segment (>= 1)
+};
+cudaError_t launch_p2_adj(const P2AdjArgs &a, int n, int E, int nblocks, cudaStream_t st);
 template <typename T> cudaError_t launch_init_uniform(T *real, long long nsites, double lo, double hi,
                                                       uint64_t seed, int field_id, cudaStream_t st);
 // product terms with several operators: Q = (first ? 0 : Q) + M(q) Pt over one

@@ -210,10 +210,11 @@ __device__ __forceinline__ int fpass_middle(float2 *&cur, float2 *&nxt, int gl, 
     return logP;
 }
 
-// last pass (radix RL, twiddled) into x[]: x[m] = f(q, X_q), q = gl + TPF m
+// last pass (radix RL, twiddled) into x[]: x[m] = f(q, m, X_q), q = gl + TPF m
+// (m a constant after unrolling: it may index the caller's register arrays)
 template <int N, int E, class F>
-__device__ __forceinline__ void fpass_last_regs(const float2 *src, int logP, int gl, const float2 *__restrict__ tw,
-                                                float2 (&x)[E], F &&f) {
+__device__ __forceinline__ void fpass_last_regs_m(const float2 *src, int logP, int gl, const float2 *__restrict__ tw,
+                                                  float2 (&x)[E], F &&f) {
     using S = GShape<N, E>;
     constexpr int R = S::RL, TPF = S::TPF, STRIDE = N / R, BPT = STRIDE / TPF, LOGR = ilog2(R);
     static_assert(BPT * R == E, "a thread's last-pass outputs are its first-pass inputs");
@@ -230,8 +231,14 @@ __device__ __forceinline__ void fpass_last_regs(const float2 *src, int logP, int
         dft_reg<R, -1, float>(u);
         const int j = ((i - k) << LOGR) + k;
 #pragma unroll
-        for (int r = 0; r < R; ++r) x[s + BPT * r] = f(j + r * P, u[r]);
+        for (int r = 0; r < R; ++r) x[s + BPT * r] = f(j + r * P, s + BPT * r, u[r]);
     }
+}
+// the same with x[m] = f(q, X_q)
+template <int N, int E, class F>
+__device__ __forceinline__ void fpass_last_regs(const float2 *src, int logP, int gl, const float2 *__restrict__ tw,
+                                                float2 (&x)[E], F &&f) {
+    fpass_last_regs_m<N, E>(src, logP, gl, tw, x, [&](int q, int, float2 v) { return f(q, v); });
 }
 
 // A group FFT from x[] (its first pass writes b0, which must be free) whose
@@ -256,6 +263,17 @@ __device__ __forceinline__ void fft_regs_regs(float2 (&x)[E], float2 *b0, float2
     float2 *cur = b0, *nxt = b1;
     const int logP = fpass_middle<N, E>(cur, nxt, gl, id, tw);
     fpass_last_regs<N, E>(cur, logP, gl, tw, x, f);
+}
+
+// fft_regs_regs with x[m] = f(q, m, X_q)
+template <int N, int E, class F>
+__device__ __forceinline__ void fft_regs_regs_m(float2 (&x)[E], float2 *b0, float2 *b1, int gl, int id,
+                                                const float2 *__restrict__ tw, F &&f) {
+    fpass_first_regs<N, E>(x, b0, gl);
+    group_sync<GShape<N, E>::TPF>(id);
+    float2 *cur = b0, *nxt = b1;
+    const int logP = fpass_middle<N, E>(cur, nxt, gl, id, tw);
+    fpass_last_regs_m<N, E>(cur, logP, gl, tw, x, f);
 }
 
 // A group FFT of the natural-order input in b1 into x[] (x[m] = f(q, X_q));
@@ -498,12 +516,15 @@ __global__ void __launch_bounds__(P2Shape<N, E, NNW>::THREADS, 1) k2p_step(const
                 }
                 if (seg && live) {
                     // the state after step n, tiled, for the adjoint's segment (a thread's own
-                    // modes, or any after the Hermitian part's barrier)
+                    // modes, or any after the Hermitian part's barrier), and the step's unit noise
                     C *so = a.seg_state + (size_t)(n + 1) * a.seg_cstride;
+                    C *sz = a.seg_noise && noisy ? a.seg_noise + (size_t)n * a.seg_cstride : nullptr;
 #pragma unroll 4
                     for (int m = 0; m < E; ++m) {
                         const int ky = gl + m * TPF;
-                        so[((size_t)(kx >> 2) * N + ky) * 4 + (kx & 3)] = STc[ky];
+                        const size_t o = ((size_t)(kx >> 2) * N + ky) * 4 + (kx & 3);
+                        so[o] = STc[ky];
+                        if (sz) sz[o] = nzc[ky];
                     }
                 }
             } else {

@@ -206,6 +206,7 @@ def test_fused_adjoint_launch_changes_no_field_bit(shape, prec):
     out = {}
     for fuse in (1, 0):
         s = _gpu_system(shape, prec, dt, seed)
+        s.set_tuning("persist_adj", 0)   # the per-step launches (the persistent pass has none to fuse)
         s.set_tuning("fuse_adjoint", fuse)
         s.adjoint_forward(n)
         l0 = s.launch_count
@@ -308,6 +309,7 @@ def test_adjoint_column_parts_on_fft_groups_match_the_generic_kernel(shape):
     for groups in (1, 0):
         for fuse in (1, 0):
             s = _gpu_system(shape, "f32", dt, seed)
+            s.set_tuning("persist_adj", 0)   # the column kernels themselves
             s.set_tuning("adj_col2", groups)
             s.set_tuning("fuse_adjoint", fuse)
             s.adjoint_forward(n)
@@ -320,3 +322,39 @@ def test_adjoint_column_parts_on_fft_groups_match_the_generic_kernel(shape):
     np.testing.assert_allclose(out[1, 1][0], out[1, 0][0], rtol=1e-9)
     assert rel(out[1, 1][1], out[0, 1][1]) < 1e-4
     assert np.max(np.abs(out[1, 1][0] - out[0, 1][0]) / np.abs(out[0, 1][0])) < 1e-4
+
+
+@pytest.mark.parametrize("shape,noisy", [((256, 256), True), ((512, 512), True), ((1024, 1024), True),
+                                         ((256, 256), False)])
+def test_persistent_backward_pass(shape, noisy):
+    # each recomputed segment's backward pass as one persistent launch (the default on
+    # the persistent path) against the per-step launches (column kernel on FFT groups,
+    # fused B + A) and the FP64 oracle; 13 steps = segments of 4, 4, 4 and 1
+    dt, seed, n = 0.02, 23, 13
+    params = dict(PARAMS) if noisy else dict(PARAMS, D=0.0)
+    m = O.model_b(shape, dt=dt, seed=seed, **params)
+    phi0 = O.to_spectrum(m, O.init_uniform(m, -0.3, 0.3))
+    c = _weights(shape)
+    lamT = 2.0 * c * O.run(m, phi0, 0, n) / m.n_sites
+    out = {}
+    for persist_adj in (1, 0):
+        s = pss().model_b(shape, dt=dt, seed=seed, precision="f32", **params)
+        s.init_uniform(0, -0.3, 0.3)
+        assert s.step_path == "persist2d"
+        s.set_tuning("persist_adj", persist_adj)
+        s.adjoint_forward(n)
+        l0 = s.launch_count
+        grads, lam0 = s.adjoint_backward(O.half(lamT), 4)
+        out[persist_adj] = (grads, lam0, s.launch_count - l0)
+        assert s.get_step() == n
+    # the same recursion and transforms (the element-wise arithmetic may fuse
+    # multiply-adds differently): FP32 rounding apart
+    assert rel(out[1][1], out[0][1]) < 1e-5
+    np.testing.assert_allclose(out[1][0], out[0][0], rtol=1e-5)
+    assert out[1][2] < out[0][2], (out[1][2], out[0][2])
+    if shape[0] <= 512:
+        lam0, g = O.adjoint(m, phi0, 0, n, lamT)
+        ref = np.array([g[1], -g[6], g[2], g[10]])
+        assert rel(out[1][1], O.half(lam0)) < 1e-3
+        k = 4 if noisy else 3
+        assert np.max(np.abs(out[1][0][:k] - ref[:k]) / np.abs(ref[:k])) < 1e-3, (out[1][0], ref)
