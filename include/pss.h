@@ -255,6 +255,11 @@ int pss_time_kernels(pss_system *s, int64_t n, double *avg_ms);
  *                 most one per column pair or row pair; values below the
  *                 smallest count that keeps every column and row pair in
  *                 shared memory are raised to it; at most the SMs);
+ *   "persist_adj" on the persistent path, the backward pass of each
+ *                 recomputed segment of pss_adjoint_backward runs as one
+ *                 cooperative launch (1, default; the segment's forward run
+ *                 then also keeps each step's noise) or as launches per
+ *                 step (0); they agree to FP32 rounding;
  *   "adj_col2"    the column parts of the FP32 2D adjoint run on FFT groups,
  *                 one column pair per CTA (1, default) or on the generic
  *                 column kernel (0); they agree to FP32 rounding;

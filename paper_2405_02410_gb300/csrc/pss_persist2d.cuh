@@ -389,7 +389,16 @@ __global__ void __launch_bounds__(P2Shape<N, E, NNW>::THREADS, 1) k2p_step(const
 
     // ================= transform warps =================
     const int g = t / TPF, gl = t - g * TPF;   // FFT group and its thread
-    for (int i = t; i < N; i += NMAIN) TW[i] = a.tw[twiddle_offset(N, E) + i];
+    {
+        constexpr int PT = (N + NMAIN - 1) / NMAIN;
+        C tv[PT];
+#pragma unroll
+        for (int q = 0; q < PT; ++q)
+            if (t + q * NMAIN < N) tv[q] = __ldg(a.tw + twiddle_offset(N, E) + t + q * NMAIN);
+#pragma unroll
+        for (int q = 0; q < PT; ++q)
+            if (t + q * NMAIN < N) TW[t + q * NMAIN] = tv[q];
+    }
     const int kmx = fp.kmax[0], kmy = fp.kmax[1];
     const float scale = sp.inv_nsites;
     const bool has_product = fp.power > 0;
@@ -400,20 +409,19 @@ __global__ void __launch_bounds__(P2Shape<N, E, NNW>::THREADS, 1) k2p_step(const
         dtM[i] = sp.dt * fp.M[i];
     }
     // the state (and, without a prologue, the first step's noise) of each column
-    // pair: 16 bytes per (pair, ky) of the tiled arrays (the two columns are neighbours)
-    for (int i = t; i < (u1 - u0) * N; i += NMAIN) {
-        const int uu = i >> ilog2(N), ky = i & (N - 1), kx0 = 2 * (u0 + uu);
+    // pair: 16 bytes per (pair, ky) of the tiled arrays (the two columns are
+    // neighbours); all of a thread's loads are issued first (their DRAM round trips
+    // overlap each other and the update factors below), the stores follow
+    constexpr int PERS = 2 * N / NMAIN;   // (pair, ky) items per thread, at most
+    const bool load_xi = first == 1 && noisy;
+    float4 sv[PERS], xv[PERS];
+#pragma unroll
+    for (int q = 0; q < PERS; ++q) {
+        const int i = t + q * NMAIN, uu = i >> ilog2(N), ky = i & (N - 1), kx0 = 2 * (u0 + uu);
         const size_t o = ((size_t)(kx0 >> 2) * N + ky) * 4 + (kx0 & 3);
-        float4 v = __ldcg(reinterpret_cast<const float4 *>(a.state + o));
-        if (kx0 + 1 >= sp.hx) { v.z = 0.f; v.w = 0.f; }   // past Nx/2
-        ST[(2 * uu) * N + ky] = mk<float>(v.x, v.y);
-        ST[(2 * uu + 1) * N + ky] = mk<float>(v.z, v.w);
-        if (first == 1 && noisy) {
-            float4 x = __ldcg(reinterpret_cast<const float4 *>(a.xi + o));
-            if (kx0 + 1 >= sp.hx) { x.z = 0.f; x.w = 0.f; }
-            NZ[(2 * uu) * N + ky] = mk<float>(x.x, x.y);
-            NZ[(2 * uu + 1) * N + ky] = mk<float>(x.z, x.w);
-        }
+        const bool in = i < (u1 - u0) * N;
+        sv[q] = in ? __ldcg(reinterpret_cast<const float4 *>(a.state + o)) : make_float4(0.f, 0.f, 0.f, 0.f);
+        xv[q] = in && load_xi ? __ldcg(reinterpret_cast<const float4 *>(a.xi + o)) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
     if constexpr (MODE == 0) {
         for (int c = 0; c < ncs; ++c) {
@@ -423,6 +431,19 @@ __global__ void __launch_bounds__(P2Shape<N, E, NNW>::THREADS, 1) k2p_step(const
                 update_factors<float>(q2sum(qx, fmul(float(signed_k(ky, N)), sp.gy)), dtO, dtM, m, gg);
                 MG[c * N + ky] = make_float2(m, gg);
             }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < PERS; ++q) {
+        const int i = t + q * NMAIN, uu = i >> ilog2(N), ky = i & (N - 1), kx0 = 2 * (u0 + uu);
+        if (i >= (u1 - u0) * N) break;
+        float4 v = sv[q], x = xv[q];
+        if (kx0 + 1 >= sp.hx) { v.z = 0.f; v.w = 0.f; x.z = 0.f; x.w = 0.f; }   // past Nx/2
+        ST[(2 * uu) * N + ky] = mk<float>(v.x, v.y);
+        ST[(2 * uu + 1) * N + ky] = mk<float>(v.z, v.w);
+        if (load_xi) {
+            NZ[(2 * uu) * N + ky] = mk<float>(x.x, x.y);
+            NZ[(2 * uu + 1) * N + ky] = mk<float>(x.z, x.w);
         }
     }
     main_sync<NMAIN>();

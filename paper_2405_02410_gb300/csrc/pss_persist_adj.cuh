@@ -78,10 +78,19 @@ __global__ void __launch_bounds__(P2AdjShape<N, E>::THREADS, 1) k2p_adj(const P2
     }
     // element ky of column kx in a tiled array; of a column-major one
     auto tiled = [&](int kx, int ky) { return ((size_t)(kx >> 2) * N + ky) * 4 + (kx & 3); };
-    // the adjoint field of the CTA's columns (zero past Nx/2)
-    for (int i = t; i < ncs * N; i += NT) {
-        const int c = i >> ilog2(N), ky = i & (N - 1), kx = 2 * u0 + c;
-        X3[i] = kx < sp.hx ? __ldcg(a.L + tiled(kx, ky)) : mk<float>(0.f, 0.f);
+    // the adjoint field of the CTA's columns (zero past Nx/2): all of a thread's loads
+    // first, then the stores
+    {
+        constexpr int PX = NG * N / NT;
+        C xv[PX];
+#pragma unroll
+        for (int q = 0; q < PX; ++q) {
+            const int i = t + q * NT, c = i >> ilog2(N), ky = i & (N - 1), kx = 2 * u0 + c;
+            xv[q] = i < ncs * N && kx < sp.hx ? __ldcg(a.L + tiled(kx, ky)) : mk<float>(0.f, 0.f);
+        }
+#pragma unroll
+        for (int q = 0; q < PX; ++q)
+            if (t + q * NT < ncs * N) X3[t + q * NT] = xv[q];
     }
     __syncthreads();
     if (s_abort) return;
