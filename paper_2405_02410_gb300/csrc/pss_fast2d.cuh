@@ -249,6 +249,136 @@ __device__ __forceinline__ void fft_fwd_group_sink(float2 *b0, float2 *b1, int g
     }
 }
 
+// ---- group FFTs with their first or last pass on registers ----------------
+// Thread gl of a group takes input points gl + TPF m (m = 0..E-1) in the first
+// pass of a transform, and the last pass leaves it with output points
+// gl + TPF (s + BPT r) of its butterflies s and outputs r: the same set.  So
+// a transform can start from values loaded from global memory, or from the
+// outputs of the transform before it, without a round trip through shared
+// memory: x[m] holds point gl + TPF m.  The butterflies and their arithmetic
+// are those of fpass, so the results are the same bits.
+
+// first pass (radix E, no twiddles) from x[] into dst (padded), as fpass<N, E, E, false, false, true>
+template <int N, int E>
+__device__ __forceinline__ void fpass_first_regs(float2 (&x)[E], float2 *dst, int gl) {
+    using S = GShape<N, E>;
+    dft_reg<E, -1, float>(x);
+    const int j = gl << S::LOGE;
+#pragma unroll
+    for (int r = 0; r < E; ++r) dst[padp<S::PS>(j + r)] = x[r];
+}
+
+// the middle passes (radix E, twiddled, padded in and out) after the first
+// pass wrote cur; on return cur is the buffer the last pass reads and nxt
+// the other one.  Returns log2 of the points combined so far.
+template <int N, int E>
+__device__ __forceinline__ int fpass_middle(float2 *&cur, float2 *&nxt, int gl, int id,
+                                            const float2 *__restrict__ tw) {
+    using S = GShape<N, E>;
+    int logP = S::LOGE;
+#pragma unroll 1
+    for (; logP + S::LOGRL < S::LOG; logP += S::LOGE) {
+        fpass<N, E, E, true, true, true>(cur, nxt, logP, gl, tw, 0);
+        group_sync<S::TPF>(id);
+        float2 *tmp = cur;
+        cur = nxt;
+        nxt = tmp;
+    }
+    return logP;
+}
+
+// last pass (radix RL, twiddled) into x[]: x[m] = f(q, m, X_q), q = gl + TPF m
+// (m a constant after unrolling: it may index the caller's register arrays)
+template <int N, int E, class F>
+__device__ __forceinline__ void fpass_last_regs_m(const float2 *src, int logP, int gl, const float2 *__restrict__ tw,
+                                                  float2 (&x)[E], F &&f) {
+    using S = GShape<N, E>;
+    constexpr int R = S::RL, TPF = S::TPF, STRIDE = N / R, BPT = STRIDE / TPF, LOGR = ilog2(R);
+    static_assert(BPT * R == E, "a thread's last-pass outputs are its first-pass inputs");
+    const int P = 1 << logP;
+#pragma unroll
+    for (int s = 0; s < BPT; ++s) {
+        const int i = gl + TPF * s, k = i & (P - 1);
+        float2 u[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) u[r] = src[padp<S::PS>(i + r * STRIDE)];
+        const float2 *__restrict__ twp = tw + (P - E) + k;
+#pragma unroll
+        for (int r = 1; r < R; ++r) u[r] = cmul<float>(u[r], twp[(r - 1) * P]);
+        dft_reg<R, -1, float>(u);
+        const int j = ((i - k) << LOGR) + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) x[s + BPT * r] = f(j + r * P, s + BPT * r, u[r]);
+    }
+}
+// the same with x[m] = f(q, X_q)
+template <int N, int E, class F>
+__device__ __forceinline__ void fpass_last_regs(const float2 *src, int logP, int gl, const float2 *__restrict__ tw,
+                                                float2 (&x)[E], F &&f) {
+    fpass_last_regs_m<N, E>(src, logP, gl, tw, x, [&](int q, int, float2 v) { return f(q, v); });
+}
+
+// A group FFT from x[] (its first pass writes b0, which must be free) whose
+// last pass hands its outputs to sink(q, value) (no barrier after it).
+template <int N, int E, class Sink>
+__device__ __forceinline__ void fft_regs_sink(float2 (&x)[E], float2 *b0, float2 *b1, int gl, int id,
+                                              const float2 *__restrict__ tw, Sink &&sink) {
+    fpass_first_regs<N, E>(x, b0, gl);
+    group_sync<GShape<N, E>::TPF>(id);
+    float2 *cur = b0, *nxt = b1;
+    const int logP = fpass_middle<N, E>(cur, nxt, gl, id, tw);
+    fpass_sink<N, E, GShape<N, E>::RL>(cur, logP, gl, tw, sink);
+}
+
+// A group FFT from x[] back into x[] (x[m] = f(q, X_q)); the last pass reads
+// b1 when the transform has an odd number of passes, else b0 (no barrier after it).
+template <int N, int E, class F>
+__device__ __forceinline__ void fft_regs_regs(float2 (&x)[E], float2 *b0, float2 *b1, int gl, int id,
+                                              const float2 *__restrict__ tw, F &&f) {
+    fpass_first_regs<N, E>(x, b0, gl);
+    group_sync<GShape<N, E>::TPF>(id);
+    float2 *cur = b0, *nxt = b1;
+    const int logP = fpass_middle<N, E>(cur, nxt, gl, id, tw);
+    fpass_last_regs<N, E>(cur, logP, gl, tw, x, f);
+}
+
+// fft_regs_regs with x[m] = f(q, m, X_q)
+template <int N, int E, class F>
+__device__ __forceinline__ void fft_regs_regs_m(float2 (&x)[E], float2 *b0, float2 *b1, int gl, int id,
+                                                const float2 *__restrict__ tw, F &&f) {
+    fpass_first_regs<N, E>(x, b0, gl);
+    group_sync<GShape<N, E>::TPF>(id);
+    float2 *cur = b0, *nxt = b1;
+    const int logP = fpass_middle<N, E>(cur, nxt, gl, id, tw);
+    fpass_last_regs_m<N, E>(cur, logP, gl, tw, x, f);
+}
+
+// A group FFT of the natural-order input in b1 into x[] (x[m] = f(q, X_q));
+// the last pass reads the same buffer as fft_regs_regs's (no barrier after it).
+template <int N, int E, class F>
+__device__ __forceinline__ void fft_smem_regs(float2 *b0, float2 *b1, int gl, int id, const float2 *__restrict__ tw,
+                                              float2 (&x)[E], F &&f) {
+    fpass<N, E, E, false, false, true>(b1, b0, 0, gl, tw, 0);
+    group_sync<GShape<N, E>::TPF>(id);
+    float2 *cur = b0, *nxt = b1;
+    const int logP = fpass_middle<N, E>(cur, nxt, gl, id, tw);
+    fpass_last_regs<N, E>(cur, logP, gl, tw, x, f);
+}
+
+// A group FFT from x[] (first pass into b0, which must be free) whose result,
+// in natural order, is returned in one of the two buffers, visible to the group.
+template <int N, int E>
+__device__ __forceinline__ float2 *fft_regs_smem(float2 (&x)[E], float2 *b0, float2 *b1, int gl, int id,
+                                                 const float2 *__restrict__ tw) {
+    fpass_first_regs<N, E>(x, b0, gl);
+    group_sync<GShape<N, E>::TPF>(id);
+    float2 *cur = b0, *nxt = b1;
+    const int logP = fpass_middle<N, E>(cur, nxt, gl, id, tw);
+    fpass<N, E, GShape<N, E>::RL, true, true, false>(cur, nxt, logP, gl, tw, 0);
+    group_sync<GShape<N, E>::TPF>(id);
+    return nxt;
+}
+
 // ---------------------------------------------------------------------------
 // k2_col: y transforms of one tile (4 columns) fused with the update.
 // Threads: four FFT groups of TPF threads (group c = column c, barrier 1 + c),
@@ -658,10 +788,15 @@ __global__ void __launch_bounds__(E == 32 ? 512 : 1024) k2_row(const RowArgs<flo
         mbar_poll(bar, 0);
         return;
     }
-    // ---- z' = F(Y) = conj(z) = a - i b; its last pass stores u = a^p + i b^p,
-    // the product of both rows (and, with real_out, the rows a and b
-    // themselves); then W = F(u).  Both results land in b1.
-    {
+    // ---- z' = F(Y) = conj(z) = a - i b; its last pass forms u = a^p + i b^p,
+    // the product of both rows (ROW_ADJ: p a^(p-1) Re z' + i p b^(p-1) (-Im z'),
+    // with the stored real rows a, b), and stores the rows a and b themselves
+    // when real_out is set; then W = F(u).  With radix-8 and radix-32 passes u
+    // goes to W's first pass in registers and W lands in the group's first
+    // buffer; the radix-16 kernels (64 registers per thread at 1024 threads)
+    // pass u through shared memory and W lands in the second buffer.
+    constexpr bool CHAIN = E != 16;
+    if constexpr (!CHAIN) {
         C *b0 = WBUF + Row2Smem<N, E>::base(g, TILED), *b1 = b0 + S::BUF;
         const C *src = b1;
         C *p0 = b0, *p1 = b1;
@@ -684,12 +819,42 @@ __global__ void __launch_bounds__(E == 32 ? 512 : 1024) k2_row(const RowArgs<flo
             p0 = o == b0 ? b1 : b0;
             p1 = o;
         }
+    } else {
+        C *b0 = WBUF + Row2Smem<N, E>::base(g, TILED), *b1 = b0 + S::BUF;
+        float *ra = nullptr, *rb = nullptr;
+        const float *ma = nullptr, *mb = nullptr;
+        if (!TILED && a.real_out) {
+            ra = a.real_out + (size_t)slot * a.real_stride + (size_t)(r0 + 2 * g) * N;
+            rb = ra + N;
+        }
+        if (adj) {
+            ma = MS + (size_t)(2 * g) * N;
+            mb = ma + N;
+        }
+        C x[E];
+        fft_smem_regs<N, E>(b0, b1, gl, 1 + g, TW, x, [&](int q, C v) {
+            if constexpr (adj) {
+                v = mk<float>(float(power) * ipow<float>(ma[q], power - 1) * v.x,
+                              float(power) * ipow<float>(mb[q], power - 1) * (-v.y));
+            } else {
+                if (ra) {
+                    ra[q] = v.x;
+                    rb[q] = -v.y;
+                }
+                if (power > 0) v = mk<float>(pow_p(v.x, power), pow_p(-v.y, power));
+            }
+            return v;
+        });
+        // the R2C's first pass writes the buffer the C2R's last pass did not read;
+        // with either pass count the result is in b0
+        constexpr bool LB1 = SinkShape<N, E>::LAST_READS_B1;
+        fft_regs_smem<N, E>(x, LB1 ? b0 : b1, LB1 ? b1 : b0, gl, 1 + g, TW);
     }
     asm volatile("bar.sync 15, %0;" ::"r"(nf) : "memory");
     // ---- split into the half spectra of the two rows:
     // A_k = (W_k + conj W_{N-k}) / 2, B_k = (W_k - conj W_{N-k}) / 2i
     auto split = [&](int k, int j) {
-        const C *Wj = WBUF + Row2Smem<N, E>::base(j, TILED) + S::BUF;
+        const C *Wj = WBUF + Row2Smem<N, E>::base(j, TILED) + (CHAIN ? 0 : S::BUF);
         const C wk = Wj[k], wm = Wj[(N - k) & (N - 1)];
         return make_float4(0.5f * (wk.x + wm.x), 0.5f * (wk.y - wm.y), 0.5f * (wk.y + wm.y), -0.5f * (wk.x - wm.x));
     };

@@ -172,136 +172,6 @@ __device__ __forceinline__ uint32_t empty_parity(int n) { return (uint32_t)(((n 
 // derivative factor i q of a mode (q = 0 at a Nyquist index, reading R14)
 __device__ __forceinline__ float dq(int k, int n, float g) { return 2 * k == n ? 0.f : fmul(float(signed_k(k, n)), g); }
 
-// ---- group FFTs with their first or last pass on registers ----------------
-// Thread gl of a group takes input points gl + TPF m (m = 0..E-1) in the first
-// pass of a transform, and the last pass leaves it with output points
-// gl + TPF (s + BPT r) of its butterflies s and outputs r: the same set.  So
-// a transform can start from values loaded from global memory, or from the
-// outputs of the transform before it, without a round trip through shared
-// memory: x[m] holds point gl + TPF m.  The butterflies and their arithmetic
-// are those of fpass, so the results are the same bits.
-
-// first pass (radix E, no twiddles) from x[] into dst (padded), as fpass<N, E, E, false, false, true>
-template <int N, int E>
-__device__ __forceinline__ void fpass_first_regs(float2 (&x)[E], float2 *dst, int gl) {
-    using S = GShape<N, E>;
-    dft_reg<E, -1, float>(x);
-    const int j = gl << S::LOGE;
-#pragma unroll
-    for (int r = 0; r < E; ++r) dst[padp<S::PS>(j + r)] = x[r];
-}
-
-// the middle passes (radix E, twiddled, padded in and out) after the first
-// pass wrote cur; on return cur is the buffer the last pass reads and nxt
-// the other one.  Returns log2 of the points combined so far.
-template <int N, int E>
-__device__ __forceinline__ int fpass_middle(float2 *&cur, float2 *&nxt, int gl, int id,
-                                            const float2 *__restrict__ tw) {
-    using S = GShape<N, E>;
-    int logP = S::LOGE;
-#pragma unroll 1
-    for (; logP + S::LOGRL < S::LOG; logP += S::LOGE) {
-        fpass<N, E, E, true, true, true>(cur, nxt, logP, gl, tw, 0);
-        group_sync<S::TPF>(id);
-        float2 *tmp = cur;
-        cur = nxt;
-        nxt = tmp;
-    }
-    return logP;
-}
-
-// last pass (radix RL, twiddled) into x[]: x[m] = f(q, m, X_q), q = gl + TPF m
-// (m a constant after unrolling: it may index the caller's register arrays)
-template <int N, int E, class F>
-__device__ __forceinline__ void fpass_last_regs_m(const float2 *src, int logP, int gl, const float2 *__restrict__ tw,
-                                                  float2 (&x)[E], F &&f) {
-    using S = GShape<N, E>;
-    constexpr int R = S::RL, TPF = S::TPF, STRIDE = N / R, BPT = STRIDE / TPF, LOGR = ilog2(R);
-    static_assert(BPT * R == E, "a thread's last-pass outputs are its first-pass inputs");
-    const int P = 1 << logP;
-#pragma unroll
-    for (int s = 0; s < BPT; ++s) {
-        const int i = gl + TPF * s, k = i & (P - 1);
-        float2 u[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) u[r] = src[padp<S::PS>(i + r * STRIDE)];
-        const float2 *__restrict__ twp = tw + (P - E) + k;
-#pragma unroll
-        for (int r = 1; r < R; ++r) u[r] = cmul<float>(u[r], twp[(r - 1) * P]);
-        dft_reg<R, -1, float>(u);
-        const int j = ((i - k) << LOGR) + k;
-#pragma unroll
-        for (int r = 0; r < R; ++r) x[s + BPT * r] = f(j + r * P, s + BPT * r, u[r]);
-    }
-}
-// the same with x[m] = f(q, X_q)
-template <int N, int E, class F>
-__device__ __forceinline__ void fpass_last_regs(const float2 *src, int logP, int gl, const float2 *__restrict__ tw,
-                                                float2 (&x)[E], F &&f) {
-    fpass_last_regs_m<N, E>(src, logP, gl, tw, x, [&](int q, int, float2 v) { return f(q, v); });
-}
-
-// A group FFT from x[] (its first pass writes b0, which must be free) whose
-// last pass hands its outputs to sink(q, value) (no barrier after it).
-template <int N, int E, class Sink>
-__device__ __forceinline__ void fft_regs_sink(float2 (&x)[E], float2 *b0, float2 *b1, int gl, int id,
-                                              const float2 *__restrict__ tw, Sink &&sink) {
-    fpass_first_regs<N, E>(x, b0, gl);
-    group_sync<GShape<N, E>::TPF>(id);
-    float2 *cur = b0, *nxt = b1;
-    const int logP = fpass_middle<N, E>(cur, nxt, gl, id, tw);
-    fpass_sink<N, E, GShape<N, E>::RL>(cur, logP, gl, tw, sink);
-}
-
-// A group FFT from x[] back into x[] (x[m] = f(q, X_q)); the last pass reads
-// b1 when the transform has an odd number of passes, else b0 (no barrier after it).
-template <int N, int E, class F>
-__device__ __forceinline__ void fft_regs_regs(float2 (&x)[E], float2 *b0, float2 *b1, int gl, int id,
-                                              const float2 *__restrict__ tw, F &&f) {
-    fpass_first_regs<N, E>(x, b0, gl);
-    group_sync<GShape<N, E>::TPF>(id);
-    float2 *cur = b0, *nxt = b1;
-    const int logP = fpass_middle<N, E>(cur, nxt, gl, id, tw);
-    fpass_last_regs<N, E>(cur, logP, gl, tw, x, f);
-}
-
-// fft_regs_regs with x[m] = f(q, m, X_q)
-template <int N, int E, class F>
-__device__ __forceinline__ void fft_regs_regs_m(float2 (&x)[E], float2 *b0, float2 *b1, int gl, int id,
-                                                const float2 *__restrict__ tw, F &&f) {
-    fpass_first_regs<N, E>(x, b0, gl);
-    group_sync<GShape<N, E>::TPF>(id);
-    float2 *cur = b0, *nxt = b1;
-    const int logP = fpass_middle<N, E>(cur, nxt, gl, id, tw);
-    fpass_last_regs_m<N, E>(cur, logP, gl, tw, x, f);
-}
-
-// A group FFT of the natural-order input in b1 into x[] (x[m] = f(q, X_q));
-// the last pass reads the same buffer as fft_regs_regs's (no barrier after it).
-template <int N, int E, class F>
-__device__ __forceinline__ void fft_smem_regs(float2 *b0, float2 *b1, int gl, int id, const float2 *__restrict__ tw,
-                                              float2 (&x)[E], F &&f) {
-    fpass<N, E, E, false, false, true>(b1, b0, 0, gl, tw, 0);
-    group_sync<GShape<N, E>::TPF>(id);
-    float2 *cur = b0, *nxt = b1;
-    const int logP = fpass_middle<N, E>(cur, nxt, gl, id, tw);
-    fpass_last_regs<N, E>(cur, logP, gl, tw, x, f);
-}
-
-// A group FFT from x[] (first pass into b0, which must be free) whose result,
-// in natural order, is returned in one of the two buffers, visible to the group.
-template <int N, int E>
-__device__ __forceinline__ float2 *fft_regs_smem(float2 (&x)[E], float2 *b0, float2 *b1, int gl, int id,
-                                                 const float2 *__restrict__ tw) {
-    fpass_first_regs<N, E>(x, b0, gl);
-    group_sync<GShape<N, E>::TPF>(id);
-    float2 *cur = b0, *nxt = b1;
-    const int logP = fpass_middle<N, E>(cur, nxt, gl, id, tw);
-    fpass<N, E, GShape<N, E>::RL, true, true, false>(cur, nxt, logP, gl, tw, 0);
-    group_sync<GShape<N, E>::TPF>(id);
-    return nxt;
-}
-
 template <int N, int E, int NNW, int MODE>
 __global__ void __launch_bounds__(P2Shape<N, E, NNW>::THREADS, 1) k2p_step(const P2Args a) {
     using C = float2;
