@@ -260,6 +260,8 @@ int pss_time_kernels(pss_system *s, int64_t n, double *avg_ms);
  *                 cooperative launch (1, default; the segment's forward run
  *                 then also keeps each step's noise) or as launches per
  *                 step (0); they agree to FP32 rounding;
+ *   "adj_radix"   FFT pass radix of that persistent backward pass (8 or
+ *                 16; 0, default: the forward step's);
  *   "adj_col2"    the column parts of the FP32 2D adjoint run on FFT groups,
  *                 one column pair per CTA (1, default) or on the generic
  *                 column kernel (0); they agree to FP32 rounding;

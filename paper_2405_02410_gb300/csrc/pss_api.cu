@@ -134,6 +134,7 @@ struct pss_system {
     int tune_test_timeout = 0;               // check of the bounded waits: one CTA's wait runs out (tests)
     int tune_persist = 1;                    // square FP32 2D systems: a run of steps as one persistent launch
     int tune_adj_col2 = 1;
+    int tune_adj_radix = 0;                  // FFT radix of that backward pass (8 or 16; 0: the forward's)
     int tune_persist_adj = 1;                // FP32 2D adjoint on the persistent path: a segment's backward pass in one launch                   // FP32 2D adjoint: column parts on FFT groups (0: generic kernel)
     int tune_persist_blocks = 0;             // its CTAs (0: every SM, at most one CTA per column pair or row pair)
     int coop = 0;                            // the device takes cooperative launches
@@ -1567,7 +1568,7 @@ template <typename T> int record_adjoint_segment(pss_system *s, cudaStream_t str
             b.d_status = s->d_status;
             b.gs = s->gs;
             b.len = (int)len;
-            e = launch_p2_adj(b, s->nx, p2_radix(s), p2_blocks(s), stream);
+            e = launch_p2_adj(b, s->nx, s->tune_adj_radix ? s->tune_adj_radix : p2_radix(s), p2_blocks(s), stream);
             s->launches++;
             if (e != cudaSuccess) return cuda_fail(s, e, "k2p_adj launch");
             return PSS_OK;
@@ -2128,6 +2129,10 @@ int pss_set_tuning(pss_system *s, const char *key, int value) {
     else if (k == "persist") s->tune_persist = value ? 1 : 0;
     else if (k == "adj_col2") s->tune_adj_col2 = value ? 1 : 0;
     else if (k == "persist_adj") s->tune_persist_adj = value ? 1 : 0;
+    else if (k == "adj_radix") {
+        if (value != 0 && value != 8 && value != 16) return fail(s, PSS_EINVAL, "adj_radix is 8 or 16 (0 = automatic)");
+        s->tune_adj_radix = value;
+    }
     else if (k == "persist_blocks") {
         if (value > 1024) return fail(s, PSS_EINVAL, "persist_blocks is at most 1024 (0 = automatic)");
         s->tune_persist_blocks = value;

@@ -194,16 +194,32 @@ __global__ void __launch_bounds__(P2AdjShape<N, E>::THREADS, 1) k2p_adj(const P2
         // ================= column phase: each group on its own column =================
         // part B of step ib (it >= 1): lambda = mu + F_y[w] / N on the kept modes, then the
         // Hermitian part on kx = 0, Nx/2; part A of step ia (ia >= 0): mu = g lambda, the
-        // gradient terms, conj(nu) = conj(dt M mu) from the last pass of F_y of the step's
-        // product, and nu back along y from registers.  A thread owns the modes
-        // ky = gl + TPF m of its group's column in both parts.
+        // gradient terms, conj(nu) = conj(dt M mu) with F_y of the step's product, and nu
+        // back along y from registers.  A thread owns the modes ky = gl + TPF m of its
+        // group's column in both parts.  A CTA with at most NG / 2 columns lets its other
+        // groups transform the product (part A's F_y) while the column's group runs part B
+        // ("split"); otherwise the column's group runs both, part A's arithmetic on the last
+        // pass of that transform.
         {
-            const int kx = 2 * u0 + g;
-            if (g < ncs && kx < sp.hx) {
-                C *b0 = gb, *b1 = gb + S::BUF;
-                C *x3 = X3 + g * N;
-                const bool kxk = kx <= kmx, herm = kx == 0 || 2 * kx == sp.nx;
-                C x[E];
+            constexpr int RES = S::NPASS % 2 == 1 ? 0 : S::BUF;   // fft_regs_smem's result in its buffers
+            const bool split = ncs <= NG / 2;
+            const bool lead = !split || g < NG / 2;                // the column's own group
+            const int col = lead ? g : g - NG / 2;
+            const int kx = 2 * u0 + col;
+            const bool mine = col < ncs && kx < sp.hx;
+            C *b0 = gb, *b1 = gb + S::BUF;
+            C *x3 = X3 + col * N;
+            const bool kxk = kx <= kmx, herm = kx == 0 || 2 * kx == sp.nx;
+            C x[E];
+            if (!lead && mine && ia >= 0) {
+                // the step's product (column-major) transformed by this helper group
+                const C *__restrict__ pr = a.seg_prod + (size_t)ia * a.cstride + (size_t)kx * N + gl;
+#pragma unroll
+                for (int m = 0; m < E; ++m) x[m] = __ldcg(pr + m * TPF);
+                fft_regs_smem<N, E>(x, b0, b1, gl, 1 + g, TW);
+            }
+            C ph[E], xi[E];
+            if (lead && mine) {
                 if (it > 0) {
 #pragma unroll
                     for (int m = 0; m < E; ++m) x[m] = __ldcg(a.W + tiled(kx, gl + m * TPF));
@@ -225,56 +241,68 @@ __global__ void __launch_bounds__(P2AdjShape<N, E>::THREADS, 1) k2p_adj(const P2
                     }
                 }
                 if (ia >= 0) {
-                    // the step's product (column-major), the state after it and its noise
-                    // (tiled) at the thread's modes, all loads in flight together
-                    C ph[E], xi[E];
+                    // the state after step ia and its noise (tiled) at the thread's modes, and
+                    // (not split) the step's product, all loads in flight together
                     const C *__restrict__ pr = a.seg_prod + (size_t)ia * a.cstride + (size_t)kx * N + gl;
                     const C *__restrict__ phn = a.seg_state + (size_t)(ia + 1) * a.cstride;
                     const C *__restrict__ nzn = noisy ? a.seg_noise + (size_t)ia * a.cstride : nullptr;
 #pragma unroll
                     for (int m = 0; m < E; ++m) {
                         const int ky = gl + m * TPF;
-                        x[m] = __ldcg(pr + m * TPF);
+                        if (!split) x[m] = __ldcg(pr + m * TPF);
                         ph[m] = __ldcg(phn + tiled(kx, ky));
                         xi[m] = noisy ? cscale<float>(__ldcg(nzn + tiled(kx, ky)), sigma0) : mk<float>(0.f, 0.f);
                     }
-                    const float qx = float(kx) * sp.gx;
-                    const float wgt = herm ? 1.f : 2.f;
-                    float st[11];
-#pragma unroll
-                    for (int k = 0; k < 11; ++k) st[k] = 0.f;
-                    fft_regs_regs_m<N, E>(x, b0, b1, gl, 1 + g, TW, [&](int ky, int m, C pv) {
-                        const float qy = float(signed_k(ky, N)) * sp.gy;
-                        const float q2 = qx * qx + qy * qy;
-                        const float gg = 1.f / (1.f + sp.dt * poly5<float>(fp.O, q2));
-                        const C mu = cscale<float>(x3[ky], gg);
-                        x3[ky] = mu;
-                        const float dtM = fp.power > 0 ? sp.dt * poly5<float>(fp.M, q2) : 0.f;
-                        const float a_phi = wgt * sp.dt * (mu.x * ph[m].x + mu.y * ph[m].y);
-                        const float a_P = wgt * sp.dt * (mu.x * pv.x + mu.y * pv.y);
-                        float q2k = 1.f;
-#pragma unroll
-                        for (int k = 0; k < 5; ++k) {
-                            st[k] -= q2k * a_phi;
-                            st[5 + k] += q2k * a_P;
-                            q2k *= q2;
-                        }
-                        st[10] += wgt * (mu.x * xi[m].x + mu.y * xi[m].y);
-                        return mk<float>(mu.x * dtM, -mu.y * dtM);   // conj(nu)
-                    });
-                    // the step's terms into the thread's compensated running sums (TwoSum)
-#pragma unroll
-                    for (int k = 0; k < 11; ++k) {
-                        const float sm = __fadd_rn(acc[k], st[k]), bp = __fsub_rn(sm, acc[k]);
-                        cmp[k] = __fadd_rn(cmp[k], __fadd_rn(__fsub_rn(acc[k], __fsub_rn(sm, bp)), __fsub_rn(st[k], bp)));
-                        acc[k] = sm;
-                    }
-                    // y-inverse of conj(nu); its first pass into the buffer the last pass did not read
-                    C *fr = SinkShape<N, E>::LAST_READS_B1 ? b0 : b1;
-                    C *__restrict__ nu = a.NU;
-                    fft_regs_sink<N, E>(x, fr, fr == b0 ? b1 : b0, gl, 1 + g, TW,
-                                        [&](int q, C v) { nu[tiled(kx, q)] = mk<float>(v.x, -v.y); });
                 }
+            }
+            if (split) main_sync<NT>();   // the helpers' transforms are in place
+            if (lead && mine && ia >= 0) {
+                const float qx = float(kx) * sp.gx;
+                const float wgt = herm ? 1.f : 2.f;
+                float st[11];
+#pragma unroll
+                for (int k = 0; k < 11; ++k) st[k] = 0.f;
+                // part A at mode ky (register m) with the product's transform pv: mu = g lambda
+                // (stored), the gradient terms, conj(nu)
+                auto part_a = [&](int ky, int m, C pv) {
+                    const float qy = float(signed_k(ky, N)) * sp.gy;
+                    const float q2 = qx * qx + qy * qy;
+                    const float gg = 1.f / (1.f + sp.dt * poly5<float>(fp.O, q2));
+                    const C mu = cscale<float>(x3[ky], gg);
+                    x3[ky] = mu;
+                    const float dtM = fp.power > 0 ? sp.dt * poly5<float>(fp.M, q2) : 0.f;
+                    const float a_phi = wgt * sp.dt * (mu.x * ph[m].x + mu.y * ph[m].y);
+                    const float a_P = wgt * sp.dt * (mu.x * pv.x + mu.y * pv.y);
+                    float q2k = 1.f;
+#pragma unroll
+                    for (int k = 0; k < 5; ++k) {
+                        st[k] -= q2k * a_phi;
+                        st[5 + k] += q2k * a_P;
+                        q2k *= q2;
+                    }
+                    st[10] += wgt * (mu.x * xi[m].x + mu.y * xi[m].y);
+                    return mk<float>(mu.x * dtM, -mu.y * dtM);   // conj(nu)
+                };
+                if (split) {
+                    const C *P = WB + (size_t)(col + NG / 2) * S::WS + RES;
+#pragma unroll
+                    for (int m = 0; m < E; ++m) x[m] = part_a(gl + m * TPF, m, P[gl + m * TPF]);
+                } else {
+                    fft_regs_regs_m<N, E>(x, b0, b1, gl, 1 + g, TW, part_a);
+                }
+                // the step's terms into the thread's compensated running sums (TwoSum)
+#pragma unroll
+                for (int k = 0; k < 11; ++k) {
+                    const float sm = __fadd_rn(acc[k], st[k]), bp = __fsub_rn(sm, acc[k]);
+                    cmp[k] = __fadd_rn(cmp[k], __fadd_rn(__fsub_rn(acc[k], __fsub_rn(sm, bp)), __fsub_rn(st[k], bp)));
+                    acc[k] = sm;
+                }
+                // y-inverse of conj(nu); its first pass into the buffer the last pass did not read
+                // (split: both are free since the barrier after part B)
+                C *fr = SinkShape<N, E>::LAST_READS_B1 ? b0 : b1;
+                C *__restrict__ nu = a.NU;
+                fft_regs_sink<N, E>(x, fr, fr == b0 ? b1 : b0, gl, 1 + g, TW,
+                                    [&](int q, C v) { nu[tiled(kx, q)] = mk<float>(v.x, -v.y); });
             }
         }
     }
