@@ -358,3 +358,72 @@ def test_persistent_backward_pass(shape, noisy):
         assert rel(out[1][1], O.half(lam0)) < 1e-3
         k = 4 if noisy else 3
         assert np.max(np.abs(out[1][0][:k] - ref[:k]) / np.abs(ref[:k])) < 1e-3, (out[1][0], ref)
+
+
+def test_adjoint_workload_at_its_own_size():
+    # the adjoint workload itself: 2D Model B 256 x 256, 2000 steps (sqrt(n) = 45-step
+    # segments), 64-bin S(q) loss against the S(q) of a run with (a, b, K) =
+    # (-0.8, 1.2, 0.9) from the same seed and initial field.  The target comes from the
+    # FP64 GPU run (the FP64 GPU path matches the oracle to 1e-10 in the parity tests;
+    # a 2000-step oracle run at 256^2 takes about 30 s of one core).  The FP64 GPU
+    # adjoint is checked against central differences of the FP64 GPU forward run with
+    # Richardson extrapolation (h = 1e-4, h / 2) within 1e-6, the FP32 adjoint of the
+    # persistent path against the FP64 adjoint within 1e-3 (measured: 4e-5)
+    shape, dt, seed, n, nb = (256, 256), 0.01, 2405, 2000, 64
+    base = dict(a=-1.0, b=1.0, K=1.0, D=0.01)
+
+    def system(prec, **kw):
+        p = dict(base)
+        p.update(kw)
+        s = pss().model_b(shape, dt=dt, seed=seed, precision=prec, **p)
+        s.init_uniform(0, -0.1, 0.1)
+        return s
+
+    t = system("f64", a=-0.8, b=1.2, K=0.9)
+    t.step(n)
+    target, _, _ = t.structure_factor(0, nb)
+    t.close()
+
+    def loss(S, cnt):
+        sel = cnt > 0
+        return float(np.sum((S[sel] - target[sel]) ** 2) / sel.sum())
+
+    def lam_T(s):
+        # dJ/dphi_T on the half spectrum: (2 / nb)(S_b - S*_b) 2 / (N^2 cnt_b) phi_q in the bin of q
+        h = s.get_spectrum(0)
+        S, cnt, _ = s.structure_factor(0, nb)
+        sel = cnt > 0
+        coef = np.zeros(nb)
+        coef[sel] = 2.0 / sel.sum() * (S[sel] - target[sel]) * 2.0 / (shape[0] * shape[1] * cnt[sel])
+        ky = np.fft.fftfreq(shape[0]) * shape[0]
+        kx = np.arange(shape[1] // 2 + 1)
+        s2 = (2.0 * nb * ky[:, None] / shape[0]) ** 2 + (2.0 * nb * kx[None, :] / shape[1]) ** 2
+        b = np.ceil(np.sqrt(s2)).astype(int) - 1
+        ok = (s2 > 0) & (np.sqrt(s2) <= nb)
+        return np.where(ok, coef[np.clip(b, 0, nb - 1)], 0.0) * h
+
+    grads = {}
+    for prec in ("f64", "f32"):
+        s = system(prec)
+        if prec == "f32":
+            assert s.step_path == "persist2d"
+        s.adjoint_forward(n)
+        grads[prec], _ = s.adjoint_backward(lam_T(s).astype(np.complex128), 4)
+        s.close()
+
+    def J_gpu(**kw):
+        s = system("f64", **kw)
+        s.step(n)
+        S, cnt, _ = s.structure_factor(0, nb)
+        s.close()
+        return loss(S, cnt)
+
+    h = 1e-4
+
+    def central(name, step):
+        return (J_gpu(**{name: base[name] + step}) - J_gpu(**{name: base[name] - step})) / (2 * step)
+
+    for i, name in enumerate(["a", "b", "K", "D"]):
+        fd = (4.0 * central(name, h / 2) - central(name, h)) / 3.0
+        assert abs(grads["f64"][i] - fd) <= 1e-6 * abs(fd), (name, grads["f64"][i], fd)
+    assert np.max(np.abs(grads["f32"] - grads["f64"]) / np.abs(grads["f64"])) < 1e-3, (grads["f32"], grads["f64"])
