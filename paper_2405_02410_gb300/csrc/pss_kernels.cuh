@@ -994,33 +994,66 @@ __global__ void k_structure_factor(SysP<T> sp, double dx0, double dx1, double dx
     const double inv_ns = 1.0 / ((double)sp.nx * sp.ny * sp.nz);
     const double dxs[3] = {dx0, dx1, dx2};
     const int Ns[3] = {sp.nx, sp.ny, sp.nz};
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
-        const int kx = (int)(i % sp.hx);
-        const long long r2 = i / sp.hx;
-        const int ky = (int)(r2 % sp.ny), kz = (int)(r2 / sp.ny);
-        const int ks[3] = {kx, signed_k(ky, sp.ny), signed_k(kz, sp.nz)};
-        double s2 = 0.0, qq = 0.0;
-        for (int j = 0; j < 3; ++j) {
-            if (Ns[j] == 1) continue;
-            const double num = __dmul_rn(__dmul_rn(__dmul_rn(2.0, (double)nbins), (double)ks[j]), dx0);
-            const double tj = __ddiv_rn(num, __dmul_rn((double)Ns[j], dxs[j]));
-            s2 = __dadd_rn(s2, __dmul_rn(tj, tj));
-            const double qj = 6.283185307179586 * ks[j] / (Ns[j] * dxs[j]);
-            qq += qj * qj;
+    const int lane = threadIdx.x & 31;
+    double tS = 0.0, tQ = 0.0;   // the thread's share of the two totals
+    // the warps step through the modes 32 at a time (neighbouring kx of one row, a
+    // handful of bins at most): lanes in one bin are summed with shuffles and one
+    // lane adds the sums to the CTA's bins
+    for (long long i0 = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); i0 < n;
+         i0 += (long long)gridDim.x * blockDim.x) {
+        const long long i = i0 + lane;
+        int b = -1;
+        double vS = 0.0, vW = 0.0;
+        if (i < n) {
+            const int kx = (int)(i % sp.hx);
+            const long long r2 = i / sp.hx;
+            const int ky = (int)(r2 % sp.ny), kz = (int)(r2 / sp.ny);
+            const int ks[3] = {kx, signed_k(ky, sp.ny), signed_k(kz, sp.nz)};
+            double s2 = 0.0, qq = 0.0;
+            for (int j = 0; j < 3; ++j) {
+                if (Ns[j] == 1) continue;
+                const double num = __dmul_rn(__dmul_rn(__dmul_rn(2.0, (double)nbins), (double)ks[j]), dx0);
+                const double tj = __ddiv_rn(num, __dmul_rn((double)Ns[j], dxs[j]));
+                s2 = __dadd_rn(s2, __dmul_rn(tj, tj));
+                const double qj = 6.283185307179586 * ks[j] / (Ns[j] * dxs[j]);
+                qq += qj * qj;
+            }
+            const double s = __dsqrt_rn(s2);
+            if (s2 != 0.0 && s <= (double)nbins) {
+                b = (int)ceil(s) - 1;
+                const int row = sp.dim == 3 ? ky * sp.nz + kz : ky;
+                const cplx<T> z = tiles[((size_t)(kx / W) * sp.rows + row) * W + kx % W];
+                const double S = ((double)z.x * z.x + (double)z.y * z.y) * inv_ns;
+                vW = (kx == 0 || 2 * kx == sp.nx) ? 1.0 : 2.0;
+                vS = vW * S;
+                tS += vS;
+                tQ += vW * sqrt(qq) * S;
+            }
         }
-        if (s2 == 0.0) continue;
-        const double s = __dsqrt_rn(s2);
-        if (s > (double)nbins) continue;
-        const int b = (int)ceil(s) - 1;
-        const int row = sp.dim == 3 ? ky * sp.nz + kz : ky;
-        const cplx<T> z = tiles[((size_t)(kx / W) * sp.rows + row) * W + kx % W];
-        const double S = ((double)z.x * z.x + (double)z.y * z.y) * inv_ns;
-        const double wgt = (kx == 0 || 2 * kx == sp.nx) ? 1.0 : 2.0;
-        atomicAdd(&sacc[b], wgt * S);
-        atomicAdd(&sacc[nbins + b], wgt);
-        atomicAdd(&sacc[2 * nbins], wgt * S);
-        atomicAdd(&sacc[2 * nbins + 1], wgt * sqrt(qq) * S);
+        unsigned todo = __ballot_sync(0xffffffffu, b >= 0);
+        while (todo) {
+            const int src = __ffs(todo) - 1;
+            const int b0 = __shfl_sync(0xffffffffu, b, src);
+            const bool mine = b == b0;
+            double sv = mine ? vS : 0.0, wv = mine ? vW : 0.0;
+            for (int o = 16; o > 0; o >>= 1) {
+                sv += __shfl_xor_sync(0xffffffffu, sv, o);
+                wv += __shfl_xor_sync(0xffffffffu, wv, o);
+            }
+            if (lane == src) {
+                atomicAdd(&sacc[b0], sv);
+                atomicAdd(&sacc[nbins + b0], wv);
+            }
+            todo &= ~__ballot_sync(0xffffffffu, mine);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        tS += __shfl_xor_sync(0xffffffffu, tS, o);
+        tQ += __shfl_xor_sync(0xffffffffu, tQ, o);
+    }
+    if (lane == 0) {
+        if (tS != 0.0) atomicAdd(&sacc[2 * nbins], tS);
+        if (tQ != 0.0) atomicAdd(&sacc[2 * nbins + 1], tQ);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < 2 * nbins + 2; i += blockDim.x)
@@ -1206,8 +1239,9 @@ template <typename T>
 cudaError_t launch_structure_factor(const SysP<T> &sp, const double dx[3], const cplx<T> *tiles, int nbins,
                                     double *acc, cudaStream_t st) {
     const long long n = (long long)sp.nz * sp.ny * sp.hx;
+    // at most 512 CTAs: each adds its 2 nbins + 2 sums to the same global words
     long long blocks = (n + 255) / 256;
-    if (blocks > 4096) blocks = 4096;
+    if (blocks > 512) blocks = 512;
     const size_t smem = sizeof(double) * (size_t)(2 * nbins + 2);
     cudaError_t e = ensure_smem(k_structure_factor<T>, smem);
     if (e != cudaSuccess) return e;
