@@ -169,7 +169,8 @@ __device__ __forceinline__ uint32_t full_parity(int n, int first) {
 }
 __device__ __forceinline__ uint32_t empty_parity(int n) { return (uint32_t)(((n - 2 - (n & 1)) >> 1) & 1); }
 
-// derivative factor i q of a mode (q = 0 at a Nyquist index, reading R14)
+// derivative factor i q of a mode; q = 0 at a Nyquist index, so that the
+// derivative of a real field stays real
 __device__ __forceinline__ float dq(int k, int n, float g) { return 2 * k == n ? 0.f : fmul(float(signed_k(k, n)), g); }
 
 template <int N, int E, int NNW, int MODE>

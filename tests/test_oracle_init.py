@@ -1,5 +1,6 @@
-"""Pins of the oracle's initial field (reading R6 of the paper's "small random
-perturbation", sections "Example" and "Writing models").
+"""Pins of the oracle's initial field: the paper's "small random perturbation"
+(sections "Example" and "Writing models"), read as a uniform field drawn from
+the same counter-based generator as the noise.
 
 phi_x = lo + (hi - lo) u_x with u_x = ((w >> 8) + 0.5) / 2^24, w the first word
 of Philox4x32-10(counter = (site, 0, field_id, 1), key = seed).  The affine map,
