@@ -40,6 +40,25 @@ def test_whole_job_rate_single_rank():
     assert t == 250.0 and value == pytest.approx(4e6)
 
 
+def test_kernel_source_hash_follows_code_not_comments(tmp_path):
+    # the traffic record stays valid across comment edits and is dropped by a code change
+    b = _bench()
+    csrc = tmp_path / "paper_2405_02410_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    src = csrc / "k.cuh"
+    old_root = b.ROOT
+    try:
+        b.ROOT = str(tmp_path)
+        src.write_text("int f(int x) {  // one\n    return x + 1;\n}\n")
+        h0 = b.kernel_source_hash()
+        src.write_text("// a new header line\nint f(int x) {  // two\n\n    return x + 1; /* note */\n}\n")
+        assert b.kernel_source_hash() == h0
+        src.write_text("int f(int x) {\n    return x + 2;\n}\n")
+        assert b.kernel_source_hash() != h0
+    finally:
+        b.ROOT = old_root
+
+
 def test_tune_report_parsing():
     from paper_2405_02410_gb300 import pss
     rep = pss.parse_tune_report("path=1 trials=25 skipped=0 initial_ms=0.015071 tuned_ms=0.0149 "
