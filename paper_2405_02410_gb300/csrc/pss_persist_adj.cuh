@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(P2AdjShape<N, E>::THREADS, 1) k2p_adj(const P2
     if (t == 0) {
         s_abort = ld_relaxed_gpu(&a.gs->abort) ? 1 : 0;   // an earlier launch gave up
     }
-    // element ky of column kx in a tiled array; of a column-major one
+    // element ky of column kx in a tiled array ([kx / 4][ky][kx % 4])
     auto tiled = [&](int kx, int ky) { return ((size_t)(kx >> 2) * N + ky) * 4 + (kx & 3); };
     // the adjoint field of the CTA's columns (zero past Nx/2): all of a thread's loads
     // first, then the stores
