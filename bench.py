@@ -714,11 +714,14 @@ def run_gpu(args):
         chunks.append(min(INTERVAL, left))
         left -= chunks[-1]
     # warm-up: W steps, then one untimed run of every interval length the timed
-    # region uses, so that each CUDA graph it replays (whole graphs of graph_steps
-    # steps and one of the remainder) is captured and instantiated before timing
+    # region uses, each after an L2 flush as in the timed region, so that each CUDA
+    # graph it replays (whole graphs of graph_steps steps and one of the remainder)
+    # is captured and instantiated before timing and the flush buffer has been
+    # written before (its first write in a process slows the launch after it)
     with torch.cuda.stream(stream):
         s.step(args.warmup)
         for c in sorted(set(chunks)):
+            flush.fill_(1.0)
             s.step(c)
     torch.cuda.synchronize()
     warm_steps = args.warmup + sum(sorted(set(chunks)))
@@ -875,7 +878,8 @@ def run_gpu(args):
                    "l2": "flushed (512 MiB write) before every 1000-step interval; the ~11 MB working set is "
                          "L2-resident inside an interval",
                    "warm_up": f"{warm_steps} untimed steps ({args.warmup} + one run of each timed interval "
-                              "length: every graph the timed region replays is captured before it)",
+                              "length after an L2 flush, as in the timed region: every graph the timed region "
+                              "replays is captured before it)",
                    "graph_steps": ((tuning or {}).get("graph_steps") or 16),
                    "autotuned": tuning},
         "roofline": {"bound": "hbm", "kernel": dom_kernel, "achieved": achieved,
