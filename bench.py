@@ -331,6 +331,7 @@ def ensemble_measurement(pss, torch, stream, steps=200, tune=True, rank=0, world
     stepped from one CUDA graph.  With world > 1 the instances are split over the ranks by cost
     (sites x steps); each rank runs its share, the time is the slowest rank's, and the per-instance
     S(q) (64 bins, FP64) are gathered and averaged per side in instance order."""
+    import numpy as np
     from paper_2405_02410_gb300 import ensemble as E
     spec = E.recipe(n=512, steps=steps)
     idx = E.share(spec, rank, world)
@@ -372,7 +373,12 @@ def ensemble_measurement(pss, torch, stream, steps=200, tune=True, rank=0, world
            "partition": "instances split by sites x steps, longest first onto the least-loaded rank",
            "instances_per_rank": [len(x) for x in E.partition([spec.cost(i) for i in range(len(spec))], world)],
            "this_rank_ms": local_ms / steps,
-           "S_q_mean_by_side": {str(k): v.tolist() for k, v in merged.items()},
+           # per side: the first bins and a digest of all 64 FP64 bin means (the full arrays
+           # would push the line's other results out of a short tail of stdout)
+           "S_q_mean_by_side": {str(k): {"bins_1_to_4": [float(x) for x in v[:4]], "sum": float(np.sum(v)),
+                                         "sha256_16": hashlib.sha256(np.ascontiguousarray(v, dtype=np.float64)
+                                                                     .tobytes()).hexdigest()[:16]}
+                                for k, v in merged.items()},
            "S_q_after_steps": warm + steps,
            "autotuned": {str(k): v for k, v in tuning.items()} if tune else None,
            "_probes": probes}
@@ -680,6 +686,34 @@ def adjoint_measurement(pss, torch, stream, n=2000, shape=(256, 256), nbins=64, 
             "adjoint_ms": t_bwd * 1e3, "adjoint_over_forward": t_bwd / t_plain, "autotuned": tuning}
 
 
+def summary_of(line):
+    """The line's main results in a few hundred characters."""
+    ex = line.get("extra", {})
+
+    def pick(d, *keys):
+        return {k: (float(f"{d[k]:.5g}") if isinstance(d.get(k), float) else d.get(k)) for k in keys if k in d}
+
+    out = {"us_per_step": round(line["ms_per_step"] * 1e3, 3), "site_steps_per_s": line["value"],
+           "roofline_frac": round(line["roofline"]["frac"], 4), "e2e": line["e2e"]["value"]}
+    if "model_ab_256cubed" in ex:
+        out["model_ab_256cubed"] = pick(ex["model_ab_256cubed"], "ms_per_step_two_fields",
+                                        "site_steps_per_s_per_field", "hbm_frac_of_measured")
+    if "ensemble_512" in ex:
+        out["ensemble_512"] = pick(ex["ensemble_512"], "ms_per_step", "site_steps_per_s", "speedup_vs_sequential")
+    if "adjoint_256" in ex:
+        out["adjoint_256"] = pick(ex["adjoint_256"], "adjoint_ms", "forward_plain_ms", "adjoint_over_forward")
+    v = ex.get("variants", {})
+    if "kpz_1024" in v:
+        out["kpz_1024"] = pick(v["kpz_1024"], "ms_per_step", "over_model_b_step")
+    if "cufft_step_1024" in ex:
+        out["cufft_1024"] = pick(ex["cufft_step_1024"], "ms_per_step", "ours_over_cufft")
+    par = line.get("parity_vs_fp64_oracle")
+    if par:
+        rels = [x for d in par.values() for k, x in d.items() if k.startswith("rel_l2")]
+        out["parity_max_rel_l2"] = max(rels) if rels else None
+    return out
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -912,6 +946,7 @@ def run_gpu(args):
     s.close()
     s2.close()
     if rank == 0:
+        line["summary"] = summary_of(line)   # last, so that a short tail of stdout shows it
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

@@ -59,6 +59,27 @@ def test_kernel_source_hash_follows_code_not_comments(tmp_path):
         b.ROOT = old_root
 
 
+def test_line_summary_is_short_and_complete():
+    # the JSON line ends with a summary of its main results, short enough for a tail of stdout
+    import json
+    line = {"ms_per_step": 0.0115, "value": 9.1e10, "roofline": {"frac": 0.285}, "e2e": {"value": 3.5e10},
+            "extra": {"model_ab_256cubed": {"ms_per_step_two_fields": 0.3646, "site_steps_per_s_per_field": 9.2e10,
+                                            "hbm_frac_of_measured": 0.449},
+                      "ensemble_512": {"ms_per_step": 0.455, "site_steps_per_s": 9.46e10, "speedup_vs_sequential": 8.9,
+                                       "S_q_mean_by_side": {"64": [0.0] * 64}},
+                      "adjoint_256": {"adjoint_ms": 30.9, "forward_plain_ms": 11.0, "adjoint_over_forward": 2.8},
+                      "variants": {"kpz_1024": {"ms_per_step": 0.0156, "over_model_b_step": 1.45}},
+                      "cufft_step_1024": {"ms_per_step": 0.0641, "ours_over_cufft": 5.96}},
+            "parity_vs_fp64_oracle": {"a": {"steps": 63, "rel_l2": 1.5e-6},
+                                      "b": {"rel_l2_model_a": 2.9e-7, "rel_l2_model_b": 6.6e-6}}}
+    sm = _bench().summary_of(line)
+    assert sm["us_per_step"] == 11.5 and sm["roofline_frac"] == 0.285
+    assert sm["model_ab_256cubed"]["hbm_frac_of_measured"] == 0.449
+    assert sm["adjoint_256"]["adjoint_over_forward"] == 2.8
+    assert sm["parity_max_rel_l2"] == 6.6e-6
+    assert "S_q_mean_by_side" not in json.dumps(sm) and len(json.dumps(sm)) < 1000
+
+
 def test_tune_report_parsing():
     from paper_2405_02410_gb300 import pss
     rep = pss.parse_tune_report("path=1 trials=25 skipped=0 initial_ms=0.015071 tuned_ms=0.0149 "
