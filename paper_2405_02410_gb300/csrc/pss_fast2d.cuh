@@ -630,7 +630,7 @@ __device__ __forceinline__ void noise_range(const SysP<float> &sp, const FieldP<
 }
 
 template <int N, int E, bool TILED, bool ADJ>
-__global__ void __launch_bounds__(E == 32 ? 512 : 1024) k2_row(const RowArgs<float> a) {
+__global__ void __launch_bounds__(E == 32 || TILED ? 512 : 1024) k2_row(const RowArgs<float> a) {
     using C = float2;
     using S = GShape<N, E>;
     constexpr int TPF = S::TPF;
@@ -795,7 +795,7 @@ __global__ void __launch_bounds__(E == 32 ? 512 : 1024) k2_row(const RowArgs<flo
     // goes to W's first pass in registers and W lands in the group's first
     // buffer; the radix-16 kernels (64 registers per thread at 1024 threads)
     // pass u through shared memory and W lands in the second buffer.
-    constexpr bool CHAIN = E != 16;
+    constexpr bool CHAIN = E != 16 || TILED;
     if constexpr (!CHAIN) {
         C *b0 = WBUF + Row2Smem<N, E>::base(g, TILED), *b1 = b0 + S::BUF;
         const C *src = b1;
@@ -901,7 +901,7 @@ template <int N, int E, bool TILED, bool ADJ>
 cudaError_t launch_row2_ne(const RowArgs<float> &a, int nslots, cudaStream_t st) {
     const int nw = a.G, threads = nw * GShape<N, E>::TPF + 32 * a.noise_warps;
     if (nw < 1 || nw > 8 || (nw & (nw - 1)) || a.sp.rows % (2 * nw) || a.noise_warps < 0 ||
-        threads > (E == 32 ? 512 : 1024) || (TILED && a.noise) || a.noise_ctas < 0 ||
+        threads > (E == 32 || TILED ? 512 : 1024) || (TILED && a.noise) || a.noise_ctas < 0 ||
         (a.noise_ctas > 0 && !a.noise) || a.noise_share < 0 || a.noise_share > 64)
         return cudaErrorInvalidConfiguration;
     // ROW_ADJ also stages the CTA's 2 nw real rows
