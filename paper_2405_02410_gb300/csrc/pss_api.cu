@@ -438,12 +438,19 @@ int p2_blocks(const pss_system *s) {
     return std::min(s->num_sms, std::max(lo, want));
 }
 
+// Defaults of the FP32 2D two-kernel path.  A batch of 8 or more instances is
+// throughput-bound rather than latency-bound; measured on GB300 (us per step,
+// single-instance defaults -> batch defaults): 256^2 x 8 11.4 -> 9.5, x 32
+// 36.4 -> 22.3, x 125 144 -> 77; 512^2 x 8 35.9 -> 25.3, x 32 130 -> 90,
+// x 123 472 -> 325 (and 256^2 x 2 6.5 -> 8.0, hence the threshold).
+bool big_batch(const pss_system *s) { return s->dim == 2 && s->batch >= 8 && s->nx <= 512; }
 int col2_radix(const pss_system *s) {
-    const int r = s->tune_col2_radix ? s->tune_col2_radix : (s->ny >= 512 ? 16 : 8);
+    const int r = s->tune_col2_radix ? s->tune_col2_radix : ((s->ny >= 512 || big_batch(s)) ? 16 : 8);
     return r == 32 && s->ny != 1024 ? 16 : r;   // radix-32 passes serve 1024 points only
 }
 int row2_radix(const pss_system *s) {
-    const int r = s->tune_row2_radix ? s->tune_row2_radix : ((s->dim == 3 || s->nx >= 512) ? 16 : 8);
+    const int r = s->tune_row2_radix ? s->tune_row2_radix
+                                     : ((s->dim == 3 || (s->nx >= 512 && !big_batch(s))) ? 16 : 8);
     return r == 32 && s->nx != 1024 ? 16 : r;
 }
 // CTA size limits of the two kernels (their launch bounds leave radix-32
@@ -453,13 +460,13 @@ int row2_max_threads(int E) { return E == 32 ? 512 : 1024; }
 int col2_warps(const pss_system *s) {
     const int E = col2_radix(s);
     const int fft_warps = 4 * s->ny / E / 32;
-    const int want = s->tune_col2_warps > 0 ? s->tune_col2_warps : 8;
+    const int want = s->tune_col2_warps > 0 ? s->tune_col2_warps : (big_batch(s) && s->ny == 256 ? 4 : 8);
     return std::max(1, std::min(want, col2_max_threads(E) / 32 - fft_warps));
 }
 int row2_noise_warps(const pss_system *s, int pairs) {
     const int E = row2_radix(s);
     const int fft_warps = pairs * s->nx / E / 32;
-    const int want = s->tune_row2_noise > 0 ? s->tune_row2_noise : 16;
+    const int want = s->tune_row2_noise > 0 ? s->tune_row2_noise : (big_batch(s) && s->nx == 256 ? 8 : 16);
     return std::max(1, std::min(want, row2_max_threads(E) / 32 - fft_warps));
 }
 bool any_noisy(const pss_system *s) {
@@ -470,7 +477,7 @@ bool any_noisy(const pss_system *s) {
 // row pairs per CTA: a power of two with at most 512 threads per CTA
 int row2_pairs(const pss_system *s) {
     const int tpf = s->nx / row2_radix(s);
-    const int nw = s->tune_row2_pairs > 0 ? s->tune_row2_pairs : 4;
+    const int nw = s->tune_row2_pairs > 0 ? s->tune_row2_pairs : (big_batch(s) ? 8 : 4);
     int p = 1;
     while (p * tpf < 32) p *= 2;   // whole warps of transform threads
     while (p * 2 <= nw && p * 2 <= 8 && p * 2 * tpf <= 512) p *= 2;
